@@ -1,0 +1,247 @@
+"""Pins of the oracle's model equations, stencils and RK4 (Sec. 2.1-2.3)."""
+import math
+
+import numpy as np
+import pytest
+from scipy.integrate import quad
+from scipy.optimize import minimize_scalar
+
+from oracle import acm
+from oracle.adapt import Solver
+from oracle.forest import Forest
+from oracle.sync import sync
+from tests.golden_util import load_golden
+
+G = load_golden("paper_constants.txt")
+
+
+def uniform(Bs, J, ph, ic, nroot=(1, 1, 1), L=1.0, mask=None, sponge=None):
+    fo = Forest(nroot=nroot, root_len=L, Bs=Bs, Jmin=J, Jmax=J,
+                max_blocks=int(np.prod(nroot)) * 8 ** J)
+    fo.init_uniform(J)
+    S = Solver(fo, ph, ic=ic, mask=mask, sponge=sponge)
+    S.eval_ic()
+    S.eval_mask()
+    return S
+
+
+def R4(z):
+    return 1 + z + z * z / 2 + z ** 3 / 6 + z ** 4 / 24
+
+
+def test_tam_webb_a3_is_the_dispersion_optimum():
+    # Tam & Webb choose the free coefficient of the 7-point 4th-order family by minimising the
+    # integrated dispersion error over kh in [0, pi/2]
+    def E(a3):
+        a1, a2 = 2 / 3 + 5 * a3, -1 / 12 - 4 * a3
+        return quad(lambda k: (k - 2 * (a1 * math.sin(k) + a2 * math.sin(2 * k) + a3 * math.sin(3 * k))) ** 2,
+                    0, math.pi / 2, epsabs=1e-15, epsrel=1e-13)[0]
+    r = minimize_scalar(E, bounds=(0.0, 0.1), method="bounded", options={"xatol": 1e-14})
+    assert abs(r.x - acm.TAM_WEBB_A3) < 1e-9
+    assert abs(acm.TAM_WEBB_A3 - 0.02651995) < 5e-9     # published to 8 digits
+
+
+@pytest.mark.parametrize("scheme", ["tam_webb", "classic"])
+def test_first_derivative_is_fourth_order_consistent(scheme):
+    a = acm.d1_coeffs(scheme)
+    assert abs(sum(2 * j * a[j - 1] for j in (1, 2, 3)) - 1.0) < 1e-15
+    assert abs(sum(j ** 3 * a[j - 1] for j in (1, 2, 3))) < 1e-15
+    if scheme == "classic":
+        assert np.allclose(a, (8 / 12, -1 / 12, 0.0), atol=1e-16)
+
+
+def _sine_block_grid(Bs, J, k, axis):
+    ph = acm.Physics(scheme="tam_webb")
+    def ic(X, Y, Z):
+        c = (X, Y, Z)[axis]
+        z = np.zeros_like(X)
+        return np.stack([np.sin(k * c), z, z.copy(), z.copy()])
+    S = uniform(Bs, J, ph, ic)
+    ext = sync(S.fo, S.U, 3, "faces")
+    return S, ext
+
+
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_modified_wavenumbers(axis):
+    Bs, J = 9, 1
+    k = 2 * math.pi * 3
+    S, ext = _sine_block_grid(Bs, J, k, axis)
+    fo = S.fo
+    h = fo.h(J)
+    a = acm.d1_coeffs("tam_webb")
+    kt1 = 2 / h * sum(a[j - 1] * math.sin(j * k * h) for j in (1, 2, 3))
+    kt2 = (30 - 32 * math.cos(k * h) + 2 * math.cos(2 * k * h)) / (12 * h * h)
+    for leaf, s in fo.leaves.items():
+        X, Y, Z = acm.block_coords(fo, leaf)
+        c = (X, Y, Z)[axis]
+        d1 = acm.d1(ext[s, 0], 3, fo.M, h, axis, a)
+        d2 = acm.d2(ext[s, 0], 3, fo.M, h, axis)
+        assert np.abs(d1 - kt1 * np.cos(k * c)).max() < 1e-12 * kt1
+        assert np.abs(d2 + kt2 * np.sin(k * c)).max() < 1e-12 * kt2
+
+
+def test_stencils_converge_at_fourth_order():
+    k = 2 * math.pi
+    e1, e2 = [], []
+    for J in (1, 2, 3):
+        S, ext = _sine_block_grid(9, J, k, 0)
+        fo = S.fo
+        h = fo.h(J)
+        a = acm.d1_coeffs("tam_webb")
+        m1 = m2 = 0.0
+        for leaf, s in list(fo.leaves.items())[:8]:
+            X, _, _ = acm.block_coords(fo, leaf)
+            m1 = max(m1, np.abs(acm.d1(ext[s, 0], 3, fo.M, h, 0, a) - k * np.cos(k * X)).max())
+            m2 = max(m2, np.abs(acm.d2(ext[s, 0], 3, fo.M, h, 0) + k * k * np.sin(k * X)).max())
+        e1.append(m1)
+        e2.append(m2)
+    s1 = np.polyfit(np.log([1, 0.5, 0.25]), np.log(e1), 1)[0]
+    s2 = np.polyfit(np.log([1, 0.5, 0.25]), np.log(e2), 1)[0]
+    assert 3.7 < s1 < 4.3 and 3.7 < s2 < 4.3
+
+
+def test_rk4_amplifies_a_diffusive_mode_by_the_rk4_polynomial():
+    # w = A sin(kx), u = v = p = 0: convection and divergence vanish identically, so one RK4
+    # step multiplies w by R(dt lambda), lambda = -nu * (modified wavenumber)^2 of the D2 stencil
+    Bs, J, nu, k = 9, 1, 0.05, 2 * math.pi * 2
+    ph = acm.Physics(nu=nu, c0=1.0, C_gamma=0.0)
+    S = uniform(Bs, J, ph, lambda X, Y, Z: np.stack([0 * X, 0 * X, 0.7 * np.sin(k * X), 0 * X]))
+    h = S.fo.h(J)
+    lam = -nu * (30 - 32 * math.cos(k * h) + 2 * math.cos(2 * k * h)) / (12 * h * h)
+    dt = 0.1 * h * h / nu
+    W0 = S.U[:, 2].copy()
+    S.rk4(dt)
+    s = S.slots()
+    assert np.abs(S.U[s, 2] - R4(dt * lam) * W0[s]).max() < 1e-14
+    assert np.abs(S.U[s][:, [0, 1, 3]]).max() == 0.0
+
+
+def test_dashpot_penalization_and_sponge_decay_rates():
+    Bs, J = 9, 1
+    # dashpot: constant p decays as dp/dt = -C_gamma p
+    ph = acm.Physics(nu=0.0, c0=3.0, C_gamma=2.0)
+    S = uniform(Bs, J, ph, lambda X, Y, Z: np.stack([0 * X, 0 * X, 0 * X, 0 * X + 0.8]))
+    dt = 0.01
+    S.rk4(dt)
+    s = S.slots()
+    assert np.abs(S.U[s, 3] - 0.8 * R4(-2.0 * dt)).max() < 1e-15
+    # obstacle penalization: chi = 1, constant u decays as du/dt = -u / C_eta (u_s = 0)
+    ph = acm.Physics(nu=0.0, c0=3.0, C_gamma=0.0, C_eta=0.05)
+    S = uniform(Bs, J, ph, lambda X, Y, Z: np.stack([0 * X + 1.0, 0 * X - 0.5, 0 * X + 0.25, 0 * X]),
+                mask=lambda X, Y, Z: np.ones_like(X))
+    S.rk4(dt)
+    for f, v in enumerate((1.0, -0.5, 0.25)):
+        assert np.abs(S.U[s, f] - v * R4(-dt / 0.05)).max() < 1e-15
+    assert np.abs(S.U[s, 3]).max() == 0.0
+    # sponge: chi_sp = 1 relaxes (u, p) towards (u_inf, p_inf) at rate 1/C_sp
+    uinf, pinf, Csp = (1.0, 0.5, 0.0), 0.3, 0.2
+    ph = acm.Physics(nu=0.0, c0=3.0, C_gamma=0.0, C_sp=Csp, u_inf=uinf, p_inf=pinf)
+    S = uniform(Bs, J, ph, lambda X, Y, Z: np.stack([0 * X, 0 * X, 0 * X, 0 * X]),
+                sponge=lambda X, Y, Z: np.ones_like(X))
+    S.rk4(dt)
+    for f, v in enumerate(uinf + (pinf,)):
+        assert np.abs(S.U[s, f] - v * (1 - R4(-dt / Csp))).max() < 1e-15
+
+
+def test_taylor_green_initial_divergence_and_energy_rate():
+    Bs, J, nu = 17, 1, 1e-2
+    ph = acm.Physics(nu=nu, c0=10.0, C_gamma=1.0)
+    S = uniform(Bs, J, ph, lambda X, Y, Z: acm.ic_taylor_green(X, Y, Z))
+    K = S.rhs(S.U.copy())
+    s = S.slots()
+    # the discrete divergence of the Taylor-Green field vanishes (both terms carry the same
+    # modified wavenumber), so dp/dt = 0 at t = 0
+    assert np.abs(K[s, 3]).max() < 1e-11
+    # discrete energy rate: sum u . rhs_u = -3 nu k2~ sum |u|^2 minus the convective defect,
+    # which is O(h^4): check to 1 % at 32 points per period
+    fo = S.fo
+    h = fo.h(J)
+    k = 2 * math.pi
+    k2 = (30 - 32 * math.cos(k * h) + 2 * math.cos(2 * k * h)) / (12 * h * h)
+    M = fo.M
+    u = S.U[s][:, :3, :M, :M, :M]
+    r = K[s][:, :3, :M, :M, :M]
+    dE = float((u * r).sum()) * h ** 3
+    E0 = 0.5 * float((u * u).sum()) * h ** 3
+    assert abs(dE - (-6 * nu * k2 * E0)) < 0.01 * abs(6 * nu * k2 * E0)
+    assert abs(E0 - 0.125) < 1e-12          # exact midpoint sum of sin^2 cos^2 cos^2 terms
+
+
+def test_time_step_rule():
+    assert G["cfl"] == 1.0 and G["cfl_eta"] == 1.0 and G["cfl_nu"] == 0.25
+    ph = acm.Physics(nu=1e-2, c0=10.0, cfl=0.5)
+    # Taylor-Green at level 2 (h = 1/64), |u|_max = 1
+    assert abs(acm.time_step(ph, 1.0, 1 / 64, False) - 0.5 / 64 / (1 + math.sqrt(101))) < 1e-18
+    ph = acm.Physics(nu=1e-3, c0=10.0, C_eta=1e-4, cfl=0.5)
+    assert acm.time_step(ph, 0.0, 1 / 64, True) == 1e-4           # penalization limit
+    assert acm.time_step(ph, 0.0, 1 / 64, False) == 0.5 / 64 / 10  # no mask: CFL limit
+    ph = acm.Physics(nu=1.0, c0=10.0, cfl=0.5)
+    assert acm.time_step(ph, 0.0, 1 / 64, False) == 0.25 / 64 ** 2  # viscous limit
+
+
+def test_force_and_energy_quadrature_count_each_point_once():
+    U0 = (0.3, -0.2, 0.7)
+    ph = acm.Physics(C_eta=1e-3)
+    S = uniform(9, 1, ph, lambda X, Y, Z: np.stack([0 * X + U0[0], 0 * X + U0[1], 0 * X + U0[2], 0 * X]),
+                nroot=(2, 1, 1), L=0.5, mask=lambda X, Y, Z: np.ones_like(X))
+    F, E = S.diagnostics()
+    vol = 1.0 * 0.5 * 0.5
+    assert np.allclose(F, np.array(U0) * vol / 1e-3, rtol=1e-13)
+    assert abs(E - 0.5 * sum(v * v for v in U0) * vol) < 1e-13
+
+
+def test_sphere_mask_profile():
+    X = np.array([1.0, 1.25, 1.0 + 0.25 + 0.1, 1.0])
+    chi = acm.sphere_mask(X, np.ones(4), np.ones(4), (1, 1, 1), 0.25, 0.01)
+    assert chi[1] == 0.5 and chi[0] == 1.0 and chi[2] < 1e-8
+
+
+@pytest.mark.slow
+def test_acoustic_pulse_travels_at_c0():
+    # nu = 0, C_gamma = 0, small amplitude: p_tt = c0^2 lap p; for a radial initial pulse f(r)
+    # with u = 0 the solution is p = [(r - ct) f(r - ct) + (r + ct) f(r + ct)] / (2r)
+    A, sig, c0 = 1e-4, 0.08, 2.0
+    ph = acm.Physics(nu=0.0, c0=c0, C_gamma=0.0)
+    S = uniform(17, 2, ph, lambda X, Y, Z: acm.ic_pulse(X, Y, Z, (0.5, 0.5, 0.5), sig, A, (1, 1, 1)))
+    h = S.fo.h(2)
+    dt = 0.5 * h / c0
+    nsteps = 16
+    for _ in range(nsteps):
+        S.rk4(dt)
+    t = nsteps * dt
+    f = lambda r: A * np.exp(-r * r / (sig * sig))
+    err = 0.0
+    for leaf, s in S.fo.leaves.items():
+        X, Y, Z = acm.block_coords(S.fo, leaf)
+        r = np.sqrt((X - 0.5) ** 2 + (Y - 0.5) ** 2 + (Z - 0.5) ** 2)
+        r = np.maximum(r, 1e-9)
+        ex = ((r - c0 * t) * f(r - c0 * t) + (r + c0 * t) * f(r + c0 * t)) / (2 * r)
+        err = max(err, float(np.abs(S.U[s, 3] - ex).max()))
+    assert err < 0.02 * A
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("scheme,T,lo", [("classic", 0.008, 2 ** 3.6), ("tam_webb", 0.016, 2 ** 3.5)])
+def test_full_scheme_self_convergence_is_fourth_order(scheme, T, lo):
+    """Taylor-Green on 16, 32, 64 points per period with dt proportional to h: the ratio of
+    successive differences is 2^4 for a 4th-order scheme in space and time (Sec. 2.3, eq.
+    discretization_error_4th; the paper fits a slope of 4.04).  The Tam-Webb dispersion error
+    changes sign over kh, so at these coarse resolutions its ratio sits a little lower."""
+    ph = acm.Physics(nu=1e-2, c0=10.0, C_gamma=1.0, scheme=scheme)
+    sol = []
+    for J in (0, 1, 2):
+        S = uniform(17, J, ph, lambda X, Y, Z: acm.ic_taylor_green(X, Y, Z))
+        dt = 0.004 / 2 ** J
+        for _ in range(int(round(T / dt))):
+            S.rk4(dt)
+        fo = S.fo
+        N = fo.npoints(J)
+        glob = np.zeros((4, N[2], N[1], N[0]))
+        M = fo.M
+        for (L, gx, gy, gz), s in fo.leaves.items():
+            glob[:, gz * M:(gz + 1) * M, gy * M:(gy + 1) * M, gx * M:(gx + 1) * M] = S.U[s][:, :M, :M, :M]
+        st = 2 ** J
+        sol.append(glob[:, ::st, ::st, ::st])
+    ratio = np.abs(sol[0] - sol[1]).max() / np.abs(sol[1] - sol[2]).max()
+    assert lo < ratio < 2 ** 4.4, ratio
+    assert G["fd_slope"] > 3.9

@@ -1,0 +1,105 @@
+"""Pins of the oracle's refine / coarsen cycle and initial grid (Sec. 3.3, 3.5)."""
+import math
+
+import numpy as np
+
+from oracle import acm
+from oracle.adapt import Solver
+from oracle.forest import Forest
+from paper_1912_05371_gb300.workloads import cubic_coefficients, random_graded_leaves
+
+
+def _poly(C, X, Y, Z):
+    return np.stack([sum(C[f, a, b, c] * X ** a * Y ** b * Z ** c
+                         for a in range(4) for b in range(4) for c in range(4)) for f in range(4)])
+
+
+def _solver(leaves, nroot=(2, 2, 2), Jmin=1, Jmax=3, ic=None, **kw):
+    fo = Forest(nroot=nroot, root_len=1.0, Bs=9, Jmin=Jmin, Jmax=Jmax, max_blocks=1 << 14)
+    fo.set_leaves(leaves)
+    S = Solver(fo, acm.Physics(), ic=ic, **kw)
+    S.eval_ic()
+    S.eval_mask()
+    return S
+
+
+def _interior_field(S):
+    return {leaf: S.U[s].copy() for leaf, s in S.fo.leaves.items()}
+
+
+def test_refine_predicts_cubics_exactly_and_coarsen_restores():
+    C = cubic_coefficients(11)
+    leaves = random_graded_leaves(4, nroot=(2, 2, 2), J0=1, Jmax=2, n_target=80)
+    S = _solver(leaves, ic=lambda X, Y, Z: _poly(C, X, Y, Z), Jmax=3, eps=1e3, dealias=False)
+    before = _interior_field(S)
+    S.refine_all()
+    assert S.fo.is_graded() and S.fo.covers_domain_exactly()
+    M = S.fo.M
+    nchk = 0
+    for leaf, s in S.fo.leaves.items():
+        X, Y, Z = acm.block_coords(S.fo, leaf)
+        lo = min(X.min(), Y.min(), Z.min())
+        hi = max(X.max(), Y.max(), Z.max())
+        if lo < 0.3 or hi > 1.7:
+            continue                    # the parent's stencils would cross the periodic seam
+        assert np.abs(S.U[s] - _poly(C, X, Y, Z)).max() < 1e-11
+        nchk += 1
+    assert nchk > 10
+    # uniform level-2 grid, J_min = 2: with every detail below a huge threshold, coarsening
+    # undoes the refinement exactly (R o P = Id)
+    fo = Forest(nroot=(1, 1, 1), root_len=1.0, Bs=9, Jmin=2, Jmax=3, max_blocks=1 << 12)
+    fo.init_uniform(2)
+    S = Solver(fo, acm.Physics(), ic=lambda X, Y, Z: _poly(C, X, Y, Z), eps=1e3, dealias=False)
+    S.eval_ic()
+    before = _interior_field(S)
+    S.refine_all()
+    assert {l[0] for l in fo.leaves} == {3}
+    S.coarsen()
+    assert set(S.fo.leaves) == set(before)
+    for leaf, s in S.fo.leaves.items():
+        assert np.array_equal(S.U[s], before[leaf])
+
+
+def test_coarsen_refine_error_below_threshold_and_grid_invariants():
+    eps = 2e-3
+    leaves = random_graded_leaves(5, nroot=(1, 1, 1), J0=1, Jmax=3, n_target=120)
+    ic = lambda X, Y, Z: np.stack([np.sin(2 * math.pi * X) * np.cos(2 * math.pi * Y),
+                                   np.cos(2 * math.pi * Z), np.sin(4 * math.pi * (X + Y)) * 0.3,
+                                   np.exp(-((X - 0.5) ** 2 + (Y - 0.5) ** 2 + (Z - 0.5) ** 2) / 0.01)])
+    S = _solver(leaves, nroot=(1, 1, 1), ic=ic, eps=eps, dealias=False)
+    ref = _interior_field(S)
+    norms = S.norms()
+    S.coarsen(max_passes=1)          # one pass: merged blocks are one level coarser
+    fo = S.fo
+    assert fo.is_graded() and fo.covers_domain_exactly()
+    merged = set(ref) - set(fo.leaves)
+    assert merged, "some groups must coarsen"
+    # refine the merged parents back: the error is the dropped details, below eps * ||f||
+    S.refine_all()
+    for leaf in merged:
+        if leaf in fo.leaves:
+            err = np.abs(S.U[fo.leaves[leaf]] - ref[leaf]).max(axis=(1, 2, 3))
+            assert np.all(err < eps * norms + 1e-14)
+    # after a full coarsening no sister group is left that could still coarsen
+    S2 = _solver(leaves, nroot=(1, 1, 1), ic=ic, eps=eps, dealias=False)
+    S2.coarsen()
+    ind, _ = S2.indicators(S2.norms())
+    assert not S2.coarsenable_groups(S2.tags(ind))
+    assert S2.fo.is_graded() and S2.fo.covers_domain_exactly()
+
+
+def test_initial_grid_tracks_the_mask_interface():
+    delta = 1.5 / (8 * 8)
+    for dealias, top in ((True, 2), (False, 3)):
+        fo = Forest(nroot=(1, 1, 1), root_len=1.0, Bs=9, Jmin=1, Jmax=3, max_blocks=1 << 12)
+        S = Solver(fo, acm.Physics(), eps=1e-3, dealias=dealias,
+                   ic=lambda X, Y, Z: acm.ic_uniform(X, Y, Z),
+                   mask=lambda X, Y, Z: acm.sphere_mask(X, Y, Z, (0.5, 0.5, 0.5), 0.2, delta))
+        S.initial_grid()
+        assert fo.is_graded() and fo.covers_domain_exactly()
+        levels = {l[0] for l in fo.leaves}
+        assert max(levels) == top
+        for leaf, s in fo.leaves.items():
+            rng = float(S.chi[s].max() - S.chi[s].min())
+            if rng > S.mask_thr:
+                assert leaf[0] == top      # the interface sits on the finest level kept
