@@ -1,0 +1,239 @@
+/*
+ * libacm -- wavelet-adaptive artificial-compressibility solver on one GB300 (sm_103a).
+ *
+ * C ABI of the hot path of Engels, Schneider, Reiss, Farge, "A wavelet-adaptive method for
+ * multiscale simulation of turbulent flows in flying insects" (arXiv:1912.05371): the
+ * per-RK4-stage update over all cubic blocks of an adaptive block grid (ghost synchronisation,
+ * fused ACM right-hand side, RK4 combination) and the per-step wavelet detail thresholding
+ * that refines and coarsens the grid.
+ *
+ * Conventions (all entry points):
+ *  - Every call returns an acm_status; nothing throws across the ABI.  On an error the forest
+ *    is left as it was before the call unless the description says otherwise, and
+ *    acm_last_error() returns a one-line message.
+ *  - Device memory: the caller hands acm_create_forest ONE device buffer (the "pool") of at
+ *    least acm_pool_bytes() bytes; all heavy data and device metadata live in it for the
+ *    lifetime of the forest (the paper allocates its block array once at start-up, Sec. 4.1).
+ *    The library makes no device allocation of its own.  The pool stays owned by the caller
+ *    and must outlive the forest.
+ *  - Streams: every device operation is enqueued on the cudaStream_t given at creation.  Calls
+ *    that return host-visible results (dt, diagnostics, topology, indicators) synchronise
+ *    that stream before returning.
+ *  - Pointers passed in are borrowed for the duration of the call only.
+ *  - Layouts: "block order" is ascending (treecode, level); a field array is block-major,
+ *    then component (u, v, w, p), then z, y, x with x fastest, Bs^3 points per block, in the
+ *    forest's precision (float for precision 32, double for 64).
+ *  - Grids are periodic in all three directions; blocks are "redundant": neighbouring blocks
+ *    share their face points (Sec. 3.1: x_{2i}^{J+1} = x_i^J, odd point count per block).
+ */
+#ifndef ACM_H
+#define ACM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct acm_forest acm_forest;
+
+typedef enum {
+  ACM_OK = 0,
+  ACM_EINVAL = 1,     /* bad argument or inconsistent parameters                          */
+  ACM_ENOMEM = 2,     /* pool too small for the requested layout                          */
+  ACM_ECAPACITY = 3,  /* block pool (max_blocks) exhausted; forest unchanged               */
+  ACM_ECUDA = 4,      /* a CUDA call failed; message in acm_last_error                      */
+  ACM_ETIMEOUT = 5,   /* reserved for bounded device waits                                  */
+  ACM_ENUMERIC = 6,   /* non-finite value met (e.g. NaN in the state)                        */
+  ACM_EGRADING = 7    /* a supplied layout is not 2:1 graded / does not tile the domain     */
+} acm_status;
+
+/* Grid of cubic blocks (Sec. 4.1).  nroot[3] roots of side root_len tile the periodic box
+ * [0, nroot*root_len]; a block at level J has side root_len/2^J and spacing
+ * h_J = root_len / (2^J (Bs-1)).  Bs must be 9 or 17.  g is the ghost depth reported by
+ * acm_sync_ghosts (1..4).  precision is 32 or 64.  fd_scheme: 1 = Tam-Webb optimised first
+ * derivative (Sec. 2.3, the paper's choice), 0 = classical (8,-1)/12.  Levels obey
+ * 0 <= Jmin <= Jmax <= 18 (Sec. 3.5). */
+typedef struct {
+  int nroot[3];
+  double root_len;
+  int Bs;
+  int g;
+  int Jmin, Jmax;
+  int precision;
+  int64_t max_blocks;
+  int fd_scheme;
+} acm_grid_params;
+
+/* Model parameters of eqs. (u_eqn-1, p_eqn-1), Sec. 2.1-2.2, and the adaptation controls of
+ * Sec. 3.3-3.5.  C_sp <= 0 or sponge == 0 disables the sponge term.  eps is C_eps (strict
+ * "<" test on the normalised details); dealias = 1 always tags blocks at Jmax; a block whose
+ * mask range max(chi)-min(chi) exceeds mask_range_thr is not coarsened unless dealiasing
+ * tags it. */
+typedef struct {
+  double nu, c0, C_eta, C_gamma, C_sp;
+  double u_inf[3], p_inf;
+  double cfl, cfl_eta, cfl_nu;
+  double eps;
+  int dealias;
+  double mask_range_thr;
+  int sponge;
+  double sponge_L[3];     /* periodic box lengths used by the sponge profile               */
+  double sponge_width;    /* L_sp: sponge thickness at each box face                        */
+  double sponge_delta;    /* smoothing length of the sponge profile                         */
+} acm_phys_params;
+
+/* Per-step diagnostics (Sec. 2.2 force by midpoint rule; every physical point counted once:
+ * the half-open points [0, Bs-2]^3 of each block, weight h_J^3).  FP64 accumulation. */
+typedef struct {
+  double force[3];        /* C_eta^{-1} sum chi (u - u_s) h^3                               */
+  double energy;          /* 1/2 sum |u|^2 h^3                                              */
+  double u_max;           /* max |u| (vector magnitude) over all stored points              */
+  double norms[4];        /* max |u|, |v|, |w|, |p| over all stored points                  */
+  int64_t n_blocks;
+  int64_t blocks_per_level[19];
+  double time;
+} acm_diag;
+
+/* Initial conditions for acm_set_ic (params in order):
+ *  ACM_IC_TAYLOR_GREEN: k, amp     u = amp sin kx cos ky cos kz, v = -amp cos kx sin ky cos kz, w = p = 0
+ *  ACM_IC_UNIFORM:      u0, v0, w0, p0
+ *  ACM_IC_PULSE:        cx, cy, cz, width, amp, Lx, Ly, Lz   (Gaussian p, u = 0, nearest periodic image) */
+enum { ACM_IC_TAYLOR_GREEN = 1, ACM_IC_UNIFORM = 2, ACM_IC_PULSE = 3 };
+
+/* Masks for acm_set_mask: ACM_MASK_NONE; ACM_MASK_SPHERE: cx, cy, cz, R, delta with
+ * chi = (1 - tanh(d/delta))/2, d the signed distance to the sphere (Sec. 2.2 smoothed mask). */
+enum { ACM_MASK_NONE = 0, ACM_MASK_SPHERE = 1 };
+
+/* Register ids for acm_sync_ghosts / acm_read_fields (U is the solution). */
+enum { ACM_REG_U = 0 };
+
+/* Bytes of device pool needed for these grid parameters (0 on invalid parameters). */
+size_t acm_pool_bytes(const acm_grid_params* grid);
+
+/* Create a forest.  stream: a cudaStream_t (borrowed; NULL = legacy default stream).
+ * device_pool/pool_bytes: caller-owned device buffer, >= acm_pool_bytes(grid), 256-byte
+ * aligned.  The forest starts empty (no blocks).  Returns ACM_EINVAL on bad parameters,
+ * ACM_ENOMEM if the pool is too small, ACM_ECUDA if the device is not usable. */
+acm_status acm_create_forest(const acm_grid_params* grid, const acm_phys_params* phys,
+                             void* stream, void* device_pool, size_t pool_bytes,
+                             acm_forest** out);
+
+/* Release host state (the pool is the caller's).  NULL is accepted. */
+acm_status acm_destroy_forest(acm_forest* f);
+
+/* Replace the grid by the uniform level-J grid (Jmin <= J <= Jmax); fields are zeroed. */
+acm_status acm_init_uniform(acm_forest* f, int J);
+
+/* Replace the grid by the given leaves (level[i], gx[i], gy[i], gz[i]: global block
+ * coordinates at that level), created in one pass in block order (Sec. 4.1 slot rule:
+ * lowest free slot in ascending key order).  ACM_EGRADING if the leaves do not tile the
+ * domain exactly or are not 26-neighbour 2:1 graded.  Fields are zeroed. */
+acm_status acm_set_leaves(acm_forest* f, const int32_t* level, const int32_t* gx,
+                          const int32_t* gy, const int32_t* gz, int64_t n);
+
+/* Evaluate an initial condition (see ACM_IC_*) at every point of every block, in FP64,
+ * stored in the forest precision. */
+acm_status acm_set_ic(acm_forest* f, int ic_kind, const double* params, int n_params);
+
+/* Set the obstacle mask chi (Sec. 2.2), evaluated analytically on every block now and after
+ * every grid change; u_s = 0.  kind ACM_MASK_NONE removes it.  t is reserved for moving
+ * bodies. */
+acm_status acm_set_mask(acm_forest* f, int kind, const double* params, int n_params, double t);
+
+/* Initial grid (Sec. 3.5, last paragraph): start from the uniform Jmin grid and repeat
+ * {refine all, evaluate the initial condition and the mask, coarsen} until the grid is
+ * unchanged.  ic as in acm_set_ic.  On return *n_blocks holds the block count. */
+acm_status acm_init_grid(acm_forest* f, int ic_kind, const double* params, int n_params,
+                         int64_t* n_blocks);
+
+/* Synchronise register reg (ACM_REG_U) and copy every block's extended array -- interior
+ * plus g ghost layers, (Bs+2g)^3 points per component, block order, layout as fields -- to
+ * out (device pointer if out_on_device, else host).  Redundant points shared with a finer
+ * leaf first take the finer value ("fine wins", modifies the register); ghost points take
+ * the value of the finest leaf holding them, else the tensor DD-4 prediction (Sec. 3.1) from
+ * the coarser neighbour (Sec. 4.2).  For tests and debugging; acm_rk4_step synchronises by
+ * itself. */
+acm_status acm_sync_ghosts(acm_forest* f, int reg, void* out, int out_on_device);
+
+/* One classical RK4 step (Sec. 2.3) of eqs. (u_eqn-1, p_eqn-1) on the current grid, each
+ * stage = ghost synchronisation + fused right-hand side + RK combination.  dt > 0: use it;
+ * dt <= 0: use the CFL rule of Sec. 2.3.  *dt_used (may be NULL) receives the step. */
+acm_status acm_rk4_step(acm_forest* f, double dt, double* dt_used);
+
+/* Right-hand side K = F(U) of eqs. (u_eqn-1, p_eqn-1) at every point of every block, after
+ * the same synchronisation as an RK4 stage, written in block order (fields layout) to out
+ * (device pointer if on_device, else host; n_elems = n_blocks*4*Bs^3).  For checks: the
+ * fused stage kernel computes exactly this K inside acm_rk4_step. */
+acm_status acm_rhs(acm_forest* f, void* out, int64_t n_elems, int on_device);
+
+/* Refine every block below Jmax by one level (Sec. 3.5 step 1); children are the DD-4
+ * prediction of the synchronised parent.  ACM_ECAPACITY (forest unchanged) if the pool of
+ * max_blocks slots is too small. */
+acm_status acm_refine_all(acm_forest* f);
+
+/* Coarsening (Sec. 3.5 step 3): details of every block, normalised per component by its
+ * global max norm (taken once, before the first pass); tag if below eps (and J > Jmin, and
+ * the mask range <= thr), or always at Jmax with dealiasing; merge tagged sister groups that
+ * keep the grid graded; repeat until nothing changes.  *n_blocks (may be NULL) receives the
+ * block count, *n_passes (may be NULL) the number of merging passes. */
+acm_status acm_coarsen(acm_forest* f, int64_t* n_blocks, int* n_passes);
+
+/* The paper's time step (Sec. 3.5): refine all, RK4 (dt as in acm_rk4_step), coarsen. */
+acm_status acm_step(acm_forest* f, double dt, double* dt_used, int64_t* n_blocks);
+
+/* Per-block indicators of the current (synchronised) state, block order:
+ * ind[i] = max over components of max |detail| / ||component||_inf (components with zero norm
+ * skipped), chi_range[i] = max chi - min chi (0 without mask).  Either pointer may be NULL. */
+acm_status acm_block_indicators(acm_forest* f, double* ind, double* chi_range, int64_t n);
+
+/* Diagnostics of the current state (see acm_diag). */
+acm_status acm_diagnostics(acm_forest* f, acm_diag* out);
+
+/* Number of blocks. */
+int64_t acm_n_blocks(const acm_forest* f);
+
+/* Topology in block order, for bit-exact checks.  Any pointer may be NULL; each non-NULL
+ * array must hold n entries (nbr: n*56, rel: n*26) with n >= acm_n_blocks.
+ *  treecode: root number << 56 | per-level octal digit (bx + 2by + 4bz) of level l at bits
+ *            3*(18-l) .. +2 (Sec. 4.1, Gargantini)
+ *  level, slot (position in the block pool)
+ *  nbr[56]: 26 directions ordered by iterating dz, dy, dx over -1,0,1 (x fastest), faces
+ *           first, then edges, then corners; face k -> entries 4k..4k+3, edge k -> 24+2k..,
+ *           corner k -> 48+k; same-level or coarser neighbour: its slot in the first entry;
+ *           finer: the touching children's slots in ascending child number; unused: -1
+ *  rel[26]: 0 same level, -1 coarser, +1 finer. */
+acm_status acm_get_topology(acm_forest* f, uint64_t* treecode, uint8_t* level, int32_t* slot,
+                            int32_t* gx, int32_t* gy, int32_t* gz, int32_t* nbr, int8_t* rel,
+                            int64_t n);
+
+/* Copy the fields of register reg in block order to/from host or device memory (layout in
+ * the header conventions; n_elems must equal n_blocks*4*Bs^3). */
+acm_status acm_read_fields(acm_forest* f, int reg, void* out, int64_t n_elems, int on_device);
+acm_status acm_write_fields(acm_forest* f, const void* in, int64_t n_elems, int on_device);
+
+/* Copy the mask chi in block order (n_blocks*Bs^3 elements, forest precision). */
+acm_status acm_read_mask(acm_forest* f, void* out, int64_t n_elems, int on_device);
+
+/* Per-kernel timing of the last acm_rk4_step (CUDA events, milliseconds summed over its
+ * launches) and algorithmic bytes moved by its fused stage kernels. */
+typedef struct {
+  double stage_ms;        /* fused RHS+RK4 stage kernels                                    */
+  double sync_ms;         /* fine-wins and coarse-face prediction kernels                    */
+  double stage_bytes;     /* algorithmic bytes of the stage kernels                          */
+  int64_t n_launches;     /* kernels launched by the step                                    */
+} acm_step_stats;
+acm_status acm_enable_timing(acm_forest* f, int on);
+acm_status acm_last_step_stats(acm_forest* f, acm_step_stats* out);
+
+/* Total kernel launches since creation (every launch of this library). */
+int64_t acm_launch_count(const acm_forest* f);
+
+const char* acm_last_error(const acm_forest* f);
+const char* acm_status_string(acm_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ACM_H */

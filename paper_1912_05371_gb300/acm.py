@@ -1,0 +1,289 @@
+"""Python binding of libacm (include/acm.h): argument marshalling only.
+
+Every operation runs in the CUDA library; this module converts arguments and raises on a
+non-zero status.  PyTorch supplies the device pool and the stream.  There is no fallback: if
+the compiled library is missing, :func:`lib` raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "libacm.so")
+
+ACM_IC_TAYLOR_GREEN, ACM_IC_UNIFORM, ACM_IC_PULSE = 1, 2, 3
+ACM_MASK_NONE, ACM_MASK_SPHERE = 0, 1
+ACM_REG_U = 0
+
+
+class GridParams(C.Structure):
+    _fields_ = [("nroot", C.c_int * 3), ("root_len", C.c_double), ("Bs", C.c_int), ("g", C.c_int),
+                ("Jmin", C.c_int), ("Jmax", C.c_int), ("precision", C.c_int),
+                ("max_blocks", C.c_int64), ("fd_scheme", C.c_int)]
+
+
+class PhysParams(C.Structure):
+    _fields_ = [("nu", C.c_double), ("c0", C.c_double), ("C_eta", C.c_double), ("C_gamma", C.c_double),
+                ("C_sp", C.c_double), ("u_inf", C.c_double * 3), ("p_inf", C.c_double),
+                ("cfl", C.c_double), ("cfl_eta", C.c_double), ("cfl_nu", C.c_double), ("eps", C.c_double),
+                ("dealias", C.c_int), ("mask_range_thr", C.c_double), ("sponge", C.c_int),
+                ("sponge_L", C.c_double * 3), ("sponge_width", C.c_double), ("sponge_delta", C.c_double)]
+
+
+class Diag(C.Structure):
+    _fields_ = [("force", C.c_double * 3), ("energy", C.c_double), ("u_max", C.c_double),
+                ("norms", C.c_double * 4), ("n_blocks", C.c_int64), ("blocks_per_level", C.c_int64 * 19),
+                ("time", C.c_double)]
+
+
+class StepStats(C.Structure):
+    _fields_ = [("stage_ms", C.c_double), ("sync_ms", C.c_double), ("stage_bytes", C.c_double),
+                ("n_launches", C.c_int64)]
+
+
+EXPORTS = {
+    "acm_pool_bytes": (C.c_size_t, [C.POINTER(GridParams)]),
+    "acm_create_forest": (C.c_int, [C.POINTER(GridParams), C.POINTER(PhysParams), C.c_void_p, C.c_void_p,
+                                    C.c_size_t, C.POINTER(C.c_void_p)]),
+    "acm_destroy_forest": (C.c_int, [C.c_void_p]),
+    "acm_init_uniform": (C.c_int, [C.c_void_p, C.c_int]),
+    "acm_set_leaves": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64]),
+    "acm_set_ic": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int]),
+    "acm_set_mask": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_double]),
+    "acm_init_grid": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.POINTER(C.c_int64)]),
+    "acm_sync_ghosts": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int]),
+    "acm_rk4_step": (C.c_int, [C.c_void_p, C.c_double, C.POINTER(C.c_double)]),
+    "acm_refine_all": (C.c_int, [C.c_void_p]),
+    "acm_rhs": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int]),
+    "acm_coarsen": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int)]),
+    "acm_step": (C.c_int, [C.c_void_p, C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
+    "acm_block_indicators": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64]),
+    "acm_diagnostics": (C.c_int, [C.c_void_p, C.POINTER(Diag)]),
+    "acm_n_blocks": (C.c_int64, [C.c_void_p]),
+    "acm_get_topology": (C.c_int, [C.c_void_p] + [C.c_void_p] * 8 + [C.c_int64]),
+    "acm_read_fields": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int64, C.c_int]),
+    "acm_write_fields": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int]),
+    "acm_read_mask": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int]),
+    "acm_enable_timing": (C.c_int, [C.c_void_p, C.c_int]),
+    "acm_last_step_stats": (C.c_int, [C.c_void_p, C.POINTER(StepStats)]),
+    "acm_launch_count": (C.c_int64, [C.c_void_p]),
+    "acm_last_error": (C.c_char_p, [C.c_void_p]),
+    "acm_status_string": (C.c_char_p, [C.c_int]),
+}
+
+_lib = None
+
+
+def lib():
+    """The loaded libacm; raises if it has not been built (no fallback exists)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libacm is not built ({LIB_PATH}); run paper_1912_05371_gb300.build")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in EXPORTS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+class AcmError(RuntimeError):
+    pass
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return C.c_void_p(a.data_ptr())
+    return a.ctypes.data_as(C.c_void_p)
+
+
+class Forest:
+    """One forest of the C library.  ``pool`` is a torch uint8 CUDA tensor (allocated here from
+    the size the library asks for) kept alive for the forest's lifetime."""
+
+    def __init__(self, grid: dict, phys: dict, stream=None, device=None):
+        import torch
+        self.L = lib()
+        g = GridParams()
+        g.nroot = (C.c_int * 3)(*grid.get("nroot", (1, 1, 1)))
+        g.root_len = grid.get("root_len", 1.0)
+        g.Bs = grid.get("Bs", 17)
+        g.g = grid.get("g", 4)
+        g.Jmin = grid.get("Jmin", 0)
+        g.Jmax = grid.get("Jmax", 18)
+        g.precision = grid.get("precision", 64)
+        g.max_blocks = grid.get("max_blocks", 4096)
+        g.fd_scheme = grid.get("fd_scheme", 1)
+        p = PhysParams()
+        p.nu = phys.get("nu", 0.0)
+        p.c0 = phys.get("c0", 1.0)
+        p.C_eta = phys.get("C_eta", 1.0)
+        p.C_gamma = phys.get("C_gamma", 0.0)
+        p.C_sp = phys.get("C_sp", 0.0)
+        p.u_inf = (C.c_double * 3)(*phys.get("u_inf", (0.0, 0.0, 0.0)))
+        p.p_inf = phys.get("p_inf", 0.0)
+        p.cfl = phys.get("cfl", 0.5)
+        p.cfl_eta = phys.get("cfl_eta", 1.0)
+        p.cfl_nu = phys.get("cfl_nu", 0.25)
+        p.eps = phys.get("eps", 1e-3)
+        p.dealias = int(phys.get("dealias", 0))
+        p.mask_range_thr = phys.get("mask_range_thr", 1e-5)
+        p.sponge = int(phys.get("sponge", 0))
+        p.sponge_L = (C.c_double * 3)(*phys.get("sponge_L", (1.0, 1.0, 1.0)))
+        p.sponge_width = phys.get("sponge_width", 0.0)
+        p.sponge_delta = phys.get("sponge_delta", 1.0)
+        self.grid, self.phys = g, p
+        self.Bs = g.Bs
+        self.dtype = np.float64 if g.precision == 64 else np.float32
+        nbytes = self.L.acm_pool_bytes(C.byref(g))
+        if nbytes == 0:
+            raise AcmError("invalid grid parameters")
+        dev = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(dev)
+        self.pool = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+        h = C.c_void_p()
+        self._check(self.L.acm_create_forest(C.byref(g), C.byref(p), C.c_void_p(self.stream.cuda_stream),
+                                             C.c_void_p(self.pool.data_ptr()), nbytes, C.byref(h)), None)
+        self.h = h
+
+    def _check(self, st, h="self"):
+        if st != 0:
+            msg = self.L.acm_status_string(st).decode()
+            if h is not None and getattr(self, "h", None):
+                msg += ": " + self.L.acm_last_error(self.h).decode()
+            raise AcmError(f"libacm status {st}: {msg}")
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.acm_destroy_forest(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- grid ------------------------------------------------------------------------------------
+    def init_uniform(self, J):
+        self._check(self.L.acm_init_uniform(self.h, J))
+
+    def set_leaves(self, leaves):
+        a = np.asarray(leaves, dtype=np.int32).reshape(-1, 4)
+        cols = [np.ascontiguousarray(a[:, i]) for i in range(4)]
+        self._check(self.L.acm_set_leaves(self.h, *[_ptr(c) for c in cols], a.shape[0]))
+
+    def set_ic(self, kind, params):
+        pr = np.asarray(params, dtype=np.float64)
+        self._check(self.L.acm_set_ic(self.h, kind, _ptr(pr), pr.size))
+
+    def set_mask(self, kind, params=(), t=0.0):
+        pr = np.asarray(params, dtype=np.float64)
+        self._check(self.L.acm_set_mask(self.h, kind, _ptr(pr) if pr.size else None, pr.size, t))
+
+    def init_grid(self, ic_kind, params):
+        pr = np.asarray(params, dtype=np.float64)
+        n = C.c_int64()
+        self._check(self.L.acm_init_grid(self.h, ic_kind, _ptr(pr), pr.size, C.byref(n)))
+        return n.value
+
+    def n_blocks(self):
+        return self.L.acm_n_blocks(self.h)
+
+    # ---- time stepping -----------------------------------------------------------------------
+    def rk4_step(self, dt=0.0):
+        d = C.c_double()
+        self._check(self.L.acm_rk4_step(self.h, dt, C.byref(d)))
+        return d.value
+
+    def rhs(self):
+        n = self.n_blocks()
+        out = np.empty((n, 4, self.Bs, self.Bs, self.Bs), dtype=self.dtype)
+        self._check(self.L.acm_rhs(self.h, _ptr(out), out.size, 0))
+        return out
+
+    def refine_all(self):
+        self._check(self.L.acm_refine_all(self.h))
+
+    def coarsen(self):
+        n, p = C.c_int64(), C.c_int()
+        self._check(self.L.acm_coarsen(self.h, C.byref(n), C.byref(p)))
+        return n.value, p.value
+
+    def step(self, dt=0.0):
+        d, n = C.c_double(), C.c_int64()
+        self._check(self.L.acm_step(self.h, dt, C.byref(d), C.byref(n)))
+        return d.value, n.value
+
+    # ---- data ---------------------------------------------------------------------------------------
+    def read_fields(self, out=None):
+        n = self.n_blocks()
+        shape = (n, 4, self.Bs, self.Bs, self.Bs)
+        if out is None:
+            out = np.empty(shape, dtype=self.dtype)
+        on_dev = int(hasattr(out, "data_ptr") and out.is_cuda)
+        self._check(self.L.acm_read_fields(self.h, ACM_REG_U, _ptr(out), int(np.prod(shape)), on_dev))
+        return out
+
+    def write_fields(self, arr):
+        n = self.n_blocks()
+        on_dev = int(hasattr(arr, "data_ptr") and arr.is_cuda)
+        if not on_dev:
+            arr = np.ascontiguousarray(arr, dtype=self.dtype)
+        self._check(self.L.acm_write_fields(self.h, _ptr(arr), n * 4 * self.Bs ** 3, on_dev))
+
+    def read_mask(self):
+        n = self.n_blocks()
+        out = np.empty((n, self.Bs, self.Bs, self.Bs), dtype=self.dtype)
+        self._check(self.L.acm_read_mask(self.h, _ptr(out), out.size, 0))
+        return out
+
+    def sync_ghosts(self):
+        n = self.n_blocks()
+        ne = self.Bs + 2 * self.grid.g
+        out = np.empty((n, 4, ne, ne, ne), dtype=self.dtype)
+        self._check(self.L.acm_sync_ghosts(self.h, ACM_REG_U, _ptr(out), 0))
+        return out
+
+    def block_indicators(self):
+        n = self.n_blocks()
+        ind = np.empty(n)
+        rng = np.empty(n)
+        self._check(self.L.acm_block_indicators(self.h, _ptr(ind), _ptr(rng), n))
+        return ind, rng
+
+    def diagnostics(self):
+        d = Diag()
+        self._check(self.L.acm_diagnostics(self.h, C.byref(d)))
+        return dict(force=tuple(d.force), energy=d.energy, u_max=d.u_max, norms=tuple(d.norms),
+                    n_blocks=d.n_blocks, blocks_per_level=tuple(d.blocks_per_level), time=d.time)
+
+    def topology(self):
+        n = self.n_blocks()
+        tc = np.empty(n, np.uint64)
+        lv = np.empty(n, np.uint8)
+        sl = np.empty(n, np.int32)
+        gx, gy, gz = np.empty(n, np.int32), np.empty(n, np.int32), np.empty(n, np.int32)
+        nbr = np.empty((n, 56), np.int32)
+        rel = np.empty((n, 26), np.int8)
+        self._check(self.L.acm_get_topology(self.h, _ptr(tc), _ptr(lv), _ptr(sl), _ptr(gx), _ptr(gy), _ptr(gz),
+                                            _ptr(nbr), _ptr(rel), n))
+        return dict(treecode=tc, level=lv, slot=sl, gx=gx, gy=gy, gz=gz, nbr=nbr, rel=rel)
+
+    def enable_timing(self, on=True):
+        self._check(self.L.acm_enable_timing(self.h, int(on)))
+
+    def last_step_stats(self):
+        s = StepStats()
+        self._check(self.L.acm_last_step_stats(self.h, C.byref(s)))
+        return dict(stage_ms=s.stage_ms, sync_ms=s.sync_ms, stage_bytes=s.stage_bytes, n_launches=s.n_launches)
+
+    def launch_count(self):
+        return self.L.acm_launch_count(self.h)

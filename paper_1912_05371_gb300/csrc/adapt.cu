@@ -1,0 +1,497 @@
+// Synchronisation, wavelet-detail, adaptation and diagnostic kernels of libacm.
+//
+// Paper: Sec. 3.1 (DD-4 prediction, decimation, details u - P R u), Sec. 3.3-3.4 (block
+// indicator: largest detail normalised per component by its global max norm), Sec. 3.5
+// (refine by prediction, coarsen by merging sister blocks), Sec. 4.2 (ghost synchronisation:
+// restrict or predict, then copy), Sec. 2.2 (smoothed mask, force by midpoint rule).
+#include "common.cuh"
+#include "kernels.hpp"
+
+namespace acm {
+
+namespace {
+
+constexpr int kNT = 256;
+
+template <typename T>
+__device__ __forceinline__ T tabs(T v) { return v < T(0) ? -v : v; }
+
+// ---- (1) fine wins: block boundary points held by a finer neighbour take its value -----------
+// task = (rank, box index d of a REFINED neighbour box).  Points of the block's boundary lying
+// in box d: coordinate 0 / M where d is -1 / +1, the whole range where d is 0.
+template <typename T, int BS>
+__global__ void __launch_bounds__(kNT) k_fine_wins(T* reg, const int2* tasks, const int32_t* nbh_all,
+                                                    const int32_t* blist) {
+  using L = Lay<T, BS>;
+  constexpr int M = L::M;
+  const int2 tk = tasks[blockIdx.x];
+  const int* nbh = nbh_all + (size_t)tk.x * kNbhStride;
+  const int me = blist[tk.x];
+  const int d = tk.y;
+  const int dd[3] = {d % 3 - 1, (d / 3) % 3 - 1, d / 9 - 1};
+  int n[3], o[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    n[a] = dd[a] == 0 ? BS : 1;
+    o[a] = dd[a] < 0 ? 0 : (dd[a] > 0 ? M : 0);
+  }
+  const int tot = n[0] * n[1] * n[2];
+  for (int i = threadIdx.x; i < tot; i += kNT) {
+    const int p[3] = {o[0] + i % n[0], o[1] + (i / n[0]) % n[1], o[2] + i / (n[0] * n[1])};
+    int c = 0, l[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const int q = p[a] - dd[a] * M;
+      const int ca = q > M / 2 ? 1 : (q < M / 2 ? 0 : (dd[a] < 0 ? 1 : 0));
+      c |= ca << a;
+      l[a] = 2 * q - ca * M;
+    }
+    const int s = nbh[8 * d + c];
+    if (s < 0) continue;
+#pragma unroll
+    for (int f = 0; f < 4; ++f)
+      reg[(size_t)me * L::BLK + (size_t)f * L::FS + L::idx(p[0], p[1], p[2])] =
+          reg[(size_t)s * L::BLK + (size_t)f * L::FS + L::idx(l[0], l[1], l[2])];
+  }
+}
+
+// ---- (2) coarse-face halo slabs ------------------------------------------------------------------
+// task = (rank, face F, slab index, -): the 3 x Bs x Bs halo points beyond face F, each the
+// value of the finest leaf holding it, else the DD-4 prediction from the coarser neighbour.
+// Slab layout [slab][comp][layer l-1][t1][t0] with (t0, t1) as in the stage kernel.
+template <typename T, int BS>
+__global__ void __launch_bounds__(kNT) k_coarse_slabs(const T* reg, T* slab, const int4* tasks,
+                                                       const int32_t* nbh_all) {
+  using L = Lay<T, BS>;
+  constexpr int M = L::M;
+  __shared__ int nbh[kNbhStride];
+  const int4 tk = tasks[blockIdx.x];
+  for (int i = threadIdx.x; i < kNbhStride; i += kNT) nbh[i] = nbh_all[(size_t)tk.x * kNbhStride + i];
+  __syncthreads();
+  const int F = tk.y, ax = F >> 1;
+  const bool plus = F & 1;
+  const int tot = 4 * 3 * BS * BS;
+  for (int i = threadIdx.x; i < tot; i += kNT) {
+    const int t0 = i % BS, t1 = (i / BS) % BS, l = (i / (BS * BS)) % 3 + 1, f = i / (3 * BS * BS);
+    const int nl = plus ? M + l : -l;
+    int x, y, z;
+    if (ax == 0) { x = nl; y = t0; z = t1; }
+    else if (ax == 1) { x = t0; y = nl; z = t1; }
+    else { x = t0; y = t1; z = nl; }
+    slab[((((size_t)tk.z * 4 + f) * 3 + (l - 1)) * BS + t1) * BS + t0] = point_value<T, BS>(reg, nbh, x, y, z, f);
+  }
+}
+
+// ---- (3) extended arrays (interior + g ghost layers) ---------------------------------------------
+template <typename T, int BS>
+__global__ void __launch_bounds__(kNT) k_sync_ext(const T* reg, T* out, int g, const int32_t* blist,
+                                                   const int32_t* nbh_all, int by_rank) {
+  using L = Lay<T, BS>;
+  constexpr int M = L::M;
+  __shared__ int nbh[kNbhStride];
+  const int slot = blist[blockIdx.x];
+  for (int i = threadIdx.x; i < kNbhStride; i += kNT) nbh[i] = nbh_all[(size_t)blockIdx.x * kNbhStride + i];
+  __syncthreads();
+  const int ne = BS + 2 * g;
+  const size_t ne3 = (size_t)ne * ne * ne;
+  T* o = out + (size_t)(by_rank ? blockIdx.x : slot) * 4 * ne3;
+  const T* me = reg + (size_t)slot * L::BLK;
+  for (size_t i = threadIdx.x; i < 4 * ne3; i += kNT) {
+    const int f = (int)(i / ne3);
+    const int r = (int)(i % ne3);
+    const int x = r % ne - g, y = (r / ne) % ne - g, z = r / (ne * ne) - g;
+    T v;
+    if (x >= 0 && x <= M && y >= 0 && y <= M && z >= 0 && z <= M)
+      v = me[(size_t)f * L::FS + L::idx(x, y, z)];
+    else
+      v = point_value<T, BS>(reg, nbh, x, y, z, f);
+    o[i] = v;
+  }
+}
+
+// ---- (4) block indicators: details (Sec. 3.1) and mask range ----------------------------------
+template <typename T, int BS>
+__global__ void __launch_bounds__(kNT) k_details(const T* ext, const T* chi, const int32_t* blist,
+                                                  const double* norms, double* ind, double* chirange) {
+  using L = Lay<T, BS>;
+  constexpr int M = L::M, NE = L::NE, G = kGE;
+  const int slot = blist[blockIdx.x];
+  const T* e = ext + (size_t)slot * L::EBLK;
+  const T w[4] = {T(-1) / T(16), T(9) / T(16), T(9) / T(16), T(-1) / T(16)};
+  const int off[4] = {-3, -1, 1, 3};
+  double best = 0.0;
+  double inv[4];
+#pragma unroll
+  for (int f = 0; f < 4; ++f) inv[f] = norms[f] > 0.0 ? 1.0 / norms[f] : 0.0;
+  for (int i = threadIdx.x; i < BS * BS * BS; i += kNT) {
+    const int x = i % BS, y = (i / BS) % BS, z = i / (BS * BS);
+    if (((x | y | z) & 1) == 0) continue;          // all-even points: detail is zero
+    const int nx = (x & 1) ? 4 : 1, ny = (y & 1) ? 4 : 1, nz = (z & 1) ? 4 : 1;
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+      if (inv[f] == 0.0) continue;
+      const T* ef = e + (size_t)f * L::NE3;
+      T accz = T(0);
+      for (int kz = 0; kz < nz; ++kz) {
+        const int zz = (nz == 4 ? z + off[kz] : z) + G;
+        const T wz = nz == 4 ? w[kz] : T(1);
+        T accy = T(0);
+        for (int ky = 0; ky < ny; ++ky) {
+          const int yy = (ny == 4 ? y + off[ky] : y) + G;
+          const T wy = ny == 4 ? w[ky] : T(1);
+          T accx = T(0);
+          for (int kx = 0; kx < nx; ++kx) {
+            const int xx = (nx == 4 ? x + off[kx] : x) + G;
+            const T wx = nx == 4 ? w[kx] : T(1);
+            accx = accx + wx * ef[(zz * NE + yy) * NE + xx];
+          }
+          accy = accy + wy * accx;
+        }
+        accz = accz + wz * accy;
+      }
+      const T dv = ef[((z + G) * NE + (y + G)) * NE + (x + G)] - accz;
+      const double r = (double)tabs(dv) * inv[f];
+      best = r > best ? r : best;
+    }
+  }
+  double cmin = 1e300, cmax = -1e300;
+  if (chi) {
+    for (int i = threadIdx.x; i < BS * BS * BS; i += kNT) {
+      const int x = i % BS, y = (i / BS) % BS, z = i / (BS * BS);
+      const double c = (double)chi[(size_t)slot * L::FS + L::idx(x, y, z)];
+      cmin = c < cmin ? c : cmin;
+      cmax = c > cmax ? c : cmax;
+    }
+  }
+  __shared__ double red[3][kNT / 32];
+  for (int o = 16; o > 0; o >>= 1) {
+    best = fmax(best, __shfl_xor_sync(0xffffffffu, best, o));
+    cmin = fmin(cmin, __shfl_xor_sync(0xffffffffu, cmin, o));
+    cmax = fmax(cmax, __shfl_xor_sync(0xffffffffu, cmax, o));
+  }
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) { red[0][wid] = best; red[1][wid] = cmin; red[2][wid] = cmax; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double b = 0.0, mn = 1e300, mx = -1e300;
+    for (int k = 0; k < kNT / 32; ++k) {
+      b = fmax(b, red[0][k]);
+      mn = fmin(mn, red[1][k]);
+      mx = fmax(mx, red[2][k]);
+    }
+    ind[blockIdx.x] = b;
+    chirange[blockIdx.x] = chi ? mx - mn : 0.0;
+  }
+}
+
+// ---- (5) max norms (Sec. 2.3 u_max, Sec. 3.4 normalisation) ------------------------------------
+template <typename T, int BS>
+__global__ void __launch_bounds__(kNT) k_maxnorm(const T* reg, const int32_t* blist, unsigned long long* out) {
+  using L = Lay<T, BS>;
+  const int slot = blist[blockIdx.x];
+  const T* b = reg + (size_t)slot * L::BLK;
+  double m[5] = {0, 0, 0, 0, 0};
+  for (int i = threadIdx.x; i < BS * BS * BS; i += kNT) {
+    const int x = i % BS, y = (i / BS) % BS, z = i / (BS * BS);
+    const int pi = L::idx(x, y, z);
+    double v[4];
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+      v[f] = (double)b[(size_t)f * L::FS + pi];
+      m[f] = fmax(m[f], fabs(v[f]));
+    }
+    m[4] = fmax(m[4], sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]));
+  }
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    for (int o = 16; o > 0; o >>= 1) m[k] = fmax(m[k], __shfl_xor_sync(0xffffffffu, m[k], o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out + k, (unsigned long long)__double_as_longlong(m[k]));
+  }
+}
+
+// ---- (6) refinement: 8 children predicted from the synchronised parent (Sec. 3.5 step 1) -------
+// task = (old parent slot, child c, new child slot, -)
+template <typename T, int BS>
+__global__ void __launch_bounds__(kNT) k_refine(const T* ext, T* reg, const int4* tasks) {
+  using L = Lay<T, BS>;
+  constexpr int M = L::M, NE = L::NE, G = kGE;
+  const int4 tk = tasks[blockIdx.x];
+  const T* e = ext + (size_t)tk.x * L::EBLK;
+  const int cb[3] = {tk.y & 1, (tk.y >> 1) & 1, (tk.y >> 2) & 1};
+  const T w[4] = {T(-1) / T(16), T(9) / T(16), T(9) / T(16), T(-1) / T(16)};
+  const int off[4] = {-3, -1, 1, 3};
+  for (int i = threadIdx.x; i < 4 * BS * BS * BS; i += kNT) {
+    const int f = i / (BS * BS * BS);
+    const int r = i % (BS * BS * BS);
+    const int ix = r % BS, iy = (r / BS) % BS, iz = r / (BS * BS);
+    // parent-local fine-lattice position (twice the parent index): c*M + i
+    const int px = cb[0] * M + ix, py = cb[1] * M + iy, pz = cb[2] * M + iz;
+    const int nx = (px & 1) ? 4 : 1, ny = (py & 1) ? 4 : 1, nz = (pz & 1) ? 4 : 1;
+    const T* ef = e + (size_t)f * L::NE3;
+    T accz = T(0);
+    for (int kz = 0; kz < nz; ++kz) {
+      const int zz = (nz == 4 ? pz + off[kz] : pz) / 2 + G;
+      const T wz = nz == 4 ? w[kz] : T(1);
+      T accy = T(0);
+      for (int ky = 0; ky < ny; ++ky) {
+        const int yy = (ny == 4 ? py + off[ky] : py) / 2 + G;
+        const T wy = ny == 4 ? w[ky] : T(1);
+        T accx = T(0);
+        for (int kx = 0; kx < nx; ++kx) {
+          const int xx = (nx == 4 ? px + off[kx] : px) / 2 + G;
+          const T wx = nx == 4 ? w[kx] : T(1);
+          accx = accx + wx * ef[(zz * NE + yy) * NE + xx];
+        }
+        accy = accy + wy * accx;
+      }
+      accz = accz + wz * accy;
+    }
+    reg[(size_t)tk.z * L::BLK + (size_t)f * L::FS + L::idx(ix, iy, iz)] = accz;
+  }
+}
+
+// ---- (7) coarsening: parent by decimation of its 8 children (Sec. 3.1 R, Sec. 3.5 step 3) ----
+// task = [new parent slot, old child slots 0..7]
+template <typename T, int BS>
+__global__ void __launch_bounds__(kNT) k_coarsen(const T* ext, T* reg, const int32_t* tasks) {
+  using L = Lay<T, BS>;
+  constexpr int M = L::M, NE = L::NE, G = kGE;
+  const int32_t* tk = tasks + (size_t)blockIdx.x * 9;
+  for (int i = threadIdx.x; i < 4 * BS * BS * BS; i += kNT) {
+    const int f = i / (BS * BS * BS);
+    const int r = i % (BS * BS * BS);
+    const int x = r % BS, y = (r / BS) % BS, z = r / (BS * BS);
+    const int cx = x > M / 2, cy = y > M / 2, cz = z > M / 2;
+    const int lx = 2 * x - cx * M, ly = 2 * y - cy * M, lz = 2 * z - cz * M;
+    const int cs = tk[1 + (cx | (cy << 1) | (cz << 2))];
+    reg[(size_t)tk[0] * L::BLK + (size_t)f * L::FS + L::idx(x, y, z)] =
+        ext[(size_t)cs * L::EBLK + (size_t)f * L::NE3 + ((lz + G) * NE + (ly + G)) * NE + (lx + G)];
+  }
+}
+
+// ---- (8) analytic initial conditions and masks, FP64 at integer-derived coordinates ------------
+__device__ __forceinline__ double coord(const PhysK& ph, int4 bi, int a, int i, int M, double h) {
+  const int g = a == 0 ? bi.y : (a == 1 ? bi.z : bi.w);
+  const long long N = ((long long)ph.nroot[a] << bi.x) * M;
+  const long long gi = ((long long)g * M + i) % N;      // periodic seam x = L taken as 0
+  return (double)gi * h;
+}
+
+template <typename T, int BS>
+__global__ void __launch_bounds__(kNT) k_ic(T* reg, const int32_t* list, const int4* binfo, const PhysK ph, const IcK ic) {
+  using L = Lay<T, BS>;
+  constexpr int M = L::M;
+  const int slot = list[blockIdx.x];
+  const int4 bi = binfo[blockIdx.x];
+  const double h = ph.root_len / ((double)(1 << bi.x) * M);
+  for (int i = threadIdx.x; i < BS * BS * BS; i += kNT) {
+    const int ix = i % BS, iy = (i / BS) % BS, iz = i / (BS * BS);
+    const double X = coord(ph, bi, 0, ix, M, h), Y = coord(ph, bi, 1, iy, M, h), Z = coord(ph, bi, 2, iz, M, h);
+    double v[4] = {0, 0, 0, 0};
+    if (ic.kind == 1) {          // Taylor-Green
+      const double k = ic.p[0], A = ic.p[1];
+      v[0] = A * sin(k * X) * cos(k * Y) * cos(k * Z);
+      v[1] = -A * cos(k * X) * sin(k * Y) * cos(k * Z);
+    } else if (ic.kind == 2) {   // uniform
+      v[0] = ic.p[0]; v[1] = ic.p[1]; v[2] = ic.p[2]; v[3] = ic.p[3];
+    } else if (ic.kind == 3) {   // Gaussian pressure pulse, nearest periodic image
+      const double c[3] = {ic.p[0], ic.p[1], ic.p[2]}, Lb[3] = {ic.p[5], ic.p[6], ic.p[7]};
+      const double P[3] = {X, Y, Z};
+      double r2 = 0.0;
+      for (int a = 0; a < 3; ++a) {
+        double d = P[a] - c[a];
+        d = d - Lb[a] * rint(d / Lb[a]);
+        r2 += d * d;
+      }
+      v[3] = ic.p[4] * exp(-r2 / (ic.p[3] * ic.p[3]));
+    }
+    const int pi = L::idx(ix, iy, iz);
+#pragma unroll
+    for (int f = 0; f < 4; ++f) reg[(size_t)slot * L::BLK + (size_t)f * L::FS + pi] = T(v[f]);
+  }
+}
+
+template <typename T, int BS>
+__global__ void __launch_bounds__(kNT) k_mask(T* chi, const int32_t* list, const int4* binfo, const PhysK ph, const MaskK m) {
+  using L = Lay<T, BS>;
+  constexpr int M = L::M;
+  const int slot = list[blockIdx.x];
+  const int4 bi = binfo[blockIdx.x];
+  const double h = ph.root_len / ((double)(1 << bi.x) * M);
+  for (int i = threadIdx.x; i < BS * BS * BS; i += kNT) {
+    const int ix = i % BS, iy = (i / BS) % BS, iz = i / (BS * BS);
+    const double X = coord(ph, bi, 0, ix, M, h), Y = coord(ph, bi, 1, iy, M, h), Z = coord(ph, bi, 2, iz, M, h);
+    double c = 0.0;
+    if (m.kind == 1) {
+      const double dx = X - m.p[0], dy = Y - m.p[1], dz = Z - m.p[2];
+      const double d = sqrt(dx * dx + dy * dy + dz * dz) - m.p[3];
+      c = 0.5 * (1.0 - tanh(d / m.p[4]));
+    }
+    chi[(size_t)slot * L::FS + L::idx(ix, iy, iz)] = T(c);
+  }
+}
+
+// ---- (9) diagnostics: raw per-block sums over the half-open points [0, M-1]^3 -----------------
+template <typename T, int BS>
+__global__ void __launch_bounds__(kNT) k_diag(const T* reg, const T* chi, const int32_t* blist, double* out) {
+  using L = Lay<T, BS>;
+  constexpr int M = L::M;
+  const int slot = blist[blockIdx.x];
+  const T* b = reg + (size_t)slot * L::BLK;
+  double s[4] = {0, 0, 0, 0};
+  for (int i = threadIdx.x; i < M * M * M; i += kNT) {
+    const int x = i % M, y = (i / M) % M, z = i / (M * M);
+    const int pi = L::idx(x, y, z);
+    const double u = b[pi], v = b[L::FS + pi], w = b[2 * L::FS + pi];
+    if (chi) {
+      const double c = chi[(size_t)slot * L::FS + pi];
+      s[0] += c * u;
+      s[1] += c * v;
+      s[2] += c * w;
+    }
+    s[3] += u * u + v * v + w * w;
+  }
+  __shared__ double red[4][kNT / 32];
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+    for (int o = 16; o > 0; o >>= 1) s[k] += __shfl_xor_sync(0xffffffffu, s[k], o);
+  if ((threadIdx.x & 31) == 0)
+    for (int k = 0; k < 4; ++k) red[k][threadIdx.x >> 5] = s[k];
+  __syncthreads();
+  if (threadIdx.x < 4) {
+    double t = 0.0;
+    for (int w = 0; w < kNT / 32; ++w) t += red[threadIdx.x][w];
+    out[(size_t)blockIdx.x * 4 + threadIdx.x] = t;
+  }
+}
+
+// ---- (10) dense <-> pool ---------------------------------------------------------------------------
+template <typename T, int BS>
+__global__ void __launch_bounds__(kNT) k_gather(const T* reg, T* dense, const int32_t* blist, int ncomp, int comp_stride_blk) {
+  using L = Lay<T, BS>;
+  const int slot = blist[blockIdx.x];
+  const int n = ncomp * BS * BS * BS;
+  for (int i = threadIdx.x; i < n; i += kNT) {
+    const int f = i / (BS * BS * BS), r = i % (BS * BS * BS);
+    const int x = r % BS, y = (r / BS) % BS, z = r / (BS * BS);
+    dense[(size_t)blockIdx.x * n + i] = reg[(size_t)slot * comp_stride_blk + (size_t)f * L::FS + L::idx(x, y, z)];
+  }
+}
+
+template <typename T, int BS>
+__global__ void __launch_bounds__(kNT) k_scatter(const T* dense, T* reg, const int32_t* blist) {
+  using L = Lay<T, BS>;
+  const int slot = blist[blockIdx.x];
+  const int n = 4 * BS * BS * BS;
+  for (int i = threadIdx.x; i < n; i += kNT) {
+    const int f = i / (BS * BS * BS), r = i % (BS * BS * BS);
+    const int x = r % BS, y = (r / BS) % BS, z = r / (BS * BS);
+    reg[(size_t)slot * L::BLK + (size_t)f * L::FS + L::idx(x, y, z)] = dense[(size_t)blockIdx.x * n + i];
+  }
+}
+
+inline dim3 grid1(int64_t n) { return dim3((unsigned)n); }
+
+}  // namespace
+
+LayoutInfo layout_info(int precision, int Bs) {
+  LayoutInfo li{};
+#define ACM_FILL(T, B)                                                                             \
+  li.PP = Lay<T, B>::PP; li.FS = Lay<T, B>::FS; li.BLK = Lay<T, B>::BLK; li.NE = Lay<T, B>::NE;  \
+  li.NE3 = Lay<T, B>::NE3; li.EBLK = Lay<T, B>::EBLK;
+  if (precision == 64) {
+    if (Bs == 17) { ACM_FILL(double, 17) } else { ACM_FILL(double, 9) }
+  } else {
+    if (Bs == 17) { ACM_FILL(float, 17) } else { ACM_FILL(float, 9) }
+  }
+#undef ACM_FILL
+  return li;
+}
+
+#define ACM_BS_DISPATCH(Bs, KERNEL, ...)                 \
+  do {                                                   \
+    if ((Bs) == 17) { KERNEL<T, 17> __VA_ARGS__; }       \
+    else { KERNEL<T, 9> __VA_ARGS__; }                   \
+  } while (0)
+
+template <typename T>
+void launch_fine_wins(int Bs, T* reg, const int2* tasks, int64_t n, const int32_t* nbh, const int32_t* blist,
+                      cudaStream_t st) {
+  if (n <= 0) return;
+  ACM_BS_DISPATCH(Bs, k_fine_wins, <<<grid1(n), kNT, 0, st>>>(reg, tasks, nbh, blist));
+}
+template <typename T>
+void launch_coarse_slabs(int Bs, const T* reg, T* slab, const int4* tasks, int64_t n, const int32_t* nbh, cudaStream_t st) {
+  if (n <= 0) return;
+  ACM_BS_DISPATCH(Bs, k_coarse_slabs, <<<grid1(n), kNT, 0, st>>>(reg, slab, tasks, nbh));
+}
+template <typename T>
+void launch_sync_ext(int Bs, const T* reg, T* out, int g, const int32_t* list, int64_t n, const int32_t* nbh, int by_rank, cudaStream_t st) {
+  if (n <= 0) return;
+  ACM_BS_DISPATCH(Bs, k_sync_ext, <<<grid1(n), kNT, 0, st>>>(reg, out, g, list, nbh, by_rank));
+}
+template <typename T>
+void launch_details(int Bs, const T* ext, const T* chi, const int32_t* blist, int64_t n, const double* norms, double* ind, double* chirange, cudaStream_t st) {
+  if (n <= 0) return;
+  ACM_BS_DISPATCH(Bs, k_details, <<<grid1(n), kNT, 0, st>>>(ext, chi, blist, norms, ind, chirange));
+}
+template <typename T>
+void launch_maxnorm(int Bs, const T* reg, const int32_t* blist, int64_t n, unsigned long long* out, cudaStream_t st) {
+  if (n <= 0) return;
+  ACM_BS_DISPATCH(Bs, k_maxnorm, <<<grid1(n), kNT, 0, st>>>(reg, blist, out));
+}
+template <typename T>
+void launch_refine(int Bs, const T* ext, T* reg, const int4* tasks, int64_t n, cudaStream_t st) {
+  if (n <= 0) return;
+  ACM_BS_DISPATCH(Bs, k_refine, <<<grid1(n), kNT, 0, st>>>(ext, reg, tasks));
+}
+template <typename T>
+void launch_coarsen(int Bs, const T* ext, T* reg, const int32_t* tasks, int64_t n, cudaStream_t st) {
+  if (n <= 0) return;
+  ACM_BS_DISPATCH(Bs, k_coarsen, <<<grid1(n), kNT, 0, st>>>(ext, reg, tasks));
+}
+template <typename T>
+void launch_ic(int Bs, T* reg, const int32_t* list, int64_t n, const int4* binfo, const PhysK& p, const IcK& ic, cudaStream_t st) {
+  if (n <= 0) return;
+  ACM_BS_DISPATCH(Bs, k_ic, <<<grid1(n), kNT, 0, st>>>(reg, list, binfo, p, ic));
+}
+template <typename T>
+void launch_mask(int Bs, T* chi, const int32_t* list, int64_t n, const int4* binfo, const PhysK& p, const MaskK& m, cudaStream_t st) {
+  if (n <= 0) return;
+  ACM_BS_DISPATCH(Bs, k_mask, <<<grid1(n), kNT, 0, st>>>(chi, list, binfo, p, m));
+}
+template <typename T>
+void launch_diag(int Bs, const T* reg, const T* chi, const int32_t* blist, int64_t n, double* out, cudaStream_t st) {
+  if (n <= 0) return;
+  ACM_BS_DISPATCH(Bs, k_diag, <<<grid1(n), kNT, 0, st>>>(reg, chi, blist, out));
+}
+template <typename T>
+void launch_gather(int Bs, const T* reg, T* dense, const int32_t* blist, int64_t n, int ncomp, cudaStream_t st) {
+  if (n <= 0) return;
+  const int stride = (int)layout_info(sizeof(T) == 8 ? 64 : 32, Bs).BLK;
+  const int cstride = ncomp == 1 ? (int)layout_info(sizeof(T) == 8 ? 64 : 32, Bs).FS : stride;
+  ACM_BS_DISPATCH(Bs, k_gather, <<<grid1(n), kNT, 0, st>>>(reg, dense, blist, ncomp, cstride));
+}
+template <typename T>
+void launch_scatter(int Bs, const T* dense, T* reg, const int32_t* blist, int64_t n, cudaStream_t st) {
+  if (n <= 0) return;
+  ACM_BS_DISPATCH(Bs, k_scatter, <<<grid1(n), kNT, 0, st>>>(dense, reg, blist));
+}
+
+#define ACM_INST(T)                                                                                        \
+  template void launch_fine_wins<T>(int, T*, const int2*, int64_t, const int32_t*, const int32_t*, cudaStream_t);          \
+  template void launch_coarse_slabs<T>(int, const T*, T*, const int4*, int64_t, const int32_t*, cudaStream_t); \
+  template void launch_sync_ext<T>(int, const T*, T*, int, const int32_t*, int64_t, const int32_t*, int, cudaStream_t); \
+  template void launch_details<T>(int, const T*, const T*, const int32_t*, int64_t, const double*, double*, double*, cudaStream_t); \
+  template void launch_maxnorm<T>(int, const T*, const int32_t*, int64_t, unsigned long long*, cudaStream_t); \
+  template void launch_refine<T>(int, const T*, T*, const int4*, int64_t, cudaStream_t);                   \
+  template void launch_coarsen<T>(int, const T*, T*, const int32_t*, int64_t, cudaStream_t);               \
+  template void launch_ic<T>(int, T*, const int32_t*, int64_t, const int4*, const PhysK&, const IcK&, cudaStream_t); \
+  template void launch_mask<T>(int, T*, const int32_t*, int64_t, const int4*, const PhysK&, const MaskK&, cudaStream_t); \
+  template void launch_diag<T>(int, const T*, const T*, const int32_t*, int64_t, double*, cudaStream_t);   \
+  template void launch_gather<T>(int, const T*, T*, const int32_t*, int64_t, int, cudaStream_t);          \
+  template void launch_scatter<T>(int, const T*, T*, const int32_t*, int64_t, cudaStream_t);
+ACM_INST(float)
+ACM_INST(double)
+
+}  // namespace acm

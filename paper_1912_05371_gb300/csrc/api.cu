@@ -1,0 +1,927 @@
+// C-ABI entry points of libacm (declared in include/acm.h).
+//
+// The host side keeps the block tree (forest.hpp) and drives the kernels (kernels.hpp) on the
+// caller's stream; all device memory is carved out of the caller's pool at creation
+// (Sec. 4.1: one allocation at start-up, released only at the end).
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/acm.h"
+#include "common.cuh"
+#include "forest.hpp"
+#include "kernels.hpp"
+
+using acm::BoxKey;
+using acm::BoxStatus;
+
+namespace {
+// Tam & Webb's free coefficient of the 4th-order 7-point first derivative: the minimiser of
+// the integrated dispersion error over kh in [0, pi/2] (published as 0.02651995).
+constexpr double kTamWebbA3 = 0.0265199520614978;
+}  // namespace
+
+struct acm_forest {
+  acm_grid_params gp;
+  acm_phys_params pp;
+  cudaStream_t st = nullptr;
+  char* pool = nullptr;
+  size_t pool_bytes = 0;
+  acm::LayoutInfo lay{};
+  size_t esz = 8;
+  std::unique_ptr<acm::Forest> fo;
+
+  // heavy data (slot-indexed)
+  void* U = nullptr;
+  void* ACC = nullptr;
+  void* YA = nullptr;
+  void* YB = nullptr;
+  void* CHI = nullptr;
+  void* EXT = nullptr;
+  void* SLAB = nullptr;
+  // metadata (rank-indexed)
+  int32_t* d_nbh = nullptr;
+  int4* d_binfo = nullptr;
+  int32_t* d_blist = nullptr;
+  int32_t* d_slabidx = nullptr;
+  int2* d_fw = nullptr;
+  int4* d_slabt = nullptr;
+  int4* d_reft = nullptr;
+  int32_t* d_crst = nullptr;
+  double* d_norms = nullptr;
+  unsigned long long* d_maxbits = nullptr;
+  double* d_ind = nullptr;
+  double* d_chir = nullptr;
+  double* d_diag = nullptr;
+
+  // host mirrors of the current topology
+  std::vector<BoxKey> order;
+  std::vector<int32_t> blist;
+  int64_t n_fw = 0, n_slab = 0;
+  int Jtop = 0;
+
+  bool mask_on = false;
+  acm::MaskK mask{};
+  acm::PhysK phk{};
+  double time = 0.0;
+  std::string err;
+  int64_t launches = 0;
+  bool timing = false;
+  acm_step_stats stats{};
+  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+};
+
+namespace {
+
+acm_status fail(acm_forest* f, acm_status s, const std::string& msg) {
+  if (f) f->err = msg;
+  return s;
+}
+
+#define CK(call)                                                                               \
+  do {                                                                                         \
+    cudaError_t e_ = (call);                                                                   \
+    if (e_ != cudaSuccess)                                                                     \
+      return fail(f, ACM_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));           \
+  } while (0)
+
+#define CKL()                                                                                  \
+  do {                                                                                         \
+    cudaError_t e_ = cudaGetLastError();                                                       \
+    if (e_ != cudaSuccess)                                                                     \
+      return fail(f, ACM_ECUDA, std::string("kernel launch: ") + cudaGetErrorString(e_));      \
+  } while (0)
+
+size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+struct Carve {
+  size_t off = 0;
+  char* base = nullptr;
+  template <typename P>
+  P* take(size_t bytes) {
+    P* p = reinterpret_cast<P*>(base ? base + off : nullptr);
+    off = align256(off + bytes);
+    return p;
+  }
+};
+
+bool valid_grid(const acm_grid_params* g) {
+  if (!g) return false;
+  if (g->Bs != 9 && g->Bs != 17) return false;
+  if (g->precision != 32 && g->precision != 64) return false;
+  if (g->g < 1 || g->g > 4) return false;
+  if (g->Jmin < 0 || g->Jmax < g->Jmin || g->Jmax > 18) return false;
+  if (g->max_blocks < 1 || g->max_blocks > (int64_t)1 << 30) return false;
+  if (!(g->root_len > 0)) return false;
+  for (int a = 0; a < 3; ++a)
+    if (g->nroot[a] < 1 || g->nroot[a] > 64) return false;
+  if ((int64_t)g->nroot[0] * g->nroot[1] * g->nroot[2] > 255) return false;
+  return true;
+}
+
+// Lay out (or just size, when base == nullptr) every device region of a forest.
+size_t carve(acm_forest* f, const acm_grid_params* g, char* base) {
+  const acm::LayoutInfo L = acm::layout_info(g->precision, g->Bs);
+  const size_t es = g->precision == 64 ? 8 : 4;
+  const size_t nb = (size_t)g->max_blocks;
+  const size_t bs2 = (size_t)g->Bs * g->Bs;
+  Carve c;
+  c.base = base;
+  void* U = c.take<char>(nb * L.BLK * es);
+  void* ACC = c.take<char>(nb * L.BLK * es);
+  void* YA = c.take<char>(nb * L.BLK * es);
+  void* YB = c.take<char>(nb * L.BLK * es);
+  void* CHI = c.take<char>(nb * L.FS * es);
+  void* EXT = c.take<char>(nb * L.EBLK * es);
+  void* SLAB = c.take<char>(nb * 6 * 4 * 3 * bs2 * es);
+  int32_t* nbh = c.take<int32_t>(nb * acm::kNbhStride * 4);
+  int4* binfo = c.take<int4>(nb * 16);
+  int32_t* blist = c.take<int32_t>(nb * 4);
+  int32_t* slabidx = c.take<int32_t>(nb * 8 * 4);
+  int2* fw = c.take<int2>(nb * 26 * 8);
+  int4* slabt = c.take<int4>(nb * 6 * 16);
+  int4* reft = c.take<int4>(nb * 16);
+  int32_t* crst = c.take<int32_t>(nb * 9 * 4);
+  double* norms = c.take<double>(16 * 8);
+  unsigned long long* maxbits = c.take<unsigned long long>(16 * 8);
+  double* ind = c.take<double>(nb * 8);
+  double* chir = c.take<double>(nb * 8);
+  double* diag = c.take<double>(nb * 4 * 8);
+  if (f) {
+    f->U = U; f->ACC = ACC; f->YA = YA; f->YB = YB; f->CHI = CHI; f->EXT = EXT; f->SLAB = SLAB;
+    f->d_nbh = nbh; f->d_binfo = binfo; f->d_blist = blist; f->d_slabidx = slabidx;
+    f->d_fw = fw; f->d_slabt = slabt; f->d_reft = reft; f->d_crst = crst;
+    f->d_norms = norms; f->d_maxbits = maxbits; f->d_ind = ind; f->d_chir = chir; f->d_diag = diag;
+  }
+  return c.off;
+}
+
+acm::TopoK topo(const acm_forest* f) {
+  acm::TopoK t;
+  t.nbh = f->d_nbh;
+  t.binfo = f->d_binfo;
+  t.blist = f->d_blist;
+  t.slabidx = f->d_slabidx;
+  t.n = (int64_t)f->order.size();
+  return t;
+}
+
+constexpr int kFaceBox[6] = {12, 14, 10, 16, 4, 22};
+
+// Rebuild the rank-indexed device metadata after any change of the grid.
+acm_status upload_topology(acm_forest* f) {
+  const acm::Forest& fo = *f->fo;
+  f->order = fo.sorted();
+  const size_t n = f->order.size();
+  f->blist.resize(n);
+  std::vector<int32_t> nbh(n * acm::kNbhStride, -1);
+  std::vector<int4> binfo(n);
+  std::vector<int32_t> slabidx(n * 8, -1);
+  std::vector<int2> fw;
+  std::vector<int4> slabt;
+  f->Jtop = 0;
+  for (size_t r = 0; r < n; ++r) {
+    const BoxKey& b = f->order[r];
+    f->blist[r] = fo.leaves.at(b);
+    binfo[r] = make_int4(b.J, b.x, b.y, b.z);
+    f->Jtop = std::max(f->Jtop, b.J);
+    int32_t* row = &nbh[r * acm::kNbhStride];
+    for (int dz = -1; dz <= 1; ++dz)
+      for (int dy = -1; dy <= 1; ++dy)
+        for (int dx = -1; dx <= 1; ++dx) {
+          const int d = acm::box_index(dx, dy, dz);
+          const BoxStatus st = fo.box_status(b.J, (int64_t)b.x + dx, (int64_t)b.y + dy, (int64_t)b.z + dz);
+          if (st.type == acm::BOX_NONE) return fail(f, ACM_EGRADING, "grid is not 2:1 graded");
+          if (st.type == acm::BOX_REFINED) {
+            // every child touching the block must be a leaf (kernels index these slots)
+            for (int c = 0; c < 8; ++c) {
+              const int cc[3] = {c & 1, (c >> 1) & 1, (c >> 2) & 1};
+              const int dd[3] = {dx, dy, dz};
+              bool touch = true;
+              for (int a = 0; a < 3; ++a)
+                if ((dd[a] == 1 && cc[a] != 0) || (dd[a] == -1 && cc[a] != 1)) touch = false;
+              if (touch && st.slot[c] < 0) return fail(f, ACM_EGRADING, "grid is not 2:1 graded");
+            }
+          }
+          for (int c = 0; c < 8; ++c) row[8 * d + c] = st.slot[c];
+          int t = st.type == acm::BOX_LEAF ? acm::kTypeLeaf
+                  : st.type == acm::BOX_COARSER ? acm::kTypeCoarser
+                                                : acm::kTypeRefined;
+          row[acm::kNbhType + d] = t | (st.octant << 4);
+          if (st.type == acm::BOX_REFINED && d != 13) fw.push_back(make_int2((int)r, d));
+        }
+    for (int F = 0; F < 6; ++F) {
+      const int d = kFaceBox[F];
+      if ((row[acm::kNbhType + d] & 15) == acm::kTypeCoarser) {
+        const int k = (int)slabt.size();
+        slabidx[r * 8 + F] = k;
+        slabt.push_back(make_int4((int)r, F, k, 0));
+      }
+    }
+  }
+  f->n_fw = (int64_t)fw.size();
+  f->n_slab = (int64_t)slabt.size();
+  if (n) {
+    CK(cudaMemcpyAsync(f->d_nbh, nbh.data(), nbh.size() * 4, cudaMemcpyHostToDevice, f->st));
+    CK(cudaMemcpyAsync(f->d_binfo, binfo.data(), n * sizeof(int4), cudaMemcpyHostToDevice, f->st));
+    CK(cudaMemcpyAsync(f->d_blist, f->blist.data(), n * 4, cudaMemcpyHostToDevice, f->st));
+    CK(cudaMemcpyAsync(f->d_slabidx, slabidx.data(), n * 8 * 4, cudaMemcpyHostToDevice, f->st));
+  }
+  if (!fw.empty()) CK(cudaMemcpyAsync(f->d_fw, fw.data(), fw.size() * sizeof(int2), cudaMemcpyHostToDevice, f->st));
+  if (!slabt.empty())
+    CK(cudaMemcpyAsync(f->d_slabt, slabt.data(), slabt.size() * sizeof(int4), cudaMemcpyHostToDevice, f->st));
+  // the host vectors die at return: make the copies complete first
+  CK(cudaStreamSynchronize(f->st));
+  return ACM_OK;
+}
+
+template <typename T>
+T* reg_ptr(acm_forest* f, void* r) { return reinterpret_cast<T*>(r); }
+
+// Fine wins + coarse-face slabs on a register (the per-stage synchronisation).
+template <typename T>
+acm_status sync_stage(acm_forest* f, T* reg) {
+  const int Bs = f->gp.Bs;
+  if (f->n_fw) {
+    acm::launch_fine_wins<T>(Bs, reg, f->d_fw, f->n_fw, f->d_nbh, f->d_blist, f->st);
+    CKL();
+    ++f->launches;
+  }
+  if (f->n_slab) {
+    acm::launch_coarse_slabs<T>(Bs, reg, reinterpret_cast<T*>(f->SLAB), f->d_slabt, f->n_slab, f->d_nbh, f->st);
+    CKL();
+    ++f->launches;
+  }
+  return ACM_OK;
+}
+
+// Fine wins + the adaptation buffer (ghost depth kGE) of every block, slot-indexed.
+template <typename T>
+acm_status sync_ext(acm_forest* f, T* reg) {
+  const int Bs = f->gp.Bs;
+  if (f->n_fw) {
+    acm::launch_fine_wins<T>(Bs, reg, f->d_fw, f->n_fw, f->d_nbh, f->d_blist, f->st);
+    CKL();
+    ++f->launches;
+  }
+  acm::launch_sync_ext<T>(Bs, reg, reinterpret_cast<T*>(f->EXT), acm::kGE, f->d_blist,
+                          (int64_t)f->order.size(), f->d_nbh, 0, f->st);
+  CKL();
+  ++f->launches;
+  return ACM_OK;
+}
+
+template <typename T>
+acm_status max_norms(acm_forest* f, double out[5]) {
+  CK(cudaMemsetAsync(f->d_maxbits, 0, 8 * sizeof(unsigned long long), f->st));
+  acm::launch_maxnorm<T>(f->gp.Bs, reinterpret_cast<const T*>(f->U), f->d_blist, (int64_t)f->order.size(),
+                         f->d_maxbits, f->st);
+  CKL();
+  ++f->launches;
+  unsigned long long bits[5];
+  CK(cudaMemcpyAsync(bits, f->d_maxbits, sizeof(bits), cudaMemcpyDeviceToHost, f->st));
+  CK(cudaStreamSynchronize(f->st));
+  for (int k = 0; k < 5; ++k) {
+    double v;
+    std::memcpy(&v, &bits[k], 8);
+    out[k] = v;
+  }
+  for (int k = 0; k < 5; ++k)
+    if (!std::isfinite(out[k])) return fail(f, ACM_ENUMERIC, "non-finite value in the state");
+  return ACM_OK;
+}
+
+double h_of(const acm_forest* f, int J) { return f->gp.root_len / ((double)(1 << J) * (f->gp.Bs - 1)); }
+
+double cfl_dt(const acm_forest* f, double u_max) {
+  const acm_phys_params& p = f->pp;
+  const double h = h_of(f, f->Jtop);
+  const double ueig = std::fabs(u_max) + std::sqrt(u_max * u_max + p.c0 * p.c0);
+  double dt = p.cfl * h / ueig;
+  if (f->mask_on) dt = std::min(dt, p.cfl_eta * p.C_eta);
+  if (p.nu > 0) dt = std::min(dt, p.cfl_nu * h * h / p.nu);
+  return dt;
+}
+
+template <typename T>
+acm_status eval_mask(acm_forest* f) {
+  if (!f->mask_on) return ACM_OK;
+  acm::launch_mask<T>(f->gp.Bs, reinterpret_cast<T*>(f->CHI), f->d_blist, (int64_t)f->order.size(), f->d_binfo,
+                      f->phk, f->mask, f->st);
+  CKL();
+  ++f->launches;
+  return ACM_OK;
+}
+
+template <typename T>
+acm_status rk4(acm_forest* f, double dt, double* dt_used) {
+  if (f->order.empty()) return fail(f, ACM_EINVAL, "empty forest");
+  if (!(dt > 0)) {
+    double m[5];
+    acm_status s = max_norms<T>(f, m);
+    if (s) return s;
+    dt = cfl_dt(f, m[4]);
+  }
+  if (dt_used) *dt_used = dt;
+  T* U = reinterpret_cast<T*>(f->U);
+  T* ACC = reinterpret_cast<T*>(f->ACC);
+  T* YA = reinterpret_cast<T*>(f->YA);
+  T* YB = reinterpret_cast<T*>(f->YB);
+  const acm::TopoK t = topo(f);
+  const int64_t l0 = f->launches;
+  double stage_ms = 0, sync_ms = 0;
+  for (int s = 1; s <= 4; ++s) {
+    T* in = s == 1 ? U : (s == 2 ? YA : (s == 3 ? YB : YA));
+    T* out = s == 1 ? YA : (s == 2 ? YB : (s == 3 ? YA : U));
+    if (f->timing) CK(cudaEventRecord(f->ev[0], f->st));
+    acm_status st = sync_stage<T>(f, in);
+    if (st) return st;
+    if (f->timing) CK(cudaEventRecord(f->ev[1], f->st));
+    acm::StageK<T> a;
+    a.in = in;
+    a.U = U;
+    a.acc = ACC;
+    a.out = out;
+    a.chi = f->mask_on ? reinterpret_cast<const T*>(f->CHI) : nullptr;
+    a.slab = reinterpret_cast<const T*>(f->SLAB);
+    a.c_acc = s == 1 ? dt / 6.0 : dt / 3.0;
+    a.c_out = s == 1 || s == 2 ? dt / 2.0 : (s == 3 ? dt : dt / 6.0);
+    acm::launch_stage<T>(s, f->gp.Bs, a, t, f->phk, f->st);
+    CKL();
+    ++f->launches;
+    if (f->timing) {
+      CK(cudaEventRecord(f->ev[2], f->st));
+      CK(cudaEventSynchronize(f->ev[2]));
+      float a01 = 0, a12 = 0;
+      CK(cudaEventElapsedTime(&a01, f->ev[0], f->ev[1]));
+      CK(cudaEventElapsedTime(&a12, f->ev[1], f->ev[2]));
+      sync_ms += a01;
+      stage_ms += a12;
+    }
+  }
+  f->time += dt;
+  const double npts = (double)f->order.size() * f->gp.Bs * f->gp.Bs * f->gp.Bs;
+  const double words = 64.0 + (f->mask_on ? 4.0 : 0.0);
+  f->stats.stage_ms = stage_ms;
+  f->stats.sync_ms = sync_ms;
+  f->stats.stage_bytes = npts * words * (double)f->esz;
+  f->stats.n_launches = f->launches - l0;
+  return ACM_OK;
+}
+
+template <typename T>
+acm_status refine_all(acm_forest* f) {
+  acm::Forest& fo = *f->fo;
+  std::vector<BoxKey> parents;
+  for (const BoxKey& b : f->order)
+    if (b.J < fo.Jmax) parents.push_back(b);
+  if (parents.empty()) return ACM_OK;
+  if ((int64_t)parents.size() * 7 > fo.n_free())
+    return fail(f, ACM_ECAPACITY, "block pool too small to refine");
+  acm_status s = sync_ext<T>(f, reinterpret_cast<T*>(f->U));
+  if (s) return s;
+  std::vector<int32_t> old_slot(parents.size());
+  std::vector<BoxKey> kids;
+  kids.reserve(parents.size() * 8);
+  for (size_t i = 0; i < parents.size(); ++i) {
+    old_slot[i] = fo.leaves.at(parents[i]);
+    for (int c = 0; c < 8; ++c) kids.push_back(acm::Forest::child(parents[i], c));
+  }
+  std::vector<int32_t> new_slot;
+  if (!fo.apply_pass(parents, kids, &new_slot)) return fail(f, ACM_ECAPACITY, "block pool exhausted");
+  std::vector<int4> tasks(kids.size());
+  for (size_t i = 0; i < kids.size(); ++i) tasks[i] = make_int4(old_slot[i / 8], (int)(i % 8), new_slot[i], 0);
+  CK(cudaMemcpyAsync(f->d_reft, tasks.data(), tasks.size() * sizeof(int4), cudaMemcpyHostToDevice, f->st));
+  acm::launch_refine<T>(f->gp.Bs, reinterpret_cast<const T*>(f->EXT), reinterpret_cast<T*>(f->U), f->d_reft,
+                        (int64_t)tasks.size(), f->st);
+  CKL();
+  ++f->launches;
+  s = upload_topology(f);   // synchronises the stream (tasks buffer lifetime)
+  if (s) return s;
+  return eval_mask<T>(f);
+}
+
+template <typename T>
+acm_status indicators(acm_forest* f, const double norms[4]) {
+  acm_status s = sync_ext<T>(f, reinterpret_cast<T*>(f->U));
+  if (s) return s;
+  CK(cudaMemcpyAsync(f->d_norms, norms, 4 * sizeof(double), cudaMemcpyHostToDevice, f->st));
+  acm::launch_details<T>(f->gp.Bs, reinterpret_cast<const T*>(f->EXT),
+                         f->mask_on ? reinterpret_cast<const T*>(f->CHI) : nullptr, f->d_blist,
+                         (int64_t)f->order.size(), f->d_norms, f->d_ind, f->d_chir, f->st);
+  CKL();
+  ++f->launches;
+  CK(cudaStreamSynchronize(f->st));
+  return ACM_OK;
+}
+
+template <typename T>
+acm_status coarsen(acm_forest* f, int64_t* n_blocks, int* n_passes) {
+  acm::Forest& fo = *f->fo;
+  double m[5];
+  acm_status s = max_norms<T>(f, m);
+  if (s) return s;
+  const double norms[4] = {m[0], m[1], m[2], m[3]};
+  int passes = 0;
+  for (int it = 0; it < 64; ++it) {
+    s = indicators<T>(f, norms);
+    if (s) return s;
+    const size_t n = f->order.size();
+    std::vector<double> ind(n), chr(n);
+    CK(cudaMemcpyAsync(ind.data(), f->d_ind, n * 8, cudaMemcpyDeviceToHost, f->st));
+    CK(cudaMemcpyAsync(chr.data(), f->d_chir, n * 8, cudaMemcpyDeviceToHost, f->st));
+    CK(cudaStreamSynchronize(f->st));
+    std::unordered_map<BoxKey, bool, acm::BoxKeyHash> tag;
+    for (size_t r = 0; r < n; ++r) {
+      const BoxKey& b = f->order[r];
+      bool t = false;
+      if (b.J > fo.Jmin) {
+        if (f->pp.dealias && b.J == fo.Jmax) t = true;
+        else t = (ind[r] < f->pp.eps) && !(chr[r] > f->pp.mask_range_thr);
+      }
+      tag[b] = t;
+    }
+    // sister groups: parents whose 8 children are leaves, all tagged, none with a finer neighbour
+    std::vector<BoxKey> groups;
+    std::unordered_map<BoxKey, int, acm::BoxKeyHash> cnt;
+    for (const BoxKey& b : f->order)
+      if (b.J > 0) cnt[BoxKey{b.J - 1, b.x >> 1, b.y >> 1, b.z >> 1}]++;
+    for (const auto& kv : cnt) {
+      if (kv.second != 8) continue;
+      const BoxKey& p = kv.first;
+      bool ok = true;
+      for (int c = 0; c < 8 && ok; ++c) {
+        const BoxKey k = acm::Forest::child(p, c);
+        if (!tag[k]) { ok = false; break; }
+        for (int d = 0; d < 26 && ok; ++d) {
+          const int* dd = acm::kDirs.d[d];
+          const BoxStatus st = fo.box_status(k.J, (int64_t)k.x + dd[0], (int64_t)k.y + dd[1], (int64_t)k.z + dd[2]);
+          if (st.type == acm::BOX_REFINED) ok = false;
+        }
+      }
+      if (ok) groups.push_back(p);
+    }
+    if (groups.empty()) break;
+    std::sort(groups.begin(), groups.end(), [&](const BoxKey& a, const BoxKey& b) { return fo.key_less(a, b); });
+    std::vector<BoxKey> removed;
+    std::vector<std::array<int32_t, 8>> kid_slots(groups.size());
+    for (size_t g = 0; g < groups.size(); ++g)
+      for (int c = 0; c < 8; ++c) {
+        const BoxKey k = acm::Forest::child(groups[g], c);
+        kid_slots[g][c] = fo.leaves.at(k);
+        removed.push_back(k);
+      }
+    std::vector<int32_t> new_slot;
+    if (!fo.apply_pass(removed, groups, &new_slot)) return fail(f, ACM_ECAPACITY, "block pool exhausted");
+    std::vector<int32_t> tasks(groups.size() * 9);
+    for (size_t g = 0; g < groups.size(); ++g) {
+      tasks[9 * g] = new_slot[g];
+      for (int c = 0; c < 8; ++c) tasks[9 * g + 1 + c] = kid_slots[g][c];
+    }
+    CK(cudaMemcpyAsync(f->d_crst, tasks.data(), tasks.size() * 4, cudaMemcpyHostToDevice, f->st));
+    acm::launch_coarsen<T>(f->gp.Bs, reinterpret_cast<const T*>(f->EXT), reinterpret_cast<T*>(f->U), f->d_crst,
+                           (int64_t)groups.size(), f->st);
+    CKL();
+    ++f->launches;
+    s = upload_topology(f);
+    if (s) return s;
+    s = eval_mask<T>(f);
+    if (s) return s;
+    ++passes;
+  }
+  if (n_blocks) *n_blocks = (int64_t)f->order.size();
+  if (n_passes) *n_passes = passes;
+  return ACM_OK;
+}
+
+template <typename T>
+acm_status set_ic(acm_forest* f, int kind, const double* params, int n) {
+  acm::IcK ic{};
+  ic.kind = kind;
+  for (int i = 0; i < n && i < 8; ++i) ic.p[i] = params[i];
+  acm::launch_ic<T>(f->gp.Bs, reinterpret_cast<T*>(f->U), f->d_blist, (int64_t)f->order.size(), f->d_binfo,
+                    f->phk, ic, f->st);
+  CKL();
+  ++f->launches;
+  return ACM_OK;
+}
+
+template <typename T>
+acm_status diagnostics(acm_forest* f, acm_diag* out) {
+  std::memset(out, 0, sizeof(*out));
+  double m[5];
+  acm_status s = max_norms<T>(f, m);
+  if (s) return s;
+  const size_t n = f->order.size();
+  acm::launch_diag<T>(f->gp.Bs, reinterpret_cast<const T*>(f->U),
+                      f->mask_on ? reinterpret_cast<const T*>(f->CHI) : nullptr, f->d_blist, (int64_t)n,
+                      f->d_diag, f->st);
+  CKL();
+  ++f->launches;
+  std::vector<double> part(n * 4);
+  CK(cudaMemcpyAsync(part.data(), f->d_diag, n * 4 * 8, cudaMemcpyDeviceToHost, f->st));
+  CK(cudaStreamSynchronize(f->st));
+  for (size_t r = 0; r < n; ++r) {
+    const double h = h_of(f, f->order[r].J);
+    const double h3 = h * h * h;
+    for (int i = 0; i < 3; ++i) out->force[i] += part[4 * r + i] * h3 / f->pp.C_eta;
+    out->energy += 0.5 * part[4 * r + 3] * h3;
+    out->blocks_per_level[f->order[r].J]++;
+  }
+  out->u_max = m[4];
+  for (int k = 0; k < 4; ++k) out->norms[k] = m[k];
+  out->n_blocks = (int64_t)n;
+  out->time = f->time;
+  return ACM_OK;
+}
+
+void fill_phys(acm_forest* f) {
+  const acm_phys_params& p = f->pp;
+  acm::PhysK& k = f->phk;
+  k.nu = p.nu;
+  k.c0sq = p.c0 * p.c0;
+  k.inv_ceta = p.C_eta > 0 ? 1.0 / p.C_eta : 0.0;
+  k.cgamma = p.C_gamma;
+  k.sponge = (p.sponge && p.C_sp > 0) ? 1 : 0;
+  k.inv_csp = k.sponge ? 1.0 / p.C_sp : 0.0;
+  for (int a = 0; a < 3; ++a) k.uinf[a] = p.u_inf[a];
+  k.pinf = p.p_inf;
+  for (int a = 0; a < 3; ++a) k.sp_L[a] = p.sponge_L[a];
+  k.sp_width = p.sponge_width;
+  k.sp_delta = p.sponge_delta > 0 ? p.sponge_delta : 1.0;
+  k.root_len = f->gp.root_len;
+  for (int a = 0; a < 3; ++a) k.nroot[a] = f->gp.nroot[a];
+  const double a3 = f->gp.fd_scheme == 1 ? kTamWebbA3 : 0.0;
+  k.a1 = 2.0 / 3.0 + 5.0 * a3;
+  k.a2 = -1.0 / 12.0 - 4.0 * a3;
+  k.a3 = a3;
+  k.mask = f->mask_on ? 1 : 0;
+}
+
+#define DISPATCH(f, fn, ...) ((f)->gp.precision == 64 ? fn<double>(__VA_ARGS__) : fn<float>(__VA_ARGS__))
+
+}  // namespace
+
+extern "C" {
+
+size_t acm_pool_bytes(const acm_grid_params* grid) {
+  if (!valid_grid(grid)) return 0;
+  return carve(nullptr, grid, nullptr) + 256;
+}
+
+acm_status acm_create_forest(const acm_grid_params* grid, const acm_phys_params* phys, void* stream,
+                             void* device_pool, size_t pool_bytes, acm_forest** out) {
+  if (!out) return ACM_EINVAL;
+  *out = nullptr;
+  if (!valid_grid(grid) || !phys || !device_pool) return ACM_EINVAL;
+  const size_t need = acm_pool_bytes(grid);
+  if (pool_bytes < need) return ACM_ENOMEM;
+  if (((uintptr_t)device_pool) & 255) return ACM_EINVAL;
+  std::unique_ptr<acm_forest> f(new acm_forest());
+  f->gp = *grid;
+  f->pp = *phys;
+  f->st = reinterpret_cast<cudaStream_t>(stream);
+  f->pool = reinterpret_cast<char*>(device_pool);
+  f->pool_bytes = pool_bytes;
+  f->lay = acm::layout_info(grid->precision, grid->Bs);
+  f->esz = grid->precision == 64 ? 8 : 4;
+  carve(f.get(), grid, f->pool);
+  f->fo.reset(new acm::Forest(grid->nroot, grid->Bs, grid->Jmin, grid->Jmax, grid->max_blocks));
+  fill_phys(f.get());
+  acm_forest* fp = f.get();
+  {
+    acm_forest* f = fp;   // for CK
+    CK(cudaEventCreate(&f->ev[0]));
+    CK(cudaEventCreate(&f->ev[1]));
+    CK(cudaEventCreate(&f->ev[2]));
+  }
+  *out = f.release();
+  return ACM_OK;
+}
+
+acm_status acm_destroy_forest(acm_forest* f) {
+  if (!f) return ACM_OK;
+  for (auto& e : f->ev)
+    if (e) cudaEventDestroy(e);
+  delete f;
+  return ACM_OK;
+}
+
+acm_status acm_init_uniform(acm_forest* f, int J) {
+  if (!f) return ACM_EINVAL;
+  if (J < f->gp.Jmin || J > f->gp.Jmax) return fail(f, ACM_EINVAL, "level outside [Jmin, Jmax]");
+  std::vector<int32_t> lv, gx, gy, gz;
+  const int64_t nx = (int64_t)f->gp.nroot[0] << J, ny = (int64_t)f->gp.nroot[1] << J, nz = (int64_t)f->gp.nroot[2] << J;
+  if (nx * ny * nz > f->gp.max_blocks) return fail(f, ACM_ECAPACITY, "uniform grid exceeds max_blocks");
+  for (int64_t z = 0; z < nz; ++z)
+    for (int64_t y = 0; y < ny; ++y)
+      for (int64_t x = 0; x < nx; ++x) {
+        lv.push_back(J);
+        gx.push_back((int32_t)x);
+        gy.push_back((int32_t)y);
+        gz.push_back((int32_t)z);
+      }
+  return acm_set_leaves(f, lv.data(), gx.data(), gy.data(), gz.data(), (int64_t)lv.size());
+}
+
+acm_status acm_set_leaves(acm_forest* f, const int32_t* level, const int32_t* gx, const int32_t* gy,
+                          const int32_t* gz, int64_t n) {
+  if (!f || !level || !gx || !gy || !gz || n <= 0) return fail(f, ACM_EINVAL, "bad leaves");
+  if (n > f->gp.max_blocks) return fail(f, ACM_ECAPACITY, "more leaves than max_blocks");
+  acm::Forest trial(f->gp.nroot, f->gp.Bs, f->gp.Jmin, f->gp.Jmax, f->gp.max_blocks);
+  std::vector<BoxKey> created((size_t)n);
+  for (int64_t i = 0; i < n; ++i) {
+    if (level[i] < 0 || level[i] > 18) return fail(f, ACM_EINVAL, "level out of range");
+    for (int a = 0; a < 3; ++a) {
+      const int32_t v = a == 0 ? gx[i] : (a == 1 ? gy[i] : gz[i]);
+      if (v < 0 || v >= trial.nblocks_axis(level[i], a)) return fail(f, ACM_EINVAL, "block coordinate out of range");
+    }
+    created[i] = BoxKey{level[i], gx[i], gy[i], gz[i]};
+  }
+  trial.apply_pass({}, created, nullptr);
+  if ((int64_t)trial.leaves.size() != n) return fail(f, ACM_EGRADING, "duplicate leaves");
+  if (!trial.tiles_domain()) return fail(f, ACM_EGRADING, "leaves do not tile the domain");
+  if (!trial.is_graded()) return fail(f, ACM_EGRADING, "leaves are not 2:1 graded");
+  f->fo->clear();
+  f->fo->apply_pass({}, created, nullptr);
+  acm_status s = upload_topology(f);
+  if (s) return s;
+  const size_t blk = (size_t)f->lay.BLK * f->esz;
+  for (int32_t sl : f->blist) CK(cudaMemsetAsync((char*)f->U + (size_t)sl * blk, 0, blk, f->st));
+  f->time = 0.0;
+  s = DISPATCH(f, eval_mask, f);
+  if (s) return s;
+  CK(cudaStreamSynchronize(f->st));
+  return ACM_OK;
+}
+
+acm_status acm_set_ic(acm_forest* f, int kind, const double* params, int n) {
+  if (!f) return ACM_EINVAL;
+  if (kind < 1 || kind > 3 || (n > 0 && !params)) return fail(f, ACM_EINVAL, "bad initial condition");
+  if (f->order.empty()) return fail(f, ACM_EINVAL, "empty forest");
+  acm_status s = DISPATCH(f, set_ic, f, kind, params, n);
+  if (s) return s;
+  CK(cudaStreamSynchronize(f->st));
+  return ACM_OK;
+}
+
+acm_status acm_set_mask(acm_forest* f, int kind, const double* params, int n, double t) {
+  (void)t;
+  if (!f) return ACM_EINVAL;
+  if (kind == ACM_MASK_NONE) {
+    f->mask_on = false;
+  } else if (kind == ACM_MASK_SPHERE) {
+    if (!params || n < 5 || !(params[4] > 0)) return fail(f, ACM_EINVAL, "sphere mask needs cx, cy, cz, R, delta>0");
+    f->mask_on = true;
+    f->mask.kind = 1;
+    for (int i = 0; i < 5; ++i) f->mask.p[i] = params[i];
+  } else {
+    return fail(f, ACM_EINVAL, "unknown mask kind");
+  }
+  fill_phys(f);
+  if (!f->order.empty()) {
+    acm_status s = DISPATCH(f, eval_mask, f);
+    if (s) return s;
+    CK(cudaStreamSynchronize(f->st));
+  }
+  return ACM_OK;
+}
+
+acm_status acm_sync_ghosts(acm_forest* f, int reg, void* out, int on_device) {
+  if (!f || !out || reg != ACM_REG_U) return fail(f, ACM_EINVAL, "bad arguments");
+  const int g = f->gp.g;
+  const int ne = f->gp.Bs + 2 * g;
+  const size_t per = (size_t)4 * ne * ne * ne * f->esz;
+  const size_t n = f->order.size();
+  // fine wins on U, then the extended arrays in chunks that fit the adaptation buffer
+  if (f->n_fw) {
+    if (f->gp.precision == 64)
+      acm::launch_fine_wins<double>(f->gp.Bs, (double*)f->U, f->d_fw, f->n_fw, f->d_nbh, f->d_blist, f->st);
+    else
+      acm::launch_fine_wins<float>(f->gp.Bs, (float*)f->U, f->d_fw, f->n_fw, f->d_nbh, f->d_blist, f->st);
+    CKL();
+    ++f->launches;
+  }
+  const size_t cap = (size_t)f->gp.max_blocks * f->lay.EBLK * f->esz / per;
+  for (size_t r0 = 0; r0 < n; r0 += cap) {
+    const size_t m = std::min(cap, n - r0);
+    char* dst = on_device ? (char*)out + r0 * per : (char*)f->EXT;
+    if (f->gp.precision == 64)
+      acm::launch_sync_ext<double>(f->gp.Bs, (const double*)f->U, (double*)dst, g, f->d_blist + r0, (int64_t)m,
+                                   f->d_nbh + r0 * acm::kNbhStride, 1, f->st);
+    else
+      acm::launch_sync_ext<float>(f->gp.Bs, (const float*)f->U, (float*)dst, g, f->d_blist + r0, (int64_t)m,
+                                  f->d_nbh + r0 * acm::kNbhStride, 1, f->st);
+    CKL();
+    ++f->launches;
+    if (!on_device) {
+      CK(cudaMemcpyAsync((char*)out + r0 * per, f->EXT, m * per, cudaMemcpyDeviceToHost, f->st));
+      CK(cudaStreamSynchronize(f->st));
+    }
+  }
+  CK(cudaStreamSynchronize(f->st));
+  return ACM_OK;
+}
+
+acm_status acm_rk4_step(acm_forest* f, double dt, double* dt_used) {
+  if (!f) return ACM_EINVAL;
+  return DISPATCH(f, rk4, f, dt, dt_used);
+}
+
+acm_status acm_refine_all(acm_forest* f) {
+  if (!f) return ACM_EINVAL;
+  acm_status s = DISPATCH(f, refine_all, f);
+  if (s) return s;
+  CK(cudaStreamSynchronize(f->st));
+  return ACM_OK;
+}
+
+acm_status acm_coarsen(acm_forest* f, int64_t* n_blocks, int* n_passes) {
+  if (!f) return ACM_EINVAL;
+  acm_status s = DISPATCH(f, coarsen, f, n_blocks, n_passes);
+  if (s) return s;
+  CK(cudaStreamSynchronize(f->st));
+  return ACM_OK;
+}
+
+acm_status acm_step(acm_forest* f, double dt, double* dt_used, int64_t* n_blocks) {
+  if (!f) return ACM_EINVAL;
+  acm_status s = acm_refine_all(f);
+  if (s) return s;
+  s = acm_rk4_step(f, dt, dt_used);
+  if (s) return s;
+  return acm_coarsen(f, n_blocks, nullptr);
+}
+
+acm_status acm_init_grid(acm_forest* f, int ic_kind, const double* params, int n, int64_t* n_blocks) {
+  if (!f) return ACM_EINVAL;
+  acm_status s = acm_init_uniform(f, f->gp.Jmin);
+  if (s) return s;
+  s = acm_set_ic(f, ic_kind, params, n);
+  if (s) return s;
+  for (int it = 0; it < 64; ++it) {
+    std::vector<BoxKey> before = f->order;
+    // refine all, then evaluate the initial condition analytically on the new grid
+    s = acm_refine_all(f);
+    if (s) return s;
+    s = acm_set_ic(f, ic_kind, params, n);
+    if (s) return s;
+    s = acm_coarsen(f, nullptr, nullptr);
+    if (s) return s;
+    if (f->order == before) {
+      if (n_blocks) *n_blocks = (int64_t)f->order.size();
+      f->time = 0.0;
+      return ACM_OK;
+    }
+  }
+  return fail(f, ACM_EINVAL, "initial grid did not converge");
+}
+
+acm_status acm_block_indicators(acm_forest* f, double* ind, double* chirange, int64_t n) {
+  if (!f) return ACM_EINVAL;
+  if (n < (int64_t)f->order.size()) return fail(f, ACM_EINVAL, "output arrays too small");
+  double m[5];
+  acm_status s = f->gp.precision == 64 ? max_norms<double>(f, m) : max_norms<float>(f, m);
+  if (s) return s;
+  const double norms[4] = {m[0], m[1], m[2], m[3]};
+  s = f->gp.precision == 64 ? indicators<double>(f, norms) : indicators<float>(f, norms);
+  if (s) return s;
+  const size_t nb = f->order.size();
+  if (ind) CK(cudaMemcpyAsync(ind, f->d_ind, nb * 8, cudaMemcpyDeviceToHost, f->st));
+  if (chirange) CK(cudaMemcpyAsync(chirange, f->d_chir, nb * 8, cudaMemcpyDeviceToHost, f->st));
+  CK(cudaStreamSynchronize(f->st));
+  return ACM_OK;
+}
+
+acm_status acm_diagnostics(acm_forest* f, acm_diag* out) {
+  if (!f || !out) return ACM_EINVAL;
+  if (f->order.empty()) return fail(f, ACM_EINVAL, "empty forest");
+  return DISPATCH(f, diagnostics, f, out);
+}
+
+int64_t acm_n_blocks(const acm_forest* f) { return f ? (int64_t)f->order.size() : 0; }
+
+acm_status acm_get_topology(acm_forest* f, uint64_t* treecode, uint8_t* level, int32_t* slot, int32_t* gx,
+                            int32_t* gy, int32_t* gz, int32_t* nbr, int8_t* rel, int64_t n) {
+  if (!f) return ACM_EINVAL;
+  const size_t nb = f->order.size();
+  if (n < (int64_t)nb) return fail(f, ACM_EINVAL, "output arrays too small");
+  for (size_t r = 0; r < nb; ++r) {
+    const BoxKey& b = f->order[r];
+    if (treecode) treecode[r] = f->fo->treecode(b);
+    if (level) level[r] = (uint8_t)b.J;
+    if (slot) slot[r] = f->blist[r];
+    if (gx) gx[r] = b.x;
+    if (gy) gy[r] = b.y;
+    if (gz) gz[r] = b.z;
+  }
+  if (nbr || rel) {
+    std::vector<int32_t> nb56(nb * 56);
+    std::vector<int8_t> r26(nb * 26);
+    f->fo->neighbour_table(f->order, nb56.data(), r26.data());
+    if (nbr) std::memcpy(nbr, nb56.data(), nb56.size() * 4);
+    if (rel) std::memcpy(rel, r26.data(), r26.size());
+  }
+  return ACM_OK;
+}
+
+static acm_status copy_fields(acm_forest* f, void* buf, int64_t n_elems, int on_device, bool to_pool, int ncomp,
+                              void* reg) {
+  const int64_t nb = (int64_t)f->order.size();
+  const int64_t need = nb * ncomp * (int64_t)f->gp.Bs * f->gp.Bs * f->gp.Bs;
+  if (n_elems != need) return fail(f, ACM_EINVAL, "element count does not match n_blocks*comp*Bs^3");
+  const size_t bytes = (size_t)need * f->esz;
+  void* dense = on_device ? buf : f->EXT;
+  if (to_pool) {
+    if (!on_device) CK(cudaMemcpyAsync(dense, buf, bytes, cudaMemcpyHostToDevice, f->st));
+    if (f->gp.precision == 64)
+      acm::launch_scatter<double>(f->gp.Bs, (const double*)dense, (double*)reg, f->d_blist, nb, f->st);
+    else
+      acm::launch_scatter<float>(f->gp.Bs, (const float*)dense, (float*)reg, f->d_blist, nb, f->st);
+  } else {
+    if (f->gp.precision == 64)
+      acm::launch_gather<double>(f->gp.Bs, (const double*)reg, (double*)dense, f->d_blist, nb, ncomp, f->st);
+    else
+      acm::launch_gather<float>(f->gp.Bs, (const float*)reg, (float*)dense, f->d_blist, nb, ncomp, f->st);
+  }
+  CKL();
+  ++f->launches;
+  if (!to_pool && !on_device) CK(cudaMemcpyAsync(buf, dense, bytes, cudaMemcpyDeviceToHost, f->st));
+  CK(cudaStreamSynchronize(f->st));
+  return ACM_OK;
+}
+
+acm_status acm_read_fields(acm_forest* f, int reg, void* out, int64_t n_elems, int on_device) {
+  if (!f || !out || reg != ACM_REG_U) return fail(f, ACM_EINVAL, "bad arguments");
+  return copy_fields(f, out, n_elems, on_device, false, 4, f->U);
+}
+
+acm_status acm_write_fields(acm_forest* f, const void* in, int64_t n_elems, int on_device) {
+  if (!f || !in) return fail(f, ACM_EINVAL, "bad arguments");
+  return copy_fields(f, const_cast<void*>(in), n_elems, on_device, true, 4, f->U);
+}
+
+acm_status acm_read_mask(acm_forest* f, void* out, int64_t n_elems, int on_device) {
+  if (!f || !out) return fail(f, ACM_EINVAL, "bad arguments");
+  if (!f->mask_on) return fail(f, ACM_EINVAL, "no mask set");
+  return copy_fields(f, out, n_elems, on_device, false, 1, f->CHI);
+}
+
+acm_status acm_rhs(acm_forest* f, void* out, int64_t n_elems, int on_device) {
+  if (!f || !out) return fail(f, ACM_EINVAL, "bad arguments");
+  if (f->order.empty()) return fail(f, ACM_EINVAL, "empty forest");
+  acm::TopoK t = topo(f);
+  if (f->gp.precision == 64) {
+    acm_status s = sync_stage<double>(f, (double*)f->U);
+    if (s) return s;
+    acm::StageK<double> a{(const double*)f->U, (const double*)f->U, (double*)f->ACC, (double*)f->YA,
+                          f->mask_on ? (const double*)f->CHI : nullptr, (const double*)f->SLAB, 0.0, 0.0};
+    acm::launch_stage<double>(0, f->gp.Bs, a, t, f->phk, f->st);
+  } else {
+    acm_status s = sync_stage<float>(f, (float*)f->U);
+    if (s) return s;
+    acm::StageK<float> a{(const float*)f->U, (const float*)f->U, (float*)f->ACC, (float*)f->YA,
+                         f->mask_on ? (const float*)f->CHI : nullptr, (const float*)f->SLAB, 0.0, 0.0};
+    acm::launch_stage<float>(0, f->gp.Bs, a, t, f->phk, f->st);
+  }
+  CKL();
+  ++f->launches;
+  return copy_fields(f, out, n_elems, on_device, false, 4, f->ACC);
+}
+
+acm_status acm_enable_timing(acm_forest* f, int on) {
+  if (!f) return ACM_EINVAL;
+  f->timing = on != 0;
+  return ACM_OK;
+}
+
+acm_status acm_last_step_stats(acm_forest* f, acm_step_stats* out) {
+  if (!f || !out) return ACM_EINVAL;
+  *out = f->stats;
+  return ACM_OK;
+}
+
+int64_t acm_launch_count(const acm_forest* f) { return f ? f->launches : 0; }
+
+const char* acm_last_error(const acm_forest* f) { return f ? f->err.c_str() : "null forest"; }
+
+const char* acm_status_string(acm_status s) {
+  switch (s) {
+    case ACM_OK: return "ok";
+    case ACM_EINVAL: return "invalid argument";
+    case ACM_ENOMEM: return "pool too small";
+    case ACM_ECAPACITY: return "block pool exhausted";
+    case ACM_ECUDA: return "CUDA error";
+    case ACM_ETIMEOUT: return "device wait timed out";
+    case ACM_ENUMERIC: return "non-finite value";
+    case ACM_EGRADING: return "layout not graded or not tiling";
+  }
+  return "unknown";
+}
+
+}  // extern "C"

@@ -1,0 +1,218 @@
+// Host-side block tree of libacm (see forest.hpp).
+#include "forest.hpp"
+
+#include <algorithm>
+
+namespace acm {
+
+Directions::Directions() {
+  int nf = 0, ne = 6, nc = 18;
+  for (int dz = -1; dz <= 1; ++dz)
+    for (int dy = -1; dy <= 1; ++dy)
+      for (int dx = -1; dx <= 1; ++dx) {
+        int n = (dx != 0) + (dy != 0) + (dz != 0);
+        int* slot = nullptr;
+        if (n == 1) slot = d[nf++];
+        else if (n == 2) slot = d[ne++];
+        else if (n == 3) slot = d[nc++];
+        if (slot) { slot[0] = dx; slot[1] = dy; slot[2] = dz; }
+      }
+}
+const Directions kDirs;
+
+Forest::Forest(const int nr[3], int bs, int jmin, int jmax, int64_t maxb)
+    : Bs(bs), M(bs - 1), Jmin(jmin), Jmax(jmax), max_blocks(maxb) {
+  for (int a = 0; a < 3; ++a) nroot[a] = nr[a];
+  clear();
+}
+
+void Forest::clear() {
+  leaves.clear();
+  free_.clear();
+  for (int64_t s = 0; s < max_blocks; ++s) free_.insert(free_.end(), (int32_t)s);
+}
+
+BoxKey Forest::wrap(int J, int64_t x, int64_t y, int64_t z) const {
+  int64_t v[3] = {x, y, z};
+  for (int a = 0; a < 3; ++a) {
+    int64_t n = nblocks_axis(J, a);
+    v[a] %= n;
+    if (v[a] < 0) v[a] += n;
+  }
+  return BoxKey{J, (int32_t)v[0], (int32_t)v[1], (int32_t)v[2]};
+}
+
+uint64_t Forest::treecode(const BoxKey& k) const {
+  const int J = k.J;
+  const uint64_t rx = (uint64_t)k.x >> J, ry = (uint64_t)k.y >> J, rz = (uint64_t)k.z >> J;
+  const uint64_t root = rx + (uint64_t)nroot[0] * (ry + (uint64_t)nroot[1] * rz);
+  uint64_t code = root << 56;
+  for (int l = 1; l <= J; ++l) {
+    const int sh = J - l;
+    const uint64_t digit = (((uint64_t)k.x >> sh) & 1) | ((((uint64_t)k.y >> sh) & 1) << 1) |
+                           ((((uint64_t)k.z >> sh) & 1) << 2);
+    code |= digit << (3 * (18 - l));
+  }
+  return code;
+}
+
+bool Forest::key_less(const BoxKey& a, const BoxKey& b) const {
+  const uint64_t ta = treecode(a), tb = treecode(b);
+  if (ta != tb) return ta < tb;
+  return a.J < b.J;
+}
+
+std::vector<BoxKey> Forest::sorted() const {
+  std::vector<std::pair<std::pair<uint64_t, int>, BoxKey>> tmp;
+  tmp.reserve(leaves.size());
+  for (const auto& kv : leaves) tmp.push_back({{treecode(kv.first), kv.first.J}, kv.first});
+  std::sort(tmp.begin(), tmp.end(),
+            [](const auto& a, const auto& b) { return a.first < b.first; });
+  std::vector<BoxKey> out;
+  out.reserve(tmp.size());
+  for (auto& t : tmp) out.push_back(t.second);
+  return out;
+}
+
+bool Forest::apply_pass(const std::vector<BoxKey>& removed, const std::vector<BoxKey>& created,
+                        std::vector<int32_t>* created_slots) {
+  if ((int64_t)created.size() - (int64_t)removed.size() > (int64_t)free_.size()) return false;
+  for (const BoxKey& k : removed) {
+    auto it = leaves.find(k);
+    if (it == leaves.end()) continue;
+    free_.insert(it->second);
+    leaves.erase(it);
+  }
+  std::vector<size_t> idx(created.size());
+  for (size_t i = 0; i < idx.size(); ++i) idx[i] = i;
+  std::vector<std::pair<uint64_t, int>> keys(created.size());
+  for (size_t i = 0; i < created.size(); ++i) keys[i] = {treecode(created[i]), created[i].J};
+  std::sort(idx.begin(), idx.end(), [&](size_t a, size_t b) { return keys[a] < keys[b]; });
+  if (created_slots) created_slots->assign(created.size(), -1);
+  for (size_t i : idx) {
+    const int32_t s = *free_.begin();
+    free_.erase(free_.begin());
+    leaves[created[i]] = s;
+    if (created_slots) (*created_slots)[i] = s;
+  }
+  return true;
+}
+
+BoxStatus Forest::box_status(int J, int64_t x, int64_t y, int64_t z) const {
+  BoxStatus st;
+  st.type = BOX_NONE;
+  st.octant = 0;
+  for (int c = 0; c < 8; ++c) st.slot[c] = -1;
+  const BoxKey k = wrap(J, x, y, z);
+  auto it = leaves.find(k);
+  if (it != leaves.end()) {
+    st.type = BOX_LEAF;
+    st.slot[0] = it->second;
+    return st;
+  }
+  if (J > 0) {
+    auto ip = leaves.find(BoxKey{J - 1, k.x >> 1, k.y >> 1, k.z >> 1});
+    if (ip != leaves.end()) {
+      st.type = BOX_COARSER;
+      st.slot[0] = ip->second;
+      st.octant = (k.x & 1) | ((k.y & 1) << 1) | ((k.z & 1) << 2);
+      return st;
+    }
+  }
+  bool any = false;
+  for (int c = 0; c < 8; ++c) {
+    auto ic = leaves.find(child(k, c));
+    if (ic != leaves.end()) {
+      st.slot[c] = ic->second;
+      any = true;
+    }
+  }
+  if (any) st.type = BOX_REFINED;
+  return st;
+}
+
+// Children of the box at offset d that touch the block (ascending child number).
+static int touching_children(const int d[3], int out[8]) {
+  int n = 0;
+  for (int c = 0; c < 8; ++c) {
+    const int cc[3] = {c & 1, (c >> 1) & 1, (c >> 2) & 1};
+    bool ok = true;
+    for (int a = 0; a < 3; ++a) {
+      if (d[a] == 1 && cc[a] != 0) ok = false;
+      if (d[a] == -1 && cc[a] != 1) ok = false;
+    }
+    if (ok) out[n++] = c;
+  }
+  return n;
+}
+
+bool Forest::is_graded() const {
+  for (const auto& kv : leaves) {
+    const BoxKey& b = kv.first;
+    for (int k = 0; k < 26; ++k) {
+      const int* d = kDirs.d[k];
+      BoxStatus st = box_status(b.J, (int64_t)b.x + d[0], (int64_t)b.y + d[1], (int64_t)b.z + d[2]);
+      if (st.type == BOX_NONE) return false;
+      if (st.type == BOX_REFINED) {
+        int tc[8];
+        const int n = touching_children(d, tc);
+        for (int i = 0; i < n; ++i)
+          if (st.slot[tc[i]] < 0) return false;
+      }
+    }
+  }
+  return true;
+}
+
+bool Forest::tiles_domain() const {
+  if (leaves.empty()) return false;
+  int Jref = 0;
+  for (const auto& kv : leaves) Jref = std::max(Jref, kv.first.J);
+  // volume count in units of level-Jref boxes, then no overlap via the parent chain
+  __int128 vol = 0;
+  for (const auto& kv : leaves) {
+    const int s = Jref - kv.first.J;
+    vol += (__int128)1 << (3 * s);
+  }
+  __int128 total = (__int128)nblocks_axis(Jref, 0) * nblocks_axis(Jref, 1) * nblocks_axis(Jref, 2);
+  if (vol != total) return false;
+  for (const auto& kv : leaves) {
+    const BoxKey& b = kv.first;
+    for (int L = b.J - 1; L >= 0; --L) {
+      const int s = b.J - L;
+      if (leaves.count(BoxKey{L, b.x >> s, b.y >> s, b.z >> s})) return false;
+    }
+  }
+  return true;
+}
+
+void Forest::neighbour_table(const std::vector<BoxKey>& order, int32_t* nbr, int8_t* rel) const {
+  for (size_t i = 0; i < order.size(); ++i) {
+    const BoxKey& b = order[i];
+    int32_t* row = nbr + 56 * i;
+    for (int e = 0; e < 56; ++e) row[e] = -1;
+    for (int k = 0; k < 26; ++k) {
+      const int* d = kDirs.d[k];
+      const BoxStatus st =
+          box_status(b.J, (int64_t)b.x + d[0], (int64_t)b.y + d[1], (int64_t)b.z + d[2]);
+      int s0, n;
+      group_of(k, &s0, &n);
+      if (st.type == BOX_LEAF) {
+        row[s0] = st.slot[0];
+        rel[26 * i + k] = 0;
+      } else if (st.type == BOX_COARSER) {
+        row[s0] = st.slot[0];
+        rel[26 * i + k] = -1;
+      } else if (st.type == BOX_REFINED) {
+        int tc[8];
+        const int nt = touching_children(d, tc);
+        for (int j = 0; j < nt && j < n; ++j) row[s0 + j] = st.slot[tc[j]];
+        rel[26 * i + k] = 1;
+      } else {
+        rel[26 * i + k] = 0;
+      }
+    }
+  }
+}
+
+}  // namespace acm

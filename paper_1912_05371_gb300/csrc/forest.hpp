@@ -1,0 +1,99 @@
+// Host-side block tree of libacm: leaves, octal treecodes, slot pool, neighbour queries.
+//
+// Paper, Sec. 4.1: equal-size Bs^3 blocks held in one preallocated array, positioned by
+// octal (Gargantini) treecodes from which level, position and neighbours are computed; the
+// tree metadata lives apart from the block data.  Sec. 3.5: refinement of all blocks and
+// coarsening of sister groups, keeping the grid graded.  The rules fixed here (treecode bit
+// layout, slot assignment, table layout, 26-neighbour 2:1 grading) are the ones documented in
+// include/acm.h.
+#pragma once
+
+#include <cstdint>
+#include <set>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+namespace acm {
+
+struct BoxKey {
+  int32_t J, x, y, z;
+  bool operator==(const BoxKey& o) const { return J == o.J && x == o.x && y == o.y && z == o.z; }
+};
+
+struct BoxKeyHash {
+  size_t operator()(const BoxKey& k) const {
+    uint64_t h = (uint64_t)(uint32_t)k.J * 0x9E3779B97F4A7C15ull;
+    h ^= (uint64_t)(uint32_t)k.x + 0x7F4A7C159E3779B9ull + (h << 6) + (h >> 2);
+    h ^= (uint64_t)(uint32_t)k.y + 0x94D049BB133111EBull + (h << 6) + (h >> 2);
+    h ^= (uint64_t)(uint32_t)k.z + 0xBF58476D1CE4E5B9ull + (h << 6) + (h >> 2);
+    return (size_t)h;
+  }
+};
+
+enum BoxType : uint8_t { BOX_LEAF = 0, BOX_COARSER = 1, BOX_REFINED = 2, BOX_NONE = 3 };
+
+// Status of a level-J box as seen from a neighbour: a leaf itself, covered by a leaf one
+// level coarser (slot[0], octant = which half per axis), or refined into level J+1 leaves
+// (slot[c] for child c = cx + 2cy + 4cz, -1 where the child is not a leaf).
+struct BoxStatus {
+  BoxType type;
+  int32_t slot[8];
+  int octant;
+};
+
+// 26 neighbour directions: iterate dz, dy, dx over -1, 0, 1 (x fastest); faces, then edges,
+// then corners.
+struct Directions {
+  int d[26][3];
+  Directions();
+};
+extern const Directions kDirs;
+
+// First table entry of direction k in the 56-entry layout and the group size.
+inline void group_of(int k, int* start, int* n) {
+  if (k < 6) { *start = 4 * k; *n = 4; }
+  else if (k < 18) { *start = 24 + 2 * (k - 6); *n = 2; }
+  else { *start = 48 + (k - 18); *n = 1; }
+}
+
+class Forest {
+ public:
+  Forest(const int nroot[3], int Bs, int Jmin, int Jmax, int64_t max_blocks);
+
+  int nroot[3];
+  int Bs, M, Jmin, Jmax;
+  int64_t max_blocks;
+  std::unordered_map<BoxKey, int32_t, BoxKeyHash> leaves;
+
+  int64_t nblocks_axis(int J, int a) const { return (int64_t)nroot[a] << J; }
+  BoxKey wrap(int J, int64_t x, int64_t y, int64_t z) const;
+  uint64_t treecode(const BoxKey& k) const;
+  bool key_less(const BoxKey& a, const BoxKey& b) const;
+  std::vector<BoxKey> sorted() const;
+  int64_t n_free() const { return (int64_t)free_.size(); }
+
+  void clear();
+  // One adaptation pass: release the slots of `removed`, then give `created` (any order)
+  // the lowest free slots in ascending key order.  Returns false (and changes nothing) if
+  // the pool is too small.  created_slots[i] is the slot of created[i].
+  bool apply_pass(const std::vector<BoxKey>& removed, const std::vector<BoxKey>& created,
+                  std::vector<int32_t>* created_slots);
+
+  BoxStatus box_status(int J, int64_t x, int64_t y, int64_t z) const;
+  bool is_graded() const;
+  bool tiles_domain() const;
+
+  // Children of a box, child c = cx + 2cy + 4cz.
+  static BoxKey child(const BoxKey& p, int c) {
+    return BoxKey{p.J + 1, 2 * p.x + (c & 1), 2 * p.y + ((c >> 1) & 1), 2 * p.z + ((c >> 2) & 1)};
+  }
+
+  // 56-entry neighbour slots and 26 relative levels of each block of `order`.
+  void neighbour_table(const std::vector<BoxKey>& order, int32_t* nbr, int8_t* rel) const;
+
+ private:
+  std::set<int32_t> free_;
+};
+
+}  // namespace acm

@@ -1,0 +1,107 @@
+// Internal launch interface of the libacm kernels (host side).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace acm {
+
+// Per-launch model constants (Sec. 2.1-2.3), in double; kernels convert to their precision.
+struct PhysK {
+  double nu, c0sq, inv_ceta, cgamma, inv_csp;
+  double uinf[3], pinf;
+  int mask, sponge;
+  double sp_L[3], sp_width, sp_delta;
+  double root_len;
+  int nroot[3];
+  double a1, a2, a3;        // first-derivative coefficients
+};
+
+// Device topology: pointers into the pool, all indexed by rank (position in block order).
+struct TopoK {
+  const int32_t* nbh;       // [n][kNbhStride] neighbourhood tables
+  const int4* binfo;        // [n] (J, gx, gy, gz)
+  const int32_t* blist;     // [n] slot of each block
+  const int32_t* slabidx;   // [n][8]: coarse-face halo slab per face (-1: none)
+  int64_t n;
+};
+
+// Stage of the fused RK4 update (Sec. 2.3).  in: the stage state (synchronised); U: the
+// state at t^n; acc: the RK accumulator; out: next stage state (or U^{n+1} in stage 4).
+template <typename T>
+struct StageK {
+  const T* in;
+  const T* U;
+  T* acc;
+  T* out;
+  const T* chi;
+  const T* slab;
+  double c_acc, c_out;      // stage coefficients (see stage.cu)
+};
+
+template <typename T>
+void launch_stage(int stage, int Bs, const StageK<T>& s, const TopoK& t, const PhysK& p,
+                  cudaStream_t st);
+
+template <typename T>
+void launch_fine_wins(int Bs, T* reg, const int2* tasks, int64_t ntasks, const int32_t* nbh,
+                      const int32_t* blist, cudaStream_t st);
+
+template <typename T>
+void launch_coarse_slabs(int Bs, const T* reg, T* slab, const int4* tasks, int64_t ntasks,
+                         const int32_t* nbh, cudaStream_t st);
+
+// Extended arrays (interior + g ghost layers) of all n blocks: out index = rank if by_rank,
+// else slot.
+template <typename T>
+void launch_sync_ext(int Bs, const T* reg, T* out, int g, const int32_t* blist, int64_t n,
+                     const int32_t* nbh, int by_rank, cudaStream_t st);
+
+template <typename T>
+void launch_details(int Bs, const T* ext, const T* chi, const int32_t* blist, int64_t n,
+                    const double* norms, double* ind, double* chirange, cudaStream_t st);
+
+// Max norms: out[0..3] = max |u|,|v|,|w|,|p|, out[4] = max |(u,v,w)|, as ordered bit patterns
+// (non-negative doubles) combined with atomicMax; out must be zeroed before.
+template <typename T>
+void launch_maxnorm(int Bs, const T* reg, const int32_t* blist, int64_t n,
+                    unsigned long long* out, cudaStream_t st);
+
+template <typename T>
+void launch_refine(int Bs, const T* ext, T* reg, const int4* tasks, int64_t ntasks,
+                   cudaStream_t st);
+
+template <typename T>
+void launch_coarsen(int Bs, const T* ext, T* reg, const int32_t* tasks /*[n][9]*/, int64_t ntasks,
+                    cudaStream_t st);
+
+struct IcK {
+  int kind;
+  double p[8];
+};
+template <typename T>
+void launch_ic(int Bs, T* reg, const int32_t* list, int64_t n, const int4* binfo, const PhysK& p,
+               const IcK& ic, cudaStream_t st);
+
+struct MaskK {
+  int kind;
+  double p[8];
+};
+template <typename T>
+void launch_mask(int Bs, T* chi, const int32_t* list, int64_t n, const int4* binfo,
+                 const PhysK& p, const MaskK& m, cudaStream_t st);
+
+// Per block raw sums over the half-open points: [sum chi u, sum chi v, sum chi w, sum |u|^2].
+template <typename T>
+void launch_diag(int Bs, const T* reg, const T* chi, const int32_t* blist, int64_t n,
+                 double* out, cudaStream_t st);
+
+// Block-order gather/scatter of interiors between the pool and a dense array.
+template <typename T>
+void launch_gather(int Bs, const T* reg, T* dense, const int32_t* blist, int64_t n, int ncomp,
+                   cudaStream_t st);
+template <typename T>
+void launch_scatter(int Bs, const T* dense, T* reg, const int32_t* blist, int64_t n,
+                    cudaStream_t st);
+
+}  // namespace acm

@@ -1,0 +1,292 @@
+// Fused right-hand side + RK4 stage kernel of libacm (the hot path).
+//
+// One CTA updates one block.  Paper, eqs. (u_eqn-1, p_eqn-1):
+//   du/dt = -(u.grad)u - grad p + nu lap u - chi/C_eta u - chi_sp/C_sp (u - u_inf)     (u_s = 0)
+//   dp/dt = -C_0^2 div u - C_gamma p - chi_sp/C_sp (p - p_inf)
+// with the Tam-Webb (or classical) 4th-order first derivative and the classical 4th-order
+// second derivative (Sec. 2.3), and one stage of classical RK4 (Sec. 2.3):
+//   stage 1: acc = Y + dt/6 K,  out = Y + dt/2 K     (Y = U^n)
+//   stage 2: acc += dt/3 K,     out = U + dt/2 K
+//   stage 3: acc += dt/3 K,     out = U + dt K
+//   stage 4:                    out = acc + dt/6 K  (= U^{n+1})
+//   stage 0 (checks only):      acc = K
+//
+// Work layout: a thread owns one (x, y) pencil of the block and marches in z.  The z-stencil
+// (7 points) lives in a register queue fed one plane ahead from global memory; the x/y
+// stencils read a shared-memory plane with a 3-point halo on each side, double-buffered, whose
+// halo is brought in by cp.async one plane ahead.  Halo points come straight from the
+// neighbour's stored interior (same level: copy; finer: decimation, Sec. 3.1 restriction) or,
+// across a face to a coarser neighbour, from the halo slab that the coarse-face kernel
+// predicted for this stage.  No ghost layer is written to HBM.
+#include "common.cuh"
+#include "kernels.hpp"
+
+namespace acm {
+
+namespace {
+
+template <int BS>
+struct Cfg {
+  static constexpr int NT = ((BS * BS + 31) / 32) * 32;
+  static constexpr int W = BS + 6;       // padded plane width: 3 halo points each side
+  static constexpr int PW = W * W;
+};
+
+// faces: 0 -x, 1 +x, 2 -y, 3 +y, 4 -z, 5 +z ; box index of the face neighbour
+__constant__ int kFaceBox[6] = {12, 14, 10, 16, 4, 22};
+
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T* dst, const T* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  if constexpr (sizeof(T) == 4) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+  } else {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+  }
+}
+template <typename T>
+__device__ __forceinline__ T tmax(T a, T b) { return a > b ? a : b; }
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// Address of one halo value: face F, distance l = 1..3 from the face plane, tangential
+// coordinates (t0, t1) = (y, z) for x-faces, (x, z) for y-faces, (x, y) for z-faces.
+template <typename T, int BS>
+__device__ __forceinline__ const T* halo_ptr(const int (&ftype)[6], const int (&fs)[6][4],
+                                             const T* __restrict__ in, const T* __restrict__ slab,
+                                             int F, int l, int t0, int t1, int f) {
+  using L = Lay<T, BS>;
+  constexpr int M = L::M;
+  const int ax = F >> 1;
+  const bool plus = F & 1;
+  const int ty = ftype[F];
+  int s, nl, u0 = t0, u1 = t1;
+  if (ty == kTypeLeaf) {
+    s = fs[F][0];
+    nl = plus ? l : M - l;
+  } else if (ty == kTypeRefined) {
+    const int c0 = t0 > M / 2, c1 = t1 > M / 2;
+    s = fs[F][c0 + 2 * c1];
+    nl = plus ? 2 * l : M - 2 * l;
+    u0 = 2 * t0 - c0 * M;
+    u1 = 2 * t1 - c1 * M;
+  } else {
+    return slab + ((((size_t)fs[F][0] * 4 + f) * 3 + (l - 1)) * BS + t1) * BS + t0;
+  }
+  int x, y, z;
+  if (ax == 0) { x = nl; y = u0; z = u1; }
+  else if (ax == 1) { x = u0; y = nl; z = u1; }
+  else { x = u0; y = u1; z = nl; }
+  return in + (size_t)s * L::BLK + (size_t)f * L::FS + L::idx(x, y, z);
+}
+
+template <typename T, int BS, int STAGE>
+__global__ void __launch_bounds__(Cfg<BS>::NT)
+k_stage(const StageK<T> a, const TopoK tp, const PhysK ph) {
+  using L = Lay<T, BS>;
+  constexpr int M = L::M;
+  constexpr int NT = Cfg<BS>::NT;
+  constexpr int W = Cfg<BS>::W;
+  constexpr int PW = Cfg<BS>::PW;
+
+  __shared__ __align__(16) T buf[2][4][PW];
+  __shared__ int ftype[6];
+  __shared__ int fs[6][4];
+  __shared__ T sp[3][BS];
+
+  const int tid = threadIdx.x;
+  const int slot = tp.blist[blockIdx.x];
+  const int4 bi = tp.binfo[blockIdx.x];
+  const int* nbh = tp.nbh + (size_t)blockIdx.x * kNbhStride;
+
+  if (tid < 24) {
+    const int F = tid >> 2, j = tid & 3;
+    const int c0 = j & 1, c1 = j >> 1;
+    const int d = kFaceBox[F];
+    int ty = nbh[kNbhType + d] & 15;
+    int s;
+    if (ty == kTypeLeaf) {
+      s = nbh[8 * d];
+    } else if (ty == kTypeRefined) {
+      const int nbit = (F & 1) ? 0 : 1;
+      const int ax = F >> 1;
+      int c;
+      if (ax == 0) c = nbit | (c0 << 1) | (c1 << 2);
+      else if (ax == 1) c = c0 | (nbit << 1) | (c1 << 2);
+      else c = c0 | (c1 << 1) | (nbit << 2);
+      s = nbh[8 * d + c];
+    } else {
+      ty = kTypeCoarser;                 // halo slab predicted by the coarse-face kernel
+      s = tp.slabidx[(size_t)blockIdx.x * 8 + F];
+    }
+    fs[F][j] = s;
+    if (j == 0) ftype[F] = ty;
+  }
+  const double h = ph.root_len / ((double)(1 << bi.x) * M);
+  if (ph.sponge && tid < 3 * BS) {
+    const int ax = tid / BS, i = tid % BS;
+    const int g = ax == 0 ? bi.y : (ax == 1 ? bi.z : bi.w);
+    const long long N = ((long long)ph.nroot[ax] << bi.x) * M;
+    long long gi = ((long long)g * M + i) % N;
+    const double c = (double)gi * h;
+    const double dist = fmin(c, ph.sp_L[ax] - c);
+    sp[ax][i] = T(0.5 * (1.0 - tanh((dist - ph.sp_width) / ph.sp_delta)));
+  }
+  __syncthreads();
+
+  const T ih = T(1.0 / h), ih2 = T(1.0 / (12.0 * h * h));
+  const T a1 = T(ph.a1), a2 = T(ph.a2), a3 = T(ph.a3);
+  const T nu = T(ph.nu), c0sq = T(ph.c0sq), cgam = T(ph.cgamma);
+  const T inv_ceta = T(ph.inv_ceta), inv_csp = T(ph.inv_csp);
+  const T uinf0 = T(ph.uinf[0]), uinf1 = T(ph.uinf[1]), uinf2 = T(ph.uinf[2]), pinf = T(ph.pinf);
+  const T c_acc = T(a.c_acc), c_out = T(a.c_out);
+  const bool act = tid < BS * BS;
+  const int x = act ? tid % BS : 0, y = act ? tid / BS : 0;
+  const T* __restrict__ inb = a.in + (size_t)slot * L::BLK;
+  const size_t bo = (size_t)slot * L::BLK;
+
+  auto plane_value = [&](int zz, int f) -> T {
+    if (zz >= 0 && zz <= M) return inb[(size_t)f * L::FS + L::idx(x, y, zz)];
+    if (zz < 0) return *halo_ptr<T, BS>(ftype, fs, a.in, a.slab, 4, -zz, x, y, f);
+    return *halo_ptr<T, BS>(ftype, fs, a.in, a.slab, 5, zz - M, x, y, f);
+  };
+  auto issue_halos = [&](int zz, T (*B)[PW]) {
+    for (int i = tid; i < 48 * BS; i += NT) {
+      const int tt = i % BS;
+      int r = i / BS;
+      const int l = r % 3 + 1;
+      r /= 3;
+      const int F = r & 3, f = r >> 2;
+      int hx, hy;
+      if (F == 0) { hx = -l; hy = tt; }
+      else if (F == 1) { hx = M + l; hy = tt; }
+      else if (F == 2) { hx = tt; hy = -l; }
+      else { hx = tt; hy = M + l; }
+      cp_async_elem(&B[f][(hy + 3) * W + hx + 3], halo_ptr<T, BS>(ftype, fs, a.in, a.slab, F, l, tt, zz, f));
+    }
+    cp_async_commit();
+  };
+
+  T q[4][8];
+#pragma unroll
+  for (int k = 0; k < 7; ++k)
+#pragma unroll
+    for (int f = 0; f < 4; ++f) q[f][k] = act ? plane_value(k - 3, f) : T(0);
+#pragma unroll
+  for (int f = 0; f < 4; ++f) q[f][7] = T(0);
+  issue_halos(0, buf[0]);
+
+  const int ci = (y + 3) * W + x + 3;
+  for (int z = 0; z <= M; ++z) {
+    T(*B)[PW] = buf[z & 1];
+    if (act) {
+#pragma unroll
+      for (int f = 0; f < 4; ++f) B[f][ci] = q[f][3];
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    if (z < M) issue_halos(z + 1, buf[(z + 1) & 1]);
+    if (act) {
+      if (z + 4 <= M + 3) {
+#pragma unroll
+        for (int f = 0; f < 4; ++f) q[f][7] = plane_value(z + 4, f);
+      }
+      const size_t pi = (size_t)L::idx(x, y, z);
+      T Uv[4], Av[4], chiv = T(0);
+      if (STAGE == 2 || STAGE == 3) {
+#pragma unroll
+        for (int f = 0; f < 4; ++f) Uv[f] = a.U[bo + (size_t)f * L::FS + pi];
+      }
+      if (STAGE != 1) {
+#pragma unroll
+        for (int f = 0; f < 4; ++f) Av[f] = a.acc[bo + (size_t)f * L::FS + pi];
+      }
+      if (ph.mask) chiv = a.chi[(size_t)slot * L::FS + pi];
+
+      T dx[4], dy[4], dz[4], lap[3];
+#pragma unroll
+      for (int f = 0; f < 4; ++f) {
+        const T* s = B[f];
+        const T c = q[f][3];
+        const T xp1 = s[ci + 1], xm1 = s[ci - 1], xp2 = s[ci + 2], xm2 = s[ci - 2];
+        const T xp3 = s[ci + 3], xm3 = s[ci - 3];
+        const T yp1 = s[ci + W], ym1 = s[ci - W], yp2 = s[ci + 2 * W], ym2 = s[ci - 2 * W];
+        const T yp3 = s[ci + 3 * W], ym3 = s[ci - 3 * W];
+        dx[f] = (a1 * (xp1 - xm1) + a2 * (xp2 - xm2) + a3 * (xp3 - xm3)) * ih;
+        dy[f] = (a1 * (yp1 - ym1) + a2 * (yp2 - ym2) + a3 * (yp3 - ym3)) * ih;
+        dz[f] = (a1 * (q[f][4] - q[f][2]) + a2 * (q[f][5] - q[f][1]) + a3 * (q[f][6] - q[f][0])) * ih;
+        if (f < 3) {
+          const T lx = T(16) * (xp1 + xm1) - (xp2 + xm2) - T(30) * c;
+          const T ly = T(16) * (yp1 + ym1) - (yp2 + ym2) - T(30) * c;
+          const T lz = T(16) * (q[f][4] + q[f][2]) - (q[f][5] + q[f][1]) - T(30) * c;
+          lap[f] = (lx + ly + lz) * ih2;
+        }
+      }
+      const T u = q[0][3], v = q[1][3], w = q[2][3], p = q[3][3];
+      T K[4];
+      K[0] = -(u * dx[0] + v * dy[0] + w * dz[0]) - dx[3] + nu * lap[0];
+      K[1] = -(u * dx[1] + v * dy[1] + w * dz[1]) - dy[3] + nu * lap[1];
+      K[2] = -(u * dx[2] + v * dy[2] + w * dz[2]) - dz[3] + nu * lap[2];
+      K[3] = -c0sq * (dx[0] + dy[1] + dz[2]) - cgam * p;
+      if (ph.mask) {
+        const T cm = chiv * inv_ceta;
+        K[0] -= cm * u;
+        K[1] -= cm * v;
+        K[2] -= cm * w;
+      }
+      if (ph.sponge) {
+        const T cs = tmax(tmax(sp[0][x], sp[1][y]), sp[2][z]) * inv_csp;
+        K[0] -= cs * (u - uinf0);
+        K[1] -= cs * (v - uinf1);
+        K[2] -= cs * (w - uinf2);
+        K[3] -= cs * (p - pinf);
+      }
+#pragma unroll
+      for (int f = 0; f < 4; ++f) {
+        const size_t o = bo + (size_t)f * L::FS + pi;
+        if (STAGE == 0) {
+          a.acc[o] = K[f];
+        } else if (STAGE == 1) {
+          a.acc[o] = q[f][3] + c_acc * K[f];
+          a.out[o] = q[f][3] + c_out * K[f];
+        } else if (STAGE == 4) {
+          a.out[o] = Av[f] + c_out * K[f];
+        } else {
+          a.acc[o] = Av[f] + c_acc * K[f];
+          a.out[o] = Uv[f] + c_out * K[f];
+        }
+      }
+    }
+#pragma unroll
+    for (int f = 0; f < 4; ++f)
+#pragma unroll
+      for (int k = 0; k < 7; ++k) q[f][k] = q[f][k + 1];
+  }
+}
+
+template <typename T, int BS>
+void launch_stage_bs(int stage, const StageK<T>& s, const TopoK& t, const PhysK& p, cudaStream_t st) {
+  if (t.n <= 0) return;
+  const dim3 grid((unsigned)t.n), block(Cfg<BS>::NT);
+  switch (stage) {
+    case 0: k_stage<T, BS, 0><<<grid, block, 0, st>>>(s, t, p); break;
+    case 1: k_stage<T, BS, 1><<<grid, block, 0, st>>>(s, t, p); break;
+    case 2: k_stage<T, BS, 2><<<grid, block, 0, st>>>(s, t, p); break;
+    case 3: k_stage<T, BS, 3><<<grid, block, 0, st>>>(s, t, p); break;
+    default: k_stage<T, BS, 4><<<grid, block, 0, st>>>(s, t, p); break;
+  }
+}
+
+}  // namespace
+
+template <typename T>
+void launch_stage(int stage, int Bs, const StageK<T>& s, const TopoK& t, const PhysK& p,
+                  cudaStream_t st) {
+  if (Bs == 17) launch_stage_bs<T, 17>(stage, s, t, p, st);
+  else launch_stage_bs<T, 9>(stage, s, t, p, st);
+}
+
+template void launch_stage<float>(int, int, const StageK<float>&, const TopoK&, const PhysK&, cudaStream_t);
+template void launch_stage<double>(int, int, const StageK<double>&, const TopoK&, const PhysK&, cudaStream_t);
+
+}  // namespace acm

@@ -1,0 +1,233 @@
+"""CUDA path (through the C-ABI) against the FP64 oracle, element by element.
+
+Tolerances: topology (treecode, level, slot, coordinates, neighbour tables) bit-exact; fields
+relative L-infinity per component <= 1e-12 in FP64 and <= 2e-5 in FP32 (FP32 against the
+FP64 oracle on the same FP64-evaluated inputs).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import acm as oacm
+from oracle.sync import sync as osync
+from paper_1912_05371_gb300.workloads import random_graded_leaves
+from tests.gpu_util import (block_order_fields, fill_from_function, oracle_forest, oracle_solver,
+                            rel_linf, smooth_field, sphere_fn, sponge_fn)
+
+pytestmark = pytest.mark.gpu
+
+TOL = {64: 1e-12, 32: 2e-5}
+
+
+@pytest.fixture(scope="module")
+def A():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1912_05371_gb300 import acm
+    acm.lib()
+    return acm
+
+
+def _grid(Bs=9, nroot=(2, 1, 1), root_len=1.0, Jmin=1, Jmax=3, precision=64, max_blocks=4096, g=4):
+    return dict(nroot=nroot, root_len=root_len, Bs=Bs, g=g, Jmin=Jmin, Jmax=Jmax, precision=precision,
+                max_blocks=max_blocks, fd_scheme=1)
+
+
+def _phys(**kw):
+    p = dict(nu=1e-2, c0=3.0, C_eta=1e-2, C_gamma=0.5, cfl=0.5, eps=1e-3, dealias=0, mask_range_thr=1e-5)
+    p.update(kw)
+    return p
+
+
+def _pair(A, grid, phys, leaves, fn_seed=1, mask=None):
+    f = A.Forest(grid, phys)
+    f.set_leaves(leaves)
+    fo = oracle_forest(grid, leaves=leaves)
+    S = oracle_solver(fo, phys, mask=sphere_fn(mask) if mask else None,
+                      sponge=sponge_fn(phys) if phys.get("sponge") else None)
+    L = tuple(n * grid["root_len"] for n in grid["nroot"])
+    fill_from_function(S, lambda X, Y, Z: smooth_field(X, Y, Z, L, fn_seed))
+    S.eval_mask()
+    if mask:
+        f.set_mask(A.ACM_MASK_SPHERE, mask)
+    f.write_fields(block_order_fields(S))
+    return f, S
+
+
+@pytest.mark.parametrize("seed,Bs", [(1, 9), (2, 17), (3, 9)])
+def test_topology_is_bit_exact(A, seed, Bs):
+    leaves = random_graded_leaves(seed, nroot=(2, 1, 1), J0=1, Jmax=3, n_target=80)
+    grid = _grid(Bs=Bs)
+    f = A.Forest(grid, _phys())
+    f.set_leaves(leaves)
+    t = f.topology()
+    fo = oracle_forest(grid, leaves=leaves)
+    tc, lv, sl, nbr, rel = fo.topology()
+    order = fo.sorted_leaves()
+    assert np.array_equal(t["treecode"], tc)
+    assert np.array_equal(t["level"], lv)
+    assert np.array_equal(t["slot"], sl)
+    assert np.array_equal(t["gx"], [l[1] for l in order])
+    assert np.array_equal(t["nbr"], nbr)
+    assert np.array_equal(t["rel"], rel)
+
+
+def test_ungraded_layout_is_rejected(A):
+    f = A.Forest(_grid(), _phys())
+    bad = [(1, x, y, z) for z in range(2) for y in range(2) for x in range(4) if (x, y, z) != (0, 0, 0)]
+    bad += [(3, x, y, z) for z in range(4) for y in range(4) for x in range(4)]  # two levels finer
+    with pytest.raises(A.AcmError):
+        f.set_leaves(bad)
+
+
+@pytest.mark.parametrize("prec,Bs,seed", [(64, 9, 4), (64, 17, 5), (32, 9, 6)])
+def test_sync_ghosts_matches_oracle(A, prec, Bs, seed):
+    leaves = random_graded_leaves(seed, nroot=(2, 1, 1), J0=1, Jmax=3, n_target=70)
+    grid = _grid(Bs=Bs, precision=prec)
+    f, S = _pair(A, grid, _phys(), leaves, fn_seed=seed)
+    gpu = f.sync_ghosts()
+    ext = osync(S.fo, S.U, grid["g"], "cube")
+    ref = np.stack([ext[S.fo.leaves[l]] for l in S.fo.sorted_leaves()])
+    assert not np.isnan(ref).any()
+    err = rel_linf(gpu.astype(np.float64), ref)
+    assert max(err) < (1e-13 if prec == 64 else 1e-6), err
+
+
+@pytest.mark.parametrize("prec,Bs,seed,masked,sponge", [(64, 9, 7, True, True), (64, 17, 8, False, False),
+                                                        (32, 9, 9, True, True), (64, 9, 10, False, True)])
+def test_fused_rhs_matches_oracle(A, prec, Bs, seed, masked, sponge):
+    leaves = random_graded_leaves(seed, nroot=(2, 1, 1), J0=1, Jmax=3, n_target=70)
+    grid = _grid(Bs=Bs, precision=prec)
+    phys = _phys(sponge=int(sponge), C_sp=0.05, u_inf=(0.4, -0.1, 0.2), p_inf=0.1,
+                 sponge_L=(2.0, 1.0, 1.0), sponge_width=0.2, sponge_delta=0.05)
+    mask = (0.8, 0.5, 0.5, 0.2, 0.04) if masked else None
+    f, S = _pair(A, grid, phys, leaves, fn_seed=seed, mask=mask)
+    gpu = f.rhs().astype(np.float64)
+    K = S.rhs(S.U.copy())
+    ref = np.stack([K[S.fo.leaves[l]] for l in S.fo.sorted_leaves()])
+    err = rel_linf(gpu, ref)
+    # FP32: the stencils difference neighbouring values, losing about log2(1/(k h)) bits
+    assert max(err) < (1e-12 if prec == 64 else 1e-4), err
+
+
+@pytest.mark.parametrize("prec,Bs,seed", [(64, 9, 11), (64, 17, 12), (32, 17, 13)])
+def test_rk4_steps_match_oracle(A, prec, Bs, seed):
+    leaves = random_graded_leaves(seed, nroot=(2, 1, 1), J0=1, Jmax=3, n_target=70)
+    grid = _grid(Bs=Bs, precision=prec)
+    phys = _phys()
+    mask = (1.2, 0.5, 0.5, 0.15, 0.05)
+    f, S = _pair(A, grid, phys, leaves, fn_seed=seed, mask=mask)
+    dt = 2e-3 if Bs == 9 else 1e-3
+    for _ in range(2):
+        f.rk4_step(dt)
+        S.rk4(dt)
+    err = rel_linf(f.read_fields().astype(np.float64), block_order_fields(S))
+    assert max(err) < TOL[prec], err
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+def test_indicators_match_oracle(A, prec):
+    leaves = random_graded_leaves(14, nroot=(2, 1, 1), J0=1, Jmax=3, n_target=70)
+    grid = _grid(Bs=9, precision=prec)
+    mask = (1.0, 0.5, 0.5, 0.2, 0.03)
+    f, S = _pair(A, grid, _phys(), leaves, fn_seed=14, mask=mask)
+    ind, rng = f.block_indicators()
+    oind, _ = S.indicators(S.norms())
+    order = S.fo.sorted_leaves()
+    ref = np.array([oind[l][0] for l in order])
+    rref = np.array([oind[l][1] for l in order])
+    tol = 1e-12 if prec == 64 else 1e-4
+    assert np.abs(ind - ref).max() <= tol * ref.max()
+    assert np.abs(rng - rref).max() <= (1e-14 if prec == 64 else 1e-6)
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+def test_refine_and_coarsen_match_oracle(A, prec):
+    leaves = random_graded_leaves(15, nroot=(2, 1, 1), J0=1, Jmax=2, n_target=40)
+    grid = _grid(Bs=9, precision=prec, Jmax=3)
+    phys = _phys(eps=3e-3)
+    f, S = _pair(A, grid, phys, leaves, fn_seed=15)
+    f.refine_all()
+    S.refine_all()
+    t = f.topology()
+    tc, lv, sl, nbr, rel = S.fo.topology()
+    assert np.array_equal(t["treecode"], tc) and np.array_equal(t["slot"], sl) and np.array_equal(t["nbr"], nbr)
+    err = rel_linf(f.read_fields().astype(np.float64), block_order_fields(S))
+    assert max(err) < TOL[prec], err
+    if prec == 64:
+        nb, npass = f.coarsen()
+        S.coarsen()
+        t = f.topology()
+        tc, lv, sl, nbr, rel = S.fo.topology()
+        assert nb == len(S.fo.leaves)
+        assert np.array_equal(t["treecode"], tc) and np.array_equal(t["slot"], sl)
+        assert np.array_equal(t["nbr"], nbr) and np.array_equal(t["rel"], rel)
+        err = rel_linf(f.read_fields(), block_order_fields(S))
+        assert max(err) < TOL[prec], err
+
+
+def _small_sphere(prec, Jmax=3):
+    grid = dict(nroot=(2, 1, 1), root_len=1.0, Bs=9, g=4, Jmin=1, Jmax=Jmax, precision=prec,
+                max_blocks=1 << 14, fd_scheme=1)
+    dxm = 1.0 / ((1 << Jmax) * 8)
+    phys = dict(nu=1e-3, c0=5.0, C_eta=1e-2, C_gamma=0.0, C_sp=0.25 / (5.0 * 20.0), u_inf=(1.0, 0.0, 0.0),
+                p_inf=0.0, cfl=0.5, cfl_eta=1.0, cfl_nu=0.25, eps=1e-3, dealias=1, mask_range_thr=1e-5,
+                sponge=1, sponge_L=(2.0, 1.0, 1.0), sponge_width=0.25, sponge_delta=1.5 * dxm)
+    mask = (0.6, 0.5, 0.5, 0.15, 1.5 * dxm)
+    return grid, phys, mask
+
+
+def test_adaptive_sphere_steps_match_oracle(A):
+    grid, phys, mask = _small_sphere(64)
+    f = A.Forest(grid, phys)
+    f.set_mask(A.ACM_MASK_SPHERE, mask)
+    nb = f.init_grid(A.ACM_IC_UNIFORM, [1.0, 0.0, 0.0, 0.0])
+    fo = oracle_forest(grid)
+    S = oracle_solver(fo, phys, ic=lambda X, Y, Z: oacm.ic_uniform(X, Y, Z), mask=sphere_fn(mask),
+                      sponge=sponge_fn(phys))
+    S.initial_grid()
+    assert nb == len(fo.leaves)
+    assert np.array_equal(f.topology()["treecode"], fo.topology()[0])
+    for _ in range(2):
+        dt, n = f.step(0.0)
+        S.refine_all()
+        dto = S.dt_cfl()
+        assert abs(dt - dto) <= 1e-14 * dto
+        S.rk4(dto)
+        S.coarsen()
+        t = f.topology()
+        tc, lv, sl, nbr, rel = fo.topology()
+        assert np.array_equal(t["treecode"], tc) and np.array_equal(t["level"], lv)
+        assert np.array_equal(t["slot"], sl) and np.array_equal(t["nbr"], nbr)
+        err = rel_linf(f.read_fields(), block_order_fields(S))
+        assert max(err) < 1e-12, err
+    d = f.diagnostics()
+    F, E = S.diagnostics()
+    assert np.allclose(d["force"], F, rtol=1e-12, atol=1e-12 * np.abs(F).max())
+    assert abs(d["energy"] - E) <= 1e-12 * E
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("prec,steps", [(64, 20), (32, 5)])
+def test_taylor_green_config(A, prec, steps):
+    """Periodic unit cube, 4x4x4 blocks of 17^3, Taylor-Green, nu = 1e-2, c0 = 10, CFL 0.5."""
+    grid = _grid(Bs=17, nroot=(1, 1, 1), Jmin=2, Jmax=2, precision=prec, max_blocks=64)
+    phys = dict(nu=1e-2, c0=10.0, C_gamma=1.0, cfl=0.5)
+    f = A.Forest(grid, phys)
+    f.init_uniform(2)
+    f.set_ic(A.ACM_IC_TAYLOR_GREEN, [2 * math.pi, 1.0])
+    fo = oracle_forest(grid, J=2)
+    S = oracle_solver(fo, phys, ic=lambda X, Y, Z: oacm.ic_taylor_green(X, Y, Z))
+    S.eval_ic()
+    for _ in range(steps):
+        dt = f.rk4_step(0.0)
+        dto = S.dt_cfl()
+        assert abs(dt - dto) <= (1e-15 if prec == 64 else 1e-6) * dto
+        S.rk4(dt)
+    err = rel_linf(f.read_fields().astype(np.float64), block_order_fields(S))
+    assert max(err) < TOL[prec], err
+    d = f.diagnostics()
+    _, E = S.diagnostics()
+    assert abs(d["energy"] - E) <= (1e-12 if prec == 64 else 1e-5) * E
