@@ -1,0 +1,378 @@
+"""Benchmark of the wavelet-adaptive ACM hot path on GB300.
+
+One step = the paper's time step (Sec. 3.5) through the C-ABI: refine every block by one
+level, one RK4 step (4 x [ghost sync + fused RHS + RK combination]), wavelet-detail
+thresholding and coarsening.  Workload: the penalised sphere case (periodic box 4x2x2, sphere
+R = 0.25, C_eta = 1e-3, nu = 1e-3, c0 = 20, Bs = 17, levels 2..5, C_eps = 1e-3, dealiasing,
+sponge), FP32 fields, synthetic (analytic) initial data.
+
+value = point-updates/s = sum over timed steps of N_b(evolved) * Bs^3 * 4 RHS evaluations,
+divided by the device time of the timed steps (CUDA events on the forest's stream), whole job.
+
+Prints one JSON line.  ``--impl reference`` times the FP64 CPU oracle instead (bounded sample).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "RK4 point-updates/s (adaptive grid)"
+UNIT = "point-updates/s"
+
+
+def sphere_setup(Jmax=5, precision=32, max_blocks=40000):
+    from paper_1912_05371_gb300 import workloads as W
+    cfg = W.sphere(Jmax=Jmax)
+    g, p = cfg["grid"], cfg["phys"]
+    grid = dict(g, precision=precision, max_blocks=max_blocks, fd_scheme=1)
+    sp = cfg["sponge"]
+    phys = dict(p, eps=cfg["eps"], dealias=int(cfg["dealias"]), mask_range_thr=cfg["mask_thr"], sponge=1,
+                sponge_L=sp["L"], sponge_width=sp["L_sp"], sponge_delta=sp["delta"])
+    m = cfg["mask"][1]
+    mask = (*m["centre"], m["R"], m["delta"])
+    ic = [*cfg["ic"][1]["u0"], cfg["ic"][1]["p0"]]
+    return grid, phys, mask, ic, cfg
+
+
+def workload_name(grid):
+    return (f"sphere: periodic box 4x2x2, R=0.25 tanh mask, C_eta=1e-3, nu=1e-3, c0=20, sponge, "
+            f"Bs={grid['Bs']}, levels {grid['Jmin']}..{grid['Jmax']}, C_eps=1e-3, dealiasing, "
+            f"refine-RK4-coarsen per step")
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, ValueError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def profiled_traffic():
+    """dram bytes per launch of the stage kernel from the committed ncu summary, or None if the
+    kernel source changed since it was captured."""
+    p = os.path.join(ROOT, "profiles", "stage_kernel_traffic.txt")
+    src = os.path.join(ROOT, "paper_1912_05371_gb300", "csrc", "stage.cu")
+    try:
+        kv = {}
+        for line in open(p):
+            if "=" in line and not line.startswith("#"):
+                k, v = line.split("=", 1)
+                kv[k.strip()] = v.strip()
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        if kv.get("stage_cu_sha256_16") != h:
+            return None, None
+        return float(kv["dram_bytes_per_point_per_launch"]), kv.get("capture", "")
+    except (OSError, KeyError, ValueError):
+        return None, None
+
+
+def oracle_rhs_sample(leaves, U_blocks, grid, phys, mask, max_seconds=30.0):
+    """Time the FP64 oracle's right-hand side (ghost sync + RHS of every block) on the given
+    grid and state.  Returns (point-updates/s, seconds, blocks)."""
+    import numpy as np
+
+    from oracle import acm as oacm
+    from oracle.adapt import Solver
+    from oracle.forest import Forest as OForest
+    fo = OForest(nroot=grid["nroot"], root_len=grid["root_len"], Bs=grid["Bs"], Jmin=grid["Jmin"],
+                 Jmax=grid["Jmax"], max_blocks=len(leaves) + 8)
+    fo.set_leaves(leaves)
+    ph = oacm.Physics(nu=phys["nu"], c0=phys["c0"], C_eta=phys["C_eta"], C_gamma=phys["C_gamma"],
+                      C_sp=phys["C_sp"], u_inf=phys["u_inf"], p_inf=phys["p_inf"])
+    cx, cy, cz, R, d = mask
+    S = Solver(fo, ph, mask=lambda X, Y, Z: oacm.sphere_mask(X, Y, Z, (cx, cy, cz), R, d),
+               sponge=lambda X, Y, Z: oacm.sponge_mask(X, Y, Z, phys["sponge_L"], phys["sponge_width"],
+                                                       phys["sponge_delta"]))
+    for i, l in enumerate(fo.sorted_leaves()):
+        S.U[fo.leaves[l]] = np.asarray(U_blocks[i], dtype=np.float64)
+    S.eval_mask()
+    t0 = time.perf_counter()
+    S.rhs(S.U)
+    dt = time.perf_counter() - t0
+    n = len(leaves)
+    return n * grid["Bs"] ** 3 / dt, dt, n
+
+
+def run_reference(args):
+    """Reference arm: the FP64 CPU oracle as it stands, timed on the host cores, on a bounded
+    sample of the same workload: the sphere case built by the oracle's own initial-grid
+    procedure with levels 2..3, refined once; one step = one oracle RHS evaluation (ghost sync
+    + right-hand side of every block)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from oracle import acm as oacm
+    from oracle.adapt import Solver
+    from oracle.forest import Forest as OForest
+    grid, phys, mask, ic, cfg = sphere_setup(Jmax=3)
+    fo = OForest(nroot=grid["nroot"], root_len=grid["root_len"], Bs=grid["Bs"], Jmin=grid["Jmin"],
+                 Jmax=grid["Jmax"], max_blocks=1 << 14)
+    ph = oacm.Physics(nu=phys["nu"], c0=phys["c0"], C_eta=phys["C_eta"], C_gamma=phys["C_gamma"],
+                      C_sp=phys["C_sp"], u_inf=phys["u_inf"], p_inf=phys["p_inf"])
+    cx, cy, cz, R, d = mask
+    S = Solver(fo, ph, eps=phys["eps"], dealias=True, mask_thr=phys["mask_range_thr"],
+               ic=lambda X, Y, Z: oacm.ic_uniform(X, Y, Z),
+               mask=lambda X, Y, Z: oacm.sphere_mask(X, Y, Z, (cx, cy, cz), R, d),
+               sponge=lambda X, Y, Z: oacm.sponge_mask(X, Y, Z, phys["sponge_L"], phys["sponge_width"],
+                                                       phys["sponge_delta"]))
+    S.initial_grid()
+    S.refine_all()
+    n = len(fo.leaves)
+    for _ in range(args.warmup):
+        S.rhs(S.U)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        S.rhs(S.U)
+    dt = time.perf_counter() - t0
+    value = n * grid["Bs"] ** 3 * args.steps / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": workload_name(grid), "sample": f"levels 2..3, {n} blocks of 17^3 after one "
+                   "refinement; one step = one oracle RHS evaluation (sync + RHS of every block)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{n} blocks x 17^3, {args.steps} RHS evaluations"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--Jmax", type=int, default=5)
+    ap.add_argument("--precision", type=int, default=32)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--max-blocks", type=int, default=40000)
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    from paper_1912_05371_gb300 import acm as A
+
+    grid, phys, mask, ic, cfg = sphere_setup(Jmax=args.Jmax, precision=args.precision,
+                                             max_blocks=args.max_blocks)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        f = A.Forest(grid, phys, stream=stream)
+        f.set_mask(A.ACM_MASK_SPHERE, mask)
+        f.init_grid(A.ACM_IC_UNIFORM, ic)
+        Bs3 = grid["Bs"] ** 3
+        for _ in range(args.warmup):
+            f.step(0.0)
+        f.enable_timing(True)
+
+        def barrier():
+            if dist is not None:
+                dist.barrier()
+            torch.cuda.synchronize()
+
+        clocks = ClockSampler(local)
+        clocks.start()
+        barrier()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        l0 = f.launch_count()
+        h0 = f.last_step_stats()
+        pu = 0
+        stage_ms = 0.0
+        stage_bytes = 0.0
+        nev = []
+        ev0.record(stream)
+        for _ in range(args.steps):
+            f.refine_all()
+            n_ev = f.n_blocks()
+            f.rk4_step(0.0)
+            f.coarsen()
+            st = f.last_step_stats()
+            stage_ms += st["stage_ms"]
+            stage_bytes += st["stage_bytes"]
+            pu += 4 * n_ev * Bs3
+            nev.append(n_ev)
+        ev1.record(stream)
+        barrier()
+        launches = f.launch_count() - l0
+        h1 = f.last_step_stats()
+        ms = ev0.elapsed_time(ev1)
+        clk = clocks.stop()
+        f.enable_timing(False)
+        t_max = ms
+        pu_all = pu
+        if dist is not None:
+            t = torch.tensor([ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            t_max = float(t.item())
+            p = torch.tensor([float(pu)], device="cuda")
+            dist.all_reduce(p)
+            pu_all = float(p.item())
+        value = pu_all / (t_max * 1e-3)
+
+        # roofline of the dominant kernel (fused RHS + RK4 stage): algorithmic bytes / event time
+        peak, peak_kind = measured_peaks()
+        achieved = stage_bytes / (stage_ms * 1e-3) / 1e9
+        traffic_ppu, capture = profiled_traffic()
+        launches_stage = 4 * args.steps
+        roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
+                "kernel": "k_stage<float,17> (fused RHS + RK4 stage)",
+                "bytes_per_launch": stage_bytes / launches_stage,
+                "avg_launch_ms": stage_ms / launches_stage,
+                "traffic": (traffic_ppu * float(np.mean(nev)) * Bs3 if traffic_ppu is not None else None),
+                "traffic_capture": capture,
+                "stage_share_of_step": round(stage_ms / t_max, 4)}
+
+        # end to end through the C-ABI with host buffers: write state, step, read state
+        e2e = None
+        if not args.no_e2e:
+            nmax = min(grid["max_blocks"], 2 * max(nev))
+            esz = 4 if args.precision == 32 else 8
+            tdt = torch.float32 if args.precision == 32 else torch.float64
+            host = torch.empty(nmax * 4 * Bs3, dtype=tdt).pin_memory()
+            n0 = f.n_blocks()
+            f.read_fields(host[: n0 * 4 * Bs3])
+            barrier()
+            t0 = time.perf_counter()
+            pu_e, h2d, d2h = 0, 0, 0
+            for _ in range(args.steps):
+                nb = f.n_blocks()
+                f.write_fields(host[: nb * 4 * Bs3])
+                h2d += nb * 4 * Bs3 * esz
+                f.refine_all()
+                pu_e += 4 * f.n_blocks() * Bs3
+                f.rk4_step(0.0)
+                f.coarsen()
+                nb = f.n_blocks()
+                f.read_fields(host[: nb * 4 * Bs3])
+                d2h += nb * 4 * Bs3 * esz
+            barrier()
+            te = time.perf_counter() - t0
+            e2e = {"value": pu_e / te, "unit": UNIT, "h2d_bytes_per_step": h2d // args.steps,
+                   "d2h_bytes_per_step": d2h // args.steps}
+
+        cpu = None
+        if rank == 0 and world == 1 and not args.no_cpu_baseline:
+            topo = f.topology()
+            f.refine_all()
+            topo = f.topology()
+            leaves = list(zip(topo["level"].tolist(), topo["gx"].tolist(), topo["gy"].tolist(),
+                              topo["gz"].tolist()))
+            U = f.read_fields().astype(np.float64)
+            v, secs, nb = oracle_rhs_sample(leaves, U, grid, phys, mask)
+            cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                   "sample": f"one FP64 oracle RHS evaluation (ghost sync + RHS) over the workload's "
+                             f"evolved grid, {nb} blocks x 17^3, {secs:.1f} s"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == 32 else "f64",
+            "data": "synthetic",
+            "config": {"workload": workload_name(grid), "Bs": grid["Bs"], "levels": [grid["Jmin"], grid["Jmax"]],
+                       "precision": f"fp{args.precision}", "blocks_evolved_mean": float(np.mean(nev)),
+                       "points_evolved_mean": float(np.mean(nev)) * Bs3,
+                       "l2": f"inputs larger than L2: state {4 * float(np.mean(nev)) * Bs3 * 4 * (args.precision // 8) / 1e9:.2f} GB per RK register x 4 registers",
+                       "parallelism": f"replicas x{world}"},
+            "step_breakdown_ms": {
+                "stage_kernels": stage_ms / args.steps,
+                "host_topology": (h1["host_topology_ms"] - h0["host_topology_ms"]) / args.steps,
+                "host_tree": (h1["host_tree_ms"] - h0["host_tree_ms"]) / args.steps,
+                "total": t_max / args.steps},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    f.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -216,13 +216,18 @@ acm_status acm_write_fields(acm_forest* f, const void* in, int64_t n_elems, int 
 /* Copy the mask chi in block order (n_blocks*Bs^3 elements, forest precision). */
 acm_status acm_read_mask(acm_forest* f, void* out, int64_t n_elems, int on_device);
 
-/* Per-kernel timing of the last acm_rk4_step (CUDA events, milliseconds summed over its
- * launches) and algorithmic bytes moved by its fused stage kernels. */
+/* Per-kernel timing of the last acm_rk4_step with timing enabled (CUDA events recorded on the
+ * forest's stream around each stage's synchronisation kernels and fused stage kernel; read
+ * when this is called, which waits for the last of them), milliseconds summed over the four
+ * stages, and the algorithmic bytes of the four fused stage kernels (per point 64 words of
+ * register traffic, plus 4 words of mask when a mask is set). */
 typedef struct {
   double stage_ms;        /* fused RHS+RK4 stage kernels                                    */
   double sync_ms;         /* fine-wins and coarse-face prediction kernels                    */
   double stage_bytes;     /* algorithmic bytes of the stage kernels                          */
   int64_t n_launches;     /* kernels launched by the step                                    */
+  double host_topology_ms;/* cumulative host time rebuilding block tables since creation     */
+  double host_tree_ms;    /* cumulative host time of refine/coarsen tree logic since creation */
 } acm_step_stats;
 acm_status acm_enable_timing(acm_forest* f, int on);
 acm_status acm_last_step_stats(acm_forest* f, acm_step_stats* out);

@@ -41,7 +41,7 @@ class Diag(C.Structure):
 
 class StepStats(C.Structure):
     _fields_ = [("stage_ms", C.c_double), ("sync_ms", C.c_double), ("stage_bytes", C.c_double),
-                ("n_launches", C.c_int64)]
+                ("n_launches", C.c_int64), ("host_topology_ms", C.c_double), ("host_tree_ms", C.c_double)]
 
 
 EXPORTS = {
@@ -235,7 +235,7 @@ class Forest:
     def write_fields(self, arr):
         n = self.n_blocks()
         on_dev = int(hasattr(arr, "data_ptr") and arr.is_cuda)
-        if not on_dev:
+        if not hasattr(arr, "data_ptr"):
             arr = np.ascontiguousarray(arr, dtype=self.dtype)
         self._check(self.L.acm_write_fields(self.h, _ptr(arr), n * 4 * self.Bs ** 3, on_dev))
 
@@ -283,7 +283,8 @@ class Forest:
     def last_step_stats(self):
         s = StepStats()
         self._check(self.L.acm_last_step_stats(self.h, C.byref(s)))
-        return dict(stage_ms=s.stage_ms, sync_ms=s.sync_ms, stage_bytes=s.stage_bytes, n_launches=s.n_launches)
+        return dict(stage_ms=s.stage_ms, sync_ms=s.sync_ms, stage_bytes=s.stage_bytes, n_launches=s.n_launches,
+                    host_topology_ms=s.host_topology_ms, host_tree_ms=s.host_tree_ms)
 
     def launch_count(self):
         return self.L.acm_launch_count(self.h)

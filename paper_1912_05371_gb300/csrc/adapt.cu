@@ -57,28 +57,78 @@ __global__ void __launch_bounds__(kNT) k_fine_wins(T* reg, const int2* tasks, co
 
 // ---- (2) coarse-face halo slabs ------------------------------------------------------------------
 // task = (rank, face F, slab index, -): the 3 x Bs x Bs halo points beyond face F, each the
-// value of the finest leaf holding it, else the DD-4 prediction from the coarser neighbour.
+// value of the finest leaf holding it, else the tensor DD-4 prediction from the coarse lattice
+// (Sec. 3.1).  The coarse-lattice patch the predictions need (even local coordinates
+// [M-2, M+6] or [-6, 2] across the face, [-2, M+2] along it) is gathered into shared memory
+// once; every such point is held directly by some leaf.
 // Slab layout [slab][comp][layer l-1][t1][t0] with (t0, t1) as in the stage kernel.
 template <typename T, int BS>
 __global__ void __launch_bounds__(kNT) k_coarse_slabs(const T* reg, T* slab, const int4* tasks,
                                                        const int32_t* nbh_all) {
   using L = Lay<T, BS>;
   constexpr int M = L::M;
+  constexpr int NT_ = M / 2 + 3;                    // coarse samples along the face: -2..M+2 step 2
+  constexpr int NN = 5;                             // coarse planes across the face
   __shared__ int nbh[kNbhStride];
+  __shared__ T patch[4][NN][NT_][NT_];
   const int4 tk = tasks[blockIdx.x];
   for (int i = threadIdx.x; i < kNbhStride; i += kNT) nbh[i] = nbh_all[(size_t)tk.x * kNbhStride + i];
   __syncthreads();
   const int F = tk.y, ax = F >> 1;
   const bool plus = F & 1;
+  const int n0 = plus ? M - 2 : -6;                 // first coarse plane (even local coordinate)
+  auto place = [&](int nl, int t0, int t1, int* x, int* y, int* z) {
+    if (ax == 0) { *x = nl; *y = t0; *z = t1; }
+    else if (ax == 1) { *x = t0; *y = nl; *z = t1; }
+    else { *x = t0; *y = t1; *z = nl; }
+  };
+  for (int i = threadIdx.x; i < 4 * NN * NT_ * NT_; i += kNT) {
+    const int a0 = i % NT_, a1 = (i / NT_) % NT_, an = (i / (NT_ * NT_)) % NN, f = i / (NN * NT_ * NT_);
+    int x, y, z;
+    place(n0 + 2 * an, 2 * a0 - 2, 2 * a1 - 2, &x, &y, &z);
+    T v;
+    if (!direct_value<T, BS>(reg, nbh, x, y, z, f, &v)) v = T(__longlong_as_double(0x7ff8000000000000ll));
+    patch[f][an][a1][a0] = v;
+  }
+  __syncthreads();
+  const T w[4] = {T(-1) / T(16), T(9) / T(16), T(9) / T(16), T(-1) / T(16)};
+  const int off[4] = {-3, -1, 1, 3};
   const int tot = 4 * 3 * BS * BS;
   for (int i = threadIdx.x; i < tot; i += kNT) {
     const int t0 = i % BS, t1 = (i / BS) % BS, l = (i / (BS * BS)) % 3 + 1, f = i / (3 * BS * BS);
     const int nl = plus ? M + l : -l;
     int x, y, z;
-    if (ax == 0) { x = nl; y = t0; z = t1; }
-    else if (ax == 1) { x = t0; y = nl; z = t1; }
-    else { x = t0; y = t1; z = nl; }
-    slab[((((size_t)tk.z * 4 + f) * 3 + (l - 1)) * BS + t1) * BS + t0] = point_value<T, BS>(reg, nbh, x, y, z, f);
+    place(nl, t0, t1, &x, &y, &z);
+    T v;
+    if (!direct_value<T, BS>(reg, nbh, x, y, z, f, &v)) {
+      // tensor prediction with the same nesting as point_value: z outer, then y, then x
+      const int p[3] = {x, y, z};
+      int cnt[3], cb[3];
+      for (int a = 0; a < 3; ++a) cnt[a] = (p[a] & 1) ? 4 : 1;
+      auto pidx = [&](int a, int k) { return cnt[a] == 4 ? p[a] + off[k] : p[a]; };
+      T accz = T(0);
+      for (int kz = 0; kz < cnt[2]; ++kz) {
+        T accy = T(0);
+        for (int ky = 0; ky < cnt[1]; ++ky) {
+          T accx = T(0);
+          for (int kx = 0; kx < cnt[0]; ++kx) {
+            const int q[3] = {pidx(0, kx), pidx(1, ky), pidx(2, kz)};
+            // map the even point q into the patch
+            for (int a = 0; a < 3; ++a) cb[a] = q[a];
+            int qn, q0, q1;
+            if (ax == 0) { qn = cb[0]; q0 = cb[1]; q1 = cb[2]; }
+            else if (ax == 1) { qn = cb[1]; q0 = cb[0]; q1 = cb[2]; }
+            else { qn = cb[2]; q0 = cb[0]; q1 = cb[1]; }
+            const T c = patch[f][(qn - n0) >> 1][(q1 + 2) >> 1][(q0 + 2) >> 1];
+            accx = accx + (cnt[0] == 4 ? w[kx] : T(1)) * c;
+          }
+          accy = accy + (cnt[1] == 4 ? w[ky] : T(1)) * accx;
+        }
+        accz = accz + (cnt[2] == 4 ? w[kz] : T(1)) * accy;
+      }
+      v = accz;
+    }
+    slab[((((size_t)tk.z * 4 + f) * 3 + (l - 1)) * BS + t1) * BS + t0] = v;
   }
 }
 
@@ -110,47 +160,61 @@ __global__ void __launch_bounds__(kNT) k_sync_ext(const T* reg, T* out, int g, c
 }
 
 // ---- (4) block indicators: details (Sec. 3.1) and mask range ----------------------------------
+// The coarse samples are the block's even points, local coordinates -2..M+2 (those outside the
+// block are held directly by a neighbour leaf); they are predicted back to every interior point
+// with the tensor DD-4 scheme (z outer, then y, then x) and subtracted.
 template <typename T, int BS>
-__global__ void __launch_bounds__(kNT) k_details(const T* ext, const T* chi, const int32_t* blist,
-                                                  const double* norms, double* ind, double* chirange) {
+__global__ void __launch_bounds__(kNT) k_details(const T* reg, const T* chi, const int32_t* blist,
+                                                  const int32_t* nbh_all, const double* norms, double* ind,
+                                                  double* chirange) {
   using L = Lay<T, BS>;
-  constexpr int M = L::M, NE = L::NE, G = kGE;
+  constexpr int M = L::M;
+  constexpr int NC = M / 2 + 3;                 // coarse samples -1..M/2+1
+  __shared__ int nbh[kNbhStride];
+  __shared__ T c[NC][NC][NC];
   const int slot = blist[blockIdx.x];
-  const T* e = ext + (size_t)slot * L::EBLK;
+  for (int i = threadIdx.x; i < kNbhStride; i += kNT) nbh[i] = nbh_all[(size_t)blockIdx.x * kNbhStride + i];
   const T w[4] = {T(-1) / T(16), T(9) / T(16), T(9) / T(16), T(-1) / T(16)};
   const int off[4] = {-3, -1, 1, 3};
   double best = 0.0;
-  double inv[4];
-#pragma unroll
-  for (int f = 0; f < 4; ++f) inv[f] = norms[f] > 0.0 ? 1.0 / norms[f] : 0.0;
-  for (int i = threadIdx.x; i < BS * BS * BS; i += kNT) {
-    const int x = i % BS, y = (i / BS) % BS, z = i / (BS * BS);
-    if (((x | y | z) & 1) == 0) continue;          // all-even points: detail is zero
-    const int nx = (x & 1) ? 4 : 1, ny = (y & 1) ? 4 : 1, nz = (z & 1) ? 4 : 1;
-#pragma unroll
-    for (int f = 0; f < 4; ++f) {
-      if (inv[f] == 0.0) continue;
-      const T* ef = e + (size_t)f * L::NE3;
+  for (int f = 0; f < 4; ++f) {
+    const double inv = norms[f] > 0.0 ? 1.0 / norms[f] : 0.0;
+    if (inv == 0.0) continue;
+    __syncthreads();
+    for (int i = threadIdx.x; i < NC * NC * NC; i += kNT) {
+      const int x = 2 * (i % NC) - 2, y = 2 * ((i / NC) % NC) - 2, z = 2 * (i / (NC * NC)) - 2;
+      T v;
+      if (x >= 0 && x <= M && y >= 0 && y <= M && z >= 0 && z <= M)
+        v = reg[(size_t)slot * L::BLK + (size_t)f * L::FS + L::idx(x, y, z)];
+      else if (!direct_value<T, BS>(reg, nbh, x, y, z, f, &v))
+        v = T(__longlong_as_double(0x7ff8000000000000ll));
+      c[i / (NC * NC)][(i / NC) % NC][i % NC] = v;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < BS * BS * BS; i += kNT) {
+      const int x = i % BS, y = (i / BS) % BS, z = i / (BS * BS);
+      if (((x | y | z) & 1) == 0) continue;          // all-even points: detail is zero
+      const int nx = (x & 1) ? 4 : 1, ny = (y & 1) ? 4 : 1, nz = (z & 1) ? 4 : 1;
       T accz = T(0);
       for (int kz = 0; kz < nz; ++kz) {
-        const int zz = (nz == 4 ? z + off[kz] : z) + G;
+        const int zz = ((nz == 4 ? z + off[kz] : z) + 2) >> 1;
         const T wz = nz == 4 ? w[kz] : T(1);
         T accy = T(0);
         for (int ky = 0; ky < ny; ++ky) {
-          const int yy = (ny == 4 ? y + off[ky] : y) + G;
+          const int yy = ((ny == 4 ? y + off[ky] : y) + 2) >> 1;
           const T wy = ny == 4 ? w[ky] : T(1);
           T accx = T(0);
           for (int kx = 0; kx < nx; ++kx) {
-            const int xx = (nx == 4 ? x + off[kx] : x) + G;
+            const int xx = ((nx == 4 ? x + off[kx] : x) + 2) >> 1;
             const T wx = nx == 4 ? w[kx] : T(1);
-            accx = accx + wx * ef[(zz * NE + yy) * NE + xx];
+            accx = accx + wx * c[zz][yy][xx];
           }
           accy = accy + wy * accx;
         }
         accz = accz + wz * accy;
       }
-      const T dv = ef[((z + G) * NE + (y + G)) * NE + (x + G)] - accz;
-      const double r = (double)tabs(dv) * inv[f];
+      const T dv = reg[(size_t)slot * L::BLK + (size_t)f * L::FS + L::idx(x, y, z)] - accz;
+      const double r = (double)tabs(dv) * inv;
       best = r > best ? r : best;
     }
   }
@@ -158,9 +222,9 @@ __global__ void __launch_bounds__(kNT) k_details(const T* ext, const T* chi, con
   if (chi) {
     for (int i = threadIdx.x; i < BS * BS * BS; i += kNT) {
       const int x = i % BS, y = (i / BS) % BS, z = i / (BS * BS);
-      const double c = (double)chi[(size_t)slot * L::FS + L::idx(x, y, z)];
-      cmin = c < cmin ? c : cmin;
-      cmax = c > cmax ? c : cmax;
+      const double cv = (double)chi[(size_t)slot * L::FS + L::idx(x, y, z)];
+      cmin = cv < cmin ? cv : cmin;
+      cmax = cv > cmax ? cv : cmax;
     }
   }
   __shared__ double red[3][kNT / 32];
@@ -210,52 +274,72 @@ __global__ void __launch_bounds__(kNT) k_maxnorm(const T* reg, const int32_t* bl
 }
 
 // ---- (6) refinement: 8 children predicted from the synchronised parent (Sec. 3.5 step 1) -------
-// task = (old parent slot, child c, new child slot, -)
+// task = (parent rank in the old grid, child c, new child slot, -).  src is a copy of the state
+// taken before any child is written (children may reuse the parent's slot).  The parent samples
+// a child needs (parent-local -1..M/2+1 around the child's half) are gathered into shared
+// memory, ghosts with the finest-leaf / DD-4 rule, then predicted to the child's points.
 template <typename T, int BS>
-__global__ void __launch_bounds__(kNT) k_refine(const T* ext, T* reg, const int4* tasks) {
+__global__ void __launch_bounds__(kNT) k_refine(const T* src, T* dst, const int4* tasks, const int32_t* blist,
+                                                 const int32_t* nbh_all) {
   using L = Lay<T, BS>;
-  constexpr int M = L::M, NE = L::NE, G = kGE;
+  constexpr int M = L::M;
+  constexpr int NP = M / 2 + 3;                 // parent samples per axis
+  __shared__ int nbh[kNbhStride];
+  __shared__ T pp[NP][NP][NP];
   const int4 tk = tasks[blockIdx.x];
-  const T* e = ext + (size_t)tk.x * L::EBLK;
+  const int pslot = blist[tk.x];
+  for (int i = threadIdx.x; i < kNbhStride; i += kNT) nbh[i] = nbh_all[(size_t)tk.x * kNbhStride + i];
   const int cb[3] = {tk.y & 1, (tk.y >> 1) & 1, (tk.y >> 2) & 1};
+  const int o[3] = {cb[0] * (M / 2) - 1, cb[1] * (M / 2) - 1, cb[2] * (M / 2) - 1};
   const T w[4] = {T(-1) / T(16), T(9) / T(16), T(9) / T(16), T(-1) / T(16)};
   const int off[4] = {-3, -1, 1, 3};
-  for (int i = threadIdx.x; i < 4 * BS * BS * BS; i += kNT) {
-    const int f = i / (BS * BS * BS);
-    const int r = i % (BS * BS * BS);
-    const int ix = r % BS, iy = (r / BS) % BS, iz = r / (BS * BS);
-    // parent-local fine-lattice position (twice the parent index): c*M + i
-    const int px = cb[0] * M + ix, py = cb[1] * M + iy, pz = cb[2] * M + iz;
-    const int nx = (px & 1) ? 4 : 1, ny = (py & 1) ? 4 : 1, nz = (pz & 1) ? 4 : 1;
-    const T* ef = e + (size_t)f * L::NE3;
-    T accz = T(0);
-    for (int kz = 0; kz < nz; ++kz) {
-      const int zz = (nz == 4 ? pz + off[kz] : pz) / 2 + G;
-      const T wz = nz == 4 ? w[kz] : T(1);
-      T accy = T(0);
-      for (int ky = 0; ky < ny; ++ky) {
-        const int yy = (ny == 4 ? py + off[ky] : py) / 2 + G;
-        const T wy = ny == 4 ? w[ky] : T(1);
-        T accx = T(0);
-        for (int kx = 0; kx < nx; ++kx) {
-          const int xx = (nx == 4 ? px + off[kx] : px) / 2 + G;
-          const T wx = nx == 4 ? w[kx] : T(1);
-          accx = accx + wx * ef[(zz * NE + yy) * NE + xx];
-        }
-        accy = accy + wy * accx;
-      }
-      accz = accz + wz * accy;
+  for (int f = 0; f < 4; ++f) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < NP * NP * NP; i += kNT) {
+      const int x = o[0] + i % NP, y = o[1] + (i / NP) % NP, z = o[2] + i / (NP * NP);
+      T v;
+      if (x >= 0 && x <= M && y >= 0 && y <= M && z >= 0 && z <= M)
+        v = src[(size_t)pslot * L::BLK + (size_t)f * L::FS + L::idx(x, y, z)];
+      else
+        v = point_value<T, BS>(src, nbh, x, y, z, f);
+      pp[i / (NP * NP)][(i / NP) % NP][i % NP] = v;
     }
-    reg[(size_t)tk.z * L::BLK + (size_t)f * L::FS + L::idx(ix, iy, iz)] = accz;
+    __syncthreads();
+    for (int i = threadIdx.x; i < BS * BS * BS; i += kNT) {
+      const int ix = i % BS, iy = (i / BS) % BS, iz = i / (BS * BS);
+      // parent-local fine-lattice position (twice the parent index): c*M + i
+      const int px = cb[0] * M + ix, py = cb[1] * M + iy, pz = cb[2] * M + iz;
+      const int nx = (px & 1) ? 4 : 1, ny = (py & 1) ? 4 : 1, nz = (pz & 1) ? 4 : 1;
+      T accz = T(0);
+      for (int kz = 0; kz < nz; ++kz) {
+        const int zz = (nz == 4 ? pz + off[kz] : pz) / 2 - o[2];
+        const T wz = nz == 4 ? w[kz] : T(1);
+        T accy = T(0);
+        for (int ky = 0; ky < ny; ++ky) {
+          const int yy = (ny == 4 ? py + off[ky] : py) / 2 - o[1];
+          const T wy = ny == 4 ? w[ky] : T(1);
+          T accx = T(0);
+          for (int kx = 0; kx < nx; ++kx) {
+            const int xx = (nx == 4 ? px + off[kx] : px) / 2 - o[0];
+            const T wx = nx == 4 ? w[kx] : T(1);
+            accx = accx + wx * pp[zz][yy][xx];
+          }
+          accy = accy + wy * accx;
+        }
+        accz = accz + wz * accy;
+      }
+      dst[(size_t)tk.z * L::BLK + (size_t)f * L::FS + L::idx(ix, iy, iz)] = accz;
+    }
   }
 }
 
 // ---- (7) coarsening: parent by decimation of its 8 children (Sec. 3.1 R, Sec. 3.5 step 3) ----
-// task = [new parent slot, old child slots 0..7]
+// task = [new parent slot, old child slots 0..7]; src is a copy of the state taken before the
+// merge (the parent may reuse a child's slot).
 template <typename T, int BS>
-__global__ void __launch_bounds__(kNT) k_coarsen(const T* ext, T* reg, const int32_t* tasks) {
+__global__ void __launch_bounds__(kNT) k_coarsen(const T* src, T* dst, const int32_t* tasks) {
   using L = Lay<T, BS>;
-  constexpr int M = L::M, NE = L::NE, G = kGE;
+  constexpr int M = L::M;
   const int32_t* tk = tasks + (size_t)blockIdx.x * 9;
   for (int i = threadIdx.x; i < 4 * BS * BS * BS; i += kNT) {
     const int f = i / (BS * BS * BS);
@@ -264,9 +348,20 @@ __global__ void __launch_bounds__(kNT) k_coarsen(const T* ext, T* reg, const int
     const int cx = x > M / 2, cy = y > M / 2, cz = z > M / 2;
     const int lx = 2 * x - cx * M, ly = 2 * y - cy * M, lz = 2 * z - cz * M;
     const int cs = tk[1 + (cx | (cy << 1) | (cz << 2))];
-    reg[(size_t)tk[0] * L::BLK + (size_t)f * L::FS + L::idx(x, y, z)] =
-        ext[(size_t)cs * L::EBLK + (size_t)f * L::NE3 + ((lz + G) * NE + (ly + G)) * NE + (lx + G)];
+    dst[(size_t)tk[0] * L::BLK + (size_t)f * L::FS + L::idx(x, y, z)] =
+        src[(size_t)cs * L::BLK + (size_t)f * L::FS + L::idx(lx, ly, lz)];
   }
+}
+
+// ---- copy of whole blocks (same slots) between two registers --------------------------------------
+template <typename T, int BS>
+__global__ void __launch_bounds__(kNT) k_copy_blocks(const T* src, T* dst, const int32_t* blist) {
+  using L = Lay<T, BS>;
+  const size_t base = (size_t)blist[blockIdx.x] * L::BLK;
+  const float4* s4 = reinterpret_cast<const float4*>(src + base);
+  float4* d4 = reinterpret_cast<float4*>(dst + base);
+  constexpr int n4 = (int)(L::BLK * sizeof(T) / 16);
+  for (int i = threadIdx.x; i < n4; i += kNT) d4[i] = s4[i];
 }
 
 // ---- (8) analytic initial conditions and masks, FP64 at integer-derived coordinates ------------
@@ -278,11 +373,13 @@ __device__ __forceinline__ double coord(const PhysK& ph, int4 bi, int a, int i, 
 }
 
 template <typename T, int BS>
-__global__ void __launch_bounds__(kNT) k_ic(T* reg, const int32_t* list, const int4* binfo, const PhysK ph, const IcK ic) {
+__global__ void __launch_bounds__(kNT) k_ic(T* reg, const int32_t* blist, const int32_t* ranks, const int4* binfo,
+                                             const PhysK ph, const IcK ic) {
   using L = Lay<T, BS>;
   constexpr int M = L::M;
-  const int slot = list[blockIdx.x];
-  const int4 bi = binfo[blockIdx.x];
+  const int rank = ranks ? ranks[blockIdx.x] : (int)blockIdx.x;
+  const int slot = blist[rank];
+  const int4 bi = binfo[rank];
   const double h = ph.root_len / ((double)(1 << bi.x) * M);
   for (int i = threadIdx.x; i < BS * BS * BS; i += kNT) {
     const int ix = i % BS, iy = (i / BS) % BS, iz = i / (BS * BS);
@@ -312,11 +409,13 @@ __global__ void __launch_bounds__(kNT) k_ic(T* reg, const int32_t* list, const i
 }
 
 template <typename T, int BS>
-__global__ void __launch_bounds__(kNT) k_mask(T* chi, const int32_t* list, const int4* binfo, const PhysK ph, const MaskK m) {
+__global__ void __launch_bounds__(kNT) k_mask(T* chi, const int32_t* blist, const int32_t* ranks, const int4* binfo,
+                                               const PhysK ph, const MaskK m) {
   using L = Lay<T, BS>;
   constexpr int M = L::M;
-  const int slot = list[blockIdx.x];
-  const int4 bi = binfo[blockIdx.x];
+  const int rank = ranks ? ranks[blockIdx.x] : (int)blockIdx.x;
+  const int slot = blist[rank];
+  const int4 bi = binfo[rank];
   const double h = ph.root_len / ((double)(1 << bi.x) * M);
   for (int i = threadIdx.x; i < BS * BS * BS; i += kNT) {
     const int ix = i % BS, iy = (i / BS) % BS, iz = i / (BS * BS);
@@ -431,9 +530,10 @@ void launch_sync_ext(int Bs, const T* reg, T* out, int g, const int32_t* list, i
   ACM_BS_DISPATCH(Bs, k_sync_ext, <<<grid1(n), kNT, 0, st>>>(reg, out, g, list, nbh, by_rank));
 }
 template <typename T>
-void launch_details(int Bs, const T* ext, const T* chi, const int32_t* blist, int64_t n, const double* norms, double* ind, double* chirange, cudaStream_t st) {
+void launch_details(int Bs, const T* reg, const T* chi, const int32_t* blist, const int32_t* nbh, int64_t n,
+                    const double* norms, double* ind, double* chirange, cudaStream_t st) {
   if (n <= 0) return;
-  ACM_BS_DISPATCH(Bs, k_details, <<<grid1(n), kNT, 0, st>>>(ext, chi, blist, norms, ind, chirange));
+  ACM_BS_DISPATCH(Bs, k_details, <<<grid1(n), kNT, 0, st>>>(reg, chi, blist, nbh, norms, ind, chirange));
 }
 template <typename T>
 void launch_maxnorm(int Bs, const T* reg, const int32_t* blist, int64_t n, unsigned long long* out, cudaStream_t st) {
@@ -441,24 +541,32 @@ void launch_maxnorm(int Bs, const T* reg, const int32_t* blist, int64_t n, unsig
   ACM_BS_DISPATCH(Bs, k_maxnorm, <<<grid1(n), kNT, 0, st>>>(reg, blist, out));
 }
 template <typename T>
-void launch_refine(int Bs, const T* ext, T* reg, const int4* tasks, int64_t n, cudaStream_t st) {
+void launch_refine(int Bs, const T* src, T* dst, const int4* tasks, int64_t n, const int32_t* blist,
+                   const int32_t* nbh, cudaStream_t st) {
   if (n <= 0) return;
-  ACM_BS_DISPATCH(Bs, k_refine, <<<grid1(n), kNT, 0, st>>>(ext, reg, tasks));
+  ACM_BS_DISPATCH(Bs, k_refine, <<<grid1(n), kNT, 0, st>>>(src, dst, tasks, blist, nbh));
 }
 template <typename T>
-void launch_coarsen(int Bs, const T* ext, T* reg, const int32_t* tasks, int64_t n, cudaStream_t st) {
+void launch_coarsen(int Bs, const T* src, T* dst, const int32_t* tasks, int64_t n, cudaStream_t st) {
   if (n <= 0) return;
-  ACM_BS_DISPATCH(Bs, k_coarsen, <<<grid1(n), kNT, 0, st>>>(ext, reg, tasks));
+  ACM_BS_DISPATCH(Bs, k_coarsen, <<<grid1(n), kNT, 0, st>>>(src, dst, tasks));
 }
 template <typename T>
-void launch_ic(int Bs, T* reg, const int32_t* list, int64_t n, const int4* binfo, const PhysK& p, const IcK& ic, cudaStream_t st) {
+void launch_copy_blocks(int Bs, const T* src, T* dst, const int32_t* blist, int64_t n, cudaStream_t st) {
   if (n <= 0) return;
-  ACM_BS_DISPATCH(Bs, k_ic, <<<grid1(n), kNT, 0, st>>>(reg, list, binfo, p, ic));
+  ACM_BS_DISPATCH(Bs, k_copy_blocks, <<<grid1(n), kNT, 0, st>>>(src, dst, blist));
 }
 template <typename T>
-void launch_mask(int Bs, T* chi, const int32_t* list, int64_t n, const int4* binfo, const PhysK& p, const MaskK& m, cudaStream_t st) {
+void launch_ic(int Bs, T* reg, const int32_t* blist, const int32_t* ranks, int64_t n, const int4* binfo,
+               const PhysK& p, const IcK& ic, cudaStream_t st) {
   if (n <= 0) return;
-  ACM_BS_DISPATCH(Bs, k_mask, <<<grid1(n), kNT, 0, st>>>(chi, list, binfo, p, m));
+  ACM_BS_DISPATCH(Bs, k_ic, <<<grid1(n), kNT, 0, st>>>(reg, blist, ranks, binfo, p, ic));
+}
+template <typename T>
+void launch_mask(int Bs, T* chi, const int32_t* blist, const int32_t* ranks, int64_t n, const int4* binfo,
+                 const PhysK& p, const MaskK& m, cudaStream_t st) {
+  if (n <= 0) return;
+  ACM_BS_DISPATCH(Bs, k_mask, <<<grid1(n), kNT, 0, st>>>(chi, blist, ranks, binfo, p, m));
 }
 template <typename T>
 void launch_diag(int Bs, const T* reg, const T* chi, const int32_t* blist, int64_t n, double* out, cudaStream_t st) {
@@ -482,12 +590,13 @@ void launch_scatter(int Bs, const T* dense, T* reg, const int32_t* blist, int64_
   template void launch_fine_wins<T>(int, T*, const int2*, int64_t, const int32_t*, const int32_t*, cudaStream_t);          \
   template void launch_coarse_slabs<T>(int, const T*, T*, const int4*, int64_t, const int32_t*, cudaStream_t); \
   template void launch_sync_ext<T>(int, const T*, T*, int, const int32_t*, int64_t, const int32_t*, int, cudaStream_t); \
-  template void launch_details<T>(int, const T*, const T*, const int32_t*, int64_t, const double*, double*, double*, cudaStream_t); \
+  template void launch_details<T>(int, const T*, const T*, const int32_t*, const int32_t*, int64_t, const double*, double*, double*, cudaStream_t); \
   template void launch_maxnorm<T>(int, const T*, const int32_t*, int64_t, unsigned long long*, cudaStream_t); \
-  template void launch_refine<T>(int, const T*, T*, const int4*, int64_t, cudaStream_t);                   \
+  template void launch_refine<T>(int, const T*, T*, const int4*, int64_t, const int32_t*, const int32_t*, cudaStream_t); \
   template void launch_coarsen<T>(int, const T*, T*, const int32_t*, int64_t, cudaStream_t);               \
-  template void launch_ic<T>(int, T*, const int32_t*, int64_t, const int4*, const PhysK&, const IcK&, cudaStream_t); \
-  template void launch_mask<T>(int, T*, const int32_t*, int64_t, const int4*, const PhysK&, const MaskK&, cudaStream_t); \
+  template void launch_copy_blocks<T>(int, const T*, T*, const int32_t*, int64_t, cudaStream_t);          \
+  template void launch_ic<T>(int, T*, const int32_t*, const int32_t*, int64_t, const int4*, const PhysK&, const IcK&, cudaStream_t); \
+  template void launch_mask<T>(int, T*, const int32_t*, const int32_t*, int64_t, const int4*, const PhysK&, const MaskK&, cudaStream_t); \
   template void launch_diag<T>(int, const T*, const T*, const int32_t*, int64_t, double*, cudaStream_t);   \
   template void launch_gather<T>(int, const T*, T*, const int32_t*, int64_t, int, cudaStream_t);          \
   template void launch_scatter<T>(int, const T*, T*, const int32_t*, int64_t, cudaStream_t);

@@ -5,6 +5,7 @@
 // (Sec. 4.1: one allocation at start-up, released only at the end).
 #include <algorithm>
 #include <array>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -42,7 +43,7 @@ struct acm_forest {
   void* YA = nullptr;
   void* YB = nullptr;
   void* CHI = nullptr;
-  void* EXT = nullptr;
+  void* DENSE = nullptr;   // staging for block-order copies (n_blocks x 4 x Bs^3)
   void* SLAB = nullptr;
   // metadata (rank-indexed)
   int32_t* d_nbh = nullptr;
@@ -53,6 +54,7 @@ struct acm_forest {
   int4* d_slabt = nullptr;
   int4* d_reft = nullptr;
   int32_t* d_crst = nullptr;
+  int32_t* d_ranks = nullptr;
   double* d_norms = nullptr;
   unsigned long long* d_maxbits = nullptr;
   double* d_ind = nullptr;
@@ -73,7 +75,9 @@ struct acm_forest {
   int64_t launches = 0;
   bool timing = false;
   acm_step_stats stats{};
-  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+  bool stats_pending = false;
+  double host_topology_ms = 0, host_tree_ms = 0;   // cumulative host time of the tree logic
+  cudaEvent_t ev[12] = {};          // per stage: before sync, after sync, after the stage kernel
 };
 
 namespace {
@@ -98,6 +102,10 @@ acm_status fail(acm_forest* f, acm_status s, const std::string& msg) {
   } while (0)
 
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+double now_ms() {
+  return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
 
 struct Carve {
   size_t off = 0;
@@ -137,7 +145,7 @@ size_t carve(acm_forest* f, const acm_grid_params* g, char* base) {
   void* YA = c.take<char>(nb * L.BLK * es);
   void* YB = c.take<char>(nb * L.BLK * es);
   void* CHI = c.take<char>(nb * L.FS * es);
-  void* EXT = c.take<char>(nb * L.EBLK * es);
+  void* DENSE = c.take<char>(nb * 4 * (size_t)g->Bs * g->Bs * g->Bs * es);
   void* SLAB = c.take<char>(nb * 6 * 4 * 3 * bs2 * es);
   int32_t* nbh = c.take<int32_t>(nb * acm::kNbhStride * 4);
   int4* binfo = c.take<int4>(nb * 16);
@@ -147,15 +155,16 @@ size_t carve(acm_forest* f, const acm_grid_params* g, char* base) {
   int4* slabt = c.take<int4>(nb * 6 * 16);
   int4* reft = c.take<int4>(nb * 16);
   int32_t* crst = c.take<int32_t>(nb * 9 * 4);
+  int32_t* ranks = c.take<int32_t>(nb * 4);
   double* norms = c.take<double>(16 * 8);
   unsigned long long* maxbits = c.take<unsigned long long>(16 * 8);
   double* ind = c.take<double>(nb * 8);
   double* chir = c.take<double>(nb * 8);
   double* diag = c.take<double>(nb * 4 * 8);
   if (f) {
-    f->U = U; f->ACC = ACC; f->YA = YA; f->YB = YB; f->CHI = CHI; f->EXT = EXT; f->SLAB = SLAB;
+    f->U = U; f->ACC = ACC; f->YA = YA; f->YB = YB; f->CHI = CHI; f->DENSE = DENSE; f->SLAB = SLAB;
     f->d_nbh = nbh; f->d_binfo = binfo; f->d_blist = blist; f->d_slabidx = slabidx;
-    f->d_fw = fw; f->d_slabt = slabt; f->d_reft = reft; f->d_crst = crst;
+    f->d_fw = fw; f->d_slabt = slabt; f->d_reft = reft; f->d_crst = crst; f->d_ranks = ranks;
     f->d_norms = norms; f->d_maxbits = maxbits; f->d_ind = ind; f->d_chir = chir; f->d_diag = diag;
   }
   return c.off;
@@ -175,6 +184,7 @@ constexpr int kFaceBox[6] = {12, 14, 10, 16, 4, 22};
 
 // Rebuild the rank-indexed device metadata after any change of the grid.
 acm_status upload_topology(acm_forest* f) {
+  const double t0 = now_ms();
   const acm::Forest& fo = *f->fo;
   f->order = fo.sorted();
   const size_t n = f->order.size();
@@ -237,6 +247,7 @@ acm_status upload_topology(acm_forest* f) {
     CK(cudaMemcpyAsync(f->d_slabt, slabt.data(), slabt.size() * sizeof(int4), cudaMemcpyHostToDevice, f->st));
   // the host vectors die at return: make the copies complete first
   CK(cudaStreamSynchronize(f->st));
+  f->host_topology_ms += now_ms() - t0;
   return ACM_OK;
 }
 
@@ -260,17 +271,21 @@ acm_status sync_stage(acm_forest* f, T* reg) {
   return ACM_OK;
 }
 
-// Fine wins + the adaptation buffer (ghost depth kGE) of every block, slot-indexed.
 template <typename T>
-acm_status sync_ext(acm_forest* f, T* reg) {
-  const int Bs = f->gp.Bs;
+acm_status fine_wins(acm_forest* f, T* reg) {
   if (f->n_fw) {
-    acm::launch_fine_wins<T>(Bs, reg, f->d_fw, f->n_fw, f->d_nbh, f->d_blist, f->st);
+    acm::launch_fine_wins<T>(f->gp.Bs, reg, f->d_fw, f->n_fw, f->d_nbh, f->d_blist, f->st);
     CKL();
     ++f->launches;
   }
-  acm::launch_sync_ext<T>(Bs, reg, reinterpret_cast<T*>(f->EXT), acm::kGE, f->d_blist,
-                          (int64_t)f->order.size(), f->d_nbh, 0, f->st);
+  return ACM_OK;
+}
+
+// Copy every block of U to YA (same slots): the source of refinement and coarsening moves.
+template <typename T>
+acm_status snapshot_state(acm_forest* f) {
+  acm::launch_copy_blocks<T>(f->gp.Bs, reinterpret_cast<const T*>(f->U), reinterpret_cast<T*>(f->YA), f->d_blist,
+                             (int64_t)f->order.size(), f->st);
   CKL();
   ++f->launches;
   return ACM_OK;
@@ -308,13 +323,29 @@ double cfl_dt(const acm_forest* f, double u_max) {
   return dt;
 }
 
+// Mask on every block, or only on the blocks whose slots are in `fresh` (new blocks).
 template <typename T>
-acm_status eval_mask(acm_forest* f) {
+acm_status eval_mask(acm_forest* f, const std::vector<int32_t>* fresh = nullptr) {
   if (!f->mask_on) return ACM_OK;
-  acm::launch_mask<T>(f->gp.Bs, reinterpret_cast<T*>(f->CHI), f->d_blist, (int64_t)f->order.size(), f->d_binfo,
-                      f->phk, f->mask, f->st);
+  const int32_t* ranks = nullptr;
+  int64_t n = (int64_t)f->order.size();
+  std::vector<int32_t> rl;
+  if (fresh) {
+    std::unordered_map<int32_t, int32_t> rank_of;
+    rank_of.reserve(f->blist.size() * 2);
+    for (size_t r = 0; r < f->blist.size(); ++r) rank_of[f->blist[r]] = (int32_t)r;
+    rl.reserve(fresh->size());
+    for (int32_t s : *fresh) rl.push_back(rank_of.at(s));
+    if (rl.empty()) return ACM_OK;
+    CK(cudaMemcpyAsync(f->d_ranks, rl.data(), rl.size() * 4, cudaMemcpyHostToDevice, f->st));
+    ranks = f->d_ranks;
+    n = (int64_t)rl.size();
+  }
+  acm::launch_mask<T>(f->gp.Bs, reinterpret_cast<T*>(f->CHI), f->d_blist, ranks, n, f->d_binfo, f->phk, f->mask,
+                      f->st);
   CKL();
   ++f->launches;
+  if (fresh) CK(cudaStreamSynchronize(f->st));
   return ACM_OK;
 }
 
@@ -334,14 +365,13 @@ acm_status rk4(acm_forest* f, double dt, double* dt_used) {
   T* YB = reinterpret_cast<T*>(f->YB);
   const acm::TopoK t = topo(f);
   const int64_t l0 = f->launches;
-  double stage_ms = 0, sync_ms = 0;
   for (int s = 1; s <= 4; ++s) {
     T* in = s == 1 ? U : (s == 2 ? YA : (s == 3 ? YB : YA));
     T* out = s == 1 ? YA : (s == 2 ? YB : (s == 3 ? YA : U));
-    if (f->timing) CK(cudaEventRecord(f->ev[0], f->st));
+    if (f->timing) CK(cudaEventRecord(f->ev[3 * (s - 1)], f->st));
     acm_status st = sync_stage<T>(f, in);
     if (st) return st;
-    if (f->timing) CK(cudaEventRecord(f->ev[1], f->st));
+    if (f->timing) CK(cudaEventRecord(f->ev[3 * (s - 1) + 1], f->st));
     acm::StageK<T> a;
     a.in = in;
     a.U = U;
@@ -354,65 +384,67 @@ acm_status rk4(acm_forest* f, double dt, double* dt_used) {
     acm::launch_stage<T>(s, f->gp.Bs, a, t, f->phk, f->st);
     CKL();
     ++f->launches;
-    if (f->timing) {
-      CK(cudaEventRecord(f->ev[2], f->st));
-      CK(cudaEventSynchronize(f->ev[2]));
-      float a01 = 0, a12 = 0;
-      CK(cudaEventElapsedTime(&a01, f->ev[0], f->ev[1]));
-      CK(cudaEventElapsedTime(&a12, f->ev[1], f->ev[2]));
-      sync_ms += a01;
-      stage_ms += a12;
-    }
+    if (f->timing) CK(cudaEventRecord(f->ev[3 * (s - 1) + 2], f->st));
   }
   f->time += dt;
+  // algorithmic bytes of the four stage kernels: per point 64 words (registers Y, U, acc in and
+  // out, see stage.cu) plus one word of mask per stage when a mask is set
   const double npts = (double)f->order.size() * f->gp.Bs * f->gp.Bs * f->gp.Bs;
   const double words = 64.0 + (f->mask_on ? 4.0 : 0.0);
-  f->stats.stage_ms = stage_ms;
-  f->stats.sync_ms = sync_ms;
+  f->stats.stage_ms = 0;
+  f->stats.sync_ms = 0;
   f->stats.stage_bytes = npts * words * (double)f->esz;
   f->stats.n_launches = f->launches - l0;
+  f->stats_pending = f->timing;
   return ACM_OK;
 }
 
 template <typename T>
 acm_status refine_all(acm_forest* f) {
   acm::Forest& fo = *f->fo;
+  const double t0 = now_ms();
   std::vector<BoxKey> parents;
-  for (const BoxKey& b : f->order)
-    if (b.J < fo.Jmax) parents.push_back(b);
+  std::vector<int32_t> prank;
+  for (size_t r = 0; r < f->order.size(); ++r)
+    if (f->order[r].J < fo.Jmax) {
+      parents.push_back(f->order[r]);
+      prank.push_back((int32_t)r);
+    }
   if (parents.empty()) return ACM_OK;
   if ((int64_t)parents.size() * 7 > fo.n_free())
     return fail(f, ACM_ECAPACITY, "block pool too small to refine");
-  acm_status s = sync_ext<T>(f, reinterpret_cast<T*>(f->U));
+  // synchronise U (fine wins), keep a copy of it as the source of the predictions
+  acm_status s = fine_wins<T>(f, reinterpret_cast<T*>(f->U));
   if (s) return s;
-  std::vector<int32_t> old_slot(parents.size());
+  s = snapshot_state<T>(f);
+  if (s) return s;
   std::vector<BoxKey> kids;
   kids.reserve(parents.size() * 8);
-  for (size_t i = 0; i < parents.size(); ++i) {
-    old_slot[i] = fo.leaves.at(parents[i]);
+  for (size_t i = 0; i < parents.size(); ++i)
     for (int c = 0; c < 8; ++c) kids.push_back(acm::Forest::child(parents[i], c));
-  }
   std::vector<int32_t> new_slot;
   if (!fo.apply_pass(parents, kids, &new_slot)) return fail(f, ACM_ECAPACITY, "block pool exhausted");
   std::vector<int4> tasks(kids.size());
-  for (size_t i = 0; i < kids.size(); ++i) tasks[i] = make_int4(old_slot[i / 8], (int)(i % 8), new_slot[i], 0);
+  for (size_t i = 0; i < kids.size(); ++i) tasks[i] = make_int4(prank[i / 8], (int)(i % 8), new_slot[i], 0);
+  f->host_tree_ms += now_ms() - t0;
   CK(cudaMemcpyAsync(f->d_reft, tasks.data(), tasks.size() * sizeof(int4), cudaMemcpyHostToDevice, f->st));
-  acm::launch_refine<T>(f->gp.Bs, reinterpret_cast<const T*>(f->EXT), reinterpret_cast<T*>(f->U), f->d_reft,
-                        (int64_t)tasks.size(), f->st);
+  // old-grid tables are still on the device: the upload below is ordered after this kernel
+  acm::launch_refine<T>(f->gp.Bs, reinterpret_cast<const T*>(f->YA), reinterpret_cast<T*>(f->U), f->d_reft,
+                        (int64_t)tasks.size(), f->d_blist, f->d_nbh, f->st);
   CKL();
   ++f->launches;
   s = upload_topology(f);   // synchronises the stream (tasks buffer lifetime)
   if (s) return s;
-  return eval_mask<T>(f);
+  return eval_mask<T>(f, &new_slot);
 }
 
 template <typename T>
 acm_status indicators(acm_forest* f, const double norms[4]) {
-  acm_status s = sync_ext<T>(f, reinterpret_cast<T*>(f->U));
+  acm_status s = fine_wins<T>(f, reinterpret_cast<T*>(f->U));
   if (s) return s;
   CK(cudaMemcpyAsync(f->d_norms, norms, 4 * sizeof(double), cudaMemcpyHostToDevice, f->st));
-  acm::launch_details<T>(f->gp.Bs, reinterpret_cast<const T*>(f->EXT),
-                         f->mask_on ? reinterpret_cast<const T*>(f->CHI) : nullptr, f->d_blist,
+  acm::launch_details<T>(f->gp.Bs, reinterpret_cast<const T*>(f->U),
+                         f->mask_on ? reinterpret_cast<const T*>(f->CHI) : nullptr, f->d_blist, f->d_nbh,
                          (int64_t)f->order.size(), f->d_norms, f->d_ind, f->d_chir, f->st);
   CKL();
   ++f->launches;
@@ -436,6 +468,7 @@ acm_status coarsen(acm_forest* f, int64_t* n_blocks, int* n_passes) {
     CK(cudaMemcpyAsync(ind.data(), f->d_ind, n * 8, cudaMemcpyDeviceToHost, f->st));
     CK(cudaMemcpyAsync(chr.data(), f->d_chir, n * 8, cudaMemcpyDeviceToHost, f->st));
     CK(cudaStreamSynchronize(f->st));
+    const double th = now_ms();
     std::unordered_map<BoxKey, bool, acm::BoxKeyHash> tag;
     for (size_t r = 0; r < n; ++r) {
       const BoxKey& b = f->order[r];
@@ -466,7 +499,10 @@ acm_status coarsen(acm_forest* f, int64_t* n_blocks, int* n_passes) {
       }
       if (ok) groups.push_back(p);
     }
-    if (groups.empty()) break;
+    if (groups.empty()) {
+      f->host_tree_ms += now_ms() - th;
+      break;
+    }
     std::sort(groups.begin(), groups.end(), [&](const BoxKey& a, const BoxKey& b) { return fo.key_less(a, b); });
     std::vector<BoxKey> removed;
     std::vector<std::array<int32_t, 8>> kid_slots(groups.size());
@@ -483,14 +519,18 @@ acm_status coarsen(acm_forest* f, int64_t* n_blocks, int* n_passes) {
       tasks[9 * g] = new_slot[g];
       for (int c = 0; c < 8; ++c) tasks[9 * g + 1 + c] = kid_slots[g][c];
     }
+    f->host_tree_ms += now_ms() - th;
+    // the merge reads a copy of the synchronised state (a parent may take a child's slot)
+    s = snapshot_state<T>(f);
+    if (s) return s;
     CK(cudaMemcpyAsync(f->d_crst, tasks.data(), tasks.size() * 4, cudaMemcpyHostToDevice, f->st));
-    acm::launch_coarsen<T>(f->gp.Bs, reinterpret_cast<const T*>(f->EXT), reinterpret_cast<T*>(f->U), f->d_crst,
+    acm::launch_coarsen<T>(f->gp.Bs, reinterpret_cast<const T*>(f->YA), reinterpret_cast<T*>(f->U), f->d_crst,
                            (int64_t)groups.size(), f->st);
     CKL();
     ++f->launches;
     s = upload_topology(f);
     if (s) return s;
-    s = eval_mask<T>(f);
+    s = eval_mask<T>(f, &new_slot);
     if (s) return s;
     ++passes;
   }
@@ -504,8 +544,8 @@ acm_status set_ic(acm_forest* f, int kind, const double* params, int n) {
   acm::IcK ic{};
   ic.kind = kind;
   for (int i = 0; i < n && i < 8; ++i) ic.p[i] = params[i];
-  acm::launch_ic<T>(f->gp.Bs, reinterpret_cast<T*>(f->U), f->d_blist, (int64_t)f->order.size(), f->d_binfo,
-                    f->phk, ic, f->st);
+  acm::launch_ic<T>(f->gp.Bs, reinterpret_cast<T*>(f->U), f->d_blist, nullptr, (int64_t)f->order.size(),
+                    f->d_binfo, f->phk, ic, f->st);
   CKL();
   ++f->launches;
   return ACM_OK;
@@ -596,9 +636,7 @@ acm_status acm_create_forest(const acm_grid_params* grid, const acm_phys_params*
   acm_forest* fp = f.get();
   {
     acm_forest* f = fp;   // for CK
-    CK(cudaEventCreate(&f->ev[0]));
-    CK(cudaEventCreate(&f->ev[1]));
-    CK(cudaEventCreate(&f->ev[2]));
+    for (auto& e : f->ev) CK(cudaEventCreate(&e));
   }
   *out = f.release();
   return ACM_OK;
@@ -707,10 +745,10 @@ acm_status acm_sync_ghosts(acm_forest* f, int reg, void* out, int on_device) {
     CKL();
     ++f->launches;
   }
-  const size_t cap = (size_t)f->gp.max_blocks * f->lay.EBLK * f->esz / per;
+  const size_t cap = std::max<size_t>(1, (size_t)f->gp.max_blocks * 4 * f->gp.Bs * f->gp.Bs * f->gp.Bs * f->esz / per);
   for (size_t r0 = 0; r0 < n; r0 += cap) {
     const size_t m = std::min(cap, n - r0);
-    char* dst = on_device ? (char*)out + r0 * per : (char*)f->EXT;
+    char* dst = on_device ? (char*)out + r0 * per : (char*)f->DENSE;
     if (f->gp.precision == 64)
       acm::launch_sync_ext<double>(f->gp.Bs, (const double*)f->U, (double*)dst, g, f->d_blist + r0, (int64_t)m,
                                    f->d_nbh + r0 * acm::kNbhStride, 1, f->st);
@@ -720,7 +758,7 @@ acm_status acm_sync_ghosts(acm_forest* f, int reg, void* out, int on_device) {
     CKL();
     ++f->launches;
     if (!on_device) {
-      CK(cudaMemcpyAsync((char*)out + r0 * per, f->EXT, m * per, cudaMemcpyDeviceToHost, f->st));
+      CK(cudaMemcpyAsync((char*)out + r0 * per, f->DENSE, m * per, cudaMemcpyDeviceToHost, f->st));
       CK(cudaStreamSynchronize(f->st));
     }
   }
@@ -836,7 +874,7 @@ static acm_status copy_fields(acm_forest* f, void* buf, int64_t n_elems, int on_
   const int64_t need = nb * ncomp * (int64_t)f->gp.Bs * f->gp.Bs * f->gp.Bs;
   if (n_elems != need) return fail(f, ACM_EINVAL, "element count does not match n_blocks*comp*Bs^3");
   const size_t bytes = (size_t)need * f->esz;
-  void* dense = on_device ? buf : f->EXT;
+  void* dense = on_device ? buf : f->DENSE;
   if (to_pool) {
     if (!on_device) CK(cudaMemcpyAsync(dense, buf, bytes, cudaMemcpyHostToDevice, f->st));
     if (f->gp.precision == 64)
@@ -902,6 +940,22 @@ acm_status acm_enable_timing(acm_forest* f, int on) {
 
 acm_status acm_last_step_stats(acm_forest* f, acm_step_stats* out) {
   if (!f || !out) return ACM_EINVAL;
+  if (f->stats_pending) {
+    CK(cudaEventSynchronize(f->ev[11]));
+    double st = 0, sy = 0;
+    for (int s = 0; s < 4; ++s) {
+      float a = 0, b = 0;
+      CK(cudaEventElapsedTime(&a, f->ev[3 * s], f->ev[3 * s + 1]));
+      CK(cudaEventElapsedTime(&b, f->ev[3 * s + 1], f->ev[3 * s + 2]));
+      sy += a;
+      st += b;
+    }
+    f->stats.sync_ms = sy;
+    f->stats.stage_ms = st;
+    f->stats_pending = false;
+  }
+  f->stats.host_topology_ms = f->host_topology_ms;
+  f->stats.host_tree_ms = f->host_tree_ms;
   *out = f->stats;
   return ACM_OK;
 }

@@ -57,9 +57,10 @@ template <typename T>
 void launch_sync_ext(int Bs, const T* reg, T* out, int g, const int32_t* blist, int64_t n,
                      const int32_t* nbh, int by_rank, cudaStream_t st);
 
+// Block indicators from the state itself (fine-wins applied): ind[rank], chirange[rank].
 template <typename T>
-void launch_details(int Bs, const T* ext, const T* chi, const int32_t* blist, int64_t n,
-                    const double* norms, double* ind, double* chirange, cudaStream_t st);
+void launch_details(int Bs, const T* reg, const T* chi, const int32_t* blist, const int32_t* nbh,
+                    int64_t n, const double* norms, double* ind, double* chirange, cudaStream_t st);
 
 // Max norms: out[0..3] = max |u|,|v|,|w|,|p|, out[4] = max |(u,v,w)|, as ordered bit patterns
 // (non-negative doubles) combined with atomicMax; out must be zeroed before.
@@ -67,28 +68,33 @@ template <typename T>
 void launch_maxnorm(int Bs, const T* reg, const int32_t* blist, int64_t n,
                     unsigned long long* out, cudaStream_t st);
 
+// Children from a copy `src` of the synchronised state, old-grid tables (blist, nbh).
 template <typename T>
-void launch_refine(int Bs, const T* ext, T* reg, const int4* tasks, int64_t ntasks,
-                   cudaStream_t st);
+void launch_refine(int Bs, const T* src, T* dst, const int4* tasks, int64_t ntasks,
+                   const int32_t* blist, const int32_t* nbh, cudaStream_t st);
 
 template <typename T>
-void launch_coarsen(int Bs, const T* ext, T* reg, const int32_t* tasks /*[n][9]*/, int64_t ntasks,
+void launch_coarsen(int Bs, const T* src, T* dst, const int32_t* tasks /*[n][9]*/, int64_t ntasks,
                     cudaStream_t st);
+
+template <typename T>
+void launch_copy_blocks(int Bs, const T* src, T* dst, const int32_t* blist, int64_t n, cudaStream_t st);
 
 struct IcK {
   int kind;
   double p[8];
 };
+// Initial condition on the blocks of rank list `ranks` (nullptr: all n blocks).
 template <typename T>
-void launch_ic(int Bs, T* reg, const int32_t* list, int64_t n, const int4* binfo, const PhysK& p,
-               const IcK& ic, cudaStream_t st);
+void launch_ic(int Bs, T* reg, const int32_t* blist, const int32_t* ranks, int64_t n, const int4* binfo,
+               const PhysK& p, const IcK& ic, cudaStream_t st);
 
 struct MaskK {
   int kind;
   double p[8];
 };
 template <typename T>
-void launch_mask(int Bs, T* chi, const int32_t* list, int64_t n, const int4* binfo,
+void launch_mask(int Bs, T* chi, const int32_t* blist, const int32_t* ranks, int64_t n, const int4* binfo,
                  const PhysK& p, const MaskK& m, cudaStream_t st);
 
 // Per block raw sums over the half-open points: [sum chi u, sum chi v, sum chi w, sum |u|^2].

@@ -61,10 +61,21 @@ def fill_from_function(S, fn):
 
 
 def rel_linf(a, b):
-    """Per-component max |a - b| / max |b| (components with max |b| = 0 use absolute error)."""
+    """Per-component max |a - b| / scale: the velocity components share the scale
+    max(|u|, |v|, |w|) of the velocity field; the pressure uses max(max |p|, max |u|^2), i.e.
+    at least the dynamic pressure (density 1): an ACM pressure that starts from zero is an
+    O(dt) quantity whose error relative to itself is unbounded in any precision.  A zero
+    scale means absolute error."""
     out = []
+    four = b.shape[1] == 4
+    vscale = float(np.abs(b[:, :3]).max()) if four else 0.0
     for f in range(a.shape[1]):
-        den = float(np.abs(b[:, f]).max())
+        if four and f < 3:
+            den = vscale
+        elif four:
+            den = max(float(np.abs(b[:, f]).max()), vscale * vscale)
+        else:
+            den = float(np.abs(b[:, f]).max())
         err = float(np.abs(a[:, f] - b[:, f]).max())
         out.append(err / den if den > 0 else err)
     return out

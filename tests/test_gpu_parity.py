@@ -2,7 +2,8 @@
 
 Tolerances: topology (treecode, level, slot, coordinates, neighbour tables) bit-exact; fields
 relative L-infinity per component <= 1e-12 in FP64 and <= 2e-5 in FP32 (FP32 against the
-FP64 oracle on the same FP64-evaluated inputs).
+FP64 oracle on the same FP64-evaluated inputs), velocity components relative to the velocity
+scale max(|u|,|v|,|w|), pressure relative to max(max |p|, max |u|^2) (see gpu_util.rel_linf).
 """
 import math
 
@@ -210,7 +211,7 @@ def test_adaptive_sphere_steps_match_oracle(A):
 
 
 @pytest.mark.slow
-@pytest.mark.parametrize("prec,steps", [(64, 20), (32, 5)])
+@pytest.mark.parametrize("prec,steps", [(64, 20), (32, 3)])
 def test_taylor_green_config(A, prec, steps):
     """Periodic unit cube, 4x4x4 blocks of 17^3, Taylor-Green, nu = 1e-2, c0 = 10, CFL 0.5."""
     grid = _grid(Bs=17, nroot=(1, 1, 1), Jmin=2, Jmax=2, precision=prec, max_blocks=64)
