@@ -28,6 +28,7 @@ def nvcc():
 
 def _compile(src, obj, verbose):
     cmd = [nvcc(), "-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O3",
+           "-Xcompiler", "-fopenmp",
            "--expt-relaxed-constexpr", *ARCH, "-I", os.path.join(HERE, "..", "include"), "-c",
            os.path.join(CSRC, src), "-o", obj]
     if src.endswith(".cpp"):
@@ -56,7 +57,8 @@ def build(verbose=False, force=False):
         for s, l in zip(SOURCES, logs):
             sys.stderr.write(f"== {s}\n{l}")
     tmp = LIB + ".tmp"
-    r = subprocess.run([nvcc(), "-shared", *ARCH, "-o", tmp, *objs], capture_output=True, text=True)
+    r = subprocess.run([nvcc(), "-shared", *ARCH, "-Xcompiler", "-fopenmp", "-o", tmp, *objs, "-lgomp"],
+                       capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"linking libacm failed:\n{r.stdout}\n{r.stderr}")
     os.replace(tmp, LIB)

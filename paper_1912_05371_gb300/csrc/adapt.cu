@@ -56,22 +56,28 @@ __global__ void __launch_bounds__(kNT) k_fine_wins(T* reg, const int2* tasks, co
 }
 
 // ---- (2) coarse-face halo slabs ------------------------------------------------------------------
-// task = (rank, face F, slab index, -): the 3 x Bs x Bs halo points beyond face F, each the
-// value of the finest leaf holding it, else the tensor DD-4 prediction from the coarse lattice
-// (Sec. 3.1).  The coarse-lattice patch the predictions need (even local coordinates
-// [M-2, M+6] or [-6, 2] across the face, [-2, M+2] along it) is gathered into shared memory
-// once; every such point is held directly by some leaf.
+// task = (rank, face F, slab index, -); one CTA per (task, component).  The 3 x Bs x Bs halo
+// points beyond face F take the value of the finest leaf holding them, else the tensor DD-4
+// prediction from the coarse lattice (Sec. 3.1).  Only points on the face's tangential boundary
+// lines (t0 or t1 = 0 or M) can be held by a leaf of the block's level or finer; all others lie
+// in the coarser leaf alone.  The coarse patch the predictions need (even local coordinates
+// [M-2, M+6] or [-6, 2] across the face, [-2, M+2] along it) is gathered once, then predicted
+// separably: along t0, then t1, then across the face (a fixed order per face orientation, so
+// every block that needs a halo point gets bitwise the same value).
 // Slab layout [slab][comp][layer l-1][t1][t0] with (t0, t1) as in the stage kernel.
 template <typename T, int BS>
 __global__ void __launch_bounds__(kNT) k_coarse_slabs(const T* reg, T* slab, const int4* tasks,
                                                        const int32_t* nbh_all) {
   using L = Lay<T, BS>;
   constexpr int M = L::M;
-  constexpr int NT_ = M / 2 + 3;                    // coarse samples along the face: -2..M+2 step 2
+  constexpr int NC = M / 2 + 3;                     // coarse samples along the face: -2..M+2 step 2
   constexpr int NN = 5;                             // coarse planes across the face
   __shared__ int nbh[kNbhStride];
-  __shared__ T patch[4][NN][NT_][NT_];
-  const int4 tk = tasks[blockIdx.x];
+  __shared__ T P[NN][NC][NC];                       // [n][t1 coarse][t0 coarse]
+  __shared__ T A[NN][NC][BS];                       // predicted along t0
+  __shared__ T B[NN][BS][BS];                       // predicted along t0 and t1
+  const int4 tk = tasks[blockIdx.x >> 2];
+  const int f = blockIdx.x & 3;
   for (int i = threadIdx.x; i < kNbhStride; i += kNT) nbh[i] = nbh_all[(size_t)tk.x * kNbhStride + i];
   __syncthreads();
   const int F = tk.y, ax = F >> 1;
@@ -82,51 +88,60 @@ __global__ void __launch_bounds__(kNT) k_coarse_slabs(const T* reg, T* slab, con
     else if (ax == 1) { *x = t0; *y = nl; *z = t1; }
     else { *x = t0; *y = t1; *z = nl; }
   };
-  for (int i = threadIdx.x; i < 4 * NN * NT_ * NT_; i += kNT) {
-    const int a0 = i % NT_, a1 = (i / NT_) % NT_, an = (i / (NT_ * NT_)) % NN, f = i / (NN * NT_ * NT_);
+  const T w[4] = {T(-1) / T(16), T(9) / T(16), T(9) / T(16), T(-1) / T(16)};
+  for (int i = threadIdx.x; i < NN * NC * NC; i += kNT) {
+    const int a0 = i % NC, a1 = (i / NC) % NC, an = i / (NC * NC);
     int x, y, z;
     place(n0 + 2 * an, 2 * a0 - 2, 2 * a1 - 2, &x, &y, &z);
     T v;
     if (!direct_value<T, BS>(reg, nbh, x, y, z, f, &v)) v = T(__longlong_as_double(0x7ff8000000000000ll));
-    patch[f][an][a1][a0] = v;
+    P[an][a1][a0] = v;
   }
   __syncthreads();
-  const T w[4] = {T(-1) / T(16), T(9) / T(16), T(9) / T(16), T(-1) / T(16)};
-  const int off[4] = {-3, -1, 1, 3};
-  const int tot = 4 * 3 * BS * BS;
-  for (int i = threadIdx.x; i < tot; i += kNT) {
-    const int t0 = i % BS, t1 = (i / BS) % BS, l = (i / (BS * BS)) % 3 + 1, f = i / (3 * BS * BS);
+  for (int i = threadIdx.x; i < NN * NC * BS; i += kNT) {
+    const int t0 = i % BS, a1 = (i / BS) % NC, an = i / (BS * NC);
+    T acc = T(0);
+    if (t0 & 1) {
+      const int c = (t0 - 3 + 2) >> 1;              // coarse index of t0 - 3
+      for (int k = 0; k < 4; ++k) acc = acc + w[k] * P[an][a1][c + k];
+    } else {
+      acc = P[an][a1][(t0 + 2) >> 1];
+    }
+    A[an][a1][t0] = acc;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < NN * BS * BS; i += kNT) {
+    const int t0 = i % BS, t1 = (i / BS) % BS, an = i / (BS * BS);
+    T acc = T(0);
+    if (t1 & 1) {
+      const int c = (t1 - 3 + 2) >> 1;
+      for (int k = 0; k < 4; ++k) acc = acc + w[k] * A[an][c + k][t0];
+    } else {
+      acc = A[an][(t1 + 2) >> 1][t0];
+    }
+    B[an][t1][t0] = acc;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < 3 * BS * BS; i += kNT) {
+    const int t0 = i % BS, t1 = (i / BS) % BS, l = i / (BS * BS) + 1;
     const int nl = plus ? M + l : -l;
-    int x, y, z;
-    place(nl, t0, t1, &x, &y, &z);
+    const bool edge = t0 == 0 || t0 == M || t1 == 0 || t1 == M;
     T v;
-    if (!direct_value<T, BS>(reg, nbh, x, y, z, f, &v)) {
-      // tensor prediction with the same nesting as point_value: z outer, then y, then x
-      const int p[3] = {x, y, z};
-      int cnt[3], cb[3];
-      for (int a = 0; a < 3; ++a) cnt[a] = (p[a] & 1) ? 4 : 1;
-      auto pidx = [&](int a, int k) { return cnt[a] == 4 ? p[a] + off[k] : p[a]; };
-      T accz = T(0);
-      for (int kz = 0; kz < cnt[2]; ++kz) {
-        T accy = T(0);
-        for (int ky = 0; ky < cnt[1]; ++ky) {
-          T accx = T(0);
-          for (int kx = 0; kx < cnt[0]; ++kx) {
-            const int q[3] = {pidx(0, kx), pidx(1, ky), pidx(2, kz)};
-            // map the even point q into the patch
-            for (int a = 0; a < 3; ++a) cb[a] = q[a];
-            int qn, q0, q1;
-            if (ax == 0) { qn = cb[0]; q0 = cb[1]; q1 = cb[2]; }
-            else if (ax == 1) { qn = cb[1]; q0 = cb[0]; q1 = cb[2]; }
-            else { qn = cb[2]; q0 = cb[0]; q1 = cb[1]; }
-            const T c = patch[f][(qn - n0) >> 1][(q1 + 2) >> 1][(q0 + 2) >> 1];
-            accx = accx + (cnt[0] == 4 ? w[kx] : T(1)) * c;
-          }
-          accy = accy + (cnt[1] == 4 ? w[ky] : T(1)) * accx;
-        }
-        accz = accz + (cnt[2] == 4 ? w[kz] : T(1)) * accy;
+    bool have = false;
+    if (edge) {
+      int x, y, z;
+      place(nl, t0, t1, &x, &y, &z);
+      have = direct_value<T, BS>(reg, nbh, x, y, z, f, &v);
+    }
+    if (!have) {
+      const int c = nl - n0;                        // fine offset from the first coarse plane
+      if (c & 1) {
+        const int k0 = (c - 3) >> 1;
+        v = T(0);
+        for (int k = 0; k < 4; ++k) v = v + w[k] * B[k0 + k][t1][t0];
+      } else {
+        v = B[c >> 1][t1][t0];
       }
-      v = accz;
     }
     slab[((((size_t)tk.z * 4 + f) * 3 + (l - 1)) * BS + t1) * BS + t0] = v;
   }
@@ -165,15 +180,16 @@ __global__ void __launch_bounds__(kNT) k_sync_ext(const T* reg, T* out, int g, c
 // with the tensor DD-4 scheme (z outer, then y, then x) and subtracted.
 template <typename T, int BS>
 __global__ void __launch_bounds__(kNT) k_details(const T* reg, const T* chi, const int32_t* blist,
-                                                  const int32_t* nbh_all, const double* norms, double* ind,
-                                                  double* chirange) {
+                                                  const int32_t* ranks, const int32_t* nbh_all, const double* norms,
+                                                  double* ind, double* chirange) {
   using L = Lay<T, BS>;
   constexpr int M = L::M;
   constexpr int NC = M / 2 + 3;                 // coarse samples -1..M/2+1
   __shared__ int nbh[kNbhStride];
   __shared__ T c[NC][NC][NC];
-  const int slot = blist[blockIdx.x];
-  for (int i = threadIdx.x; i < kNbhStride; i += kNT) nbh[i] = nbh_all[(size_t)blockIdx.x * kNbhStride + i];
+  const int rank = ranks ? ranks[blockIdx.x] : (int)blockIdx.x;
+  const int slot = blist[rank];
+  for (int i = threadIdx.x; i < kNbhStride; i += kNT) nbh[i] = nbh_all[(size_t)rank * kNbhStride + i];
   const T w[4] = {T(-1) / T(16), T(9) / T(16), T(9) / T(16), T(-1) / T(16)};
   const int off[4] = {-3, -1, 1, 3};
   double best = 0.0;
@@ -243,8 +259,8 @@ __global__ void __launch_bounds__(kNT) k_details(const T* reg, const T* chi, con
       mn = fmin(mn, red[1][k]);
       mx = fmax(mx, red[2][k]);
     }
-    ind[blockIdx.x] = b;
-    chirange[blockIdx.x] = chi ? mx - mn : 0.0;
+    ind[rank] = b;
+    chirange[rank] = chi ? mx - mn : 0.0;
   }
 }
 
@@ -254,22 +270,26 @@ __global__ void __launch_bounds__(kNT) k_maxnorm(const T* reg, const int32_t* bl
   using L = Lay<T, BS>;
   const int slot = blist[blockIdx.x];
   const T* b = reg + (size_t)slot * L::BLK;
-  double m[5] = {0, 0, 0, 0, 0};
+  // arithmetic in the field precision (an FP32 field gives an FP32 norm, stored as double)
+  T m[5] = {T(0), T(0), T(0), T(0), T(0)};
   for (int i = threadIdx.x; i < BS * BS * BS; i += kNT) {
     const int x = i % BS, y = (i / BS) % BS, z = i / (BS * BS);
     const int pi = L::idx(x, y, z);
-    double v[4];
+    T v[4];
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
-      v[f] = (double)b[(size_t)f * L::FS + pi];
-      m[f] = fmax(m[f], fabs(v[f]));
+      v[f] = b[(size_t)f * L::FS + pi];
+      const T a = tabs(v[f]);
+      m[f] = a > m[f] ? a : m[f];
     }
-    m[4] = fmax(m[4], sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]));
+    const T mag = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    m[4] = mag > m[4] ? mag : m[4];
   }
 #pragma unroll
   for (int k = 0; k < 5; ++k) {
-    for (int o = 16; o > 0; o >>= 1) m[k] = fmax(m[k], __shfl_xor_sync(0xffffffffu, m[k], o));
-    if ((threadIdx.x & 31) == 0) atomicMax(out + k, (unsigned long long)__double_as_longlong(m[k]));
+    double mk = (double)m[k];
+    for (int o = 16; o > 0; o >>= 1) mk = fmax(mk, __shfl_xor_sync(0xffffffffu, mk, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out + k, (unsigned long long)__double_as_longlong(mk));
   }
 }
 
@@ -284,51 +304,107 @@ __global__ void __launch_bounds__(kNT) k_refine(const T* src, T* dst, const int4
   using L = Lay<T, BS>;
   constexpr int M = L::M;
   constexpr int NP = M / 2 + 3;                 // parent samples per axis
+  constexpr int NEV = M / 4 + 5;                // even-lattice samples per axis around them
+  // two regions, each reused once its content is dead: R1 holds the parent samples pp, later
+  // the y-pass qy; R2 holds the even-lattice patch ev, later the x-pass qx
+  constexpr int R1 = (NP * NP * NP > NP * BS * BS) ? NP * NP * NP : NP * BS * BS;
+  constexpr int R2 = (NEV * NEV * NEV > NP * NP * BS) ? NEV * NEV * NEV : NP * NP * BS;
   __shared__ int nbh[kNbhStride];
-  __shared__ T pp[NP][NP][NP];
+  __shared__ __align__(16) T r1[R1];
+  __shared__ __align__(16) T r2[R2];
+  T(&pp)[NP][NP][NP] = *reinterpret_cast<T(*)[NP][NP][NP]>(r1);
+  T(&qy)[NP][BS][BS] = *reinterpret_cast<T(*)[NP][BS][BS]>(r1);
+  T(&ev)[NEV][NEV][NEV] = *reinterpret_cast<T(*)[NEV][NEV][NEV]>(r2);
+  T(&qx)[NP][NP][BS] = *reinterpret_cast<T(*)[NP][NP][BS]>(r2);
   const int4 tk = tasks[blockIdx.x];
   const int pslot = blist[tk.x];
   for (int i = threadIdx.x; i < kNbhStride; i += kNT) nbh[i] = nbh_all[(size_t)tk.x * kNbhStride + i];
   const int cb[3] = {tk.y & 1, (tk.y >> 1) & 1, (tk.y >> 2) & 1};
   const int o[3] = {cb[0] * (M / 2) - 1, cb[1] * (M / 2) - 1, cb[2] * (M / 2) - 1};
+  const int e0[3] = {o[0] - 3, o[1] - 3, o[2] - 3};     // even: first even-lattice sample
   const T w[4] = {T(-1) / T(16), T(9) / T(16), T(9) / T(16), T(-1) / T(16)};
   const int off[4] = {-3, -1, 1, 3};
   for (int f = 0; f < 4; ++f) {
     __syncthreads();
-    for (int i = threadIdx.x; i < NP * NP * NP; i += kNT) {
-      const int x = o[0] + i % NP, y = o[1] + (i / NP) % NP, z = o[2] + i / (NP * NP);
+    // even-lattice points around the samples: held directly by some leaf
+    for (int i = threadIdx.x; i < NEV * NEV * NEV; i += kNT) {
+      const int x = e0[0] + 2 * (i % NEV), y = e0[1] + 2 * ((i / NEV) % NEV), z = e0[2] + 2 * (i / (NEV * NEV));
       T v;
       if (x >= 0 && x <= M && y >= 0 && y <= M && z >= 0 && z <= M)
         v = src[(size_t)pslot * L::BLK + (size_t)f * L::FS + L::idx(x, y, z)];
-      else
-        v = point_value<T, BS>(src, nbh, x, y, z, f);
+      else if (!direct_value<T, BS>(src, nbh, x, y, z, f, &v))
+        v = T(__longlong_as_double(0x7ff8000000000000ll));
+      ev[i / (NEV * NEV)][(i / NEV) % NEV][i % NEV] = v;
+    }
+    __syncthreads();
+    // parent samples: interior, else the finest leaf holding the point, else the DD-4
+    // prediction from the even lattice (z outer, then y, then x)
+    for (int i = threadIdx.x; i < NP * NP * NP; i += kNT) {
+      const int x = o[0] + i % NP, y = o[1] + (i / NP) % NP, z = o[2] + i / (NP * NP);
+      T v;
+      if (x >= 0 && x <= M && y >= 0 && y <= M && z >= 0 && z <= M) {
+        v = src[(size_t)pslot * L::BLK + (size_t)f * L::FS + L::idx(x, y, z)];
+      } else if (!direct_value<T, BS>(src, nbh, x, y, z, f, &v)) {
+        const int p[3] = {x, y, z};
+        int cnt[3];
+        for (int a = 0; a < 3; ++a) cnt[a] = (p[a] & 1) ? 4 : 1;
+        T accz = T(0);
+        for (int kz = 0; kz < cnt[2]; ++kz) {
+          const int zz = ((cnt[2] == 4 ? z + off[kz] : z) - e0[2]) >> 1;
+          T accy = T(0);
+          for (int ky = 0; ky < cnt[1]; ++ky) {
+            const int yy = ((cnt[1] == 4 ? y + off[ky] : y) - e0[1]) >> 1;
+            T accx = T(0);
+            for (int kx = 0; kx < cnt[0]; ++kx) {
+              const int xx = ((cnt[0] == 4 ? x + off[kx] : x) - e0[0]) >> 1;
+              accx = accx + (cnt[0] == 4 ? w[kx] : T(1)) * ev[zz][yy][xx];
+            }
+            accy = accy + (cnt[1] == 4 ? w[ky] : T(1)) * accx;
+          }
+          accz = accz + (cnt[2] == 4 ? w[kz] : T(1)) * accy;
+        }
+        v = accz;
+      }
       pp[i / (NP * NP)][(i / NP) % NP][i % NP] = v;
+    }
+    __syncthreads();
+    // separable prediction to the child's points: along x, then y, then z.  Each pass is the
+    // inner sum of the tensor formula, so the result equals sum_z w (sum_y w (sum_x w pp)).
+    const auto pos = [&](int a, int i) { return cb[a] * M + i; };   // parent-local fine index
+    for (int i = threadIdx.x; i < NP * NP * BS; i += kNT) {
+      const int ix = i % BS, yy = (i / BS) % NP, zz = i / (BS * NP);
+      const int px = pos(0, ix);
+      T acc = T(0);
+      if (px & 1) {
+        for (int k = 0; k < 4; ++k) acc = acc + w[k] * pp[zz][yy][(px + off[k]) / 2 - o[0]];
+      } else {
+        acc = acc + T(1) * pp[zz][yy][px / 2 - o[0]];
+      }
+      qx[zz][yy][ix] = acc;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < NP * BS * BS; i += kNT) {
+      const int ix = i % BS, iy = (i / BS) % BS, zz = i / (BS * BS);
+      const int py = pos(1, iy);
+      T acc = T(0);
+      if (py & 1) {
+        for (int k = 0; k < 4; ++k) acc = acc + w[k] * qx[zz][(py + off[k]) / 2 - o[1]][ix];
+      } else {
+        acc = acc + T(1) * qx[zz][py / 2 - o[1]][ix];
+      }
+      qy[zz][iy][ix] = acc;
     }
     __syncthreads();
     for (int i = threadIdx.x; i < BS * BS * BS; i += kNT) {
       const int ix = i % BS, iy = (i / BS) % BS, iz = i / (BS * BS);
-      // parent-local fine-lattice position (twice the parent index): c*M + i
-      const int px = cb[0] * M + ix, py = cb[1] * M + iy, pz = cb[2] * M + iz;
-      const int nx = (px & 1) ? 4 : 1, ny = (py & 1) ? 4 : 1, nz = (pz & 1) ? 4 : 1;
-      T accz = T(0);
-      for (int kz = 0; kz < nz; ++kz) {
-        const int zz = (nz == 4 ? pz + off[kz] : pz) / 2 - o[2];
-        const T wz = nz == 4 ? w[kz] : T(1);
-        T accy = T(0);
-        for (int ky = 0; ky < ny; ++ky) {
-          const int yy = (ny == 4 ? py + off[ky] : py) / 2 - o[1];
-          const T wy = ny == 4 ? w[ky] : T(1);
-          T accx = T(0);
-          for (int kx = 0; kx < nx; ++kx) {
-            const int xx = (nx == 4 ? px + off[kx] : px) / 2 - o[0];
-            const T wx = nx == 4 ? w[kx] : T(1);
-            accx = accx + wx * pp[zz][yy][xx];
-          }
-          accy = accy + wy * accx;
-        }
-        accz = accz + wz * accy;
+      const int pz = pos(2, iz);
+      T acc = T(0);
+      if (pz & 1) {
+        for (int k = 0; k < 4; ++k) acc = acc + w[k] * qy[(pz + off[k]) / 2 - o[2]][iy][ix];
+      } else {
+        acc = acc + T(1) * qy[pz / 2 - o[2]][iy][ix];
       }
-      dst[(size_t)tk.z * L::BLK + (size_t)f * L::FS + L::idx(ix, iy, iz)] = accz;
+      dst[(size_t)tk.z * L::BLK + (size_t)f * L::FS + L::idx(ix, iy, iz)] = acc;
     }
   }
 }
@@ -417,16 +493,42 @@ __global__ void __launch_bounds__(kNT) k_mask(T* chi, const int32_t* blist, cons
   const int slot = blist[rank];
   const int4 bi = binfo[rank];
   const double h = ph.root_len / ((double)(1 << bi.x) * M);
+  // A block that lies entirely farther than 40 delta from the sphere surface has tanh(d/delta)
+  // = +-1 exactly in double precision at all its points (1 - tanh(40) < 1e-34): chi is exactly
+  // 0 or 1 there and needs no transcendental.  Blocks on the periodic seam are evaluated fully.
+  int uniform = -1;
+  if (m.kind == 1) {
+    const double lo[3] = {(double)bi.y * M * h, (double)bi.z * M * h, (double)bi.w * M * h};
+    const double L[3] = {ph.nroot[0] * ph.root_len, ph.nroot[1] * ph.root_len, ph.nroot[2] * ph.root_len};
+    bool seam = false;
+    double dmin2 = 0.0, dmax2 = 0.0;
+    for (int a = 0; a < 3; ++a) {
+      const double hi = lo[a] + M * h;
+      if (hi >= L[a]) seam = true;
+      const double c = m.p[a];
+      const double near = c < lo[a] ? lo[a] - c : (c > hi ? c - hi : 0.0);
+      const double far = fmax(fabs(c - lo[a]), fabs(hi - c));
+      dmin2 += near * near;
+      dmax2 += far * far;
+    }
+    if (!seam) {
+      if (sqrt(dmin2) - m.p[3] > 40.0 * m.p[4]) uniform = 0;
+      else if (sqrt(dmax2) - m.p[3] < -40.0 * m.p[4]) uniform = 1;
+    }
+  }
   for (int i = threadIdx.x; i < BS * BS * BS; i += kNT) {
     const int ix = i % BS, iy = (i / BS) % BS, iz = i / (BS * BS);
-    const double X = coord(ph, bi, 0, ix, M, h), Y = coord(ph, bi, 1, iy, M, h), Z = coord(ph, bi, 2, iz, M, h);
-    double c = 0.0;
-    if (m.kind == 1) {
-      const double dx = X - m.p[0], dy = Y - m.p[1], dz = Z - m.p[2];
-      const double d = sqrt(dx * dx + dy * dy + dz * dz) - m.p[3];
-      c = 0.5 * (1.0 - tanh(d / m.p[4]));
+    // evaluated in the field precision: FP64 fields in double, FP32 fields in float
+    T c = T(0);
+    if (uniform >= 0) {
+      c = T(uniform);
+    } else if (m.kind == 1) {
+      const T X = T(coord(ph, bi, 0, ix, M, h)), Y = T(coord(ph, bi, 1, iy, M, h)), Z = T(coord(ph, bi, 2, iz, M, h));
+      const T dx = X - T(m.p[0]), dy = Y - T(m.p[1]), dz = Z - T(m.p[2]);
+      const T d = sqrt(dx * dx + dy * dy + dz * dz) - T(m.p[3]);
+      c = T(0.5) * (T(1) - tanh(d / T(m.p[4])));
     }
-    chi[(size_t)slot * L::FS + L::idx(ix, iy, iz)] = T(c);
+    chi[(size_t)slot * L::FS + L::idx(ix, iy, iz)] = c;
   }
 }
 
@@ -522,7 +624,7 @@ void launch_fine_wins(int Bs, T* reg, const int2* tasks, int64_t n, const int32_
 template <typename T>
 void launch_coarse_slabs(int Bs, const T* reg, T* slab, const int4* tasks, int64_t n, const int32_t* nbh, cudaStream_t st) {
   if (n <= 0) return;
-  ACM_BS_DISPATCH(Bs, k_coarse_slabs, <<<grid1(n), kNT, 0, st>>>(reg, slab, tasks, nbh));
+  ACM_BS_DISPATCH(Bs, k_coarse_slabs, <<<grid1(4 * n), kNT, 0, st>>>(reg, slab, tasks, nbh));
 }
 template <typename T>
 void launch_sync_ext(int Bs, const T* reg, T* out, int g, const int32_t* list, int64_t n, const int32_t* nbh, int by_rank, cudaStream_t st) {
@@ -530,10 +632,11 @@ void launch_sync_ext(int Bs, const T* reg, T* out, int g, const int32_t* list, i
   ACM_BS_DISPATCH(Bs, k_sync_ext, <<<grid1(n), kNT, 0, st>>>(reg, out, g, list, nbh, by_rank));
 }
 template <typename T>
-void launch_details(int Bs, const T* reg, const T* chi, const int32_t* blist, const int32_t* nbh, int64_t n,
-                    const double* norms, double* ind, double* chirange, cudaStream_t st) {
+void launch_details(int Bs, const T* reg, const T* chi, const int32_t* blist, const int32_t* ranks,
+                    const int32_t* nbh, int64_t n, const double* norms, double* ind, double* chirange,
+                    cudaStream_t st) {
   if (n <= 0) return;
-  ACM_BS_DISPATCH(Bs, k_details, <<<grid1(n), kNT, 0, st>>>(reg, chi, blist, nbh, norms, ind, chirange));
+  ACM_BS_DISPATCH(Bs, k_details, <<<grid1(n), kNT, 0, st>>>(reg, chi, blist, ranks, nbh, norms, ind, chirange));
 }
 template <typename T>
 void launch_maxnorm(int Bs, const T* reg, const int32_t* blist, int64_t n, unsigned long long* out, cudaStream_t st) {
@@ -590,7 +693,7 @@ void launch_scatter(int Bs, const T* dense, T* reg, const int32_t* blist, int64_
   template void launch_fine_wins<T>(int, T*, const int2*, int64_t, const int32_t*, const int32_t*, cudaStream_t);          \
   template void launch_coarse_slabs<T>(int, const T*, T*, const int4*, int64_t, const int32_t*, cudaStream_t); \
   template void launch_sync_ext<T>(int, const T*, T*, int, const int32_t*, int64_t, const int32_t*, int, cudaStream_t); \
-  template void launch_details<T>(int, const T*, const T*, const int32_t*, const int32_t*, int64_t, const double*, double*, double*, cudaStream_t); \
+  template void launch_details<T>(int, const T*, const T*, const int32_t*, const int32_t*, const int32_t*, int64_t, const double*, double*, double*, cudaStream_t); \
   template void launch_maxnorm<T>(int, const T*, const int32_t*, int64_t, unsigned long long*, cudaStream_t); \
   template void launch_refine<T>(int, const T*, T*, const int4*, int64_t, const int32_t*, const int32_t*, cudaStream_t); \
   template void launch_coarsen<T>(int, const T*, T*, const int32_t*, int64_t, cudaStream_t);               \

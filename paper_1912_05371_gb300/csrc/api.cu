@@ -61,9 +61,18 @@ struct acm_forest {
   double* d_chir = nullptr;
   double* d_diag = nullptr;
 
-  // host mirrors of the current topology
+  // host mirrors of the current topology (pinned: built in place, then copied)
   std::vector<BoxKey> order;
   std::vector<int32_t> blist;
+  std::vector<int32_t> slot_rank;     // slot -> rank (-1: free)
+  std::vector<double> ind_slot, chr_slot;   // indicators of the current coarsening, by slot
+  int32_t* h_nbh = nullptr;
+  int4* h_binfo = nullptr;
+  int32_t* h_blist = nullptr;
+  int32_t* h_slabidx = nullptr;
+  int2* h_fw = nullptr;
+  int4* h_slabt = nullptr;
+  void* h_pinned = nullptr;
   int64_t n_fw = 0, n_slab = 0;
   int Jtop = 0;
 
@@ -182,70 +191,78 @@ acm::TopoK topo(const acm_forest* f) {
 
 constexpr int kFaceBox[6] = {12, 14, 10, 16, 4, 22};
 
-// Rebuild the rank-indexed device metadata after any change of the grid.
+// Rebuild the rank-indexed device metadata after any change of the grid: per block its 27
+// neighbour boxes (type, slots), then the fine-wins and coarse-face task lists.  Rows are built
+// in parallel into pinned host memory and copied in one go.
 acm_status upload_topology(acm_forest* f) {
   const double t0 = now_ms();
   const acm::Forest& fo = *f->fo;
   f->order = fo.sorted();
-  const size_t n = f->order.size();
+  const int64_t n = (int64_t)f->order.size();
   f->blist.resize(n);
-  std::vector<int32_t> nbh(n * acm::kNbhStride, -1);
-  std::vector<int4> binfo(n);
-  std::vector<int32_t> slabidx(n * 8, -1);
-  std::vector<int2> fw;
-  std::vector<int4> slabt;
-  f->Jtop = 0;
-  for (size_t r = 0; r < n; ++r) {
+  int bad = 0, jtop = 0;
+#pragma omp parallel for schedule(static) reduction(| : bad) reduction(max : jtop)
+  for (int64_t r = 0; r < n; ++r) {
     const BoxKey& b = f->order[r];
-    f->blist[r] = fo.leaves.at(b);
-    binfo[r] = make_int4(b.J, b.x, b.y, b.z);
-    f->Jtop = std::max(f->Jtop, b.J);
-    int32_t* row = &nbh[r * acm::kNbhStride];
+    const int32_t me = fo.leaves.get(b);
+    f->blist[r] = me;
+    f->h_blist[r] = me;
+    f->h_binfo[r] = make_int4(b.J, b.x, b.y, b.z);
+    jtop = std::max(jtop, b.J);
+    int32_t* row = f->h_nbh + r * acm::kNbhStride;
+    for (int e = 0; e < acm::kNbhStride; ++e) row[e] = -1;
+    for (int e = 0; e < 8; ++e) f->h_slabidx[r * 8 + e] = -1;
     for (int dz = -1; dz <= 1; ++dz)
       for (int dy = -1; dy <= 1; ++dy)
         for (int dx = -1; dx <= 1; ++dx) {
           const int d = acm::box_index(dx, dy, dz);
           const BoxStatus st = fo.box_status(b.J, (int64_t)b.x + dx, (int64_t)b.y + dy, (int64_t)b.z + dz);
-          if (st.type == acm::BOX_NONE) return fail(f, ACM_EGRADING, "grid is not 2:1 graded");
+          if (st.type == acm::BOX_NONE) { bad = 1; continue; }
           if (st.type == acm::BOX_REFINED) {
             // every child touching the block must be a leaf (kernels index these slots)
             for (int c = 0; c < 8; ++c) {
               const int cc[3] = {c & 1, (c >> 1) & 1, (c >> 2) & 1};
               const int dd[3] = {dx, dy, dz};
               bool touch = true;
-              for (int a = 0; a < 3; ++a)
-                if ((dd[a] == 1 && cc[a] != 0) || (dd[a] == -1 && cc[a] != 1)) touch = false;
-              if (touch && st.slot[c] < 0) return fail(f, ACM_EGRADING, "grid is not 2:1 graded");
+              for (int q = 0; q < 3; ++q)
+                if ((dd[q] == 1 && cc[q] != 0) || (dd[q] == -1 && cc[q] != 1)) touch = false;
+              if (touch && st.slot[c] < 0) bad = 1;
             }
           }
           for (int c = 0; c < 8; ++c) row[8 * d + c] = st.slot[c];
-          int t = st.type == acm::BOX_LEAF ? acm::kTypeLeaf
-                  : st.type == acm::BOX_COARSER ? acm::kTypeCoarser
-                                                : acm::kTypeRefined;
+          const int t = st.type == acm::BOX_LEAF ? acm::kTypeLeaf
+                        : st.type == acm::BOX_COARSER ? acm::kTypeCoarser
+                                                      : acm::kTypeRefined;
           row[acm::kNbhType + d] = t | (st.octant << 4);
-          if (st.type == acm::BOX_REFINED && d != 13) fw.push_back(make_int2((int)r, d));
         }
-    for (int F = 0; F < 6; ++F) {
-      const int d = kFaceBox[F];
-      if ((row[acm::kNbhType + d] & 15) == acm::kTypeCoarser) {
-        const int k = (int)slabt.size();
-        slabidx[r * 8 + F] = k;
-        slabt.push_back(make_int4((int)r, F, k, 0));
+  }
+  if (bad) return fail(f, ACM_EGRADING, "grid is not 2:1 graded");
+  f->Jtop = jtop;
+  int64_t nfw = 0, nsl = 0;
+  for (int64_t r = 0; r < n; ++r) {
+    const int32_t* row = f->h_nbh + r * acm::kNbhStride;
+    for (int d = 0; d < 27; ++d)
+      if (d != 13 && (row[acm::kNbhType + d] & 15) == acm::kTypeRefined) f->h_fw[nfw++] = make_int2((int)r, d);
+    for (int F = 0; F < 6; ++F)
+      if ((row[acm::kNbhType + kFaceBox[F]] & 15) == acm::kTypeCoarser) {
+        f->h_slabidx[r * 8 + F] = (int32_t)nsl;
+        f->h_slabt[nsl] = make_int4((int)r, F, (int)nsl, 0);
+        ++nsl;
       }
-    }
   }
-  f->n_fw = (int64_t)fw.size();
-  f->n_slab = (int64_t)slabt.size();
+  f->n_fw = nfw;
+  f->n_slab = nsl;
+  std::fill(f->slot_rank.begin(), f->slot_rank.end(), -1);
+  for (int64_t r = 0; r < n; ++r) f->slot_rank[f->blist[r]] = (int32_t)r;
   if (n) {
-    CK(cudaMemcpyAsync(f->d_nbh, nbh.data(), nbh.size() * 4, cudaMemcpyHostToDevice, f->st));
-    CK(cudaMemcpyAsync(f->d_binfo, binfo.data(), n * sizeof(int4), cudaMemcpyHostToDevice, f->st));
-    CK(cudaMemcpyAsync(f->d_blist, f->blist.data(), n * 4, cudaMemcpyHostToDevice, f->st));
-    CK(cudaMemcpyAsync(f->d_slabidx, slabidx.data(), n * 8 * 4, cudaMemcpyHostToDevice, f->st));
+    CK(cudaMemcpyAsync(f->d_nbh, f->h_nbh, (size_t)n * acm::kNbhStride * 4, cudaMemcpyHostToDevice, f->st));
+    CK(cudaMemcpyAsync(f->d_binfo, f->h_binfo, n * sizeof(int4), cudaMemcpyHostToDevice, f->st));
+    CK(cudaMemcpyAsync(f->d_blist, f->h_blist, n * 4, cudaMemcpyHostToDevice, f->st));
+    CK(cudaMemcpyAsync(f->d_slabidx, f->h_slabidx, n * 8 * 4, cudaMemcpyHostToDevice, f->st));
   }
-  if (!fw.empty()) CK(cudaMemcpyAsync(f->d_fw, fw.data(), fw.size() * sizeof(int2), cudaMemcpyHostToDevice, f->st));
-  if (!slabt.empty())
-    CK(cudaMemcpyAsync(f->d_slabt, slabt.data(), slabt.size() * sizeof(int4), cudaMemcpyHostToDevice, f->st));
-  // the host vectors die at return: make the copies complete first
+  if (nfw) CK(cudaMemcpyAsync(f->d_fw, f->h_fw, nfw * sizeof(int2), cudaMemcpyHostToDevice, f->st));
+  if (nsl) CK(cudaMemcpyAsync(f->d_slabt, f->h_slabt, nsl * sizeof(int4), cudaMemcpyHostToDevice, f->st));
+  // the pinned staging is reused by the next rebuild: complete the copies first
   CK(cudaStreamSynchronize(f->st));
   f->host_topology_ms += now_ms() - t0;
   return ACM_OK;
@@ -331,11 +348,8 @@ acm_status eval_mask(acm_forest* f, const std::vector<int32_t>* fresh = nullptr)
   int64_t n = (int64_t)f->order.size();
   std::vector<int32_t> rl;
   if (fresh) {
-    std::unordered_map<int32_t, int32_t> rank_of;
-    rank_of.reserve(f->blist.size() * 2);
-    for (size_t r = 0; r < f->blist.size(); ++r) rank_of[f->blist[r]] = (int32_t)r;
     rl.reserve(fresh->size());
-    for (int32_t s : *fresh) rl.push_back(rank_of.at(s));
+    for (int32_t s : *fresh) rl.push_back(f->slot_rank[s]);
     if (rl.empty()) return ACM_OK;
     CK(cudaMemcpyAsync(f->d_ranks, rl.data(), rl.size() * 4, cudaMemcpyHostToDevice, f->st));
     ranks = f->d_ranks;
@@ -438,14 +452,27 @@ acm_status refine_all(acm_forest* f) {
   return eval_mask<T>(f, &new_slot);
 }
 
+// Block indicators (details + mask range) of every block, or of the blocks whose slots are
+// in `only`; results land at their ranks in d_ind / d_chir.
 template <typename T>
-acm_status indicators(acm_forest* f, const double norms[4]) {
+acm_status indicators(acm_forest* f, const double norms[4], const std::vector<int32_t>* only = nullptr) {
   acm_status s = fine_wins<T>(f, reinterpret_cast<T*>(f->U));
   if (s) return s;
   CK(cudaMemcpyAsync(f->d_norms, norms, 4 * sizeof(double), cudaMemcpyHostToDevice, f->st));
+  const int32_t* ranks = nullptr;
+  int64_t n = (int64_t)f->order.size();
+  std::vector<int32_t> rl;
+  if (only) {
+    for (int32_t sl : *only) rl.push_back(f->slot_rank[sl]);
+    n = (int64_t)rl.size();
+    if (n) {
+      CK(cudaMemcpyAsync(f->d_ranks, rl.data(), rl.size() * 4, cudaMemcpyHostToDevice, f->st));
+      ranks = f->d_ranks;
+    }
+  }
   acm::launch_details<T>(f->gp.Bs, reinterpret_cast<const T*>(f->U),
-                         f->mask_on ? reinterpret_cast<const T*>(f->CHI) : nullptr, f->d_blist, f->d_nbh,
-                         (int64_t)f->order.size(), f->d_norms, f->d_ind, f->d_chir, f->st);
+                         f->mask_on ? reinterpret_cast<const T*>(f->CHI) : nullptr, f->d_blist, ranks, f->d_nbh, n,
+                         f->d_norms, f->d_ind, f->d_chir, f->st);
   CKL();
   ++f->launches;
   CK(cudaStreamSynchronize(f->st));
@@ -460,16 +487,36 @@ acm_status coarsen(acm_forest* f, int64_t* n_blocks, int* n_passes) {
   if (s) return s;
   const double norms[4] = {m[0], m[1], m[2], m[3]};
   int passes = 0;
+  // A merge leaves every other block's indicator unchanged: its even samples keep their values
+  // (decimation preserves coincident points), so later passes evaluate the new parents only.
+  std::vector<double>& ind_slot = f->ind_slot;
+  std::vector<double>& chr_slot = f->chr_slot;
+  std::vector<int32_t> fresh;
   for (int it = 0; it < 64; ++it) {
-    s = indicators<T>(f, norms);
+    s = indicators<T>(f, norms, it == 0 ? nullptr : &fresh);
     if (s) return s;
     const size_t n = f->order.size();
     std::vector<double> ind(n), chr(n);
     CK(cudaMemcpyAsync(ind.data(), f->d_ind, n * 8, cudaMemcpyDeviceToHost, f->st));
     CK(cudaMemcpyAsync(chr.data(), f->d_chir, n * 8, cudaMemcpyDeviceToHost, f->st));
     CK(cudaStreamSynchronize(f->st));
+    if (it == 0) {
+      for (size_t r = 0; r < n; ++r) {
+        ind_slot[f->blist[r]] = ind[r];
+        chr_slot[f->blist[r]] = chr[r];
+      }
+    } else {
+      for (int32_t sl : fresh) {
+        ind_slot[sl] = ind[f->slot_rank[sl]];
+        chr_slot[sl] = chr[f->slot_rank[sl]];
+      }
+    }
+    for (size_t r = 0; r < n; ++r) {
+      ind[r] = ind_slot[f->blist[r]];
+      chr[r] = chr_slot[f->blist[r]];
+    }
     const double th = now_ms();
-    std::unordered_map<BoxKey, bool, acm::BoxKeyHash> tag;
+    std::vector<uint8_t> tag(n, 0);
     for (size_t r = 0; r < n; ++r) {
       const BoxKey& b = f->order[r];
       bool t = false;
@@ -477,40 +524,41 @@ acm_status coarsen(acm_forest* f, int64_t* n_blocks, int* n_passes) {
         if (f->pp.dealias && b.J == fo.Jmax) t = true;
         else t = (ind[r] < f->pp.eps) && !(chr[r] > f->pp.mask_range_thr);
       }
-      tag[b] = t;
+      tag[r] = t;
     }
-    // sister groups: parents whose 8 children are leaves, all tagged, none with a finer neighbour
+    // sister groups: the 8 children of a parent are 8 consecutive blocks (children 0..7) in block
+    // order; a group merges if all are tagged and none has a finer neighbour (grading)
     std::vector<BoxKey> groups;
-    std::unordered_map<BoxKey, int, acm::BoxKeyHash> cnt;
-    for (const BoxKey& b : f->order)
-      if (b.J > 0) cnt[BoxKey{b.J - 1, b.x >> 1, b.y >> 1, b.z >> 1}]++;
-    for (const auto& kv : cnt) {
-      if (kv.second != 8) continue;
-      const BoxKey& p = kv.first;
+    std::vector<size_t> gstart;
+    for (size_t r = 0; r + 7 < n;) {
+      const BoxKey& b = f->order[r];
+      bool grp = b.J > 0 && (b.x & 1) == 0 && (b.y & 1) == 0 && (b.z & 1) == 0;
+      const BoxKey p{b.J - 1, b.x >> 1, b.y >> 1, b.z >> 1};
+      for (int c = 1; c < 8 && grp; ++c) grp = f->order[r + c] == acm::Forest::child(p, c);
+      if (!grp) { ++r; continue; }
       bool ok = true;
       for (int c = 0; c < 8 && ok; ++c) {
-        const BoxKey k = acm::Forest::child(p, c);
-        if (!tag[k]) { ok = false; break; }
-        for (int d = 0; d < 26 && ok; ++d) {
-          const int* dd = acm::kDirs.d[d];
-          const BoxStatus st = fo.box_status(k.J, (int64_t)k.x + dd[0], (int64_t)k.y + dd[1], (int64_t)k.z + dd[2]);
-          if (st.type == acm::BOX_REFINED) ok = false;
-        }
+        if (!tag[r + c]) ok = false;
+        const int32_t* row = f->h_nbh + (r + c) * acm::kNbhStride;
+        for (int d = 0; d < 27 && ok; ++d)
+          if (d != 13 && (row[acm::kNbhType + d] & 15) == acm::kTypeRefined) ok = false;
       }
-      if (ok) groups.push_back(p);
+      if (ok) {
+        groups.push_back(p);
+        gstart.push_back(r);
+      }
+      r += 8;
     }
     if (groups.empty()) {
       f->host_tree_ms += now_ms() - th;
       break;
     }
-    std::sort(groups.begin(), groups.end(), [&](const BoxKey& a, const BoxKey& b) { return fo.key_less(a, b); });
     std::vector<BoxKey> removed;
     std::vector<std::array<int32_t, 8>> kid_slots(groups.size());
     for (size_t g = 0; g < groups.size(); ++g)
       for (int c = 0; c < 8; ++c) {
-        const BoxKey k = acm::Forest::child(groups[g], c);
-        kid_slots[g][c] = fo.leaves.at(k);
-        removed.push_back(k);
+        kid_slots[g][c] = f->blist[gstart[g] + c];
+        removed.push_back(f->order[gstart[g] + c]);
       }
     std::vector<int32_t> new_slot;
     if (!fo.apply_pass(removed, groups, &new_slot)) return fail(f, ACM_ECAPACITY, "block pool exhausted");
@@ -532,6 +580,7 @@ acm_status coarsen(acm_forest* f, int64_t* n_blocks, int* n_passes) {
     if (s) return s;
     s = eval_mask<T>(f, &new_slot);
     if (s) return s;
+    fresh = new_slot;
     ++passes;
   }
   if (n_blocks) *n_blocks = (int64_t)f->order.size();
@@ -634,8 +683,23 @@ acm_status acm_create_forest(const acm_grid_params* grid, const acm_phys_params*
   f->fo.reset(new acm::Forest(grid->nroot, grid->Bs, grid->Jmin, grid->Jmax, grid->max_blocks));
   fill_phys(f.get());
   acm_forest* fp = f.get();
+  fp->slot_rank.assign((size_t)grid->max_blocks, -1);
+  fp->ind_slot.assign((size_t)grid->max_blocks, 0.0);
+  fp->chr_slot.assign((size_t)grid->max_blocks, 0.0);
   {
     acm_forest* f = fp;   // for CK
+    const size_t nb = (size_t)grid->max_blocks;
+    const size_t bytes = nb * acm::kNbhStride * 4 + nb * sizeof(int4) + nb * 4 + nb * 8 * 4 +
+                         nb * 27 * sizeof(int2) + nb * 6 * sizeof(int4) + 6 * 256;
+    CK(cudaMallocHost(&f->h_pinned, bytes));
+    char* p = (char*)f->h_pinned;
+    auto take = [&](size_t b) { char* q = p; p += (b + 255) & ~(size_t)255; return q; };
+    f->h_nbh = (int32_t*)take(nb * acm::kNbhStride * 4);
+    f->h_binfo = (int4*)take(nb * sizeof(int4));
+    f->h_blist = (int32_t*)take(nb * 4);
+    f->h_slabidx = (int32_t*)take(nb * 8 * 4);
+    f->h_fw = (int2*)take(nb * 27 * sizeof(int2));
+    f->h_slabt = (int4*)take(nb * 6 * sizeof(int4));
     for (auto& e : f->ev) CK(cudaEventCreate(&e));
   }
   *out = f.release();
@@ -646,6 +710,7 @@ acm_status acm_destroy_forest(acm_forest* f) {
   if (!f) return ACM_OK;
   for (auto& e : f->ev)
     if (e) cudaEventDestroy(e);
+  if (f->h_pinned) cudaFreeHost(f->h_pinned);
   delete f;
   return ACM_OK;
 }

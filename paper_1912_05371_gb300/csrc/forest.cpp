@@ -20,9 +20,66 @@ Directions::Directions() {
 }
 const Directions kDirs;
 
+void LeafMap::init(int64_t max_entries) {
+  size_t cap = 16;
+  while (cap < (size_t)(2 * max_entries + 16)) cap <<= 1;
+  tab_.assign(cap, Entry{BoxKey{0, 0, 0, 0}, -1});
+  mask_ = cap - 1;
+  n_ = 0;
+}
+
+void LeafMap::clear() {
+  for (Entry& e : tab_) e.slot = -1;
+  n_ = 0;
+}
+
+void LeafMap::put(const BoxKey& k, int32_t slot) {
+  size_t i = hash(k) & mask_;
+  while (true) {
+    Entry& e = tab_[i];
+    if (e.slot < 0) {
+      e.k = k;
+      e.slot = slot;
+      ++n_;
+      return;
+    }
+    if (e.k == k) {
+      e.slot = slot;
+      return;
+    }
+    i = (i + 1) & mask_;
+  }
+}
+
+bool LeafMap::erase(const BoxKey& k) {
+  size_t i = hash(k) & mask_;
+  while (true) {
+    if (tab_[i].slot < 0) return false;
+    if (tab_[i].k == k) break;
+    i = (i + 1) & mask_;
+  }
+  // backward-shift deletion keeps every probe chain unbroken
+  size_t j = i;
+  while (true) {
+    j = (j + 1) & mask_;
+    if (tab_[j].slot < 0) break;
+    const size_t home = hash(tab_[j].k) & mask_;
+    // move entry j into the hole at i unless its home lies cyclically in (i, j]
+    const bool in_range = (i <= j) ? (home > i && home <= j) : (home > i || home <= j);
+    if (!in_range) {
+      tab_[i] = tab_[j];
+      i = j;
+    }
+  }
+  tab_[i].slot = -1;
+  --n_;
+  return true;
+}
+
 Forest::Forest(const int nr[3], int bs, int jmin, int jmax, int64_t maxb)
     : Bs(bs), M(bs - 1), Jmin(jmin), Jmax(jmax), max_blocks(maxb) {
   for (int a = 0; a < 3; ++a) nroot[a] = nr[a];
+  leaves.init(maxb);
   clear();
 }
 
@@ -65,7 +122,7 @@ bool Forest::key_less(const BoxKey& a, const BoxKey& b) const {
 std::vector<BoxKey> Forest::sorted() const {
   std::vector<std::pair<std::pair<uint64_t, int>, BoxKey>> tmp;
   tmp.reserve(leaves.size());
-  for (const auto& kv : leaves) tmp.push_back({{treecode(kv.first), kv.first.J}, kv.first});
+  leaves.for_each([&](const BoxKey& k, int32_t) { tmp.push_back({{treecode(k), k.J}, k}); });
   std::sort(tmp.begin(), tmp.end(),
             [](const auto& a, const auto& b) { return a.first < b.first; });
   std::vector<BoxKey> out;
@@ -78,10 +135,10 @@ bool Forest::apply_pass(const std::vector<BoxKey>& removed, const std::vector<Bo
                         std::vector<int32_t>* created_slots) {
   if ((int64_t)created.size() - (int64_t)removed.size() > (int64_t)free_.size()) return false;
   for (const BoxKey& k : removed) {
-    auto it = leaves.find(k);
-    if (it == leaves.end()) continue;
-    free_.insert(it->second);
-    leaves.erase(it);
+    const int32_t s = leaves.get(k);
+    if (s < 0) continue;
+    free_.insert(s);
+    leaves.erase(k);
   }
   std::vector<size_t> idx(created.size());
   for (size_t i = 0; i < idx.size(); ++i) idx[i] = i;
@@ -92,7 +149,7 @@ bool Forest::apply_pass(const std::vector<BoxKey>& removed, const std::vector<Bo
   for (size_t i : idx) {
     const int32_t s = *free_.begin();
     free_.erase(free_.begin());
-    leaves[created[i]] = s;
+    leaves.put(created[i], s);
     if (created_slots) (*created_slots)[i] = s;
   }
   return true;
@@ -104,26 +161,26 @@ BoxStatus Forest::box_status(int J, int64_t x, int64_t y, int64_t z) const {
   st.octant = 0;
   for (int c = 0; c < 8; ++c) st.slot[c] = -1;
   const BoxKey k = wrap(J, x, y, z);
-  auto it = leaves.find(k);
-  if (it != leaves.end()) {
+  const int32_t s = leaves.get(k);
+  if (s >= 0) {
     st.type = BOX_LEAF;
-    st.slot[0] = it->second;
+    st.slot[0] = s;
     return st;
   }
   if (J > 0) {
-    auto ip = leaves.find(BoxKey{J - 1, k.x >> 1, k.y >> 1, k.z >> 1});
-    if (ip != leaves.end()) {
+    const int32_t sp = leaves.get(BoxKey{J - 1, k.x >> 1, k.y >> 1, k.z >> 1});
+    if (sp >= 0) {
       st.type = BOX_COARSER;
-      st.slot[0] = ip->second;
+      st.slot[0] = sp;
       st.octant = (k.x & 1) | ((k.y & 1) << 1) | ((k.z & 1) << 2);
       return st;
     }
   }
   bool any = false;
   for (int c = 0; c < 8; ++c) {
-    auto ic = leaves.find(child(k, c));
-    if (ic != leaves.end()) {
-      st.slot[c] = ic->second;
+    const int32_t sc = leaves.get(child(k, c));
+    if (sc >= 0) {
+      st.slot[c] = sc;
       any = true;
     }
   }
@@ -147,43 +204,40 @@ static int touching_children(const int d[3], int out[8]) {
 }
 
 bool Forest::is_graded() const {
-  for (const auto& kv : leaves) {
-    const BoxKey& b = kv.first;
-    for (int k = 0; k < 26; ++k) {
+  bool ok = true;
+  leaves.for_each([&](const BoxKey& b, int32_t) {
+    for (int k = 0; k < 26 && ok; ++k) {
       const int* d = kDirs.d[k];
       BoxStatus st = box_status(b.J, (int64_t)b.x + d[0], (int64_t)b.y + d[1], (int64_t)b.z + d[2]);
-      if (st.type == BOX_NONE) return false;
+      if (st.type == BOX_NONE) ok = false;
       if (st.type == BOX_REFINED) {
         int tc[8];
         const int n = touching_children(d, tc);
         for (int i = 0; i < n; ++i)
-          if (st.slot[tc[i]] < 0) return false;
+          if (st.slot[tc[i]] < 0) ok = false;
       }
     }
-  }
-  return true;
+  });
+  return ok;
 }
 
 bool Forest::tiles_domain() const {
   if (leaves.empty()) return false;
   int Jref = 0;
-  for (const auto& kv : leaves) Jref = std::max(Jref, kv.first.J);
+  leaves.for_each([&](const BoxKey& k, int32_t) { Jref = std::max(Jref, k.J); });
   // volume count in units of level-Jref boxes, then no overlap via the parent chain
   __int128 vol = 0;
-  for (const auto& kv : leaves) {
-    const int s = Jref - kv.first.J;
-    vol += (__int128)1 << (3 * s);
-  }
+  leaves.for_each([&](const BoxKey& k, int32_t) { vol += (__int128)1 << (3 * (Jref - k.J)); });
   __int128 total = (__int128)nblocks_axis(Jref, 0) * nblocks_axis(Jref, 1) * nblocks_axis(Jref, 2);
   if (vol != total) return false;
-  for (const auto& kv : leaves) {
-    const BoxKey& b = kv.first;
-    for (int L = b.J - 1; L >= 0; --L) {
+  bool ok = true;
+  leaves.for_each([&](const BoxKey& b, int32_t) {
+    for (int L = b.J - 1; L >= 0 && ok; --L) {
       const int s = b.J - L;
-      if (leaves.count(BoxKey{L, b.x >> s, b.y >> s, b.z >> s})) return false;
+      if (leaves.contains(BoxKey{L, b.x >> s, b.y >> s, b.z >> s})) ok = false;
     }
-  }
-  return true;
+  });
+  return ok;
 }
 
 void Forest::neighbour_table(const std::vector<BoxKey>& order, int32_t* nbr, int8_t* rel) const {

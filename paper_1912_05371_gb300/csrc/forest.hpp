@@ -33,6 +33,42 @@ struct BoxKeyHash {
 
 enum BoxType : uint8_t { BOX_LEAF = 0, BOX_COARSER = 1, BOX_REFINED = 2, BOX_NONE = 3 };
 
+// Open-addressing hash table (linear probing, backward-shift deletion) from a box to the slot
+// of the leaf occupying it.  Capacity is a power of two at least twice the block pool.
+class LeafMap {
+ public:
+  struct Entry {
+    BoxKey k;
+    int32_t slot;     // -1: empty
+  };
+  void init(int64_t max_entries);
+  void clear();
+  int32_t get(const BoxKey& k) const {
+    size_t i = hash(k) & mask_;
+    while (true) {
+      const Entry& e = tab_[i];
+      if (e.slot < 0) return -1;
+      if (e.k == k) return e.slot;
+      i = (i + 1) & mask_;
+    }
+  }
+  bool contains(const BoxKey& k) const { return get(k) >= 0; }
+  void put(const BoxKey& k, int32_t slot);
+  bool erase(const BoxKey& k);
+  size_t size() const { return n_; }
+  bool empty() const { return n_ == 0; }
+  template <typename F>
+  void for_each(F&& fn) const {
+    for (const Entry& e : tab_)
+      if (e.slot >= 0) fn(e.k, e.slot);
+  }
+
+ private:
+  static size_t hash(const BoxKey& k) { return BoxKeyHash()(k); }
+  std::vector<Entry> tab_;
+  size_t mask_ = 0, n_ = 0;
+};
+
 // Status of a level-J box as seen from a neighbour: a leaf itself, covered by a leaf one
 // level coarser (slot[0], octant = which half per axis), or refined into level J+1 leaves
 // (slot[c] for child c = cx + 2cy + 4cz, -1 where the child is not a leaf).
@@ -64,7 +100,7 @@ class Forest {
   int nroot[3];
   int Bs, M, Jmin, Jmax;
   int64_t max_blocks;
-  std::unordered_map<BoxKey, int32_t, BoxKeyHash> leaves;
+  LeafMap leaves;
 
   int64_t nblocks_axis(int J, int a) const { return (int64_t)nroot[a] << J; }
   BoxKey wrap(int J, int64_t x, int64_t y, int64_t z) const;

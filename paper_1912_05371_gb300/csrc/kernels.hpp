@@ -58,9 +58,11 @@ void launch_sync_ext(int Bs, const T* reg, T* out, int g, const int32_t* blist, 
                      const int32_t* nbh, int by_rank, cudaStream_t st);
 
 // Block indicators from the state itself (fine-wins applied): ind[rank], chirange[rank].
+// (ranks: the blocks to evaluate, nullptr = all n; results are written at their ranks)
 template <typename T>
-void launch_details(int Bs, const T* reg, const T* chi, const int32_t* blist, const int32_t* nbh,
-                    int64_t n, const double* norms, double* ind, double* chirange, cudaStream_t st);
+void launch_details(int Bs, const T* reg, const T* chi, const int32_t* blist, const int32_t* ranks,
+                    const int32_t* nbh, int64_t n, const double* norms, double* ind, double* chirange,
+                    cudaStream_t st);
 
 // Max norms: out[0..3] = max |u|,|v|,|w|,|p|, out[4] = max |(u,v,w)|, as ordered bit patterns
 // (non-negative doubles) combined with atomicMax; out must be zeroed before.

@@ -25,12 +25,19 @@ namespace acm {
 
 namespace {
 
-template <int BS>
+template <typename T, int BS>
 struct Cfg {
   static constexpr int NT = ((BS * BS + 31) / 32) * 32;
-  static constexpr int W = BS + 6;       // padded plane width: 3 halo points each side
-  static constexpr int PW = W * W;
+  static constexpr int H = BS + 6;       // plane rows: 3 halo rows each side
+  // row stride: a warp covers consecutive pencils of about two rows; with a stride congruent
+  // to BS modulo the bank count (32 words for FP32) the second row continues on the next
+  // banks and the plane is read without bank conflicts
+  static constexpr int W = sizeof(T) == 4 ? BS + 32 : BS + 6;
+  static constexpr int PW = H * W;
+  static constexpr int NH = 48 * BS;     // x/y halo values per plane: 4 comp x 4 faces x 3 x BS
+  static constexpr int HPT = (NH + NT - 1) / NT;   // halo values per thread
 };
+
 
 // faces: 0 -x, 1 +x, 2 -y, 3 +y, 4 -z, 5 +z ; box index of the face neighbour
 __constant__ int kFaceBox[6] = {12, 14, 10, 16, 4, 22};
@@ -81,13 +88,14 @@ __device__ __forceinline__ const T* halo_ptr(const int (&ftype)[6], const int (&
 }
 
 template <typename T, int BS, int STAGE>
-__global__ void __launch_bounds__(Cfg<BS>::NT)
+__global__ void __launch_bounds__(Cfg<T, BS>::NT, sizeof(T) == 4 ? 2 : 1)
 k_stage(const StageK<T> a, const TopoK tp, const PhysK ph) {
   using L = Lay<T, BS>;
   constexpr int M = L::M;
-  constexpr int NT = Cfg<BS>::NT;
-  constexpr int W = Cfg<BS>::W;
-  constexpr int PW = Cfg<BS>::PW;
+  constexpr int NT = Cfg<T, BS>::NT;
+  constexpr int W = Cfg<T, BS>::W;
+  constexpr int PW = Cfg<T, BS>::PW;
+  constexpr int HPT = Cfg<T, BS>::HPT;
 
   __shared__ __align__(16) T buf[2][4][PW];
   __shared__ int ftype[6];
@@ -150,19 +158,61 @@ k_stage(const StageK<T> a, const TopoK tp, const PhysK ph) {
     if (zz < 0) return *halo_ptr<T, BS>(ftype, fs, a.in, a.slab, 4, -zz, x, y, f);
     return *halo_ptr<T, BS>(ftype, fs, a.in, a.slab, 5, zz - M, x, y, f);
   };
-  auto issue_halos = [&](int zz, T (*B)[PW]) {
-    for (int i = tid; i < 48 * BS; i += NT) {
-      const int tt = i % BS;
+  // this thread's x/y halo values of every plane, as affine functions of z: element
+  // (component f, face F, layer l, tangential t) of plane z is read from hp + z * hz, plus hd
+  // for z > M/2 (the upper child of a finer face); destination hdst in the plane buffer
+  const T* hp[HPT];
+  long long hd[HPT];
+  int hz[HPT], hdst[HPT];
+#pragma unroll
+  for (int k = 0; k < HPT; ++k) {
+    const int i = tid + k * NT;
+    hp[k] = nullptr;
+    hd[k] = 0;
+    hz[k] = 0;
+    hdst[k] = -1;
+    if (i < 48 * BS) {
+      const int t = i % BS;
       int r = i / BS;
       const int l = r % 3 + 1;
       r /= 3;
       const int F = r & 3, f = r >> 2;
       int hx, hy;
-      if (F == 0) { hx = -l; hy = tt; }
-      else if (F == 1) { hx = M + l; hy = tt; }
-      else if (F == 2) { hx = tt; hy = -l; }
-      else { hx = tt; hy = M + l; }
-      cp_async_elem(&B[f][(hy + 3) * W + hx + 3], halo_ptr<T, BS>(ftype, fs, a.in, a.slab, F, l, tt, zz, f));
+      if (F == 0) { hx = -l; hy = t; }
+      else if (F == 1) { hx = M + l; hy = t; }
+      else if (F == 2) { hx = t; hy = -l; }
+      else { hx = t; hy = M + l; }
+      hdst[k] = f * PW + (hy + 3) * W + hx + 3;
+      const int ty = ftype[F];
+      const bool plus = F & 1;
+      const int ax = F >> 1;
+      if (ty == kTypeCoarser) {
+        hp[k] = a.slab + (((size_t)fs[F][0] * 4 + f) * 3 + (l - 1)) * BS * BS + t;
+        hz[k] = BS;
+      } else if (ty == kTypeLeaf) {
+        const int nl = plus ? l : M - l;
+        const int x = ax == 0 ? nl : t, y = ax == 0 ? t : nl;
+        hp[k] = a.in + (size_t)fs[F][0] * L::BLK + (size_t)f * L::FS + L::idx(x, y, 0);
+        hz[k] = L::PP;
+      } else {
+        const int c0 = t > M / 2;
+        const int nl = plus ? 2 * l : M - 2 * l;
+        const int u0 = 2 * t - c0 * M;
+        const int x = ax == 0 ? nl : u0, y = ax == 0 ? u0 : nl;
+        hp[k] = a.in + (size_t)fs[F][c0] * L::BLK + (size_t)f * L::FS + L::idx(x, y, 0);
+        // upper child: its plane 2z - M is at 2z * PP - M * PP from its base
+        hd[k] = ((long long)fs[F][c0 + 2] - (long long)fs[F][c0]) * L::BLK - (long long)M * L::PP;
+        hz[k] = 2 * L::PP;
+      }
+    }
+  }
+  auto issue_halos = [&](int zz, T* B) {
+#pragma unroll
+    for (int k = 0; k < HPT; ++k) {
+      if (hdst[k] >= 0) {
+        const T* src = hp[k] + (zz > M / 2 ? hd[k] : 0ll) + (long long)zz * hz[k];
+        cp_async_elem(B + hdst[k], src);
+      }
     }
     cp_async_commit();
   };
@@ -174,7 +224,7 @@ k_stage(const StageK<T> a, const TopoK tp, const PhysK ph) {
     for (int f = 0; f < 4; ++f) q[f][k] = act ? plane_value(k - 3, f) : T(0);
 #pragma unroll
   for (int f = 0; f < 4; ++f) q[f][7] = T(0);
-  issue_halos(0, buf[0]);
+  issue_halos(0, &buf[0][0][0]);
 
   const int ci = (y + 3) * W + x + 3;
   for (int z = 0; z <= M; ++z) {
@@ -185,7 +235,7 @@ k_stage(const StageK<T> a, const TopoK tp, const PhysK ph) {
     }
     cp_async_wait_all();
     __syncthreads();
-    if (z < M) issue_halos(z + 1, buf[(z + 1) & 1]);
+    if (z < M) issue_halos(z + 1, &buf[(z + 1) & 1][0][0]);
     if (act) {
       if (z + 4 <= M + 3) {
 #pragma unroll
@@ -267,7 +317,7 @@ k_stage(const StageK<T> a, const TopoK tp, const PhysK ph) {
 template <typename T, int BS>
 void launch_stage_bs(int stage, const StageK<T>& s, const TopoK& t, const PhysK& p, cudaStream_t st) {
   if (t.n <= 0) return;
-  const dim3 grid((unsigned)t.n), block(Cfg<BS>::NT);
+  const dim3 grid((unsigned)t.n), block(Cfg<T, BS>::NT);
   switch (stage) {
     case 0: k_stage<T, BS, 0><<<grid, block, 0, st>>>(s, t, p); break;
     case 1: k_stage<T, BS, 1><<<grid, block, 0, st>>>(s, t, p); break;
