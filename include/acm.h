@@ -228,6 +228,9 @@ typedef struct {
   int64_t n_launches;     /* kernels launched by the step                                    */
   double host_topology_ms;/* cumulative host time rebuilding block tables since creation     */
   double host_tree_ms;    /* cumulative host time of refine/coarsen tree logic since creation */
+  double host_sort_ms;    /* part of host_topology_ms: ordering the blocks                     */
+  double host_rows_ms;    /* part of host_topology_ms: building the neighbourhood rows          */
+  double host_wait_ms;    /* part of host_topology_ms: waiting for the stream after the copies  */
 } acm_step_stats;
 acm_status acm_enable_timing(acm_forest* f, int on);
 acm_status acm_last_step_stats(acm_forest* f, acm_step_stats* out);

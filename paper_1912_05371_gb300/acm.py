@@ -41,7 +41,8 @@ class Diag(C.Structure):
 
 class StepStats(C.Structure):
     _fields_ = [("stage_ms", C.c_double), ("sync_ms", C.c_double), ("stage_bytes", C.c_double),
-                ("n_launches", C.c_int64), ("host_topology_ms", C.c_double), ("host_tree_ms", C.c_double)]
+                ("n_launches", C.c_int64), ("host_topology_ms", C.c_double), ("host_tree_ms", C.c_double),
+                ("host_sort_ms", C.c_double), ("host_rows_ms", C.c_double), ("host_wait_ms", C.c_double)]
 
 
 EXPORTS = {
@@ -284,7 +285,8 @@ class Forest:
         s = StepStats()
         self._check(self.L.acm_last_step_stats(self.h, C.byref(s)))
         return dict(stage_ms=s.stage_ms, sync_ms=s.sync_ms, stage_bytes=s.stage_bytes, n_launches=s.n_launches,
-                    host_topology_ms=s.host_topology_ms, host_tree_ms=s.host_tree_ms)
+                    host_topology_ms=s.host_topology_ms, host_tree_ms=s.host_tree_ms, host_sort_ms=s.host_sort_ms,
+                    host_rows_ms=s.host_rows_ms, host_wait_ms=s.host_wait_ms)
 
     def launch_count(self):
         return self.L.acm_launch_count(self.h)

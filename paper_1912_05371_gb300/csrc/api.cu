@@ -86,6 +86,7 @@ struct acm_forest {
   acm_step_stats stats{};
   bool stats_pending = false;
   double host_topology_ms = 0, host_tree_ms = 0;   // cumulative host time of the tree logic
+  double host_sort_ms = 0, host_rows_ms = 0, host_wait_ms = 0;   // parts of host_topology_ms
   cudaEvent_t ev[12] = {};          // per stage: before sync, after sync, after the stage kernel
 };
 
@@ -194,10 +195,13 @@ constexpr int kFaceBox[6] = {12, 14, 10, 16, 4, 22};
 // Rebuild the rank-indexed device metadata after any change of the grid: per block its 27
 // neighbour boxes (type, slots), then the fine-wins and coarse-face task lists.  Rows are built
 // in parallel into pinned host memory and copied in one go.
-acm_status upload_topology(acm_forest* f) {
+acm_status upload_topology(acm_forest* f, std::vector<BoxKey>* new_order = nullptr) {
   const double t0 = now_ms();
   const acm::Forest& fo = *f->fo;
-  f->order = fo.sorted();
+  if (new_order) f->order.swap(*new_order);
+  else f->order = fo.sorted();
+  const double t1 = now_ms();
+  f->host_sort_ms += t1 - t0;
   const int64_t n = (int64_t)f->order.size();
   f->blist.resize(n);
   int bad = 0, jtop = 0;
@@ -238,6 +242,8 @@ acm_status upload_topology(acm_forest* f) {
   }
   if (bad) return fail(f, ACM_EGRADING, "grid is not 2:1 graded");
   f->Jtop = jtop;
+  const double t2 = now_ms();
+  f->host_rows_ms += t2 - t1;
   int64_t nfw = 0, nsl = 0;
   for (int64_t r = 0; r < n; ++r) {
     const int32_t* row = f->h_nbh + r * acm::kNbhStride;
@@ -263,7 +269,9 @@ acm_status upload_topology(acm_forest* f) {
   if (nfw) CK(cudaMemcpyAsync(f->d_fw, f->h_fw, nfw * sizeof(int2), cudaMemcpyHostToDevice, f->st));
   if (nsl) CK(cudaMemcpyAsync(f->d_slabt, f->h_slabt, nsl * sizeof(int4), cudaMemcpyHostToDevice, f->st));
   // the pinned staging is reused by the next rebuild: complete the copies first
+  const double t3 = now_ms();
   CK(cudaStreamSynchronize(f->st));
+  f->host_wait_ms += now_ms() - t3;
   f->host_topology_ms += now_ms() - t0;
   return ACM_OK;
 }
@@ -436,8 +444,17 @@ acm_status refine_all(acm_forest* f) {
   kids.reserve(parents.size() * 8);
   for (size_t i = 0; i < parents.size(); ++i)
     for (int c = 0; c < 8; ++c) kids.push_back(acm::Forest::child(parents[i], c));
+  // block order of the refined grid: every parent replaced in place by its children 0..7
+  std::vector<BoxKey> order2;
+  order2.reserve(f->order.size() + 7 * parents.size());
+  for (const BoxKey& b : f->order) {
+    if (b.J < fo.Jmax)
+      for (int c = 0; c < 8; ++c) order2.push_back(acm::Forest::child(b, c));
+    else
+      order2.push_back(b);
+  }
   std::vector<int32_t> new_slot;
-  if (!fo.apply_pass(parents, kids, &new_slot)) return fail(f, ACM_ECAPACITY, "block pool exhausted");
+  if (!fo.apply_pass(parents, kids, &new_slot, true)) return fail(f, ACM_ECAPACITY, "block pool exhausted");
   std::vector<int4> tasks(kids.size());
   for (size_t i = 0; i < kids.size(); ++i) tasks[i] = make_int4(prank[i / 8], (int)(i % 8), new_slot[i], 0);
   f->host_tree_ms += now_ms() - t0;
@@ -447,7 +464,7 @@ acm_status refine_all(acm_forest* f) {
                         (int64_t)tasks.size(), f->d_blist, f->d_nbh, f->st);
   CKL();
   ++f->launches;
-  s = upload_topology(f);   // synchronises the stream (tasks buffer lifetime)
+  s = upload_topology(f, &order2);   // synchronises the stream (tasks buffer lifetime)
   if (s) return s;
   return eval_mask<T>(f, &new_slot);
 }
@@ -561,7 +578,19 @@ acm_status coarsen(acm_forest* f, int64_t* n_blocks, int* n_passes) {
         removed.push_back(f->order[gstart[g] + c]);
       }
     std::vector<int32_t> new_slot;
-    if (!fo.apply_pass(removed, groups, &new_slot)) return fail(f, ACM_ECAPACITY, "block pool exhausted");
+    if (!fo.apply_pass(removed, groups, &new_slot, true)) return fail(f, ACM_ECAPACITY, "block pool exhausted");
+    // block order of the merged grid: each group's 8 consecutive children replaced by the parent
+    std::vector<BoxKey> order2;
+    order2.reserve(n);
+    for (size_t r = 0, g = 0; r < n;) {
+      if (g < gstart.size() && r == gstart[g]) {
+        order2.push_back(groups[g]);
+        r += 8;
+        ++g;
+      } else {
+        order2.push_back(f->order[r++]);
+      }
+    }
     std::vector<int32_t> tasks(groups.size() * 9);
     for (size_t g = 0; g < groups.size(); ++g) {
       tasks[9 * g] = new_slot[g];
@@ -576,7 +605,7 @@ acm_status coarsen(acm_forest* f, int64_t* n_blocks, int* n_passes) {
                            (int64_t)groups.size(), f->st);
     CKL();
     ++f->launches;
-    s = upload_topology(f);
+    s = upload_topology(f, &order2);
     if (s) return s;
     s = eval_mask<T>(f, &new_slot);
     if (s) return s;
@@ -1021,6 +1050,9 @@ acm_status acm_last_step_stats(acm_forest* f, acm_step_stats* out) {
   }
   f->stats.host_topology_ms = f->host_topology_ms;
   f->stats.host_tree_ms = f->host_tree_ms;
+  f->stats.host_sort_ms = f->host_sort_ms;
+  f->stats.host_rows_ms = f->host_rows_ms;
+  f->stats.host_wait_ms = f->host_wait_ms;
   *out = f->stats;
   return ACM_OK;
 }

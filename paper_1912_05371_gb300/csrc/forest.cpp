@@ -85,8 +85,9 @@ Forest::Forest(const int nr[3], int bs, int jmin, int jmax, int64_t maxb)
 
 void Forest::clear() {
   leaves.clear();
-  free_.clear();
-  for (int64_t s = 0; s < max_blocks; ++s) free_.insert(free_.end(), (int32_t)s);
+  free_.assign((size_t)((max_blocks + 63) / 64), ~0ull);
+  if (max_blocks % 64) free_.back() = (1ull << (max_blocks % 64)) - 1;
+  nfree_ = max_blocks;
 }
 
 BoxKey Forest::wrap(int J, int64_t x, int64_t y, int64_t z) const {
@@ -99,18 +100,25 @@ BoxKey Forest::wrap(int J, int64_t x, int64_t y, int64_t z) const {
   return BoxKey{J, (int32_t)v[0], (int32_t)v[1], (int32_t)v[2]};
 }
 
+// Spread the low 21 bits of v to every third bit (bit i -> bit 3i).
+static inline uint64_t spread3(uint64_t v) {
+  v &= 0x1fffffull;
+  v = (v | v << 32) & 0x1f00000000ffffull;
+  v = (v | v << 16) & 0x1f0000ff0000ffull;
+  v = (v | v << 8) & 0x100f00f00f00f00full;
+  v = (v | v << 4) & 0x10c30c30c30c30c3ull;
+  v = (v | v << 2) & 0x1249249249249249ull;
+  return v;
+}
+
 uint64_t Forest::treecode(const BoxKey& k) const {
   const int J = k.J;
   const uint64_t rx = (uint64_t)k.x >> J, ry = (uint64_t)k.y >> J, rz = (uint64_t)k.z >> J;
   const uint64_t root = rx + (uint64_t)nroot[0] * (ry + (uint64_t)nroot[1] * rz);
-  uint64_t code = root << 56;
-  for (int l = 1; l <= J; ++l) {
-    const int sh = J - l;
-    const uint64_t digit = (((uint64_t)k.x >> sh) & 1) | ((((uint64_t)k.y >> sh) & 1) << 1) |
-                           ((((uint64_t)k.z >> sh) & 1) << 2);
-    code |= digit << (3 * (18 - l));
-  }
-  return code;
+  const uint64_t m = (1ull << J) - 1;
+  // digit of level l (bx + 2 by + 4 bz from bit J-l of the in-root coordinates) at bits 3(18-l)
+  const uint64_t il = spread3(k.x & m) | (spread3(k.y & m) << 1) | (spread3(k.z & m) << 2);
+  return (root << 56) | (J ? il << (3 * (18 - J)) : 0ull);
 }
 
 bool Forest::key_less(const BoxKey& a, const BoxKey& b) const {
@@ -132,23 +140,31 @@ std::vector<BoxKey> Forest::sorted() const {
 }
 
 bool Forest::apply_pass(const std::vector<BoxKey>& removed, const std::vector<BoxKey>& created,
-                        std::vector<int32_t>* created_slots) {
-  if ((int64_t)created.size() - (int64_t)removed.size() > (int64_t)free_.size()) return false;
+                        std::vector<int32_t>* created_slots, bool created_sorted) {
+  if ((int64_t)created.size() - (int64_t)removed.size() > nfree_) return false;
   for (const BoxKey& k : removed) {
     const int32_t s = leaves.get(k);
     if (s < 0) continue;
-    free_.insert(s);
+    free_[s >> 6] |= 1ull << (s & 63);
+    ++nfree_;
     leaves.erase(k);
   }
   std::vector<size_t> idx(created.size());
   for (size_t i = 0; i < idx.size(); ++i) idx[i] = i;
-  std::vector<std::pair<uint64_t, int>> keys(created.size());
-  for (size_t i = 0; i < created.size(); ++i) keys[i] = {treecode(created[i]), created[i].J};
-  std::sort(idx.begin(), idx.end(), [&](size_t a, size_t b) { return keys[a] < keys[b]; });
+  if (!created_sorted) {
+    std::vector<std::pair<uint64_t, int>> keys(created.size());
+    for (size_t i = 0; i < created.size(); ++i) keys[i] = {treecode(created[i]), created[i].J};
+    std::sort(idx.begin(), idx.end(), [&](size_t a, size_t b) { return keys[a] < keys[b]; });
+  }
   if (created_slots) created_slots->assign(created.size(), -1);
+  // ascending key order takes ascending free slots: one forward sweep over the bitmap
+  size_t w = 0;
   for (size_t i : idx) {
-    const int32_t s = *free_.begin();
-    free_.erase(free_.begin());
+    while (free_[w] == 0) ++w;
+    const int b = __builtin_ctzll(free_[w]);
+    free_[w] &= free_[w] - 1;
+    --nfree_;
+    const int32_t s = (int32_t)(w * 64 + b);
     leaves.put(created[i], s);
     if (created_slots) (*created_slots)[i] = s;
   }

@@ -107,14 +107,14 @@ class Forest {
   uint64_t treecode(const BoxKey& k) const;
   bool key_less(const BoxKey& a, const BoxKey& b) const;
   std::vector<BoxKey> sorted() const;
-  int64_t n_free() const { return (int64_t)free_.size(); }
+  int64_t n_free() const { return nfree_; }
 
   void clear();
   // One adaptation pass: release the slots of `removed`, then give `created` (any order)
   // the lowest free slots in ascending key order.  Returns false (and changes nothing) if
   // the pool is too small.  created_slots[i] is the slot of created[i].
   bool apply_pass(const std::vector<BoxKey>& removed, const std::vector<BoxKey>& created,
-                  std::vector<int32_t>* created_slots);
+                  std::vector<int32_t>* created_slots, bool created_sorted = false);
 
   BoxStatus box_status(int J, int64_t x, int64_t y, int64_t z) const;
   bool is_graded() const;
@@ -129,7 +129,8 @@ class Forest {
   void neighbour_table(const std::vector<BoxKey>& order, int32_t* nbr, int8_t* rel) const;
 
  private:
-  std::set<int32_t> free_;
+  std::vector<uint64_t> free_;    // bit set = slot free
+  int64_t nfree_ = 0;
 };
 
 }  // namespace acm
