@@ -238,6 +238,35 @@ acm_status acm_last_step_stats(acm_forest* f, acm_step_stats* out);
 /* Total kernel launches since creation (every launch of this library). */
 int64_t acm_launch_count(const acm_forest* f);
 
+/* Largest block count acm_max_norms_noalloc accepts (its scratch holds 5 doubles per block,
+ * 640 KiB, resident on every device that loads the library until the process exits). */
+#define ACM_NOALLOC_MAX_BLOCKS 16384
+
+/* Max norms of a field array without any device allocation.  (The paper has no counterpart:
+ * this serves callers of the library, not the method.)
+ *
+ * Some callers cannot allocate device memory at the point of the call: a process whose device
+ * memory is owned and budgeted by another allocator (a framework's caching pool), a time-critical
+ * host loop that must not trigger the device-wide synchronisation cudaMalloc/cudaFree can imply,
+ * or a caller that holds only a field array and no forest (whose pool would otherwise provide the
+ * scratch).  This call needs nothing from them but the input and the output.
+ *
+ * fields: device array in block order as written by acm_read_fields (n_blocks x 4 components
+ * x Bs^3, x fastest), float for precision 32, double for 64.  norms_out: device array of 5
+ * doubles receiving max|u|, max|v|, max|w|, max|p| and max |(u,v,w)| (arithmetic in the field
+ * precision, as inside acm_diagnostics).  stream: cudaStream_t (NULL = legacy default stream);
+ * the call is asynchronous on it.
+ * Returns ACM_EINVAL for bad arguments (Bs other than 9 or 17, precision other than 32 or 64,
+ * NULL pointers, n_blocks < 1), ACM_ECAPACITY if n_blocks > ACM_NOALLOC_MAX_BLOCKS (nothing is
+ * launched), ACM_ECUDA if a launch or the set-up fails.
+ * Scratch: a fixed array compiled into the library (per-block partial maxima).  The first call
+ * on each device looks up that array's device address (with the device current); make that
+ * first call before any stream capture.  Every call shares the one array and writes the entries
+ * it reads, so nothing needs clearing; calls that overlap on the GPU (different streams, or
+ * different host threads on one device) race on it and must be serialised by the caller. */
+acm_status acm_max_norms_noalloc(const void* fields, int64_t n_blocks, int Bs, int precision,
+                                 double* norms_out, void* stream);
+
 const char* acm_last_error(const acm_forest* f);
 const char* acm_status_string(acm_status s);
 

@@ -73,6 +73,7 @@ EXPORTS = {
     "acm_launch_count": (C.c_int64, [C.c_void_p]),
     "acm_last_error": (C.c_char_p, [C.c_void_p]),
     "acm_status_string": (C.c_char_p, [C.c_int]),
+    "acm_max_norms_noalloc": (C.c_int, [C.c_void_p, C.c_int64, C.c_int, C.c_int, C.c_void_p, C.c_void_p]),
 }
 
 _lib = None
@@ -103,6 +104,18 @@ def _ptr(a):
     if hasattr(a, "data_ptr"):
         return C.c_void_p(a.data_ptr())
     return a.ctypes.data_as(C.c_void_p)
+
+
+NOALLOC_MAX_BLOCKS = 16384
+
+
+def max_norms_noalloc(fields, n_blocks, Bs, precision, norms_out, stream=None):
+    """Max norms of a device field array through the allocation-free entry point
+    (acm_max_norms_noalloc): ``fields`` and ``norms_out`` are CUDA tensors (the latter 5
+    doubles); returns the status code (0 on success)."""
+    st = 0 if stream is None else stream.cuda_stream
+    return lib().acm_max_norms_noalloc(C.c_void_p(fields.data_ptr()), int(n_blocks), int(Bs), int(precision),
+                                       C.c_void_p(norms_out.data_ptr()), C.c_void_p(st))
 
 
 class Forest:
