@@ -16,6 +16,24 @@ constexpr int kNT = 256;
 template <typename T>
 __device__ __forceinline__ T tabs(T v) { return v < T(0) ? -v : v; }
 
+// Gather n values v(i) into dst[i] with U independent loads in flight per thread.
+template <typename T, int U, typename F>
+__device__ __forceinline__ void gather(T* dst, int n, F&& val) {
+  for (int base = threadIdx.x; base < n; base += kNT * U) {
+    T v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int i = base + u * kNT;
+      v[u] = i < n ? val(i) : T(0);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int i = base + u * kNT;
+      if (i < n) dst[i] = v[u];
+    }
+  }
+}
+
 // ---- (1) fine wins: block boundary points held by a finer neighbour take its value -----------
 // task = (rank, box index d of a REFINED neighbour box).  Points of the block's boundary lying
 // in box d: coordinate 0 / M where d is -1 / +1, the whole range where d is 0.
@@ -89,14 +107,14 @@ __global__ void __launch_bounds__(kNT) k_coarse_slabs(const T* reg, T* slab, con
     else { *x = t0; *y = t1; *z = nl; }
   };
   const T w[4] = {T(-1) / T(16), T(9) / T(16), T(9) / T(16), T(-1) / T(16)};
-  for (int i = threadIdx.x; i < NN * NC * NC; i += kNT) {
+  gather<T, 4>(&P[0][0][0], NN * NC * NC, [&](int i) {
     const int a0 = i % NC, a1 = (i / NC) % NC, an = i / (NC * NC);
     int x, y, z;
     place(n0 + 2 * an, 2 * a0 - 2, 2 * a1 - 2, &x, &y, &z);
     T v;
     if (!direct_value<T, BS>(reg, nbh, x, y, z, f, &v)) v = T(__longlong_as_double(0x7ff8000000000000ll));
-    P[an][a1][a0] = v;
-  }
+    return v;
+  });
   __syncthreads();
   for (int i = threadIdx.x; i < NN * NC * BS; i += kNT) {
     const int t0 = i % BS, a1 = (i / BS) % NC, an = i / (BS * NC);
@@ -177,71 +195,95 @@ __global__ void __launch_bounds__(kNT) k_sync_ext(const T* reg, T* out, int g, c
 // ---- (4) block indicators: details (Sec. 3.1) and mask range ----------------------------------
 // The coarse samples are the block's even points, local coordinates -2..M+2 (those outside the
 // block are held directly by a neighbour leaf); they are predicted back to every interior point
-// with the tensor DD-4 scheme (z outer, then y, then x) and subtracted.
+// separably (x, then y, then z: the tensor DD-4 sum in that nesting) and subtracted.
 template <typename T, int BS>
 __global__ void __launch_bounds__(kNT) k_details(const T* reg, const T* chi, const int32_t* blist,
-                                                  const int32_t* ranks, const int32_t* nbh_all, const double* norms,
-                                                  double* ind, double* chirange) {
+                                                  const int32_t* ranks, const int32_t* nbh_all,
+                                                  const unsigned long long* norm_bits, double* ind,
+                                                  double* chirange) {
   using L = Lay<T, BS>;
   constexpr int M = L::M;
   constexpr int NC = M / 2 + 3;                 // coarse samples -1..M/2+1
+  constexpr int RA = (NC * NC * NC > NC * BS * BS) ? NC * NC * NC : NC * BS * BS;
   __shared__ int nbh[kNbhStride];
-  __shared__ T c[NC][NC][NC];
+  __shared__ __align__(16) T ra[RA];            // coarse samples c, later the y-pass py
+  __shared__ __align__(16) T rb[NC * NC * BS];  // x-pass px
+  T(&c)[NC][NC][NC] = *reinterpret_cast<T(*)[NC][NC][NC]>(ra);
+  T(&py)[NC][BS][BS] = *reinterpret_cast<T(*)[NC][BS][BS]>(ra);
+  T(&px)[NC][NC][BS] = *reinterpret_cast<T(*)[NC][NC][BS]>(rb);
   const int rank = ranks ? ranks[blockIdx.x] : (int)blockIdx.x;
   const int slot = blist[rank];
   for (int i = threadIdx.x; i < kNbhStride; i += kNT) nbh[i] = nbh_all[(size_t)rank * kNbhStride + i];
   const T w[4] = {T(-1) / T(16), T(9) / T(16), T(9) / T(16), T(-1) / T(16)};
-  const int off[4] = {-3, -1, 1, 3};
   double best = 0.0;
   for (int f = 0; f < 4; ++f) {
-    const double inv = norms[f] > 0.0 ? 1.0 / norms[f] : 0.0;
+    // global max norm of component f, as left by the max-norm reduction (non-negative double bits)
+    const double nf = __longlong_as_double((long long)norm_bits[f]);
+    const double inv = nf > 0.0 ? 1.0 / nf : 0.0;
     if (inv == 0.0) continue;
+    T dmax = T(0);      // max |detail| in the field precision; max(|d| inv) = max|d| inv exactly
     __syncthreads();
-    for (int i = threadIdx.x; i < NC * NC * NC; i += kNT) {
+    gather<T, 4>(ra, NC * NC * NC, [&](int i) {
       const int x = 2 * (i % NC) - 2, y = 2 * ((i / NC) % NC) - 2, z = 2 * (i / (NC * NC)) - 2;
       T v;
       if (x >= 0 && x <= M && y >= 0 && y <= M && z >= 0 && z <= M)
         v = reg[(size_t)slot * L::BLK + (size_t)f * L::FS + L::idx(x, y, z)];
       else if (!direct_value<T, BS>(reg, nbh, x, y, z, f, &v))
         v = T(__longlong_as_double(0x7ff8000000000000ll));
-      c[i / (NC * NC)][(i / NC) % NC][i % NC] = v;
+      return v;
+    });
+    __syncthreads();
+    for (int i = threadIdx.x; i < NC * NC * BS; i += kNT) {
+      const int x = i % BS, yc = (i / BS) % NC, zc = i / (BS * NC);
+      T acc = T(0);
+      if (x & 1) {
+        const int k0 = (x - 1) >> 1;            // coarse index of x - 3
+        for (int k = 0; k < 4; ++k) acc = acc + w[k] * c[zc][yc][k0 + k];
+      } else {
+        acc = acc + T(1) * c[zc][yc][(x + 2) >> 1];
+      }
+      px[zc][yc][x] = acc;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < NC * BS * BS; i += kNT) {
+      const int x = i % BS, y = (i / BS) % BS, zc = i / (BS * BS);
+      T acc = T(0);
+      if (y & 1) {
+        const int k0 = (y - 1) >> 1;
+        for (int k = 0; k < 4; ++k) acc = acc + w[k] * px[zc][k0 + k][x];
+      } else {
+        acc = acc + T(1) * px[zc][(y + 2) >> 1][x];
+      }
+      py[zc][y][x] = acc;
     }
     __syncthreads();
     for (int i = threadIdx.x; i < BS * BS * BS; i += kNT) {
       const int x = i % BS, y = (i / BS) % BS, z = i / (BS * BS);
       if (((x | y | z) & 1) == 0) continue;          // all-even points: detail is zero
-      const int nx = (x & 1) ? 4 : 1, ny = (y & 1) ? 4 : 1, nz = (z & 1) ? 4 : 1;
-      T accz = T(0);
-      for (int kz = 0; kz < nz; ++kz) {
-        const int zz = ((nz == 4 ? z + off[kz] : z) + 2) >> 1;
-        const T wz = nz == 4 ? w[kz] : T(1);
-        T accy = T(0);
-        for (int ky = 0; ky < ny; ++ky) {
-          const int yy = ((ny == 4 ? y + off[ky] : y) + 2) >> 1;
-          const T wy = ny == 4 ? w[ky] : T(1);
-          T accx = T(0);
-          for (int kx = 0; kx < nx; ++kx) {
-            const int xx = ((nx == 4 ? x + off[kx] : x) + 2) >> 1;
-            const T wx = nx == 4 ? w[kx] : T(1);
-            accx = accx + wx * c[zz][yy][xx];
-          }
-          accy = accy + wy * accx;
-        }
-        accz = accz + wz * accy;
+      T acc = T(0);
+      if (z & 1) {
+        const int k0 = (z - 1) >> 1;
+        for (int k = 0; k < 4; ++k) acc = acc + w[k] * py[k0 + k][y][x];
+      } else {
+        acc = acc + T(1) * py[(z + 2) >> 1][y][x];
       }
-      const T dv = reg[(size_t)slot * L::BLK + (size_t)f * L::FS + L::idx(x, y, z)] - accz;
-      const double r = (double)tabs(dv) * inv;
-      best = r > best ? r : best;
+      const T dv = tabs(reg[(size_t)slot * L::BLK + (size_t)f * L::FS + L::idx(x, y, z)] - acc);
+      dmax = dv > dmax ? dv : dmax;
     }
+    const double r = (double)dmax * inv;
+    best = r > best ? r : best;
   }
   double cmin = 1e300, cmax = -1e300;
   if (chi) {
+    T tmin = T(1e30), tmax = T(-1e30);
     for (int i = threadIdx.x; i < BS * BS * BS; i += kNT) {
       const int x = i % BS, y = (i / BS) % BS, z = i / (BS * BS);
-      const double cv = (double)chi[(size_t)slot * L::FS + L::idx(x, y, z)];
-      cmin = cv < cmin ? cv : cmin;
-      cmax = cv > cmax ? cv : cmax;
+      const T cv = chi[(size_t)slot * L::FS + L::idx(x, y, z)];
+      tmin = cv < tmin ? cv : tmin;
+      tmax = cv > tmax ? cv : tmax;
     }
+    cmin = (double)tmin;
+    cmax = (double)tmax;
   }
   __shared__ double red[3][kNT / 32];
   for (int o = 16; o > 0; o >>= 1) {
@@ -294,53 +336,61 @@ __global__ void __launch_bounds__(kNT) k_maxnorm(const T* reg, const int32_t* bl
 }
 
 // ---- (6) refinement: 8 children predicted from the synchronised parent (Sec. 3.5 step 1) -------
-// task = (parent rank in the old grid, child c, new child slot, -).  src is a copy of the state
-// taken before any child is written (children may reuse the parent's slot).  The parent samples
-// a child needs (parent-local -1..M/2+1 around the child's half) are gathered into shared
-// memory, ghosts with the finest-leaf / DD-4 rule, then predicted to the child's points.
+// One CTA per (parent, component); task = [parent rank in the old grid, new slots of children
+// 0..7].  src is
+// a copy of the state taken before any child is written (children may reuse the parent's slot).
+// Per component: the parent's samples over local [-1, M+1]^3 (its ghost layer with the
+// finest-leaf rule, else the DD-4 prediction from the even lattice [-4, M+4]) are gathered into
+// shared memory once; each child is then predicted separably (x, then y, then z).
+// Dynamic shared memory: pp (M+3)^3 + ev/qx + qy, in T.
 template <typename T, int BS>
-__global__ void __launch_bounds__(kNT) k_refine(const T* src, T* dst, const int4* tasks, const int32_t* blist,
-                                                 const int32_t* nbh_all) {
+struct RefSmem {
+  static constexpr int M = BS - 1;
+  static constexpr int NPP = M + 3;                 // parent samples per axis: -1..M+1
+  static constexpr int NEV = M / 2 + 5;             // even lattice per axis: -4..M+4
+  static constexpr int NP = M / 2 + 3;              // samples per axis one child uses
+  static constexpr int PP = NPP * NPP * NPP;
+  static constexpr int EQ = (NEV * NEV * NEV > NP * NP * BS) ? NEV * NEV * NEV : NP * NP * BS;
+  static constexpr int QY = NP * BS * BS;
+  static constexpr size_t bytes = (size_t)(PP + EQ + QY) * sizeof(T) + kNbhStride * sizeof(int);
+};
+
+template <typename T, int BS>
+__global__ void __launch_bounds__(kNT, 4) k_refine(const T* src, T* dst, const int32_t* tasks, const int32_t* blist,
+                                                    const int32_t* nbh_all) {
   using L = Lay<T, BS>;
-  constexpr int M = L::M;
-  constexpr int NP = M / 2 + 3;                 // parent samples per axis
-  constexpr int NEV = M / 4 + 5;                // even-lattice samples per axis around them
-  // two regions, each reused once its content is dead: R1 holds the parent samples pp, later
-  // the y-pass qy; R2 holds the even-lattice patch ev, later the x-pass qx
-  constexpr int R1 = (NP * NP * NP > NP * BS * BS) ? NP * NP * NP : NP * BS * BS;
-  constexpr int R2 = (NEV * NEV * NEV > NP * NP * BS) ? NEV * NEV * NEV : NP * NP * BS;
-  __shared__ int nbh[kNbhStride];
-  __shared__ __align__(16) T r1[R1];
-  __shared__ __align__(16) T r2[R2];
-  T(&pp)[NP][NP][NP] = *reinterpret_cast<T(*)[NP][NP][NP]>(r1);
-  T(&qy)[NP][BS][BS] = *reinterpret_cast<T(*)[NP][BS][BS]>(r1);
-  T(&ev)[NEV][NEV][NEV] = *reinterpret_cast<T(*)[NEV][NEV][NEV]>(r2);
-  T(&qx)[NP][NP][BS] = *reinterpret_cast<T(*)[NP][NP][BS]>(r2);
-  const int4 tk = tasks[blockIdx.x];
-  const int pslot = blist[tk.x];
-  for (int i = threadIdx.x; i < kNbhStride; i += kNT) nbh[i] = nbh_all[(size_t)tk.x * kNbhStride + i];
-  const int cb[3] = {tk.y & 1, (tk.y >> 1) & 1, (tk.y >> 2) & 1};
-  const int o[3] = {cb[0] * (M / 2) - 1, cb[1] * (M / 2) - 1, cb[2] * (M / 2) - 1};
-  const int e0[3] = {o[0] - 3, o[1] - 3, o[2] - 3};     // even: first even-lattice sample
+  using S = RefSmem<T, BS>;
+  constexpr int M = L::M, NPP = S::NPP, NEV = S::NEV, NP = S::NP;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* pp = reinterpret_cast<T*>(smem_raw);
+  T* eq = pp + S::PP;                           // even lattice ev, later the x-pass qx
+  T* qy = eq + S::EQ;
+  int* nbh = reinterpret_cast<int*>(qy + S::QY);
+  const int32_t* tk = tasks + (size_t)(blockIdx.x >> 2) * 9;
+  const int f = blockIdx.x & 3;
+  const int prank = tk[0];
+  const int pslot = blist[prank];
+  for (int i = threadIdx.x; i < kNbhStride; i += kNT) nbh[i] = nbh_all[(size_t)prank * kNbhStride + i];
   const T w[4] = {T(-1) / T(16), T(9) / T(16), T(9) / T(16), T(-1) / T(16)};
   const int off[4] = {-3, -1, 1, 3};
-  for (int f = 0; f < 4; ++f) {
+  auto PPI = [&](int x, int y, int z) { return ((z + 1) * NPP + (y + 1)) * NPP + (x + 1); };
+  {
     __syncthreads();
-    // even-lattice points around the samples: held directly by some leaf
-    for (int i = threadIdx.x; i < NEV * NEV * NEV; i += kNT) {
-      const int x = e0[0] + 2 * (i % NEV), y = e0[1] + 2 * ((i / NEV) % NEV), z = e0[2] + 2 * (i / (NEV * NEV));
+    // even-lattice points -4..M+4 (held directly by some leaf)
+    gather<T, 4>(eq, NEV * NEV * NEV, [&](int i) {
+      const int x = 2 * (i % NEV) - 4, y = 2 * ((i / NEV) % NEV) - 4, z = 2 * (i / (NEV * NEV)) - 4;
       T v;
       if (x >= 0 && x <= M && y >= 0 && y <= M && z >= 0 && z <= M)
         v = src[(size_t)pslot * L::BLK + (size_t)f * L::FS + L::idx(x, y, z)];
       else if (!direct_value<T, BS>(src, nbh, x, y, z, f, &v))
         v = T(__longlong_as_double(0x7ff8000000000000ll));
-      ev[i / (NEV * NEV)][(i / NEV) % NEV][i % NEV] = v;
-    }
+      return v;
+    });
     __syncthreads();
-    // parent samples: interior, else the finest leaf holding the point, else the DD-4
+    // parent samples: interior, else the finest leaf holding the point, else the tensor DD-4
     // prediction from the even lattice (z outer, then y, then x)
-    for (int i = threadIdx.x; i < NP * NP * NP; i += kNT) {
-      const int x = o[0] + i % NP, y = o[1] + (i / NP) % NP, z = o[2] + i / (NP * NP);
+    for (int i = threadIdx.x; i < S::PP; i += kNT) {
+      const int x = i % NPP - 1, y = (i / NPP) % NPP - 1, z = i / (NPP * NPP) - 1;
       T v;
       if (x >= 0 && x <= M && y >= 0 && y <= M && z >= 0 && z <= M) {
         v = src[(size_t)pslot * L::BLK + (size_t)f * L::FS + L::idx(x, y, z)];
@@ -350,14 +400,14 @@ __global__ void __launch_bounds__(kNT) k_refine(const T* src, T* dst, const int4
         for (int a = 0; a < 3; ++a) cnt[a] = (p[a] & 1) ? 4 : 1;
         T accz = T(0);
         for (int kz = 0; kz < cnt[2]; ++kz) {
-          const int zz = ((cnt[2] == 4 ? z + off[kz] : z) - e0[2]) >> 1;
+          const int zz = ((cnt[2] == 4 ? z + off[kz] : z) + 4) >> 1;
           T accy = T(0);
           for (int ky = 0; ky < cnt[1]; ++ky) {
-            const int yy = ((cnt[1] == 4 ? y + off[ky] : y) - e0[1]) >> 1;
+            const int yy = ((cnt[1] == 4 ? y + off[ky] : y) + 4) >> 1;
             T accx = T(0);
             for (int kx = 0; kx < cnt[0]; ++kx) {
-              const int xx = ((cnt[0] == 4 ? x + off[kx] : x) - e0[0]) >> 1;
-              accx = accx + (cnt[0] == 4 ? w[kx] : T(1)) * ev[zz][yy][xx];
+              const int xx = ((cnt[0] == 4 ? x + off[kx] : x) + 4) >> 1;
+              accx = accx + (cnt[0] == 4 ? w[kx] : T(1)) * eq[(zz * NEV + yy) * NEV + xx];
             }
             accy = accy + (cnt[1] == 4 ? w[ky] : T(1)) * accx;
           }
@@ -365,46 +415,51 @@ __global__ void __launch_bounds__(kNT) k_refine(const T* src, T* dst, const int4
         }
         v = accz;
       }
-      pp[i / (NP * NP)][(i / NP) % NP][i % NP] = v;
+      pp[i] = v;
     }
-    __syncthreads();
-    // separable prediction to the child's points: along x, then y, then z.  Each pass is the
-    // inner sum of the tensor formula, so the result equals sum_z w (sum_y w (sum_x w pp)).
-    const auto pos = [&](int a, int i) { return cb[a] * M + i; };   // parent-local fine index
-    for (int i = threadIdx.x; i < NP * NP * BS; i += kNT) {
-      const int ix = i % BS, yy = (i / BS) % NP, zz = i / (BS * NP);
-      const int px = pos(0, ix);
-      T acc = T(0);
-      if (px & 1) {
-        for (int k = 0; k < 4; ++k) acc = acc + w[k] * pp[zz][yy][(px + off[k]) / 2 - o[0]];
-      } else {
-        acc = acc + T(1) * pp[zz][yy][px / 2 - o[0]];
+    for (int c = 0; c < 8; ++c) {
+      const int cb[3] = {c & 1, (c >> 1) & 1, (c >> 2) & 1};
+      const int o[3] = {cb[0] * (M / 2) - 1, cb[1] * (M / 2) - 1, cb[2] * (M / 2) - 1};
+      T* qx = eq;
+      __syncthreads();
+      // along x: qx[zz][yy][ix], zz, yy over the child's samples o..o+NP-1
+      for (int i = threadIdx.x; i < NP * NP * BS; i += kNT) {
+        const int ix = i % BS, yy = (i / BS) % NP, zz = i / (BS * NP);
+        const int px = cb[0] * M + ix;             // parent-local fine index (twice the parent index)
+        const int y = o[1] + yy, z = o[2] + zz;
+        T acc = T(0);
+        if (px & 1) {
+          for (int k = 0; k < 4; ++k) acc = acc + w[k] * pp[PPI((px + off[k]) / 2, y, z)];
+        } else {
+          acc = acc + T(1) * pp[PPI(px / 2, y, z)];
+        }
+        qx[(zz * NP + yy) * BS + ix] = acc;
       }
-      qx[zz][yy][ix] = acc;
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < NP * BS * BS; i += kNT) {
-      const int ix = i % BS, iy = (i / BS) % BS, zz = i / (BS * BS);
-      const int py = pos(1, iy);
-      T acc = T(0);
-      if (py & 1) {
-        for (int k = 0; k < 4; ++k) acc = acc + w[k] * qx[zz][(py + off[k]) / 2 - o[1]][ix];
-      } else {
-        acc = acc + T(1) * qx[zz][py / 2 - o[1]][ix];
+      __syncthreads();
+      for (int i = threadIdx.x; i < NP * BS * BS; i += kNT) {
+        const int ix = i % BS, iy = (i / BS) % BS, zz = i / (BS * BS);
+        const int py = cb[1] * M + iy;
+        T acc = T(0);
+        if (py & 1) {
+          for (int k = 0; k < 4; ++k) acc = acc + w[k] * qx[(zz * NP + ((py + off[k]) / 2 - o[1])) * BS + ix];
+        } else {
+          acc = acc + T(1) * qx[(zz * NP + (py / 2 - o[1])) * BS + ix];
+        }
+        qy[(zz * BS + iy) * BS + ix] = acc;
       }
-      qy[zz][iy][ix] = acc;
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < BS * BS * BS; i += kNT) {
-      const int ix = i % BS, iy = (i / BS) % BS, iz = i / (BS * BS);
-      const int pz = pos(2, iz);
-      T acc = T(0);
-      if (pz & 1) {
-        for (int k = 0; k < 4; ++k) acc = acc + w[k] * qy[(pz + off[k]) / 2 - o[2]][iy][ix];
-      } else {
-        acc = acc + T(1) * qy[pz / 2 - o[2]][iy][ix];
+      __syncthreads();
+      T* out = dst + (size_t)tk[1 + c] * L::BLK + (size_t)f * L::FS;
+      for (int i = threadIdx.x; i < BS * BS * BS; i += kNT) {
+        const int ix = i % BS, iy = (i / BS) % BS, iz = i / (BS * BS);
+        const int pz = cb[2] * M + iz;
+        T acc = T(0);
+        if (pz & 1) {
+          for (int k = 0; k < 4; ++k) acc = acc + w[k] * qy[(((pz + off[k]) / 2 - o[2]) * BS + iy) * BS + ix];
+        } else {
+          acc = acc + T(1) * qy[((pz / 2 - o[2]) * BS + iy) * BS + ix];
+        }
+        out[L::idx(ix, iy, iz)] = acc;
       }
-      dst[(size_t)tk.z * L::BLK + (size_t)f * L::FS + L::idx(ix, iy, iz)] = acc;
     }
   }
 }
@@ -441,11 +496,18 @@ __global__ void __launch_bounds__(kNT) k_copy_blocks(const T* src, T* dst, const
 }
 
 // ---- (8) analytic initial conditions and masks, FP64 at integer-derived coordinates ------------
+__device__ __forceinline__ int lattice(const PhysK& ph, int4 bi, int a, int i, int M) {
+  const int g = a == 0 ? bi.y : (a == 1 ? bi.z : bi.w);
+  const int N = (ph.nroot[a] << bi.x) * M;
+  const int gi = g * M + i;                               // in [0, N]
+  return gi >= N ? gi - N : gi;                           // periodic seam x = L taken as 0
+}
+
 __device__ __forceinline__ double coord(const PhysK& ph, int4 bi, int a, int i, int M, double h) {
   const int g = a == 0 ? bi.y : (a == 1 ? bi.z : bi.w);
   const long long N = ((long long)ph.nroot[a] << bi.x) * M;
-  const long long gi = ((long long)g * M + i) % N;      // periodic seam x = L taken as 0
-  return (double)gi * h;
+  const long long gi = (long long)g * M + i;             // in [0, N]
+  return (double)(gi >= N ? gi - N : gi) * h;             // periodic seam x = L taken as 0
 }
 
 template <typename T, int BS>
@@ -523,10 +585,17 @@ __global__ void __launch_bounds__(kNT) k_mask(T* chi, const int32_t* blist, cons
     if (uniform >= 0) {
       c = T(uniform);
     } else if (m.kind == 1) {
-      const T X = T(coord(ph, bi, 0, ix, M, h)), Y = T(coord(ph, bi, 1, iy, M, h)), Z = T(coord(ph, bi, 2, iz, M, h));
+      // coordinates in the field precision: i h with i the wrapped lattice index (exact when h
+      // is dyadic, as for power-of-two root sides)
+      const T X = T(lattice(ph, bi, 0, ix, M)) * T(h), Y = T(lattice(ph, bi, 1, iy, M)) * T(h),
+              Z = T(lattice(ph, bi, 2, iz, M)) * T(h);
       const T dx = X - T(m.p[0]), dy = Y - T(m.p[1]), dz = Z - T(m.p[2]);
       const T d = sqrt(dx * dx + dy * dy + dz * dz) - T(m.p[3]);
-      c = T(0.5) * (T(1) - tanh(d / T(m.p[4])));
+      // beyond 10 delta (FP32) / 20 delta (FP64) tanh(d/delta) rounds to exactly +-1
+      const T cut = T(sizeof(T) == 4 ? 10.0 : 20.0) * T(m.p[4]);
+      if (d > cut) c = T(0);
+      else if (d < -cut) c = T(1);
+      else c = T(0.5) * (T(1) - tanh(d / T(m.p[4])));
     }
     chi[(size_t)slot * L::FS + L::idx(ix, iy, iz)] = c;
   }
@@ -633,21 +702,32 @@ void launch_sync_ext(int Bs, const T* reg, T* out, int g, const int32_t* list, i
 }
 template <typename T>
 void launch_details(int Bs, const T* reg, const T* chi, const int32_t* blist, const int32_t* ranks,
-                    const int32_t* nbh, int64_t n, const double* norms, double* ind, double* chirange,
-                    cudaStream_t st) {
+                    const int32_t* nbh, int64_t n, const unsigned long long* norm_bits, double* ind,
+                    double* chirange, cudaStream_t st) {
   if (n <= 0) return;
-  ACM_BS_DISPATCH(Bs, k_details, <<<grid1(n), kNT, 0, st>>>(reg, chi, blist, ranks, nbh, norms, ind, chirange));
+  ACM_BS_DISPATCH(Bs, k_details, <<<grid1(n), kNT, 0, st>>>(reg, chi, blist, ranks, nbh, norm_bits, ind, chirange));
 }
 template <typename T>
 void launch_maxnorm(int Bs, const T* reg, const int32_t* blist, int64_t n, unsigned long long* out, cudaStream_t st) {
   if (n <= 0) return;
   ACM_BS_DISPATCH(Bs, k_maxnorm, <<<grid1(n), kNT, 0, st>>>(reg, blist, out));
 }
+template <typename T, int BS>
+void launch_refine_bs(const T* src, T* dst, const int32_t* tasks, int64_t n, const int32_t* blist,
+                      const int32_t* nbh, cudaStream_t st) {
+  static bool attr = false;             // opt in to more than 48 KB of dynamic shared memory once
+  if (!attr) {
+    cudaFuncSetAttribute(k_refine<T, BS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RefSmem<T, BS>::bytes);
+    attr = true;
+  }
+  k_refine<T, BS><<<grid1(4 * n), kNT, RefSmem<T, BS>::bytes, st>>>(src, dst, tasks, blist, nbh);
+}
 template <typename T>
-void launch_refine(int Bs, const T* src, T* dst, const int4* tasks, int64_t n, const int32_t* blist,
+void launch_refine(int Bs, const T* src, T* dst, const int32_t* tasks, int64_t n, const int32_t* blist,
                    const int32_t* nbh, cudaStream_t st) {
   if (n <= 0) return;
-  ACM_BS_DISPATCH(Bs, k_refine, <<<grid1(n), kNT, 0, st>>>(src, dst, tasks, blist, nbh));
+  if (Bs == 17) launch_refine_bs<T, 17>(src, dst, tasks, n, blist, nbh, st);
+  else launch_refine_bs<T, 9>(src, dst, tasks, n, blist, nbh, st);
 }
 template <typename T>
 void launch_coarsen(int Bs, const T* src, T* dst, const int32_t* tasks, int64_t n, cudaStream_t st) {
@@ -693,9 +773,9 @@ void launch_scatter(int Bs, const T* dense, T* reg, const int32_t* blist, int64_
   template void launch_fine_wins<T>(int, T*, const int2*, int64_t, const int32_t*, const int32_t*, cudaStream_t);          \
   template void launch_coarse_slabs<T>(int, const T*, T*, const int4*, int64_t, const int32_t*, cudaStream_t); \
   template void launch_sync_ext<T>(int, const T*, T*, int, const int32_t*, int64_t, const int32_t*, int, cudaStream_t); \
-  template void launch_details<T>(int, const T*, const T*, const int32_t*, const int32_t*, const int32_t*, int64_t, const double*, double*, double*, cudaStream_t); \
+  template void launch_details<T>(int, const T*, const T*, const int32_t*, const int32_t*, const int32_t*, int64_t, const unsigned long long*, double*, double*, cudaStream_t); \
   template void launch_maxnorm<T>(int, const T*, const int32_t*, int64_t, unsigned long long*, cudaStream_t); \
-  template void launch_refine<T>(int, const T*, T*, const int4*, int64_t, const int32_t*, const int32_t*, cudaStream_t); \
+  template void launch_refine<T>(int, const T*, T*, const int32_t*, int64_t, const int32_t*, const int32_t*, cudaStream_t); \
   template void launch_coarsen<T>(int, const T*, T*, const int32_t*, int64_t, cudaStream_t);               \
   template void launch_copy_blocks<T>(int, const T*, T*, const int32_t*, int64_t, cudaStream_t);          \
   template void launch_ic<T>(int, T*, const int32_t*, const int32_t*, int64_t, const int4*, const PhysK&, const IcK&, cudaStream_t); \

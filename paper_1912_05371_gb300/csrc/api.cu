@@ -163,7 +163,7 @@ size_t carve(acm_forest* f, const acm_grid_params* g, char* base) {
   int32_t* slabidx = c.take<int32_t>(nb * 8 * 4);
   int2* fw = c.take<int2>(nb * 26 * 8);
   int4* slabt = c.take<int4>(nb * 6 * 16);
-  int4* reft = c.take<int4>(nb * 16);
+  int4* reft = c.take<int4>(nb * 16);   // refinement tasks: 9 int32 per parent fit in 16 B per block
   int32_t* crst = c.take<int32_t>(nb * 9 * 4);
   int32_t* ranks = c.take<int32_t>(nb * 4);
   double* norms = c.take<double>(16 * 8);
@@ -316,6 +316,17 @@ acm_status snapshot_state(acm_forest* f) {
   return ACM_OK;
 }
 
+// Enqueue the max-norm reduction into d_maxbits without waiting for it.
+template <typename T>
+acm_status max_norms_async(acm_forest* f) {
+  CK(cudaMemsetAsync(f->d_maxbits, 0, 8 * sizeof(unsigned long long), f->st));
+  acm::launch_maxnorm<T>(f->gp.Bs, reinterpret_cast<const T*>(f->U), f->d_blist, (int64_t)f->order.size(),
+                         f->d_maxbits, f->st);
+  CKL();
+  ++f->launches;
+  return ACM_OK;
+}
+
 template <typename T>
 acm_status max_norms(acm_forest* f, double out[5]) {
   CK(cudaMemsetAsync(f->d_maxbits, 0, 8 * sizeof(unsigned long long), f->st));
@@ -367,7 +378,6 @@ acm_status eval_mask(acm_forest* f, const std::vector<int32_t>* fresh = nullptr)
                       f->st);
   CKL();
   ++f->launches;
-  if (fresh) CK(cudaStreamSynchronize(f->st));
   return ACM_OK;
 }
 
@@ -455,13 +465,17 @@ acm_status refine_all(acm_forest* f) {
   }
   std::vector<int32_t> new_slot;
   if (!fo.apply_pass(parents, kids, &new_slot, true)) return fail(f, ACM_ECAPACITY, "block pool exhausted");
-  std::vector<int4> tasks(kids.size());
-  for (size_t i = 0; i < kids.size(); ++i) tasks[i] = make_int4(prank[i / 8], (int)(i % 8), new_slot[i], 0);
+  std::vector<int32_t> tasks(parents.size() * 9);
+  for (size_t i = 0; i < parents.size(); ++i) {
+    tasks[9 * i] = prank[i];
+    for (int c = 0; c < 8; ++c) tasks[9 * i + 1 + c] = new_slot[8 * i + c];
+  }
   f->host_tree_ms += now_ms() - t0;
-  CK(cudaMemcpyAsync(f->d_reft, tasks.data(), tasks.size() * sizeof(int4), cudaMemcpyHostToDevice, f->st));
+  CK(cudaMemcpyAsync(f->d_reft, tasks.data(), tasks.size() * sizeof(int32_t), cudaMemcpyHostToDevice, f->st));
   // old-grid tables are still on the device: the upload below is ordered after this kernel
-  acm::launch_refine<T>(f->gp.Bs, reinterpret_cast<const T*>(f->YA), reinterpret_cast<T*>(f->U), f->d_reft,
-                        (int64_t)tasks.size(), f->d_blist, f->d_nbh, f->st);
+  acm::launch_refine<T>(f->gp.Bs, reinterpret_cast<const T*>(f->YA), reinterpret_cast<T*>(f->U),
+                        reinterpret_cast<const int32_t*>(f->d_reft), (int64_t)parents.size(), f->d_blist, f->d_nbh,
+                        f->st);
   CKL();
   ++f->launches;
   s = upload_topology(f, &order2);   // synchronises the stream (tasks buffer lifetime)
@@ -470,12 +484,13 @@ acm_status refine_all(acm_forest* f) {
 }
 
 // Block indicators (details + mask range) of every block, or of the blocks whose slots are
-// in `only`; results land at their ranks in d_ind / d_chir.
+// in `only`, copied to ind/chr (host, by rank); the component norms are read on the device from
+// the last max-norm reduction.  One stream synchronisation.
 template <typename T>
-acm_status indicators(acm_forest* f, const double norms[4], const std::vector<int32_t>* only = nullptr) {
+acm_status indicators(acm_forest* f, std::vector<double>& ind, std::vector<double>& chr,
+                      const std::vector<int32_t>* only = nullptr) {
   acm_status s = fine_wins<T>(f, reinterpret_cast<T*>(f->U));
   if (s) return s;
-  CK(cudaMemcpyAsync(f->d_norms, norms, 4 * sizeof(double), cudaMemcpyHostToDevice, f->st));
   const int32_t* ranks = nullptr;
   int64_t n = (int64_t)f->order.size();
   std::vector<int32_t> rl;
@@ -489,9 +504,14 @@ acm_status indicators(acm_forest* f, const double norms[4], const std::vector<in
   }
   acm::launch_details<T>(f->gp.Bs, reinterpret_cast<const T*>(f->U),
                          f->mask_on ? reinterpret_cast<const T*>(f->CHI) : nullptr, f->d_blist, ranks, f->d_nbh, n,
-                         f->d_norms, f->d_ind, f->d_chir, f->st);
+                         f->d_maxbits, f->d_ind, f->d_chir, f->st);
   CKL();
   ++f->launches;
+  const size_t nb = f->order.size();
+  ind.resize(nb);
+  chr.resize(nb);
+  CK(cudaMemcpyAsync(ind.data(), f->d_ind, nb * 8, cudaMemcpyDeviceToHost, f->st));
+  CK(cudaMemcpyAsync(chr.data(), f->d_chir, nb * 8, cudaMemcpyDeviceToHost, f->st));
   CK(cudaStreamSynchronize(f->st));
   return ACM_OK;
 }
@@ -499,24 +519,20 @@ acm_status indicators(acm_forest* f, const double norms[4], const std::vector<in
 template <typename T>
 acm_status coarsen(acm_forest* f, int64_t* n_blocks, int* n_passes) {
   acm::Forest& fo = *f->fo;
-  double m[5];
-  acm_status s = max_norms<T>(f, m);
+  // component norms, taken once before the first pass, stay on the device (d_maxbits)
+  acm_status s = max_norms_async<T>(f);
   if (s) return s;
-  const double norms[4] = {m[0], m[1], m[2], m[3]};
   int passes = 0;
   // A merge leaves every other block's indicator unchanged: its even samples keep their values
   // (decimation preserves coincident points), so later passes evaluate the new parents only.
   std::vector<double>& ind_slot = f->ind_slot;
   std::vector<double>& chr_slot = f->chr_slot;
   std::vector<int32_t> fresh;
+  std::vector<double> ind, chr;
   for (int it = 0; it < 64; ++it) {
-    s = indicators<T>(f, norms, it == 0 ? nullptr : &fresh);
+    s = indicators<T>(f, ind, chr, it == 0 ? nullptr : &fresh);
     if (s) return s;
     const size_t n = f->order.size();
-    std::vector<double> ind(n), chr(n);
-    CK(cudaMemcpyAsync(ind.data(), f->d_ind, n * 8, cudaMemcpyDeviceToHost, f->st));
-    CK(cudaMemcpyAsync(chr.data(), f->d_chir, n * 8, cudaMemcpyDeviceToHost, f->st));
-    CK(cudaStreamSynchronize(f->st));
     if (it == 0) {
       for (size_t r = 0; r < n; ++r) {
         ind_slot[f->blist[r]] = ind[r];
@@ -917,16 +933,13 @@ acm_status acm_init_grid(acm_forest* f, int ic_kind, const double* params, int n
 acm_status acm_block_indicators(acm_forest* f, double* ind, double* chirange, int64_t n) {
   if (!f) return ACM_EINVAL;
   if (n < (int64_t)f->order.size()) return fail(f, ACM_EINVAL, "output arrays too small");
-  double m[5];
-  acm_status s = f->gp.precision == 64 ? max_norms<double>(f, m) : max_norms<float>(f, m);
+  acm_status s = f->gp.precision == 64 ? max_norms_async<double>(f) : max_norms_async<float>(f);
   if (s) return s;
-  const double norms[4] = {m[0], m[1], m[2], m[3]};
-  s = f->gp.precision == 64 ? indicators<double>(f, norms) : indicators<float>(f, norms);
+  std::vector<double> iv, cv;
+  s = f->gp.precision == 64 ? indicators<double>(f, iv, cv) : indicators<float>(f, iv, cv);
   if (s) return s;
-  const size_t nb = f->order.size();
-  if (ind) CK(cudaMemcpyAsync(ind, f->d_ind, nb * 8, cudaMemcpyDeviceToHost, f->st));
-  if (chirange) CK(cudaMemcpyAsync(chirange, f->d_chir, nb * 8, cudaMemcpyDeviceToHost, f->st));
-  CK(cudaStreamSynchronize(f->st));
+  if (ind) std::memcpy(ind, iv.data(), iv.size() * 8);
+  if (chirange) std::memcpy(chirange, cv.data(), cv.size() * 8);
   return ACM_OK;
 }
 

@@ -58,11 +58,12 @@ void launch_sync_ext(int Bs, const T* reg, T* out, int g, const int32_t* blist, 
                      const int32_t* nbh, int by_rank, cudaStream_t st);
 
 // Block indicators from the state itself (fine-wins applied): ind[rank], chirange[rank].
-// (ranks: the blocks to evaluate, nullptr = all n; results are written at their ranks)
+// (ranks: the blocks to evaluate, nullptr = all n; results are written at their ranks;
+// norm_bits: the 4 component max norms as left by launch_maxnorm, read on the device)
 template <typename T>
 void launch_details(int Bs, const T* reg, const T* chi, const int32_t* blist, const int32_t* ranks,
-                    const int32_t* nbh, int64_t n, const double* norms, double* ind, double* chirange,
-                    cudaStream_t st);
+                    const int32_t* nbh, int64_t n, const unsigned long long* norm_bits, double* ind,
+                    double* chirange, cudaStream_t st);
 
 // Max norms: out[0..3] = max |u|,|v|,|w|,|p|, out[4] = max |(u,v,w)|, as ordered bit patterns
 // (non-negative doubles) combined with atomicMax; out must be zeroed before.
@@ -70,9 +71,10 @@ template <typename T>
 void launch_maxnorm(int Bs, const T* reg, const int32_t* blist, int64_t n,
                     unsigned long long* out, cudaStream_t st);
 
-// Children from a copy `src` of the synchronised state, old-grid tables (blist, nbh).
+// Children from a copy `src` of the synchronised state, old-grid tables (blist, nbh);
+// one task per parent: [parent rank, new slots of children 0..7].
 template <typename T>
-void launch_refine(int Bs, const T* src, T* dst, const int4* tasks, int64_t ntasks,
+void launch_refine(int Bs, const T* src, T* dst, const int32_t* tasks, int64_t nparents,
                    const int32_t* blist, const int32_t* nbh, cudaStream_t st);
 
 template <typename T>

@@ -135,7 +135,8 @@ k_stage(const StageK<T> a, const TopoK tp, const PhysK ph) {
     const int ax = tid / BS, i = tid % BS;
     const int g = ax == 0 ? bi.y : (ax == 1 ? bi.z : bi.w);
     const long long N = ((long long)ph.nroot[ax] << bi.x) * M;
-    long long gi = ((long long)g * M + i) % N;
+    long long gi = (long long)g * M + i;        // in [0, N]; the seam x = L is taken as 0
+    if (gi >= N) gi -= N;
     const double c = (double)gi * h;
     const double dist = fmin(c, ph.sp_L[ax] - c);
     sp[ax][i] = T(0.5 * (1.0 - tanh((dist - ph.sp_width) / ph.sp_delta)));
