@@ -54,7 +54,8 @@ typedef enum {
  * h_J = root_len / (2^J (Bs-1)).  Bs must be 9 or 17.  g is the ghost depth reported by
  * acm_sync_ghosts (1..4).  precision is 32 or 64.  fd_scheme: 1 = Tam-Webb optimised first
  * derivative (Sec. 2.3, the paper's choice), 0 = classical (8,-1)/12.  Levels obey
- * 0 <= Jmin <= Jmax <= 18 (Sec. 3.5). */
+ * 0 <= Jmin <= Jmax <= 18 (Sec. 3.5).  max_blocks (the block pool) is at most
+ * 2^32 / (72 Bs^2) blocks (206,000 at Bs = 17): device offsets into the pool are 32-bit. */
 typedef struct {
   int nroot[3];
   double root_len;

@@ -60,6 +60,8 @@ struct acm_forest {
   double* d_ind = nullptr;
   double* d_chir = nullptr;
   double* d_diag = nullptr;
+  int* d_err = nullptr;            // set by kernels whose bounded waits expired
+  int* h_err = nullptr;            // pinned copy, refreshed after every RK4 step
 
   // host mirrors of the current topology (pinned: built in place, then copied)
   std::vector<BoxKey> order;
@@ -113,6 +115,12 @@ acm_status fail(acm_forest* f, acm_status s, const std::string& msg) {
 
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
+// After a stream synchronisation: did a kernel's bounded wait expire?
+acm_status device_error(acm_forest* f) {
+  if (f->h_err && *f->h_err) return fail(f, ACM_ETIMEOUT, "a bounded wait inside a kernel expired");
+  return ACM_OK;
+}
+
 double now_ms() {
   return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
@@ -139,6 +147,11 @@ bool valid_grid(const acm_grid_params* g) {
   for (int a = 0; a < 3; ++a)
     if (g->nroot[a] < 1 || g->nroot[a] > 64) return false;
   if ((int64_t)g->nroot[0] * g->nroot[1] * g->nroot[2] > 255) return false;
+  // the stage kernel addresses the block pool and the coarse-face slab buffer with 32-bit
+  // element offsets
+  const acm::LayoutInfo L = acm::layout_info(g->precision, g->Bs);
+  const int64_t slab_per_block = 6 * 4 * 3 * (int64_t)g->Bs * g->Bs;
+  if (g->max_blocks * std::max<int64_t>(L.BLK, slab_per_block) >= ((int64_t)1 << 32)) return false;
   return true;
 }
 
@@ -171,11 +184,13 @@ size_t carve(acm_forest* f, const acm_grid_params* g, char* base) {
   double* ind = c.take<double>(nb * 8);
   double* chir = c.take<double>(nb * 8);
   double* diag = c.take<double>(nb * 4 * 8);
+  int* errf = c.take<int>(16);
   if (f) {
     f->U = U; f->ACC = ACC; f->YA = YA; f->YB = YB; f->CHI = CHI; f->DENSE = DENSE; f->SLAB = SLAB;
     f->d_nbh = nbh; f->d_binfo = binfo; f->d_blist = blist; f->d_slabidx = slabidx;
     f->d_fw = fw; f->d_slabt = slabt; f->d_reft = reft; f->d_crst = crst; f->d_ranks = ranks;
     f->d_norms = norms; f->d_maxbits = maxbits; f->d_ind = ind; f->d_chir = chir; f->d_diag = diag;
+    f->d_err = errf;
   }
   return c.off;
 }
@@ -337,6 +352,7 @@ acm_status max_norms(acm_forest* f, double out[5]) {
   unsigned long long bits[5];
   CK(cudaMemcpyAsync(bits, f->d_maxbits, sizeof(bits), cudaMemcpyDeviceToHost, f->st));
   CK(cudaStreamSynchronize(f->st));
+  if (acm_status e = device_error(f)) return e;
   for (int k = 0; k < 5; ++k) {
     double v;
     std::memcpy(&v, &bits[k], 8);
@@ -413,11 +429,12 @@ acm_status rk4(acm_forest* f, double dt, double* dt_used) {
     a.slab = reinterpret_cast<const T*>(f->SLAB);
     a.c_acc = s == 1 ? dt / 6.0 : dt / 3.0;
     a.c_out = s == 1 || s == 2 ? dt / 2.0 : (s == 3 ? dt : dt / 6.0);
-    acm::launch_stage<T>(s, f->gp.Bs, a, t, f->phk, f->st);
+    acm::launch_stage<T>(s, f->gp.Bs, a, t, f->phk, f->d_err, f->st);
     CKL();
     ++f->launches;
     if (f->timing) CK(cudaEventRecord(f->ev[3 * (s - 1) + 2], f->st));
   }
+  CK(cudaMemcpyAsync(f->h_err, f->d_err, sizeof(int), cudaMemcpyDeviceToHost, f->st));
   f->time += dt;
   // algorithmic bytes of the four stage kernels: per point 64 words (registers Y, U, acc in and
   // out, see stage.cu) plus one word of mask per stage when a mask is set
@@ -513,7 +530,7 @@ acm_status indicators(acm_forest* f, std::vector<double>& ind, std::vector<doubl
   CK(cudaMemcpyAsync(ind.data(), f->d_ind, nb * 8, cudaMemcpyDeviceToHost, f->st));
   CK(cudaMemcpyAsync(chr.data(), f->d_chir, nb * 8, cudaMemcpyDeviceToHost, f->st));
   CK(cudaStreamSynchronize(f->st));
-  return ACM_OK;
+  return device_error(f);
 }
 
 template <typename T>
@@ -735,7 +752,7 @@ acm_status acm_create_forest(const acm_grid_params* grid, const acm_phys_params*
     acm_forest* f = fp;   // for CK
     const size_t nb = (size_t)grid->max_blocks;
     const size_t bytes = nb * acm::kNbhStride * 4 + nb * sizeof(int4) + nb * 4 + nb * 8 * 4 +
-                         nb * 27 * sizeof(int2) + nb * 6 * sizeof(int4) + 6 * 256;
+                         nb * 27 * sizeof(int2) + nb * 6 * sizeof(int4) + 8 * 256;
     CK(cudaMallocHost(&f->h_pinned, bytes));
     char* p = (char*)f->h_pinned;
     auto take = [&](size_t b) { char* q = p; p += (b + 255) & ~(size_t)255; return q; };
@@ -745,6 +762,9 @@ acm_status acm_create_forest(const acm_grid_params* grid, const acm_phys_params*
     f->h_slabidx = (int32_t*)take(nb * 8 * 4);
     f->h_fw = (int2*)take(nb * 27 * sizeof(int2));
     f->h_slabt = (int4*)take(nb * 6 * sizeof(int4));
+    f->h_err = (int*)take(16);
+    *f->h_err = 0;
+    CK(cudaMemset(f->d_err, 0, 16 * sizeof(int)));
     for (auto& e : f->ev) CK(cudaEventCreate(&e));
   }
   *out = f.release();
@@ -998,7 +1018,7 @@ static acm_status copy_fields(acm_forest* f, void* buf, int64_t n_elems, int on_
   ++f->launches;
   if (!to_pool && !on_device) CK(cudaMemcpyAsync(buf, dense, bytes, cudaMemcpyDeviceToHost, f->st));
   CK(cudaStreamSynchronize(f->st));
-  return ACM_OK;
+  return device_error(f);
 }
 
 acm_status acm_read_fields(acm_forest* f, int reg, void* out, int64_t n_elems, int on_device) {
@@ -1026,13 +1046,13 @@ acm_status acm_rhs(acm_forest* f, void* out, int64_t n_elems, int on_device) {
     if (s) return s;
     acm::StageK<double> a{(const double*)f->U, (const double*)f->U, (double*)f->ACC, (double*)f->YA,
                           f->mask_on ? (const double*)f->CHI : nullptr, (const double*)f->SLAB, 0.0, 0.0};
-    acm::launch_stage<double>(0, f->gp.Bs, a, t, f->phk, f->st);
+    acm::launch_stage<double>(0, f->gp.Bs, a, t, f->phk, f->d_err, f->st);
   } else {
     acm_status s = sync_stage<float>(f, (float*)f->U);
     if (s) return s;
     acm::StageK<float> a{(const float*)f->U, (const float*)f->U, (float*)f->ACC, (float*)f->YA,
                          f->mask_on ? (const float*)f->CHI : nullptr, (const float*)f->SLAB, 0.0, 0.0};
-    acm::launch_stage<float>(0, f->gp.Bs, a, t, f->phk, f->st);
+    acm::launch_stage<float>(0, f->gp.Bs, a, t, f->phk, f->d_err, f->st);
   }
   CKL();
   ++f->launches;

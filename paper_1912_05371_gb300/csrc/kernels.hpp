@@ -26,6 +26,16 @@ struct TopoK {
   int64_t n;
 };
 
+// Model and RK constants of one stage in the field precision (kernel parameters, so the
+// stage kernel reads them from the constant bank).
+template <typename T>
+struct StageConst {
+  T a1, a2, a3;             // first-derivative coefficients
+  T nu, c0sq, cgam, inv_ceta, inv_csp;
+  T uinf[3], pinf;
+  T c_acc, c_out;           // RK coefficients of the stage
+};
+
 // Stage of the fused RK4 update (Sec. 2.3).  in: the stage state (synchronised); U: the
 // state at t^n; acc: the RK accumulator; out: next stage state (or U^{n+1} in stage 4).
 template <typename T>
@@ -37,10 +47,12 @@ struct StageK {
   const T* chi;
   const T* slab;
   double c_acc, c_out;      // stage coefficients (see stage.cu)
+  StageConst<T> kc;         // the constants above in the field precision (filled by launch_stage)
 };
 
+// err: device int set to 1 if a bounded wait inside the kernel expired (never cleared here).
 template <typename T>
-void launch_stage(int stage, int Bs, const StageK<T>& s, const TopoK& t, const PhysK& p,
+void launch_stage(int stage, int Bs, const StageK<T>& s, const TopoK& t, const PhysK& p, int* err,
                   cudaStream_t st);
 
 template <typename T>

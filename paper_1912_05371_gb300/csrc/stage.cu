@@ -36,6 +36,7 @@ struct Cfg {
   static constexpr int PW = H * W;
   static constexpr int NH = 48 * BS;     // x/y halo values per plane: 4 comp x 4 faces x 3 x BS
   static constexpr int HPT = (NH + NT - 1) / NT;   // halo values per thread
+  static_assert(4 * PW < 0x8000, "plane buffer offsets must fit 15 bits");
 };
 
 
@@ -88,8 +89,8 @@ __device__ __forceinline__ const T* halo_ptr(const int (&ftype)[6], const int (&
 }
 
 template <typename T, int BS, int STAGE>
-__global__ void __launch_bounds__(Cfg<T, BS>::NT, sizeof(T) == 4 ? 2 : 1)
-k_stage(const StageK<T> a, const TopoK tp, const PhysK ph) {
+__global__ void __launch_bounds__(Cfg<T, BS>::NT, sizeof(T) == 4 ? 3 : 1)
+k_stage(const StageK<T> a, const TopoK tp, const PhysK ph, int* err) {
   using L = Lay<T, BS>;
   constexpr int M = L::M;
   constexpr int NT = Cfg<T, BS>::NT;
@@ -101,6 +102,9 @@ k_stage(const StageK<T> a, const TopoK tp, const PhysK ph) {
   __shared__ int ftype[6];
   __shared__ int fs[6][4];
   __shared__ T sp[3][BS];
+  // x/y halo values of every plane as affine functions of z (see below)
+  constexpr int NH = Cfg<T, BS>::NH;
+  __shared__ unsigned hlo[NH], hhi[NH], hzd[NH];
 
   const int tid = threadIdx.x;
   const int slot = tp.blist[blockIdx.x];
@@ -144,13 +148,11 @@ k_stage(const StageK<T> a, const TopoK tp, const PhysK ph) {
   __syncthreads();
 
   const T ih = T(1.0 / h), ih2 = T(1.0 / (12.0 * h * h));
-  const T a1 = T(ph.a1), a2 = T(ph.a2), a3 = T(ph.a3);
-  const T nu = T(ph.nu), c0sq = T(ph.c0sq), cgam = T(ph.cgamma);
-  const T inv_ceta = T(ph.inv_ceta), inv_csp = T(ph.inv_csp);
-  const T uinf0 = T(ph.uinf[0]), uinf1 = T(ph.uinf[1]), uinf2 = T(ph.uinf[2]), pinf = T(ph.pinf);
-  const T c_acc = T(a.c_acc), c_out = T(a.c_out);
+  // model and RK constants are read from the kernel parameters (constant bank), not registers
+  const StageConst<T>& kc = a.kc;
   const bool act = tid < BS * BS;
   const int x = act ? tid % BS : 0, y = act ? tid / BS : 0;
+  (void)err;   // this kernel has no waits that can expire
   const T* __restrict__ inb = a.in + (size_t)slot * L::BLK;
   const size_t bo = (size_t)slot * L::BLK;
 
@@ -160,59 +162,60 @@ k_stage(const StageK<T> a, const TopoK tp, const PhysK ph) {
     return *halo_ptr<T, BS>(ftype, fs, a.in, a.slab, 5, zz - M, x, y, f);
   };
   // this thread's x/y halo values of every plane, as affine functions of z: element
-  // (component f, face F, layer l, tangential t) of plane z is read from hp + z * hz, plus hd
-  // for z > M/2 (the upper child of a finer face); destination hdst in the plane buffer
-  const T* hp[HPT];
-  long long hd[HPT];
-  int hz[HPT], hdst[HPT];
+  // (component f, face F, layer l, tangential t) of plane z is read at offset
+  // (z <= M/2 ? lo : hi) + z * hz from the state (or from the slab buffer, flag bit 15) and
+  // lands at dst of the plane buffer: hzd = hz << 16 | slab << 15 | dst.  The offsets are
+  // element indices (32-bit: pool and slab sizes are checked at forest creation); hi differs
+  // from lo for the upper child of a finer face.  Thread tid owns entries tid + k NT.
 #pragma unroll
   for (int k = 0; k < HPT; ++k) {
     const int i = tid + k * NT;
-    hp[k] = nullptr;
-    hd[k] = 0;
-    hz[k] = 0;
-    hdst[k] = -1;
-    if (i < 48 * BS) {
-      const int t = i % BS;
-      int r = i / BS;
-      const int l = r % 3 + 1;
-      r /= 3;
-      const int F = r & 3, f = r >> 2;
+    if (i < NH) {
+      const int g = i / (3 * BS), el = i % (3 * BS);
+      const int F = g & 3, f = g >> 2;
+      int l, t;
+      // x-faces take the 3 layers of a row as consecutive elements (one sector), y-faces a row
+      if (F < 2) { l = el % 3 + 1; t = el / 3; }
+      else { t = el % BS; l = el / BS + 1; }
       int hx, hy;
       if (F == 0) { hx = -l; hy = t; }
       else if (F == 1) { hx = M + l; hy = t; }
       else if (F == 2) { hx = t; hy = -l; }
       else { hx = t; hy = M + l; }
-      hdst[k] = f * PW + (hy + 3) * W + hx + 3;
+      const unsigned dst = (unsigned)(f * PW + (hy + 3) * W + hx + 3);
       const int ty = ftype[F];
       const bool plus = F & 1;
       const int ax = F >> 1;
       if (ty == kTypeCoarser) {
-        hp[k] = a.slab + (((size_t)fs[F][0] * 4 + f) * 3 + (l - 1)) * BS * BS + t;
-        hz[k] = BS;
+        const unsigned o = (unsigned)((((size_t)fs[F][0] * 4 + f) * 3 + (l - 1)) * BS * BS + t);
+        hlo[i] = o; hhi[i] = o; hzd[i] = ((unsigned)BS << 16) | 0x8000u | dst;
       } else if (ty == kTypeLeaf) {
         const int nl = plus ? l : M - l;
-        const int x = ax == 0 ? nl : t, y = ax == 0 ? t : nl;
-        hp[k] = a.in + (size_t)fs[F][0] * L::BLK + (size_t)f * L::FS + L::idx(x, y, 0);
-        hz[k] = L::PP;
+        const int xx = ax == 0 ? nl : t, yy = ax == 0 ? t : nl;
+        const unsigned o = (unsigned)((size_t)fs[F][0] * L::BLK + (size_t)f * L::FS + L::idx(xx, yy, 0));
+        hlo[i] = o; hhi[i] = o; hzd[i] = ((unsigned)L::PP << 16) | dst;
       } else {
         const int c0 = t > M / 2;
         const int nl = plus ? 2 * l : M - 2 * l;
         const int u0 = 2 * t - c0 * M;
-        const int x = ax == 0 ? nl : u0, y = ax == 0 ? u0 : nl;
-        hp[k] = a.in + (size_t)fs[F][c0] * L::BLK + (size_t)f * L::FS + L::idx(x, y, 0);
-        // upper child: its plane 2z - M is at 2z * PP - M * PP from its base
-        hd[k] = ((long long)fs[F][c0 + 2] - (long long)fs[F][c0]) * L::BLK - (long long)M * L::PP;
-        hz[k] = 2 * L::PP;
+        const int xx = ax == 0 ? nl : u0, yy = ax == 0 ? u0 : nl;
+        const unsigned lo = (unsigned)((size_t)fs[F][c0] * L::BLK + (size_t)f * L::FS + L::idx(xx, yy, 0));
+        // upper child: its plane 2z - M sits at 2z * PP - M * PP from its base (the sum with
+        // z * hz is taken modulo 2^32 and is non-negative)
+        const unsigned hi = (unsigned)((size_t)fs[F][c0 + 2] * L::BLK + (size_t)f * L::FS + L::idx(xx, yy, 0)) -
+                            (unsigned)(M * L::PP);
+        hlo[i] = lo; hhi[i] = hi; hzd[i] = ((unsigned)(2 * L::PP) << 16) | dst;
       }
     }
   }
   auto issue_halos = [&](int zz, T* B) {
 #pragma unroll
     for (int k = 0; k < HPT; ++k) {
-      if (hdst[k] >= 0) {
-        const T* src = hp[k] + (zz > M / 2 ? hd[k] : 0ll) + (long long)zz * hz[k];
-        cp_async_elem(B + hdst[k], src);
+      const int i = tid + k * NT;
+      if (i < NH) {
+        const unsigned zd = hzd[i];
+        const unsigned off = (zz > M / 2 ? hhi[i] : hlo[i]) + (unsigned)zz * (zd >> 16);
+        cp_async_elem(B + (zd & 0x7fffu), ((zd & 0x8000u) ? a.slab : a.in) + (size_t)off);
       }
     }
     cp_async_commit();
@@ -263,9 +266,9 @@ k_stage(const StageK<T> a, const TopoK tp, const PhysK ph) {
         const T xp3 = s[ci + 3], xm3 = s[ci - 3];
         const T yp1 = s[ci + W], ym1 = s[ci - W], yp2 = s[ci + 2 * W], ym2 = s[ci - 2 * W];
         const T yp3 = s[ci + 3 * W], ym3 = s[ci - 3 * W];
-        dx[f] = (a1 * (xp1 - xm1) + a2 * (xp2 - xm2) + a3 * (xp3 - xm3)) * ih;
-        dy[f] = (a1 * (yp1 - ym1) + a2 * (yp2 - ym2) + a3 * (yp3 - ym3)) * ih;
-        dz[f] = (a1 * (q[f][4] - q[f][2]) + a2 * (q[f][5] - q[f][1]) + a3 * (q[f][6] - q[f][0])) * ih;
+        dx[f] = (kc.a1 * (xp1 - xm1) + kc.a2 * (xp2 - xm2) + kc.a3 * (xp3 - xm3)) * ih;
+        dy[f] = (kc.a1 * (yp1 - ym1) + kc.a2 * (yp2 - ym2) + kc.a3 * (yp3 - ym3)) * ih;
+        dz[f] = (kc.a1 * (q[f][4] - q[f][2]) + kc.a2 * (q[f][5] - q[f][1]) + kc.a3 * (q[f][6] - q[f][0])) * ih;
         if (f < 3) {
           const T lx = T(16) * (xp1 + xm1) - (xp2 + xm2) - T(30) * c;
           const T ly = T(16) * (yp1 + ym1) - (yp2 + ym2) - T(30) * c;
@@ -275,22 +278,22 @@ k_stage(const StageK<T> a, const TopoK tp, const PhysK ph) {
       }
       const T u = q[0][3], v = q[1][3], w = q[2][3], p = q[3][3];
       T K[4];
-      K[0] = -(u * dx[0] + v * dy[0] + w * dz[0]) - dx[3] + nu * lap[0];
-      K[1] = -(u * dx[1] + v * dy[1] + w * dz[1]) - dy[3] + nu * lap[1];
-      K[2] = -(u * dx[2] + v * dy[2] + w * dz[2]) - dz[3] + nu * lap[2];
-      K[3] = -c0sq * (dx[0] + dy[1] + dz[2]) - cgam * p;
+      K[0] = -(u * dx[0] + v * dy[0] + w * dz[0]) - dx[3] + kc.nu * lap[0];
+      K[1] = -(u * dx[1] + v * dy[1] + w * dz[1]) - dy[3] + kc.nu * lap[1];
+      K[2] = -(u * dx[2] + v * dy[2] + w * dz[2]) - dz[3] + kc.nu * lap[2];
+      K[3] = -kc.c0sq * (dx[0] + dy[1] + dz[2]) - kc.cgam * p;
       if (ph.mask) {
-        const T cm = chiv * inv_ceta;
+        const T cm = chiv * kc.inv_ceta;
         K[0] -= cm * u;
         K[1] -= cm * v;
         K[2] -= cm * w;
       }
       if (ph.sponge) {
-        const T cs = tmax(tmax(sp[0][x], sp[1][y]), sp[2][z]) * inv_csp;
-        K[0] -= cs * (u - uinf0);
-        K[1] -= cs * (v - uinf1);
-        K[2] -= cs * (w - uinf2);
-        K[3] -= cs * (p - pinf);
+        const T cs = tmax(tmax(sp[0][x], sp[1][y]), sp[2][z]) * kc.inv_csp;
+        K[0] -= cs * (u - kc.uinf[0]);
+        K[1] -= cs * (v - kc.uinf[1]);
+        K[2] -= cs * (w - kc.uinf[2]);
+        K[3] -= cs * (p - kc.pinf);
       }
 #pragma unroll
       for (int f = 0; f < 4; ++f) {
@@ -298,13 +301,13 @@ k_stage(const StageK<T> a, const TopoK tp, const PhysK ph) {
         if (STAGE == 0) {
           a.acc[o] = K[f];
         } else if (STAGE == 1) {
-          a.acc[o] = q[f][3] + c_acc * K[f];
-          a.out[o] = q[f][3] + c_out * K[f];
+          a.acc[o] = q[f][3] + kc.c_acc * K[f];
+          a.out[o] = q[f][3] + kc.c_out * K[f];
         } else if (STAGE == 4) {
-          a.out[o] = Av[f] + c_out * K[f];
+          a.out[o] = Av[f] + kc.c_out * K[f];
         } else {
-          a.acc[o] = Av[f] + c_acc * K[f];
-          a.out[o] = Uv[f] + c_out * K[f];
+          a.acc[o] = Av[f] + kc.c_acc * K[f];
+          a.out[o] = Uv[f] + kc.c_out * K[f];
         }
       }
     }
@@ -316,28 +319,36 @@ k_stage(const StageK<T> a, const TopoK tp, const PhysK ph) {
 }
 
 template <typename T, int BS>
-void launch_stage_bs(int stage, const StageK<T>& s, const TopoK& t, const PhysK& p, cudaStream_t st) {
+void launch_stage_bs(int stage, const StageK<T>& s, const TopoK& t, const PhysK& p, int* err, cudaStream_t st) {
   if (t.n <= 0) return;
   const dim3 grid((unsigned)t.n), block(Cfg<T, BS>::NT);
   switch (stage) {
-    case 0: k_stage<T, BS, 0><<<grid, block, 0, st>>>(s, t, p); break;
-    case 1: k_stage<T, BS, 1><<<grid, block, 0, st>>>(s, t, p); break;
-    case 2: k_stage<T, BS, 2><<<grid, block, 0, st>>>(s, t, p); break;
-    case 3: k_stage<T, BS, 3><<<grid, block, 0, st>>>(s, t, p); break;
-    default: k_stage<T, BS, 4><<<grid, block, 0, st>>>(s, t, p); break;
+    case 0: k_stage<T, BS, 0><<<grid, block, 0, st>>>(s, t, p, err); break;
+    case 1: k_stage<T, BS, 1><<<grid, block, 0, st>>>(s, t, p, err); break;
+    case 2: k_stage<T, BS, 2><<<grid, block, 0, st>>>(s, t, p, err); break;
+    case 3: k_stage<T, BS, 3><<<grid, block, 0, st>>>(s, t, p, err); break;
+    default: k_stage<T, BS, 4><<<grid, block, 0, st>>>(s, t, p, err); break;
   }
 }
 
 }  // namespace
 
 template <typename T>
-void launch_stage(int stage, int Bs, const StageK<T>& s, const TopoK& t, const PhysK& p,
+void launch_stage(int stage, int Bs, const StageK<T>& s, const TopoK& t, const PhysK& p, int* err,
                   cudaStream_t st) {
-  if (Bs == 17) launch_stage_bs<T, 17>(stage, s, t, p, st);
-  else launch_stage_bs<T, 9>(stage, s, t, p, st);
+  StageK<T> a = s;
+  StageConst<T>& c = a.kc;
+  c.a1 = T(p.a1); c.a2 = T(p.a2); c.a3 = T(p.a3);
+  c.nu = T(p.nu); c.c0sq = T(p.c0sq); c.cgam = T(p.cgamma);
+  c.inv_ceta = T(p.inv_ceta); c.inv_csp = T(p.inv_csp);
+  for (int i = 0; i < 3; ++i) c.uinf[i] = T(p.uinf[i]);
+  c.pinf = T(p.pinf);
+  c.c_acc = T(s.c_acc); c.c_out = T(s.c_out);
+  if (Bs == 17) launch_stage_bs<T, 17>(stage, a, t, p, err, st);
+  else launch_stage_bs<T, 9>(stage, a, t, p, err, st);
 }
 
-template void launch_stage<float>(int, int, const StageK<float>&, const TopoK&, const PhysK&, cudaStream_t);
-template void launch_stage<double>(int, int, const StageK<double>&, const TopoK&, const PhysK&, cudaStream_t);
+template void launch_stage<float>(int, int, const StageK<float>&, const TopoK&, const PhysK&, int*, cudaStream_t);
+template void launch_stage<double>(int, int, const StageK<double>&, const TopoK&, const PhysK&, int*, cudaStream_t);
 
 }  // namespace acm
