@@ -83,20 +83,30 @@ __global__ void __launch_bounds__(kNT) k_fine_wins(T* reg, const int2* tasks, co
 // separably: along t0, then t1, then across the face (a fixed order per face orientation, so
 // every block that needs a halo point gets bitwise the same value).
 // Slab layout [slab][comp][layer l-1][t1][t0] with (t0, t1) as in the stage kernel.
+// One thread per halo column (t0, t1); each separable pass gives a thread one whole line.  The
+// direct values of the edge columns are looked up and loaded together with the coarse patch.
+template <int BS>
+struct SlabCfg {
+  static constexpr int NT = ((BS * BS + 31) / 32) * 32;
+};
+
 template <typename T, int BS>
-__global__ void __launch_bounds__(kNT) k_coarse_slabs(const T* reg, T* slab, const int4* tasks,
-                                                       const int32_t* nbh_all) {
+__global__ void __launch_bounds__(SlabCfg<BS>::NT) k_coarse_slabs(const T* reg, T* slab, const int4* tasks,
+                                                                   const int32_t* nbh_all) {
   using L = Lay<T, BS>;
   constexpr int M = L::M;
+  constexpr int NT = SlabCfg<BS>::NT;
   constexpr int NC = M / 2 + 3;                     // coarse samples along the face: -2..M+2 step 2
   constexpr int NN = 5;                             // coarse planes across the face
+  constexpr int NP3 = NN * NC * NC;
   __shared__ int nbh[kNbhStride];
   __shared__ T P[NN][NC][NC];                       // [n][t1 coarse][t0 coarse]
   __shared__ T A[NN][NC][BS];                       // predicted along t0
   __shared__ T B[NN][BS][BS];                       // predicted along t0 and t1
+  const int tid = threadIdx.x;
   const int4 tk = tasks[blockIdx.x >> 2];
   const int f = blockIdx.x & 3;
-  for (int i = threadIdx.x; i < kNbhStride; i += kNT) nbh[i] = nbh_all[(size_t)tk.x * kNbhStride + i];
+  for (int i = tid; i < kNbhStride; i += NT) nbh[i] = nbh_all[(size_t)tk.x * kNbhStride + i];
   __syncthreads();
   const int F = tk.y, ax = F >> 1;
   const bool plus = F & 1;
@@ -106,62 +116,82 @@ __global__ void __launch_bounds__(kNT) k_coarse_slabs(const T* reg, T* slab, con
     else if (ax == 1) { *x = t0; *y = nl; *z = t1; }
     else { *x = t0; *y = t1; *z = nl; }
   };
-  const T w[4] = {T(-1) / T(16), T(9) / T(16), T(9) / T(16), T(-1) / T(16)};
-  gather<T, 4>(&P[0][0][0], NN * NC * NC, [&](int i) {
-    const int a0 = i % NC, a1 = (i / NC) % NC, an = i / (NC * NC);
-    int x, y, z;
-    place(n0 + 2 * an, 2 * a0 - 2, 2 * a1 - 2, &x, &y, &z);
-    T v;
-    if (!direct_value<T, BS>(reg, nbh, x, y, z, f, &v)) v = T(__longlong_as_double(0x7ff8000000000000ll));
-    return v;
-  });
-  __syncthreads();
-  for (int i = threadIdx.x; i < NN * NC * BS; i += kNT) {
-    const int t0 = i % BS, a1 = (i / BS) % NC, an = i / (BS * NC);
-    T acc = T(0);
-    if (t0 & 1) {
-      const int c = (t0 - 3 + 2) >> 1;              // coarse index of t0 - 3
-      for (int k = 0; k < 4; ++k) acc = acc + w[k] * P[an][a1][c + k];
-    } else {
-      acc = P[an][a1][(t0 + 2) >> 1];
-    }
-    A[an][a1][t0] = acc;
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < NN * BS * BS; i += kNT) {
-    const int t0 = i % BS, t1 = (i / BS) % BS, an = i / (BS * BS);
-    T acc = T(0);
-    if (t1 & 1) {
-      const int c = (t1 - 3 + 2) >> 1;
-      for (int k = 0; k < 4; ++k) acc = acc + w[k] * A[an][c + k][t0];
-    } else {
-      acc = A[an][(t1 + 2) >> 1][t0];
-    }
-    B[an][t1][t0] = acc;
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < 3 * BS * BS; i += kNT) {
-    const int t0 = i % BS, t1 = (i / BS) % BS, l = i / (BS * BS) + 1;
-    const int nl = plus ? M + l : -l;
-    const bool edge = t0 == 0 || t0 == M || t1 == 0 || t1 == M;
-    T v;
-    bool have = false;
-    if (edge) {
+  const bool col = tid < BS * BS;
+  const int t0 = col ? tid % BS : 0, t1 = col ? tid / BS : 0;
+  const bool edge = col && (t0 == 0 || t0 == M || t1 == 0 || t1 == M);
+  long long eo[3] = {-1, -1, -1};
+  if (edge) {
+#pragma unroll
+    for (int l = 1; l <= 3; ++l) {
       int x, y, z;
-      place(nl, t0, t1, &x, &y, &z);
-      have = direct_value<T, BS>(reg, nbh, x, y, z, f, &v);
+      place(plus ? M + l : -l, t0, t1, &x, &y, &z);
+      eo[l - 1] = direct_offset<T, BS>(nbh, x, y, z, f);
     }
-    if (!have) {
-      const int c = nl - n0;                        // fine offset from the first coarse plane
-      if (c & 1) {
-        const int k0 = (c - 3) >> 1;
-        v = T(0);
-        for (int k = 0; k < 4; ++k) v = v + w[k] * B[k0 + k][t1][t0];
+  }
+  constexpr int U = (NP3 + NT - 1) / NT;
+  long long off[U];
+#pragma unroll
+  for (int k = 0; k < U; ++k) {
+    const int i = tid + k * NT;
+    off[k] = -2;
+    if (i < NP3) {
+      const int a0 = i % NC, a1 = (i / NC) % NC, an = i / (NC * NC);
+      int x, y, z;
+      place(n0 + 2 * an, 2 * a0 - 2, 2 * a1 - 2, &x, &y, &z);
+      off[k] = direct_offset<T, BS>(nbh, x, y, z, f);
+    }
+  }
+  T ev[3];
+#pragma unroll
+  for (int l = 0; l < 3; ++l) ev[l] = eo[l] >= 0 ? reg[eo[l]] : T(0);
+  T pv[U];
+#pragma unroll
+  for (int k = 0; k < U; ++k) pv[k] = off[k] >= 0 ? reg[off[k]] : T(__longlong_as_double(0x7ff8000000000000ll));
+#pragma unroll
+  for (int k = 0; k < U; ++k)
+    if (off[k] != -2) (&P[0][0][0])[tid + k * NT] = pv[k];
+  __syncthreads();
+  if (tid < NN * NC) {                              // along t0: line (a1, n)
+    const int a1 = tid % NC, an = tid / NC;
+    T cv[NC];
+#pragma unroll
+    for (int k = 0; k < NC; ++k) cv[k] = P[an][a1][k];
+#pragma unroll
+    for (int i = 0; i < BS; ++i) A[an][a1][i] = dd4_line<T, BS>(cv, i);
+  }
+  __syncthreads();
+  if (tid < NN * BS) {                              // along t1: line (t0, n)
+    const int l0 = tid % BS, an = tid / BS;
+    T cv[NC];
+#pragma unroll
+    for (int k = 0; k < NC; ++k) cv[k] = A[an][k][l0];
+#pragma unroll
+    for (int i = 0; i < BS; ++i) B[an][i][l0] = dd4_line<T, BS>(cv, i);
+  }
+  __syncthreads();
+  if (col) {                                        // across the face: column (t0, t1)
+    T cn[NN];
+#pragma unroll
+    for (int n = 0; n < NN; ++n) cn[n] = B[n][t1][t0];
+    const T w[4] = {T(-1) / T(16), T(9) / T(16), T(9) / T(16), T(-1) / T(16)};
+#pragma unroll
+    for (int l = 1; l <= 3; ++l) {
+      T v;
+      if (eo[l - 1] >= 0) {
+        v = ev[l - 1];
       } else {
-        v = B[c >> 1][t1][t0];
+        const int c = (plus ? M + l : -l) - n0;     // fine offset from the first coarse plane
+        if (c & 1) {
+          const int k0 = (c - 3) >> 1;
+          v = T(0);
+#pragma unroll
+          for (int k = 0; k < 4; ++k) v = v + w[k] * (k0 == 0 ? cn[k] : cn[k + 1]);
+        } else {
+          v = cn[c >> 1];
+        }
       }
+      slab[((((size_t)tk.z * 4 + f) * 3 + (l - 1)) * BS + t1) * BS + t0] = v;
     }
-    slab[((((size_t)tk.z * 4 + f) * 3 + (l - 1)) * BS + t1) * BS + t0] = v;
   }
 }
 
@@ -193,116 +223,149 @@ __global__ void __launch_bounds__(kNT) k_sync_ext(const T* reg, T* out, int g, c
 }
 
 // ---- (4) block indicators: details (Sec. 3.1) and mask range ----------------------------------
-// The coarse samples are the block's even points, local coordinates -2..M+2 (those outside the
-// block are held directly by a neighbour leaf); they are predicted back to every interior point
-// separably (x, then y, then z: the tensor DD-4 sum in that nesting) and subtracted.
+// One CTA per (block, component f = 0..3) and one per block (f = 4) for the mask range
+// max(chi) - min(chi).  The coarse samples are the block's even points, local coordinates
+// -2..M+2 (those outside the block are held directly by a neighbour leaf); they are predicted
+// back to every point separably (x, then y, then z: the tensor DD-4 sum in that nesting) and
+// subtracted.  In every pass a thread owns one whole line: it reads the line's coarse samples
+// once and produces its Bs values.  The block's own values, needed by the last pass, are loaded
+// at the start (one z-column per thread) and arrive while the passes run.  ind[rank] (zeroed by
+// the caller) receives the largest normalised detail over the components as an atomic maximum
+// on its bits: non-negative doubles order like their bit patterns.
+template <int BS>
+struct DetCfg {
+  static constexpr int NT = ((BS * BS + 31) / 32) * 32;
+  static constexpr int NC = (BS - 1) / 2 + 3;   // coarse samples per axis, -1..M/2+1
+};
+
 template <typename T, int BS>
-__global__ void __launch_bounds__(kNT) k_details(const T* reg, const T* chi, const int32_t* blist,
-                                                  const int32_t* ranks, const int32_t* nbh_all,
-                                                  const unsigned long long* norm_bits, double* ind,
-                                                  double* chirange) {
+__global__ void __launch_bounds__(DetCfg<BS>::NT) k_details(const T* reg, const T* chi, const int32_t* blist,
+                                                             const int32_t* ranks, const int32_t* nbh_all,
+                                                             const unsigned long long* norm_bits,
+                                                             unsigned long long* ind_bits, double* chirange) {
   using L = Lay<T, BS>;
   constexpr int M = L::M;
-  constexpr int NC = M / 2 + 3;                 // coarse samples -1..M/2+1
-  constexpr int RA = (NC * NC * NC > NC * BS * BS) ? NC * NC * NC : NC * BS * BS;
+  constexpr int NT = DetCfg<BS>::NT, NC = DetCfg<BS>::NC;
+  constexpr int NC3 = NC * NC * NC;
+  constexpr int RA = NC3 > NC * BS * BS ? NC3 : NC * BS * BS;
   __shared__ int nbh[kNbhStride];
-  __shared__ __align__(16) T ra[RA];            // coarse samples c, later the y-pass py
-  __shared__ __align__(16) T rb[NC * NC * BS];  // x-pass px
-  T(&c)[NC][NC][NC] = *reinterpret_cast<T(*)[NC][NC][NC]>(ra);
-  T(&py)[NC][BS][BS] = *reinterpret_cast<T(*)[NC][BS][BS]>(ra);
-  T(&px)[NC][NC][BS] = *reinterpret_cast<T(*)[NC][NC][BS]>(rb);
-  const int rank = ranks ? ranks[blockIdx.x] : (int)blockIdx.x;
+  __shared__ __align__(16) T ra[RA];            // coarse samples c[zc][yc][xc], later py[zc][y][x]
+  __shared__ __align__(16) T px[NC * NC * BS];  // x-pass px[zc][yc][x]
+  __shared__ T red[2][NT / 32];
+  const int tid = threadIdx.x;
+  const int item = blockIdx.x / 5, f = blockIdx.x - 5 * item;
+  const int rank = ranks ? ranks[item] : item;
   const int slot = blist[rank];
-  for (int i = threadIdx.x; i < kNbhStride; i += kNT) nbh[i] = nbh_all[(size_t)rank * kNbhStride + i];
-  const T w[4] = {T(-1) / T(16), T(9) / T(16), T(9) / T(16), T(-1) / T(16)};
-  double best = 0.0;
-  for (int f = 0; f < 4; ++f) {
-    // global max norm of component f, as left by the max-norm reduction (non-negative double bits)
-    const double nf = __longlong_as_double((long long)norm_bits[f]);
-    const double inv = nf > 0.0 ? 1.0 / nf : 0.0;
-    if (inv == 0.0) continue;
-    T dmax = T(0);      // max |detail| in the field precision; max(|d| inv) = max|d| inv exactly
-    __syncthreads();
-    gather<T, 4>(ra, NC * NC * NC, [&](int i) {
-      const int x = 2 * (i % NC) - 2, y = 2 * ((i / NC) % NC) - 2, z = 2 * (i / (NC * NC)) - 2;
-      T v;
-      if (x >= 0 && x <= M && y >= 0 && y <= M && z >= 0 && z <= M)
-        v = reg[(size_t)slot * L::BLK + (size_t)f * L::FS + L::idx(x, y, z)];
-      else if (!direct_value<T, BS>(reg, nbh, x, y, z, f, &v))
-        v = T(__longlong_as_double(0x7ff8000000000000ll));
-      return v;
-    });
-    __syncthreads();
-    for (int i = threadIdx.x; i < NC * NC * BS; i += kNT) {
-      const int x = i % BS, yc = (i / BS) % NC, zc = i / (BS * NC);
-      T acc = T(0);
-      if (x & 1) {
-        const int k0 = (x - 1) >> 1;            // coarse index of x - 3
-        for (int k = 0; k < 4; ++k) acc = acc + w[k] * c[zc][yc][k0 + k];
-      } else {
-        acc = acc + T(1) * c[zc][yc][(x + 2) >> 1];
+  const bool col = tid < BS * BS;
+  const int x = col ? tid % BS : 0, y = col ? tid / BS : 0;
+  const int wid = tid >> 5, lane = tid & 31;
+
+  if (f == 4) {
+    T tmin = T(1e30), tmax = T(-1e30);
+    if (chi && col) {
+      const T* cb = chi + (size_t)slot * L::FS;
+      T v[BS];
+#pragma unroll
+      for (int z = 0; z < BS; ++z) v[z] = cb[L::idx(x, y, z)];
+#pragma unroll
+      for (int z = 0; z < BS; ++z) {
+        tmin = v[z] < tmin ? v[z] : tmin;
+        tmax = v[z] > tmax ? v[z] : tmax;
       }
-      px[zc][yc][x] = acc;
     }
-    __syncthreads();
-    for (int i = threadIdx.x; i < NC * BS * BS; i += kNT) {
-      const int x = i % BS, y = (i / BS) % BS, zc = i / (BS * BS);
-      T acc = T(0);
-      if (y & 1) {
-        const int k0 = (y - 1) >> 1;
-        for (int k = 0; k < 4; ++k) acc = acc + w[k] * px[zc][k0 + k][x];
-      } else {
-        acc = acc + T(1) * px[zc][(y + 2) >> 1][x];
-      }
-      py[zc][y][x] = acc;
+    for (int o = 16; o > 0; o >>= 1) {
+      const T a = __shfl_xor_sync(0xffffffffu, tmin, o), b = __shfl_xor_sync(0xffffffffu, tmax, o);
+      tmin = a < tmin ? a : tmin;
+      tmax = b > tmax ? b : tmax;
     }
+    if (lane == 0) { red[0][wid] = tmin; red[1][wid] = tmax; }
     __syncthreads();
-    for (int i = threadIdx.x; i < BS * BS * BS; i += kNT) {
-      const int x = i % BS, y = (i / BS) % BS, z = i / (BS * BS);
-      if (((x | y | z) & 1) == 0) continue;          // all-even points: detail is zero
-      T acc = T(0);
-      if (z & 1) {
-        const int k0 = (z - 1) >> 1;
-        for (int k = 0; k < 4; ++k) acc = acc + w[k] * py[k0 + k][y][x];
-      } else {
-        acc = acc + T(1) * py[(z + 2) >> 1][y][x];
+    if (tid == 0) {
+      T mn = red[0][0], mx = red[1][0];
+      for (int k = 1; k < NT / 32; ++k) {
+        mn = red[0][k] < mn ? red[0][k] : mn;
+        mx = red[1][k] > mx ? red[1][k] : mx;
       }
-      const T dv = tabs(reg[(size_t)slot * L::BLK + (size_t)f * L::FS + L::idx(x, y, z)] - acc);
+      chirange[rank] = chi ? (double)mx - (double)mn : 0.0;
+    }
+    return;
+  }
+
+  // global max norm of component f, as left by the max-norm reduction (non-negative double bits)
+  const double nf = __longlong_as_double((long long)norm_bits[f]);
+  const double inv = nf > 0.0 ? 1.0 / nf : 0.0;
+  if (inv == 0.0) return;
+  const T* bf = reg + (size_t)slot * L::BLK + (size_t)f * L::FS;
+  T u[BS];
+  if (col) {
+#pragma unroll
+    for (int z = 0; z < BS; ++z) u[z] = bf[L::idx(x, y, z)];
+  }
+  for (int i = tid; i < kNbhStride; i += NT) nbh[i] = nbh_all[(size_t)rank * kNbhStride + i];
+  __syncthreads();
+  {
+    // coarse samples: offsets first, then all loads of the thread at once
+    constexpr int U = (NC3 + NT - 1) / NT;
+    long long off[U];
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+      const int i = tid + k * NT;
+      off[k] = -2;
+      if (i < NC3) {
+        const int cx = 2 * (i % NC) - 2, cy = 2 * ((i / NC) % NC) - 2, cz = 2 * (i / (NC * NC)) - 2;
+        if (cx >= 0 && cx <= M && cy >= 0 && cy <= M && cz >= 0 && cz <= M)
+          off[k] = (long long)slot * L::BLK + (long long)f * L::FS + L::idx(cx, cy, cz);
+        else
+          off[k] = direct_offset<T, BS>(nbh, cx, cy, cz, f);
+      }
+    }
+    T v[U];
+#pragma unroll
+    for (int k = 0; k < U; ++k) v[k] = off[k] >= 0 ? reg[off[k]] : T(__longlong_as_double(0x7ff8000000000000ll));
+#pragma unroll
+    for (int k = 0; k < U; ++k)
+      if (off[k] != -2) ra[tid + k * NT] = v[k];
+  }
+  __syncthreads();
+  if (tid < NC * NC) {                       // x-pass: line (yc, zc) = tid
+    T cv[NC];
+#pragma unroll
+    for (int k = 0; k < NC; ++k) cv[k] = ra[tid * NC + k];
+#pragma unroll
+    for (int i = 0; i < BS; ++i) px[tid * BS + i] = dd4_line<T, BS>(cv, i);
+  }
+  __syncthreads();
+  if (tid < NC * BS) {                       // y-pass: line (x, zc)
+    const int lx = tid % BS, zc = tid / BS;
+    T cv[NC];
+#pragma unroll
+    for (int k = 0; k < NC; ++k) cv[k] = px[(zc * NC + k) * BS + lx];
+#pragma unroll
+    for (int i = 0; i < BS; ++i) ra[(zc * BS + i) * BS + lx] = dd4_line<T, BS>(cv, i);
+  }
+  __syncthreads();
+  T dmax = T(0);      // max |detail| in the field precision; max(|d| inv) = max|d| inv exactly
+  if (col) {                                 // z-pass: column (x, y), compared with the block
+    T cv[NC];
+#pragma unroll
+    for (int k = 0; k < NC; ++k) cv[k] = ra[(k * BS + y) * BS + x];
+#pragma unroll
+    for (int z = 0; z < BS; ++z) {
+      const T dv = tabs(u[z] - dd4_line<T, BS>(cv, z));
       dmax = dv > dmax ? dv : dmax;
     }
-    const double r = (double)dmax * inv;
-    best = r > best ? r : best;
   }
-  double cmin = 1e300, cmax = -1e300;
-  if (chi) {
-    T tmin = T(1e30), tmax = T(-1e30);
-    for (int i = threadIdx.x; i < BS * BS * BS; i += kNT) {
-      const int x = i % BS, y = (i / BS) % BS, z = i / (BS * BS);
-      const T cv = chi[(size_t)slot * L::FS + L::idx(x, y, z)];
-      tmin = cv < tmin ? cv : tmin;
-      tmax = cv > tmax ? cv : tmax;
-    }
-    cmin = (double)tmin;
-    cmax = (double)tmax;
-  }
-  __shared__ double red[3][kNT / 32];
   for (int o = 16; o > 0; o >>= 1) {
-    best = fmax(best, __shfl_xor_sync(0xffffffffu, best, o));
-    cmin = fmin(cmin, __shfl_xor_sync(0xffffffffu, cmin, o));
-    cmax = fmax(cmax, __shfl_xor_sync(0xffffffffu, cmax, o));
+    const T a = __shfl_xor_sync(0xffffffffu, dmax, o);
+    dmax = a > dmax ? a : dmax;
   }
-  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (lane == 0) { red[0][wid] = best; red[1][wid] = cmin; red[2][wid] = cmax; }
+  if (lane == 0) red[0][wid] = dmax;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    double b = 0.0, mn = 1e300, mx = -1e300;
-    for (int k = 0; k < kNT / 32; ++k) {
-      b = fmax(b, red[0][k]);
-      mn = fmin(mn, red[1][k]);
-      mx = fmax(mx, red[2][k]);
-    }
-    ind[rank] = b;
-    chirange[rank] = chi ? mx - mn : 0.0;
+  if (tid == 0) {
+    T m = red[0][0];
+    for (int k = 1; k < NT / 32; ++k) m = red[0][k] > m ? red[0][k] : m;
+    const double r = (double)m * inv;
+    atomicMax(ind_bits + rank, (unsigned long long)__double_as_longlong(r));
   }
 }
 
@@ -312,39 +375,61 @@ __global__ void __launch_bounds__(kNT) k_maxnorm(const T* reg, const int32_t* bl
   using L = Lay<T, BS>;
   const int slot = blist[blockIdx.x];
   const T* b = reg + (size_t)slot * L::BLK;
-  // arithmetic in the field precision (an FP32 field gives an FP32 norm, stored as double)
+  // arithmetic in the field precision (an FP32 field gives an FP32 norm, stored as double);
+  // m[4] holds the squared magnitude, its root is taken once at the end
   T m[5] = {T(0), T(0), T(0), T(0), T(0)};
-  for (int i = threadIdx.x; i < BS * BS * BS; i += kNT) {
-    const int x = i % BS, y = (i / BS) % BS, z = i / (BS * BS);
-    const int pi = L::idx(x, y, z);
-    T v[4];
+  constexpr int N = BS * BS * BS, U = 4;
+  for (int base = threadIdx.x; base < N; base += kNT * U) {
+    T v[U][4];
 #pragma unroll
-    for (int f = 0; f < 4; ++f) {
-      v[f] = b[(size_t)f * L::FS + pi];
-      const T a = tabs(v[f]);
-      m[f] = a > m[f] ? a : m[f];
+    for (int k = 0; k < U; ++k) {
+      const int i = base + k * kNT;
+      const int pi = i < N ? L::idx(i % BS, (i / BS) % BS, i / (BS * BS)) : 0;
+#pragma unroll
+      for (int f = 0; f < 4; ++f) v[k][f] = i < N ? b[(size_t)f * L::FS + pi] : T(0);
     }
-    const T mag = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
-    m[4] = mag > m[4] ? mag : m[4];
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+#pragma unroll
+      for (int f = 0; f < 4; ++f) {
+        const T a = tabs(v[k][f]);
+        m[f] = a > m[f] ? a : m[f];
+      }
+      const T m2 = mag2(v[k][0], v[k][1], v[k][2]);
+      m[4] = m2 > m[4] ? m2 : m[4];
+    }
   }
+  __shared__ T red[5][kNT / 32];
 #pragma unroll
   for (int k = 0; k < 5; ++k) {
-    double mk = (double)m[k];
-    for (int o = 16; o > 0; o >>= 1) mk = fmax(mk, __shfl_xor_sync(0xffffffffu, mk, o));
-    if ((threadIdx.x & 31) == 0) atomicMax(out + k, (unsigned long long)__double_as_longlong(mk));
+    T mk = m[k];
+    for (int o = 16; o > 0; o >>= 1) {
+      const T t = __shfl_xor_sync(0xffffffffu, mk, o);
+      mk = t > mk ? t : mk;
+    }
+    if ((threadIdx.x & 31) == 0) red[k][threadIdx.x >> 5] = mk;
+  }
+  __syncthreads();
+  if (threadIdx.x < 5) {
+    T mk = T(0);
+    for (int w = 0; w < kNT / 32; ++w) mk = red[threadIdx.x][w] > mk ? red[threadIdx.x][w] : mk;
+    const double d = threadIdx.x == 4 ? (double)sqrt(mk) : (double)mk;
+    atomicMax(out + threadIdx.x, (unsigned long long)__double_as_longlong(d));
   }
 }
 
 // ---- (6) refinement: 8 children predicted from the synchronised parent (Sec. 3.5 step 1) -------
 // One CTA per (parent, component); task = [parent rank in the old grid, new slots of children
-// 0..7].  src is
-// a copy of the state taken before any child is written (children may reuse the parent's slot).
-// Per component: the parent's samples over local [-1, M+1]^3 (its ghost layer with the
-// finest-leaf rule, else the DD-4 prediction from the even lattice [-4, M+4]) are gathered into
-// shared memory once; each child is then predicted separably (x, then y, then z).
-// Dynamic shared memory: pp (M+3)^3 + ev/qx + qy, in T.
+// 0..7].  src is a copy of the state taken before any child is written (children may reuse the
+// parent's slot).  Per component the parent's samples over local [-1, M+1]^3 are put in shared
+// memory once: the interior one z-column per thread, the ghost shell from the finest leaf
+// holding each point, else by the tensor DD-4 prediction from the even lattice [-4, M+4] (only
+// gathered when a neighbour box is coarser).  Each child is then predicted separably (x, then
+// y, then z), a thread producing one whole line per pass; the z-pass writes the child.
+// Dynamic shared memory: pp (M+3)^3, ev/qx, qy in T, then the neighbourhood.
 template <typename T, int BS>
 struct RefSmem {
+  static constexpr int NT = ((BS * BS + 31) / 32) * 32;
   static constexpr int M = BS - 1;
   static constexpr int NPP = M + 3;                 // parent samples per axis: -1..M+1
   static constexpr int NEV = M / 2 + 5;             // even lattice per axis: -4..M+4
@@ -352,121 +437,173 @@ struct RefSmem {
   static constexpr int PP = NPP * NPP * NPP;
   static constexpr int EQ = (NEV * NEV * NEV > NP * NP * BS) ? NEV * NEV * NEV : NP * NP * BS;
   static constexpr int QY = NP * BS * BS;
+  static constexpr int NSHELL = PP - BS * BS * BS;  // ghost-shell points
   static constexpr size_t bytes = (size_t)(PP + EQ + QY) * sizeof(T) + kNbhStride * sizeof(int);
 };
 
 template <typename T, int BS>
-__global__ void __launch_bounds__(kNT, 4) k_refine(const T* src, T* dst, const int32_t* tasks, const int32_t* blist,
-                                                    const int32_t* nbh_all) {
+__global__ void __launch_bounds__(RefSmem<T, BS>::NT, sizeof(T) == 4 ? 3 : 2)
+k_refine(const T* src, T* dst, const int32_t* tasks, const int32_t* blist, const int32_t* nbh_all) {
   using L = Lay<T, BS>;
   using S = RefSmem<T, BS>;
-  constexpr int M = L::M, NPP = S::NPP, NEV = S::NEV, NP = S::NP;
+  constexpr int M = L::M, NPP = S::NPP, NEV = S::NEV, NP = S::NP, NT = S::NT;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* pp = reinterpret_cast<T*>(smem_raw);
   T* eq = pp + S::PP;                           // even lattice ev, later the x-pass qx
   T* qy = eq + S::EQ;
   int* nbh = reinterpret_cast<int*>(qy + S::QY);
+  const int tid = threadIdx.x;
   const int32_t* tk = tasks + (size_t)(blockIdx.x >> 2) * 9;
   const int f = blockIdx.x & 3;
   const int prank = tk[0];
   const int pslot = blist[prank];
-  for (int i = threadIdx.x; i < kNbhStride; i += kNT) nbh[i] = nbh_all[(size_t)prank * kNbhStride + i];
-  const T w[4] = {T(-1) / T(16), T(9) / T(16), T(9) / T(16), T(-1) / T(16)};
-  const int off[4] = {-3, -1, 1, 3};
-  auto PPI = [&](int x, int y, int z) { return ((z + 1) * NPP + (y + 1)) * NPP + (x + 1); };
+  const bool col = tid < BS * BS;
+  const int x = col ? tid % BS : 0, y = col ? tid / BS : 0;
+  const T NaN = T(__longlong_as_double(0x7ff8000000000000ll));
+  auto PPI = [&](int px, int py, int pz) { return ((pz + 1) * NPP + (py + 1)) * NPP + (px + 1); };
+
+  // the parent's interior, one z-column per thread (stored once the loads have arrived)
+  const T* pb = src + (size_t)pslot * L::BLK + (size_t)f * L::FS;
+  T u[BS];
+  if (col) {
+#pragma unroll
+    for (int z = 0; z < BS; ++z) u[z] = pb[L::idx(x, y, z)];
+  }
+  for (int i = tid; i < kNbhStride; i += NT) nbh[i] = nbh_all[(size_t)prank * kNbhStride + i];
+  __syncthreads();
+  const int coarser = __syncthreads_or(tid < 27 && tid != 13 && (nbh[kNbhType + tid] & 15) == kTypeCoarser);
+  if (coarser) {
+    // even-lattice points -4..M+4 (each held directly by some leaf)
+    constexpr int NE3 = NEV * NEV * NEV;
+    constexpr int U = (NE3 + NT - 1) / NT;
+    long long off[U];
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+      const int i = tid + k * NT;
+      off[k] = -2;
+      if (i < NE3) {
+        const int ex = 2 * (i % NEV) - 4, ey = 2 * ((i / NEV) % NEV) - 4, ez = 2 * (i / (NEV * NEV)) - 4;
+        if (ex >= 0 && ex <= M && ey >= 0 && ey <= M && ez >= 0 && ez <= M)
+          off[k] = (long long)pslot * L::BLK + (long long)f * L::FS + L::idx(ex, ey, ez);
+        else
+          off[k] = direct_offset<T, BS>(nbh, ex, ey, ez, f);
+      }
+    }
+    T v[U];
+#pragma unroll
+    for (int k = 0; k < U; ++k) v[k] = off[k] >= 0 ? src[off[k]] : NaN;
+#pragma unroll
+    for (int k = 0; k < U; ++k)
+      if (off[k] != -2) eq[tid + k * NT] = v[k];
+  }
   {
-    __syncthreads();
-    // even-lattice points -4..M+4 (held directly by some leaf)
-    gather<T, 4>(eq, NEV * NEV * NEV, [&](int i) {
-      const int x = 2 * (i % NEV) - 4, y = 2 * ((i / NEV) % NEV) - 4, z = 2 * (i / (NEV * NEV)) - 4;
-      T v;
-      if (x >= 0 && x <= M && y >= 0 && y <= M && z >= 0 && z <= M)
-        v = src[(size_t)pslot * L::BLK + (size_t)f * L::FS + L::idx(x, y, z)];
-      else if (!direct_value<T, BS>(src, nbh, x, y, z, f, &v))
-        v = T(__longlong_as_double(0x7ff8000000000000ll));
-      return v;
-    });
-    __syncthreads();
-    // parent samples: interior, else the finest leaf holding the point, else the tensor DD-4
-    // prediction from the even lattice (z outer, then y, then x)
-    for (int i = threadIdx.x; i < S::PP; i += kNT) {
-      const int x = i % NPP - 1, y = (i / NPP) % NPP - 1, z = i / (NPP * NPP) - 1;
-      T v;
-      if (x >= 0 && x <= M && y >= 0 && y <= M && z >= 0 && z <= M) {
-        v = src[(size_t)pslot * L::BLK + (size_t)f * L::FS + L::idx(x, y, z)];
-      } else if (!direct_value<T, BS>(src, nbh, x, y, z, f, &v)) {
-        const int p[3] = {x, y, z};
+    // ghost shell of [-1, M+1]^3: the z = -1, M+1 planes, then y = -1, M+1 rows (z in 0..M),
+    // then x = -1, M+1 (y, z in 0..M)
+    constexpr int U = (S::NSHELL + NT - 1) / NT;
+    constexpr int NZ = 2 * NPP * NPP, NY = 2 * NPP * BS;
+    int gi[U];
+    long long off[U];
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+      int i = tid + k * NT;
+      gi[k] = -1;
+      off[k] = -1;
+      if (i < S::NSHELL) {
+        int gx, gy, gz;
+        if (i < NZ) {
+          const int r = i % (NPP * NPP);
+          gx = r % NPP - 1; gy = r / NPP - 1; gz = i < NZ / 2 ? -1 : M + 1;
+        } else if ((i -= NZ) < NY) {
+          const int r = i % (NPP * BS);
+          gx = r % NPP - 1; gz = r / NPP; gy = i < NY / 2 ? -1 : M + 1;
+        } else {
+          i -= NY;
+          const int r = i % (BS * BS);
+          gy = r % BS; gz = r / BS; gx = i < BS * BS ? -1 : M + 1;
+        }
+        gi[k] = PPI(gx, gy, gz);
+        off[k] = direct_offset<T, BS>(nbh, gx, gy, gz, f);
+      }
+    }
+    T v[U];
+#pragma unroll
+    for (int k = 0; k < U; ++k) v[k] = off[k] >= 0 ? src[off[k]] : T(0);
+    if (col) {
+#pragma unroll
+      for (int z = 0; z < BS; ++z) pp[PPI(x, y, z)] = u[z];
+    }
+    __syncthreads();                          // ev complete
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+      if (gi[k] < 0) continue;
+      if (off[k] < 0) {
+        // tensor DD-4 prediction from the even lattice (z outer, then y, then x)
+        const int i = gi[k];
+        const int gx = i % NPP - 1, gy = (i / NPP) % NPP - 1, gz = i / (NPP * NPP) - 1;
+        const int p[3] = {gx, gy, gz};
+        const T w[4] = {T(-1) / T(16), T(9) / T(16), T(9) / T(16), T(-1) / T(16)};
+        const int o4[4] = {-3, -1, 1, 3};
         int cnt[3];
         for (int a = 0; a < 3; ++a) cnt[a] = (p[a] & 1) ? 4 : 1;
         T accz = T(0);
         for (int kz = 0; kz < cnt[2]; ++kz) {
-          const int zz = ((cnt[2] == 4 ? z + off[kz] : z) + 4) >> 1;
+          const int zz = ((cnt[2] == 4 ? gz + o4[kz] : gz) + 4) >> 1;
           T accy = T(0);
           for (int ky = 0; ky < cnt[1]; ++ky) {
-            const int yy = ((cnt[1] == 4 ? y + off[ky] : y) + 4) >> 1;
+            const int yy = ((cnt[1] == 4 ? gy + o4[ky] : gy) + 4) >> 1;
             T accx = T(0);
             for (int kx = 0; kx < cnt[0]; ++kx) {
-              const int xx = ((cnt[0] == 4 ? x + off[kx] : x) + 4) >> 1;
+              const int xx = ((cnt[0] == 4 ? gx + o4[kx] : gx) + 4) >> 1;
               accx = accx + (cnt[0] == 4 ? w[kx] : T(1)) * eq[(zz * NEV + yy) * NEV + xx];
             }
             accy = accy + (cnt[1] == 4 ? w[ky] : T(1)) * accx;
           }
           accz = accz + (cnt[2] == 4 ? w[kz] : T(1)) * accy;
         }
-        v = accz;
+        v[k] = accz;
       }
-      pp[i] = v;
+      pp[gi[k]] = v[k];
     }
-    for (int c = 0; c < 8; ++c) {
-      const int cb[3] = {c & 1, (c >> 1) & 1, (c >> 2) & 1};
-      const int o[3] = {cb[0] * (M / 2) - 1, cb[1] * (M / 2) - 1, cb[2] * (M / 2) - 1};
-      T* qx = eq;
-      __syncthreads();
-      // along x: qx[zz][yy][ix], zz, yy over the child's samples o..o+NP-1
-      for (int i = threadIdx.x; i < NP * NP * BS; i += kNT) {
-        const int ix = i % BS, yy = (i / BS) % NP, zz = i / (BS * NP);
-        const int px = cb[0] * M + ix;             // parent-local fine index (twice the parent index)
-        const int y = o[1] + yy, z = o[2] + zz;
-        T acc = T(0);
-        if (px & 1) {
-          for (int k = 0; k < 4; ++k) acc = acc + w[k] * pp[PPI((px + off[k]) / 2, y, z)];
-        } else {
-          acc = acc + T(1) * pp[PPI(px / 2, y, z)];
-        }
-        qx[(zz * NP + yy) * BS + ix] = acc;
-      }
-      __syncthreads();
-      for (int i = threadIdx.x; i < NP * BS * BS; i += kNT) {
-        const int ix = i % BS, iy = (i / BS) % BS, zz = i / (BS * BS);
-        const int py = cb[1] * M + iy;
-        T acc = T(0);
-        if (py & 1) {
-          for (int k = 0; k < 4; ++k) acc = acc + w[k] * qx[(zz * NP + ((py + off[k]) / 2 - o[1])) * BS + ix];
-        } else {
-          acc = acc + T(1) * qx[(zz * NP + (py / 2 - o[1])) * BS + ix];
-        }
-        qy[(zz * BS + iy) * BS + ix] = acc;
-      }
-      __syncthreads();
+  }
+  for (int c = 0; c < 8; ++c) {
+    const int cb[3] = {c & 1, (c >> 1) & 1, (c >> 2) & 1};
+    // the child's parent samples start at parent index o = cb M/2 - 1 on each axis
+    const int o[3] = {cb[0] * (M / 2) - 1, cb[1] * (M / 2) - 1, cb[2] * (M / 2) - 1};
+    T* qx = eq;
+    __syncthreads();                          // pp complete / previous child's passes done
+    if (tid < NP * NP) {                      // x-pass: line (yy, zz)
+      const int yy = tid % NP, zz = tid / NP;
+      T cv[NP];
+#pragma unroll
+      for (int k = 0; k < NP; ++k) cv[k] = pp[PPI(o[0] + k, o[1] + yy, o[2] + zz)];
+#pragma unroll
+      for (int i = 0; i < BS; ++i) qx[(zz * NP + yy) * BS + i] = dd4_line<T, BS>(cv, i);
+    }
+    __syncthreads();
+    if (tid < NP * BS) {                      // y-pass: line (ix, zz)
+      const int ix = tid % BS, zz = tid / BS;
+      T cv[NP];
+#pragma unroll
+      for (int k = 0; k < NP; ++k) cv[k] = qx[(zz * NP + k) * BS + ix];
+#pragma unroll
+      for (int i = 0; i < BS; ++i) qy[(zz * BS + i) * BS + ix] = dd4_line<T, BS>(cv, i);
+    }
+    __syncthreads();
+    if (col) {                                // z-pass: column (x, y), written to the child
+      T cv[NP];
+#pragma unroll
+      for (int k = 0; k < NP; ++k) cv[k] = qy[(k * BS + y) * BS + x];
       T* out = dst + (size_t)tk[1 + c] * L::BLK + (size_t)f * L::FS;
-      for (int i = threadIdx.x; i < BS * BS * BS; i += kNT) {
-        const int ix = i % BS, iy = (i / BS) % BS, iz = i / (BS * BS);
-        const int pz = cb[2] * M + iz;
-        T acc = T(0);
-        if (pz & 1) {
-          for (int k = 0; k < 4; ++k) acc = acc + w[k] * qy[(((pz + off[k]) / 2 - o[2]) * BS + iy) * BS + ix];
-        } else {
-          acc = acc + T(1) * qy[((pz / 2 - o[2]) * BS + iy) * BS + ix];
-        }
-        out[L::idx(ix, iy, iz)] = acc;
-      }
+#pragma unroll
+      for (int z = 0; z < BS; ++z) out[L::idx(x, y, z)] = dd4_line<T, BS>(cv, z);
     }
   }
 }
 
 // ---- (7) coarsening: parent by decimation of its 8 children (Sec. 3.1 R, Sec. 3.5 step 3) ----
-// task = [new parent slot, old child slots 0..7]; src is a copy of the state taken before the
-// merge (the parent may reuse a child's slot).
+// task = [new parent slot, old child slots 0..7]; dst is a register other than src (a parent
+// may take a slot freed by a child that another CTA is still reading): the parents are copied
+// into the state afterwards.
 template <typename T, int BS>
 __global__ void __launch_bounds__(kNT) k_coarsen(const T* src, T* dst, const int32_t* tasks) {
   using L = Lay<T, BS>;
@@ -485,10 +622,11 @@ __global__ void __launch_bounds__(kNT) k_coarsen(const T* src, T* dst, const int
 }
 
 // ---- copy of whole blocks (same slots) between two registers --------------------------------------
+// Slots list[i * stride], i = 0..n-1.
 template <typename T, int BS>
-__global__ void __launch_bounds__(kNT) k_copy_blocks(const T* src, T* dst, const int32_t* blist) {
+__global__ void __launch_bounds__(kNT) k_copy_blocks(const T* src, T* dst, const int32_t* list, int stride) {
   using L = Lay<T, BS>;
-  const size_t base = (size_t)blist[blockIdx.x] * L::BLK;
+  const size_t base = (size_t)list[(size_t)blockIdx.x * stride] * L::BLK;
   const float4* s4 = reinterpret_cast<const float4*>(src + base);
   float4* d4 = reinterpret_cast<float4*>(dst + base);
   constexpr int n4 = (int)(L::BLK * sizeof(T) / 16);
@@ -693,7 +831,8 @@ void launch_fine_wins(int Bs, T* reg, const int2* tasks, int64_t n, const int32_
 template <typename T>
 void launch_coarse_slabs(int Bs, const T* reg, T* slab, const int4* tasks, int64_t n, const int32_t* nbh, cudaStream_t st) {
   if (n <= 0) return;
-  ACM_BS_DISPATCH(Bs, k_coarse_slabs, <<<grid1(4 * n), kNT, 0, st>>>(reg, slab, tasks, nbh));
+  if (Bs == 17) k_coarse_slabs<T, 17><<<grid1(4 * n), SlabCfg<17>::NT, 0, st>>>(reg, slab, tasks, nbh);
+  else k_coarse_slabs<T, 9><<<grid1(4 * n), SlabCfg<9>::NT, 0, st>>>(reg, slab, tasks, nbh);
 }
 template <typename T>
 void launch_sync_ext(int Bs, const T* reg, T* out, int g, const int32_t* list, int64_t n, const int32_t* nbh, int by_rank, cudaStream_t st) {
@@ -705,7 +844,11 @@ void launch_details(int Bs, const T* reg, const T* chi, const int32_t* blist, co
                     const int32_t* nbh, int64_t n, const unsigned long long* norm_bits, double* ind,
                     double* chirange, cudaStream_t st) {
   if (n <= 0) return;
-  ACM_BS_DISPATCH(Bs, k_details, <<<grid1(n), kNT, 0, st>>>(reg, chi, blist, ranks, nbh, norm_bits, ind, chirange));
+  auto* bits = reinterpret_cast<unsigned long long*>(ind);
+  if (Bs == 17)
+    k_details<T, 17><<<grid1(5 * n), DetCfg<17>::NT, 0, st>>>(reg, chi, blist, ranks, nbh, norm_bits, bits, chirange);
+  else
+    k_details<T, 9><<<grid1(5 * n), DetCfg<9>::NT, 0, st>>>(reg, chi, blist, ranks, nbh, norm_bits, bits, chirange);
 }
 template <typename T>
 void launch_maxnorm(int Bs, const T* reg, const int32_t* blist, int64_t n, unsigned long long* out, cudaStream_t st) {
@@ -720,7 +863,7 @@ void launch_refine_bs(const T* src, T* dst, const int32_t* tasks, int64_t n, con
     cudaFuncSetAttribute(k_refine<T, BS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RefSmem<T, BS>::bytes);
     attr = true;
   }
-  k_refine<T, BS><<<grid1(4 * n), kNT, RefSmem<T, BS>::bytes, st>>>(src, dst, tasks, blist, nbh);
+  k_refine<T, BS><<<grid1(4 * n), RefSmem<T, BS>::NT, RefSmem<T, BS>::bytes, st>>>(src, dst, tasks, blist, nbh);
 }
 template <typename T>
 void launch_refine(int Bs, const T* src, T* dst, const int32_t* tasks, int64_t n, const int32_t* blist,
@@ -735,9 +878,9 @@ void launch_coarsen(int Bs, const T* src, T* dst, const int32_t* tasks, int64_t 
   ACM_BS_DISPATCH(Bs, k_coarsen, <<<grid1(n), kNT, 0, st>>>(src, dst, tasks));
 }
 template <typename T>
-void launch_copy_blocks(int Bs, const T* src, T* dst, const int32_t* blist, int64_t n, cudaStream_t st) {
+void launch_copy_blocks(int Bs, const T* src, T* dst, const int32_t* list, int stride, int64_t n, cudaStream_t st) {
   if (n <= 0) return;
-  ACM_BS_DISPATCH(Bs, k_copy_blocks, <<<grid1(n), kNT, 0, st>>>(src, dst, blist));
+  ACM_BS_DISPATCH(Bs, k_copy_blocks, <<<grid1(n), kNT, 0, st>>>(src, dst, list, stride));
 }
 template <typename T>
 void launch_ic(int Bs, T* reg, const int32_t* blist, const int32_t* ranks, int64_t n, const int4* binfo,
@@ -777,7 +920,7 @@ void launch_scatter(int Bs, const T* dense, T* reg, const int32_t* blist, int64_
   template void launch_maxnorm<T>(int, const T*, const int32_t*, int64_t, unsigned long long*, cudaStream_t); \
   template void launch_refine<T>(int, const T*, T*, const int32_t*, int64_t, const int32_t*, const int32_t*, cudaStream_t); \
   template void launch_coarsen<T>(int, const T*, T*, const int32_t*, int64_t, cudaStream_t);               \
-  template void launch_copy_blocks<T>(int, const T*, T*, const int32_t*, int64_t, cudaStream_t);          \
+  template void launch_copy_blocks<T>(int, const T*, T*, const int32_t*, int, int64_t, cudaStream_t);          \
   template void launch_ic<T>(int, T*, const int32_t*, const int32_t*, int64_t, const int4*, const PhysK&, const IcK&, cudaStream_t); \
   template void launch_mask<T>(int, T*, const int32_t*, const int32_t*, int64_t, const int4*, const PhysK&, const MaskK&, cudaStream_t); \
   template void launch_diag<T>(int, const T*, const T*, const int32_t*, int64_t, double*, cudaStream_t);   \

@@ -87,6 +87,8 @@ struct acm_forest {
   bool timing = false;
   acm_step_stats stats{};
   bool stats_pending = false;
+  // d_maxbits holds the max norms of U as the last RK4 stage left it (nothing changed U since)
+  bool norms_fresh = false;
   double host_topology_ms = 0, host_tree_ms = 0;   // cumulative host time of the tree logic
   double host_sort_ms = 0, host_rows_ms = 0, host_wait_ms = 0;   // parts of host_topology_ms
   cudaEvent_t ev[12] = {};          // per stage: before sync, after sync, after the stage kernel
@@ -324,7 +326,7 @@ acm_status fine_wins(acm_forest* f, T* reg) {
 // Copy every block of U to YA (same slots): the source of refinement and coarsening moves.
 template <typename T>
 acm_status snapshot_state(acm_forest* f) {
-  acm::launch_copy_blocks<T>(f->gp.Bs, reinterpret_cast<const T*>(f->U), reinterpret_cast<T*>(f->YA), f->d_blist,
+  acm::launch_copy_blocks<T>(f->gp.Bs, reinterpret_cast<const T*>(f->U), reinterpret_cast<T*>(f->YA), f->d_blist, 1,
                              (int64_t)f->order.size(), f->st);
   CKL();
   ++f->launches;
@@ -429,12 +431,19 @@ acm_status rk4(acm_forest* f, double dt, double* dt_used) {
     a.slab = reinterpret_cast<const T*>(f->SLAB);
     a.c_acc = s == 1 ? dt / 6.0 : dt / 3.0;
     a.c_out = s == 1 || s == 2 ? dt / 2.0 : (s == 3 ? dt : dt / 6.0);
+    a.norms = nullptr;
+    if (s == 4) {
+      // the last stage also reduces the max norms of U^{n+1} (read by the next coarsening)
+      CK(cudaMemsetAsync(f->d_maxbits, 0, 8 * sizeof(unsigned long long), f->st));
+      a.norms = f->d_maxbits;
+    }
     acm::launch_stage<T>(s, f->gp.Bs, a, t, f->phk, f->d_err, f->st);
     CKL();
     ++f->launches;
     if (f->timing) CK(cudaEventRecord(f->ev[3 * (s - 1) + 2], f->st));
   }
   CK(cudaMemcpyAsync(f->h_err, f->d_err, sizeof(int), cudaMemcpyDeviceToHost, f->st));
+  f->norms_fresh = true;
   f->time += dt;
   // algorithmic bytes of the four stage kernels: per point 64 words (registers Y, U, acc in and
   // out, see stage.cu) plus one word of mask per stage when a mask is set
@@ -450,6 +459,7 @@ acm_status rk4(acm_forest* f, double dt, double* dt_used) {
 
 template <typename T>
 acm_status refine_all(acm_forest* f) {
+  f->norms_fresh = false;
   acm::Forest& fo = *f->fo;
   const double t0 = now_ms();
   std::vector<BoxKey> parents;
@@ -519,6 +529,7 @@ acm_status indicators(acm_forest* f, std::vector<double>& ind, std::vector<doubl
       ranks = f->d_ranks;
     }
   }
+  CK(cudaMemsetAsync(f->d_ind, 0, f->order.size() * sizeof(double), f->st));
   acm::launch_details<T>(f->gp.Bs, reinterpret_cast<const T*>(f->U),
                          f->mask_on ? reinterpret_cast<const T*>(f->CHI) : nullptr, f->d_blist, ranks, f->d_nbh, n,
                          f->d_maxbits, f->d_ind, f->d_chir, f->st);
@@ -536,8 +547,11 @@ acm_status indicators(acm_forest* f, std::vector<double>& ind, std::vector<doubl
 template <typename T>
 acm_status coarsen(acm_forest* f, int64_t* n_blocks, int* n_passes) {
   acm::Forest& fo = *f->fo;
-  // component norms, taken once before the first pass, stay on the device (d_maxbits)
-  acm_status s = max_norms_async<T>(f);
+  // component norms of the state before the first pass stay on the device (d_maxbits): left
+  // there by the last RK4 stage when nothing has changed the state since, else reduced here
+  acm_status s = ACM_OK;
+  if (!f->norms_fresh) s = max_norms_async<T>(f);
+  f->norms_fresh = false;
   if (s) return s;
   int passes = 0;
   // A merge leaves every other block's indicator unchanged: its even samples keep their values
@@ -630,14 +644,16 @@ acm_status coarsen(acm_forest* f, int64_t* n_blocks, int* n_passes) {
       for (int c = 0; c < 8; ++c) tasks[9 * g + 1 + c] = kid_slots[g][c];
     }
     f->host_tree_ms += now_ms() - th;
-    // the merge reads a copy of the synchronised state (a parent may take a child's slot)
-    s = snapshot_state<T>(f);
-    if (s) return s;
+    // the parents are decimated into YA (a parent may take a slot freed by a child that is still
+    // being read), then copied into U
     CK(cudaMemcpyAsync(f->d_crst, tasks.data(), tasks.size() * 4, cudaMemcpyHostToDevice, f->st));
-    acm::launch_coarsen<T>(f->gp.Bs, reinterpret_cast<const T*>(f->YA), reinterpret_cast<T*>(f->U), f->d_crst,
+    acm::launch_coarsen<T>(f->gp.Bs, reinterpret_cast<const T*>(f->U), reinterpret_cast<T*>(f->YA), f->d_crst,
                            (int64_t)groups.size(), f->st);
     CKL();
-    ++f->launches;
+    acm::launch_copy_blocks<T>(f->gp.Bs, reinterpret_cast<const T*>(f->YA), reinterpret_cast<T*>(f->U), f->d_crst, 9,
+                               (int64_t)groups.size(), f->st);
+    CKL();
+    f->launches += 2;
     s = upload_topology(f, &order2);
     if (s) return s;
     s = eval_mask<T>(f, &new_slot);
@@ -652,6 +668,7 @@ acm_status coarsen(acm_forest* f, int64_t* n_blocks, int* n_passes) {
 
 template <typename T>
 acm_status set_ic(acm_forest* f, int kind, const double* params, int n) {
+  f->norms_fresh = false;
   acm::IcK ic{};
   ic.kind = kind;
   for (int i = 0; i < n && i < 8; ++i) ic.p[i] = params[i];
@@ -801,6 +818,7 @@ acm_status acm_set_leaves(acm_forest* f, const int32_t* level, const int32_t* gx
                           const int32_t* gz, int64_t n) {
   if (!f || !level || !gx || !gy || !gz || n <= 0) return fail(f, ACM_EINVAL, "bad leaves");
   if (n > f->gp.max_blocks) return fail(f, ACM_ECAPACITY, "more leaves than max_blocks");
+  f->norms_fresh = false;
   acm::Forest trial(f->gp.nroot, f->gp.Bs, f->gp.Jmin, f->gp.Jmax, f->gp.max_blocks);
   std::vector<BoxKey> created((size_t)n);
   for (int64_t i = 0; i < n; ++i) {
@@ -862,6 +880,7 @@ acm_status acm_set_mask(acm_forest* f, int kind, const double* params, int n, do
 
 acm_status acm_sync_ghosts(acm_forest* f, int reg, void* out, int on_device) {
   if (!f || !out || reg != ACM_REG_U) return fail(f, ACM_EINVAL, "bad arguments");
+  f->norms_fresh = false;
   const int g = f->gp.g;
   const int ne = f->gp.Bs + 2 * g;
   const size_t per = (size_t)4 * ne * ne * ne * f->esz;
@@ -953,6 +972,7 @@ acm_status acm_init_grid(acm_forest* f, int ic_kind, const double* params, int n
 acm_status acm_block_indicators(acm_forest* f, double* ind, double* chirange, int64_t n) {
   if (!f) return ACM_EINVAL;
   if (n < (int64_t)f->order.size()) return fail(f, ACM_EINVAL, "output arrays too small");
+  f->norms_fresh = false;
   acm_status s = f->gp.precision == 64 ? max_norms_async<double>(f) : max_norms_async<float>(f);
   if (s) return s;
   std::vector<double> iv, cv;
@@ -1003,6 +1023,7 @@ static acm_status copy_fields(acm_forest* f, void* buf, int64_t n_elems, int on_
   const size_t bytes = (size_t)need * f->esz;
   void* dense = on_device ? buf : f->DENSE;
   if (to_pool) {
+    f->norms_fresh = false;
     if (!on_device) CK(cudaMemcpyAsync(dense, buf, bytes, cudaMemcpyHostToDevice, f->st));
     if (f->gp.precision == 64)
       acm::launch_scatter<double>(f->gp.Bs, (const double*)dense, (double*)reg, f->d_blist, nb, f->st);
@@ -1039,6 +1060,7 @@ acm_status acm_read_mask(acm_forest* f, void* out, int64_t n_elems, int on_devic
 
 acm_status acm_rhs(acm_forest* f, void* out, int64_t n_elems, int on_device) {
   if (!f || !out) return fail(f, ACM_EINVAL, "bad arguments");
+  f->norms_fresh = false;
   if (f->order.empty()) return fail(f, ACM_EINVAL, "empty forest");
   acm::TopoK t = topo(f);
   if (f->gp.precision == 64) {

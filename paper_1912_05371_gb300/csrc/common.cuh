@@ -46,14 +46,14 @@ __host__ __device__ constexpr int box_index(int dx, int dy, int dz) {
   return (dx + 1) + 3 * (dy + 1) + 9 * (dz + 1);
 }
 
-// Value at local lattice point p of the block whose neighbourhood is nbh (level-J lattice,
-// local coordinates in [-M, 2M]) taken from the finest leaf that holds p as a grid point:
-// a finer leaf (decimation), else a same-level leaf (copy), else a coarser leaf if p lies on
-// its lattice.  Returns false if p is covered by coarser leaves only and is not on their
-// lattice (it must then be predicted).
+// Element offset (from the start of the register, component f) of local lattice point p of the
+// block whose neighbourhood is nbh (level-J lattice, local coordinates in [-M, 2M]) in the
+// finest leaf that holds p as a grid point: a finer leaf (decimation), else a same-level leaf
+// (copy), else a coarser leaf if p lies on its lattice.  Returns -1 if p is covered by coarser
+// leaves only and is not on their lattice (it must then be predicted).  Only shared/constant
+// data is read, so callers can find several offsets first and then issue their loads together.
 template <typename T, int BS>
-__device__ __forceinline__ bool direct_value(const T* __restrict__ reg, const int* __restrict__ nbh,
-                                             int px, int py, int pz, int f, T* out) {
+__device__ __forceinline__ long long direct_offset(const int* __restrict__ nbh, int px, int py, int pz, int f) {
   using L = Lay<T, BS>;
   constexpr int M = L::M;
   const int p[3] = {px, py, pz};
@@ -76,7 +76,7 @@ __device__ __forceinline__ bool direct_value(const T* __restrict__ reg, const in
           bd[0] = dx; bd[1] = dy; bd[2] = dz;
         }
       }
-  if (bestp == 0) return false;
+  if (bestp == 0) return -1;
   int q[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) q[a] = p[a] - bd[a] * M;   // in [0, M] inside box `best`
@@ -98,14 +98,50 @@ __device__ __forceinline__ bool direct_value(const T* __restrict__ reg, const in
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
       const int r = ((oct >> a) & 1) * M + q[a];
-      if (r & 1) return false;
+      if (r & 1) return -1;
       l[a] = r >> 1;
     }
     s = nbh[8 * best];
   }
-  if (s < 0) return false;
-  *out = reg[(size_t)s * L::BLK + (size_t)f * L::FS + L::idx(l[0], l[1], l[2])];
+  if (s < 0) return -1;
+  return (long long)s * L::BLK + (long long)f * L::FS + L::idx(l[0], l[1], l[2]);
+}
+
+// Value at local lattice point p from the finest leaf holding it (see direct_offset); false if
+// it must be predicted.
+template <typename T, int BS>
+__device__ __forceinline__ bool direct_value(const T* __restrict__ reg, const int* __restrict__ nbh,
+                                             int px, int py, int pz, int f, T* out) {
+  const long long o = direct_offset<T, BS>(nbh, px, py, pz, f);
+  if (o < 0) return false;
+  *out = reg[o];
   return true;
+}
+
+// Squared velocity magnitude with one fixed rounding sequence, so every kernel that takes the
+// max norm of (u, v, w) gets bitwise the same value (sqrt of the max = max of the sqrt).
+template <typename T>
+__device__ __forceinline__ T mag2(T u, T v, T w) {
+  T s = u * u;
+  s = fma(v, v, s);
+  return fma(w, w, s);
+}
+
+// DD-4 prediction of one line (Sec. 3.1): from NC = M/2 + 3 coarse samples c[k] at coarse
+// index k - 1 (fine index 2k - 2), the fine value at fine index i = 0..M: the sample itself at
+// even i, the 4-point stencil (-1, 9, 9, -1)/16 around it at odd i.  The sum runs left to right.
+template <typename T, int BS>
+__device__ __forceinline__ T dd4_line(const T (&c)[BS / 2 + 3], int i) {
+  if (i & 1) {
+    const int k0 = (i - 1) >> 1;            // coarse sample at fine index i - 3
+    T acc = T(0);
+    acc = acc + (T(-1) / T(16)) * c[k0];
+    acc = acc + (T(9) / T(16)) * c[k0 + 1];
+    acc = acc + (T(9) / T(16)) * c[k0 + 2];
+    acc = acc + (T(-1) / T(16)) * c[k0 + 3];
+    return acc;
+  }
+  return c[(i + 2) >> 1];
 }
 
 // Point value with the DD-4 fallback (Sec. 3.1): points held only by coarser leaves are the

@@ -48,6 +48,8 @@ struct StageK {
   const T* slab;
   double c_acc, c_out;      // stage coefficients (see stage.cu)
   StageConst<T> kc;         // the constants above in the field precision (filled by launch_stage)
+  // stage 4 only, if set: the max norms of U^{n+1} (layout and zeroing as for launch_maxnorm)
+  unsigned long long* norms;
 };
 
 // err: device int set to 1 if a bounded wait inside the kernel expired (never cleared here).
@@ -71,7 +73,8 @@ void launch_sync_ext(int Bs, const T* reg, T* out, int g, const int32_t* blist, 
 
 // Block indicators from the state itself (fine-wins applied): ind[rank], chirange[rank].
 // (ranks: the blocks to evaluate, nullptr = all n; results are written at their ranks;
-// norm_bits: the 4 component max norms as left by launch_maxnorm, read on the device)
+// norm_bits: the 4 component max norms as left by launch_maxnorm, read on the device; ind is
+// combined by an atomic maximum and must be zero at the evaluated ranks before the launch)
 template <typename T>
 void launch_details(int Bs, const T* reg, const T* chi, const int32_t* blist, const int32_t* ranks,
                     const int32_t* nbh, int64_t n, const unsigned long long* norm_bits, double* ind,
@@ -94,7 +97,7 @@ void launch_coarsen(int Bs, const T* src, T* dst, const int32_t* tasks /*[n][9]*
                     cudaStream_t st);
 
 template <typename T>
-void launch_copy_blocks(int Bs, const T* src, T* dst, const int32_t* blist, int64_t n, cudaStream_t st);
+void launch_copy_blocks(int Bs, const T* src, T* dst, const int32_t* list, int stride, int64_t n, cudaStream_t st);
 
 struct IcK {
   int kind;

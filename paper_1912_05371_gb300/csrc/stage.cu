@@ -221,6 +221,7 @@ k_stage(const StageK<T> a, const TopoK tp, const PhysK ph, int* err) {
     cp_async_commit();
   };
 
+  T nm[5] = {T(0), T(0), T(0), T(0), T(0)};   // stage 4: max |u|,|v|,|w|,|p|, |(u,v,w)|^2
   T q[4][8];
 #pragma unroll
   for (int k = 0; k < 7; ++k)
@@ -304,17 +305,46 @@ k_stage(const StageK<T> a, const TopoK tp, const PhysK ph, int* err) {
           a.acc[o] = q[f][3] + kc.c_acc * K[f];
           a.out[o] = q[f][3] + kc.c_out * K[f];
         } else if (STAGE == 4) {
-          a.out[o] = Av[f] + kc.c_out * K[f];
+          const T nv = Av[f] + kc.c_out * K[f];
+          a.out[o] = nv;
+          const T av = nv < T(0) ? -nv : nv;
+          nm[f] = av > nm[f] ? av : nm[f];
+          Uv[f] = nv;
         } else {
           a.acc[o] = Av[f] + kc.c_acc * K[f];
           a.out[o] = Uv[f] + kc.c_out * K[f];
         }
+      }
+      if (STAGE == 4) {
+        const T m2 = mag2(Uv[0], Uv[1], Uv[2]);
+        nm[4] = m2 > nm[4] ? m2 : nm[4];
       }
     }
 #pragma unroll
     for (int f = 0; f < 4; ++f)
 #pragma unroll
       for (int k = 0; k < 7; ++k) q[f][k] = q[f][k + 1];
+  }
+  if (STAGE == 4 && a.norms) {
+    // block maxima (buf is free now), then one atomic maximum per norm and block
+    __syncthreads();
+    T* red = &buf[0][0][0];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+      T m = nm[k];
+      for (int o = 16; o > 0; o >>= 1) {
+        const T t = __shfl_xor_sync(0xffffffffu, m, o);
+        m = t > m ? t : m;
+      }
+      if ((tid & 31) == 0) red[k * (NT / 32) + (tid >> 5)] = m;
+    }
+    __syncthreads();
+    if (tid < 5) {
+      T m = T(0);
+      for (int w = 0; w < NT / 32; ++w) m = red[tid * (NT / 32) + w] > m ? red[tid * (NT / 32) + w] : m;
+      const double d = tid == 4 ? (double)sqrt(m) : (double)m;
+      atomicMax(a.norms + tid, (unsigned long long)__double_as_longlong(d));
+    }
   }
 }
 
