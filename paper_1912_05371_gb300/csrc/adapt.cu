@@ -74,38 +74,44 @@ __global__ void __launch_bounds__(kNT) k_fine_wins(T* reg, const int2* tasks, co
 }
 
 // ---- (2) coarse-face halo slabs ------------------------------------------------------------------
-// task = (rank, face F, slab index, -); one CTA per (task, component).  The 3 x Bs x Bs halo
-// points beyond face F take the value of the finest leaf holding them, else the tensor DD-4
+// task = (rank, face F, slab index, -); one CTA per task, all four components.  The 3 x Bs x Bs
+// halo points beyond face F take the value of the finest leaf holding them, else the tensor DD-4
 // prediction from the coarse lattice (Sec. 3.1).  Only points on the face's tangential boundary
 // lines (t0 or t1 = 0 or M) can be held by a leaf of the block's level or finer; all others lie
 // in the coarser leaf alone.  The coarse patch the predictions need (even local coordinates
 // [M-2, M+6] or [-6, 2] across the face, [-2, M+2] along it) is gathered once, then predicted
 // separably: along t0, then t1, then across the face (a fixed order per face orientation, so
-// every block that needs a halo point gets bitwise the same value).
+// every block that needs a halo point gets bitwise the same value).  The leaf lookups are done
+// once per point for all components; each separable pass gives a thread one whole line, and
+// the last pass one halo column (t0, t1).
 // Slab layout [slab][comp][layer l-1][t1][t0] with (t0, t1) as in the stage kernel.
-// One thread per halo column (t0, t1); each separable pass gives a thread one whole line.  The
-// direct values of the edge columns are looked up and loaded together with the coarse patch.
-template <int BS>
-struct SlabCfg {
+// Dynamic shared memory: P, A, B below in T, then the neighbourhood.
+template <typename T, int BS>
+struct SlabSmem {
   static constexpr int NT = ((BS * BS + 31) / 32) * 32;
+  static constexpr int M = BS - 1;
+  static constexpr int NC = M / 2 + 3;              // coarse samples along the face: -2..M+2 step 2
+  static constexpr int NN = 5;                      // coarse planes across the face
+  static constexpr int P = 4 * NN * NC * NC;        // [f][n][t1 coarse][t0 coarse]
+  static constexpr int A = 4 * NN * NC * BS;        // [f][n][t1 coarse][t0]: predicted along t0
+  static constexpr int B = 4 * NN * BS * BS;        // [f][n][t1][t0]: predicted along t0 and t1
+  static constexpr size_t bytes = (size_t)(P + A + B) * sizeof(T) + kNbhStride * sizeof(int);
 };
 
 template <typename T, int BS>
-__global__ void __launch_bounds__(SlabCfg<BS>::NT) k_coarse_slabs(const T* reg, T* slab, const int4* tasks,
-                                                                   const int32_t* nbh_all) {
+__global__ void __launch_bounds__(SlabSmem<T, BS>::NT) k_coarse_slabs(const T* reg, T* slab, const int4* tasks,
+                                                                       const int32_t* nbh_all) {
   using L = Lay<T, BS>;
-  constexpr int M = L::M;
-  constexpr int NT = SlabCfg<BS>::NT;
-  constexpr int NC = M / 2 + 3;                     // coarse samples along the face: -2..M+2 step 2
-  constexpr int NN = 5;                             // coarse planes across the face
+  using S = SlabSmem<T, BS>;
+  constexpr int M = L::M, NT = S::NT, NC = S::NC, NN = S::NN;
   constexpr int NP3 = NN * NC * NC;
-  __shared__ int nbh[kNbhStride];
-  __shared__ T P[NN][NC][NC];                       // [n][t1 coarse][t0 coarse]
-  __shared__ T A[NN][NC][BS];                       // predicted along t0
-  __shared__ T B[NN][BS][BS];                       // predicted along t0 and t1
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* P = reinterpret_cast<T*>(smem_raw);
+  T* A = P + S::P;
+  T* B = A + S::A;
+  int* nbh = reinterpret_cast<int*>(B + S::B);
   const int tid = threadIdx.x;
-  const int4 tk = tasks[blockIdx.x >> 2];
-  const int f = blockIdx.x & 3;
+  const int4 tk = tasks[blockIdx.x];
   for (int i = tid; i < kNbhStride; i += NT) nbh[i] = nbh_all[(size_t)tk.x * kNbhStride + i];
   __syncthreads();
   const int F = tk.y, ax = F >> 1;
@@ -119,13 +125,14 @@ __global__ void __launch_bounds__(SlabCfg<BS>::NT) k_coarse_slabs(const T* reg, 
   const bool col = tid < BS * BS;
   const int t0 = col ? tid % BS : 0, t1 = col ? tid / BS : 0;
   const bool edge = col && (t0 == 0 || t0 == M || t1 == 0 || t1 == M);
+  // leaf lookups (component 0 offsets; component f is FS further), then all loads at once
   long long eo[3] = {-1, -1, -1};
   if (edge) {
 #pragma unroll
     for (int l = 1; l <= 3; ++l) {
       int x, y, z;
       place(plus ? M + l : -l, t0, t1, &x, &y, &z);
-      eo[l - 1] = direct_offset<T, BS>(nbh, x, y, z, f);
+      eo[l - 1] = direct_offset<T, BS>(nbh, x, y, z, 0);
     }
   }
   constexpr int U = (NP3 + NT - 1) / NT;
@@ -138,59 +145,68 @@ __global__ void __launch_bounds__(SlabCfg<BS>::NT) k_coarse_slabs(const T* reg, 
       const int a0 = i % NC, a1 = (i / NC) % NC, an = i / (NC * NC);
       int x, y, z;
       place(n0 + 2 * an, 2 * a0 - 2, 2 * a1 - 2, &x, &y, &z);
-      off[k] = direct_offset<T, BS>(nbh, x, y, z, f);
+      off[k] = direct_offset<T, BS>(nbh, x, y, z, 0);
     }
   }
-  T ev[3];
+  T ev[3][4];
 #pragma unroll
-  for (int l = 0; l < 3; ++l) ev[l] = eo[l] >= 0 ? reg[eo[l]] : T(0);
-  T pv[U];
+  for (int l = 0; l < 3; ++l)
 #pragma unroll
-  for (int k = 0; k < U; ++k) pv[k] = off[k] >= 0 ? reg[off[k]] : T(__longlong_as_double(0x7ff8000000000000ll));
+    for (int f = 0; f < 4; ++f) ev[l][f] = eo[l] >= 0 ? reg[eo[l] + (long long)f * L::FS] : T(0);
+  T pv[U][4];
 #pragma unroll
   for (int k = 0; k < U; ++k)
-    if (off[k] != -2) (&P[0][0][0])[tid + k * NT] = pv[k];
+#pragma unroll
+    for (int f = 0; f < 4; ++f)
+      pv[k][f] = off[k] >= 0 ? reg[off[k] + (long long)f * L::FS] : T(__longlong_as_double(0x7ff8000000000000ll));
+#pragma unroll
+  for (int k = 0; k < U; ++k)
+    if (off[k] != -2)
+#pragma unroll
+      for (int f = 0; f < 4; ++f) P[f * NP3 + tid + k * NT] = pv[k][f];
   __syncthreads();
-  if (tid < NN * NC) {                              // along t0: line (a1, n)
-    const int a1 = tid % NC, an = tid / NC;
+  for (int it = tid; it < 4 * NN * NC; it += NT) {  // along t0: line (f, n, a1)
     T cv[NC];
 #pragma unroll
-    for (int k = 0; k < NC; ++k) cv[k] = P[an][a1][k];
+    for (int k = 0; k < NC; ++k) cv[k] = P[it * NC + k];
 #pragma unroll
-    for (int i = 0; i < BS; ++i) A[an][a1][i] = dd4_line<T, BS>(cv, i);
+    for (int i = 0; i < BS; ++i) A[it * BS + i] = dd4_line<T, BS>(cv, i);
   }
   __syncthreads();
-  if (tid < NN * BS) {                              // along t1: line (t0, n)
-    const int l0 = tid % BS, an = tid / BS;
+  for (int it = tid; it < 4 * NN * BS; it += NT) {  // along t1: line (f, n, t0)
+    const int l0 = it % BS, fn = it / BS;
     T cv[NC];
 #pragma unroll
-    for (int k = 0; k < NC; ++k) cv[k] = A[an][k][l0];
+    for (int k = 0; k < NC; ++k) cv[k] = A[(fn * NC + k) * BS + l0];
 #pragma unroll
-    for (int i = 0; i < BS; ++i) B[an][i][l0] = dd4_line<T, BS>(cv, i);
+    for (int i = 0; i < BS; ++i) B[(fn * BS + i) * BS + l0] = dd4_line<T, BS>(cv, i);
   }
   __syncthreads();
   if (col) {                                        // across the face: column (t0, t1)
-    T cn[NN];
-#pragma unroll
-    for (int n = 0; n < NN; ++n) cn[n] = B[n][t1][t0];
     const T w[4] = {T(-1) / T(16), T(9) / T(16), T(9) / T(16), T(-1) / T(16)};
 #pragma unroll
-    for (int l = 1; l <= 3; ++l) {
-      T v;
-      if (eo[l - 1] >= 0) {
-        v = ev[l - 1];
-      } else {
-        const int c = (plus ? M + l : -l) - n0;     // fine offset from the first coarse plane
-        if (c & 1) {
-          const int k0 = (c - 3) >> 1;
-          v = T(0);
+    for (int f = 0; f < 4; ++f) {
+      T cn[NN];
 #pragma unroll
-          for (int k = 0; k < 4; ++k) v = v + w[k] * (k0 == 0 ? cn[k] : cn[k + 1]);
+      for (int n = 0; n < NN; ++n) cn[n] = B[((f * NN + n) * BS + t1) * BS + t0];
+#pragma unroll
+      for (int l = 1; l <= 3; ++l) {
+        T v;
+        if (eo[l - 1] >= 0) {
+          v = ev[l - 1][f];
         } else {
-          v = cn[c >> 1];
+          const int c = (plus ? M + l : -l) - n0;   // fine offset from the first coarse plane
+          if (c & 1) {
+            const int k0 = (c - 3) >> 1;            // 0 or 1
+            v = T(0);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) v = v + w[k] * (k0 == 0 ? cn[k] : cn[k + 1]);
+          } else {
+            v = cn[c >> 1];
+          }
         }
+        slab[((((size_t)tk.z * 4 + f) * 3 + (l - 1)) * BS + t1) * BS + t0] = v;
       }
-      slab[((((size_t)tk.z * 4 + f) * 3 + (l - 1)) * BS + t1) * BS + t0] = v;
     }
   }
 }
@@ -828,11 +844,20 @@ void launch_fine_wins(int Bs, T* reg, const int2* tasks, int64_t n, const int32_
   if (n <= 0) return;
   ACM_BS_DISPATCH(Bs, k_fine_wins, <<<grid1(n), kNT, 0, st>>>(reg, tasks, nbh, blist));
 }
+template <typename T, int BS>
+void launch_coarse_slabs_bs(const T* reg, T* slab, const int4* tasks, int64_t n, const int32_t* nbh, cudaStream_t st) {
+  static bool attr = false;             // opt in to more than 48 KB of dynamic shared memory once
+  if (!attr) {
+    cudaFuncSetAttribute(k_coarse_slabs<T, BS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SlabSmem<T, BS>::bytes);
+    attr = true;
+  }
+  k_coarse_slabs<T, BS><<<grid1(n), SlabSmem<T, BS>::NT, SlabSmem<T, BS>::bytes, st>>>(reg, slab, tasks, nbh);
+}
 template <typename T>
 void launch_coarse_slabs(int Bs, const T* reg, T* slab, const int4* tasks, int64_t n, const int32_t* nbh, cudaStream_t st) {
   if (n <= 0) return;
-  if (Bs == 17) k_coarse_slabs<T, 17><<<grid1(4 * n), SlabCfg<17>::NT, 0, st>>>(reg, slab, tasks, nbh);
-  else k_coarse_slabs<T, 9><<<grid1(4 * n), SlabCfg<9>::NT, 0, st>>>(reg, slab, tasks, nbh);
+  if (Bs == 17) launch_coarse_slabs_bs<T, 17>(reg, slab, tasks, n, nbh, st);
+  else launch_coarse_slabs_bs<T, 9>(reg, slab, tasks, n, nbh, st);
 }
 template <typename T>
 void launch_sync_ext(int Bs, const T* reg, T* out, int g, const int32_t* list, int64_t n, const int32_t* nbh, int by_rank, cudaStream_t st) {
