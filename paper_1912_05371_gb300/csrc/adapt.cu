@@ -239,88 +239,65 @@ __global__ void __launch_bounds__(kNT) k_sync_ext(const T* reg, T* out, int g, c
 }
 
 // ---- (4) block indicators: details (Sec. 3.1) and mask range ----------------------------------
-// One CTA per (block, component f = 0..3) and one per block (f = 4) for the mask range
-// max(chi) - min(chi).  The coarse samples are the block's even points, local coordinates
-// -2..M+2 (those outside the block are held directly by a neighbour leaf); they are predicted
-// back to every point separably (x, then y, then z: the tensor DD-4 sum in that nesting) and
-// subtracted.  In every pass a thread owns one whole line: it reads the line's coarse samples
-// once and produces its Bs values.  The block's own values, needed by the last pass, are loaded
-// at the start (one z-column per thread) and arrive while the passes run.  ind[rank] (zeroed by
-// the caller) receives the largest normalised detail over the components as an atomic maximum
-// on its bits: non-negative doubles order like their bit patterns.
-template <int BS>
-struct DetCfg {
+// One CTA per block.  The coarse samples are the block's even points, local coordinates -2..M+2
+// (those outside the block are held directly by a neighbour leaf; each is looked up once for
+// all four components); they are predicted back to every point separably (x, then y, then z:
+// the tensor DD-4 sum in that nesting) and subtracted.  In every pass a thread owns one whole
+// line: it reads the line's coarse samples once and produces its Bs values.  Components run one
+// after another through the passes; the block's own values of a component, compared in its last
+// pass, are loaded one z-column per thread when its first pass starts.  The z-pass of one
+// component and the x-pass of the next share a phase (they touch different buffers).
+// Dynamic shared memory: c [4][NC^3], px [NC][NC][Bs], py [NC][Bs][Bs] in T, then the
+// neighbourhood.
+template <typename T, int BS>
+struct DetSmem {
   static constexpr int NT = ((BS * BS + 31) / 32) * 32;
   static constexpr int NC = (BS - 1) / 2 + 3;   // coarse samples per axis, -1..M/2+1
+  static constexpr int NC3 = NC * NC * NC;
+  static constexpr int PX = NC * NC * BS, PY = NC * BS * BS;
+  static constexpr size_t bytes = (size_t)(4 * NC3 + PX + PY) * sizeof(T) + kNbhStride * sizeof(int);
 };
 
 template <typename T, int BS>
-__global__ void __launch_bounds__(DetCfg<BS>::NT) k_details(const T* reg, const T* chi, const int32_t* blist,
-                                                             const int32_t* ranks, const int32_t* nbh_all,
-                                                             const unsigned long long* norm_bits,
-                                                             unsigned long long* ind_bits, double* chirange) {
+__global__ void __launch_bounds__(DetSmem<T, BS>::NT) k_details(const T* reg, const T* chi, const int32_t* blist,
+                                                                 const int32_t* ranks, const int32_t* nbh_all,
+                                                                 const unsigned long long* norm_bits, double* ind,
+                                                                 double* chirange) {
   using L = Lay<T, BS>;
+  using S = DetSmem<T, BS>;
   constexpr int M = L::M;
-  constexpr int NT = DetCfg<BS>::NT, NC = DetCfg<BS>::NC;
-  constexpr int NC3 = NC * NC * NC;
-  constexpr int RA = NC3 > NC * BS * BS ? NC3 : NC * BS * BS;
-  __shared__ int nbh[kNbhStride];
-  __shared__ __align__(16) T ra[RA];            // coarse samples c[zc][yc][xc], later py[zc][y][x]
-  __shared__ __align__(16) T px[NC * NC * BS];  // x-pass px[zc][yc][x]
-  __shared__ T red[2][NT / 32];
+  constexpr int NT = S::NT, NC = S::NC, NC3 = S::NC3;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* cs = reinterpret_cast<T*>(smem_raw);       // c[f][zc][yc][xc]
+  T* px = cs + 4 * NC3;                         // px[zc][yc][x]
+  T* py = px + S::PX;                           // py[zc][y][x]
+  int* nbh = reinterpret_cast<int*>(py + S::PY);
+  __shared__ T red[6][NT / 32];
   const int tid = threadIdx.x;
-  const int item = blockIdx.x / 5, f = blockIdx.x - 5 * item;
-  const int rank = ranks ? ranks[item] : item;
+  const int rank = ranks ? ranks[blockIdx.x] : (int)blockIdx.x;
   const int slot = blist[rank];
   const bool col = tid < BS * BS;
   const int x = col ? tid % BS : 0, y = col ? tid / BS : 0;
   const int wid = tid >> 5, lane = tid & 31;
+  const T* bb = reg + (size_t)slot * L::BLK;
 
-  if (f == 4) {
-    T tmin = T(1e30), tmax = T(-1e30);
-    if (chi && col) {
-      const T* cb = chi + (size_t)slot * L::FS;
-      T v[BS];
+  // mask range from one z-column per thread
+  T tmin = T(1e30), tmax = T(-1e30);
+  if (chi && col) {
+    const T* cb = chi + (size_t)slot * L::FS;
+    T v[BS];
 #pragma unroll
-      for (int z = 0; z < BS; ++z) v[z] = cb[L::idx(x, y, z)];
+    for (int z = 0; z < BS; ++z) v[z] = cb[L::idx(x, y, z)];
 #pragma unroll
-      for (int z = 0; z < BS; ++z) {
-        tmin = v[z] < tmin ? v[z] : tmin;
-        tmax = v[z] > tmax ? v[z] : tmax;
-      }
+    for (int z = 0; z < BS; ++z) {
+      tmin = v[z] < tmin ? v[z] : tmin;
+      tmax = v[z] > tmax ? v[z] : tmax;
     }
-    for (int o = 16; o > 0; o >>= 1) {
-      const T a = __shfl_xor_sync(0xffffffffu, tmin, o), b = __shfl_xor_sync(0xffffffffu, tmax, o);
-      tmin = a < tmin ? a : tmin;
-      tmax = b > tmax ? b : tmax;
-    }
-    if (lane == 0) { red[0][wid] = tmin; red[1][wid] = tmax; }
-    __syncthreads();
-    if (tid == 0) {
-      T mn = red[0][0], mx = red[1][0];
-      for (int k = 1; k < NT / 32; ++k) {
-        mn = red[0][k] < mn ? red[0][k] : mn;
-        mx = red[1][k] > mx ? red[1][k] : mx;
-      }
-      chirange[rank] = chi ? (double)mx - (double)mn : 0.0;
-    }
-    return;
-  }
-
-  // global max norm of component f, as left by the max-norm reduction (non-negative double bits)
-  const double nf = __longlong_as_double((long long)norm_bits[f]);
-  const double inv = nf > 0.0 ? 1.0 / nf : 0.0;
-  if (inv == 0.0) return;
-  const T* bf = reg + (size_t)slot * L::BLK + (size_t)f * L::FS;
-  T u[BS];
-  if (col) {
-#pragma unroll
-    for (int z = 0; z < BS; ++z) u[z] = bf[L::idx(x, y, z)];
   }
   for (int i = tid; i < kNbhStride; i += NT) nbh[i] = nbh_all[(size_t)rank * kNbhStride + i];
   __syncthreads();
   {
-    // coarse samples: offsets first, then all loads of the thread at once
+    // coarse samples: offsets (component 0) first, then the loads of all components at once
     constexpr int U = (NC3 + NT - 1) / NT;
     long long off[U];
 #pragma unroll
@@ -330,58 +307,95 @@ __global__ void __launch_bounds__(DetCfg<BS>::NT) k_details(const T* reg, const 
       if (i < NC3) {
         const int cx = 2 * (i % NC) - 2, cy = 2 * ((i / NC) % NC) - 2, cz = 2 * (i / (NC * NC)) - 2;
         if (cx >= 0 && cx <= M && cy >= 0 && cy <= M && cz >= 0 && cz <= M)
-          off[k] = (long long)slot * L::BLK + (long long)f * L::FS + L::idx(cx, cy, cz);
+          off[k] = (long long)slot * L::BLK + L::idx(cx, cy, cz);
         else
-          off[k] = direct_offset<T, BS>(nbh, cx, cy, cz, f);
+          off[k] = direct_offset<T, BS>(nbh, cx, cy, cz, 0);
       }
     }
-    T v[U];
-#pragma unroll
-    for (int k = 0; k < U; ++k) v[k] = off[k] >= 0 ? reg[off[k]] : T(__longlong_as_double(0x7ff8000000000000ll));
+    T v[U][4];
 #pragma unroll
     for (int k = 0; k < U; ++k)
-      if (off[k] != -2) ra[tid + k * NT] = v[k];
+#pragma unroll
+      for (int f = 0; f < 4; ++f)
+        v[k][f] = off[k] >= 0 ? reg[off[k] + (long long)f * L::FS] : T(__longlong_as_double(0x7ff8000000000000ll));
+#pragma unroll
+    for (int k = 0; k < U; ++k)
+      if (off[k] != -2)
+#pragma unroll
+        for (int f = 0; f < 4; ++f) cs[f * NC3 + tid + k * NT] = v[k][f];
   }
   __syncthreads();
-  if (tid < NC * NC) {                       // x-pass: line (yc, zc) = tid
-    T cv[NC];
+  auto xpass = [&](int f) {
+    if (tid < NC * NC) {                        // line (yc, zc) = tid
+      T cv[NC];
 #pragma unroll
-    for (int k = 0; k < NC; ++k) cv[k] = ra[tid * NC + k];
+      for (int k = 0; k < NC; ++k) cv[k] = cs[f * NC3 + tid * NC + k];
 #pragma unroll
-    for (int i = 0; i < BS; ++i) px[tid * BS + i] = dd4_line<T, BS>(cv, i);
-  }
-  __syncthreads();
-  if (tid < NC * BS) {                       // y-pass: line (x, zc)
-    const int lx = tid % BS, zc = tid / BS;
-    T cv[NC];
-#pragma unroll
-    for (int k = 0; k < NC; ++k) cv[k] = px[(zc * NC + k) * BS + lx];
-#pragma unroll
-    for (int i = 0; i < BS; ++i) ra[(zc * BS + i) * BS + lx] = dd4_line<T, BS>(cv, i);
-  }
-  __syncthreads();
-  T dmax = T(0);      // max |detail| in the field precision; max(|d| inv) = max|d| inv exactly
-  if (col) {                                 // z-pass: column (x, y), compared with the block
-    T cv[NC];
-#pragma unroll
-    for (int k = 0; k < NC; ++k) cv[k] = ra[(k * BS + y) * BS + x];
-#pragma unroll
-    for (int z = 0; z < BS; ++z) {
-      const T dv = tabs(u[z] - dd4_line<T, BS>(cv, z));
-      dmax = dv > dmax ? dv : dmax;
+      for (int i = 0; i < BS; ++i) px[tid * BS + i] = dd4_line<T, BS>(cv, i);
     }
+  };
+  double best = 0.0;
+  T u[BS];
+  xpass(0);
+  for (int f = 0; f < 4; ++f) {
+    if (col) {
+#pragma unroll
+      for (int z = 0; z < BS; ++z) u[z] = bb[(size_t)f * L::FS + L::idx(x, y, z)];
+    }
+    __syncthreads();                            // px of component f complete
+    if (tid < NC * BS) {                        // y-pass: line (x, zc)
+      const int lx = tid % BS, zc = tid / BS;
+      T cv[NC];
+#pragma unroll
+      for (int k = 0; k < NC; ++k) cv[k] = px[(zc * NC + k) * BS + lx];
+#pragma unroll
+      for (int i = 0; i < BS; ++i) py[(zc * BS + i) * BS + lx] = dd4_line<T, BS>(cv, i);
+    }
+    __syncthreads();                            // py complete, px free
+    T dmax = T(0);    // max |detail| in the field precision; max(|d| inv) = max|d| inv exactly
+    if (col) {                                  // z-pass: column (x, y), compared with the block
+      T cv[NC];
+#pragma unroll
+      for (int k = 0; k < NC; ++k) cv[k] = py[(k * BS + y) * BS + x];
+#pragma unroll
+      for (int z = 0; z < BS; ++z) {
+        const T dv = tabs(u[z] - dd4_line<T, BS>(cv, z));
+        dmax = dv > dmax ? dv : dmax;
+      }
+    }
+    if (f < 3) xpass(f + 1);
+    for (int o = 16; o > 0; o >>= 1) {
+      const T t = __shfl_xor_sync(0xffffffffu, dmax, o);
+      dmax = t > dmax ? t : dmax;
+    }
+    if (lane == 0) red[f][wid] = dmax;
+    // the barrier at the top of the next component (or the one below) orders py's reuse
   }
   for (int o = 16; o > 0; o >>= 1) {
-    const T a = __shfl_xor_sync(0xffffffffu, dmax, o);
-    dmax = a > dmax ? a : dmax;
+    const T a = __shfl_xor_sync(0xffffffffu, tmin, o), b = __shfl_xor_sync(0xffffffffu, tmax, o);
+    tmin = a < tmin ? a : tmin;
+    tmax = b > tmax ? b : tmax;
   }
-  if (lane == 0) red[0][wid] = dmax;
+  if (lane == 0) { red[4][wid] = tmin; red[5][wid] = tmax; }
   __syncthreads();
   if (tid == 0) {
-    T m = red[0][0];
-    for (int k = 1; k < NT / 32; ++k) m = red[0][k] > m ? red[0][k] : m;
-    const double r = (double)m * inv;
-    atomicMax(ind_bits + rank, (unsigned long long)__double_as_longlong(r));
+    for (int f = 0; f < 4; ++f) {
+      // global max norm of component f, as left by the max-norm reduction (non-negative bits)
+      const double nf = __longlong_as_double((long long)norm_bits[f]);
+      const double inv = nf > 0.0 ? 1.0 / nf : 0.0;
+      if (inv == 0.0) continue;
+      T m = red[f][0];
+      for (int k = 1; k < NT / 32; ++k) m = red[f][k] > m ? red[f][k] : m;
+      const double r = (double)m * inv;
+      best = r > best ? r : best;
+    }
+    T mn = red[4][0], mx = red[5][0];
+    for (int k = 1; k < NT / 32; ++k) {
+      mn = red[4][k] < mn ? red[4][k] : mn;
+      mx = red[5][k] > mx ? red[5][k] : mx;
+    }
+    ind[rank] = best;
+    chirange[rank] = chi ? (double)mx - (double)mn : 0.0;
   }
 }
 
@@ -620,21 +634,32 @@ k_refine(const T* src, T* dst, const int32_t* tasks, const int32_t* blist, const
 // task = [new parent slot, old child slots 0..7]; dst is a register other than src (a parent
 // may take a slot freed by a child that another CTA is still reading): the parents are copied
 // into the state afterwards.
+// One CTA per (task, component); a thread owns one z-column of the parent and has all its loads
+// in flight before it stores.
+template <int BS>
+struct ColCfg {
+  static constexpr int NT = ((BS * BS + 31) / 32) * 32;
+};
+
 template <typename T, int BS>
-__global__ void __launch_bounds__(kNT) k_coarsen(const T* src, T* dst, const int32_t* tasks) {
+__global__ void __launch_bounds__(ColCfg<BS>::NT) k_coarsen(const T* src, T* dst, const int32_t* tasks) {
   using L = Lay<T, BS>;
   constexpr int M = L::M;
-  const int32_t* tk = tasks + (size_t)blockIdx.x * 9;
-  for (int i = threadIdx.x; i < 4 * BS * BS * BS; i += kNT) {
-    const int f = i / (BS * BS * BS);
-    const int r = i % (BS * BS * BS);
-    const int x = r % BS, y = (r / BS) % BS, z = r / (BS * BS);
-    const int cx = x > M / 2, cy = y > M / 2, cz = z > M / 2;
-    const int lx = 2 * x - cx * M, ly = 2 * y - cy * M, lz = 2 * z - cz * M;
-    const int cs = tk[1 + (cx | (cy << 1) | (cz << 2))];
-    dst[(size_t)tk[0] * L::BLK + (size_t)f * L::FS + L::idx(x, y, z)] =
-        src[(size_t)cs * L::BLK + (size_t)f * L::FS + L::idx(lx, ly, lz)];
-  }
+  const int32_t* tk = tasks + (size_t)(blockIdx.x >> 2) * 9;
+  const int f = blockIdx.x & 3;
+  const int tid = threadIdx.x;
+  if (tid >= BS * BS) return;
+  const int x = tid % BS, y = tid / BS;
+  const int cx = x > M / 2, cy = y > M / 2;
+  const int lx = 2 * x - cx * M, ly = 2 * y - cy * M;
+  const T* c0 = src + (size_t)tk[1 + (cx | (cy << 1))] * L::BLK + (size_t)f * L::FS;       // cz = 0
+  const T* c1 = src + (size_t)tk[1 + (cx | (cy << 1) | 4)] * L::BLK + (size_t)f * L::FS;   // cz = 1
+  T v[BS];
+#pragma unroll
+  for (int z = 0; z < BS; ++z) v[z] = z <= M / 2 ? c0[L::idx(lx, ly, 2 * z)] : c1[L::idx(lx, ly, 2 * z - M)];
+  T* out = dst + (size_t)tk[0] * L::BLK + (size_t)f * L::FS;
+#pragma unroll
+  for (int z = 0; z < BS; ++z) out[L::idx(x, y, z)] = v[z];
 }
 
 // ---- copy of whole blocks (same slots) between two registers --------------------------------------
@@ -701,8 +726,8 @@ __global__ void __launch_bounds__(kNT) k_ic(T* reg, const int32_t* blist, const 
 }
 
 template <typename T, int BS>
-__global__ void __launch_bounds__(kNT) k_mask(T* chi, const int32_t* blist, const int32_t* ranks, const int4* binfo,
-                                               const PhysK ph, const MaskK m) {
+__global__ void __launch_bounds__(ColCfg<BS>::NT) k_mask(T* chi, const int32_t* blist, const int32_t* ranks,
+                                                         const int4* binfo, const PhysK ph, const MaskK m) {
   using L = Lay<T, BS>;
   constexpr int M = L::M;
   const int rank = ranks ? ranks[blockIdx.x] : (int)blockIdx.x;
@@ -731,27 +756,36 @@ __global__ void __launch_bounds__(kNT) k_mask(T* chi, const int32_t* blist, cons
       if (sqrt(dmin2) - m.p[3] > 40.0 * m.p[4]) uniform = 0;
       else if (sqrt(dmax2) - m.p[3] < -40.0 * m.p[4]) uniform = 1;
     }
+  } else {
+    uniform = 0;
   }
-  for (int i = threadIdx.x; i < BS * BS * BS; i += kNT) {
-    const int ix = i % BS, iy = (i / BS) % BS, iz = i / (BS * BS);
-    // evaluated in the field precision: FP64 fields in double, FP32 fields in float
-    T c = T(0);
-    if (uniform >= 0) {
-      c = T(uniform);
-    } else if (m.kind == 1) {
-      // coordinates in the field precision: i h with i the wrapped lattice index (exact when h
-      // is dyadic, as for power-of-two root sides)
-      const T X = T(lattice(ph, bi, 0, ix, M)) * T(h), Y = T(lattice(ph, bi, 1, iy, M)) * T(h),
-              Z = T(lattice(ph, bi, 2, iz, M)) * T(h);
-      const T dx = X - T(m.p[0]), dy = Y - T(m.p[1]), dz = Z - T(m.p[2]);
-      const T d = sqrt(dx * dx + dy * dy + dz * dz) - T(m.p[3]);
-      // beyond 10 delta (FP32) / 20 delta (FP64) tanh(d/delta) rounds to exactly +-1
-      const T cut = T(sizeof(T) == 4 ? 10.0 : 20.0) * T(m.p[4]);
-      if (d > cut) c = T(0);
-      else if (d < -cut) c = T(1);
-      else c = T(0.5) * (T(1) - tanh(d / T(m.p[4])));
-    }
-    chi[(size_t)slot * L::FS + L::idx(ix, iy, iz)] = c;
+  const int tid = threadIdx.x;
+  if (tid >= BS * BS) return;
+  const int ix = tid % BS, iy = tid / BS;
+  T* out = chi + (size_t)slot * L::FS;
+  if (uniform >= 0) {
+#pragma unroll
+    for (int iz = 0; iz < BS; ++iz) out[L::idx(ix, iy, iz)] = T(uniform);
+    return;
+  }
+  // evaluated in the field precision: FP64 fields in double, FP32 fields in float; the
+  // conversions of the constants are done once, outside the point loop
+  const T hT = T(h);
+  const T c0 = T(m.p[0]), c1 = T(m.p[1]), c2 = T(m.p[2]), R = T(m.p[3]), dl = T(m.p[4]);
+  // beyond 10 delta (FP32) / 20 delta (FP64) tanh(d/delta) rounds to exactly +-1
+  const T cut = T(sizeof(T) == 4 ? 10.0 : 20.0) * dl;
+  // coordinates i h with i the wrapped lattice index (exact when h is dyadic, as for
+  // power-of-two root sides)
+  const T dx = T(lattice(ph, bi, 0, ix, M)) * hT - c0, dy = T(lattice(ph, bi, 1, iy, M)) * hT - c1;
+#pragma unroll
+  for (int iz = 0; iz < BS; ++iz) {
+    const T dz = T(lattice(ph, bi, 2, iz, M)) * hT - c2;
+    const T d = sqrt(dx * dx + dy * dy + dz * dz) - R;
+    T c;
+    if (d > cut) c = T(0);
+    else if (d < -cut) c = T(1);
+    else c = T(0.5) * (T(1) - tanh(d / dl));
+    out[L::idx(ix, iy, iz)] = c;
   }
 }
 
@@ -864,16 +898,24 @@ void launch_sync_ext(int Bs, const T* reg, T* out, int g, const int32_t* list, i
   if (n <= 0) return;
   ACM_BS_DISPATCH(Bs, k_sync_ext, <<<grid1(n), kNT, 0, st>>>(reg, out, g, list, nbh, by_rank));
 }
+template <typename T, int BS>
+void launch_details_bs(const T* reg, const T* chi, const int32_t* blist, const int32_t* ranks, const int32_t* nbh,
+                       int64_t n, const unsigned long long* norm_bits, double* ind, double* chirange, cudaStream_t st) {
+  static bool attr = false;             // opt in to more than 48 KB of dynamic shared memory once
+  if (!attr) {
+    cudaFuncSetAttribute(k_details<T, BS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DetSmem<T, BS>::bytes);
+    attr = true;
+  }
+  k_details<T, BS><<<grid1(n), DetSmem<T, BS>::NT, DetSmem<T, BS>::bytes, st>>>(reg, chi, blist, ranks, nbh,
+                                                                              norm_bits, ind, chirange);
+}
 template <typename T>
 void launch_details(int Bs, const T* reg, const T* chi, const int32_t* blist, const int32_t* ranks,
                     const int32_t* nbh, int64_t n, const unsigned long long* norm_bits, double* ind,
                     double* chirange, cudaStream_t st) {
   if (n <= 0) return;
-  auto* bits = reinterpret_cast<unsigned long long*>(ind);
-  if (Bs == 17)
-    k_details<T, 17><<<grid1(5 * n), DetCfg<17>::NT, 0, st>>>(reg, chi, blist, ranks, nbh, norm_bits, bits, chirange);
-  else
-    k_details<T, 9><<<grid1(5 * n), DetCfg<9>::NT, 0, st>>>(reg, chi, blist, ranks, nbh, norm_bits, bits, chirange);
+  if (Bs == 17) launch_details_bs<T, 17>(reg, chi, blist, ranks, nbh, n, norm_bits, ind, chirange, st);
+  else launch_details_bs<T, 9>(reg, chi, blist, ranks, nbh, n, norm_bits, ind, chirange, st);
 }
 template <typename T>
 void launch_maxnorm(int Bs, const T* reg, const int32_t* blist, int64_t n, unsigned long long* out, cudaStream_t st) {
@@ -900,7 +942,8 @@ void launch_refine(int Bs, const T* src, T* dst, const int32_t* tasks, int64_t n
 template <typename T>
 void launch_coarsen(int Bs, const T* src, T* dst, const int32_t* tasks, int64_t n, cudaStream_t st) {
   if (n <= 0) return;
-  ACM_BS_DISPATCH(Bs, k_coarsen, <<<grid1(n), kNT, 0, st>>>(src, dst, tasks));
+  if (Bs == 17) k_coarsen<T, 17><<<grid1(4 * n), ColCfg<17>::NT, 0, st>>>(src, dst, tasks);
+  else k_coarsen<T, 9><<<grid1(4 * n), ColCfg<9>::NT, 0, st>>>(src, dst, tasks);
 }
 template <typename T>
 void launch_copy_blocks(int Bs, const T* src, T* dst, const int32_t* list, int stride, int64_t n, cudaStream_t st) {
@@ -917,7 +960,8 @@ template <typename T>
 void launch_mask(int Bs, T* chi, const int32_t* blist, const int32_t* ranks, int64_t n, const int4* binfo,
                  const PhysK& p, const MaskK& m, cudaStream_t st) {
   if (n <= 0) return;
-  ACM_BS_DISPATCH(Bs, k_mask, <<<grid1(n), kNT, 0, st>>>(chi, blist, ranks, binfo, p, m));
+  if (Bs == 17) k_mask<T, 17><<<grid1(n), ColCfg<17>::NT, 0, st>>>(chi, blist, ranks, binfo, p, m);
+  else k_mask<T, 9><<<grid1(n), ColCfg<9>::NT, 0, st>>>(chi, blist, ranks, binfo, p, m);
 }
 template <typename T>
 void launch_diag(int Bs, const T* reg, const T* chi, const int32_t* blist, int64_t n, double* out, cudaStream_t st) {

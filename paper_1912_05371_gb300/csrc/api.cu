@@ -529,7 +529,6 @@ acm_status indicators(acm_forest* f, std::vector<double>& ind, std::vector<doubl
       ranks = f->d_ranks;
     }
   }
-  CK(cudaMemsetAsync(f->d_ind, 0, f->order.size() * sizeof(double), f->st));
   acm::launch_details<T>(f->gp.Bs, reinterpret_cast<const T*>(f->U),
                          f->mask_on ? reinterpret_cast<const T*>(f->CHI) : nullptr, f->d_blist, ranks, f->d_nbh, n,
                          f->d_maxbits, f->d_ind, f->d_chir, f->st);

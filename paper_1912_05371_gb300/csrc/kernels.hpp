@@ -73,8 +73,7 @@ void launch_sync_ext(int Bs, const T* reg, T* out, int g, const int32_t* blist, 
 
 // Block indicators from the state itself (fine-wins applied): ind[rank], chirange[rank].
 // (ranks: the blocks to evaluate, nullptr = all n; results are written at their ranks;
-// norm_bits: the 4 component max norms as left by launch_maxnorm, read on the device; ind is
-// combined by an atomic maximum and must be zero at the evaluated ranks before the launch)
+// norm_bits: the 4 component max norms as left by launch_maxnorm, read on the device)
 template <typename T>
 void launch_details(int Bs, const T* reg, const T* chi, const int32_t* blist, const int32_t* ranks,
                     const int32_t* nbh, int64_t n, const unsigned long long* norm_bits, double* ind,

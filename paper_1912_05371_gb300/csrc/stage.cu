@@ -54,6 +54,10 @@ __device__ __forceinline__ void cp_async_elem(T* dst, const T* src) {
 }
 template <typename T>
 __device__ __forceinline__ T tmax(T a, T b) { return a > b ? a : b; }
+// Bulk prefetch of a contiguous range into L2 (address and size multiples of 16 bytes).
+__device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(p), "r"(bytes) : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
@@ -222,6 +226,23 @@ k_stage(const StageK<T> a, const TopoK tp, const PhysK ph, int* err) {
   };
 
   T nm[5] = {T(0), T(0), T(0), T(0), T(0)};   // stage 4: max |u|,|v|,|w|,|p|, |(u,v,w)|^2
+  // L2 prefetch of the planes an iteration reads kPf iterations ahead: one thread per array
+  // (stage input planes z + 4 + kPf, U, acc and chi planes z + kPf), one bulk request each
+  constexpr int kPf = 2;
+  constexpr unsigned kPlaneBytes = (unsigned)(L::PP * sizeof(T));
+  auto prefetch_planes = [&](int zin, int zo) {
+    if (tid < 4) {
+      if (zin <= M) prefetch_l2(inb + (size_t)tid * L::FS + (size_t)zin * L::PP, kPlaneBytes);
+    } else if (tid < 8) {
+      if ((STAGE == 2 || STAGE == 3) && zo <= M)
+        prefetch_l2(a.U + bo + (size_t)(tid - 4) * L::FS + (size_t)zo * L::PP, kPlaneBytes);
+    } else if (tid < 12) {
+      if (STAGE >= 2 && zo <= M) prefetch_l2(a.acc + bo + (size_t)(tid - 8) * L::FS + (size_t)zo * L::PP, kPlaneBytes);
+    } else if (tid == 12) {
+      if (ph.mask && zo <= M) prefetch_l2(a.chi + (size_t)slot * L::FS + (size_t)zo * L::PP, kPlaneBytes);
+    }
+  };
+  for (int k = 0; k < kPf; ++k) prefetch_planes(4 + k, k);
   T q[4][8];
 #pragma unroll
   for (int k = 0; k < 7; ++k)
@@ -241,6 +262,7 @@ k_stage(const StageK<T> a, const TopoK tp, const PhysK ph, int* err) {
     cp_async_wait_all();
     __syncthreads();
     if (z < M) issue_halos(z + 1, &buf[(z + 1) & 1][0][0]);
+    prefetch_planes(z + 4 + kPf, z + kPf);
     if (act) {
       if (z + 4 <= M + 3) {
 #pragma unroll
