@@ -18,7 +18,8 @@
  *    and must outlive the forest.
  *  - Streams: every device operation is enqueued on the cudaStream_t given at creation.  Calls
  *    that return host-visible results (dt, diagnostics, topology, indicators) synchronise
- *    that stream before returning.
+ *    that stream before returning; the others may return while their kernels still run, and
+ *    a device error then surfaces at the next synchronising call.
  *  - Pointers passed in are borrowed for the duration of the call only.
  *  - Layouts: "block order" is ascending (treecode, level); a field array is block-major,
  *    then component (u, v, w, p), then z, y, x with x fastest, Bs^3 points per block, in the

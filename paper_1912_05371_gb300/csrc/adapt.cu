@@ -443,7 +443,7 @@ __global__ void __launch_bounds__(kNT) k_maxnorm(const T* reg, const int32_t* bl
   if (threadIdx.x < 5) {
     T mk = T(0);
     for (int w = 0; w < kNT / 32; ++w) mk = red[threadIdx.x][w] > mk ? red[threadIdx.x][w] : mk;
-    const double d = threadIdx.x == 4 ? (double)sqrt(mk) : (double)mk;
+    const double d = threadIdx.x == 4 ? (double)tsqrt(mk) : (double)mk;
     atomicMax(out + threadIdx.x, (unsigned long long)__double_as_longlong(d));
   }
 }
@@ -697,7 +697,7 @@ __global__ void __launch_bounds__(kNT) k_ic(T* reg, const int32_t* blist, const 
   const int rank = ranks ? ranks[blockIdx.x] : (int)blockIdx.x;
   const int slot = blist[rank];
   const int4 bi = binfo[rank];
-  const double h = ph.root_len / ((double)(1 << bi.x) * M);
+  const double h = ph.h[bi.x];
   for (int i = threadIdx.x; i < BS * BS * BS; i += kNT) {
     const int ix = i % BS, iy = (i / BS) % BS, iz = i / (BS * BS);
     const double X = coord(ph, bi, 0, ix, M, h), Y = coord(ph, bi, 1, iy, M, h), Z = coord(ph, bi, 2, iz, M, h);
@@ -733,32 +733,38 @@ __global__ void __launch_bounds__(ColCfg<BS>::NT) k_mask(T* chi, const int32_t* 
   const int rank = ranks ? ranks[blockIdx.x] : (int)blockIdx.x;
   const int slot = blist[rank];
   const int4 bi = binfo[rank];
-  const double h = ph.root_len / ((double)(1 << bi.x) * M);
+  const double h = ph.h[bi.x];
   // A block that lies entirely farther than 40 delta from the sphere surface has tanh(d/delta)
   // = +-1 exactly in double precision at all its points (1 - tanh(40) < 1e-34): chi is exactly
   // 0 or 1 there and needs no transcendental.  Blocks on the periodic seam are evaluated fully.
-  int uniform = -1;
-  if (m.kind == 1) {
-    const double lo[3] = {(double)bi.y * M * h, (double)bi.z * M * h, (double)bi.w * M * h};
-    const double L[3] = {ph.nroot[0] * ph.root_len, ph.nroot[1] * ph.root_len, ph.nroot[2] * ph.root_len};
-    bool seam = false;
-    double dmin2 = 0.0, dmax2 = 0.0;
-    for (int a = 0; a < 3; ++a) {
-      const double hi = lo[a] + M * h;
-      if (hi >= L[a]) seam = true;
-      const double c = m.p[a];
-      const double near = c < lo[a] ? lo[a] - c : (c > hi ? c - hi : 0.0);
-      const double far = fmax(fabs(c - lo[a]), fabs(hi - c));
-      dmin2 += near * near;
-      dmax2 += far * far;
+  // One thread decides (FP64), the block reads the answer.
+  __shared__ int s_uniform;
+  if (threadIdx.x == 0) {
+    int uniform = 0;
+    if (m.kind == 1) {
+      uniform = -1;
+      const double lo[3] = {(double)bi.y * M * h, (double)bi.z * M * h, (double)bi.w * M * h};
+      const double L[3] = {ph.nroot[0] * ph.root_len, ph.nroot[1] * ph.root_len, ph.nroot[2] * ph.root_len};
+      bool seam = false;
+      double dmin2 = 0.0, dmax2 = 0.0;
+      for (int a = 0; a < 3; ++a) {
+        const double hi = lo[a] + M * h;
+        if (hi >= L[a]) seam = true;
+        const double c = m.p[a];
+        const double near = c < lo[a] ? lo[a] - c : (c > hi ? c - hi : 0.0);
+        const double far = fmax(fabs(c - lo[a]), fabs(hi - c));
+        dmin2 += near * near;
+        dmax2 += far * far;
+      }
+      if (!seam) {
+        if (sqrt(dmin2) - m.p[3] > 40.0 * m.p[4]) uniform = 0;
+        else if (sqrt(dmax2) - m.p[3] < -40.0 * m.p[4]) uniform = 1;
+      }
     }
-    if (!seam) {
-      if (sqrt(dmin2) - m.p[3] > 40.0 * m.p[4]) uniform = 0;
-      else if (sqrt(dmax2) - m.p[3] < -40.0 * m.p[4]) uniform = 1;
-    }
-  } else {
-    uniform = 0;
+    s_uniform = uniform;
   }
+  __syncthreads();
+  const int uniform = s_uniform;
   const int tid = threadIdx.x;
   if (tid >= BS * BS) return;
   const int ix = tid % BS, iy = tid / BS;
@@ -780,11 +786,11 @@ __global__ void __launch_bounds__(ColCfg<BS>::NT) k_mask(T* chi, const int32_t* 
 #pragma unroll
   for (int iz = 0; iz < BS; ++iz) {
     const T dz = T(lattice(ph, bi, 2, iz, M)) * hT - c2;
-    const T d = sqrt(dx * dx + dy * dy + dz * dz) - R;
+    const T d = tsqrt(dx * dx + dy * dy + dz * dz) - R;
     T c;
     if (d > cut) c = T(0);
     else if (d < -cut) c = T(1);
-    else c = T(0.5) * (T(1) - tanh(d / dl));
+    else c = T(0.5) * (T(1) - ttanh(d / dl));
     out[L::idx(ix, iy, iz)] = c;
   }
 }

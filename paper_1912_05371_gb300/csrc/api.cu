@@ -462,49 +462,56 @@ acm_status refine_all(acm_forest* f) {
   f->norms_fresh = false;
   acm::Forest& fo = *f->fo;
   const double t0 = now_ms();
-  std::vector<BoxKey> parents;
-  std::vector<int32_t> prank;
+  std::vector<int32_t> prank, pslot;
   for (size_t r = 0; r < f->order.size(); ++r)
     if (f->order[r].J < fo.Jmax) {
-      parents.push_back(f->order[r]);
       prank.push_back((int32_t)r);
+      pslot.push_back(f->blist[r]);
     }
-  if (parents.empty()) return ACM_OK;
-  if ((int64_t)parents.size() * 7 > fo.n_free())
-    return fail(f, ACM_ECAPACITY, "block pool too small to refine");
-  // synchronise U (fine wins), keep a copy of it as the source of the predictions
-  acm_status s = fine_wins<T>(f, reinterpret_cast<T*>(f->U));
-  if (s) return s;
-  s = snapshot_state<T>(f);
-  if (s) return s;
-  std::vector<BoxKey> kids;
-  kids.reserve(parents.size() * 8);
-  for (size_t i = 0; i < parents.size(); ++i)
-    for (int c = 0; c < 8; ++c) kids.push_back(acm::Forest::child(parents[i], c));
-  // block order of the refined grid: every parent replaced in place by its children 0..7
-  std::vector<BoxKey> order2;
-  order2.reserve(f->order.size() + 7 * parents.size());
-  for (const BoxKey& b : f->order) {
-    if (b.J < fo.Jmax)
-      for (int c = 0; c < 8; ++c) order2.push_back(acm::Forest::child(b, c));
-    else
-      order2.push_back(b);
-  }
+  if (prank.empty()) return ACM_OK;
+  // children in ascending key order (each parent's children 0..7 in turn) take the lowest free
+  // slots once the parents' slots are released
   std::vector<int32_t> new_slot;
-  if (!fo.apply_pass(parents, kids, &new_slot, true)) return fail(f, ACM_ECAPACITY, "block pool exhausted");
-  std::vector<int32_t> tasks(parents.size() * 9);
-  for (size_t i = 0; i < parents.size(); ++i) {
+  if (!fo.take_slots(pslot, prank.size() * 8, &new_slot))
+    return fail(f, ACM_ECAPACITY, "block pool too small to refine");
+  std::vector<int32_t> tasks(prank.size() * 9);
+  for (size_t i = 0; i < prank.size(); ++i) {
     tasks[9 * i] = prank[i];
     for (int c = 0; c < 8; ++c) tasks[9 * i + 1 + c] = new_slot[8 * i + c];
   }
   f->host_tree_ms += now_ms() - t0;
+  // synchronise U (fine wins), keep a copy of it as the source of the predictions, refine; the
+  // old-grid tables are still on the device (the upload below is ordered after these kernels)
+  acm_status s = fine_wins<T>(f, reinterpret_cast<T*>(f->U));
+  if (s) return s;
+  s = snapshot_state<T>(f);
+  if (s) return s;
   CK(cudaMemcpyAsync(f->d_reft, tasks.data(), tasks.size() * sizeof(int32_t), cudaMemcpyHostToDevice, f->st));
-  // old-grid tables are still on the device: the upload below is ordered after this kernel
   acm::launch_refine<T>(f->gp.Bs, reinterpret_cast<const T*>(f->YA), reinterpret_cast<T*>(f->U),
-                        reinterpret_cast<const int32_t*>(f->d_reft), (int64_t)parents.size(), f->d_blist, f->d_nbh,
+                        reinterpret_cast<const int32_t*>(f->d_reft), (int64_t)prank.size(), f->d_blist, f->d_nbh,
                         f->st);
   CKL();
   ++f->launches;
+  // the host-side tree and the block order of the refined grid, while the GPU refines: every
+  // parent replaced in place by its children 0..7
+  const double t1 = now_ms();
+  std::vector<BoxKey> parents, kids, order2;
+  parents.reserve(prank.size());
+  kids.reserve(prank.size() * 8);
+  order2.reserve(f->order.size() + 7 * prank.size());
+  for (const BoxKey& b : f->order) {
+    if (b.J < fo.Jmax) {
+      parents.push_back(b);
+      for (int c = 0; c < 8; ++c) {
+        kids.push_back(acm::Forest::child(b, c));
+        order2.push_back(kids.back());
+      }
+    } else {
+      order2.push_back(b);
+    }
+  }
+  fo.update_leaves(parents, kids, new_slot);
+  f->host_tree_ms += now_ms() - t1;
   s = upload_topology(f, &order2);   // synchronises the stream (tasks buffer lifetime)
   if (s) return s;
   return eval_mask<T>(f, &new_slot);
@@ -616,15 +623,33 @@ acm_status coarsen(acm_forest* f, int64_t* n_blocks, int* n_passes) {
       f->host_tree_ms += now_ms() - th;
       break;
     }
-    std::vector<BoxKey> removed;
-    std::vector<std::array<int32_t, 8>> kid_slots(groups.size());
+    // parents (ascending keys) take the lowest free slots once the children's are released
+    std::vector<int32_t> freed(groups.size() * 8);
     for (size_t g = 0; g < groups.size(); ++g)
-      for (int c = 0; c < 8; ++c) {
-        kid_slots[g][c] = f->blist[gstart[g] + c];
-        removed.push_back(f->order[gstart[g] + c]);
-      }
+      for (int c = 0; c < 8; ++c) freed[8 * g + c] = f->blist[gstart[g] + c];
     std::vector<int32_t> new_slot;
-    if (!fo.apply_pass(removed, groups, &new_slot, true)) return fail(f, ACM_ECAPACITY, "block pool exhausted");
+    if (!fo.take_slots(freed, groups.size(), &new_slot)) return fail(f, ACM_ECAPACITY, "block pool exhausted");
+    std::vector<int32_t> tasks(groups.size() * 9);
+    for (size_t g = 0; g < groups.size(); ++g) {
+      tasks[9 * g] = new_slot[g];
+      for (int c = 0; c < 8; ++c) tasks[9 * g + 1 + c] = freed[8 * g + c];
+    }
+    // the parents are decimated into YA (a parent may take a slot freed by a child that is still
+    // being read), then copied into U
+    CK(cudaMemcpyAsync(f->d_crst, tasks.data(), tasks.size() * 4, cudaMemcpyHostToDevice, f->st));
+    acm::launch_coarsen<T>(f->gp.Bs, reinterpret_cast<const T*>(f->U), reinterpret_cast<T*>(f->YA), f->d_crst,
+                           (int64_t)groups.size(), f->st);
+    CKL();
+    acm::launch_copy_blocks<T>(f->gp.Bs, reinterpret_cast<const T*>(f->YA), reinterpret_cast<T*>(f->U), f->d_crst, 9,
+                               (int64_t)groups.size(), f->st);
+    CKL();
+    f->launches += 2;
+    // the host-side tree while the GPU merges
+    std::vector<BoxKey> removed;
+    removed.reserve(groups.size() * 8);
+    for (size_t g = 0; g < groups.size(); ++g)
+      for (int c = 0; c < 8; ++c) removed.push_back(f->order[gstart[g] + c]);
+    fo.update_leaves(removed, groups, new_slot);
     // block order of the merged grid: each group's 8 consecutive children replaced by the parent
     std::vector<BoxKey> order2;
     order2.reserve(n);
@@ -637,22 +662,7 @@ acm_status coarsen(acm_forest* f, int64_t* n_blocks, int* n_passes) {
         order2.push_back(f->order[r++]);
       }
     }
-    std::vector<int32_t> tasks(groups.size() * 9);
-    for (size_t g = 0; g < groups.size(); ++g) {
-      tasks[9 * g] = new_slot[g];
-      for (int c = 0; c < 8; ++c) tasks[9 * g + 1 + c] = kid_slots[g][c];
-    }
     f->host_tree_ms += now_ms() - th;
-    // the parents are decimated into YA (a parent may take a slot freed by a child that is still
-    // being read), then copied into U
-    CK(cudaMemcpyAsync(f->d_crst, tasks.data(), tasks.size() * 4, cudaMemcpyHostToDevice, f->st));
-    acm::launch_coarsen<T>(f->gp.Bs, reinterpret_cast<const T*>(f->U), reinterpret_cast<T*>(f->YA), f->d_crst,
-                           (int64_t)groups.size(), f->st);
-    CKL();
-    acm::launch_copy_blocks<T>(f->gp.Bs, reinterpret_cast<const T*>(f->YA), reinterpret_cast<T*>(f->U), f->d_crst, 9,
-                               (int64_t)groups.size(), f->st);
-    CKL();
-    f->launches += 2;
     s = upload_topology(f, &order2);
     if (s) return s;
     s = eval_mask<T>(f, &new_slot);
@@ -728,6 +738,7 @@ void fill_phys(acm_forest* f) {
   k.a2 = -1.0 / 12.0 - 4.0 * a3;
   k.a3 = a3;
   k.mask = f->mask_on ? 1 : 0;
+  for (int J = 0; J <= acm::kMaxLevel; ++J) k.h[J] = h_of(f, J);
 }
 
 #define DISPATCH(f, fn, ...) ((f)->gp.precision == 64 ? fn<double>(__VA_ARGS__) : fn<float>(__VA_ARGS__))
@@ -921,18 +932,12 @@ acm_status acm_rk4_step(acm_forest* f, double dt, double* dt_used) {
 
 acm_status acm_refine_all(acm_forest* f) {
   if (!f) return ACM_EINVAL;
-  acm_status s = DISPATCH(f, refine_all, f);
-  if (s) return s;
-  CK(cudaStreamSynchronize(f->st));
-  return ACM_OK;
+  return DISPATCH(f, refine_all, f);
 }
 
 acm_status acm_coarsen(acm_forest* f, int64_t* n_blocks, int* n_passes) {
   if (!f) return ACM_EINVAL;
-  acm_status s = DISPATCH(f, coarsen, f, n_blocks, n_passes);
-  if (s) return s;
-  CK(cudaStreamSynchronize(f->st));
-  return ACM_OK;
+  return DISPATCH(f, coarsen, f, n_blocks, n_passes);
 }
 
 acm_status acm_step(acm_forest* f, double dt, double* dt_used, int64_t* n_blocks) {

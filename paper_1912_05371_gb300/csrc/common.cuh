@@ -118,6 +118,13 @@ __device__ __forceinline__ bool direct_value(const T* __restrict__ reg, const in
   return true;
 }
 
+// Square root and tanh in the argument's own precision (float arguments never take the double
+// routines, which run on the much slower FP64 pipe).
+__device__ __forceinline__ float tsqrt(float x) { return sqrtf(x); }
+__device__ __forceinline__ double tsqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ float ttanh(float x) { return tanhf(x); }
+__device__ __forceinline__ double ttanh(double x) { return tanh(x); }
+
 // Squared velocity magnitude with one fixed rounding sequence, so every kernel that takes the
 // max norm of (u, v, w) gets bitwise the same value (sqrt of the max = max of the sqrt).
 template <typename T>

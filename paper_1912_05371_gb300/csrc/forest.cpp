@@ -171,6 +171,30 @@ bool Forest::apply_pass(const std::vector<BoxKey>& removed, const std::vector<Bo
   return true;
 }
 
+bool Forest::take_slots(const std::vector<int32_t>& freed, size_t n, std::vector<int32_t>* slots) {
+  if ((int64_t)n - (int64_t)freed.size() > nfree_) return false;
+  for (int32_t s : freed) {
+    free_[s >> 6] |= 1ull << (s & 63);
+    ++nfree_;
+  }
+  slots->resize(n);
+  size_t w = 0;
+  for (size_t i = 0; i < n; ++i) {
+    while (free_[w] == 0) ++w;
+    const int b = __builtin_ctzll(free_[w]);
+    free_[w] &= free_[w] - 1;
+    --nfree_;
+    (*slots)[i] = (int32_t)(w * 64 + b);
+  }
+  return true;
+}
+
+void Forest::update_leaves(const std::vector<BoxKey>& removed, const std::vector<BoxKey>& created,
+                           const std::vector<int32_t>& slots) {
+  for (const BoxKey& k : removed) leaves.erase(k);
+  for (size_t i = 0; i < created.size(); ++i) leaves.put(created[i], slots[i]);
+}
+
 BoxStatus Forest::box_status(int J, int64_t x, int64_t y, int64_t z) const {
   BoxStatus st;
   st.type = BOX_NONE;

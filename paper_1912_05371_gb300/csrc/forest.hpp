@@ -115,6 +115,13 @@ class Forest {
   // the pool is too small.  created_slots[i] is the slot of created[i].
   bool apply_pass(const std::vector<BoxKey>& removed, const std::vector<BoxKey>& created,
                   std::vector<int32_t>* created_slots, bool created_sorted = false);
+  // The same pass in two halves, for callers that know the removed leaves' slots and hold the
+  // created boxes in ascending key order: take_slots releases `freed` and assigns the n lowest
+  // free slots in ascending order (false, and nothing changed, if the pool is too small);
+  // update_leaves then records the pass in the leaf map.
+  bool take_slots(const std::vector<int32_t>& freed, size_t n, std::vector<int32_t>* slots);
+  void update_leaves(const std::vector<BoxKey>& removed, const std::vector<BoxKey>& created,
+                     const std::vector<int32_t>& slots);
 
   BoxStatus box_status(int J, int64_t x, int64_t y, int64_t z) const;
   bool is_graded() const;

@@ -7,6 +7,8 @@
 namespace acm {
 
 // Per-launch model constants (Sec. 2.1-2.3), in double; kernels convert to their precision.
+constexpr int kMaxLevel = 18;   // finest level a grid may use
+
 struct PhysK {
   double nu, c0sq, inv_ceta, cgamma, inv_csp;
   double uinf[3], pinf;
@@ -15,6 +17,7 @@ struct PhysK {
   double root_len;
   int nroot[3];
   double a1, a2, a3;        // first-derivative coefficients
+  double h[kMaxLevel + 1];  // grid spacing of each level, root_len / (2^J (Bs-1))
 };
 
 // Device topology: pointers into the pool, all indexed by rank (position in block order).
@@ -34,6 +37,8 @@ struct StageConst {
   T nu, c0sq, cgam, inv_ceta, inv_csp;
   T uinf[3], pinf;
   T c_acc, c_out;           // RK coefficients of the stage
+  T ih[kMaxLevel + 1];      // 1 / h_J
+  T ih2[kMaxLevel + 1];     // 1 / (12 h_J^2)
 };
 
 // Stage of the fused RK4 update (Sec. 2.3).  in: the stage state (synchronised); U: the

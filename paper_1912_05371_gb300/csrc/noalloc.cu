@@ -25,6 +25,8 @@ void* g_scratch[kMaxDevices] = {};
 
 template <typename T>
 __device__ __forceinline__ T absval(T v) { return v < T(0) ? -v : v; }
+__device__ __forceinline__ float root(float v) { return sqrtf(v); }
+__device__ __forceinline__ double root(double v) { return sqrt(v); }
 
 // One CTA per block of the dense block-order array (component-major, then z, y, x).
 template <typename T>
@@ -40,7 +42,7 @@ __global__ void __launch_bounds__(kNT) k_block_max(const T* __restrict__ fields,
       const T a = absval(v[f]);
       m[f] = a > m[f] ? a : m[f];
     }
-    const T mag = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    const T mag = root(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
     m[4] = mag > m[4] ? mag : m[4];
   }
   __shared__ double red[5][kNT / 32];

@@ -138,22 +138,24 @@ k_stage(const StageK<T> a, const TopoK tp, const PhysK ph, int* err) {
     fs[F][j] = s;
     if (j == 0) ftype[F] = ty;
   }
-  const double h = ph.root_len / ((double)(1 << bi.x) * M);
   if (ph.sponge && tid < 3 * BS) {
+    const double h = ph.h[bi.x];
     const int ax = tid / BS, i = tid % BS;
     const int g = ax == 0 ? bi.y : (ax == 1 ? bi.z : bi.w);
     const long long N = ((long long)ph.nroot[ax] << bi.x) * M;
     long long gi = (long long)g * M + i;        // in [0, N]; the seam x = L is taken as 0
     if (gi >= N) gi -= N;
     const double c = (double)gi * h;
-    const double dist = fmin(c, ph.sp_L[ax] - c);
-    sp[ax][i] = T(0.5 * (1.0 - tanh((dist - ph.sp_width) / ph.sp_delta)));
+    // the profile in the field precision (FP32 fields keep tanh off the FP64 pipe)
+    const T dist = T(fmin(c, ph.sp_L[ax] - c));
+    sp[ax][i] = T(0.5) * (T(1) - ttanh((dist - T(ph.sp_width)) / T(ph.sp_delta)));
   }
   __syncthreads();
 
-  const T ih = T(1.0 / h), ih2 = T(1.0 / (12.0 * h * h));
-  // model and RK constants are read from the kernel parameters (constant bank), not registers
+  // model and RK constants are read from the kernel parameters (constant bank), not registers;
+  // so are the level's 1/h and 1/(12 h^2) (no per-thread FP64 division)
   const StageConst<T>& kc = a.kc;
+  const T ih = kc.ih[bi.x], ih2 = kc.ih2[bi.x];
   const bool act = tid < BS * BS;
   const int x = act ? tid % BS : 0, y = act ? tid / BS : 0;
   (void)err;   // this kernel has no waits that can expire
@@ -364,7 +366,7 @@ k_stage(const StageK<T> a, const TopoK tp, const PhysK ph, int* err) {
     if (tid < 5) {
       T m = T(0);
       for (int w = 0; w < NT / 32; ++w) m = red[tid * (NT / 32) + w] > m ? red[tid * (NT / 32) + w] : m;
-      const double d = tid == 4 ? (double)sqrt(m) : (double)m;
+      const double d = tid == 4 ? (double)tsqrt(m) : (double)m;
       atomicMax(a.norms + tid, (unsigned long long)__double_as_longlong(d));
     }
   }
@@ -396,6 +398,10 @@ void launch_stage(int stage, int Bs, const StageK<T>& s, const TopoK& t, const P
   for (int i = 0; i < 3; ++i) c.uinf[i] = T(p.uinf[i]);
   c.pinf = T(p.pinf);
   c.c_acc = T(s.c_acc); c.c_out = T(s.c_out);
+  for (int J = 0; J <= kMaxLevel; ++J) {
+    c.ih[J] = T(1.0 / p.h[J]);
+    c.ih2[J] = T(1.0 / (12.0 * p.h[J] * p.h[J]));
+  }
   if (Bs == 17) launch_stage_bs<T, 17>(stage, a, t, p, err, st);
   else launch_stage_bs<T, 9>(stage, a, t, p, err, st);
 }

@@ -128,6 +128,22 @@ def test_rk4_steps_match_oracle(A, prec, Bs, seed):
     assert max(err) < TOL[prec], err
 
 
+@pytest.mark.parametrize("prec,Bs", [(64, 9), (32, 17), (32, 9)])
+def test_mask_matches_oracle(A, prec, Bs):
+    """chi of every block (smoothed sphere, Sec. 2.2) against the oracle's FP64 values."""
+    leaves = random_graded_leaves(16, nroot=(2, 1, 1), J0=1, Jmax=3, n_target=70)
+    grid = _grid(Bs=Bs, precision=prec)
+    mask = (0.9, 0.5, 0.5, 0.2, 0.02)
+    f, S = _pair(A, grid, _phys(), leaves, fn_seed=16, mask=mask)
+    chi = f.read_mask().astype(np.float64)
+    ref = np.stack([S.chi[S.fo.leaves[l]] for l in S.fo.sorted_leaves()])
+    assert chi.shape == ref.shape
+    # FP32: the distance to the surface rounds at about 1e-7 of the box size, 5e-6 of delta in
+    # the argument of tanh, so chi (in [0, 1]) is good to about half of that
+    assert np.abs(chi - ref).max() <= (1e-14 if prec == 64 else 1e-5)
+    assert np.all((chi >= 0.0) & (chi <= 1.0))
+
+
 @pytest.mark.parametrize("prec", [64, 32])
 def test_indicators_match_oracle(A, prec):
     leaves = random_graded_leaves(14, nroot=(2, 1, 1), J0=1, Jmax=3, n_target=70)
