@@ -4,6 +4,8 @@
 // indicator: largest detail normalised per component by its global max norm), Sec. 3.5
 // (refine by prediction, coarsen by merging sister blocks), Sec. 4.2 (ghost synchronisation:
 // restrict or predict, then copy), Sec. 2.2 (smoothed mask, force by midpoint rule).
+#include <algorithm>
+
 #include "common.cuh"
 #include "kernels.hpp"
 
@@ -36,13 +38,12 @@ __device__ __forceinline__ void gather(T* dst, int n, F&& val) {
 
 // ---- (1) fine wins: block boundary points held by a finer neighbour take its value -----------
 // task = (rank, box index d of a REFINED neighbour box).  Points of the block's boundary lying
-// in box d: coordinate 0 / M where d is -1 / +1, the whole range where d is 0.
+// in box d: coordinate 0 / M where d is -1 / +1, the whole range where d is 0.  The CTAs walk
+// the task list (its length is on the device).
 template <typename T, int BS>
-__global__ void __launch_bounds__(kNT) k_fine_wins(T* reg, const int2* tasks, const int32_t* nbh_all,
-                                                    const int32_t* blist) {
+__device__ __forceinline__ void fine_wins_task(T* reg, const int2 tk, const int32_t* nbh_all, const int32_t* blist) {
   using L = Lay<T, BS>;
   constexpr int M = L::M;
-  const int2 tk = tasks[blockIdx.x];
   const int* nbh = nbh_all + (size_t)tk.x * kNbhStride;
   const int me = blist[tk.x];
   const int d = tk.y;
@@ -73,8 +74,16 @@ __global__ void __launch_bounds__(kNT) k_fine_wins(T* reg, const int2* tasks, co
   }
 }
 
+template <typename T, int BS>
+__global__ void __launch_bounds__(kNT) k_fine_wins(T* reg, const int2* tasks, const int32_t* ntasks,
+                                                    const int32_t* nbh_all, const int32_t* blist) {
+  const int nt = *ntasks;
+  for (int t = blockIdx.x; t < nt; t += gridDim.x) fine_wins_task<T, BS>(reg, tasks[t], nbh_all, blist);
+}
+
 // ---- (2) coarse-face halo slabs ------------------------------------------------------------------
-// task = (rank, face F, slab index, -); one CTA per task, all four components.  The 3 x Bs x Bs
+// task = (rank, face F, slab index, -); a CTA per task at a time, all four components (the CTAs
+// walk the task list, whose length is on the device).  The 3 x Bs x Bs
 // halo points beyond face F take the value of the finest leaf holding them, else the tensor DD-4
 // prediction from the coarse lattice (Sec. 3.1).  Only points on the face's tangential boundary
 // lines (t0 or t1 = 0 or M) can be held by a leaf of the block's level or finer; all others lie
@@ -100,7 +109,7 @@ struct SlabSmem {
 
 template <typename T, int BS>
 __global__ void __launch_bounds__(SlabSmem<T, BS>::NT) k_coarse_slabs(const T* reg, T* slab, const int4* tasks,
-                                                                       const int32_t* nbh_all) {
+                                                                       const int32_t* ntasks, const int32_t* nbh_all) {
   using L = Lay<T, BS>;
   using S = SlabSmem<T, BS>;
   constexpr int M = L::M, NT = S::NT, NC = S::NC, NN = S::NN;
@@ -111,7 +120,10 @@ __global__ void __launch_bounds__(SlabSmem<T, BS>::NT) k_coarse_slabs(const T* r
   T* B = A + S::A;
   int* nbh = reinterpret_cast<int*>(B + S::B);
   const int tid = threadIdx.x;
-  const int4 tk = tasks[blockIdx.x];
+  const int nt = *ntasks;
+  for (int task = blockIdx.x; task < nt; task += gridDim.x) {
+  const int4 tk = tasks[task];
+  __syncthreads();                                  // previous task done with shared memory
   for (int i = tid; i < kNbhStride; i += NT) nbh[i] = nbh_all[(size_t)tk.x * kNbhStride + i];
   __syncthreads();
   const int F = tk.y, ax = F >> 1;
@@ -208,6 +220,7 @@ __global__ void __launch_bounds__(SlabSmem<T, BS>::NT) k_coarse_slabs(const T* r
         slab[((((size_t)tk.z * 4 + f) * 3 + (l - 1)) * BS + t1) * BS + t0] = v;
       }
     }
+  }
   }
 }
 
@@ -879,25 +892,30 @@ LayoutInfo layout_info(int precision, int Bs) {
   } while (0)
 
 template <typename T>
-void launch_fine_wins(int Bs, T* reg, const int2* tasks, int64_t n, const int32_t* nbh, const int32_t* blist,
-                      cudaStream_t st) {
-  if (n <= 0) return;
-  ACM_BS_DISPATCH(Bs, k_fine_wins, <<<grid1(n), kNT, 0, st>>>(reg, tasks, nbh, blist));
+void launch_fine_wins(int Bs, T* reg, const int2* tasks, const int32_t* ntasks, int64_t max_tasks,
+                      const int32_t* nbh, const int32_t* blist, cudaStream_t st) {
+  if (max_tasks <= 0) return;
+  const int64_t g = std::min<int64_t>(max_tasks, 8 * (int64_t)sm_count());
+  ACM_BS_DISPATCH(Bs, k_fine_wins, <<<grid1(g), kNT, 0, st>>>(reg, tasks, ntasks, nbh, blist));
 }
 template <typename T, int BS>
-void launch_coarse_slabs_bs(const T* reg, T* slab, const int4* tasks, int64_t n, const int32_t* nbh, cudaStream_t st) {
+void launch_coarse_slabs_bs(const T* reg, T* slab, const int4* tasks, const int32_t* ntasks, int64_t max_tasks,
+                            const int32_t* nbh, cudaStream_t st) {
   static bool attr = false;             // opt in to more than 48 KB of dynamic shared memory once
   if (!attr) {
     cudaFuncSetAttribute(k_coarse_slabs<T, BS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SlabSmem<T, BS>::bytes);
     attr = true;
   }
-  k_coarse_slabs<T, BS><<<grid1(n), SlabSmem<T, BS>::NT, SlabSmem<T, BS>::bytes, st>>>(reg, slab, tasks, nbh);
+  // resident CTAs: 3 per SM (register-limited) for Bs = 17
+  const int64_t g = std::min<int64_t>(max_tasks, 3 * (int64_t)sm_count());
+  k_coarse_slabs<T, BS><<<grid1(g), SlabSmem<T, BS>::NT, SlabSmem<T, BS>::bytes, st>>>(reg, slab, tasks, ntasks, nbh);
 }
 template <typename T>
-void launch_coarse_slabs(int Bs, const T* reg, T* slab, const int4* tasks, int64_t n, const int32_t* nbh, cudaStream_t st) {
-  if (n <= 0) return;
-  if (Bs == 17) launch_coarse_slabs_bs<T, 17>(reg, slab, tasks, n, nbh, st);
-  else launch_coarse_slabs_bs<T, 9>(reg, slab, tasks, n, nbh, st);
+void launch_coarse_slabs(int Bs, const T* reg, T* slab, const int4* tasks, const int32_t* ntasks, int64_t max_tasks,
+                         const int32_t* nbh, cudaStream_t st) {
+  if (max_tasks <= 0) return;
+  if (Bs == 17) launch_coarse_slabs_bs<T, 17>(reg, slab, tasks, ntasks, max_tasks, nbh, st);
+  else launch_coarse_slabs_bs<T, 9>(reg, slab, tasks, ntasks, max_tasks, nbh, st);
 }
 template <typename T>
 void launch_sync_ext(int Bs, const T* reg, T* out, int g, const int32_t* list, int64_t n, const int32_t* nbh, int by_rank, cudaStream_t st) {
@@ -988,8 +1006,8 @@ void launch_scatter(int Bs, const T* dense, T* reg, const int32_t* blist, int64_
 }
 
 #define ACM_INST(T)                                                                                        \
-  template void launch_fine_wins<T>(int, T*, const int2*, int64_t, const int32_t*, const int32_t*, cudaStream_t);          \
-  template void launch_coarse_slabs<T>(int, const T*, T*, const int4*, int64_t, const int32_t*, cudaStream_t); \
+  template void launch_fine_wins<T>(int, T*, const int2*, const int32_t*, int64_t, const int32_t*, const int32_t*, cudaStream_t); \
+  template void launch_coarse_slabs<T>(int, const T*, T*, const int4*, const int32_t*, int64_t, const int32_t*, cudaStream_t); \
   template void launch_sync_ext<T>(int, const T*, T*, int, const int32_t*, int64_t, const int32_t*, int, cudaStream_t); \
   template void launch_details<T>(int, const T*, const T*, const int32_t*, const int32_t*, const int32_t*, int64_t, const unsigned long long*, double*, double*, cudaStream_t); \
   template void launch_maxnorm<T>(int, const T*, const int32_t*, int64_t, unsigned long long*, cudaStream_t); \

@@ -60,22 +60,31 @@ struct acm_forest {
   double* d_ind = nullptr;
   double* d_chir = nullptr;
   double* d_diag = nullptr;
-  int* d_err = nullptr;            // set by kernels whose bounded waits expired
-  int* h_err = nullptr;            // pinned copy, refreshed after every RK4 step
+  int* d_err = nullptr;            // error bits set by kernels (see device_error)
+  int* h_err = nullptr;            // pinned copy, refreshed after every RK4 step and every
+                                   // indicator evaluation
+  acm::LeafEntry* d_leaves = nullptr;   // byte copy of the host leaf map (topology kernels)
+  uint8_t* d_finer = nullptr;      // per rank: a neighbour box is refined
+  uint32_t* d_fwmask = nullptr;    // per rank scratch of the topology build
+  uint32_t* d_slabmask = nullptr;
+  int32_t* d_fwoff = nullptr;
+  int32_t* d_slaboff = nullptr;
+  int32_t* d_counts = nullptr;     // [0] fine-wins tasks, [1] coarse-face slabs
 
-  // host mirrors of the current topology (pinned: built in place, then copied)
+  // host side of the current topology; the leaf map and the staging arrays are pinned and
+  // copied to the device as they are (the neighbourhood tables are built there)
   std::vector<BoxKey> order;
   std::vector<int32_t> blist;
   std::vector<int32_t> slot_rank;     // slot -> rank (-1: free)
   std::vector<double> ind_slot, chr_slot;   // indicators of the current coarsening, by slot
-  int32_t* h_nbh = nullptr;
+  acm::LeafMap::Entry* h_leaves = nullptr;
+  size_t leaf_cap = 0;
   int4* h_binfo = nullptr;
   int32_t* h_blist = nullptr;
-  int32_t* h_slabidx = nullptr;
-  int2* h_fw = nullptr;
-  int4* h_slabt = nullptr;
+  uint8_t* h_finer = nullptr;
   void* h_pinned = nullptr;
-  int64_t n_fw = 0, n_slab = 0;
+  cudaEvent_t ev_topo = nullptr;      // after the copies of the last topology upload
+  bool topo_pending = false;
   int Jtop = 0;
 
   bool mask_on = false;
@@ -117,10 +126,13 @@ acm_status fail(acm_forest* f, acm_status s, const std::string& msg) {
 
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
-// After a stream synchronisation: did a kernel's bounded wait expire?
+// After a stream synchronisation that refreshed h_err: bit 0 a kernel's bounded wait expired,
+// bit 1 the device topology build met an ungraded grid, bit 2 the leaf table was full.
 acm_status device_error(acm_forest* f) {
-  if (f->h_err && *f->h_err) return fail(f, ACM_ETIMEOUT, "a bounded wait inside a kernel expired");
-  return ACM_OK;
+  if (!f->h_err || !*f->h_err) return ACM_OK;
+  if (*f->h_err & 1) return fail(f, ACM_ETIMEOUT, "a bounded wait inside a kernel expired");
+  if (*f->h_err & 2) return fail(f, ACM_EGRADING, "grid is not 2:1 graded");
+  return fail(f, ACM_ECUDA, "leaf table probe exceeded its capacity");
 }
 
 double now_ms() {
@@ -187,12 +199,21 @@ size_t carve(acm_forest* f, const acm_grid_params* g, char* base) {
   double* chir = c.take<double>(nb * 8);
   double* diag = c.take<double>(nb * 4 * 8);
   int* errf = c.take<int>(16);
+  acm::LeafEntry* leaves = c.take<acm::LeafEntry>(acm::LeafMap::capacity_for(g->max_blocks) * sizeof(acm::LeafEntry));
+  uint8_t* finer = c.take<uint8_t>(nb);
+  uint32_t* fwmask = c.take<uint32_t>(nb * 4);
+  uint32_t* slabmask = c.take<uint32_t>(nb * 4);
+  int32_t* fwoff = c.take<int32_t>(nb * 4);
+  int32_t* slaboff = c.take<int32_t>(nb * 4);
+  int32_t* counts = c.take<int32_t>(16);
   if (f) {
     f->U = U; f->ACC = ACC; f->YA = YA; f->YB = YB; f->CHI = CHI; f->DENSE = DENSE; f->SLAB = SLAB;
     f->d_nbh = nbh; f->d_binfo = binfo; f->d_blist = blist; f->d_slabidx = slabidx;
     f->d_fw = fw; f->d_slabt = slabt; f->d_reft = reft; f->d_crst = crst; f->d_ranks = ranks;
     f->d_norms = norms; f->d_maxbits = maxbits; f->d_ind = ind; f->d_chir = chir; f->d_diag = diag;
     f->d_err = errf;
+    f->d_leaves = leaves; f->d_finer = finer; f->d_fwmask = fwmask; f->d_slabmask = slabmask;
+    f->d_fwoff = fwoff; f->d_slaboff = slaboff; f->d_counts = counts;
   }
   return c.off;
 }
@@ -207,88 +228,67 @@ acm::TopoK topo(const acm_forest* f) {
   return t;
 }
 
-constexpr int kFaceBox[6] = {12, 14, 10, 16, 4, 22};
+// The host may rewrite the pinned staging arrays and the leaf map only once the copies of the
+// previous topology upload have been consumed.
+acm_status topo_copies_done(acm_forest* f) {
+  if (f->topo_pending) {
+    const double t0 = now_ms();
+    CK(cudaEventSynchronize(f->ev_topo));
+    f->host_wait_ms += now_ms() - t0;
+    f->topo_pending = false;
+  }
+  return ACM_OK;
+}
 
-// Rebuild the rank-indexed device metadata after any change of the grid: per block its 27
-// neighbour boxes (type, slots), then the fine-wins and coarse-face task lists.  Rows are built
-// in parallel into pinned host memory and copied in one go.
-acm_status upload_topology(acm_forest* f, std::vector<BoxKey>* new_order = nullptr) {
+// Install the block order after a grid change (new_order / new_blist: the order and its slots
+// when the caller knows them, else sorted from the leaf map) and rebuild the rank-indexed
+// device metadata: block info and slots are copied from pinned staging, the leaf map is copied
+// byte for byte, and the neighbourhood rows and the task lists are built by the topology
+// kernels.  Nothing here waits for the device.
+acm_status upload_topology(acm_forest* f, std::vector<BoxKey>* new_order = nullptr,
+                           std::vector<int32_t>* new_blist = nullptr) {
   const double t0 = now_ms();
   const acm::Forest& fo = *f->fo;
+  for (int32_t sl : f->blist) f->slot_rank[sl] = -1;
   if (new_order) f->order.swap(*new_order);
   else f->order = fo.sorted();
+  const int64_t n = (int64_t)f->order.size();
+  if (new_blist) {
+    f->blist.swap(*new_blist);
+  } else {
+    f->blist.resize(n);
+    for (int64_t r = 0; r < n; ++r) f->blist[r] = fo.leaves.get(f->order[r]);
+  }
   const double t1 = now_ms();
   f->host_sort_ms += t1 - t0;
-  const int64_t n = (int64_t)f->order.size();
-  f->blist.resize(n);
-  int bad = 0, jtop = 0;
-#pragma omp parallel for schedule(static) reduction(| : bad) reduction(max : jtop)
+  acm_status s = topo_copies_done(f);
+  if (s) return s;
+  int jtop = 0;
   for (int64_t r = 0; r < n; ++r) {
     const BoxKey& b = f->order[r];
-    const int32_t me = fo.leaves.get(b);
-    f->blist[r] = me;
-    f->h_blist[r] = me;
+    f->h_blist[r] = f->blist[r];
     f->h_binfo[r] = make_int4(b.J, b.x, b.y, b.z);
+    f->slot_rank[f->blist[r]] = (int32_t)r;
     jtop = std::max(jtop, b.J);
-    int32_t* row = f->h_nbh + r * acm::kNbhStride;
-    for (int e = 0; e < acm::kNbhStride; ++e) row[e] = -1;
-    for (int e = 0; e < 8; ++e) f->h_slabidx[r * 8 + e] = -1;
-    for (int dz = -1; dz <= 1; ++dz)
-      for (int dy = -1; dy <= 1; ++dy)
-        for (int dx = -1; dx <= 1; ++dx) {
-          const int d = acm::box_index(dx, dy, dz);
-          const BoxStatus st = fo.box_status(b.J, (int64_t)b.x + dx, (int64_t)b.y + dy, (int64_t)b.z + dz);
-          if (st.type == acm::BOX_NONE) { bad = 1; continue; }
-          if (st.type == acm::BOX_REFINED) {
-            // every child touching the block must be a leaf (kernels index these slots)
-            for (int c = 0; c < 8; ++c) {
-              const int cc[3] = {c & 1, (c >> 1) & 1, (c >> 2) & 1};
-              const int dd[3] = {dx, dy, dz};
-              bool touch = true;
-              for (int q = 0; q < 3; ++q)
-                if ((dd[q] == 1 && cc[q] != 0) || (dd[q] == -1 && cc[q] != 1)) touch = false;
-              if (touch && st.slot[c] < 0) bad = 1;
-            }
-          }
-          for (int c = 0; c < 8; ++c) row[8 * d + c] = st.slot[c];
-          const int t = st.type == acm::BOX_LEAF ? acm::kTypeLeaf
-                        : st.type == acm::BOX_COARSER ? acm::kTypeCoarser
-                                                      : acm::kTypeRefined;
-          row[acm::kNbhType + d] = t | (st.octant << 4);
-        }
   }
-  if (bad) return fail(f, ACM_EGRADING, "grid is not 2:1 graded");
   f->Jtop = jtop;
-  const double t2 = now_ms();
-  f->host_rows_ms += t2 - t1;
-  int64_t nfw = 0, nsl = 0;
-  for (int64_t r = 0; r < n; ++r) {
-    const int32_t* row = f->h_nbh + r * acm::kNbhStride;
-    for (int d = 0; d < 27; ++d)
-      if (d != 13 && (row[acm::kNbhType + d] & 15) == acm::kTypeRefined) f->h_fw[nfw++] = make_int2((int)r, d);
-    for (int F = 0; F < 6; ++F)
-      if ((row[acm::kNbhType + kFaceBox[F]] & 15) == acm::kTypeCoarser) {
-        f->h_slabidx[r * 8 + F] = (int32_t)nsl;
-        f->h_slabt[nsl] = make_int4((int)r, F, (int)nsl, 0);
-        ++nsl;
-      }
-  }
-  f->n_fw = nfw;
-  f->n_slab = nsl;
-  std::fill(f->slot_rank.begin(), f->slot_rank.end(), -1);
-  for (int64_t r = 0; r < n; ++r) f->slot_rank[f->blist[r]] = (int32_t)r;
   if (n) {
-    CK(cudaMemcpyAsync(f->d_nbh, f->h_nbh, (size_t)n * acm::kNbhStride * 4, cudaMemcpyHostToDevice, f->st));
     CK(cudaMemcpyAsync(f->d_binfo, f->h_binfo, n * sizeof(int4), cudaMemcpyHostToDevice, f->st));
     CK(cudaMemcpyAsync(f->d_blist, f->h_blist, n * 4, cudaMemcpyHostToDevice, f->st));
-    CK(cudaMemcpyAsync(f->d_slabidx, f->h_slabidx, n * 8 * 4, cudaMemcpyHostToDevice, f->st));
   }
-  if (nfw) CK(cudaMemcpyAsync(f->d_fw, f->h_fw, nfw * sizeof(int2), cudaMemcpyHostToDevice, f->st));
-  if (nsl) CK(cudaMemcpyAsync(f->d_slabt, f->h_slabt, nsl * sizeof(int4), cudaMemcpyHostToDevice, f->st));
-  // the pinned staging is reused by the next rebuild: complete the copies first
-  const double t3 = now_ms();
-  CK(cudaStreamSynchronize(f->st));
-  f->host_wait_ms += now_ms() - t3;
+  CK(cudaMemcpyAsync(f->d_leaves, f->h_leaves, f->leaf_cap * sizeof(acm::LeafEntry), cudaMemcpyHostToDevice,
+                     f->st));
+  CK(cudaEventRecord(f->ev_topo, f->st));
+  f->topo_pending = true;
+  acm::TreeK tk;
+  tk.tab = f->d_leaves;
+  tk.mask = (unsigned long long)(f->leaf_cap - 1);
+  for (int a = 0; a < 3; ++a) tk.nroot[a] = f->gp.nroot[a];
+  acm::launch_topology(tk, f->d_binfo, n, f->d_nbh, f->d_finer, f->d_fwmask, f->d_slabmask, f->d_fwoff,
+                       f->d_slaboff, f->d_counts, f->d_fw, f->d_slabt, f->d_slabidx, f->d_err, f->st);
+  CKL();
+  f->launches += 3;
+  f->host_rows_ms += now_ms() - t1;
   f->host_topology_ms += now_ms() - t0;
   return ACM_OK;
 }
@@ -300,26 +300,22 @@ T* reg_ptr(acm_forest* f, void* r) { return reinterpret_cast<T*>(r); }
 template <typename T>
 acm_status sync_stage(acm_forest* f, T* reg) {
   const int Bs = f->gp.Bs;
-  if (f->n_fw) {
-    acm::launch_fine_wins<T>(Bs, reg, f->d_fw, f->n_fw, f->d_nbh, f->d_blist, f->st);
-    CKL();
-    ++f->launches;
-  }
-  if (f->n_slab) {
-    acm::launch_coarse_slabs<T>(Bs, reg, reinterpret_cast<T*>(f->SLAB), f->d_slabt, f->n_slab, f->d_nbh, f->st);
-    CKL();
-    ++f->launches;
-  }
+  const int64_t n = (int64_t)f->order.size();
+  acm::launch_fine_wins<T>(Bs, reg, f->d_fw, f->d_counts, 26 * n, f->d_nbh, f->d_blist, f->st);
+  CKL();
+  acm::launch_coarse_slabs<T>(Bs, reg, reinterpret_cast<T*>(f->SLAB), f->d_slabt, f->d_counts + 1, 6 * n, f->d_nbh,
+                              f->st);
+  CKL();
+  f->launches += 2;
   return ACM_OK;
 }
 
 template <typename T>
 acm_status fine_wins(acm_forest* f, T* reg) {
-  if (f->n_fw) {
-    acm::launch_fine_wins<T>(f->gp.Bs, reg, f->d_fw, f->n_fw, f->d_nbh, f->d_blist, f->st);
-    CKL();
-    ++f->launches;
-  }
+  acm::launch_fine_wins<T>(f->gp.Bs, reg, f->d_fw, f->d_counts, 26 * (int64_t)f->order.size(), f->d_nbh, f->d_blist,
+                           f->st);
+  CKL();
+  ++f->launches;
   return ACM_OK;
 }
 
@@ -496,23 +492,31 @@ acm_status refine_all(acm_forest* f) {
   // parent replaced in place by its children 0..7
   const double t1 = now_ms();
   std::vector<BoxKey> parents, kids, order2;
+  std::vector<int32_t> blist2;
   parents.reserve(prank.size());
   kids.reserve(prank.size() * 8);
   order2.reserve(f->order.size() + 7 * prank.size());
-  for (const BoxKey& b : f->order) {
+  blist2.reserve(f->order.size() + 7 * prank.size());
+  for (size_t r = 0, i = 0; r < f->order.size(); ++r) {
+    const BoxKey& b = f->order[r];
     if (b.J < fo.Jmax) {
       parents.push_back(b);
       for (int c = 0; c < 8; ++c) {
         kids.push_back(acm::Forest::child(b, c));
         order2.push_back(kids.back());
+        blist2.push_back(new_slot[8 * i + c]);
       }
+      ++i;
     } else {
       order2.push_back(b);
+      blist2.push_back(f->blist[r]);
     }
   }
+  s = topo_copies_done(f);            // the leaf map may still be in flight to the device
+  if (s) return s;
   fo.update_leaves(parents, kids, new_slot);
   f->host_tree_ms += now_ms() - t1;
-  s = upload_topology(f, &order2);   // synchronises the stream (tasks buffer lifetime)
+  s = upload_topology(f, &order2, &blist2);
   if (s) return s;
   return eval_mask<T>(f, &new_slot);
 }
@@ -546,6 +550,8 @@ acm_status indicators(acm_forest* f, std::vector<double>& ind, std::vector<doubl
   chr.resize(nb);
   CK(cudaMemcpyAsync(ind.data(), f->d_ind, nb * 8, cudaMemcpyDeviceToHost, f->st));
   CK(cudaMemcpyAsync(chr.data(), f->d_chir, nb * 8, cudaMemcpyDeviceToHost, f->st));
+  CK(cudaMemcpyAsync(f->h_finer, f->d_finer, nb, cudaMemcpyDeviceToHost, f->st));
+  CK(cudaMemcpyAsync(f->h_err, f->d_err, sizeof(int), cudaMemcpyDeviceToHost, f->st));
   CK(cudaStreamSynchronize(f->st));
   return device_error(f);
 }
@@ -607,12 +613,8 @@ acm_status coarsen(acm_forest* f, int64_t* n_blocks, int* n_passes) {
       for (int c = 1; c < 8 && grp; ++c) grp = f->order[r + c] == acm::Forest::child(p, c);
       if (!grp) { ++r; continue; }
       bool ok = true;
-      for (int c = 0; c < 8 && ok; ++c) {
-        if (!tag[r + c]) ok = false;
-        const int32_t* row = f->h_nbh + (r + c) * acm::kNbhStride;
-        for (int d = 0; d < 27 && ok; ++d)
-          if (d != 13 && (row[acm::kNbhType + d] & 15) == acm::kTypeRefined) ok = false;
-      }
+      for (int c = 0; c < 8 && ok; ++c)
+        if (!tag[r + c] || f->h_finer[r + c]) ok = false;
       if (ok) {
         groups.push_back(p);
         gstart.push_back(r);
@@ -649,21 +651,27 @@ acm_status coarsen(acm_forest* f, int64_t* n_blocks, int* n_passes) {
     removed.reserve(groups.size() * 8);
     for (size_t g = 0; g < groups.size(); ++g)
       for (int c = 0; c < 8; ++c) removed.push_back(f->order[gstart[g] + c]);
+    s = topo_copies_done(f);
+    if (s) return s;
     fo.update_leaves(removed, groups, new_slot);
     // block order of the merged grid: each group's 8 consecutive children replaced by the parent
     std::vector<BoxKey> order2;
+    std::vector<int32_t> blist2;
     order2.reserve(n);
+    blist2.reserve(n);
     for (size_t r = 0, g = 0; r < n;) {
       if (g < gstart.size() && r == gstart[g]) {
         order2.push_back(groups[g]);
+        blist2.push_back(new_slot[g]);
         r += 8;
         ++g;
       } else {
+        blist2.push_back(f->blist[r]);
         order2.push_back(f->order[r++]);
       }
     }
     f->host_tree_ms += now_ms() - th;
-    s = upload_topology(f, &order2);
+    s = upload_topology(f, &order2, &blist2);
     if (s) return s;
     s = eval_mask<T>(f, &new_slot);
     if (s) return s;
@@ -769,7 +777,6 @@ acm_status acm_create_forest(const acm_grid_params* grid, const acm_phys_params*
   f->lay = acm::layout_info(grid->precision, grid->Bs);
   f->esz = grid->precision == 64 ? 8 : 4;
   carve(f.get(), grid, f->pool);
-  f->fo.reset(new acm::Forest(grid->nroot, grid->Bs, grid->Jmin, grid->Jmax, grid->max_blocks));
   fill_phys(f.get());
   acm_forest* fp = f.get();
   fp->slot_rank.assign((size_t)grid->max_blocks, -1);
@@ -778,21 +785,22 @@ acm_status acm_create_forest(const acm_grid_params* grid, const acm_phys_params*
   {
     acm_forest* f = fp;   // for CK
     const size_t nb = (size_t)grid->max_blocks;
-    const size_t bytes = nb * acm::kNbhStride * 4 + nb * sizeof(int4) + nb * 4 + nb * 8 * 4 +
-                         nb * 27 * sizeof(int2) + nb * 6 * sizeof(int4) + 8 * 256;
+    f->leaf_cap = acm::LeafMap::capacity_for(grid->max_blocks);
+    const size_t bytes = f->leaf_cap * sizeof(acm::LeafMap::Entry) + nb * sizeof(int4) + nb * 4 + nb + 8 * 256;
     CK(cudaMallocHost(&f->h_pinned, bytes));
     char* p = (char*)f->h_pinned;
     auto take = [&](size_t b) { char* q = p; p += (b + 255) & ~(size_t)255; return q; };
-    f->h_nbh = (int32_t*)take(nb * acm::kNbhStride * 4);
+    f->h_leaves = (acm::LeafMap::Entry*)take(f->leaf_cap * sizeof(acm::LeafMap::Entry));
     f->h_binfo = (int4*)take(nb * sizeof(int4));
     f->h_blist = (int32_t*)take(nb * 4);
-    f->h_slabidx = (int32_t*)take(nb * 8 * 4);
-    f->h_fw = (int2*)take(nb * 27 * sizeof(int2));
-    f->h_slabt = (int4*)take(nb * 6 * sizeof(int4));
+    f->h_finer = (uint8_t*)take(nb);
     f->h_err = (int*)take(16);
     *f->h_err = 0;
+    f->fo.reset(new acm::Forest(grid->nroot, grid->Bs, grid->Jmin, grid->Jmax, grid->max_blocks, f->h_leaves));
     CK(cudaMemset(f->d_err, 0, 16 * sizeof(int)));
+    CK(cudaMemset(f->d_counts, 0, 16 * sizeof(int32_t)));
     for (auto& e : f->ev) CK(cudaEventCreate(&e));
+    CK(cudaEventCreateWithFlags(&f->ev_topo, cudaEventDisableTiming));
   }
   *out = f.release();
   return ACM_OK;
@@ -800,8 +808,11 @@ acm_status acm_create_forest(const acm_grid_params* grid, const acm_phys_params*
 
 acm_status acm_destroy_forest(acm_forest* f) {
   if (!f) return ACM_OK;
+  cudaStreamSynchronize(f->st);   // no copy may still read the pinned memory
   for (auto& e : f->ev)
     if (e) cudaEventDestroy(e);
+  if (f->ev_topo) cudaEventDestroy(f->ev_topo);
+  f->fo.reset();
   if (f->h_pinned) cudaFreeHost(f->h_pinned);
   delete f;
   return ACM_OK;
@@ -843,9 +854,11 @@ acm_status acm_set_leaves(acm_forest* f, const int32_t* level, const int32_t* gx
   if ((int64_t)trial.leaves.size() != n) return fail(f, ACM_EGRADING, "duplicate leaves");
   if (!trial.tiles_domain()) return fail(f, ACM_EGRADING, "leaves do not tile the domain");
   if (!trial.is_graded()) return fail(f, ACM_EGRADING, "leaves are not 2:1 graded");
+  acm_status s = topo_copies_done(f);
+  if (s) return s;
   f->fo->clear();
   f->fo->apply_pass({}, created, nullptr);
-  acm_status s = upload_topology(f);
+  s = upload_topology(f);
   if (s) return s;
   const size_t blk = (size_t)f->lay.BLK * f->esz;
   for (int32_t sl : f->blist) CK(cudaMemsetAsync((char*)f->U + (size_t)sl * blk, 0, blk, f->st));
@@ -896,13 +909,9 @@ acm_status acm_sync_ghosts(acm_forest* f, int reg, void* out, int on_device) {
   const size_t per = (size_t)4 * ne * ne * ne * f->esz;
   const size_t n = f->order.size();
   // fine wins on U, then the extended arrays in chunks that fit the adaptation buffer
-  if (f->n_fw) {
-    if (f->gp.precision == 64)
-      acm::launch_fine_wins<double>(f->gp.Bs, (double*)f->U, f->d_fw, f->n_fw, f->d_nbh, f->d_blist, f->st);
-    else
-      acm::launch_fine_wins<float>(f->gp.Bs, (float*)f->U, f->d_fw, f->n_fw, f->d_nbh, f->d_blist, f->st);
-    CKL();
-    ++f->launches;
+  {
+    acm_status s = f->gp.precision == 64 ? fine_wins<double>(f, (double*)f->U) : fine_wins<float>(f, (float*)f->U);
+    if (s) return s;
   }
   const size_t cap = std::max<size_t>(1, (size_t)f->gp.max_blocks * 4 * f->gp.Bs * f->gp.Bs * f->gp.Bs * f->esz / per);
   for (size_t r0 = 0; r0 < n; r0 += cap) {

@@ -20,16 +20,28 @@ Directions::Directions() {
 }
 const Directions kDirs;
 
-void LeafMap::init(int64_t max_entries) {
+size_t LeafMap::capacity_for(int64_t max_entries) {
   size_t cap = 16;
   while (cap < (size_t)(2 * max_entries + 16)) cap <<= 1;
-  tab_.assign(cap, Entry{BoxKey{0, 0, 0, 0}, -1});
+  return cap;
+}
+
+void LeafMap::init(int64_t max_entries, Entry* storage) {
+  const size_t cap = capacity_for(max_entries);
+  if (storage) {
+    own_.clear();
+    tab_ = storage;
+  } else {
+    own_.assign(cap, Entry{BoxKey{0, 0, 0, 0}, -1});
+    tab_ = own_.data();
+  }
+  for (size_t i = 0; i < cap; ++i) tab_[i] = Entry{BoxKey{0, 0, 0, 0}, -1};
   mask_ = cap - 1;
   n_ = 0;
 }
 
 void LeafMap::clear() {
-  for (Entry& e : tab_) e.slot = -1;
+  for (size_t i = 0; i <= mask_; ++i) tab_[i].slot = -1;
   n_ = 0;
 }
 
@@ -76,10 +88,10 @@ bool LeafMap::erase(const BoxKey& k) {
   return true;
 }
 
-Forest::Forest(const int nr[3], int bs, int jmin, int jmax, int64_t maxb)
+Forest::Forest(const int nr[3], int bs, int jmin, int jmax, int64_t maxb, LeafMap::Entry* leaf_storage)
     : Bs(bs), M(bs - 1), Jmin(jmin), Jmax(jmax), max_blocks(maxb) {
   for (int a = 0; a < 3; ++a) nroot[a] = nr[a];
-  leaves.init(maxb);
+  leaves.init(maxb, leaf_storage);
   clear();
 }
 

@@ -9,10 +9,10 @@
 #pragma once
 
 #include <cstdint>
-#include <set>
 #include <string>
-#include <unordered_map>
 #include <vector>
+
+#include "leafhash.hpp"
 
 namespace acm {
 
@@ -22,26 +22,26 @@ struct BoxKey {
 };
 
 struct BoxKeyHash {
-  size_t operator()(const BoxKey& k) const {
-    uint64_t h = (uint64_t)(uint32_t)k.J * 0x9E3779B97F4A7C15ull;
-    h ^= (uint64_t)(uint32_t)k.x + 0x7F4A7C159E3779B9ull + (h << 6) + (h >> 2);
-    h ^= (uint64_t)(uint32_t)k.y + 0x94D049BB133111EBull + (h << 6) + (h >> 2);
-    h ^= (uint64_t)(uint32_t)k.z + 0xBF58476D1CE4E5B9ull + (h << 6) + (h >> 2);
-    return (size_t)h;
-  }
+  size_t operator()(const BoxKey& k) const { return (size_t)leaf_hash(k.J, k.x, k.y, k.z); }
 };
 
 enum BoxType : uint8_t { BOX_LEAF = 0, BOX_COARSER = 1, BOX_REFINED = 2, BOX_NONE = 3 };
 
 // Open-addressing hash table (linear probing, backward-shift deletion) from a box to the slot
-// of the leaf occupying it.  Capacity is a power of two at least twice the block pool.
+// of the leaf occupying it.  Capacity is a power of two at least twice the block pool, so a
+// probe always meets an empty entry.  The table may live in caller-provided storage (pinned
+// host memory, copied byte for byte to the device, which probes it with the same hash).
 class LeafMap {
  public:
   struct Entry {
     BoxKey k;
     int32_t slot;     // -1: empty
   };
-  void init(int64_t max_entries);
+  static size_t capacity_for(int64_t max_entries);
+  // storage: capacity_for(max_entries) entries owned by the caller, or nullptr (owned here)
+  void init(int64_t max_entries, Entry* storage = nullptr);
+  const Entry* data() const { return tab_; }
+  size_t capacity() const { return mask_ + 1; }
   void clear();
   int32_t get(const BoxKey& k) const {
     size_t i = hash(k) & mask_;
@@ -59,15 +59,17 @@ class LeafMap {
   bool empty() const { return n_ == 0; }
   template <typename F>
   void for_each(F&& fn) const {
-    for (const Entry& e : tab_)
-      if (e.slot >= 0) fn(e.k, e.slot);
+    for (size_t i = 0; i <= mask_; ++i)
+      if (tab_[i].slot >= 0) fn(tab_[i].k, tab_[i].slot);
   }
 
  private:
   static size_t hash(const BoxKey& k) { return BoxKeyHash()(k); }
-  std::vector<Entry> tab_;
+  std::vector<Entry> own_;
+  Entry* tab_ = nullptr;
   size_t mask_ = 0, n_ = 0;
 };
+static_assert(sizeof(LeafMap::Entry) == sizeof(LeafEntry), "leaf map entries are copied to the device");
 
 // Status of a level-J box as seen from a neighbour: a leaf itself, covered by a leaf one
 // level coarser (slot[0], octant = which half per axis), or refined into level J+1 leaves
@@ -95,7 +97,9 @@ inline void group_of(int k, int* start, int* n) {
 
 class Forest {
  public:
-  Forest(const int nroot[3], int Bs, int Jmin, int Jmax, int64_t max_blocks);
+  // leaf_storage: LeafMap::capacity_for(max_blocks) entries owned by the caller, or nullptr
+  Forest(const int nroot[3], int Bs, int Jmin, int Jmax, int64_t max_blocks,
+         LeafMap::Entry* leaf_storage = nullptr);
 
   int nroot[3];
   int Bs, M, Jmin, Jmax;

@@ -4,11 +4,13 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "leafhash.hpp"
+
 namespace acm {
 
-// Per-launch model constants (Sec. 2.1-2.3), in double; kernels convert to their precision.
 constexpr int kMaxLevel = 18;   // finest level a grid may use
 
+// Per-launch model constants (Sec. 2.1-2.3), in double; kernels convert to their precision.
 struct PhysK {
   double nu, c0sq, inv_ceta, cgamma, inv_csp;
   double uinf[3], pinf;
@@ -19,6 +21,21 @@ struct PhysK {
   double a1, a2, a3;        // first-derivative coefficients
   double h[kMaxLevel + 1];  // grid spacing of each level, root_len / (2^J (Bs-1))
 };
+
+// The host's leaf map as the device sees it (a byte copy of the open-addressing table).
+struct TreeK {
+  const LeafEntry* tab;
+  unsigned long long mask;   // capacity - 1 (capacity a power of two)
+  int nroot[3];
+};
+
+// Neighbourhood rows (nbh, rank-indexed), per-block flag "a neighbour box is refined" (finer),
+// and the fine-wins task list (fw) and coarse-face slab list (slabt, slabidx) for the blocks
+// binfo[0..n) of the current order; counts[0], counts[1] receive the two list lengths.
+// fwmask/slabmask/fw_off/slab_off: per-block scratch.  err |= 2 if the grid is not graded.
+void launch_topology(const TreeK& t, const int4* binfo, int64_t n, int32_t* nbh, uint8_t* finer,
+                     uint32_t* fwmask, uint32_t* slabmask, int32_t* fw_off, int32_t* slab_off, int32_t* counts,
+                     int2* fw, int4* slabt, int32_t* slabidx, int* err, cudaStream_t st);
 
 // Device topology: pointers into the pool, all indexed by rank (position in block order).
 struct TopoK {
@@ -62,13 +79,18 @@ template <typename T>
 void launch_stage(int stage, int Bs, const StageK<T>& s, const TopoK& t, const PhysK& p, int* err,
                   cudaStream_t st);
 
+// The per-stage synchronisation kernels walk a task list whose length the device holds
+// (*ntasks, written by launch_topology); max_tasks bounds it and sizes the grid.
 template <typename T>
-void launch_fine_wins(int Bs, T* reg, const int2* tasks, int64_t ntasks, const int32_t* nbh,
-                      const int32_t* blist, cudaStream_t st);
+void launch_fine_wins(int Bs, T* reg, const int2* tasks, const int32_t* ntasks, int64_t max_tasks,
+                      const int32_t* nbh, const int32_t* blist, cudaStream_t st);
 
 template <typename T>
-void launch_coarse_slabs(int Bs, const T* reg, T* slab, const int4* tasks, int64_t ntasks,
-                         const int32_t* nbh, cudaStream_t st);
+void launch_coarse_slabs(int Bs, const T* reg, T* slab, const int4* tasks, const int32_t* ntasks,
+                         int64_t max_tasks, const int32_t* nbh, cudaStream_t st);
+
+// Streaming multiprocessors of the current device (cached per device).
+int sm_count();
 
 // Extended arrays (interior + g ghost layers) of all n blocks: out index = rank if by_rank,
 // else slot.

@@ -1,0 +1,225 @@
+// Device-side topology of libacm: the neighbourhood table of every block, the fine-wins task
+// list and the coarse-face slab list, built on the GPU from a byte copy of the host's leaf map.
+//
+// Paper, Sec. 4.1: blocks are located through their treecodes and the neighbours of a block are
+// found from its own coordinates (no pointers between blocks).  Here every (block, neighbour
+// box) pair is one thread that probes the leaf map exactly as the host does (same table, same
+// hash, same probe order), so the device tables equal what a host build would give.
+#include "common.cuh"
+#include "kernels.hpp"
+
+namespace acm {
+
+namespace {
+
+__constant__ int kFaceBoxT[6] = {12, 14, 10, 16, 4, 22};
+
+// Probe the leaf map for box (J, x, y, z) (already wrapped); -1 if it is not a leaf.  The table
+// always holds an empty entry (capacity >= 2 x entries), so the probe ends within `cap` steps;
+// the bound is only a guard (a full table sets the error flag).
+__device__ __forceinline__ int leaf_get(const TreeK& t, int J, int x, int y, int z, int* err) {
+  size_t i = (size_t)(leaf_hash(J, x, y, z) & t.mask);
+  for (unsigned long long n = 0; n <= t.mask; ++n) {
+    const LeafEntry e = t.tab[i];
+    if (e.slot < 0) return -1;
+    if (e.J == J && e.x == x && e.y == y && e.z == z) return e.slot;
+    i = (i + 1) & (size_t)t.mask;
+  }
+  atomicOr(err, 4);
+  return -1;
+}
+
+__device__ __forceinline__ int wrap_axis(long long v, long long n) {
+  v %= n;
+  return (int)(v < 0 ? v + n : v);
+}
+
+// Status of the level-J box (x, y, z) (unwrapped) as seen from a neighbour: a leaf, covered by a
+// leaf one level coarser (octant = which half per axis), or refined into level J+1 leaves.
+struct DevStatus {
+  int type;          // kTypeLeaf, kTypeCoarser, kTypeRefined, kTypeNone
+  int octant;
+  int slot[8];
+};
+
+__device__ DevStatus box_status_dev(const TreeK& t, int J, long long x, long long y, long long z, int* err) {
+  DevStatus st;
+  st.type = kTypeNone;
+  st.octant = 0;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) st.slot[c] = -1;
+  const int kx = wrap_axis(x, (long long)t.nroot[0] << J);
+  const int ky = wrap_axis(y, (long long)t.nroot[1] << J);
+  const int kz = wrap_axis(z, (long long)t.nroot[2] << J);
+  const int s = leaf_get(t, J, kx, ky, kz, err);
+  if (s >= 0) {
+    st.type = kTypeLeaf;
+    st.slot[0] = s;
+    return st;
+  }
+  if (J > 0) {
+    const int sp = leaf_get(t, J - 1, kx >> 1, ky >> 1, kz >> 1, err);
+    if (sp >= 0) {
+      st.type = kTypeCoarser;
+      st.slot[0] = sp;
+      st.octant = (kx & 1) | ((ky & 1) << 1) | ((kz & 1) << 2);
+      return st;
+    }
+  }
+  bool any = false;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const int sc = leaf_get(t, J + 1, 2 * kx + (c & 1), 2 * ky + ((c >> 1) & 1), 2 * kz + ((c >> 2) & 1), err);
+    if (sc >= 0) {
+      st.slot[c] = sc;
+      any = true;
+    }
+  }
+  if (any) st.type = kTypeRefined;
+  return st;
+}
+
+// One warp per block (rank), lane d < 27 = neighbour box d.  Writes the block's neighbourhood
+// row, whether a neighbour box is refined (finer), the mask of refined boxes (fine-wins tasks)
+// and of faces covered by a coarser leaf (halo slabs).  A box that is missing, or refined with
+// a touching child missing, breaks the 2:1 grading the kernels rely on: error flag bit 2.
+__global__ void __launch_bounds__(256) k_rows(TreeK t, const int4* binfo, int64_t n, int32_t* nbh,
+                                              uint8_t* finer, uint32_t* fwmask, uint32_t* slabmask, int* err) {
+  const int64_t rank = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (rank >= n) return;
+  const int4 b = binfo[rank];
+  int32_t* row = nbh + rank * kNbhStride;
+  int type = kTypeNone;
+  if (lane < 27) {
+    const int dx = lane % 3 - 1, dy = (lane / 3) % 3 - 1, dz = lane / 9 - 1;
+    const DevStatus st = box_status_dev(t, b.x, (long long)b.y + dx, (long long)b.z + dy, (long long)b.w + dz, err);
+    bool bad = st.type == kTypeNone;
+    if (st.type == kTypeRefined) {
+      // every child touching the block must be a leaf (kernels index these slots)
+      const int dd[3] = {dx, dy, dz};
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        bool touch = true;
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+          const int cq = (c >> q) & 1;
+          if ((dd[q] == 1 && cq != 0) || (dd[q] == -1 && cq != 1)) touch = false;
+        }
+        if (touch && st.slot[c] < 0) bad = true;
+      }
+    }
+    if (bad) atomicOr(err, 2);
+#pragma unroll
+    for (int c = 0; c < 8; ++c) row[8 * lane + c] = st.type == kTypeNone ? -1 : st.slot[c];
+    row[kNbhType + lane] = st.type == kTypeNone ? -1 : (st.type | (st.octant << 4));
+    type = st.type;
+  } else {
+    for (int e = kNbhType + 27 + (lane - 27); e < kNbhStride; e += 5) row[e] = -1;
+  }
+  const unsigned refined = __ballot_sync(0xffffffffu, lane < 27 && lane != 13 && type == kTypeRefined);
+  const unsigned coarser = __ballot_sync(0xffffffffu, lane < 27 && type == kTypeCoarser);
+  if (lane == 0) {
+    unsigned faces = 0;
+#pragma unroll
+    for (int F = 0; F < 6; ++F)
+      if ((coarser >> kFaceBoxT[F]) & 1u) faces |= 1u << F;
+    finer[rank] = refined != 0;
+    fwmask[rank] = refined;
+    slabmask[rank] = faces;
+  }
+}
+
+// Exclusive prefix sums of the per-block task counts (one CTA; each thread scans a contiguous
+// chunk); counts[0] = fine-wins tasks, counts[1] = slabs.
+constexpr int kScanNT = 1024;
+__global__ void __launch_bounds__(kScanNT) k_scan(const uint32_t* fwmask, const uint32_t* slabmask, int64_t n,
+                                                  int32_t* fw_off, int32_t* slab_off, int32_t* counts) {
+  __shared__ int32_t sa[kScanNT], sb[kScanNT];
+  const int tid = threadIdx.x;
+  const int64_t per = (n + kScanNT - 1) / kScanNT;
+  const int64_t lo = tid * per, hi = lo + per < n ? lo + per : n;
+  int32_t a = 0, b = 0;
+  for (int64_t r = lo; r < hi; ++r) {
+    a += __popc(fwmask[r]);
+    b += __popc(slabmask[r]);
+  }
+  sa[tid] = a;
+  sb[tid] = b;
+  __syncthreads();
+  // Hillis-Steele inclusive scan of the chunk sums
+  for (int o = 1; o < kScanNT; o <<= 1) {
+    const int32_t va = tid >= o ? sa[tid - o] : 0, vb = tid >= o ? sb[tid - o] : 0;
+    __syncthreads();
+    sa[tid] += va;
+    sb[tid] += vb;
+    __syncthreads();
+  }
+  int32_t oa = sa[tid] - a, ob = sb[tid] - b;
+  for (int64_t r = lo; r < hi; ++r) {
+    fw_off[r] = oa;
+    slab_off[r] = ob;
+    oa += __popc(fwmask[r]);
+    ob += __popc(slabmask[r]);
+  }
+  if (tid == kScanNT - 1) {
+    counts[0] = sa[tid];
+    counts[1] = sb[tid];
+  }
+}
+
+// Task lists in block order, then ascending box index / face: fine-wins task (rank, d) per refined
+// neighbour box; slab (rank, face, index) per face covered by a coarser leaf, and the block's
+// slab index per face (-1: none).
+__global__ void __launch_bounds__(256) k_fill(const uint32_t* fwmask, const uint32_t* slabmask, const int32_t* fw_off,
+                                              const int32_t* slab_off, int64_t n, int2* fw, int4* slabt,
+                                              int32_t* slabidx) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  const uint32_t m = fwmask[r];
+  int j = fw_off[r];
+  for (int d = 0; d < 27; ++d)
+    if ((m >> d) & 1u) fw[j++] = make_int2((int)r, d);
+  const uint32_t sm = slabmask[r];
+  int k = slab_off[r];
+  for (int F = 0; F < 8; ++F) {
+    int idx = -1;
+    if (F < 6 && ((sm >> F) & 1u)) {
+      idx = k++;
+      slabt[idx] = make_int4((int)r, F, idx, 0);
+    }
+    slabidx[r * 8 + F] = idx;
+  }
+}
+
+}  // namespace
+
+void launch_topology(const TreeK& t, const int4* binfo, int64_t n, int32_t* nbh, uint8_t* finer,
+                     uint32_t* fwmask, uint32_t* slabmask, int32_t* fw_off, int32_t* slab_off, int32_t* counts,
+                     int2* fw, int4* slabt, int32_t* slabidx, int* err, cudaStream_t st) {
+  if (n <= 0) {
+    cudaMemsetAsync(counts, 0, 2 * sizeof(int32_t), st);
+    return;
+  }
+  k_rows<<<(unsigned)((n * 32 + 255) / 256), 256, 0, st>>>(t, binfo, n, nbh, finer, fwmask, slabmask, err);
+  k_scan<<<1, kScanNT, 0, st>>>(fwmask, slabmask, n, fw_off, slab_off, counts);
+  k_fill<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(fwmask, slabmask, fw_off, slab_off, n, fw, slabt, slabidx);
+}
+
+}  // namespace acm
+
+namespace acm {
+
+int sm_count() {
+  static int cache[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
+  if (!cache[dev]) {
+    int v = 0;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    cache[dev] = v > 0 ? v : 1;
+  }
+  return cache[dev];
+}
+
+}  // namespace acm
