@@ -63,7 +63,9 @@ struct acm_forest {
   int* d_err = nullptr;            // error bits set by kernels (see device_error)
   int* h_err = nullptr;            // pinned copy, refreshed after every RK4 step and every
                                    // indicator evaluation
-  acm::LeafEntry* d_leaves = nullptr;   // byte copy of the host leaf map (topology kernels)
+  int* d_ltab = nullptr;            // device leaf table (slot words) and box per slot, rebuilt
+  int4* d_bslot = nullptr;          // by the topology kernels after every grid change
+  size_t leaf_cap = 0;
   uint8_t* d_finer = nullptr;      // per rank: a neighbour box is refined
   uint32_t* d_fwmask = nullptr;    // per rank scratch of the topology build
   uint32_t* d_slabmask = nullptr;
@@ -71,14 +73,13 @@ struct acm_forest {
   int32_t* d_slaboff = nullptr;
   int32_t* d_counts = nullptr;     // [0] fine-wins tasks, [1] coarse-face slabs
 
-  // host side of the current topology; the leaf map and the staging arrays are pinned and
-  // copied to the device as they are (the neighbourhood tables are built there)
+  // host side of the current topology (the neighbourhood tables are built on the device from
+  // the block list; the host leaf map is brought up to date only when a host query needs it)
   std::vector<BoxKey> order;
   std::vector<int32_t> blist;
   std::vector<int32_t> slot_rank;     // slot -> rank (-1: free)
   std::vector<double> ind_slot, chr_slot;   // indicators of the current coarsening, by slot
-  acm::LeafMap::Entry* h_leaves = nullptr;
-  size_t leaf_cap = 0;
+  bool leaves_stale = false;          // fo->leaves lags behind (order, blist)
   int4* h_binfo = nullptr;
   int32_t* h_blist = nullptr;
   uint8_t* h_finer = nullptr;
@@ -199,7 +200,8 @@ size_t carve(acm_forest* f, const acm_grid_params* g, char* base) {
   double* chir = c.take<double>(nb * 8);
   double* diag = c.take<double>(nb * 4 * 8);
   int* errf = c.take<int>(16);
-  acm::LeafEntry* leaves = c.take<acm::LeafEntry>(acm::LeafMap::capacity_for(g->max_blocks) * sizeof(acm::LeafEntry));
+  int* ltab = c.take<int>(acm::LeafMap::capacity_for(g->max_blocks) * sizeof(int));
+  int4* bslot = c.take<int4>(nb * sizeof(int4));
   uint8_t* finer = c.take<uint8_t>(nb);
   uint32_t* fwmask = c.take<uint32_t>(nb * 4);
   uint32_t* slabmask = c.take<uint32_t>(nb * 4);
@@ -212,7 +214,7 @@ size_t carve(acm_forest* f, const acm_grid_params* g, char* base) {
     f->d_fw = fw; f->d_slabt = slabt; f->d_reft = reft; f->d_crst = crst; f->d_ranks = ranks;
     f->d_norms = norms; f->d_maxbits = maxbits; f->d_ind = ind; f->d_chir = chir; f->d_diag = diag;
     f->d_err = errf;
-    f->d_leaves = leaves; f->d_finer = finer; f->d_fwmask = fwmask; f->d_slabmask = slabmask;
+    f->d_ltab = ltab; f->d_bslot = bslot; f->d_finer = finer; f->d_fwmask = fwmask; f->d_slabmask = slabmask;
     f->d_fwoff = fwoff; f->d_slaboff = slaboff; f->d_counts = counts;
   }
   return c.off;
@@ -228,8 +230,8 @@ acm::TopoK topo(const acm_forest* f) {
   return t;
 }
 
-// The host may rewrite the pinned staging arrays and the leaf map only once the copies of the
-// previous topology upload have been consumed.
+// The host may rewrite the pinned staging arrays only once the copies of the previous topology
+// upload have been consumed.
 acm_status topo_copies_done(acm_forest* f) {
   if (f->topo_pending) {
     const double t0 = now_ms();
@@ -240,11 +242,19 @@ acm_status topo_copies_done(acm_forest* f) {
   return ACM_OK;
 }
 
+// Bring the host leaf map up to date with (order, blist) when a host query needs it.
+void sync_leaf_map(acm_forest* f) {
+  if (!f->leaves_stale) return;
+  f->fo->leaves.clear();
+  for (size_t r = 0; r < f->order.size(); ++r) f->fo->leaves.put(f->order[r], f->blist[r]);
+  f->leaves_stale = false;
+}
+
 // Install the block order after a grid change (new_order / new_blist: the order and its slots
 // when the caller knows them, else sorted from the leaf map) and rebuild the rank-indexed
-// device metadata: block info and slots are copied from pinned staging, the leaf map is copied
-// byte for byte, and the neighbourhood rows and the task lists are built by the topology
-// kernels.  Nothing here waits for the device.
+// device metadata: block info and slots are copied from pinned staging, and the device leaf
+// table, the neighbourhood rows and the task lists are built by the topology kernels.
+// Nothing here waits for the device.
 acm_status upload_topology(acm_forest* f, std::vector<BoxKey>* new_order = nullptr,
                            std::vector<int32_t>* new_blist = nullptr) {
   const double t0 = now_ms();
@@ -276,18 +286,18 @@ acm_status upload_topology(acm_forest* f, std::vector<BoxKey>* new_order = nullp
     CK(cudaMemcpyAsync(f->d_binfo, f->h_binfo, n * sizeof(int4), cudaMemcpyHostToDevice, f->st));
     CK(cudaMemcpyAsync(f->d_blist, f->h_blist, n * 4, cudaMemcpyHostToDevice, f->st));
   }
-  CK(cudaMemcpyAsync(f->d_leaves, f->h_leaves, f->leaf_cap * sizeof(acm::LeafEntry), cudaMemcpyHostToDevice,
-                     f->st));
   CK(cudaEventRecord(f->ev_topo, f->st));
   f->topo_pending = true;
   acm::TreeK tk;
-  tk.tab = f->d_leaves;
+  tk.tab = f->d_ltab;
+  tk.box = f->d_bslot;
   tk.mask = (unsigned long long)(f->leaf_cap - 1);
   for (int a = 0; a < 3; ++a) tk.nroot[a] = f->gp.nroot[a];
-  acm::launch_topology(tk, f->d_binfo, n, f->d_nbh, f->d_finer, f->d_fwmask, f->d_slabmask, f->d_fwoff,
-                       f->d_slaboff, f->d_counts, f->d_fw, f->d_slabt, f->d_slabidx, f->d_err, f->st);
+  acm::launch_topology(tk, f->d_ltab, f->d_bslot, f->d_binfo, f->d_blist, n, f->d_nbh, f->d_finer, f->d_fwmask,
+                       f->d_slabmask, f->d_fwoff, f->d_slaboff, f->d_counts, f->d_fw, f->d_slabt, f->d_slabidx,
+                       f->d_err, f->st);
   CKL();
-  f->launches += 3;
+  f->launches += 4;
   f->host_rows_ms += now_ms() - t1;
   f->host_topology_ms += now_ms() - t0;
   return ACM_OK;
@@ -488,22 +498,18 @@ acm_status refine_all(acm_forest* f) {
                         f->st);
   CKL();
   ++f->launches;
-  // the host-side tree and the block order of the refined grid, while the GPU refines: every
-  // parent replaced in place by its children 0..7
+  // the block order of the refined grid, while the GPU refines: every parent replaced in place
+  // by its children 0..7
   const double t1 = now_ms();
-  std::vector<BoxKey> parents, kids, order2;
+  std::vector<BoxKey> order2;
   std::vector<int32_t> blist2;
-  parents.reserve(prank.size());
-  kids.reserve(prank.size() * 8);
   order2.reserve(f->order.size() + 7 * prank.size());
   blist2.reserve(f->order.size() + 7 * prank.size());
   for (size_t r = 0, i = 0; r < f->order.size(); ++r) {
     const BoxKey& b = f->order[r];
     if (b.J < fo.Jmax) {
-      parents.push_back(b);
       for (int c = 0; c < 8; ++c) {
-        kids.push_back(acm::Forest::child(b, c));
-        order2.push_back(kids.back());
+        order2.push_back(acm::Forest::child(b, c));
         blist2.push_back(new_slot[8 * i + c]);
       }
       ++i;
@@ -512,9 +518,7 @@ acm_status refine_all(acm_forest* f) {
       blist2.push_back(f->blist[r]);
     }
   }
-  s = topo_copies_done(f);            // the leaf map may still be in flight to the device
-  if (s) return s;
-  fo.update_leaves(parents, kids, new_slot);
+  f->leaves_stale = true;
   f->host_tree_ms += now_ms() - t1;
   s = upload_topology(f, &order2, &blist2);
   if (s) return s;
@@ -646,14 +650,8 @@ acm_status coarsen(acm_forest* f, int64_t* n_blocks, int* n_passes) {
                                (int64_t)groups.size(), f->st);
     CKL();
     f->launches += 2;
-    // the host-side tree while the GPU merges
-    std::vector<BoxKey> removed;
-    removed.reserve(groups.size() * 8);
-    for (size_t g = 0; g < groups.size(); ++g)
-      for (int c = 0; c < 8; ++c) removed.push_back(f->order[gstart[g] + c]);
-    s = topo_copies_done(f);
-    if (s) return s;
-    fo.update_leaves(removed, groups, new_slot);
+    // the host side of the merged grid while the GPU merges
+    f->leaves_stale = true;
     // block order of the merged grid: each group's 8 consecutive children replaced by the parent
     std::vector<BoxKey> order2;
     std::vector<int32_t> blist2;
@@ -786,17 +784,16 @@ acm_status acm_create_forest(const acm_grid_params* grid, const acm_phys_params*
     acm_forest* f = fp;   // for CK
     const size_t nb = (size_t)grid->max_blocks;
     f->leaf_cap = acm::LeafMap::capacity_for(grid->max_blocks);
-    const size_t bytes = f->leaf_cap * sizeof(acm::LeafMap::Entry) + nb * sizeof(int4) + nb * 4 + nb + 8 * 256;
+    const size_t bytes = nb * sizeof(int4) + nb * 4 + nb + 8 * 256;
     CK(cudaMallocHost(&f->h_pinned, bytes));
     char* p = (char*)f->h_pinned;
     auto take = [&](size_t b) { char* q = p; p += (b + 255) & ~(size_t)255; return q; };
-    f->h_leaves = (acm::LeafMap::Entry*)take(f->leaf_cap * sizeof(acm::LeafMap::Entry));
     f->h_binfo = (int4*)take(nb * sizeof(int4));
     f->h_blist = (int32_t*)take(nb * 4);
     f->h_finer = (uint8_t*)take(nb);
     f->h_err = (int*)take(16);
     *f->h_err = 0;
-    f->fo.reset(new acm::Forest(grid->nroot, grid->Bs, grid->Jmin, grid->Jmax, grid->max_blocks, f->h_leaves));
+    f->fo.reset(new acm::Forest(grid->nroot, grid->Bs, grid->Jmin, grid->Jmax, grid->max_blocks));
     CK(cudaMemset(f->d_err, 0, 16 * sizeof(int)));
     CK(cudaMemset(f->d_counts, 0, 16 * sizeof(int32_t)));
     for (auto& e : f->ev) CK(cudaEventCreate(&e));
@@ -857,6 +854,7 @@ acm_status acm_set_leaves(acm_forest* f, const int32_t* level, const int32_t* gx
   acm_status s = topo_copies_done(f);
   if (s) return s;
   f->fo->clear();
+  f->leaves_stale = false;
   f->fo->apply_pass({}, created, nullptr);
   s = upload_topology(f);
   if (s) return s;
@@ -1019,6 +1017,7 @@ acm_status acm_get_topology(acm_forest* f, uint64_t* treecode, uint8_t* level, i
     if (gz) gz[r] = b.z;
   }
   if (nbr || rel) {
+    sync_leaf_map(f);
     std::vector<int32_t> nb56(nb * 56);
     std::vector<int8_t> r26(nb * 26);
     f->fo->neighbour_table(f->order, nb56.data(), r26.data());

@@ -22,20 +22,24 @@ struct PhysK {
   double h[kMaxLevel + 1];  // grid spacing of each level, root_len / (2^J (Bs-1))
 };
 
-// The host's leaf map as the device sees it (a byte copy of the open-addressing table).
+// Device leaf table: open addressing on leaf_hash(box) over `mask + 1` slot words (-1 empty);
+// the box of a slot is box[slot] = (J, x, y, z).
 struct TreeK {
-  const LeafEntry* tab;
-  unsigned long long mask;   // capacity - 1 (capacity a power of two)
+  const int* tab;
+  const int4* box;
+  unsigned long long mask;   // capacity - 1 (capacity a power of two, >= 2 x max_blocks)
   int nroot[3];
 };
 
-// Neighbourhood rows (nbh, rank-indexed), per-block flag "a neighbour box is refined" (finer),
-// and the fine-wins task list (fw) and coarse-face slab list (slabt, slabidx) for the blocks
-// binfo[0..n) of the current order; counts[0], counts[1] receive the two list lengths.
-// fwmask/slabmask/fw_off/slab_off: per-block scratch.  err |= 2 if the grid is not graded.
-void launch_topology(const TreeK& t, const int4* binfo, int64_t n, int32_t* nbh, uint8_t* finer,
-                     uint32_t* fwmask, uint32_t* slabmask, int32_t* fw_off, int32_t* slab_off, int32_t* counts,
-                     int2* fw, int4* slabt, int32_t* slabidx, int* err, cudaStream_t st);
+// Rebuild the device leaf table (tab, box) from the blocks binfo/blist[0..n) of the current order,
+// then the neighbourhood rows (nbh, rank-indexed), the per-block flag "a neighbour box is
+// refined" (finer), and the fine-wins task list (fw) and coarse-face slab list (slabt, slabidx);
+// counts[0], counts[1] receive the two list lengths.  fwmask/slabmask/fw_off/slab_off: per-block
+// scratch.  err |= 2 if the grid is not graded, |= 4 if the table overflowed.
+void launch_topology(const TreeK& t, int* tab, int4* box, const int4* binfo, const int32_t* blist, int64_t n,
+                     int32_t* nbh, uint8_t* finer, uint32_t* fwmask, uint32_t* slabmask, int32_t* fw_off,
+                     int32_t* slab_off, int32_t* counts, int2* fw, int4* slabt, int32_t* slabidx, int* err,
+                     cudaStream_t st);
 
 // Device topology: pointers into the pool, all indexed by rank (position in block order).
 struct TopoK {

@@ -1,10 +1,11 @@
 // Device-side topology of libacm: the neighbourhood table of every block, the fine-wins task
-// list and the coarse-face slab list, built on the GPU from a byte copy of the host's leaf map.
+// list and the coarse-face slab list, built on the GPU from the block list alone.
 //
 // Paper, Sec. 4.1: blocks are located through their treecodes and the neighbours of a block are
-// found from its own coordinates (no pointers between blocks).  Here every (block, neighbour
-// box) pair is one thread that probes the leaf map exactly as the host does (same table, same
-// hash, same probe order), so the device tables equal what a host build would give.
+// found from its own coordinates (no pointers between blocks).  Here the leaves are first put
+// into a device hash table (box -> slot; the table stores slots and keys are read back through
+// a slot-indexed box array), then every (block, neighbour box) pair is one thread that resolves
+// the box the way the host tree does (leaf, else coarser leaf, else refined into leaves).
 #include "common.cuh"
 #include "kernels.hpp"
 
@@ -14,19 +15,37 @@ namespace {
 
 __constant__ int kFaceBoxT[6] = {12, 14, 10, 16, 4, 22};
 
-// Probe the leaf map for box (J, x, y, z) (already wrapped); -1 if it is not a leaf.  The table
-// always holds an empty entry (capacity >= 2 x entries), so the probe ends within `cap` steps;
-// the bound is only a guard (a full table sets the error flag).
+// Probe the table for box (J, x, y, z) (already wrapped); -1 if it is not a leaf.  The table
+// always holds empty entries (capacity >= 2 x leaves), so a probe ends long before `cap` steps;
+// the bound is only a guard (error flag bit 2).
 __device__ __forceinline__ int leaf_get(const TreeK& t, int J, int x, int y, int z, int* err) {
   size_t i = (size_t)(leaf_hash(J, x, y, z) & t.mask);
   for (unsigned long long n = 0; n <= t.mask; ++n) {
-    const LeafEntry e = t.tab[i];
-    if (e.slot < 0) return -1;
-    if (e.J == J && e.x == x && e.y == y && e.z == z) return e.slot;
+    const int s = t.tab[i];
+    if (s < 0) return -1;
+    const int4 k = t.box[s];
+    if (k.x == J && k.y == x && k.z == y && k.w == z) return s;
     i = (i + 1) & (size_t)t.mask;
   }
   atomicOr(err, 4);
   return -1;
+}
+
+// Insert every leaf (rank r: box binfo[r], slot blist[r]) into the table (all entries -1 before)
+// and record its box by slot.  Linear probing with compare-and-swap on the slot word.
+__global__ void __launch_bounds__(256) k_index(TreeK t, const int4* binfo, const int32_t* blist, int64_t n,
+                                               int* tab, int4* box, int* err) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  const int4 b = binfo[r];
+  const int s = blist[r];
+  box[s] = b;
+  size_t i = (size_t)(leaf_hash(b.x, b.y, b.z, b.w) & t.mask);
+  for (unsigned long long k = 0; k <= t.mask; ++k) {
+    if (atomicCAS(tab + i, -1, s) == -1) return;
+    i = (i + 1) & (size_t)t.mask;
+  }
+  atomicOr(err, 4);
 }
 
 __device__ __forceinline__ int wrap_axis(long long v, long long n) {
@@ -194,13 +213,16 @@ __global__ void __launch_bounds__(256) k_fill(const uint32_t* fwmask, const uint
 
 }  // namespace
 
-void launch_topology(const TreeK& t, const int4* binfo, int64_t n, int32_t* nbh, uint8_t* finer,
-                     uint32_t* fwmask, uint32_t* slabmask, int32_t* fw_off, int32_t* slab_off, int32_t* counts,
-                     int2* fw, int4* slabt, int32_t* slabidx, int* err, cudaStream_t st) {
+void launch_topology(const TreeK& t, int* tab, int4* box, const int4* binfo, const int32_t* blist, int64_t n,
+                     int32_t* nbh, uint8_t* finer, uint32_t* fwmask, uint32_t* slabmask, int32_t* fw_off,
+                     int32_t* slab_off, int32_t* counts, int2* fw, int4* slabt, int32_t* slabidx, int* err,
+                     cudaStream_t st) {
+  cudaMemsetAsync(tab, 0xff, (size_t)(t.mask + 1) * sizeof(int), st);
   if (n <= 0) {
     cudaMemsetAsync(counts, 0, 2 * sizeof(int32_t), st);
     return;
   }
+  k_index<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(t, binfo, blist, n, tab, box, err);
   k_rows<<<(unsigned)((n * 32 + 255) / 256), 256, 0, st>>>(t, binfo, n, nbh, finer, fwmask, slabmask, err);
   k_scan<<<1, kScanNT, 0, st>>>(fwmask, slabmask, n, fw_off, slab_off, counts);
   k_fill<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(fwmask, slabmask, fw_off, slab_off, n, fw, slabt, slabidx);
