@@ -134,7 +134,7 @@ def profiled_traffic():
         return None, None
 
 
-def oracle_rhs_sample(leaves, U_blocks, grid, phys, mask, max_seconds=30.0):
+def oracle_rhs_sample(leaves, U_blocks, grid, phys, mask):
     """Time the FP64 oracle's right-hand side (ghost sync + RHS of every block) on the given
     grid and state.  Returns (point-updates/s, seconds, blocks)."""
     import numpy as np
@@ -159,6 +159,19 @@ def oracle_rhs_sample(leaves, U_blocks, grid, phys, mask, max_seconds=30.0):
     dt = time.perf_counter() - t0
     n = len(leaves)
     return n * grid["Bs"] ** 3 / dt, dt, n
+
+
+def reduce_over_ranks(ms, point_updates, dist=None, device="cpu"):
+    """Whole-job figures over the ranks of a replica run: the slowest rank's time and the sum of
+    all ranks' point-updates (each rank runs its own replica: weak scaling)."""
+    if dist is None:
+        return float(ms), float(point_updates)
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    p = torch.tensor([float(point_updates)], dtype=torch.float64, device=device)
+    dist.all_reduce(p)
+    return float(t.item()), float(p.item())
 
 
 def run_reference(args):
@@ -282,15 +295,7 @@ def main():
         ms = ev0.elapsed_time(ev1)
         clk = clocks.stop()
         f.enable_timing(False)
-        t_max = ms
-        pu_all = pu
-        if dist is not None:
-            t = torch.tensor([ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            t_max = float(t.item())
-            p = torch.tensor([float(pu)], device="cuda")
-            dist.all_reduce(p)
-            pu_all = float(p.item())
+        t_max, pu_all = reduce_over_ranks(ms, pu, dist, "cuda")
         value = pu_all / (t_max * 1e-3)
 
         # roofline of the dominant kernel (fused RHS + RK4 stage): algorithmic bytes / event time
@@ -337,16 +342,23 @@ def main():
 
         cpu = None
         if rank == 0 and world == 1 and not args.no_cpu_baseline:
-            topo = f.topology()
-            f.refine_all()
-            topo = f.topology()
+            # bounded sample (10-30 s of one core): the same workload with levels 2..4, its grid
+            # built and refined by the library, the oracle evaluating one RHS on that state
+            g4, p4, m4, ic4, _ = sphere_setup(Jmax=min(args.Jmax, 4), precision=args.precision, max_blocks=8000)
+            f4 = A.Forest(g4, p4, stream=stream)
+            f4.set_mask(A.ACM_MASK_SPHERE, m4)
+            f4.init_grid(A.ACM_IC_UNIFORM, ic4)
+            f4.refine_all()
+            topo = f4.topology()
             leaves = list(zip(topo["level"].tolist(), topo["gx"].tolist(), topo["gy"].tolist(),
                               topo["gz"].tolist()))
-            U = f.read_fields().astype(np.float64)
-            v, secs, nb = oracle_rhs_sample(leaves, U, grid, phys, mask)
+            U = f4.read_fields().astype(np.float64)
+            del f4
+            v, secs, nb = oracle_rhs_sample(leaves, U, g4, p4, m4)
             cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                   "sample": f"one FP64 oracle RHS evaluation (ghost sync + RHS) over the workload's "
-                             f"evolved grid, {nb} blocks x 17^3, {secs:.1f} s"}
+                   "sample": f"one FP64 oracle RHS evaluation (ghost sync + RHS) over the same workload at "
+                             f"levels {g4['Jmin']}..{g4['Jmax']} after refinement, {nb} blocks x 17^3, "
+                             f"{secs:.1f} s"}
 
     if rank == 0:
         line = {

@@ -94,6 +94,9 @@ __global__ void __launch_bounds__(kNT) k_fine_wins(T* reg, const int2* tasks, co
 // once per point for all components; each separable pass gives a thread one whole line, and
 // the last pass one halo column (t0, t1).
 // Slab layout [slab][comp][layer l-1][t1][t0] with (t0, t1) as in the stage kernel.
+// The leaf lookups depend on the grid only: with `offc` set, a launch with use_cache = 0 stores
+// them per slab (SlabSmem::NOFF words: the patch, then 3 layers of the 4M edge columns) and a
+// later launch on the same grid with use_cache = 1 reads them back instead of searching again.
 // Dynamic shared memory: P, A, B below in T, then the neighbourhood.
 template <typename T, int BS>
 struct SlabSmem {
@@ -105,11 +108,24 @@ struct SlabSmem {
   static constexpr int A = 4 * NN * NC * BS;        // [f][n][t1 coarse][t0]: predicted along t0
   static constexpr int B = 4 * NN * BS * BS;        // [f][n][t1][t0]: predicted along t0 and t1
   static constexpr size_t bytes = (size_t)(P + A + B) * sizeof(T) + kNbhStride * sizeof(int);
+  static constexpr int NEDGE = 4 * M;                 // halo columns on the face's boundary lines
+  static constexpr int NOFF = NN * NC * NC + 3 * NEDGE;
 };
 
+// Compact index of an edge column (t0 or t1 on the boundary), 0..4M-1.
+template <int BS>
+__device__ __forceinline__ int edge_index(int t0, int t1) {
+  constexpr int M = BS - 1;
+  if (t1 == 0) return t0;
+  if (t1 == M) return BS + t0;
+  if (t0 == 0) return 2 * BS + t1 - 1;
+  return 2 * BS + (BS - 2) + t1 - 1;
+}
+
 template <typename T, int BS>
-__global__ void __launch_bounds__(SlabSmem<T, BS>::NT) k_coarse_slabs(const T* reg, T* slab, const int4* tasks,
-                                                                       const int32_t* ntasks, const int32_t* nbh_all) {
+__global__ void __launch_bounds__(SlabSmem<T, BS>::NT, 3) k_coarse_slabs(const T* reg, T* slab, const int4* tasks,
+                                                                       const int32_t* ntasks, const int32_t* nbh_all,
+                                                                       uint32_t* offc, int use_cache) {
   using L = Lay<T, BS>;
   using S = SlabSmem<T, BS>;
   constexpr int M = L::M, NT = S::NT, NC = S::NC, NN = S::NN;
@@ -123,9 +139,13 @@ __global__ void __launch_bounds__(SlabSmem<T, BS>::NT) k_coarse_slabs(const T* r
   const int nt = *ntasks;
   for (int task = blockIdx.x; task < nt; task += gridDim.x) {
   const int4 tk = tasks[task];
+  uint32_t* oc = offc ? offc + (size_t)tk.z * S::NOFF : nullptr;
+  const bool cached = oc && use_cache;
   __syncthreads();                                  // previous task done with shared memory
-  for (int i = tid; i < kNbhStride; i += NT) nbh[i] = nbh_all[(size_t)tk.x * kNbhStride + i];
-  __syncthreads();
+  if (!cached) {
+    for (int i = tid; i < kNbhStride; i += NT) nbh[i] = nbh_all[(size_t)tk.x * kNbhStride + i];
+    __syncthreads();
+  }
   const int F = tk.y, ax = F >> 1;
   const bool plus = F & 1;
   const int n0 = plus ? M - 2 : -6;                 // first coarse plane (even local coordinate)
@@ -139,12 +159,19 @@ __global__ void __launch_bounds__(SlabSmem<T, BS>::NT) k_coarse_slabs(const T* r
   const bool edge = col && (t0 == 0 || t0 == M || t1 == 0 || t1 == M);
   // leaf lookups (component 0 offsets; component f is FS further), then all loads at once
   long long eo[3] = {-1, -1, -1};
+  const int ei = edge ? edge_index<BS>(t0, t1) : 0;
   if (edge) {
 #pragma unroll
     for (int l = 1; l <= 3; ++l) {
-      int x, y, z;
-      place(plus ? M + l : -l, t0, t1, &x, &y, &z);
-      eo[l - 1] = direct_offset<T, BS>(nbh, x, y, z, 0);
+      if (cached) {
+        const uint32_t v = oc[NP3 + 3 * ei + l - 1];
+        eo[l - 1] = v == 0xffffffffu ? -1 : (long long)v;
+      } else {
+        int x, y, z;
+        place(plus ? M + l : -l, t0, t1, &x, &y, &z);
+        eo[l - 1] = direct_offset<T, BS>(nbh, x, y, z, 0);
+        if (oc) oc[NP3 + 3 * ei + l - 1] = eo[l - 1] < 0 ? 0xffffffffu : (uint32_t)eo[l - 1];
+      }
     }
   }
   constexpr int U = (NP3 + NT - 1) / NT;
@@ -154,10 +181,16 @@ __global__ void __launch_bounds__(SlabSmem<T, BS>::NT) k_coarse_slabs(const T* r
     const int i = tid + k * NT;
     off[k] = -2;
     if (i < NP3) {
-      const int a0 = i % NC, a1 = (i / NC) % NC, an = i / (NC * NC);
-      int x, y, z;
-      place(n0 + 2 * an, 2 * a0 - 2, 2 * a1 - 2, &x, &y, &z);
-      off[k] = direct_offset<T, BS>(nbh, x, y, z, 0);
+      if (cached) {
+        const uint32_t v = oc[i];
+        off[k] = v == 0xffffffffu ? -1 : (long long)v;
+      } else {
+        const int a0 = i % NC, a1 = (i / NC) % NC, an = i / (NC * NC);
+        int x, y, z;
+        place(n0 + 2 * an, 2 * a0 - 2, 2 * a1 - 2, &x, &y, &z);
+        off[k] = direct_offset<T, BS>(nbh, x, y, z, 0);
+        if (oc) oc[i] = off[k] < 0 ? 0xffffffffu : (uint32_t)off[k];
+      }
     }
   }
   T ev[3][4];
@@ -900,7 +933,7 @@ void launch_fine_wins(int Bs, T* reg, const int2* tasks, const int32_t* ntasks, 
 }
 template <typename T, int BS>
 void launch_coarse_slabs_bs(const T* reg, T* slab, const int4* tasks, const int32_t* ntasks, int64_t max_tasks,
-                            const int32_t* nbh, cudaStream_t st) {
+                            const int32_t* nbh, uint32_t* offc, int use_cache, cudaStream_t st) {
   static bool attr = false;             // opt in to more than 48 KB of dynamic shared memory once
   if (!attr) {
     cudaFuncSetAttribute(k_coarse_slabs<T, BS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SlabSmem<T, BS>::bytes);
@@ -908,15 +941,17 @@ void launch_coarse_slabs_bs(const T* reg, T* slab, const int4* tasks, const int3
   }
   // resident CTAs: 3 per SM (register-limited) for Bs = 17
   const int64_t g = std::min<int64_t>(max_tasks, 3 * (int64_t)sm_count());
-  k_coarse_slabs<T, BS><<<grid1(g), SlabSmem<T, BS>::NT, SlabSmem<T, BS>::bytes, st>>>(reg, slab, tasks, ntasks, nbh);
+  k_coarse_slabs<T, BS><<<grid1(g), SlabSmem<T, BS>::NT, SlabSmem<T, BS>::bytes, st>>>(reg, slab, tasks, ntasks, nbh,
+                                                                                       offc, use_cache);
 }
 template <typename T>
 void launch_coarse_slabs(int Bs, const T* reg, T* slab, const int4* tasks, const int32_t* ntasks, int64_t max_tasks,
-                         const int32_t* nbh, cudaStream_t st) {
+                         const int32_t* nbh, uint32_t* offc, int use_cache, cudaStream_t st) {
   if (max_tasks <= 0) return;
-  if (Bs == 17) launch_coarse_slabs_bs<T, 17>(reg, slab, tasks, ntasks, max_tasks, nbh, st);
-  else launch_coarse_slabs_bs<T, 9>(reg, slab, tasks, ntasks, max_tasks, nbh, st);
+  if (Bs == 17) launch_coarse_slabs_bs<T, 17>(reg, slab, tasks, ntasks, max_tasks, nbh, offc, use_cache, st);
+  else launch_coarse_slabs_bs<T, 9>(reg, slab, tasks, ntasks, max_tasks, nbh, offc, use_cache, st);
 }
+size_t slab_offset_words(int Bs) { return Bs == 17 ? SlabSmem<float, 17>::NOFF : SlabSmem<float, 9>::NOFF; }
 template <typename T>
 void launch_sync_ext(int Bs, const T* reg, T* out, int g, const int32_t* list, int64_t n, const int32_t* nbh, int by_rank, cudaStream_t st) {
   if (n <= 0) return;
@@ -1007,7 +1042,7 @@ void launch_scatter(int Bs, const T* dense, T* reg, const int32_t* blist, int64_
 
 #define ACM_INST(T)                                                                                        \
   template void launch_fine_wins<T>(int, T*, const int2*, const int32_t*, int64_t, const int32_t*, const int32_t*, cudaStream_t); \
-  template void launch_coarse_slabs<T>(int, const T*, T*, const int4*, const int32_t*, int64_t, const int32_t*, cudaStream_t); \
+  template void launch_coarse_slabs<T>(int, const T*, T*, const int4*, const int32_t*, int64_t, const int32_t*, uint32_t*, int, cudaStream_t); \
   template void launch_sync_ext<T>(int, const T*, T*, int, const int32_t*, int64_t, const int32_t*, int, cudaStream_t); \
   template void launch_details<T>(int, const T*, const T*, const int32_t*, const int32_t*, const int32_t*, int64_t, const unsigned long long*, double*, double*, cudaStream_t); \
   template void launch_maxnorm<T>(int, const T*, const int32_t*, int64_t, unsigned long long*, cudaStream_t); \

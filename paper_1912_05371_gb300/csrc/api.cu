@@ -72,6 +72,7 @@ struct acm_forest {
   int32_t* d_fwoff = nullptr;
   int32_t* d_slaboff = nullptr;
   int32_t* d_counts = nullptr;     // [0] fine-wins tasks, [1] coarse-face slabs
+  uint32_t* d_slaboffc = nullptr;  // slab leaf-lookup cache (filled by RK stage 1)
 
   // host side of the current topology (the neighbourhood tables are built on the device from
   // the block list; the host leaf map is brought up to date only when a host query needs it)
@@ -208,6 +209,7 @@ size_t carve(acm_forest* f, const acm_grid_params* g, char* base) {
   int32_t* fwoff = c.take<int32_t>(nb * 4);
   int32_t* slaboff = c.take<int32_t>(nb * 4);
   int32_t* counts = c.take<int32_t>(16);
+  uint32_t* slaboffc = c.take<uint32_t>(nb * 6 * acm::slab_offset_words(g->Bs) * 4);
   if (f) {
     f->U = U; f->ACC = ACC; f->YA = YA; f->YB = YB; f->CHI = CHI; f->DENSE = DENSE; f->SLAB = SLAB;
     f->d_nbh = nbh; f->d_binfo = binfo; f->d_blist = blist; f->d_slabidx = slabidx;
@@ -215,7 +217,7 @@ size_t carve(acm_forest* f, const acm_grid_params* g, char* base) {
     f->d_norms = norms; f->d_maxbits = maxbits; f->d_ind = ind; f->d_chir = chir; f->d_diag = diag;
     f->d_err = errf;
     f->d_ltab = ltab; f->d_bslot = bslot; f->d_finer = finer; f->d_fwmask = fwmask; f->d_slabmask = slabmask;
-    f->d_fwoff = fwoff; f->d_slaboff = slaboff; f->d_counts = counts;
+    f->d_fwoff = fwoff; f->d_slaboff = slaboff; f->d_counts = counts; f->d_slaboffc = slaboffc;
   }
   return c.off;
 }
@@ -308,13 +310,13 @@ T* reg_ptr(acm_forest* f, void* r) { return reinterpret_cast<T*>(r); }
 
 // Fine wins + coarse-face slabs on a register (the per-stage synchronisation).
 template <typename T>
-acm_status sync_stage(acm_forest* f, T* reg) {
+acm_status sync_stage(acm_forest* f, T* reg, int use_slab_cache = 0) {
   const int Bs = f->gp.Bs;
   const int64_t n = (int64_t)f->order.size();
   acm::launch_fine_wins<T>(Bs, reg, f->d_fw, f->d_counts, 26 * n, f->d_nbh, f->d_blist, f->st);
   CKL();
   acm::launch_coarse_slabs<T>(Bs, reg, reinterpret_cast<T*>(f->SLAB), f->d_slabt, f->d_counts + 1, 6 * n, f->d_nbh,
-                              f->st);
+                              f->d_slaboffc, use_slab_cache, f->st);
   CKL();
   f->launches += 2;
   return ACM_OK;
@@ -425,7 +427,8 @@ acm_status rk4(acm_forest* f, double dt, double* dt_used) {
     T* in = s == 1 ? U : (s == 2 ? YA : (s == 3 ? YB : YA));
     T* out = s == 1 ? YA : (s == 2 ? YB : (s == 3 ? YA : U));
     if (f->timing) CK(cudaEventRecord(f->ev[3 * (s - 1)], f->st));
-    acm_status st = sync_stage<T>(f, in);
+    // stage 1 looks up the slabs' source points and caches them for stages 2-4 (same grid)
+    acm_status st = sync_stage<T>(f, in, s > 1);
     if (st) return st;
     if (f->timing) CK(cudaEventRecord(f->ev[3 * (s - 1) + 1], f->st));
     acm::StageK<T> a;

@@ -89,9 +89,12 @@ template <typename T>
 void launch_fine_wins(int Bs, T* reg, const int2* tasks, const int32_t* ntasks, int64_t max_tasks,
                       const int32_t* nbh, const int32_t* blist, cudaStream_t st);
 
+// offc: per-slab cache of the leaf lookups (slab_offset_words(Bs) words per slab) or nullptr;
+// use_cache = 0 fills it, 1 reads it (valid while the grid is unchanged).
 template <typename T>
 void launch_coarse_slabs(int Bs, const T* reg, T* slab, const int4* tasks, const int32_t* ntasks,
-                         int64_t max_tasks, const int32_t* nbh, cudaStream_t st);
+                         int64_t max_tasks, const int32_t* nbh, uint32_t* offc, int use_cache, cudaStream_t st);
+size_t slab_offset_words(int Bs);
 
 // Streaming multiprocessors of the current device (cached per device).
 int sm_count();

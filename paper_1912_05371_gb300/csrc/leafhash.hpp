@@ -1,6 +1,5 @@
-// Leaf-map entry and hash shared by the host tree (forest.cpp) and the device topology kernels
-// (topo.cu): the device reads a byte copy of the host's open-addressing table, so both sides
-// must probe with the same function.
+// Leaf-map entry and box hash, shared by the host tree (forest.cpp) and the device leaf table of
+// the topology kernels (topo.cu).
 #pragma once
 
 #include <cstdint>
@@ -21,11 +20,19 @@ struct LeafEntry {
 };
 static_assert(sizeof(LeafEntry) == 20, "LeafEntry must be 5 packed int32");
 
+// Combine the four coordinates, then mix all bits into the low ones (the 64-bit finaliser of
+// MurmurHash3): tables index with the low bits, and without the final mixing neighbouring boxes
+// fall into long runs of occupied entries under linear probing.
 ACM_HD uint64_t leaf_hash(int32_t J, int32_t x, int32_t y, int32_t z) {
   uint64_t h = (uint64_t)(uint32_t)J * 0x9E3779B97F4A7C15ull;
   h ^= (uint64_t)(uint32_t)x + 0x7F4A7C159E3779B9ull + (h << 6) + (h >> 2);
   h ^= (uint64_t)(uint32_t)y + 0x94D049BB133111EBull + (h << 6) + (h >> 2);
   h ^= (uint64_t)(uint32_t)z + 0xBF58476D1CE4E5B9ull + (h << 6) + (h >> 2);
+  h ^= h >> 33;
+  h *= 0xff51afd7ed558ccdull;
+  h ^= h >> 33;
+  h *= 0xc4ceb9fe1a85ec53ull;
+  h ^= h >> 33;
   return h;
 }
 

@@ -15,22 +15,6 @@ namespace {
 
 __constant__ int kFaceBoxT[6] = {12, 14, 10, 16, 4, 22};
 
-// Probe the table for box (J, x, y, z) (already wrapped); -1 if it is not a leaf.  The table
-// always holds empty entries (capacity >= 2 x leaves), so a probe ends long before `cap` steps;
-// the bound is only a guard (error flag bit 2).
-__device__ __forceinline__ int leaf_get(const TreeK& t, int J, int x, int y, int z, int* err) {
-  size_t i = (size_t)(leaf_hash(J, x, y, z) & t.mask);
-  for (unsigned long long n = 0; n <= t.mask; ++n) {
-    const int s = t.tab[i];
-    if (s < 0) return -1;
-    const int4 k = t.box[s];
-    if (k.x == J && k.y == x && k.z == y && k.w == z) return s;
-    i = (i + 1) & (size_t)t.mask;
-  }
-  atomicOr(err, 4);
-  return -1;
-}
-
 // Insert every leaf (rank r: box binfo[r], slot blist[r]) into the table (all entries -1 before)
 // and record its box by slot.  Linear probing with compare-and-swap on the slot word.
 __global__ void __launch_bounds__(256) k_index(TreeK t, const int4* binfo, const int32_t* blist, int64_t n,
@@ -48,9 +32,11 @@ __global__ void __launch_bounds__(256) k_index(TreeK t, const int4* binfo, const
   atomicOr(err, 4);
 }
 
+// Periodic wrap of a neighbour coordinate (within one box of the range: no division).
 __device__ __forceinline__ int wrap_axis(long long v, long long n) {
-  v %= n;
-  return (int)(v < 0 ? v + n : v);
+  if (v < 0) v += n;
+  else if (v >= n) v -= n;
+  return (int)v;
 }
 
 // Status of the level-J box (x, y, z) (unwrapped) as seen from a neighbour: a leaf, covered by a
@@ -61,6 +47,10 @@ struct DevStatus {
   int slot[8];
 };
 
+// The box itself, its parent and its 8 children are looked up together: the first probe of each
+// of the 10 keys is issued at once (independent loads), and only a key whose first table entry
+// belongs to another box continues probing.  The answer is the host tree's: leaf, else coarser
+// leaf, else refined.
 __device__ DevStatus box_status_dev(const TreeK& t, int J, long long x, long long y, long long z, int* err) {
   DevStatus st;
   st.type = kTypeNone;
@@ -70,29 +60,62 @@ __device__ DevStatus box_status_dev(const TreeK& t, int J, long long x, long lon
   const int kx = wrap_axis(x, (long long)t.nroot[0] << J);
   const int ky = wrap_axis(y, (long long)t.nroot[1] << J);
   const int kz = wrap_axis(z, (long long)t.nroot[2] << J);
-  const int s = leaf_get(t, J, kx, ky, kz, err);
-  if (s >= 0) {
+  int4 key[10];
+  key[0] = make_int4(J, kx, ky, kz);
+  key[1] = make_int4(J - 1, kx >> 1, ky >> 1, kz >> 1);      // only meaningful for J > 0
+#pragma unroll
+  for (int c = 0; c < 8; ++c) key[2 + c] = make_int4(J + 1, 2 * kx + (c & 1), 2 * ky + ((c >> 1) & 1), 2 * kz + ((c >> 2) & 1));
+  size_t pos[10];
+  int s[10];
+#pragma unroll
+  for (int q = 0; q < 10; ++q) {
+    pos[q] = (size_t)(leaf_hash(key[q].x, key[q].y, key[q].z, key[q].w) & t.mask);
+    s[q] = (q == 1 && J == 0) ? -1 : t.tab[pos[q]];
+  }
+  int4 kb[10];
+#pragma unroll
+  for (int q = 0; q < 10; ++q) kb[q] = s[q] >= 0 ? t.box[s[q]] : make_int4(-1, 0, 0, 0);
+  int res[10];
+#pragma unroll
+  for (int q = 0; q < 10; ++q) {
+    if (s[q] < 0) {
+      res[q] = -1;
+    } else if (kb[q].x == key[q].x && kb[q].y == key[q].y && kb[q].z == key[q].z && kb[q].w == key[q].w) {
+      res[q] = s[q];
+    } else {
+      // the first entry holds another box: continue the probe sequence
+      res[q] = -1;
+      size_t i = (pos[q] + 1) & (size_t)t.mask;
+      unsigned long long n = 1;
+      for (; n <= t.mask; ++n) {
+        const int e = t.tab[i];
+        if (e < 0) break;
+        const int4 k = t.box[e];
+        if (k.x == key[q].x && k.y == key[q].y && k.z == key[q].z && k.w == key[q].w) {
+          res[q] = e;
+          break;
+        }
+        i = (i + 1) & (size_t)t.mask;
+      }
+      if (n > t.mask) atomicOr(err, 4);
+    }
+  }
+  if (res[0] >= 0) {
     st.type = kTypeLeaf;
-    st.slot[0] = s;
+    st.slot[0] = res[0];
     return st;
   }
-  if (J > 0) {
-    const int sp = leaf_get(t, J - 1, kx >> 1, ky >> 1, kz >> 1, err);
-    if (sp >= 0) {
-      st.type = kTypeCoarser;
-      st.slot[0] = sp;
-      st.octant = (kx & 1) | ((ky & 1) << 1) | ((kz & 1) << 2);
-      return st;
-    }
+  if (J > 0 && res[1] >= 0) {
+    st.type = kTypeCoarser;
+    st.slot[0] = res[1];
+    st.octant = (kx & 1) | ((ky & 1) << 1) | ((kz & 1) << 2);
+    return st;
   }
   bool any = false;
 #pragma unroll
   for (int c = 0; c < 8; ++c) {
-    const int sc = leaf_get(t, J + 1, 2 * kx + (c & 1), 2 * ky + ((c >> 1) & 1), 2 * kz + ((c >> 2) & 1), err);
-    if (sc >= 0) {
-      st.slot[c] = sc;
-      any = true;
-    }
+    st.slot[c] = res[2 + c];
+    any = any || res[2 + c] >= 0;
   }
   if (any) st.type = kTypeRefined;
   return st;
