@@ -155,7 +155,8 @@ k_stage(const StageK<T> a, const TopoK tp, const PhysK ph, int* err) {
   // model and RK constants are read from the kernel parameters (constant bank), not registers;
   // so are the level's 1/h and 1/(12 h^2) (no per-thread FP64 division)
   const StageConst<T>& kc = a.kc;
-  const T ih = kc.ih[bi.x], ih2 = kc.ih2[bi.x];
+  // 1/h is applied once per right-hand side term, not to every difference
+  const T ih = kc.ih[bi.x], nu_ih2 = kc.nu * kc.ih2[bi.x], c0sq_ih = kc.c0sq * ih;
   const bool act = tid < BS * BS;
   const int x = act ? tid % BS : 0, y = act ? tid / BS : 0;
   (void)err;   // this kernel has no waits that can expire
@@ -255,6 +256,7 @@ k_stage(const StageK<T> a, const TopoK tp, const PhysK ph, int* err) {
   issue_halos(0, &buf[0][0][0]);
 
   const int ci = (y + 3) * W + x + 3;
+  const T sp_xy = ph.sponge ? tmax(sp[0][x], sp[1][y]) : T(0);   // the sponge profile's x/y part
   for (int z = 0; z <= M; ++z) {
     T(*B)[PW] = buf[z & 1];
     if (act) {
@@ -291,22 +293,23 @@ k_stage(const StageK<T> a, const TopoK tp, const PhysK ph, int* err) {
         const T xp3 = s[ci + 3], xm3 = s[ci - 3];
         const T yp1 = s[ci + W], ym1 = s[ci - W], yp2 = s[ci + 2 * W], ym2 = s[ci - 2 * W];
         const T yp3 = s[ci + 3 * W], ym3 = s[ci - 3 * W];
-        dx[f] = (kc.a1 * (xp1 - xm1) + kc.a2 * (xp2 - xm2) + kc.a3 * (xp3 - xm3)) * ih;
-        dy[f] = (kc.a1 * (yp1 - ym1) + kc.a2 * (yp2 - ym2) + kc.a3 * (yp3 - ym3)) * ih;
-        dz[f] = (kc.a1 * (q[f][4] - q[f][2]) + kc.a2 * (q[f][5] - q[f][1]) + kc.a3 * (q[f][6] - q[f][0])) * ih;
+        // h dx, h dy, h dz and 12 h^2 lap (the spacing factors are applied in K below)
+        dx[f] = kc.a1 * (xp1 - xm1) + kc.a2 * (xp2 - xm2) + kc.a3 * (xp3 - xm3);
+        dy[f] = kc.a1 * (yp1 - ym1) + kc.a2 * (yp2 - ym2) + kc.a3 * (yp3 - ym3);
+        dz[f] = kc.a1 * (q[f][4] - q[f][2]) + kc.a2 * (q[f][5] - q[f][1]) + kc.a3 * (q[f][6] - q[f][0]);
         if (f < 3) {
           const T lx = T(16) * (xp1 + xm1) - (xp2 + xm2) - T(30) * c;
           const T ly = T(16) * (yp1 + ym1) - (yp2 + ym2) - T(30) * c;
           const T lz = T(16) * (q[f][4] + q[f][2]) - (q[f][5] + q[f][1]) - T(30) * c;
-          lap[f] = (lx + ly + lz) * ih2;
+          lap[f] = lx + ly + lz;
         }
       }
       const T u = q[0][3], v = q[1][3], w = q[2][3], p = q[3][3];
       T K[4];
-      K[0] = -(u * dx[0] + v * dy[0] + w * dz[0]) - dx[3] + kc.nu * lap[0];
-      K[1] = -(u * dx[1] + v * dy[1] + w * dz[1]) - dy[3] + kc.nu * lap[1];
-      K[2] = -(u * dx[2] + v * dy[2] + w * dz[2]) - dz[3] + kc.nu * lap[2];
-      K[3] = -kc.c0sq * (dx[0] + dy[1] + dz[2]) - kc.cgam * p;
+      K[0] = -(u * dx[0] + v * dy[0] + w * dz[0] + dx[3]) * ih + nu_ih2 * lap[0];
+      K[1] = -(u * dx[1] + v * dy[1] + w * dz[1] + dy[3]) * ih + nu_ih2 * lap[1];
+      K[2] = -(u * dx[2] + v * dy[2] + w * dz[2] + dz[3]) * ih + nu_ih2 * lap[2];
+      K[3] = -c0sq_ih * (dx[0] + dy[1] + dz[2]) - kc.cgam * p;
       if (ph.mask) {
         const T cm = chiv * kc.inv_ceta;
         K[0] -= cm * u;
@@ -314,7 +317,7 @@ k_stage(const StageK<T> a, const TopoK tp, const PhysK ph, int* err) {
         K[2] -= cm * w;
       }
       if (ph.sponge) {
-        const T cs = tmax(tmax(sp[0][x], sp[1][y]), sp[2][z]) * kc.inv_csp;
+        const T cs = tmax(sp_xy, sp[2][z]) * kc.inv_csp;
         K[0] -= cs * (u - kc.uinf[0]);
         K[1] -= cs * (v - kc.uinf[1]);
         K[2] -= cs * (w - kc.uinf[2]);
