@@ -161,6 +161,44 @@ def oracle_rhs_sample(leaves, U_blocks, grid, phys, mask):
     return n * grid["Bs"] ** 3 / dt, dt, n
 
 
+def graph_comparison(A, stream, precision, nsteps=200):
+    """RK4 steps on config 1's grid (periodic unit cube, 4x4x4 blocks of 17^3, Taylor-Green,
+    nu = 1e-2, c0 = 10, CFL 0.5), three ways: one C-ABI call per step with the time step on the
+    host (a stream synchronisation per step), the same steps with the time step on the device
+    (plain launches, no synchronisation), and replayed from one captured CUDA graph."""
+    import torch
+    grid = dict(nroot=(1, 1, 1), root_len=1.0, Bs=17, g=4, Jmin=2, Jmax=2, precision=precision, max_blocks=64,
+                fd_scheme=1)
+    phys = dict(nu=1e-2, c0=10.0, C_gamma=1.0, cfl=0.5)
+    out = {}
+    for mode in ("host_dt_calls", "device_dt", "graph"):
+        f = A.Forest(grid, phys, stream=stream)
+        f.init_uniform(2)
+        f.set_ic(A.ACM_IC_TAYLOR_GREEN, [2 * math.pi, 1.0])
+
+        def run(n):
+            if mode == "host_dt_calls":
+                for _ in range(n):
+                    f.rk4_step(0.0)
+            else:
+                f.rk4_steps(n, 0.0, graph=(mode == "graph"))
+        run(5)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        run(nsteps)
+        e1.record(stream)
+        e1.synchronize()
+        out[mode] = e0.elapsed_time(e1) / nsteps
+        f.close()
+    pts = 64 * 17 ** 3 * 4
+    return {"workload": "Taylor-Green, periodic unit cube, 4x4x4 blocks of 17^3 (config 1 grid)",
+            "precision": f"fp{precision}", "steps": nsteps,
+            "ms_per_step": {k: round(v, 5) for k, v in out.items()},
+            "point_updates_per_s": {k: pts / (v * 1e-3) for k, v in out.items()},
+            "graph_speedup_vs_host_dt_calls": out["host_dt_calls"] / out["graph"]}
+
+
 def reduce_over_ranks(ms, point_updates, dist=None, device="cpu"):
     """Whole-job figures over the ranks of a replica run: the slowest rank's time and the sum of
     all ranks' point-updates (each rank runs its own replica: weak scaling)."""
@@ -340,6 +378,8 @@ def main():
             e2e = {"value": pu_e / te, "unit": UNIT, "h2d_bytes_per_step": h2d // args.steps,
                    "d2h_bytes_per_step": d2h // args.steps}
 
+        graph = graph_comparison(A, stream, args.precision) if rank == 0 else None
+
         cpu = None
         if rank == 0 and world == 1 and not args.no_cpu_baseline:
             # bounded sample (10-30 s of one core): the same workload with levels 2..4, its grid
@@ -376,7 +416,7 @@ def main():
                 "host_topology": (h1["host_topology_ms"] - h0["host_topology_ms"]) / args.steps,
                 "host_tree": (h1["host_tree_ms"] - h0["host_tree_ms"]) / args.steps,
                 "total": t_max / args.steps},
-            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "rk4_graph": graph,
             "clocks": clk,
         }
         print(json.dumps(line), flush=True)

@@ -164,6 +164,17 @@ acm_status acm_sync_ghosts(acm_forest* f, int reg, void* out, int out_on_device)
  * dt <= 0: use the CFL rule of Sec. 2.3.  *dt_used (may be NULL) receives the step. */
 acm_status acm_rk4_step(acm_forest* f, double dt, double* dt_used);
 
+/* nsteps classical RK4 steps (Sec. 2.3) on the current grid, without adaptation, with the time
+ * step computed on the device (dt > 0: fixed; dt <= 0: the CFL rule of Sec. 2.3 from the
+ * velocity max norm of the state, each step), so no step waits for the host.  use_graph = 1: the
+ * first step runs as plain launches, the second is captured into a CUDA graph and the remaining
+ * steps replay it (the graph is kept while the grid and the dt mode stay the same); the legacy
+ * default stream cannot be captured and always runs plain launches.  Bitwise the same result as
+ * nsteps calls of acm_rk4_step with the same dt rule.  Synchronises the stream at the end;
+ * *t_end (may be NULL) receives the simulated time, *graph_used (may be NULL) whether a graph
+ * ran.  No counterpart in the paper (a GPU execution form of its time loop). */
+acm_status acm_rk4_steps(acm_forest* f, int nsteps, double dt, int use_graph, double* t_end, int* graph_used);
+
 /* Right-hand side K = F(U) of eqs. (u_eqn-1, p_eqn-1) at every point of every block, after
  * the same synchronisation as an RK4 stage, written in block order (fields layout) to out
  * (device pointer if on_device, else host; n_elems = n_blocks*4*Bs^3).  For checks: the

@@ -57,6 +57,8 @@ EXPORTS = {
     "acm_init_grid": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.POINTER(C.c_int64)]),
     "acm_sync_ghosts": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int]),
     "acm_rk4_step": (C.c_int, [C.c_void_p, C.c_double, C.POINTER(C.c_double)]),
+    "acm_rk4_steps": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_int, C.POINTER(C.c_double),
+                                C.POINTER(C.c_int)]),
     "acm_refine_all": (C.c_int, [C.c_void_p]),
     "acm_rhs": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int]),
     "acm_coarsen": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int)]),
@@ -216,6 +218,14 @@ class Forest:
         d = C.c_double()
         self._check(self.L.acm_rk4_step(self.h, dt, C.byref(d)))
         return d.value
+
+    def rk4_steps(self, nsteps, dt=0.0, graph=True):
+        """nsteps RK4 steps on the current grid with the time step on the device; returns
+        (simulated time, whether a CUDA graph ran)."""
+        t = C.c_double()
+        g = C.c_int()
+        self._check(self.L.acm_rk4_steps(self.h, int(nsteps), float(dt), int(bool(graph)), C.byref(t), C.byref(g)))
+        return t.value, bool(g.value)
 
     def rhs(self):
         n = self.n_blocks()

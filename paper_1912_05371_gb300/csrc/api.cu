@@ -73,6 +73,15 @@ struct acm_forest {
   int32_t* d_slaboff = nullptr;
   int32_t* d_counts = nullptr;     // [0] fine-wins tasks, [1] coarse-face slabs
   uint32_t* d_slaboffc = nullptr;  // slab leaf-lookup cache (filled by RK stage 1)
+  double* d_rk = nullptr;          // device time step: [0] dt, [1] time, [2..9] stage coefficients
+  // RK4 steps captured as a CUDA graph (acm_rk4_steps), valid for one grid and one dt mode
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  int64_t graph_gen = -1;
+  double graph_dt = 0.0;
+  int64_t graph_launches = 0;
+  int64_t topo_gen = 0;            // incremented by every topology upload
+  double* h_scal = nullptr;        // pinned scalars (time in / out of the device)
 
   // host side of the current topology (the neighbourhood tables are built on the device from
   // the block list; the host leaf map is brought up to date only when a host query needs it)
@@ -210,6 +219,7 @@ size_t carve(acm_forest* f, const acm_grid_params* g, char* base) {
   int32_t* slaboff = c.take<int32_t>(nb * 4);
   int32_t* counts = c.take<int32_t>(16);
   uint32_t* slaboffc = c.take<uint32_t>(nb * 6 * acm::slab_offset_words(g->Bs) * 4);
+  double* rk = c.take<double>(32 * 8);
   if (f) {
     f->U = U; f->ACC = ACC; f->YA = YA; f->YB = YB; f->CHI = CHI; f->DENSE = DENSE; f->SLAB = SLAB;
     f->d_nbh = nbh; f->d_binfo = binfo; f->d_blist = blist; f->d_slabidx = slabidx;
@@ -218,6 +228,7 @@ size_t carve(acm_forest* f, const acm_grid_params* g, char* base) {
     f->d_err = errf;
     f->d_ltab = ltab; f->d_bslot = bslot; f->d_finer = finer; f->d_fwmask = fwmask; f->d_slabmask = slabmask;
     f->d_fwoff = fwoff; f->d_slaboff = slaboff; f->d_counts = counts; f->d_slaboffc = slaboffc;
+    f->d_rk = rk;
   }
   return c.off;
 }
@@ -290,6 +301,7 @@ acm_status upload_topology(acm_forest* f, std::vector<BoxKey>* new_order = nullp
   }
   CK(cudaEventRecord(f->ev_topo, f->st));
   f->topo_pending = true;
+  ++f->topo_gen;
   acm::TreeK tk;
   tk.tab = f->d_ltab;
   tk.box = f->d_bslot;
@@ -431,7 +443,7 @@ acm_status rk4(acm_forest* f, double dt, double* dt_used) {
     acm_status st = sync_stage<T>(f, in, s > 1);
     if (st) return st;
     if (f->timing) CK(cudaEventRecord(f->ev[3 * (s - 1) + 1], f->st));
-    acm::StageK<T> a;
+    acm::StageK<T> a{};
     a.in = in;
     a.U = U;
     a.acc = ACC;
@@ -464,6 +476,114 @@ acm_status rk4(acm_forest* f, double dt, double* dt_used) {
   f->stats.n_launches = f->launches - l0;
   f->stats_pending = f->timing;
   return ACM_OK;
+}
+
+// One RK4 step with the time step computed on the device (no host synchronisation): the
+// time-step kernel, then 4 x (synchronisation, stage kernel reading its coefficients from device
+// memory); stage 4 reduces the max norms of U^{n+1}, which the next step's time step reads.
+template <typename T>
+acm_status enqueue_rk4_device_dt(acm_forest* f, double dt) {
+  acm::RkK rp;
+  rp.dt_fixed = dt;
+  rp.h = h_of(f, f->Jtop);
+  rp.c0 = f->pp.c0;
+  rp.cfl = f->pp.cfl;
+  rp.cfl_eta = f->pp.cfl_eta;
+  rp.C_eta = f->pp.C_eta;
+  rp.cfl_nu = f->pp.cfl_nu;
+  rp.nu = f->pp.nu;
+  rp.mask = f->mask_on ? 1 : 0;
+  acm::launch_rk_coefs(f->d_maxbits, rp, f->d_rk, f->st);
+  CKL();
+  ++f->launches;
+  T* U = reinterpret_cast<T*>(f->U);
+  T* ACC = reinterpret_cast<T*>(f->ACC);
+  T* YA = reinterpret_cast<T*>(f->YA);
+  T* YB = reinterpret_cast<T*>(f->YB);
+  const acm::TopoK t = topo(f);
+  for (int s = 1; s <= 4; ++s) {
+    T* in = s == 1 ? U : (s == 2 ? YA : (s == 3 ? YB : YA));
+    T* out = s == 1 ? YA : (s == 2 ? YB : (s == 3 ? YA : U));
+    acm_status st = sync_stage<T>(f, in, s > 1);
+    if (st) return st;
+    acm::StageK<T> a{};
+    a.in = in;
+    a.U = U;
+    a.acc = ACC;
+    a.out = out;
+    a.chi = f->mask_on ? reinterpret_cast<const T*>(f->CHI) : nullptr;
+    a.slab = reinterpret_cast<const T*>(f->SLAB);
+    a.c_acc = 0.0;
+    a.c_out = 0.0;
+    a.coefp = f->d_rk + 2;
+    a.norms = nullptr;
+    if (s == 4) {
+      CK(cudaMemsetAsync(f->d_maxbits, 0, 8 * sizeof(unsigned long long), f->st));
+      a.norms = f->d_maxbits;
+    }
+    acm::launch_stage<T>(s, f->gp.Bs, a, t, f->phk, f->d_err, f->st);
+    CKL();
+    ++f->launches;
+  }
+  return ACM_OK;
+}
+
+// nsteps RK4 steps on the current grid.  With use_graph the first step runs as plain launches
+// and the second is captured into a CUDA graph that the remaining steps replay (the grid, and so
+// every launch, stays the same; the time step lives in device memory).  A stream that cannot be
+// captured (the legacy default stream) runs every step as plain launches.
+template <typename T>
+acm_status rk4_steps(acm_forest* f, int nsteps, double dt, int use_graph, int* graph_used) {
+  if (f->order.empty()) return fail(f, ACM_EINVAL, "empty forest");
+  if (nsteps < 0) return fail(f, ACM_EINVAL, "negative step count");
+  if (graph_used) *graph_used = 0;
+  if (nsteps == 0) return ACM_OK;
+  // the device clock starts from the host's; the first time step needs the norms of U
+  *f->h_scal = f->time;
+  CK(cudaMemcpyAsync(f->d_rk + 1, f->h_scal, sizeof(double), cudaMemcpyHostToDevice, f->st));
+  if (!(dt > 0) && !f->norms_fresh) {
+    acm_status s = max_norms_async<T>(f);
+    if (s) return s;
+  }
+  const bool can_graph = use_graph && f->st != nullptr;
+  for (int k = 0; k < nsteps; ++k) {
+    const bool reuse = can_graph && f->gexec && f->graph_gen == f->topo_gen && f->graph_dt == dt;
+    if (reuse) {
+      CK(cudaGraphLaunch(f->gexec, f->st));
+      f->launches += f->graph_launches;
+      if (graph_used) *graph_used = 1;
+    } else if (can_graph && k >= 1) {
+      // capture one step (every launch attribute was set by the plain step before)
+      if (f->gexec) { cudaGraphExecDestroy(f->gexec); f->gexec = nullptr; }
+      if (f->graph) { cudaGraphDestroy(f->graph); f->graph = nullptr; }
+      const int64_t l0 = f->launches;
+      CK(cudaStreamBeginCapture(f->st, cudaStreamCaptureModeThreadLocal));
+      acm_status s = enqueue_rk4_device_dt<T>(f, dt);
+      cudaGraph_t g = nullptr;
+      const cudaError_t ec = cudaStreamEndCapture(f->st, &g);
+      if (s) {
+        if (g) cudaGraphDestroy(g);
+        return s;
+      }
+      if (ec != cudaSuccess) return fail(f, ACM_ECUDA, std::string("graph capture: ") + cudaGetErrorString(ec));
+      f->graph = g;
+      CK(cudaGraphInstantiate(&f->gexec, f->graph, 0));
+      f->graph_gen = f->topo_gen;
+      f->graph_dt = dt;
+      f->graph_launches = f->launches - l0;
+      CK(cudaGraphLaunch(f->gexec, f->st));
+      if (graph_used) *graph_used = 1;
+    } else {
+      acm_status s = enqueue_rk4_device_dt<T>(f, dt);
+      if (s) return s;
+    }
+  }
+  CK(cudaMemcpyAsync(f->h_scal, f->d_rk, 2 * sizeof(double), cudaMemcpyDeviceToHost, f->st));
+  CK(cudaMemcpyAsync(f->h_err, f->d_err, sizeof(int), cudaMemcpyDeviceToHost, f->st));
+  CK(cudaStreamSynchronize(f->st));
+  f->time = f->h_scal[1];
+  f->norms_fresh = true;
+  return device_error(f);
 }
 
 template <typename T>
@@ -787,7 +907,7 @@ acm_status acm_create_forest(const acm_grid_params* grid, const acm_phys_params*
     acm_forest* f = fp;   // for CK
     const size_t nb = (size_t)grid->max_blocks;
     f->leaf_cap = acm::LeafMap::capacity_for(grid->max_blocks);
-    const size_t bytes = nb * sizeof(int4) + nb * 4 + nb + 8 * 256;
+    const size_t bytes = nb * sizeof(int4) + nb * 4 + nb + 9 * 256;
     CK(cudaMallocHost(&f->h_pinned, bytes));
     char* p = (char*)f->h_pinned;
     auto take = [&](size_t b) { char* q = p; p += (b + 255) & ~(size_t)255; return q; };
@@ -796,6 +916,7 @@ acm_status acm_create_forest(const acm_grid_params* grid, const acm_phys_params*
     f->h_finer = (uint8_t*)take(nb);
     f->h_err = (int*)take(16);
     *f->h_err = 0;
+    f->h_scal = (double*)take(8 * sizeof(double));
     f->fo.reset(new acm::Forest(grid->nroot, grid->Bs, grid->Jmin, grid->Jmax, grid->max_blocks));
     CK(cudaMemset(f->d_err, 0, 16 * sizeof(int)));
     CK(cudaMemset(f->d_counts, 0, 16 * sizeof(int32_t)));
@@ -812,6 +933,8 @@ acm_status acm_destroy_forest(acm_forest* f) {
   for (auto& e : f->ev)
     if (e) cudaEventDestroy(e);
   if (f->ev_topo) cudaEventDestroy(f->ev_topo);
+  if (f->gexec) cudaGraphExecDestroy(f->gexec);
+  if (f->graph) cudaGraphDestroy(f->graph);
   f->fo.reset();
   if (f->h_pinned) cudaFreeHost(f->h_pinned);
   delete f;
@@ -938,6 +1061,14 @@ acm_status acm_sync_ghosts(acm_forest* f, int reg, void* out, int on_device) {
 acm_status acm_rk4_step(acm_forest* f, double dt, double* dt_used) {
   if (!f) return ACM_EINVAL;
   return DISPATCH(f, rk4, f, dt, dt_used);
+}
+
+acm_status acm_rk4_steps(acm_forest* f, int nsteps, double dt, int use_graph, double* t_end, int* graph_used) {
+  if (!f) return ACM_EINVAL;
+  acm_status s = DISPATCH(f, rk4_steps, f, nsteps, dt, use_graph, graph_used);
+  if (s) return s;
+  if (t_end) *t_end = f->time;
+  return ACM_OK;
 }
 
 acm_status acm_refine_all(acm_forest* f) {

@@ -76,7 +76,18 @@ struct StageK {
   StageConst<T> kc;         // the constants above in the field precision (filled by launch_stage)
   // stage 4 only, if set: the max norms of U^{n+1} (layout and zeroing as for launch_maxnorm)
   unsigned long long* norms;
+  // if set, the stage reads its (c_acc, c_out) from coefp[2 (stage-1)], written on the device by
+  // launch_rk_coefs, instead of c_acc/c_out
+  const double* coefp;
 };
+
+// Parameters of the device time step (Sec. 2.3): CFL rule as on the host; h = finest spacing.
+struct RkK {
+  double dt_fixed;          // > 0: use it
+  double h, c0, cfl, cfl_eta, C_eta, cfl_nu, nu;
+  int mask;
+};
+void launch_rk_coefs(const unsigned long long* maxbits, const RkK& p, double* rk, cudaStream_t st);
 
 // err: device int set to 1 if a bounded wait inside the kernel expired (never cleared here).
 template <typename T>

@@ -157,6 +157,13 @@ k_stage(const StageK<T> a, const TopoK tp, const PhysK ph, int* err) {
   const StageConst<T>& kc = a.kc;
   // 1/h is applied once per right-hand side term, not to every difference
   const T ih = kc.ih[bi.x], nu_ih2 = kc.nu * kc.ih2[bi.x], c0sq_ih = kc.c0sq * ih;
+  // RK coefficients: kernel parameters, or (steps with the time step on the device) the values
+  // the time-step kernel left in device memory
+  T c_acc = kc.c_acc, c_out = kc.c_out;
+  if (STAGE >= 1 && a.coefp) {
+    c_acc = T(a.coefp[2 * (STAGE - 1)]);
+    c_out = T(a.coefp[2 * (STAGE - 1) + 1]);
+  }
   const bool act = tid < BS * BS;
   const int x = act ? tid % BS : 0, y = act ? tid / BS : 0;
   (void)err;   // this kernel has no waits that can expire
@@ -329,17 +336,17 @@ k_stage(const StageK<T> a, const TopoK tp, const PhysK ph, int* err) {
         if (STAGE == 0) {
           a.acc[o] = K[f];
         } else if (STAGE == 1) {
-          a.acc[o] = q[f][3] + kc.c_acc * K[f];
-          a.out[o] = q[f][3] + kc.c_out * K[f];
+          a.acc[o] = q[f][3] + c_acc * K[f];
+          a.out[o] = q[f][3] + c_out * K[f];
         } else if (STAGE == 4) {
-          const T nv = Av[f] + kc.c_out * K[f];
+          const T nv = Av[f] + c_out * K[f];
           a.out[o] = nv;
           const T av = nv < T(0) ? -nv : nv;
           nm[f] = av > nm[f] ? av : nm[f];
           Uv[f] = nv;
         } else {
-          a.acc[o] = Av[f] + kc.c_acc * K[f];
-          a.out[o] = Uv[f] + kc.c_out * K[f];
+          a.acc[o] = Av[f] + c_acc * K[f];
+          a.out[o] = Uv[f] + c_out * K[f];
         }
       }
       if (STAGE == 4) {
@@ -375,6 +382,28 @@ k_stage(const StageK<T> a, const TopoK tp, const PhysK ph, int* err) {
   }
 }
 
+// Time step of one RK4 step on the device (Sec. 2.3): dt_fixed if > 0, else the CFL rule from the
+// velocity max norm of the last reduction (maxbits[4]); writes rk[0] = dt, rk[1] += dt (time)
+// and the stage coefficients rk[2..9] = (c_acc, c_out) of stages 1..4, in double, by the same
+// expressions as the host path.
+__global__ void k_rk_coefs(const unsigned long long* maxbits, RkK p, double* rk) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double dt = p.dt_fixed;
+  if (!(dt > 0.0)) {
+    const double u = __longlong_as_double((long long)maxbits[4]);
+    const double ueig = fabs(u) + sqrt(u * u + p.c0 * p.c0);
+    dt = p.cfl * p.h / ueig;
+    if (p.mask) dt = fmin(dt, p.cfl_eta * p.C_eta);
+    if (p.nu > 0) dt = fmin(dt, p.cfl_nu * p.h * p.h / p.nu);
+  }
+  rk[0] = dt;
+  rk[1] += dt;
+  rk[2] = dt / 6.0; rk[3] = dt / 2.0;
+  rk[4] = dt / 3.0; rk[5] = dt / 2.0;
+  rk[6] = dt / 3.0; rk[7] = dt;
+  rk[8] = dt / 3.0; rk[9] = dt / 6.0;
+}
+
 template <typename T, int BS>
 void launch_stage_bs(int stage, const StageK<T>& s, const TopoK& t, const PhysK& p, int* err, cudaStream_t st) {
   if (t.n <= 0) return;
@@ -407,6 +436,10 @@ void launch_stage(int stage, int Bs, const StageK<T>& s, const TopoK& t, const P
   }
   if (Bs == 17) launch_stage_bs<T, 17>(stage, a, t, p, err, st);
   else launch_stage_bs<T, 9>(stage, a, t, p, err, st);
+}
+
+void launch_rk_coefs(const unsigned long long* maxbits, const RkK& p, double* rk, cudaStream_t st) {
+  k_rk_coefs<<<1, 32, 0, st>>>(maxbits, p, rk);
 }
 
 template void launch_stage<float>(int, int, const StageK<float>&, const TopoK&, const PhysK&, int*, cudaStream_t);

@@ -144,6 +144,35 @@ def test_mask_matches_oracle(A, prec, Bs):
     assert np.all((chi >= 0.0) & (chi <= 1.0))
 
 
+@pytest.mark.parametrize("prec,Bs", [(64, 9), (32, 17)])
+def test_rk4_steps_device_dt_and_graph_match_host_steps(A, prec, Bs):
+    """acm_rk4_steps (time step on the device, CUDA graph replay) gives bitwise the result of the
+    same number of acm_rk4_step calls with the CFL rule, and the same simulated time."""
+    leaves = random_graded_leaves(17, nroot=(2, 1, 1), J0=1, Jmax=3, n_target=70)
+    grid = _grid(Bs=Bs, precision=prec)
+    phys = _phys(sponge=1, C_sp=0.05, u_inf=(0.4, -0.1, 0.2), p_inf=0.1, sponge_L=(2.0, 1.0, 1.0),
+                 sponge_width=0.2, sponge_delta=0.05)
+    mask = (0.8, 0.5, 0.5, 0.2, 0.04)
+    import torch
+    st = torch.cuda.Stream()
+    runs = []
+    with torch.cuda.stream(st):
+        for mode in ("host", "device", "graph"):
+            f, _ = _pair(A, grid, phys, leaves, fn_seed=17, mask=mask)
+            used = False
+            if mode == "host":
+                t = 0.0
+                for _ in range(5):
+                    t += f.rk4_step(0.0)
+            else:
+                t, used = f.rk4_steps(5, 0.0, graph=(mode == "graph"))
+            runs.append((mode, t, used, f.read_fields()))
+    (_, t0, _, u0), (_, t1, g1, u1), (_, t2, g2, u2) = runs
+    assert not g1
+    assert t1 == t0 and t2 == t0
+    assert np.array_equal(u1, u0) and np.array_equal(u2, u0)
+
+
 @pytest.mark.parametrize("prec", [64, 32])
 def test_indicators_match_oracle(A, prec):
     leaves = random_graded_leaves(14, nroot=(2, 1, 1), J0=1, Jmax=3, n_target=70)
