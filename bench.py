@@ -199,6 +199,51 @@ def graph_comparison(A, stream, precision, nsteps=200):
             "graph_speedup_vs_host_dt_calls": out["host_dt_calls"] / out["graph"]}
 
 
+def batched_comparison(A, precision, seed=0, n=64, nsteps=10):
+    """The batched workload: n independent instances (periodic unit cubes, N_b ~ U{8..512} blocks
+    of 17^3 on random graded layouts over levels 2..5, pulse + vortex ring, seeded), nsteps RK4
+    steps each, three ways: one C-ABI call per instance and step (time step on the host), all
+    instances' steps as plain launches on their own streams (time step on the device), and one
+    CUDA graph per step holding every instance as a parallel branch."""
+    import torch
+    from paper_1912_05371_gb300 import workloads as W
+    insts = W.batched_instances(seed=seed, n=n)
+    phys = dict(nu=1e-3, c0=10.0, C_gamma=0.0, cfl=0.5)
+    streams = [torch.cuda.Stream() for _ in insts]
+    forests = []
+    for inst, s in zip(insts, streams):
+        grid = dict(nroot=(1, 1, 1), root_len=1.0, Bs=17, g=4, Jmin=1, Jmax=5, precision=precision,
+                    max_blocks=len(inst["leaves"]) + 8, fd_scheme=1)
+        f = A.Forest(grid, phys, stream=s)
+        f.set_leaves(inst["leaves"])
+        f.set_ic(A.ACM_IC_PULSE_RING, inst["ic"])
+        forests.append(f)
+    nb = sum(len(i["leaves"]) for i in insts)
+    pts = nb * 17 ** 3 * 4 * nsteps
+    out = {}
+    for mode in ("per_instance_calls", "streams", "graph"):
+        def run(k):
+            if mode == "per_instance_calls":
+                for _ in range(k):
+                    for f in forests:
+                        f.rk4_step(0.0)
+            else:
+                A.rk4_steps_batch(forests, k, 0.0, graph=(mode == "graph"))
+        run(2)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        run(nsteps)
+        torch.cuda.synchronize()
+        out[mode] = time.perf_counter() - t0
+    for f in forests:
+        f.close()
+    return {"workload": f"{n} independent instances, {nb} blocks of 17^3 in all (N_b ~ U{{8..512}}, levels 1..5), "
+                        f"pulse + vortex ring, seed {seed}", "precision": f"fp{precision}", "steps": nsteps,
+            "ms_per_step": {k: round(1e3 * v / nsteps, 4) for k, v in out.items()},
+            "point_updates_per_s": {k: pts / v for k, v in out.items()},
+            "graph_speedup_vs_per_instance_calls": out["per_instance_calls"] / out["graph"]}
+
+
 def reduce_over_ranks(ms, point_updates, dist=None, device="cpu"):
     """Whole-job figures over the ranks of a replica run: the slowest rank's time and the sum of
     all ranks' point-updates (each rank runs its own replica: weak scaling)."""
@@ -270,6 +315,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--max-blocks", type=int, default=40000)
+    ap.add_argument("--no-batched", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -379,6 +425,7 @@ def main():
                    "d2h_bytes_per_step": d2h // args.steps}
 
         graph = graph_comparison(A, stream, args.precision) if rank == 0 else None
+        batched = batched_comparison(A, args.precision) if rank == 0 and not args.no_batched else None
 
         cpu = None
         if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -417,6 +464,7 @@ def main():
                 "host_tree": (h1["host_tree_ms"] - h0["host_tree_ms"]) / args.steps,
                 "total": t_max / args.steps},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "rk4_graph": graph,
+            "batched": batched,
             "clocks": clk,
         }
         print(json.dumps(line), flush=True)

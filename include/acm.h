@@ -101,8 +101,14 @@ typedef struct {
 /* Initial conditions for acm_set_ic (params in order):
  *  ACM_IC_TAYLOR_GREEN: k, amp     u = amp sin kx cos ky cos kz, v = -amp cos kx sin ky cos kz, w = p = 0
  *  ACM_IC_UNIFORM:      u0, v0, w0, p0
- *  ACM_IC_PULSE:        cx, cy, cz, width, amp, Lx, Ly, Lz   (Gaussian p, u = 0, nearest periodic image) */
-enum { ACM_IC_TAYLOR_GREEN = 1, ACM_IC_UNIFORM = 2, ACM_IC_PULSE = 3 };
+ *  ACM_IC_PULSE:        cx, cy, cz, width, amp, Lx, Ly, Lz   (Gaussian p, u = 0, nearest periodic image)
+ *  ACM_IC_PULSE_RING:   the pulse's 8 parameters, then ring cx, cy, cz, axis nx, ny, nz, R, gamma,
+ *                       sigma (17 in all): the pulse's p plus a vortex ring's velocity
+ *                       u = curl(psi e_theta), psi = gamma/(2 pi) (rho/R) exp(-((rho-R)^2 + zeta^2)/sigma^2)
+ *                       in ring coordinates (zeta along the unit axis, rho from it), nearest
+ *                       periodic image of the centre -- the synthetic input of the batched
+ *                       workload (no counterpart in the paper). */
+enum { ACM_IC_TAYLOR_GREEN = 1, ACM_IC_UNIFORM = 2, ACM_IC_PULSE = 3, ACM_IC_PULSE_RING = 4 };
 
 /* Masks for acm_set_mask: ACM_MASK_NONE; ACM_MASK_SPHERE: cx, cy, cz, R, delta with
  * chi = (1 - tanh(d/delta))/2, d the signed distance to the sphere (Sec. 2.2 smoothed mask). */
@@ -136,7 +142,8 @@ acm_status acm_set_leaves(acm_forest* f, const int32_t* level, const int32_t* gx
                           const int32_t* gy, const int32_t* gz, int64_t n);
 
 /* Evaluate an initial condition (see ACM_IC_*) at every point of every block, in FP64,
- * stored in the forest precision. */
+ * stored in the forest precision.  n_params must be at least the kind's count (2, 4, 8, 17)
+ * and at most 24; ACM_EINVAL otherwise. */
 acm_status acm_set_ic(acm_forest* f, int ic_kind, const double* params, int n_params);
 
 /* Set the obstacle mask chi (Sec. 2.2), evaluated analytically on every block now and after
@@ -174,6 +181,16 @@ acm_status acm_rk4_step(acm_forest* f, double dt, double* dt_used);
  * *t_end (may be NULL) receives the simulated time, *graph_used (may be NULL) whether a graph
  * ran.  No counterpart in the paper (a GPU execution form of its time loop). */
 acm_status acm_rk4_steps(acm_forest* f, int nsteps, double dt, int use_graph, double* t_end, int* graph_used);
+
+/* acm_rk4_steps for n distinct forests on one device (independent instances, each on its own
+ * stream): every step enqueues each instance's step on its stream, so the instances run side by
+ * side.  use_graph = 1: the second step of all instances is captured into ONE CUDA graph (each
+ * instance a parallel branch forked from forests[0]'s stream) and replayed for the remaining
+ * steps.  Synchronises every stream at the end; t_end (may be NULL) receives n simulated times.
+ * Errors are reported on the forest concerned (forests[0] for capture errors).  No counterpart
+ * in the paper. */
+acm_status acm_rk4_steps_batch(acm_forest* const* forests, int n, int nsteps, double dt, int use_graph,
+                               double* t_end, int* graph_used);
 
 /* Right-hand side K = F(U) of eqs. (u_eqn-1, p_eqn-1) at every point of every block, after
  * the same synchronisation as an RK4 stage, written in block order (fields layout) to out

@@ -159,6 +159,58 @@ def ic_pulse(X, Y, Z, centre, width, amp, L):
     return np.stack([z, z.copy(), z.copy(), p])
 
 
+def _nearest_image(c, c0, Lc):
+    d = c - c0
+    return d - Lc * np.round(d / Lc)
+
+
+def ic_vortex_ring(X, Y, Z, centre, axis, R, gamma, sigma, L):
+    """Vortex ring velocity u = curl(psi e_theta), p = 0 (a synthetic divergence-free field).
+
+    In ring coordinates about the centre (nearest periodic image) and the unit axis n: zeta =
+    d.n, r_perp = d - zeta n, rho = |r_perp|, e_theta = n x r_perp / rho.  The azimuthal vector
+    potential psi = gamma / (2 pi) (rho / R) exp(-((rho - R)^2 + zeta^2) / sigma^2) vanishes on the
+    axis; its curl in cylindrical coordinates, u_rho = -d psi/d zeta and
+    u_zeta = (1/rho) d(rho psi)/d rho, is with E the exponential and K = gamma E / (2 pi R)
+        u = K [ (2 zeta / sigma^2) r_perp + (2 - 2 rho (rho - R) / sigma^2) n ]."""
+    n = np.asarray(axis, dtype=np.float64)
+    n = n / np.linalg.norm(n)
+    d = [_nearest_image(c, c0, Lc) for c, c0, Lc in zip((X, Y, Z), centre, L)]
+    zeta = d[0] * n[0] + d[1] * n[1] + d[2] * n[2]
+    rp = [d[a] - zeta * n[a] for a in range(3)]
+    rho = np.sqrt(rp[0] ** 2 + rp[1] ** 2 + rp[2] ** 2)
+    E = np.exp(-((rho - R) ** 2 + zeta ** 2) / (sigma * sigma))
+    K = gamma * E / (2.0 * math.pi * R)
+    a_r = K * 2.0 * zeta / (sigma * sigma)
+    a_n = K * (2.0 - 2.0 * rho * (rho - R) / (sigma * sigma))
+    u = [a_r * rp[a] + a_n * n[a] for a in range(3)]
+    return np.stack([u[0], u[1], u[2], np.zeros_like(X)])
+
+
+def vortex_ring_potential(X, Y, Z, centre, axis, R, gamma, sigma, L):
+    """The vector potential psi e_theta of ic_vortex_ring (for checks of its curl)."""
+    n = np.asarray(axis, dtype=np.float64)
+    n = n / np.linalg.norm(n)
+    d = [_nearest_image(c, c0, Lc) for c, c0, Lc in zip((X, Y, Z), centre, L)]
+    zeta = d[0] * n[0] + d[1] * n[1] + d[2] * n[2]
+    rp = [d[a] - zeta * n[a] for a in range(3)]
+    rho = np.sqrt(rp[0] ** 2 + rp[1] ** 2 + rp[2] ** 2)
+    psi_over_rho = gamma / (2.0 * math.pi * R) * np.exp(-((rho - R) ** 2 + zeta ** 2) / (sigma * sigma))
+    # psi e_theta = (psi / rho) (n x r_perp)
+    cx = n[1] * rp[2] - n[2] * rp[1]
+    cy = n[2] * rp[0] - n[0] * rp[2]
+    cz = n[0] * rp[1] - n[1] * rp[0]
+    return np.stack([psi_over_rho * cx, psi_over_rho * cy, psi_over_rho * cz])
+
+
+def ic_pulse_ring(X, Y, Z, pulse, ring, L):
+    """Gaussian pressure pulse plus vortex-ring velocity: pulse = (centre, width, amp), ring =
+    (centre, axis, R, gamma, sigma)."""
+    out = ic_vortex_ring(X, Y, Z, *ring, L)
+    out[3] = ic_pulse(X, Y, Z, *pulse, L)[3]
+    return out
+
+
 # ---- time step, RK4 ---------------------------------------------------------------------------
 
 def time_step(ph, u_max, h_min, masked):

@@ -14,7 +14,7 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_lib", "libacm.so")
 
-ACM_IC_TAYLOR_GREEN, ACM_IC_UNIFORM, ACM_IC_PULSE = 1, 2, 3
+ACM_IC_TAYLOR_GREEN, ACM_IC_UNIFORM, ACM_IC_PULSE, ACM_IC_PULSE_RING = 1, 2, 3, 4
 ACM_MASK_NONE, ACM_MASK_SPHERE = 0, 1
 ACM_REG_U = 0
 
@@ -59,6 +59,8 @@ EXPORTS = {
     "acm_rk4_step": (C.c_int, [C.c_void_p, C.c_double, C.POINTER(C.c_double)]),
     "acm_rk4_steps": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_int, C.POINTER(C.c_double),
                                 C.POINTER(C.c_int)]),
+    "acm_rk4_steps_batch": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_int, C.c_double, C.c_int,
+                                      C.POINTER(C.c_double), C.POINTER(C.c_int)]),
     "acm_refine_all": (C.c_int, [C.c_void_p]),
     "acm_rhs": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int]),
     "acm_coarsen": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int)]),
@@ -109,6 +111,20 @@ def _ptr(a):
 
 
 NOALLOC_MAX_BLOCKS = 16384
+
+
+def rk4_steps_batch(forests, nsteps, dt=0.0, graph=True):
+    """nsteps RK4 steps of several independent forests (each on its own stream), optionally as
+    one CUDA graph per step; returns (list of simulated times, whether a graph ran)."""
+    n = len(forests)
+    hs = (C.c_void_p * n)(*[f.h for f in forests])
+    t = (C.c_double * n)()
+    g = C.c_int()
+    st = lib().acm_rk4_steps_batch(hs, n, int(nsteps), float(dt), int(bool(graph)), t, C.byref(g))
+    if st != 0:
+        msg = lib().acm_status_string(st).decode()
+        raise AcmError(f"libacm status {st}: {msg}")
+    return list(t), bool(g.value)
 
 
 def max_norms_noalloc(fields, n_blocks, Bs, precision, norms_out, stream=None):

@@ -764,6 +764,32 @@ __global__ void __launch_bounds__(kNT) k_ic(T* reg, const int32_t* blist, const 
         r2 += d * d;
       }
       v[3] = ic.p[4] * exp(-r2 / (ic.p[3] * ic.p[3]));
+    } else if (ic.kind == 4) {   // pulse + vortex ring (curl of an azimuthal vector potential)
+      const double c[3] = {ic.p[0], ic.p[1], ic.p[2]}, Lb[3] = {ic.p[5], ic.p[6], ic.p[7]};
+      const double P[3] = {X, Y, Z};
+      double r2 = 0.0, d[3];
+      for (int a = 0; a < 3; ++a) {
+        double e = P[a] - c[a];
+        e = e - Lb[a] * rint(e / Lb[a]);
+        r2 += e * e;
+        double g = P[a] - ic.p[8 + a];
+        d[a] = g - Lb[a] * rint(g / Lb[a]);
+      }
+      v[3] = ic.p[4] * exp(-r2 / (ic.p[3] * ic.p[3]));
+      const double nn = sqrt(ic.p[11] * ic.p[11] + ic.p[12] * ic.p[12] + ic.p[13] * ic.p[13]);
+      const double n[3] = {ic.p[11] / nn, ic.p[12] / nn, ic.p[13] / nn};
+      const double R = ic.p[14], gam = ic.p[15], sg = ic.p[16];
+      const double zeta = d[0] * n[0] + d[1] * n[1] + d[2] * n[2];
+      double rp[3], rho2 = 0.0;
+      for (int a = 0; a < 3; ++a) {
+        rp[a] = d[a] - zeta * n[a];
+        rho2 += rp[a] * rp[a];
+      }
+      const double rho = sqrt(rho2);
+      const double E = exp(-((rho - R) * (rho - R) + zeta * zeta) / (sg * sg));
+      const double K = gam * E / (2.0 * 3.14159265358979323846 * R);
+      const double ar = K * 2.0 * zeta / (sg * sg), an = K * (2.0 - 2.0 * rho * (rho - R) / (sg * sg));
+      for (int a = 0; a < 3; ++a) v[a] = ar * rp[a] + an * n[a];
     }
     const int pi = L::idx(ix, iy, iz);
 #pragma unroll

@@ -809,7 +809,7 @@ acm_status set_ic(acm_forest* f, int kind, const double* params, int n) {
   f->norms_fresh = false;
   acm::IcK ic{};
   ic.kind = kind;
-  for (int i = 0; i < n && i < 8; ++i) ic.p[i] = params[i];
+  for (int i = 0; i < n && i < 24; ++i) ic.p[i] = params[i];
   acm::launch_ic<T>(f->gp.Bs, reinterpret_cast<T*>(f->U), f->d_blist, nullptr, (int64_t)f->order.size(),
                     f->d_binfo, f->phk, ic, f->st);
   CKL();
@@ -995,7 +995,8 @@ acm_status acm_set_leaves(acm_forest* f, const int32_t* level, const int32_t* gx
 
 acm_status acm_set_ic(acm_forest* f, int kind, const double* params, int n) {
   if (!f) return ACM_EINVAL;
-  if (kind < 1 || kind > 3 || (n > 0 && !params)) return fail(f, ACM_EINVAL, "bad initial condition");
+  static const int need[5] = {0, 2, 4, 8, 17};   // parameters each kind reads
+  if (kind < 1 || kind > 4 || n < need[kind] || n > 24 || !params) return fail(f, ACM_EINVAL, "bad initial condition");
   if (f->order.empty()) return fail(f, ACM_EINVAL, "empty forest");
   acm_status s = DISPATCH(f, set_ic, f, kind, params, n);
   if (s) return s;
@@ -1068,6 +1069,118 @@ acm_status acm_rk4_steps(acm_forest* f, int nsteps, double dt, int use_graph, do
   acm_status s = DISPATCH(f, rk4_steps, f, nsteps, dt, use_graph, graph_used);
   if (s) return s;
   if (t_end) *t_end = f->time;
+  return ACM_OK;
+}
+
+acm_status acm_rk4_steps_batch(acm_forest* const* forests, int n, int nsteps, double dt, int use_graph,
+                               double* t_end, int* graph_used) {
+  if (!forests || n <= 0 || nsteps < 0) return ACM_EINVAL;
+  if (graph_used) *graph_used = 0;
+  for (int i = 0; i < n; ++i) {
+    if (!forests[i]) return ACM_EINVAL;
+    if (forests[i]->order.empty()) return fail(forests[i], ACM_EINVAL, "empty forest");
+    for (int j = 0; j < i; ++j)
+      if (forests[j] == forests[i]) return fail(forests[i], ACM_EINVAL, "forest listed twice");
+  }
+  if (nsteps == 0) return ACM_OK;
+  auto step = [&](acm_forest* f) {
+    return f->gp.precision == 64 ? enqueue_rk4_device_dt<double>(f, dt) : enqueue_rk4_device_dt<float>(f, dt);
+  };
+  // the device clocks start from the host's; the first time step needs the norms of each U
+  for (int i = 0; i < n; ++i) {
+    acm_forest* f = forests[i];
+    *f->h_scal = f->time;
+    CK(cudaMemcpyAsync(f->d_rk + 1, f->h_scal, sizeof(double), cudaMemcpyHostToDevice, f->st));
+    if (!(dt > 0) && !f->norms_fresh) {
+      acm_status s = f->gp.precision == 64 ? max_norms_async<double>(f) : max_norms_async<float>(f);
+      if (s) return s;
+    }
+  }
+  bool can_graph = use_graph != 0;
+  for (int i = 0; i < n; ++i)
+    if (!forests[i]->st) can_graph = false;
+  acm_forest* f = forests[0];             // for CK: errors are reported on the first forest
+  cudaStream_t origin = f->st;
+  std::vector<cudaEvent_t> ev((size_t)n + 1, nullptr);
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  std::vector<int64_t> per_step((size_t)n, 0);
+  auto cleanup = [&]() {
+    if (gexec) cudaGraphExecDestroy(gexec);
+    if (graph) cudaGraphDestroy(graph);
+    for (cudaEvent_t e : ev)
+      if (e) cudaEventDestroy(e);
+  };
+  acm_status rs = ACM_OK;
+  if (can_graph)
+    for (auto& e : ev)
+      if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) { cleanup(); return fail(f, ACM_ECUDA, "event"); }
+  for (int k = 0; k < nsteps && !rs; ++k) {
+    if (!can_graph || k == 0) {
+      // plain launches, every instance on its own stream (they run side by side)
+      for (int i = 0; i < n && !rs; ++i) rs = step(forests[i]);
+      continue;
+    }
+    if (!gexec) {
+      // the graph reads what the instances' streams wrote: order the origin after them
+      for (int i = 1; i < n; ++i) {
+        cudaEventRecord(ev[i], forests[i]->st);
+        cudaStreamWaitEvent(origin, ev[i], 0);
+      }
+      // capture one step of every instance as parallel branches forked from the origin stream
+      if (cudaStreamBeginCapture(origin, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cleanup();
+        return fail(f, ACM_ECUDA, "graph capture could not start");
+      }
+      cudaEventRecord(ev[0], origin);
+      for (int i = 1; i < n; ++i) cudaStreamWaitEvent(forests[i]->st, ev[0], 0);
+      for (int i = 0; i < n && !rs; ++i) {
+        const int64_t l0 = forests[i]->launches;
+        rs = step(forests[i]);
+        per_step[i] = forests[i]->launches - l0;
+      }
+      for (int i = 1; i < n; ++i) {
+        cudaEventRecord(ev[i], forests[i]->st);
+        cudaStreamWaitEvent(origin, ev[i], 0);
+      }
+      const cudaError_t ec = cudaStreamEndCapture(origin, &graph);
+      if (rs) break;
+      if (ec != cudaSuccess || cudaGraphInstantiate(&gexec, graph, 0) != cudaSuccess) {
+        cleanup();
+        return fail(f, ACM_ECUDA, std::string("graph capture: ") + cudaGetErrorString(ec));
+      }
+      if (graph_used) *graph_used = 1;
+    } else {
+      for (int i = 0; i < n; ++i) forests[i]->launches += per_step[i];
+    }
+    if (cudaGraphLaunch(gexec, origin) != cudaSuccess) { cleanup(); return fail(f, ACM_ECUDA, "graph launch"); }
+  }
+  if (gexec) {
+    // the instances' streams continue after the last replay
+    cudaEventRecord(ev[n], origin);
+    for (int i = 1; i < n; ++i) cudaStreamWaitEvent(forests[i]->st, ev[n], 0);
+  }
+  if (rs) {
+    cleanup();
+    return rs;
+  }
+  for (int i = 0; i < n; ++i) {
+    acm_forest* g = forests[i];
+    if (cudaMemcpyAsync(g->h_scal, g->d_rk, 2 * sizeof(double), cudaMemcpyDeviceToHost, g->st) != cudaSuccess ||
+        cudaMemcpyAsync(g->h_err, g->d_err, sizeof(int), cudaMemcpyDeviceToHost, g->st) != cudaSuccess) {
+      cleanup();
+      return fail(g, ACM_ECUDA, "copy");
+    }
+  }
+  for (int i = 0; i < n; ++i) {
+    acm_forest* g = forests[i];
+    if (cudaStreamSynchronize(g->st) != cudaSuccess) { cleanup(); return fail(g, ACM_ECUDA, "synchronise"); }
+    g->time = g->h_scal[1];
+    g->norms_fresh = true;
+    if (t_end) t_end[i] = g->time;
+    if (acm_status e = device_error(g)) { cleanup(); return e; }
+  }
+  cleanup();
   return ACM_OK;
 }
 

@@ -145,7 +145,7 @@ void launch_copy_blocks(int Bs, const T* src, T* dst, const int32_t* list, int s
 
 struct IcK {
   int kind;
-  double p[8];
+  double p[24];
 };
 // Initial condition on the blocks of rank list `ranks` (nullptr: all n blocks).
 template <typename T>

@@ -152,3 +152,30 @@ def cubic_coefficients(seed):
     coordinate, per component (tensor-product cubic)."""
     rng = np.random.default_rng(seed)
     return rng.uniform(-1.0, 1.0, size=(4, 4, 4, 4))
+
+
+def batched_instances(seed=0, n=64, nb_range=(8, 512), Jmax=5):
+    """Independent instances of the batched workload, all drawn from one seed: each a periodic
+    unit cube with a random 2:1-graded layout of about N_b ~ U{8..512} blocks (from level 2, or
+    level 1 when N_b < 64, up to Jmax), a Gaussian pressure pulse (width U[0.05, 0.2], amplitude
+    U[0.01, 1], centre uniform) and a vortex ring (radius U[0.1, 0.3], circulation parameter
+    U[0.5, 2], centre uniform, axis uniform on the sphere, core width a quarter of the radius).
+    Returns a list of dicts with leaves and the 17 ACM_IC_PULSE_RING parameters."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        nb = int(rng.integers(nb_range[0], nb_range[1] + 1))
+        J0 = 2 if nb >= 64 else 1
+        leaves = random_graded_leaves(int(rng.integers(0, 2 ** 31)), nroot=(1, 1, 1), J0=J0, Jmax=Jmax, n_target=nb)
+        pc = rng.uniform(0.0, 1.0, 3)
+        width = rng.uniform(0.05, 0.2)
+        amp = rng.uniform(0.01, 1.0)
+        rc = rng.uniform(0.0, 1.0, 3)
+        ax = rng.normal(size=3)
+        ax = ax / np.linalg.norm(ax)
+        R = rng.uniform(0.1, 0.3)
+        gamma = rng.uniform(0.5, 2.0)
+        params = [*pc, width, amp, 1.0, 1.0, 1.0, *rc, *ax, R, gamma, 0.25 * R]
+        out.append(dict(leaves=leaves, ic=[float(v) for v in params], J0=J0,
+                        pulse=(tuple(pc), width, amp), ring=(tuple(rc), tuple(ax), R, gamma, 0.25 * R)))
+    return out

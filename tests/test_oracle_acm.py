@@ -245,3 +245,47 @@ def test_full_scheme_self_convergence_is_fourth_order(scheme, T, lo):
     ratio = np.abs(sol[0] - sol[1]).max() / np.abs(sol[1] - sol[2]).max()
     assert lo < ratio < 2 ** 4.4, ratio
     assert G["fd_slope"] > 3.9
+
+
+def _periodic_d1(F, h, axis):
+    """4th-order central first derivative on a periodic grid (arrays indexed z, y, x)."""
+    return (8.0 * (np.roll(F, -1, axis) - np.roll(F, 1, axis)) - (np.roll(F, -2, axis) - np.roll(F, 2, axis))) / (12.0 * h)
+
+
+def test_vortex_ring_is_the_curl_of_its_potential_and_divergence_free():
+    """The ring velocity (config 3's synthetic input) equals the curl of its stated vector
+    potential, computed here by 4th-order differences independently of the closed form, and
+    has no divergence; axis points are finite."""
+    n = 128
+    h = 1.0 / n
+    x = np.arange(n) * h
+    Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
+    ring = ((0.45, 0.55, 0.5), (0.3, -0.5, 0.8), 0.2, 1.3, 0.08)
+    L = (1.0, 1.0, 1.0)
+    u = acm.ic_vortex_ring(X, Y, Z, *ring, L)
+    A = acm.vortex_ring_potential(X, Y, Z, *ring, L)
+    assert np.all(np.isfinite(u))
+    d = lambda F, ax: _periodic_d1(F, h, {0: 2, 1: 1, 2: 0}[ax])   # derivative along x, y, z
+    curl = np.stack([d(A[2], 1) - d(A[1], 2), d(A[0], 2) - d(A[2], 0), d(A[1], 0) - d(A[0], 1)])
+    scale = np.abs(u[:3]).max()
+    assert np.abs(curl - u[:3]).max() <= 2e-3 * scale
+    div = d(u[0], 0) + d(u[1], 1) + d(u[2], 2)
+    grad_scale = max(np.abs(d(u[c], c)).max() for c in range(3))
+    assert np.abs(div).max() <= 2e-3 * grad_scale
+    # the curl check fails for a plausible slip in the closed form (sign of the radial part)
+    nvec = np.array(ring[1]) / np.linalg.norm(ring[1])
+    radial = u[:3] - (u[:3] * nvec[:, None, None, None]).sum(0) * nvec[:, None, None, None]
+    wrong = u[:3] - 2.0 * radial
+    assert np.abs(curl - wrong).max() > 0.1 * scale
+
+
+def test_pulse_ring_combines_both_fields():
+    n = 16
+    x = np.arange(n) / n
+    Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
+    L = (1.0, 1.0, 1.0)
+    pulse = ((0.3, 0.6, 0.2), 0.1, 0.5)
+    ring = ((0.5, 0.5, 0.5), (0.0, 0.0, 1.0), 0.2, 1.0, 0.06)
+    F = acm.ic_pulse_ring(X, Y, Z, pulse, ring, L)
+    assert np.array_equal(F[:3], acm.ic_vortex_ring(X, Y, Z, *ring, L)[:3])
+    assert np.array_equal(F[3], acm.ic_pulse(X, Y, Z, *pulse, L)[3])
