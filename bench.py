@@ -344,6 +344,11 @@ def main():
         Bs3 = grid["Bs"] ** 3
         for _ in range(args.warmup):
             f.step(0.0)
+        # autotune the launch knobs on the evolved (refined) grid, then finish that step
+        f.refine_all()
+        tuned = f.autotune()
+        f.rk4_step(0.0)
+        f.coarsen()
         f.enable_timing(True)
 
         def barrier():
@@ -465,6 +470,7 @@ def main():
                 "total": t_max / args.steps},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "rk4_graph": graph,
             "batched": batched,
+            "autotune": {"fine_wins_ctas_per_sm": tuned[0], "slab_ctas_per_sm": tuned[1]},
             "clocks": clk,
         }
         print(json.dumps(line), flush=True)

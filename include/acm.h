@@ -192,6 +192,14 @@ acm_status acm_rk4_steps(acm_forest* f, int nsteps, double dt, int use_graph, do
 acm_status acm_rk4_steps_batch(acm_forest* const* forests, int n, int nsteps, double dt, int use_graph,
                                double* t_end, int* graph_used);
 
+/* Autotuner: on the current grid, time the two task-list kernels of the per-stage ghost
+ * synchronisation -- fine wins and the coarse-face halo slabs -- for each number of CTAs per SM
+ * walking the list (fine wins 2, 4, 8, 16; slabs 1, 2, 3) and keep the fastest of each for this
+ * forest (either output may be NULL).  Like every synchronisation it first lets finer leaves'
+ * values win on shared boundary points of U; nothing else of the state changes.  Synchronises
+ * the stream.  No counterpart in the paper. */
+acm_status acm_autotune(acm_forest* f, int* fw_ctas, int* slab_ctas);
+
 /* Right-hand side K = F(U) of eqs. (u_eqn-1, p_eqn-1) at every point of every block, after
  * the same synchronisation as an RK4 stage, written in block order (fields layout) to out
  * (device pointer if on_device, else host; n_elems = n_blocks*4*Bs^3).  For checks: the

@@ -59,6 +59,7 @@ EXPORTS = {
     "acm_rk4_step": (C.c_int, [C.c_void_p, C.c_double, C.POINTER(C.c_double)]),
     "acm_rk4_steps": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_int, C.POINTER(C.c_double),
                                 C.POINTER(C.c_int)]),
+    "acm_autotune": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "acm_rk4_steps_batch": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_int, C.c_double, C.c_int,
                                       C.POINTER(C.c_double), C.POINTER(C.c_int)]),
     "acm_refine_all": (C.c_int, [C.c_void_p]),
@@ -242,6 +243,13 @@ class Forest:
         g = C.c_int()
         self._check(self.L.acm_rk4_steps(self.h, int(nsteps), float(dt), int(bool(graph)), C.byref(t), C.byref(g)))
         return t.value, bool(g.value)
+
+    def autotune(self):
+        """Choose this forest's launch knobs by timing them on the current grid; returns the CTAs
+        per SM of the fine-wins and of the coarse-face slab kernels."""
+        a, b = C.c_int(), C.c_int()
+        self._check(self.L.acm_autotune(self.h, C.byref(a), C.byref(b)))
+        return a.value, b.value
 
     def rhs(self):
         n = self.n_blocks()

@@ -952,30 +952,30 @@ LayoutInfo layout_info(int precision, int Bs) {
 
 template <typename T>
 void launch_fine_wins(int Bs, T* reg, const int2* tasks, const int32_t* ntasks, int64_t max_tasks,
-                      const int32_t* nbh, const int32_t* blist, cudaStream_t st) {
+                      const int32_t* nbh, const int32_t* blist, int ctas_per_sm, cudaStream_t st) {
   if (max_tasks <= 0) return;
-  const int64_t g = std::min<int64_t>(max_tasks, 8 * (int64_t)sm_count());
+  const int64_t g = std::min<int64_t>(max_tasks, (int64_t)std::max(1, ctas_per_sm) * sm_count());
   ACM_BS_DISPATCH(Bs, k_fine_wins, <<<grid1(g), kNT, 0, st>>>(reg, tasks, ntasks, nbh, blist));
 }
 template <typename T, int BS>
 void launch_coarse_slabs_bs(const T* reg, T* slab, const int4* tasks, const int32_t* ntasks, int64_t max_tasks,
-                            const int32_t* nbh, uint32_t* offc, int use_cache, cudaStream_t st) {
+                            const int32_t* nbh, uint32_t* offc, int use_cache, int ctas_per_sm, cudaStream_t st) {
   static bool attr = false;             // opt in to more than 48 KB of dynamic shared memory once
   if (!attr) {
     cudaFuncSetAttribute(k_coarse_slabs<T, BS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SlabSmem<T, BS>::bytes);
     attr = true;
   }
-  // resident CTAs: 3 per SM (register-limited) for Bs = 17
-  const int64_t g = std::min<int64_t>(max_tasks, 3 * (int64_t)sm_count());
+  // CTAs walking the task list: ctas_per_sm per SM (at most 3 are resident for Bs = 17)
+  const int64_t g = std::min<int64_t>(max_tasks, (int64_t)std::max(1, ctas_per_sm) * sm_count());
   k_coarse_slabs<T, BS><<<grid1(g), SlabSmem<T, BS>::NT, SlabSmem<T, BS>::bytes, st>>>(reg, slab, tasks, ntasks, nbh,
                                                                                        offc, use_cache);
 }
 template <typename T>
 void launch_coarse_slabs(int Bs, const T* reg, T* slab, const int4* tasks, const int32_t* ntasks, int64_t max_tasks,
-                         const int32_t* nbh, uint32_t* offc, int use_cache, cudaStream_t st) {
+                         const int32_t* nbh, uint32_t* offc, int use_cache, int ctas_per_sm, cudaStream_t st) {
   if (max_tasks <= 0) return;
-  if (Bs == 17) launch_coarse_slabs_bs<T, 17>(reg, slab, tasks, ntasks, max_tasks, nbh, offc, use_cache, st);
-  else launch_coarse_slabs_bs<T, 9>(reg, slab, tasks, ntasks, max_tasks, nbh, offc, use_cache, st);
+  if (Bs == 17) launch_coarse_slabs_bs<T, 17>(reg, slab, tasks, ntasks, max_tasks, nbh, offc, use_cache, ctas_per_sm, st);
+  else launch_coarse_slabs_bs<T, 9>(reg, slab, tasks, ntasks, max_tasks, nbh, offc, use_cache, ctas_per_sm, st);
 }
 size_t slab_offset_words(int Bs) { return Bs == 17 ? SlabSmem<float, 17>::NOFF : SlabSmem<float, 9>::NOFF; }
 template <typename T>
@@ -1067,8 +1067,8 @@ void launch_scatter(int Bs, const T* dense, T* reg, const int32_t* blist, int64_
 }
 
 #define ACM_INST(T)                                                                                        \
-  template void launch_fine_wins<T>(int, T*, const int2*, const int32_t*, int64_t, const int32_t*, const int32_t*, cudaStream_t); \
-  template void launch_coarse_slabs<T>(int, const T*, T*, const int4*, const int32_t*, int64_t, const int32_t*, uint32_t*, int, cudaStream_t); \
+  template void launch_fine_wins<T>(int, T*, const int2*, const int32_t*, int64_t, const int32_t*, const int32_t*, int, cudaStream_t); \
+  template void launch_coarse_slabs<T>(int, const T*, T*, const int4*, const int32_t*, int64_t, const int32_t*, uint32_t*, int, int, cudaStream_t); \
   template void launch_sync_ext<T>(int, const T*, T*, int, const int32_t*, int64_t, const int32_t*, int, cudaStream_t); \
   template void launch_details<T>(int, const T*, const T*, const int32_t*, const int32_t*, const int32_t*, int64_t, const unsigned long long*, double*, double*, cudaStream_t); \
   template void launch_maxnorm<T>(int, const T*, const int32_t*, int64_t, unsigned long long*, cudaStream_t); \

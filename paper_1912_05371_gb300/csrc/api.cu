@@ -82,6 +82,9 @@ struct acm_forest {
   int64_t graph_launches = 0;
   int64_t topo_gen = 0;            // incremented by every topology upload
   double* h_scal = nullptr;        // pinned scalars (time in / out of the device)
+  // launch knobs chosen by acm_autotune (defaults until it runs)
+  int tune_fw_ctas = 8;            // fine-wins kernel: CTAs per SM walking the task list
+  int tune_slab_ctas = 3;          // coarse-face slab kernel: CTAs per SM walking the task list
 
   // host side of the current topology (the neighbourhood tables are built on the device from
   // the block list; the host leaf map is brought up to date only when a host query needs it)
@@ -325,10 +328,10 @@ template <typename T>
 acm_status sync_stage(acm_forest* f, T* reg, int use_slab_cache = 0) {
   const int Bs = f->gp.Bs;
   const int64_t n = (int64_t)f->order.size();
-  acm::launch_fine_wins<T>(Bs, reg, f->d_fw, f->d_counts, 26 * n, f->d_nbh, f->d_blist, f->st);
+  acm::launch_fine_wins<T>(Bs, reg, f->d_fw, f->d_counts, 26 * n, f->d_nbh, f->d_blist, f->tune_fw_ctas, f->st);
   CKL();
   acm::launch_coarse_slabs<T>(Bs, reg, reinterpret_cast<T*>(f->SLAB), f->d_slabt, f->d_counts + 1, 6 * n, f->d_nbh,
-                              f->d_slaboffc, use_slab_cache, f->st);
+                              f->d_slaboffc, use_slab_cache, f->tune_slab_ctas, f->st);
   CKL();
   f->launches += 2;
   return ACM_OK;
@@ -337,7 +340,7 @@ acm_status sync_stage(acm_forest* f, T* reg, int use_slab_cache = 0) {
 template <typename T>
 acm_status fine_wins(acm_forest* f, T* reg) {
   acm::launch_fine_wins<T>(f->gp.Bs, reg, f->d_fw, f->d_counts, 26 * (int64_t)f->order.size(), f->d_nbh, f->d_blist,
-                           f->st);
+                           f->tune_fw_ctas, f->st);
   CKL();
   ++f->launches;
   return ACM_OK;
@@ -874,6 +877,74 @@ void fill_phys(acm_forest* f) {
 
 }  // namespace
 
+namespace {
+
+// Time `launch` (reps times after one warm-up) on the forest's stream; median milliseconds.
+template <typename F>
+acm_status time_launches(acm_forest* f, F&& launch, int reps, float* ms_out) {
+  std::vector<float> v;
+  launch();
+  for (int r = 0; r < reps; ++r) {
+    CK(cudaEventRecord(f->ev[0], f->st));
+    launch();
+    CK(cudaEventRecord(f->ev[1], f->st));
+    CK(cudaEventSynchronize(f->ev[1]));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, f->ev[0], f->ev[1]));
+    v.push_back(ms);
+  }
+  CKL();
+  std::sort(v.begin(), v.end());
+  *ms_out = v[v.size() / 2];
+  return ACM_OK;
+}
+
+// The autotuner: on the current grid, time the two task-list kernels of the per-stage
+// synchronisation for each number of CTAs per SM walking the list (fine wins: 2, 4, 8, 16; coarse
+// faces: 1, 2, 3 -- at most 3 are resident) and keep the fastest of each.  Fine wins rewrites
+// stored boundary points with the values of finer leaves (what every synchronisation does first);
+// the slab kernel writes only the slab buffer.
+template <typename T>
+acm_status autotune(acm_forest* f, int* fw_ctas, int* slab_ctas) {
+  if (f->order.empty()) return fail(f, ACM_EINVAL, "empty forest");
+  const int64_t n = (int64_t)f->order.size();
+  T* U = reinterpret_cast<T*>(f->U);
+  float best = 1e30f;
+  int best_fw = f->tune_fw_ctas;
+  for (int c : {2, 4, 8, 16}) {
+    float ms = 0.f;
+    acm_status s = time_launches(f, [&]() {
+      acm::launch_fine_wins<T>(f->gp.Bs, U, f->d_fw, f->d_counts, 26 * n, f->d_nbh, f->d_blist, c, f->st);
+    }, 5, &ms);
+    if (s) return s;
+    f->launches += 6;
+    if (ms < best) { best = ms; best_fw = c; }
+  }
+  best = 1e30f;
+  int best_sc = f->tune_slab_ctas;
+  for (int c = 1; c <= 3; ++c) {
+    float ms = 0.f;
+    acm_status s = time_launches(f, [&]() {
+      acm::launch_coarse_slabs<T>(f->gp.Bs, U, reinterpret_cast<T*>(f->SLAB), f->d_slabt, f->d_counts + 1, 6 * n,
+                                  f->d_nbh, f->d_slaboffc, 0, c, f->st);
+    }, 5, &ms);
+    if (s) return s;
+    f->launches += 6;
+    if (ms < best) { best = ms; best_sc = c; }
+  }
+  f->tune_fw_ctas = best_fw;
+  f->tune_slab_ctas = best_sc;
+  f->norms_fresh = false;
+  // a captured graph holds the old launch knobs
+  if (f->gexec) { cudaGraphExecDestroy(f->gexec); f->gexec = nullptr; }
+  if (f->graph) { cudaGraphDestroy(f->graph); f->graph = nullptr; }
+  if (fw_ctas) *fw_ctas = best_fw;
+  if (slab_ctas) *slab_ctas = best_sc;
+  return ACM_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 size_t acm_pool_bytes(const acm_grid_params* grid) {
@@ -1182,6 +1253,11 @@ acm_status acm_rk4_steps_batch(acm_forest* const* forests, int n, int nsteps, do
   }
   cleanup();
   return ACM_OK;
+}
+
+acm_status acm_autotune(acm_forest* f, int* fw_ctas, int* slab_ctas) {
+  if (!f) return ACM_EINVAL;
+  return DISPATCH(f, autotune, f, fw_ctas, slab_ctas);
 }
 
 acm_status acm_refine_all(acm_forest* f) {

@@ -95,16 +95,19 @@ void launch_stage(int stage, int Bs, const StageK<T>& s, const TopoK& t, const P
                   cudaStream_t st);
 
 // The per-stage synchronisation kernels walk a task list whose length the device holds
-// (*ntasks, written by launch_topology); max_tasks bounds it and sizes the grid.
+// (*ntasks, written by launch_topology); max_tasks bounds it and sizes the grid, with
+// ctas_per_sm CTAs per SM.
 template <typename T>
 void launch_fine_wins(int Bs, T* reg, const int2* tasks, const int32_t* ntasks, int64_t max_tasks,
-                      const int32_t* nbh, const int32_t* blist, cudaStream_t st);
+                      const int32_t* nbh, const int32_t* blist, int ctas_per_sm, cudaStream_t st);
 
 // offc: per-slab cache of the leaf lookups (slab_offset_words(Bs) words per slab) or nullptr;
 // use_cache = 0 fills it, 1 reads it (valid while the grid is unchanged).
+// ctas_per_sm: resident CTAs per SM the grid is sized for (1..3 for Bs = 17).
 template <typename T>
 void launch_coarse_slabs(int Bs, const T* reg, T* slab, const int4* tasks, const int32_t* ntasks,
-                         int64_t max_tasks, const int32_t* nbh, uint32_t* offc, int use_cache, cudaStream_t st);
+                         int64_t max_tasks, const int32_t* nbh, uint32_t* offc, int use_cache, int ctas_per_sm,
+                         cudaStream_t st);
 size_t slab_offset_words(int Bs);
 
 // Streaming multiprocessors of the current device (cached per device).

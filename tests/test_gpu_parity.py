@@ -173,6 +173,23 @@ def test_rk4_steps_device_dt_and_graph_match_host_steps(A, prec, Bs):
     assert np.array_equal(u1, u0) and np.array_equal(u2, u0)
 
 
+def test_autotune_keeps_the_state_and_the_results(A):
+    """The autotuner only changes launch knobs: the state is what a synchronisation leaves, and a
+    step after it is bitwise the step without it."""
+    leaves = random_graded_leaves(18, nroot=(2, 1, 1), J0=1, Jmax=3, n_target=70)
+    grid = _grid(Bs=17, precision=32)
+    mask = (0.8, 0.5, 0.5, 0.2, 0.04)
+    f, _ = _pair(A, grid, _phys(), leaves, fn_seed=18, mask=mask)
+    g, _ = _pair(A, grid, _phys(), leaves, fn_seed=18, mask=mask)
+    fw, sc = f.autotune()
+    assert fw in (2, 4, 8, 16) and 1 <= sc <= 3
+    g.sync_ghosts()                      # the same fine-wins update the autotuner made
+    assert np.array_equal(f.read_fields(), g.read_fields())
+    f.rk4_step(1e-3)
+    g.rk4_step(1e-3)
+    assert np.array_equal(f.read_fields(), g.read_fields())
+
+
 @pytest.mark.parametrize("prec", [64, 32])
 def test_indicators_match_oracle(A, prec):
     leaves = random_graded_leaves(14, nroot=(2, 1, 1), J0=1, Jmax=3, n_target=70)
