@@ -103,3 +103,45 @@ def test_initial_grid_tracks_the_mask_interface():
             rng = float(S.chi[s].max() - S.chi[s].min())
             if rng > S.mask_thr:
                 assert leaf[0] == top      # the interface sits on the finest level kept
+
+
+def test_adaptive_run_stays_within_the_threshold_error_of_the_uniform_run():
+    """Sec. 3.4: an adaptive run (refine, RK4, coarsen per step) differs from the same steps on the
+    uniform finest grid by at most about N_t C_eps ||u||: each step's coarsening drops details
+    below C_eps ||u|| and the (stable) scheme carries the dropped parts along."""
+    eps, steps = 1e-3, 3
+    ph = acm.Physics(nu=1e-2, c0=3.0, C_gamma=0.5)
+    ic = lambda X, Y, Z: np.stack([np.sin(2 * math.pi * X) * np.cos(2 * math.pi * Y),
+                                   0.5 * np.cos(2 * math.pi * X) * np.sin(2 * math.pi * Z),
+                                   0.2 * np.sin(2 * math.pi * (Y + Z)), np.zeros_like(X)])
+    fa = Forest(nroot=(1, 1, 1), root_len=1.0, Bs=9, Jmin=1, Jmax=3, max_blocks=1 << 12)
+    A = Solver(fa, ph, eps=eps, dealias=False, ic=ic)
+    A.initial_grid()
+    fu = Forest(nroot=(1, 1, 1), root_len=1.0, Bs=9, Jmin=3, Jmax=3, max_blocks=1 << 12)
+    fu.init_uniform(3)
+    Uni = Solver(fu, ph, ic=ic)
+    Uni.eval_ic()
+    assert len(fa.leaves) < len(fu.leaves)        # the adaptive grid is coarser somewhere
+    scale = float(np.abs(np.stack([Uni.U[s] for s in fu.leaves.values()])[:, :3]).max())
+    for _ in range(steps):
+        A.refine_all()
+        dt = A.dt_cfl()
+        A.rk4(dt)
+        A.coarsen()
+        Uni.rk4(dt)
+    # compare on the adaptive grid's points (each is a point of the uniform level-3 lattice)
+    M = fa.M
+    err = 0.0
+    for (J, gx, gy, gz), s in fa.leaves.items():
+        k = 1 << (3 - J)
+        for c in range(8 ** (3 - J)):
+            cx, cy, cz = c % k, (c // k) % k, c // (k * k)
+            leaf3 = (3, gx * k + cx, gy * k + cy, gz * k + cz)
+            u3 = Uni.U[fu.leaves[leaf3]]
+            # points of the level-3 block that lie on the level-J lattice
+            sub = u3[:3, ::k, ::k, ::k]
+            n = M // k
+            ua = A.U[s][:3, cz * n:cz * n + n + 1, cy * n:cy * n + n + 1, cx * n:cx * n + n + 1]
+            err = max(err, float(np.abs(ua - sub).max()))
+    assert err <= steps * eps * scale, (err, steps * eps * scale)
+    assert err > 0.0
