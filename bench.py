@@ -316,6 +316,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--max-blocks", type=int, default=40000)
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-graph", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -429,7 +430,7 @@ def main():
             e2e = {"value": pu_e / te, "unit": UNIT, "h2d_bytes_per_step": h2d // args.steps,
                    "d2h_bytes_per_step": d2h // args.steps}
 
-        graph = graph_comparison(A, stream, args.precision) if rank == 0 else None
+        graph = graph_comparison(A, stream, args.precision) if rank == 0 and not args.no_graph else None
         batched = batched_comparison(A, args.precision) if rank == 0 and not args.no_batched else None
 
         cpu = None
