@@ -199,6 +199,37 @@ def graph_comparison(A, stream, precision, nsteps=200):
             "graph_speedup_vs_host_dt_calls": out["host_dt_calls"] / out["graph"]}
 
 
+def uniform_roofline(A, stream, precision, J=5, nsteps=5):
+    """The fused stage kernel on a uniform periodic grid (unit cube at level J: 8^J blocks of
+    17^3, Taylor-Green, the config-1 physics): its CUDA-event time per launch over nsteps RK4
+    steps and the algorithmic bandwidth (64 words per point and RK4 step without a mask)."""
+    import torch
+    nb = 8 ** J
+    grid = dict(nroot=(1, 1, 1), root_len=1.0, Bs=17, g=4, Jmin=J, Jmax=J, precision=precision, max_blocks=nb,
+                fd_scheme=1)
+    phys = dict(nu=1e-2, c0=10.0, C_gamma=1.0, cfl=0.5)
+    f = A.Forest(grid, phys, stream=stream)
+    f.init_uniform(J)
+    f.set_ic(A.ACM_IC_TAYLOR_GREEN, [2 * math.pi, 1.0])
+    for _ in range(2):
+        f.rk4_step(1e-5)
+    f.enable_timing(True)
+    ms = byt = 0.0
+    for _ in range(nsteps):
+        f.rk4_step(1e-5)
+        st = f.last_step_stats()
+        ms += st["stage_ms"]
+        byt += st["stage_bytes"]
+    f.enable_timing(False)
+    f.close()
+    torch.cuda.synchronize()
+    peak, kind = measured_peaks()
+    gbs = byt / (ms * 1e-3) / 1e9
+    return {"workload": f"Taylor-Green, periodic unit cube, uniform level {J}: {nb} blocks of 17^3",
+            "precision": f"fp{precision}", "stage_ms_per_launch": ms / (4 * nsteps), "achieved_gbs": gbs,
+            "frac": gbs / peak, "peak_kind": kind}
+
+
 def batched_comparison(A, precision, seed=0, n=64, nsteps=10):
     """The batched workload: n independent instances (periodic unit cubes, N_b ~ U{8..512} blocks
     of 17^3 on random graded layouts over levels 2..5, pulse + vortex ring, seeded), nsteps RK4
@@ -317,6 +348,7 @@ def main():
     ap.add_argument("--max-blocks", type=int, default=40000)
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-graph", action="store_true")
+    ap.add_argument("--no-uniform", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -431,6 +463,7 @@ def main():
                    "d2h_bytes_per_step": d2h // args.steps}
 
         graph = graph_comparison(A, stream, args.precision) if rank == 0 and not args.no_graph else None
+        uniform = uniform_roofline(A, stream, args.precision) if rank == 0 and not args.no_uniform else None
         batched = batched_comparison(A, args.precision) if rank == 0 and not args.no_batched else None
 
         cpu = None
@@ -471,6 +504,7 @@ def main():
                 "total": t_max / args.steps},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "rk4_graph": graph,
             "batched": batched,
+            "uniform_roofline": uniform,
             "autotune": {"fine_wins_ctas_per_sm": tuned[0], "slab_ctas_per_sm": tuned[1]},
             "clocks": clk,
         }

@@ -501,7 +501,8 @@ __global__ void __launch_bounds__(kNT) k_maxnorm(const T* reg, const int32_t* bl
 // memory once: the interior one z-column per thread, the ghost shell from the finest leaf
 // holding each point, else by the tensor DD-4 prediction from the even lattice [-4, M+4] (only
 // gathered when a neighbour box is coarser).  Each child is then predicted separably (x, then
-// y, then z), a thread producing one whole line per pass; the z-pass writes the child.
+// y, then z), a thread producing one whole line per pass; the z-pass writes the child, and the
+// next child's x-pass runs in the same phase (it writes qx while the z-pass reads qy).
 // Dynamic shared memory: pp (M+3)^3, ev/qx, qy in T, then the neighbourhood.
 template <typename T, int BS>
 struct RefSmem {
@@ -641,21 +642,23 @@ k_refine(const T* src, T* dst, const int32_t* tasks, const int32_t* blist, const
       pp[gi[k]] = v[k];
     }
   }
+  T* qx = eq;
+  // x-pass of child c: line (yy, zz) = item; the threads from the top of the CTA take these
+  // lines, so that in the phase shared with the previous child's z-pass few threads do both
+  auto xpass = [&](int c, int item) {
+    const int o0 = (c & 1) * (M / 2) - 1, o1 = ((c >> 1) & 1) * (M / 2) - 1, o2 = ((c >> 2) & 1) * (M / 2) - 1;
+    const int yy = item % NP, zz = item / NP;
+    T cv[NP];
+#pragma unroll
+    for (int k = 0; k < NP; ++k) cv[k] = pp[PPI(o0 + k, o1 + yy, o2 + zz)];
+#pragma unroll
+    for (int i = 0; i < BS; ++i) qx[(zz * NP + yy) * BS + i] = dd4_line<T, BS>(cv, i);
+  };
+  const int xitem = NT - 1 - tid;             // x-pass line of this thread, if < NP^2
+  __syncthreads();                            // pp complete
+  if (xitem < NP * NP) xpass(0, xitem);
   for (int c = 0; c < 8; ++c) {
-    const int cb[3] = {c & 1, (c >> 1) & 1, (c >> 2) & 1};
-    // the child's parent samples start at parent index o = cb M/2 - 1 on each axis
-    const int o[3] = {cb[0] * (M / 2) - 1, cb[1] * (M / 2) - 1, cb[2] * (M / 2) - 1};
-    T* qx = eq;
-    __syncthreads();                          // pp complete / previous child's passes done
-    if (tid < NP * NP) {                      // x-pass: line (yy, zz)
-      const int yy = tid % NP, zz = tid / NP;
-      T cv[NP];
-#pragma unroll
-      for (int k = 0; k < NP; ++k) cv[k] = pp[PPI(o[0] + k, o[1] + yy, o[2] + zz)];
-#pragma unroll
-      for (int i = 0; i < BS; ++i) qx[(zz * NP + yy) * BS + i] = dd4_line<T, BS>(cv, i);
-    }
-    __syncthreads();
+    __syncthreads();                          // qx of child c complete, qy free
     if (tid < NP * BS) {                      // y-pass: line (ix, zz)
       const int ix = tid % BS, zz = tid / BS;
       T cv[NP];
@@ -664,7 +667,7 @@ k_refine(const T* src, T* dst, const int32_t* tasks, const int32_t* blist, const
 #pragma unroll
       for (int i = 0; i < BS; ++i) qy[(zz * BS + i) * BS + ix] = dd4_line<T, BS>(cv, i);
     }
-    __syncthreads();
+    __syncthreads();                          // qy complete, qx free
     if (col) {                                // z-pass: column (x, y), written to the child
       T cv[NP];
 #pragma unroll
@@ -673,6 +676,7 @@ k_refine(const T* src, T* dst, const int32_t* tasks, const int32_t* blist, const
 #pragma unroll
       for (int z = 0; z < BS; ++z) out[L::idx(x, y, z)] = dd4_line<T, BS>(cv, z);
     }
+    if (c < 7 && xitem < NP * NP) xpass(c + 1, xitem);   // the next child's x-pass alongside
   }
 }
 
