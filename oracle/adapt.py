@@ -14,7 +14,14 @@ its details are below C_eps, with each component normalised by its global L-infi
 (Sec. 3.4).  Sec. 2.3: classical RK4.
 
 Readings: the norms are taken once per coarsening phase, before its first pass; a component
-with zero norm is skipped; the mask-range threshold is 1e-5; merging is decimation (CDF 4/0).
+with zero norm is skipped; the mask-range threshold is 1e-5.  Merging is decimation with the
+CDF 4/0 wavelet.  With CDF 4/4 (Sec. 3.2.1; the paper's choice for its later runs) the parent
+takes the lifted analysis low-pass h~ of the level-(J+1) point values V_{J+1} (the values the
+ghost synchronisation defines, so the 4 fine points outside the sister group come from its
+neighbours) at its interior points; its boundary points keep the decimated value.  The
+boundary reading keeps redundant points shared with a same-level leaf that is not merged in
+the same pass bitwise equal in both blocks (that leaf holds the decimated value after fine
+wins), and the 13-tap filter then needs 4 fine ghost layers, not 6.
 """
 from __future__ import annotations
 
@@ -22,15 +29,17 @@ import numpy as np
 
 from . import acm
 from .forest import DIRECTIONS, Forest
-from .mra import block_details, predict_3d
-from .sync import sync
+from .mra import block_details, cdf44_lowpass, lowpass_decimate_axis, predict_3d
+from .sync import PointValues, local_points, sync
 
 
 class Solver:
     """State of one simulation: forest, register U (slot-indexed) and the analytic mask."""
 
     def __init__(self, forest: Forest, ph: acm.Physics, eps=1e-3, dealias=True,
-                 mask_thr=1e-5, ic=None, mask=None, sponge=None):
+                 mask_thr=1e-5, ic=None, mask=None, sponge=None, wavelet="cdf40"):
+        assert wavelet in ("cdf40", "cdf44")
+        self.wavelet = wavelet
         self.fo = forest
         self.ph = ph
         self.eps, self.dealias, self.mask_thr = eps, dealias, mask_thr
@@ -149,12 +158,33 @@ class Solver:
                 out.append(parent)
         return out
 
+    def lowpass_parent(self, parent, src):
+        """CDF 4/4 values of ``parent`` at its interior points 1..M-1 (per axis), (4, M-1, M-1,
+        M-1): V_{J+1} of the current forest on the fine points -4..2M+4 around the parent's
+        box (parent point i sits at fine point 2i), low-passed along x, then y, then z."""
+        fo = self.fo
+        M = fo.M
+        g = 4
+        J, px, py, pz = parent
+        Pl = local_points(2 * M, g, "cube")                 # x fastest, then y, then z
+        P = Pl + 2 * M * np.array([px, py, pz])
+        vals = PointValues(fo, src).value(J + 1, P)         # (n, 4)
+        n = 2 * M + 1 + 2 * g
+        e = np.moveaxis(vals.reshape(n, n, n, -1), -1, 0)   # (4, z, y, x)
+        ht = cdf44_lowpass()
+        a = lowpass_decimate_axis(e, -1, ht, g, M)
+        a = lowpass_decimate_axis(a, -2, ht, g, M)
+        return lowpass_decimate_axis(a, -3, ht, g, M)
+
     def merge(self, groups, src):
         """Replace each sister group by its parent; parent points are decimated children points
-        taken from ``src`` (slot-indexed synchronised interiors)."""
+        taken from ``src`` (slot-indexed synchronised interiors); with CDF 4/4 the interior
+        points then take the low-passed values (``lowpass_parent``, on the forest before the
+        merge)."""
         fo = self.fo
         M = fo.M
         half = M // 2
+        lp = {p: self.lowpass_parent(p, src) for p in groups} if self.wavelet == "cdf44" else {}
         old = {p: [fo.leaves[k] for k in fo.children_of(p)] for p in groups}
         removed = [k for p in groups for k in fo.children_of(p)]
         new = fo.apply_pass(removed, list(groups))
@@ -168,6 +198,8 @@ class Solver:
             kid_slots = np.array(old[p])
             P = src[kid_slots[cn], :, LZ, LY, LX]          # (z, y, x, 4)
             self.U[new[p]] = np.moveaxis(P, -1, 0)
+            if p in lp:
+                self.U[new[p]][:, 1:M, 1:M, 1:M] = lp[p]
         return new
 
     def coarsen(self, max_passes=64):

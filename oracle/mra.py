@@ -7,8 +7,10 @@ Paper, Sec. 3.1: prediction P_{J->J+1} keeps the even points and fills the odd o
 decimation u_i^J = u_{2i}^{J+1}; R o P = Id; the details are u - P R u, zero at even points
 (eq. "details").  Sec. 3.2: the same operators written as filters, with
 g~_n = (-1)^{1-n} h_{1-n} and g_n = (-1)^{1-n} h~_{1-n}.  Sec. 3.2.1: primal lifting of the
-linear case with s_0 = s_1 = -1/4 (CDF 2/0 -> CDF 2/2).  Sec. 3.4: tensor products in 3D,
-each component of a vector field separately, normalised by its global L-infinity norm.
+linear case with s_0 = s_1 = -1/4 (CDF 2/0 -> CDF 2/2), and of the cubic case
+(CDF 4/0 -> CDF 4/4), whose analysis low-pass h~ the CDF 4/4 coarsening applies before
+decimation.  Sec. 3.4: tensor products in 3D, each component of a vector field separately,
+normalised by its global L-infinity norm.
 """
 from __future__ import annotations
 
@@ -147,3 +149,38 @@ def lifting_coefficients(h, g, nvanish, ks):
 def moments(filt, pmax):
     """sum_n n^p f_n for p = 0..pmax-1."""
     return [sum((float(n) ** p) * v for n, v in filt.items()) for p in range(pmax)]
+
+
+# ---- CDF 4/4: the lifted analysis low-pass (Sec. 3.2.1) ------------------------------------------
+
+def cdf44_lowpass():
+    """Analysis low-pass h~ of CDF 4/4 as a dict n -> h~_n (n = -6..6).
+
+    Sec. 3.2.1: the cubic interpolating MRA (CDF 4/0: h~ = delta_0) is lifted with update
+    weights s_k chosen so that the new primal wavelet has 4 vanishing moments; the dual scaling
+    filter then changes to h~_new[m] = h~[m] + sum_k s_k g~[m + 2k] (``lift_primal``).  The
+    weights are solved for, not typed in: four unknowns s_{-1..2} (the four details around an
+    even point), four moment equations."""
+    h, ht, g, gt = dd4_filters()
+    s = lifting_coefficients(h, g, 4, [-1, 0, 1, 2])
+    _, ht_new = lift_primal(h, ht, g, gt, s)
+    return ht_new
+
+
+def lowpass_decimate_axis(a, axis, ht, g, M):
+    """Coarse values at coarse indices 1..M-1 along ``axis``: c_i = sum_n h~_n f_{2i+n}.
+
+    ``a`` holds fine samples at local fine indices -g..2M+g along ``axis`` (array index
+    fine index + g); the filter's reach max|n| must be <= g + 2, so that c_1 and c_{M-1} find
+    all their samples."""
+    reach = max(abs(n) for n in ht)
+    assert reach <= g + 2
+    a = np.moveaxis(np.asarray(a, dtype=np.float64), axis, -1)
+    assert a.shape[-1] == 2 * M + 1 + 2 * g
+    out = np.zeros(a.shape[:-1] + (M - 1,))
+    for i in range(1, M):
+        acc = np.zeros(a.shape[:-1])
+        for n in sorted(ht):
+            acc = acc + ht[n] * a[..., g + 2 * i + n]
+        out[..., i - 1] = acc
+    return np.moveaxis(out, -1, axis)
