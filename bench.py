@@ -230,6 +230,40 @@ def uniform_roofline(A, stream, precision, J=5, nsteps=5):
             "frac": gbs / peak, "peak_kind": kind}
 
 
+def wavelet_comparison(A, stream, precision, Jmax, max_blocks, nsteps=10, warmup=3):
+    """The sphere workload with the CDF 4/4 wavelet (Sec. 3.2.1: merged parents take the lifted
+    low-pass): whole steps (refine, RK4, coarsen) timed by CUDA events, as in the main line."""
+    import numpy as np
+    import torch
+    grid, phys, mask, ic, _ = sphere_setup(Jmax=Jmax, precision=precision, max_blocks=max_blocks)
+    grid = dict(grid, wavelet=44)
+    f = A.Forest(grid, phys, stream=stream)
+    f.set_mask(A.ACM_MASK_SPHERE, mask)
+    f.init_grid(A.ACM_IC_UNIFORM, ic)
+    for _ in range(warmup):
+        f.step(0.0)
+    Bs3 = grid["Bs"] ** 3
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    pu, nev = 0, []
+    e0.record(stream)
+    for _ in range(nsteps):
+        f.refine_all()
+        n_ev = f.n_blocks()
+        f.rk4_step(0.0)
+        f.coarsen()
+        pu += 4 * n_ev * Bs3
+        nev.append(n_ev)
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    nb = f.n_blocks()
+    f.close()
+    return {"workload": "the sphere workload above with the CDF 4/4 wavelet", "precision": f"fp{precision}",
+            "steps": nsteps, "ms_per_step": ms / nsteps, "value": pu / (ms * 1e-3), "unit": UNIT,
+            "blocks_evolved_mean": float(np.mean(nev)), "blocks_after_coarsening": nb}
+
+
 def batched_comparison(A, precision, seed=0, n=64, nsteps=10):
     """The batched workload: n independent instances (periodic unit cubes, N_b ~ U{8..512} blocks
     of 17^3 on random graded layouts over levels 2..5, pulse + vortex ring, seeded), nsteps RK4
@@ -349,6 +383,7 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--no-uniform", action="store_true")
+    ap.add_argument("--no-cdf44", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -465,6 +500,8 @@ def main():
         graph = graph_comparison(A, stream, args.precision) if rank == 0 and not args.no_graph else None
         uniform = uniform_roofline(A, stream, args.precision) if rank == 0 and not args.no_uniform else None
         batched = batched_comparison(A, args.precision) if rank == 0 and not args.no_batched else None
+        cdf44 = (wavelet_comparison(A, stream, args.precision, args.Jmax, args.max_blocks)
+                 if rank == 0 and not args.no_cdf44 else None)
 
         cpu = None
         if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -493,7 +530,8 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == 32 else "f64",
             "data": "synthetic",
             "config": {"workload": workload_name(grid), "Bs": grid["Bs"], "levels": [grid["Jmin"], grid["Jmax"]],
-                       "precision": f"fp{args.precision}", "blocks_evolved_mean": float(np.mean(nev)),
+                       "precision": f"fp{args.precision}", "wavelet": "CDF 4/0",
+                       "blocks_evolved_mean": float(np.mean(nev)),
                        "points_evolved_mean": float(np.mean(nev)) * Bs3,
                        "l2": f"inputs larger than L2: state {4 * float(np.mean(nev)) * Bs3 * 4 * (args.precision // 8) / 1e9:.2f} GB per RK register x 4 registers",
                        "parallelism": f"replicas x{world}"},
@@ -504,6 +542,7 @@ def main():
                 "total": t_max / args.steps},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "rk4_graph": graph,
             "batched": batched,
+            "cdf44": cdf44,
             "uniform_roofline": uniform,
             "autotune": {"fine_wins_ctas_per_sm": tuned[0], "slab_ctas_per_sm": tuned[1]},
             "clocks": clk,

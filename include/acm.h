@@ -56,7 +56,12 @@ typedef enum {
  * acm_sync_ghosts (1..4).  precision is 32 or 64.  fd_scheme: 1 = Tam-Webb optimised first
  * derivative (Sec. 2.3, the paper's choice), 0 = classical (8,-1)/12.  Levels obey
  * 0 <= Jmin <= Jmax <= 18 (Sec. 3.5).  max_blocks (the block pool) is at most
- * 2^32 / (72 Bs^2) blocks (206,000 at Bs = 17): device offsets into the pool are 32-bit. */
+ * 2^32 / (72 Bs^2) blocks (206,000 at Bs = 17): device offsets into the pool are 32-bit.
+ * wavelet (Sec. 3.2): 40 = CDF 4/0, the interpolating wavelet (a merged parent is the decimated
+ * children); 44 = CDF 4/4, its lifted form (Sec. 3.2.1): a merged parent's interior points take
+ * the lifted analysis low-pass of the children's level and the 4 fine points around them, its
+ * boundary points the decimated value.  Details, thresholds and refinement are the same for
+ * both.  0 is read as 40; other values are ACM_EINVAL. */
 typedef struct {
   int nroot[3];
   double root_len;
@@ -66,6 +71,7 @@ typedef struct {
   int precision;
   int64_t max_blocks;
   int fd_scheme;
+  int wavelet;
 } acm_grid_params;
 
 /* Model parameters of eqs. (u_eqn-1, p_eqn-1), Sec. 2.1-2.2, and the adaptation controls of
@@ -214,8 +220,9 @@ acm_status acm_refine_all(acm_forest* f);
 /* Coarsening (Sec. 3.5 step 3): details of every block, normalised per component by its
  * global max norm (taken once, before the first pass); tag if below eps (and J > Jmin, and
  * the mask range <= thr), or always at Jmax with dealiasing; merge tagged sister groups that
- * keep the grid graded; repeat until nothing changes.  *n_blocks (may be NULL) receives the
- * block count, *n_passes (may be NULL) the number of merging passes. */
+ * keep the grid graded; repeat until nothing changes.  A merged parent is made as the grid's
+ * wavelet says (decimation for CDF 4/0, the lifted low-pass inside for CDF 4/4).  *n_blocks (may
+ * be NULL) receives the block count, *n_passes (may be NULL) the number of merging passes. */
 acm_status acm_coarsen(acm_forest* f, int64_t* n_blocks, int* n_passes);
 
 /* The paper's time step (Sec. 3.5): refine all, RK4 (dt as in acm_rk4_step), coarsen. */

@@ -22,7 +22,7 @@ ACM_REG_U = 0
 class GridParams(C.Structure):
     _fields_ = [("nroot", C.c_int * 3), ("root_len", C.c_double), ("Bs", C.c_int), ("g", C.c_int),
                 ("Jmin", C.c_int), ("Jmax", C.c_int), ("precision", C.c_int),
-                ("max_blocks", C.c_int64), ("fd_scheme", C.c_int)]
+                ("max_blocks", C.c_int64), ("fd_scheme", C.c_int), ("wavelet", C.c_int)]
 
 
 class PhysParams(C.Structure):
@@ -154,6 +154,7 @@ class Forest:
         g.precision = grid.get("precision", 64)
         g.max_blocks = grid.get("max_blocks", 4096)
         g.fd_scheme = grid.get("fd_scheme", 1)
+        g.wavelet = grid.get("wavelet", 40)
         p = PhysParams()
         p.nu = phys.get("nu", 0.0)
         p.c0 = phys.get("c0", 1.0)

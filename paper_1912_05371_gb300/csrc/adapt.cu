@@ -712,6 +712,112 @@ __global__ void __launch_bounds__(ColCfg<BS>::NT) k_coarsen(const T* src, T* dst
   for (int z = 0; z < BS; ++z) out[L::idx(x, y, z)] = v[z];
 }
 
+// ---- (7b) CDF 4/4 coarsening (Sec. 3.2.1 lifted wavelet, Sec. 3.5 step 3) ------------------------
+// The parent's interior points (1..M-1 per axis) take the CDF 4/4 analysis low-pass of the
+// level-(J+1) point values around the sister group; its boundary points keep the decimated
+// child values, so a redundant point that the parent shares with a same-level leaf not merged
+// in this pass keeps the value that leaf holds.  The low-pass is the primal lifting of the cubic
+// interpolating transform: details d_j = f_{2j+1} - (-f_{2j-2} + 9 f_{2j} + 9 f_{2j+2} - f_{2j+4})/16,
+// then c_i = f_{2i} + (-d_{i-2} + 9 d_{i-1} + 9 d_i - d_{i+1})/32 (the update weights that give
+// the lifted wavelet 4 vanishing moments).  Expanded, c_i is the symmetric 13-tap filter
+// (348; 144, -63, -16, 18, 0, -1)/512 on f_{2i}, f_{2i+-1}, ..., f_{2i+-6}, applied here along
+// x, then y, then z.  It reaches 6 fine points past the parent's points 1 and M-1, i.e. 4 past
+// the group: the fine values there are the children's ghost values (finest leaf holding the
+// point, else the tensor DD-4 prediction), looked up with the children's own neighbourhoods.
+// task = [new parent slot, old child slots 0..7, rank of child 0] (the children are 8
+// consecutive blocks of the old order); dst is a register other than src.
+// One CTA per (task, component).  The fine lattice -4..2M+4 of the group is streamed one z-plane
+// at a time through shared memory; each plane is filtered along x, then y, and kept; the z-pass
+// at the end gives one parent column per thread.
+template <typename T, int BS>
+struct C44Smem {
+  static constexpr int M = BS - 1;
+  static constexpr int NF = 2 * M + 9;        // fine points per axis: -4..2M+4
+  static constexpr int NI = M - 1;            // filtered parent points per axis: 1..M-1
+  static constexpr int NT = ((NI * NI + 31) / 32) * 32;
+  static constexpr int PL = NF * NF, TX = NF * NI, TZ = NF * NI * NI;
+  static constexpr size_t bytes = (size_t)(PL + TX + TZ) * sizeof(T) + 8 * kNbhStride * sizeof(int);
+};
+
+// The expanded lifting filter at p[0] = f_{2i}, neighbours s elements apart.
+template <typename T>
+__device__ __forceinline__ T cdf44_lowpass(const T* p, int s) {
+  T acc = T(348) * p[0];
+  acc = fma(T(144), p[-s] + p[s], acc);
+  acc = fma(T(-63), p[-2 * s] + p[2 * s], acc);
+  acc = fma(T(-16), p[-3 * s] + p[3 * s], acc);
+  acc = fma(T(18), p[-4 * s] + p[4 * s], acc);
+  acc = acc - (p[-6 * s] + p[6 * s]);
+  return acc * (T(1) / T(512));
+}
+
+template <typename T, int BS>
+__global__ void __launch_bounds__(C44Smem<T, BS>::NT) k_coarsen44(const T* src, T* dst, const int32_t* tasks,
+                                                                  const int32_t* nbh_all) {
+  using L = Lay<T, BS>;
+  using S = C44Smem<T, BS>;
+  constexpr int M = L::M, NF = S::NF, NI = S::NI, NT = S::NT;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* pl = reinterpret_cast<T*>(smem_raw);           // pl[Y][X]: one fine plane
+  T* tx = pl + S::PL;                               // tx[Y][i]: the plane filtered along x
+  T* tz = tx + S::TX;                               // tz[Z][j][i]: the planes filtered along x and y
+  int* nbh = reinterpret_cast<int*>(tz + S::TZ);    // neighbourhoods of children 0..7
+  __shared__ int cslot[8];
+  const int tid = threadIdx.x;
+  const int32_t* tk = tasks + (size_t)(blockIdx.x >> 2) * 10;
+  const int f = blockIdx.x & 3;
+  if (tid < 8) cslot[tid] = tk[1 + tid];
+  for (int i = tid; i < 8 * kNbhStride; i += NT) nbh[i] = nbh_all[(size_t)tk[9] * kNbhStride + i];
+  __syncthreads();
+  const size_t fo = (size_t)f * L::FS;
+  // fine point (X, Y, Z) of the group (0..2M inside) belongs to, or is a ghost of, child
+  // c = [X > M] + 2 [Y > M] + 4 [Z > M], at local coordinates (X, Y, Z) - M (cx, cy, cz)
+  auto load_plane = [&](int Z) {
+    const int cz = Z > M, lz = Z - cz * M;
+    const bool zin = Z >= 0 && Z <= 2 * M;
+    for (int i = tid; i < NF * NF; i += NT) {
+      const int X = i % NF - 4, Y = i / NF - 4;
+      const int cx = X > M, cy = Y > M;
+      const int c = cx | (cy << 1) | (cz << 2);
+      const int lx = X - cx * M, ly = Y - cy * M;
+      T v;
+      if (zin && X >= 0 && X <= 2 * M && Y >= 0 && Y <= 2 * M)
+        v = src[(size_t)cslot[c] * L::BLK + fo + L::idx(lx, ly, lz)];
+      else
+        v = point_value<T, BS>(src, nbh + c * kNbhStride, lx, ly, lz, f);
+      pl[i] = v;
+    }
+  };
+  load_plane(-4);
+  __syncthreads();
+  for (int Z = -4; Z <= 2 * M + 4; ++Z) {
+    for (int i = tid; i < NF * NI; i += NT) {       // x-pass: row Y, parent index i + 1
+      const int Y = i / NI, ic = i % NI + 1;
+      tx[i] = cdf44_lowpass(pl + Y * NF + 2 * ic + 4, 1);
+    }
+    __syncthreads();                                // tx complete, pl free
+    if (tid < NI * NI) {                            // y-pass: parent (i + 1, j + 1)
+      const int j = tid / NI + 1, i = tid % NI;
+      tz[((Z + 4) * NI + (j - 1)) * NI + i] = cdf44_lowpass(tx + (2 * j + 4) * NI + i, NI);
+    }
+    if (Z < 2 * M + 4) load_plane(Z + 1);
+    __syncthreads();                                // next plane in pl, tx free
+  }
+  T* out = dst + (size_t)tk[0] * L::BLK + fo;
+  if (tid < NI * NI) {                              // z-pass: parent column (i + 1, j + 1)
+    const int j = tid / NI, i = tid % NI;
+    for (int k = 1; k <= NI; ++k)
+      out[L::idx(i + 1, j + 1, k)] = cdf44_lowpass(tz + ((2 * k + 4) * NI + j) * NI + i, NI * NI);
+  }
+  for (int p = tid; p < BS * BS * BS; p += NT) {   // boundary points: decimated children
+    const int x = p % BS, y = (p / BS) % BS, z = p / (BS * BS);
+    if (x > 0 && x < M && y > 0 && y < M && z > 0 && z < M) continue;
+    const int cx = x > M / 2, cy = y > M / 2, cz = z > M / 2;
+    const int c = cx | (cy << 1) | (cz << 2);
+    out[L::idx(x, y, z)] = src[(size_t)cslot[c] * L::BLK + fo + L::idx(2 * x - cx * M, 2 * y - cy * M, 2 * z - cz * M)];
+  }
+}
+
 // ---- copy of whole blocks (same slots) between two registers --------------------------------------
 // Slots list[i * stride], i = 0..n-1.
 template <typename T, int BS>
@@ -1034,6 +1140,21 @@ void launch_coarsen(int Bs, const T* src, T* dst, const int32_t* tasks, int64_t 
   if (Bs == 17) k_coarsen<T, 17><<<grid1(4 * n), ColCfg<17>::NT, 0, st>>>(src, dst, tasks);
   else k_coarsen<T, 9><<<grid1(4 * n), ColCfg<9>::NT, 0, st>>>(src, dst, tasks);
 }
+template <typename T, int BS>
+void launch_coarsen44_bs(const T* src, T* dst, const int32_t* tasks, int64_t n, const int32_t* nbh, cudaStream_t st) {
+  static bool attr = false;             // opt in to more than 48 KB of dynamic shared memory once
+  if (!attr) {
+    cudaFuncSetAttribute(k_coarsen44<T, BS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C44Smem<T, BS>::bytes);
+    attr = true;
+  }
+  k_coarsen44<T, BS><<<grid1(4 * n), C44Smem<T, BS>::NT, C44Smem<T, BS>::bytes, st>>>(src, dst, tasks, nbh);
+}
+template <typename T>
+void launch_coarsen44(int Bs, const T* src, T* dst, const int32_t* tasks, int64_t n, const int32_t* nbh, cudaStream_t st) {
+  if (n <= 0) return;
+  if (Bs == 17) launch_coarsen44_bs<T, 17>(src, dst, tasks, n, nbh, st);
+  else launch_coarsen44_bs<T, 9>(src, dst, tasks, n, nbh, st);
+}
 template <typename T>
 void launch_copy_blocks(int Bs, const T* src, T* dst, const int32_t* list, int stride, int64_t n, cudaStream_t st) {
   if (n <= 0) return;
@@ -1078,6 +1199,7 @@ void launch_scatter(int Bs, const T* dense, T* reg, const int32_t* blist, int64_
   template void launch_maxnorm<T>(int, const T*, const int32_t*, int64_t, unsigned long long*, cudaStream_t); \
   template void launch_refine<T>(int, const T*, T*, const int32_t*, int64_t, const int32_t*, const int32_t*, cudaStream_t); \
   template void launch_coarsen<T>(int, const T*, T*, const int32_t*, int64_t, cudaStream_t);               \
+  template void launch_coarsen44<T>(int, const T*, T*, const int32_t*, int64_t, const int32_t*, cudaStream_t); \
   template void launch_copy_blocks<T>(int, const T*, T*, const int32_t*, int, int64_t, cudaStream_t);          \
   template void launch_ic<T>(int, T*, const int32_t*, const int32_t*, int64_t, const int4*, const PhysK&, const IcK&, cudaStream_t); \
   template void launch_mask<T>(int, T*, const int32_t*, const int32_t*, int64_t, const int4*, const PhysK&, const MaskK&, cudaStream_t); \

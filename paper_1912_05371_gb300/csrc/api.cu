@@ -169,6 +169,7 @@ bool valid_grid(const acm_grid_params* g) {
   if (g->Bs != 9 && g->Bs != 17) return false;
   if (g->precision != 32 && g->precision != 64) return false;
   if (g->g < 1 || g->g > 4) return false;
+  if (g->wavelet != 0 && g->wavelet != 40 && g->wavelet != 44) return false;
   if (g->Jmin < 0 || g->Jmax < g->Jmin || g->Jmax > 18) return false;
   if (g->max_blocks < 1 || g->max_blocks > (int64_t)1 << 30) return false;
   if (!(g->root_len > 0)) return false;
@@ -696,17 +697,21 @@ acm_status coarsen(acm_forest* f, int64_t* n_blocks, int* n_passes) {
   f->norms_fresh = false;
   if (s) return s;
   int passes = 0;
-  // A merge leaves every other block's indicator unchanged: its even samples keep their values
-  // (decimation preserves coincident points), so later passes evaluate the new parents only.
+  // With CDF 4/0 a merge leaves every other block's indicator unchanged: its even samples keep
+  // their values (decimation preserves coincident points), so later passes evaluate the new
+  // parents only.  The CDF 4/4 low-pass changes the parents' interior points, which the details
+  // of their neighbours read: every pass evaluates every block.
+  const bool c44 = f->gp.wavelet == 44;
+  const int tstride = c44 ? 10 : 9;
   std::vector<double>& ind_slot = f->ind_slot;
   std::vector<double>& chr_slot = f->chr_slot;
   std::vector<int32_t> fresh;
   std::vector<double> ind, chr;
   for (int it = 0; it < 64; ++it) {
-    s = indicators<T>(f, ind, chr, it == 0 ? nullptr : &fresh);
+    s = indicators<T>(f, ind, chr, it == 0 || c44 ? nullptr : &fresh);
     if (s) return s;
     const size_t n = f->order.size();
-    if (it == 0) {
+    if (it == 0 || c44) {
       for (size_t r = 0; r < n; ++r) {
         ind_slot[f->blist[r]] = ind[r];
         chr_slot[f->blist[r]] = chr[r];
@@ -761,19 +766,25 @@ acm_status coarsen(acm_forest* f, int64_t* n_blocks, int* n_passes) {
       for (int c = 0; c < 8; ++c) freed[8 * g + c] = f->blist[gstart[g] + c];
     std::vector<int32_t> new_slot;
     if (!fo.take_slots(freed, groups.size(), &new_slot)) return fail(f, ACM_ECAPACITY, "block pool exhausted");
-    std::vector<int32_t> tasks(groups.size() * 9);
+    std::vector<int32_t> tasks(groups.size() * tstride);
     for (size_t g = 0; g < groups.size(); ++g) {
-      tasks[9 * g] = new_slot[g];
-      for (int c = 0; c < 8; ++c) tasks[9 * g + 1 + c] = freed[8 * g + c];
+      tasks[tstride * g] = new_slot[g];
+      for (int c = 0; c < 8; ++c) tasks[tstride * g + 1 + c] = freed[8 * g + c];
+      if (c44) tasks[tstride * g + 9] = (int32_t)gstart[g];
     }
-    // the parents are decimated into YA (a parent may take a slot freed by a child that is still
-    // being read), then copied into U
+    // the parents are made in YA (a parent may take a slot freed by a child that is still being
+    // read), then copied into U; the CDF 4/4 low-pass reads the old grid's neighbourhoods, which
+    // the topology upload below replaces only after it (stream order)
     CK(cudaMemcpyAsync(f->d_crst, tasks.data(), tasks.size() * 4, cudaMemcpyHostToDevice, f->st));
-    acm::launch_coarsen<T>(f->gp.Bs, reinterpret_cast<const T*>(f->U), reinterpret_cast<T*>(f->YA), f->d_crst,
-                           (int64_t)groups.size(), f->st);
+    if (c44)
+      acm::launch_coarsen44<T>(f->gp.Bs, reinterpret_cast<const T*>(f->U), reinterpret_cast<T*>(f->YA), f->d_crst,
+                               (int64_t)groups.size(), f->d_nbh, f->st);
+    else
+      acm::launch_coarsen<T>(f->gp.Bs, reinterpret_cast<const T*>(f->U), reinterpret_cast<T*>(f->YA), f->d_crst,
+                             (int64_t)groups.size(), f->st);
     CKL();
-    acm::launch_copy_blocks<T>(f->gp.Bs, reinterpret_cast<const T*>(f->YA), reinterpret_cast<T*>(f->U), f->d_crst, 9,
-                               (int64_t)groups.size(), f->st);
+    acm::launch_copy_blocks<T>(f->gp.Bs, reinterpret_cast<const T*>(f->YA), reinterpret_cast<T*>(f->U), f->d_crst,
+                               tstride, (int64_t)groups.size(), f->st);
     CKL();
     f->launches += 2;
     // the host side of the merged grid while the GPU merges
@@ -962,6 +973,7 @@ acm_status acm_create_forest(const acm_grid_params* grid, const acm_phys_params*
   if (((uintptr_t)device_pool) & 255) return ACM_EINVAL;
   std::unique_ptr<acm_forest> f(new acm_forest());
   f->gp = *grid;
+  if (f->gp.wavelet == 0) f->gp.wavelet = 40;
   f->pp = *phys;
   f->st = reinterpret_cast<cudaStream_t>(stream);
   f->pool = reinterpret_cast<char*>(device_pool);

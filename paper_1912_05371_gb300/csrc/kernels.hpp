@@ -143,6 +143,12 @@ template <typename T>
 void launch_coarsen(int Bs, const T* src, T* dst, const int32_t* tasks /*[n][9]*/, int64_t ntasks,
                     cudaStream_t st);
 
+// CDF 4/4 coarsening: tasks [n][10] = [new parent slot, old child slots 0..7, rank of child 0]
+// (the children are consecutive in the old block order; nbh is the old grid's table).
+template <typename T>
+void launch_coarsen44(int Bs, const T* src, T* dst, const int32_t* tasks, int64_t ntasks, const int32_t* nbh,
+                      cudaStream_t st);
+
 template <typename T>
 void launch_copy_blocks(int Bs, const T* src, T* dst, const int32_t* list, int stride, int64_t n, cudaStream_t st);
 

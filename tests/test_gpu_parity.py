@@ -31,9 +31,9 @@ def A():
     return acm
 
 
-def _grid(Bs=9, nroot=(2, 1, 1), root_len=1.0, Jmin=1, Jmax=3, precision=64, max_blocks=4096, g=4):
+def _grid(Bs=9, nroot=(2, 1, 1), root_len=1.0, Jmin=1, Jmax=3, precision=64, max_blocks=4096, g=4, wavelet=40):
     return dict(nroot=nroot, root_len=root_len, Bs=Bs, g=g, Jmin=Jmin, Jmax=Jmax, precision=precision,
-                max_blocks=max_blocks, fd_scheme=1)
+                max_blocks=max_blocks, fd_scheme=1, wavelet=wavelet)
 
 
 def _phys(**kw):
@@ -47,7 +47,7 @@ def _pair(A, grid, phys, leaves, fn_seed=1, mask=None):
     f.set_leaves(leaves)
     fo = oracle_forest(grid, leaves=leaves)
     S = oracle_solver(fo, phys, mask=sphere_fn(mask) if mask else None,
-                      sponge=sponge_fn(phys) if phys.get("sponge") else None)
+                      sponge=sponge_fn(phys) if phys.get("sponge") else None, wavelet=grid.get("wavelet", 40))
     L = tuple(n * grid["root_len"] for n in grid["nroot"])
     fill_from_function(S, lambda X, Y, Z: smooth_field(X, Y, Z, L, fn_seed))
     S.eval_mask()
@@ -231,9 +231,50 @@ def test_refine_and_coarsen_match_oracle(A, prec):
         assert max(err) < TOL[prec], err
 
 
-def _small_sphere(prec, Jmax=3):
+@pytest.mark.parametrize("prec,Bs", [(64, 9), (32, 9), (64, 17), (32, 17)])
+def test_cdf44_coarsen_to_jmin_matches_oracle(A, prec, Bs):
+    """Every block tagged (huge threshold): the merges are decided by the grading alone, so the
+    topology does not depend on the precision; several passes of the lifted low-pass."""
+    leaves = random_graded_leaves(16 + Bs, nroot=(2, 1, 1), J0=1, Jmax=3, n_target=60 if Bs == 9 else 30)
+    grid = _grid(Bs=Bs, precision=prec, Jmax=3, wavelet=44)
+    f, S = _pair(A, grid, _phys(eps=1e30), leaves, fn_seed=16)
+    nb, npass = f.coarsen()
+    opass = S.coarsen()
+    assert npass == opass and nb == len(S.fo.leaves) == 16
+    t = f.topology()
+    tc, lv, sl, nbr, rel = S.fo.topology()
+    assert np.array_equal(t["treecode"], tc) and np.array_equal(t["slot"], sl)
+    err = rel_linf(f.read_fields().astype(np.float64), block_order_fields(S))
+    assert max(err) < TOL[prec], err
+
+
+def test_cdf44_refine_and_coarsen_match_oracle(A):
+    leaves = random_graded_leaves(17, nroot=(2, 1, 1), J0=1, Jmax=2, n_target=40)
+    grid = _grid(Bs=9, precision=64, Jmax=3, wavelet=44)
+    f, S = _pair(A, grid, _phys(eps=3e-3), leaves, fn_seed=17)
+    f.refine_all()
+    S.refine_all()
+    nb, npass = f.coarsen()
+    opass = S.coarsen()
+    t = f.topology()
+    tc, lv, sl, nbr, rel = S.fo.topology()
+    assert npass == opass >= 1 and nb == len(S.fo.leaves)
+    assert np.array_equal(t["treecode"], tc) and np.array_equal(t["slot"], sl)
+    assert np.array_equal(t["nbr"], nbr) and np.array_equal(t["rel"], rel)
+    err = rel_linf(f.read_fields(), block_order_fields(S))
+    assert max(err) < TOL[64], err
+    # the two wavelets give different parents from the same refined state
+    g40 = _grid(Bs=9, precision=64, Jmax=3, wavelet=40)
+    f40, _ = _pair(A, g40, _phys(eps=3e-3), leaves, fn_seed=17)
+    f40.refine_all()
+    f40.coarsen()
+    if np.array_equal(f40.topology()["treecode"], t["treecode"]):
+        assert not np.array_equal(f40.read_fields(), f.read_fields())
+
+
+def _small_sphere(prec, Jmax=3, wavelet=40):
     grid = dict(nroot=(2, 1, 1), root_len=1.0, Bs=9, g=4, Jmin=1, Jmax=Jmax, precision=prec,
-                max_blocks=1 << 14, fd_scheme=1)
+                max_blocks=1 << 14, fd_scheme=1, wavelet=wavelet)
     dxm = 1.0 / ((1 << Jmax) * 8)
     phys = dict(nu=1e-3, c0=5.0, C_eta=1e-2, C_gamma=0.0, C_sp=0.25 / (5.0 * 20.0), u_inf=(1.0, 0.0, 0.0),
                 p_inf=0.0, cfl=0.5, cfl_eta=1.0, cfl_nu=0.25, eps=1e-3, dealias=1, mask_range_thr=1e-5,
@@ -242,14 +283,15 @@ def _small_sphere(prec, Jmax=3):
     return grid, phys, mask
 
 
-def test_adaptive_sphere_steps_match_oracle(A):
-    grid, phys, mask = _small_sphere(64)
+@pytest.mark.parametrize("wavelet", [40, 44])
+def test_adaptive_sphere_steps_match_oracle(A, wavelet):
+    grid, phys, mask = _small_sphere(64, wavelet=wavelet)
     f = A.Forest(grid, phys)
     f.set_mask(A.ACM_MASK_SPHERE, mask)
     nb = f.init_grid(A.ACM_IC_UNIFORM, [1.0, 0.0, 0.0, 0.0])
     fo = oracle_forest(grid)
     S = oracle_solver(fo, phys, ic=lambda X, Y, Z: oacm.ic_uniform(X, Y, Z), mask=sphere_fn(mask),
-                      sponge=sponge_fn(phys))
+                      sponge=sponge_fn(phys), wavelet=wavelet)
     S.initial_grid()
     assert nb == len(fo.leaves)
     assert np.array_equal(f.topology()["treecode"], fo.topology()[0])
