@@ -723,21 +723,35 @@ __global__ void __launch_bounds__(ColCfg<BS>::NT) k_coarsen(const T* src, T* dst
 // (348; 144, -63, -16, 18, 0, -1)/512 on f_{2i}, f_{2i+-1}, ..., f_{2i+-6}, applied here along
 // x, then y, then z.  It reaches 6 fine points past the parent's points 1 and M-1, i.e. 4 past
 // the group: the fine values there are the children's ghost values (finest leaf holding the
-// point, else the tensor DD-4 prediction), looked up with the children's own neighbourhoods.
+// point, else the tensor DD-4 prediction from the coarse lattice).
 // task = [new parent slot, old child slots 0..7, rank of child 0] (the children are 8
 // consecutive blocks of the old order); dst is a register other than src.
-// One CTA per (task, component).  The fine lattice -4..2M+4 of the group is streamed one z-plane
-// at a time through shared memory; each plane is filtered along x, then y, and kept; the z-pass
-// at the end gives one parent column per thread.
+//
+// One CTA per task, all four components together (each point is looked up once).  The 64
+// child-sized boxes around and inside the group (-1..2 per axis, in units of a child) are read
+// once from the children's neighbourhoods into a box table, so a lookup is a few shifts and one
+// shared-memory read.  If a box is coarser than the children, the offsets of the even fine points
+// -6..2M+6 (the coarse lattice, held directly by some leaf) are tabled as well and the points
+// that must be predicted take the tensor DD-4 sum of their stencil from there.  The fine lattice
+// -4..2M+4 of the group is streamed one z-plane at a time: the loads of the next plane are in
+// flight while the current one is filtered along x, then y; the x-y filtered values of each
+// (component, parent column) are kept for the last 13 planes, and a parent point's z-pass runs as
+// soon as its 13th plane has arrived.
 template <typename T, int BS>
 struct C44Smem {
   static constexpr int M = BS - 1;
+  static constexpr int LM = M == 16 ? 4 : 3;  // log2 M
   static constexpr int NF = 2 * M + 9;        // fine points per axis: -4..2M+4
   static constexpr int NI = M - 1;            // filtered parent points per axis: 1..M-1
-  static constexpr int NT = ((NI * NI + 31) / 32) * 32;
-  static constexpr int PL = NF * NF, TX = NF * NI, TZ = NF * NI * NI;
-  static constexpr size_t bytes = (size_t)(PL + TX + TZ) * sizeof(T) + 8 * kNbhStride * sizeof(int);
+  static constexpr int NEV = M + 7;           // even fine points per axis: -6..2M+6
+  static constexpr int RING = 13;             // planes one z-output reads
+  static constexpr int NT = BS == 17 ? 512 : 128;
+  static constexpr int UP = (NF * NF + NT - 1) / NT;   // plane points per thread
+  static constexpr int NCOL = 4 * NI * NI;             // (component, parent column) items
+  static constexpr int PL = 4 * NF * NF, TX = 4 * NF * NI, RG = RING * NCOL, EV = NEV * NEV * NEV;
+  static constexpr size_t bytes = 64 * sizeof(int4) + (size_t)(PL + TX + RG) * sizeof(T) + (size_t)EV * sizeof(uint32_t);
 };
+static_assert(C44Smem<double, 17>::bytes <= 227 * 1024, "CDF 4/4 coarsening: shared memory");
 
 // The expanded lifting filter at p[0] = f_{2i}, neighbours s elements apart.
 template <typename T>
@@ -751,70 +765,232 @@ __device__ __forceinline__ T cdf44_lowpass(const T* p, int s) {
   return acc * (T(1) / T(512));
 }
 
+constexpr uint32_t kOffPred = 0xFFFFFFFEu;    // the point must be predicted
+constexpr uint32_t kOffBad = 0xFFFFFFFFu;     // no leaf holds the point (not a graded grid)
+
 template <typename T, int BS>
-__global__ void __launch_bounds__(C44Smem<T, BS>::NT) k_coarsen44(const T* src, T* dst, const int32_t* tasks,
-                                                                  const int32_t* nbh_all) {
+__global__ void __launch_bounds__(C44Smem<T, BS>::NT, 1) k_coarsen44(const T* src, T* dst, const int32_t* tasks,
+                                                                     const int32_t* nbh_all) {
   using L = Lay<T, BS>;
   using S = C44Smem<T, BS>;
-  constexpr int M = L::M, NF = S::NF, NI = S::NI, NT = S::NT;
+  constexpr int M = L::M, LM = S::LM, NF = S::NF, NI = S::NI, NEV = S::NEV, NT = S::NT, UP = S::UP;
+  constexpr int RING = S::RING, NCOL = S::NCOL, NF2 = NF * NF;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* pl = reinterpret_cast<T*>(smem_raw);           // pl[Y][X]: one fine plane
-  T* tx = pl + S::PL;                               // tx[Y][i]: the plane filtered along x
-  T* tz = tx + S::TX;                               // tz[Z][j][i]: the planes filtered along x and y
-  int* nbh = reinterpret_cast<int*>(tz + S::TZ);    // neighbourhoods of children 0..7
+  // 16-byte box table first, then the T arrays (8-byte aligned), the 4-byte offsets last
+  int4* gb = reinterpret_cast<int4*>(smem_raw);              // box table [bz+1][by+1][bx+1]
+  T* pl = reinterpret_cast<T*>(gb + 64);                     // pl[f][Y][X]: one fine plane
+  T* tx = pl + S::PL;                                        // tx[f][Y][i]: filtered along x
+  T* rg = tx + S::TX;                                        // rg[plane % 13][item]: along x and y
+  uint32_t* ev = reinterpret_cast<uint32_t*>(rg + S::RG);    // ev[Z][Y][X]: offsets of even points
   __shared__ int cslot[8];
   const int tid = threadIdx.x;
-  const int32_t* tk = tasks + (size_t)(blockIdx.x >> 2) * 10;
-  const int f = blockIdx.x & 3;
+  const int32_t* tk = tasks + (size_t)blockIdx.x * 10;
+  const int r0 = tk[9];
+  const T NaN = T(__longlong_as_double(0x7ff8000000000000ll));
   if (tid < 8) cslot[tid] = tk[1 + tid];
-  for (int i = tid; i < 8 * kNbhStride; i += NT) nbh[i] = nbh_all[(size_t)tk[9] * kNbhStride + i];
-  __syncthreads();
-  const size_t fo = (size_t)f * L::FS;
-  // fine point (X, Y, Z) of the group (0..2M inside) belongs to, or is a ghost of, child
-  // c = [X > M] + 2 [Y > M] + 4 [Z > M], at local coordinates (X, Y, Z) - M (cx, cy, cz)
-  auto load_plane = [&](int Z) {
+  int mine = 0;
+  if (tid < 64) {
+    // box (bx, by, bz) seen from the child next to it; children see themselves as box 13
+    const int bx = tid % 4 - 1, by = (tid / 4) % 4 - 1, bz = tid / 16 - 1;
+    const int cx = bx < 0 ? 0 : (bx > 1 ? 1 : bx), cy = by < 0 ? 0 : (by > 1 ? 1 : by),
+              cz = bz < 0 ? 0 : (bz > 1 ? 1 : bz);
+    const int d = box_index(bx - cx, by - cy, bz - cz);
+    const size_t rowi = (size_t)(r0 + (cx | (cy << 1) | (cz << 2))) * kNbhStride;
+    const int tw = nbh_all[rowi + kNbhType + d];
+    int4 g = make_int4(tw, nbh_all[rowi + 8 * d], 0, 0);
+    if ((tw & 15) == kTypeRefined) g.y = (int)(rowi + 8 * d);   // where its children's slots are
+    gb[tid] = g;
+    mine = (tw & 15) == kTypeCoarser;
+  }
+  const int coarser = __syncthreads_or(mine);
+  // Element offset (component 0) of fine point P of the group's lattice (-6..2M+6 per axis) in the
+  // finest leaf holding it: candidate boxes b = floor(P/M), and b - 1 if P is on their face.
+  auto group_offset = [&](int X, int Y, int Z) -> uint32_t {
+    const int P[3] = {X, Y, Z};
+    int b[3], nc[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      b[a] = ((P[a] + M) >> LM) - 1;
+      nc[a] = (P[a] & (M - 1)) == 0 ? 2 : 1;
+    }
+    int best = 0, bestp = 0, bb[3] = {0, 0, 0};
+    for (int kz = 0; kz < nc[2]; ++kz)
+      for (int ky = 0; ky < nc[1]; ++ky)
+        for (int kx = 0; kx < nc[0]; ++kx) {
+          const int e = ((b[2] - kz + 1) * 4 + (b[1] - ky + 1)) * 4 + (b[0] - kx + 1);
+          const int t = gb[e].x & 15;
+          const int pr = t == kTypeRefined ? 3 : (t == kTypeLeaf ? 2 : (t == kTypeCoarser ? 1 : 0));
+          if (pr > bestp) {
+            bestp = pr;
+            best = e;
+            bb[0] = b[0] - kx; bb[1] = b[1] - ky; bb[2] = b[2] - kz;
+          }
+        }
+    if (bestp == 0) return kOffBad;
+    const int4 g = gb[best];
+    int q[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) q[a] = P[a] - bb[a] * M;   // 0..M inside the box
+    if (bestp == 2) return (uint32_t)g.y * (uint32_t)L::BLK + (uint32_t)L::idx(q[0], q[1], q[2]);
+    if (bestp == 1) {
+      const int oct = g.x >> 4;
+      int r[3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) r[a] = ((oct >> a) & 1) * M + q[a];
+      if ((r[0] | r[1] | r[2]) & 1) return kOffPred;
+      return (uint32_t)g.y * (uint32_t)L::BLK + (uint32_t)L::idx(r[0] >> 1, r[1] >> 1, r[2] >> 1);
+    }
+    int c = 0, l[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const int ca = q[a] > M / 2;
+      c |= ca << a;
+      l[a] = 2 * q[a] - ca * M;
+    }
+    const int sl = nbh_all[(size_t)g.y + c];
+    return sl < 0 ? kOffBad : (uint32_t)sl * (uint32_t)L::BLK + (uint32_t)L::idx(l[0], l[1], l[2]);
+  };
+  if (coarser) {
+    for (int i = tid; i < S::EV; i += NT) {
+      const uint32_t o = group_offset(2 * (i % NEV) - 6, 2 * ((i / NEV) % NEV) - 6, 2 * (i / (NEV * NEV)) - 6);
+      ev[i] = o == kOffPred ? kOffBad : o;
+    }
+  }
+  auto load = [&](uint32_t o, int f) -> T { return o < kOffPred ? src[(size_t)o + (size_t)f * L::FS] : NaN; };
+  // tensor DD-4 prediction of the 4 components at fine point (X, Y, Z): x innermost, then y, z
+  auto predict = [&](int X, int Y, int Z, T (&v)[4]) {
+    const bool ox = X & 1, oy = Y & 1, oz = Z & 1;
+    T az[4] = {T(0), T(0), T(0), T(0)};
+#pragma unroll
+    for (int kz = 0; kz < 4; ++kz) {
+      if (!oz && kz) continue;
+      const int zz = ((oz ? Z + 2 * kz - 3 : Z) + 6) >> 1;
+      const T wz = oz ? ((kz == 0 || kz == 3) ? T(-1) / T(16) : T(9) / T(16)) : T(1);
+      T ay[4] = {T(0), T(0), T(0), T(0)};
+#pragma unroll
+      for (int ky = 0; ky < 4; ++ky) {
+        if (!oy && ky) continue;
+        const int yy = ((oy ? Y + 2 * ky - 3 : Y) + 6) >> 1;
+        const T wy = oy ? ((ky == 0 || ky == 3) ? T(-1) / T(16) : T(9) / T(16)) : T(1);
+        T ax[4] = {T(0), T(0), T(0), T(0)};
+#pragma unroll
+        for (int kx = 0; kx < 4; ++kx) {
+          if (!ox && kx) continue;
+          const int xx = ((ox ? X + 2 * kx - 3 : X) + 6) >> 1;
+          const T wx = ox ? ((kx == 0 || kx == 3) ? T(-1) / T(16) : T(9) / T(16)) : T(1);
+          const uint32_t o = ev[(zz * NEV + yy) * NEV + xx];
+#pragma unroll
+          for (int f = 0; f < 4; ++f) ax[f] = ax[f] + wx * load(o, f);
+        }
+#pragma unroll
+        for (int f = 0; f < 4; ++f) ay[f] = ay[f] + wy * ax[f];
+      }
+#pragma unroll
+      for (int f = 0; f < 4; ++f) az[f] = az[f] + wz * ay[f];
+    }
+#pragma unroll
+    for (int f = 0; f < 4; ++f) v[f] = az[f];
+  };
+  // per-thread geometry, the same in every plane: plane points, x-pass and y-pass items
+  constexpr int UX = (4 * NF * NI + NT - 1) / NT, UY = (NCOL + NT - 1) / NT;
+  int px[UP], py[UP];
+#pragma unroll
+  for (int k = 0; k < UP; ++k) {
+    const int i = tid + k * NT;
+    px[k] = i < NF2 ? i % NF - 4 : -1000;           // -1000: no point
+    py[k] = i / NF - 4;
+  }
+  int xs[UX];                                       // x-pass: pl offset of f_{2i} (-1: none)
+#pragma unroll
+  for (int u = 0; u < UX; ++u) {
+    const int it = tid + u * NT;
+    const int f = it / (NF * NI), r = it % (NF * NI);
+    xs[u] = it < 4 * NF * NI ? f * NF2 + (r / NI) * NF + 2 * (r % NI + 1) + 4 : -1;
+  }
+  int ys[UY], yo[UY];                               // y-pass: tx offset; parent offset at z = 0
+#pragma unroll
+  for (int u = 0; u < UY; ++u) {
+    const int it = tid + u * NT;
+    const int f = it / (NI * NI), r = it % (NI * NI);
+    const int j = r / NI + 1, i = r % NI;
+    ys[u] = it < NCOL ? f * NF * NI + (2 * j + 4) * NI + i : -1;
+    yo[u] = f * L::FS + L::idx(i + 1, j, 0);
+  }
+  uint32_t poff[UP];
+  T pv[UP][4];
+  auto issue = [&](int Z) {                         // offsets and loads of plane Z
     const int cz = Z > M, lz = Z - cz * M;
     const bool zin = Z >= 0 && Z <= 2 * M;
-    for (int i = tid; i < NF * NF; i += NT) {
-      const int X = i % NF - 4, Y = i / NF - 4;
-      const int cx = X > M, cy = Y > M;
-      const int c = cx | (cy << 1) | (cz << 2);
-      const int lx = X - cx * M, ly = Y - cy * M;
-      T v;
-      if (zin && X >= 0 && X <= 2 * M && Y >= 0 && Y <= 2 * M)
-        v = src[(size_t)cslot[c] * L::BLK + fo + L::idx(lx, ly, lz)];
-      else
-        v = point_value<T, BS>(src, nbh + c * kNbhStride, lx, ly, lz, f);
-      pl[i] = v;
+#pragma unroll
+    for (int k = 0; k < UP; ++k) {
+      const int X = px[k], Y = py[k];
+      uint32_t o = kOffBad;
+      if (X != -1000) {
+        if (zin && X >= 0 && X <= 2 * M && Y >= 0 && Y <= 2 * M) {
+          const int cx = X > M, cy = Y > M;
+          o = (uint32_t)cslot[cx | (cy << 1) | (cz << 2)] * (uint32_t)L::BLK +
+              (uint32_t)L::idx(X - cx * M, Y - cy * M, lz);
+        } else {
+          o = group_offset(X, Y, Z);
+        }
+      }
+      poff[k] = o;
+    }
+#pragma unroll
+    for (int k = 0; k < UP; ++k)
+#pragma unroll
+      for (int f = 0; f < 4; ++f) pv[k][f] = load(poff[k], f);
+  };
+  auto finish = [&](int Z) {                        // plane Z into pl, predicted points filled in
+#pragma unroll
+    for (int k = 0; k < UP; ++k) {
+      if (px[k] == -1000) continue;
+      if (poff[k] == kOffPred && coarser) predict(px[k], py[k], Z, pv[k]);
+      const int i = tid + k * NT;
+#pragma unroll
+      for (int f = 0; f < 4; ++f) pl[f * NF2 + i] = pv[k][f];
     }
   };
-  load_plane(-4);
-  __syncthreads();
+  T* out = dst + (size_t)tk[0] * L::BLK;
+  __syncthreads();                                  // ev complete
+  issue(-4);
+  int slot = 0;                                     // ring slot of the current plane
   for (int Z = -4; Z <= 2 * M + 4; ++Z) {
-    for (int i = tid; i < NF * NI; i += NT) {       // x-pass: row Y, parent index i + 1
-      const int Y = i / NI, ic = i % NI + 1;
-      tx[i] = cdf44_lowpass(pl + Y * NF + 2 * ic + 4, 1);
+    finish(Z);
+    __syncthreads();                                // pl complete; tx free
+    if (Z < 2 * M + 4) issue(Z + 1);
+#pragma unroll
+    for (int u = 0; u < UX; ++u)                    // x-pass: component, row Y, parent index
+      if (xs[u] >= 0) tx[tid + u * NT] = cdf44_lowpass(pl + xs[u], 1);
+    __syncthreads();                                // tx complete; pl free
+    const int zi = Z + 4;
+    const bool zpass = zi >= 12 && !(zi & 1);       // plane 2k + 6 arrived: z-pass of point k
+#pragma unroll
+    for (int u = 0; u < UY; ++u) {                  // y-pass, then the z-pass once complete
+      if (ys[u] < 0) continue;
+      const int it = tid + u * NT;
+      rg[slot * NCOL + it] = cdf44_lowpass(tx + ys[u], NI);
+      if (zpass) {
+        T a[RING];
+#pragma unroll
+        for (int n = 0; n < RING; ++n) {            // plane zi - 12 + n sits in slot + 1 + n (mod 13)
+          int sn = slot + 1 + n;
+          sn -= sn >= RING ? RING : 0;
+          a[n] = rg[sn * NCOL + it];
+        }
+        out[yo[u] + ((Z - 6) >> 1) * L::PP] = cdf44_lowpass(a + 6, 1);
+      }
     }
-    __syncthreads();                                // tx complete, pl free
-    if (tid < NI * NI) {                            // y-pass: parent (i + 1, j + 1)
-      const int j = tid / NI + 1, i = tid % NI;
-      tz[((Z + 4) * NI + (j - 1)) * NI + i] = cdf44_lowpass(tx + (2 * j + 4) * NI + i, NI);
-    }
-    if (Z < 2 * M + 4) load_plane(Z + 1);
-    __syncthreads();                                // next plane in pl, tx free
-  }
-  T* out = dst + (size_t)tk[0] * L::BLK + fo;
-  if (tid < NI * NI) {                              // z-pass: parent column (i + 1, j + 1)
-    const int j = tid / NI, i = tid % NI;
-    for (int k = 1; k <= NI; ++k)
-      out[L::idx(i + 1, j + 1, k)] = cdf44_lowpass(tz + ((2 * k + 4) * NI + j) * NI + i, NI * NI);
+    slot = slot + 1 == RING ? 0 : slot + 1;
   }
   for (int p = tid; p < BS * BS * BS; p += NT) {   // boundary points: decimated children
     const int x = p % BS, y = (p / BS) % BS, z = p / (BS * BS);
     if (x > 0 && x < M && y > 0 && y < M && z > 0 && z < M) continue;
     const int cx = x > M / 2, cy = y > M / 2, cz = z > M / 2;
-    const int c = cx | (cy << 1) | (cz << 2);
-    out[L::idx(x, y, z)] = src[(size_t)cslot[c] * L::BLK + fo + L::idx(2 * x - cx * M, 2 * y - cy * M, 2 * z - cz * M)];
+    const size_t o = (size_t)cslot[cx | (cy << 1) | (cz << 2)] * L::BLK +
+                     L::idx(2 * x - cx * M, 2 * y - cy * M, 2 * z - cz * M);
+#pragma unroll
+    for (int f = 0; f < 4; ++f) out[(size_t)f * L::FS + L::idx(x, y, z)] = src[o + (size_t)f * L::FS];
   }
 }
 
@@ -1147,7 +1323,7 @@ void launch_coarsen44_bs(const T* src, T* dst, const int32_t* tasks, int64_t n, 
     cudaFuncSetAttribute(k_coarsen44<T, BS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C44Smem<T, BS>::bytes);
     attr = true;
   }
-  k_coarsen44<T, BS><<<grid1(4 * n), C44Smem<T, BS>::NT, C44Smem<T, BS>::bytes, st>>>(src, dst, tasks, nbh);
+  k_coarsen44<T, BS><<<grid1(n), C44Smem<T, BS>::NT, C44Smem<T, BS>::bytes, st>>>(src, dst, tasks, nbh);
 }
 template <typename T>
 void launch_coarsen44(int Bs, const T* src, T* dst, const int32_t* tasks, int64_t n, const int32_t* nbh, cudaStream_t st) {
