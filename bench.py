@@ -384,6 +384,8 @@ def main():
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--no-uniform", action="store_true")
     ap.add_argument("--no-cdf44", action="store_true")
+    ap.add_argument("--wavelet", type=int, default=40, choices=[40, 44],
+                    help="wavelet of the main line: 40 = CDF 4/0 (default), 44 = CDF 4/4")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -404,6 +406,7 @@ def main():
 
     grid, phys, mask, ic, cfg = sphere_setup(Jmax=args.Jmax, precision=args.precision,
                                              max_blocks=args.max_blocks)
+    grid["wavelet"] = args.wavelet
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
         f = A.Forest(grid, phys, stream=stream)
@@ -501,7 +504,7 @@ def main():
         uniform = uniform_roofline(A, stream, args.precision) if rank == 0 and not args.no_uniform else None
         batched = batched_comparison(A, args.precision) if rank == 0 and not args.no_batched else None
         cdf44 = (wavelet_comparison(A, stream, args.precision, args.Jmax, args.max_blocks)
-                 if rank == 0 and not args.no_cdf44 else None)
+                 if rank == 0 and not args.no_cdf44 and args.wavelet == 40 else None)
 
         cpu = None
         if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -530,7 +533,7 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == 32 else "f64",
             "data": "synthetic",
             "config": {"workload": workload_name(grid), "Bs": grid["Bs"], "levels": [grid["Jmin"], grid["Jmax"]],
-                       "precision": f"fp{args.precision}", "wavelet": "CDF 4/0",
+                       "precision": f"fp{args.precision}", "wavelet": f"CDF 4/{args.wavelet % 10}",
                        "blocks_evolved_mean": float(np.mean(nev)),
                        "points_evolved_mean": float(np.mean(nev)) * Bs3,
                        "l2": f"inputs larger than L2: state {4 * float(np.mean(nev)) * Bs3 * 4 * (args.precision // 8) / 1e9:.2f} GB per RK register x 4 registers",
