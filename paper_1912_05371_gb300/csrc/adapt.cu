@@ -891,14 +891,28 @@ __global__ void __launch_bounds__(C44Smem<T, BS>::NT, 1) k_coarsen44(const T* sr
 #pragma unroll
     for (int f = 0; f < 4; ++f) v[f] = az[f];
   };
-  // per-thread geometry, the same in every plane: plane points, x-pass and y-pass items
+  // Per-thread geometry, the same in every plane.  Plane points are enumerated so that warps
+  // meet one kind of point: in a plane that cuts the group, first its (2M+1)^2 points inside the
+  // group, then the ring around them (4 rows below, 4 rows above, then 4 + 4 points on each side
+  // of the rows in between); a plane outside the group row by row.
   constexpr int UX = (4 * NF * NI + NT - 1) / NT, UY = (NCOL + NT - 1) / NT;
-  int px[UP], py[UP];
+  constexpr int NG = 2 * M + 1, NGI = NG * NG;
+  int gx[UP], gy[UP], sx[UP], sy[UP];               // -1000: no point
 #pragma unroll
   for (int k = 0; k < UP; ++k) {
-    const int i = tid + k * NT;
-    px[k] = i < NF2 ? i % NF - 4 : -1000;           // -1000: no point
-    py[k] = i / NF - 4;
+    const int p = tid + k * NT;
+    if (p < NGI) {
+      gx[k] = p % NG; gy[k] = p / NG;
+    } else if (p < NF2) {
+      const int q = p - NGI;
+      if (q < 4 * NF) { gx[k] = q % NF - 4; gy[k] = q / NF - 4; }
+      else if (q < 8 * NF) { gx[k] = (q - 4 * NF) % NF - 4; gy[k] = 2 * M + 1 + (q - 4 * NF) / NF; }
+      else { const int r = q - 8 * NF, e = r % 8; gy[k] = r / 8; gx[k] = e < 4 ? e - 4 : 2 * M + 1 + (e - 4); }
+    } else {
+      gx[k] = -1000; gy[k] = 0;
+    }
+    sx[k] = p < NF2 ? p % NF - 4 : -1000;
+    sy[k] = p / NF - 4;
   }
   int xs[UX];                                       // x-pass: pl offset of f_{2i} (-1: none)
 #pragma unroll
@@ -918,12 +932,15 @@ __global__ void __launch_bounds__(C44Smem<T, BS>::NT, 1) k_coarsen44(const T* sr
   }
   uint32_t poff[UP];
   T pv[UP][4];
+  int px[UP], py[UP];                               // the points of the plane in flight
   auto issue = [&](int Z) {                         // offsets and loads of plane Z
     const int cz = Z > M, lz = Z - cz * M;
     const bool zin = Z >= 0 && Z <= 2 * M;
 #pragma unroll
     for (int k = 0; k < UP; ++k) {
-      const int X = px[k], Y = py[k];
+      const int X = zin ? gx[k] : sx[k], Y = zin ? gy[k] : sy[k];
+      px[k] = X;
+      py[k] = Y;
       uint32_t o = kOffBad;
       if (X != -1000) {
         if (zin && X >= 0 && X <= 2 * M && Y >= 0 && Y <= 2 * M) {
@@ -946,7 +963,7 @@ __global__ void __launch_bounds__(C44Smem<T, BS>::NT, 1) k_coarsen44(const T* sr
     for (int k = 0; k < UP; ++k) {
       if (px[k] == -1000) continue;
       if (poff[k] == kOffPred && coarser) predict(px[k], py[k], Z, pv[k]);
-      const int i = tid + k * NT;
+      const int i = (py[k] + 4) * NF + (px[k] + 4);
 #pragma unroll
       for (int f = 0; f < 4; ++f) pl[f * NF2 + i] = pv[k][f];
     }
