@@ -14,6 +14,9 @@ Modules, each following the paper section it cites:
 * ``sync``    -- ghost-node values on the redundant block grid              (Sec. 4.2, Sec. 3.1)
 * ``acm``     -- stencils, ACM right-hand side, RK4, time step, mask, force (Sec. 2.1-2.3)
 * ``adapt``   -- refine-all / evolve / coarsen cycle, initial grid          (Sec. 3.5)
+* ``adjoint`` -- discrete adjoint of RK4 steps on a frozen grid: gradients of a
+                 force + energy objective w.r.t. the initial state and the sphere mask
+                 (Sec. 2.1-2.3; the adjoint itself is an extension, not in the paper)
 
 Parity status: every function is pinned by a ``-m "not gpu"`` test against a closed form,
 an invariant, a brute-force computation or a value the paper prints; none is "parity unpinned".
