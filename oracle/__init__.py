@@ -17,6 +17,8 @@ Modules, each following the paper section it cites:
 * ``adjoint`` -- discrete adjoint of RK4 steps on a frozen grid: gradients of a
                  force + energy objective w.r.t. the initial state and the sphere mask
                  (Sec. 2.1-2.3; the adjoint itself is an extension, not in the paper)
+* ``plate``   -- moving rigid plate: box signed distance, stroke/pitch kinematics,
+                 solid velocity, RK4 with the mask evaluated at every stage time (Sec. 2.2)
 
 Parity status: every function is pinned by a ``-m "not gpu"`` test against a closed form,
 an invariant, a brute-force computation or a value the paper prints; none is "parity unpinned".

@@ -1,0 +1,144 @@
+"""Pins of the oracle's moving plate (Sec. 2.2 mask and solid velocity, time-dependent)."""
+import math
+
+import numpy as np
+
+from oracle import acm
+from oracle.adapt import Solver
+from oracle.forest import Forest
+from oracle.plate import MovingSolver, Plate, box_sdf, rot_y, rot_z
+
+
+def test_rotations_and_angular_velocity():
+    P = Plate()
+    for t in (0.0, 0.13, 0.37, 0.8):
+        R = P.rotation(t)
+        assert np.allclose(R @ R.T, np.eye(3), atol=1e-15) and abs(np.linalg.det(R) - 1.0) < 1e-14
+        h = 1e-5
+        dR = (P.rotation(t + h) - P.rotation(t - h)) / (2 * h)
+        Wm = dR @ R.T                                   # [omega]_x
+        assert np.allclose(Wm, -Wm.T, atol=1e-7)
+        w = np.array([Wm[2, 1], Wm[0, 2], Wm[1, 0]])
+        assert np.allclose(w, P.omega(t), atol=1e-7)
+    # t = 0: no stroke, full pitch; t = 1/4: full stroke, no pitch
+    assert np.allclose(P.rotation(0.0), rot_y(math.radians(45.0)), atol=1e-15)
+    assert np.allclose(P.rotation(0.25), rot_z(math.radians(60.0)), atol=1e-15)
+
+
+def test_solid_velocity_is_the_material_derivative():
+    P = Plate()
+    rng = np.random.default_rng(0)
+    xb = rng.uniform([-0.5, 0.0, -0.025], [0.5, 3.0, 0.025], size=(5, 3))
+    for t in (0.05, 0.4, 0.77):
+        h = 1e-5
+        pos = lambda s: P.root + xb @ P.rotation(s).T      # x = root + R x_b
+        v_fd = (pos(t + h) - pos(t - h)) / (2 * h)
+        x = pos(t)
+        _, us = P.fields(x[:, 0], x[:, 1], x[:, 2], t)
+        assert np.abs(us.T - v_fd).max() < 1e-7 * np.abs(v_fd).max()
+
+
+def test_box_signed_distance_against_a_sampled_surface():
+    lo, hi = np.array([-0.5, 0.0, -0.1]), np.array([0.5, 2.0, 0.1])
+    d = 0.01
+    faces = []
+    for a in range(3):
+        b, c = [k for k in range(3) if k != a]
+        u = np.arange(lo[b], hi[b] + d / 2, d)
+        v = np.arange(lo[c], hi[c] + d / 2, d)
+        U, V = np.meshgrid(u, v, indexing="ij")
+        for side in (lo[a], hi[a]):
+            F = np.zeros(U.shape + (3,))
+            F[..., a], F[..., b], F[..., c] = side, U, V
+            faces.append(F.reshape(-1, 3))
+    S = np.concatenate(faces)
+    rng = np.random.default_rng(1)
+    P = rng.uniform(lo - 0.4, hi + 0.4, size=(300, 3))
+    dist = np.sqrt(((P[:, None, :] - S[None, :, :]) ** 2).sum(-1)).min(axis=1)
+    inside = np.all((P >= lo) & (P <= hi), axis=1)
+    sd = box_sdf(P, lo, hi)
+    assert np.all((sd < 0) == inside)
+    assert np.abs(np.abs(sd) - dist).max() <= d * math.sqrt(2) / 2 + 1e-12
+    # exact values on the axes through the centre
+    c = (lo + hi) / 2
+    assert box_sdf(c, lo, hi) == -0.1 and abs(box_sdf(c + [0.0, 0.0, 0.3], lo, hi) - 0.2) < 1e-15
+
+
+def test_mask_is_one_half_on_the_plate_surface():
+    P = Plate(delta=0.02)
+    t = 0.3
+    R = P.rotation(t)
+    pts_b = np.array([[0.5, 1.0, 0.0], [0.0, 3.0, 0.0], [0.1, 2.0, 0.025], [-0.5, 0.5, -0.01]])
+    x = P.root + pts_b @ R.T
+    chi, _ = P.fields(x[:, 0], x[:, 1], x[:, 2], t)
+    assert np.allclose(chi, 0.5, atol=1e-12)
+    far = P.root + np.array([[0.0, -1.0, 0.0]]) @ R.T      # behind the root
+    chi, _ = P.fields(far[:, 0], far[:, 1], far[:, 2], t)
+    assert chi[0] < 1e-12
+
+
+def _forest():
+    fo = Forest(nroot=(1, 1, 1), root_len=8.0, Bs=9, Jmin=2, Jmax=2, max_blocks=128)
+    fo.init_uniform(2)
+    return fo
+
+
+def test_moving_solver_uses_the_stage_times():
+    fo = _forest()
+    ph = acm.Physics(nu=1e-3, c0=5.0, C_eta=1e-2, C_gamma=0.0)
+    S = MovingSolver(fo, ph, Plate(delta=0.3), ic=lambda X, Y, Z: np.zeros((4,) + X.shape))
+    S.eval_ic()
+    S.eval_mask()
+    # from rest the right-hand side is the penalization alone: chi(t) u_s(t) / C_eta, p' = 0
+    for t in (0.0, 0.21):
+        K = S.rhs_at(S.U.copy(), t)
+        for leaf, s in fo.leaves.items():
+            X, Y, Z = acm.block_coords(fo, leaf)
+            chi, us = S.plate.fields(X, Y, Z, t)
+            assert np.allclose(K[s, :3], chi * us / ph.C_eta, rtol=0, atol=1e-12 * max(1.0, np.abs(us).max()) / ph.C_eta)
+            assert np.all(K[s, 3] == 0.0)
+    times = []
+    orig = S.rhs_at
+    S.rhs_at = lambda F, t: (times.append(t), orig(F, t))[1]
+    S.t = 0.1
+    S.rk4(0.02)
+    assert np.allclose(times, [0.1, 0.11, 0.11, 0.12], rtol=0, atol=1e-15) and times[1] == times[2]
+    assert abs(S.t - 0.12) < 1e-15
+
+
+def test_static_plate_equals_the_static_solver():
+    fo = _forest()
+    ph = acm.Physics(nu=1e-3, c0=5.0, C_eta=1e-2, C_gamma=0.0)
+    plate = Plate(phi_m=0.0, alpha_m=0.0, delta=0.3)
+    ic = lambda X, Y, Z: np.stack([np.sin(X), np.cos(Y), 0.1 * np.sin(Z), 0.0 * X])
+    A = MovingSolver(fo, ph, plate, ic=ic)
+    A.eval_ic()
+    A.eval_mask()
+    B = Solver(fo, ph, ic=ic, mask=lambda X, Y, Z: plate.fields(X, Y, Z, 0.0)[0])
+    B.eval_ic()
+    B.eval_mask()
+    for _ in range(2):
+        A.rk4(0.01)
+        B.rk4(0.01)
+    sl = sorted(fo.leaves.values())
+    assert np.array_equal(A.U[sl], B.U[sl])
+    Fa, Ea = A.diagnostics()
+    Fb, Eb = B.diagnostics()
+    assert np.array_equal(Fa, Fb) and Ea == Eb
+
+
+def test_fluid_moving_with_the_plate_feels_no_force():
+    fo = _forest()
+    ph = acm.Physics(nu=1e-3, c0=5.0, C_eta=1e-2, C_gamma=0.0)
+    S = MovingSolver(fo, ph, Plate(delta=0.3), ic=lambda X, Y, Z: np.zeros((4,) + X.shape))
+    S.eval_ic()
+    S.t = 0.17
+    S.eval_mask()
+    for leaf, s in fo.leaves.items():
+        S.U[s, :3] = S.us[s]                 # u = u_s everywhere: no relative motion
+    F, E = S.diagnostics()
+    assert np.all(F == 0.0) and E > 0
+    for leaf, s in fo.leaves.items():
+        S.U[s, :3] = 0.0
+    F0, _ = S.diagnostics()
+    assert np.abs(F0).max() > 0             # while a fluid at rest is pushed
