@@ -206,6 +206,24 @@ acm_status acm_rk4_steps_batch(acm_forest* const* forests, int n, int nsteps, do
  * the stream.  No counterpart in the paper. */
 acm_status acm_autotune(acm_forest* f, int* fw_ctas, int* slab_ctas);
 
+/* Discrete adjoint (an extension; the paper has none).  For nsteps RK4 steps of fixed dt from
+ * the current state on the current grid, frozen (no adaptation: adaptation is not
+ * differentiable), the objective J = (1/N) sum_{n=1..N} [F_x(U_n) + w_energy E(U_n)] with the
+ * force and energy of Sec. 2.2, and its gradient with respect to the sphere mask's centre and
+ * radius (dJ_dtheta[0..3] = d/dcx, d/dcy, d/dcz, d/dR, host) and the initial state (dJ_dU0,
+ * block order, fields layout of acm_read_fields, n_elems = n_blocks*4*Bs^3; device pointer if
+ * on_device, else host; may be NULL).  FP64 forests with the sphere mask only (ACM_EINVAL
+ * otherwise).  The states at every ckpt_every-th step are kept and each segment is recomputed
+ * in the backward sweep.  ws: caller device buffer of at least acm_adjoint_bytes(f, nsteps,
+ * ckpt_every) bytes (ACM_ENOMEM if smaller).  The forest's state and time are unchanged on
+ * return; the call synchronises the stream.  ACM_EGRADING if a ghost point's source is
+ * missing.  The gradient with respect to U_0 is that of the forward map as computed: a point
+ * shared by several blocks carries its sensitivity in the copy the forward map reads. */
+size_t acm_adjoint_bytes(const acm_forest* f, int nsteps, int ckpt_every);
+acm_status acm_adjoint_sphere(acm_forest* f, int nsteps, double dt, int ckpt_every, double w_energy, void* ws,
+                              size_t ws_bytes, double* J, double* dJ_dtheta, void* dJ_dU0, int64_t n_elems,
+                              int on_device);
+
 /* Right-hand side K = F(U) of eqs. (u_eqn-1, p_eqn-1) at every point of every block, after
  * the same synchronisation as an RK4 stage, written in block order (fields layout) to out
  * (device pointer if on_device, else host; n_elems = n_blocks*4*Bs^3).  For checks: the

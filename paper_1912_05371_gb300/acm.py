@@ -60,6 +60,9 @@ EXPORTS = {
     "acm_rk4_steps": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_int, C.POINTER(C.c_double),
                                 C.POINTER(C.c_int)]),
     "acm_autotune": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    "acm_adjoint_bytes": (C.c_size_t, [C.c_void_p, C.c_int, C.c_int]),
+    "acm_adjoint_sphere": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_int, C.c_double, C.c_void_p, C.c_size_t,
+                                     C.POINTER(C.c_double), C.c_void_p, C.c_void_p, C.c_int64, C.c_int]),
     "acm_rk4_steps_batch": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_int, C.c_double, C.c_int,
                                       C.POINTER(C.c_double), C.POINTER(C.c_int)]),
     "acm_refine_all": (C.c_int, [C.c_void_p]),
@@ -252,6 +255,22 @@ class Forest:
         self._check(self.L.acm_autotune(self.h, C.byref(a), C.byref(b)))
         return a.value, b.value
 
+    def adjoint_sphere(self, nsteps, dt, ckpt_every=10, w_energy=0.1):
+        """J = (1/N) sum_n [F_x(U_n) + w_energy E(U_n)] over nsteps fixed-dt RK4 steps on the frozen
+        grid, and its gradient: returns (J, dJ/d(cx, cy, cz, R) (4,), dJ/dU_0 in the layout of
+        read_fields).  FP64 forests with the sphere mask; the forest's state is unchanged."""
+        import torch
+        nbytes = int(self.L.acm_adjoint_bytes(self.h, int(nsteps), int(ckpt_every)))
+        ws = torch.empty(nbytes, dtype=torch.uint8, device=self.pool.device)
+        n = self.n_blocks()
+        g = np.empty((n, 4, self.Bs, self.Bs, self.Bs), dtype=np.float64)
+        J = C.c_double()
+        th = np.zeros(4)
+        self._check(self.L.acm_adjoint_sphere(self.h, int(nsteps), float(dt), int(ckpt_every), float(w_energy),
+                                              C.c_void_p(ws.data_ptr()), nbytes, C.byref(J), _ptr(th), _ptr(g),
+                                              g.size, 0))
+        return J.value, th, g
+
     def rhs(self):
         n = self.n_blocks()
         out = np.empty((n, 4, self.Bs, self.Bs, self.Bs), dtype=self.dtype)
@@ -338,3 +357,28 @@ class Forest:
 
     def launch_count(self):
         return self.L.acm_launch_count(self.h)
+
+
+def sphere_objective_function():
+    """A torch.autograd.Function over a forest: forward(forest, U0, theta, nsteps, dt, ckpt_every,
+    w_energy) writes U0 (block order, read_fields layout, float64) and the sphere mask theta =
+    (cx, cy, cz, R, delta) into the forest and returns J; backward returns dJ/dU0 and
+    dJ/d(cx, cy, cz, R) (no gradient for delta), both computed by the hand-written adjoint."""
+    import torch
+
+    class SphereObjective(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, forest, U0, theta, nsteps, dt, ckpt_every=10, w_energy=0.1):
+            forest.write_fields(U0.detach().cpu().numpy())
+            forest.set_mask(ACM_MASK_SPHERE, [float(v) for v in theta.detach().cpu()])
+            J, gth, gU = forest.adjoint_sphere(nsteps, dt, ckpt_every, w_energy)
+            ctx.save_for_backward(torch.from_numpy(gU).to(U0.device),
+                                  torch.tensor(list(gth) + [0.0], dtype=torch.float64, device=theta.device))
+            return torch.tensor(J, dtype=torch.float64, device=U0.device)
+
+        @staticmethod
+        def backward(ctx, gJ):
+            gU, gth = ctx.saved_tensors
+            return None, gJ * gU, gJ * gth, None, None, None, None
+
+    return SphereObjective

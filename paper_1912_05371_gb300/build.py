@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libacm.so")
-SOURCES = ["stage.cu", "adapt.cu", "topo.cu", "api.cu", "forest.cpp", "noalloc.cu"]
+SOURCES = ["stage.cu", "adapt.cu", "topo.cu", "api.cu", "adjoint.cu", "forest.cpp", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -146,6 +146,7 @@ acm_status device_error(acm_forest* f) {
   if (!f->h_err || !*f->h_err) return ACM_OK;
   if (*f->h_err & 1) return fail(f, ACM_ETIMEOUT, "a bounded wait inside a kernel expired");
   if (*f->h_err & 2) return fail(f, ACM_EGRADING, "grid is not 2:1 graded");
+  if (*f->h_err & 8) return fail(f, ACM_EGRADING, "adjoint: a ghost point's source leaf is missing");
   return fail(f, ACM_ECUDA, "leaf table probe exceeded its capacity");
 }
 
@@ -423,8 +424,10 @@ acm_status eval_mask(acm_forest* f, const std::vector<int32_t>* fresh = nullptr)
   return ACM_OK;
 }
 
+// save (optional, 4 registers): receives each stage's synchronised input Y_s (the adjoint
+// recomputes a step with it).
 template <typename T>
-acm_status rk4(acm_forest* f, double dt, double* dt_used) {
+acm_status rk4(acm_forest* f, double dt, double* dt_used, T* const* save = nullptr) {
   if (f->order.empty()) return fail(f, ACM_EINVAL, "empty forest");
   if (!(dt > 0)) {
     double m[5];
@@ -446,6 +449,11 @@ acm_status rk4(acm_forest* f, double dt, double* dt_used) {
     // stage 1 looks up the slabs' source points and caches them for stages 2-4 (same grid)
     acm_status st = sync_stage<T>(f, in, s > 1);
     if (st) return st;
+    if (save) {
+      acm::launch_copy_blocks<T>(f->gp.Bs, in, save[s - 1], f->d_blist, 1, (int64_t)f->order.size(), f->st);
+      CKL();
+      ++f->launches;
+    }
     if (f->timing) CK(cudaEventRecord(f->ev[3 * (s - 1) + 1], f->st));
     acm::StageK<T> a{};
     a.in = in;
@@ -954,6 +962,174 @@ acm_status autotune(acm_forest* f, int* fw_ctas, int* slab_ctas) {
   return ACM_OK;
 }
 
+// ---- discrete adjoint of RK4 steps on the frozen grid (FP64 forests) ------------------------------
+// Workspace (caller-provided, 256-byte aligned regions): registers lam, kappa, nu, sum of nu, the 4
+// stage states of the step being differentiated, the c + 1 states of a checkpoint segment, the
+// ceil(N / c) checkpoints, the mask sensitivity (one component), the loc^T coefficients and the
+// 4 parameter sums.
+struct AdjLayout {
+  size_t lam, kap, nu, sum, y[4], seg, ck, gchi, wgt, theta, total, reg;
+  int nck;
+};
+
+AdjLayout adj_layout(const acm_forest* f, int nsteps, int c) {
+  AdjLayout L{};
+  L.reg = (size_t)f->gp.max_blocks * (size_t)f->lay.BLK * 8;
+  size_t o = 0;
+  auto take = [&](size_t b) { const size_t r = o; o = (o + b + 255) & ~(size_t)255; return r; };
+  L.lam = take(L.reg);
+  L.kap = take(L.reg);
+  L.nu = take(L.reg);
+  L.sum = take(L.reg);
+  for (int s = 0; s < 4; ++s) L.y[s] = take(L.reg);
+  L.seg = take(L.reg * (size_t)(c + 1));
+  L.nck = (nsteps - 1) / c + 1;
+  L.ck = take(L.reg * (size_t)L.nck);
+  L.gchi = take((size_t)f->gp.max_blocks * (size_t)f->lay.FS * 8);
+  L.wgt = take(acm::adj_weight_doubles(f->gp.Bs, f->gp.max_blocks) * 8);
+  L.theta = take(64);
+  L.total = o + 256;
+  return L;
+}
+
+// F_x and E of the current state (Sec. 2.2), as acm_diagnostics sums them.
+acm_status force_energy(acm_forest* f, double* Fx, double* E) {
+  const size_t n = f->order.size();
+  acm::launch_diag<double>(f->gp.Bs, reinterpret_cast<const double*>(f->U),
+                           f->mask_on ? reinterpret_cast<const double*>(f->CHI) : nullptr, f->d_blist, (int64_t)n,
+                           f->d_diag, f->st);
+  CKL();
+  ++f->launches;
+  std::vector<double> part(n * 4);
+  CK(cudaMemcpyAsync(part.data(), f->d_diag, n * 4 * 8, cudaMemcpyDeviceToHost, f->st));
+  CK(cudaStreamSynchronize(f->st));
+  *Fx = 0.0;
+  *E = 0.0;
+  for (size_t r = 0; r < n; ++r) {
+    const double h = h_of(f, f->order[r].J);
+    const double h3 = h * h * h;
+    *Fx += part[4 * r] * h3 / f->pp.C_eta;
+    *E += 0.5 * part[4 * r + 3] * h3;
+  }
+  return ACM_OK;
+}
+
+acm_status adjoint_sphere(acm_forest* f, int nsteps, double dt, int c, double wE, void* ws, size_t ws_bytes,
+                          double* J_out, double* dtheta, void* dU0, int64_t n_elems, int on_device) {
+  if (f->gp.precision != 64) return fail(f, ACM_EINVAL, "the adjoint runs on FP64 forests");
+  if (!f->mask_on || f->mask.kind != 1) return fail(f, ACM_EINVAL, "the adjoint needs the sphere mask");
+  if (nsteps < 1 || c < 1 || !(dt > 0) || !ws || !J_out || !dtheta) return fail(f, ACM_EINVAL, "bad arguments");
+  if (f->order.empty()) return fail(f, ACM_EINVAL, "empty forest");
+  const AdjLayout L = adj_layout(f, nsteps, c);
+  if (ws_bytes < L.total) return fail(f, ACM_ENOMEM, "adjoint workspace too small");
+  const int64_t nb = (int64_t)f->order.size();
+  if (dU0 && n_elems != nb * 4 * (int64_t)f->gp.Bs * f->gp.Bs * f->gp.Bs)
+    return fail(f, ACM_EINVAL, "element count does not match n_blocks*4*Bs^3");
+  char* base = reinterpret_cast<char*>(((uintptr_t)ws + 255) & ~(uintptr_t)255);
+  auto R = [&](size_t off) { return reinterpret_cast<double*>(base + off); };
+  double* LAM = R(L.lam);
+  double* KAP = R(L.kap);
+  double* NU = R(L.nu);
+  double* SUM = R(L.sum);
+  double* Y[4] = {R(L.y[0]), R(L.y[1]), R(L.y[2]), R(L.y[3])};
+  double* GCHI = R(L.gchi);
+  double* WGT = R(L.wgt);
+  double* TH = R(L.theta);
+  auto SEG = [&](int k) { return R(L.seg + (size_t)k * L.reg); };
+  auto CKP = [&](int k) { return R(L.ck + (size_t)k * L.reg); };
+  const int Bs = f->gp.Bs;
+  double* U = reinterpret_cast<double*>(f->U);
+  const double* CHI = reinterpret_cast<const double*>(f->CHI);
+  const double t0 = f->time;
+  auto copy = [&](const double* src, double* dst) {
+    acm::launch_copy_blocks<double>(Bs, src, dst, f->d_blist, 1, nb, f->st);
+    ++f->launches;
+    return cudaGetLastError();
+  };
+  auto lin = [&](double* out, double a, const double* x, double b, const double* y) {
+    acm::launch_adj_lin(Bs, out, a, x, b, y, f->d_blist, nb, f->st);
+    ++f->launches;
+  };
+  // nu = J_G(Y)^T kappa (and the mask sensitivity of this stage into gchi)
+  auto jgt = [&](const double* Ys) {
+    CK(cudaMemsetAsync(NU, 0, L.reg, f->st));
+    acm::launch_adj_jgt(Bs, Ys, KAP, CHI, GCHI, WGT, NU, f->d_blist, f->d_binfo, f->d_nbh, f->d_finer, nb, f->phk,
+                        f->d_err, f->st);
+    f->launches += 3;
+    return cudaGetLastError() == cudaSuccess ? ACM_OK : fail(f, ACM_ECUDA, "adjoint kernel launch failed");
+  };
+  auto objective = [&](const double* Us) {
+    acm::launch_adj_objective(Bs, Us, CHI, LAM, GCHI, f->d_blist, f->d_binfo, nb, f->phk, 1.0 / nsteps, wE, f->st);
+    ++f->launches;
+  };
+  acm_status s;
+  // forward: the objective and the checkpoints
+  CK(copy(U, CKP(0)));
+  double J = 0.0;
+  for (int k = 1; k <= nsteps; ++k) {
+    if ((s = rk4<double>(f, dt, nullptr))) return s;
+    double Fx, E;
+    if ((s = force_energy(f, &Fx, &E))) return s;
+    J += (Fx + wE * E) / nsteps;
+    if (k % c == 0 && k < nsteps) CK(copy(U, CKP(k / c)));
+  }
+  // backward sweep, one checkpoint segment at a time (its states recomputed)
+  CK(cudaMemsetAsync(LAM, 0, L.reg, f->st));
+  CK(cudaMemsetAsync(GCHI, 0, (size_t)f->gp.max_blocks * f->lay.FS * 8, f->st));
+  CK(cudaMemsetAsync(TH, 0, 64, f->st));
+  for (int a = ((nsteps - 1) / c) * c; a >= 0; a -= c) {
+    const int b = std::min(a + c, nsteps);
+    CK(copy(CKP(a / c), SEG(0)));
+    for (int k = a; k < b; ++k) {
+      CK(copy(SEG(k - a), U));
+      if ((s = rk4<double>(f, dt, nullptr))) return s;
+      CK(copy(U, SEG(k - a + 1)));
+    }
+    if (b == nsteps) objective(SEG(b - a));
+    for (int k = b - 1; k >= a; --k) {
+      CK(copy(SEG(k - a), U));
+      if ((s = rk4<double>(f, dt, nullptr, Y))) return s;
+      lin(KAP, dt / 6.0, LAM, 0.0, nullptr);
+      if ((s = jgt(Y[3]))) return s;
+      lin(SUM, 1.0, NU, 0.0, nullptr);
+      lin(KAP, dt / 3.0, LAM, dt, NU);
+      if ((s = jgt(Y[2]))) return s;
+      lin(SUM, 1.0, SUM, 1.0, NU);
+      lin(KAP, dt / 3.0, LAM, dt / 2.0, NU);
+      if ((s = jgt(Y[1]))) return s;
+      lin(SUM, 1.0, SUM, 1.0, NU);
+      lin(KAP, dt / 6.0, LAM, dt / 2.0, NU);
+      if ((s = jgt(Y[0]))) return s;
+      lin(SUM, 1.0, SUM, 1.0, NU);
+      lin(LAM, 1.0, LAM, 1.0, SUM);
+      acm::launch_adj_fw_T(Bs, LAM, f->d_blist, f->d_nbh, f->d_finer, nb, f->st);
+      ++f->launches;
+      if (k >= 1) objective(SEG(k - a));
+    }
+  }
+  acm::launch_adj_theta(Bs, GCHI, f->d_blist, f->d_binfo, nb, f->phk, f->mask, TH, f->st);
+  ++f->launches;
+  CKL();
+  CK(cudaMemcpyAsync(dtheta, TH, 4 * sizeof(double), cudaMemcpyDeviceToHost, f->st));
+  // the forest keeps its state and time
+  CK(copy(CKP(0), U));
+  f->time = t0;
+  f->norms_fresh = false;
+  CK(cudaMemcpyAsync(f->h_err, f->d_err, sizeof(int), cudaMemcpyDeviceToHost, f->st));
+  CK(cudaStreamSynchronize(f->st));
+  if ((s = device_error(f))) return s;
+  *J_out = J;
+  if (dU0) {
+    void* dense = on_device ? dU0 : f->DENSE;
+    acm::launch_gather<double>(Bs, LAM, reinterpret_cast<double*>(dense), f->d_blist, nb, 4, f->st);
+    CKL();
+    ++f->launches;
+    if (!on_device) CK(cudaMemcpyAsync(dU0, dense, (size_t)n_elems * 8, cudaMemcpyDeviceToHost, f->st));
+    CK(cudaStreamSynchronize(f->st));
+  }
+  return ACM_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1265,6 +1441,18 @@ acm_status acm_rk4_steps_batch(acm_forest* const* forests, int n, int nsteps, do
   }
   cleanup();
   return ACM_OK;
+}
+
+size_t acm_adjoint_bytes(const acm_forest* f, int nsteps, int ckpt_every) {
+  if (!f || nsteps < 1 || ckpt_every < 1) return 0;
+  return adj_layout(f, nsteps, ckpt_every).total;
+}
+
+acm_status acm_adjoint_sphere(acm_forest* f, int nsteps, double dt, int ckpt_every, double w_energy, void* ws,
+                              size_t ws_bytes, double* J, double* dJ_dtheta, void* dJ_dU0, int64_t n_elems,
+                              int on_device) {
+  if (!f) return ACM_EINVAL;
+  return adjoint_sphere(f, nsteps, dt, ckpt_every, w_energy, ws, ws_bytes, J, dJ_dtheta, dJ_dU0, n_elems, on_device);
 }
 
 acm_status acm_autotune(acm_forest* f, int* fw_ctas, int* slab_ctas) {

@@ -1,0 +1,95 @@
+"""The CUDA discrete adjoint (frozen grid, fixed dt, FP64) against the oracle's.
+
+The objective and its gradient with respect to the sphere's centre and radius are compared
+directly; the gradient with respect to U_0 is compared per physical point, summed over the
+blocks that hold the point (the two forward maps read a shared point from different copies, so
+only the sum over the copies is the same linear functional)."""
+import numpy as np
+import pytest
+
+from oracle.adjoint import FrozenGridAdjoint
+from tests.gpu_util import block_order_fields
+from tests.test_oracle_adjoint import CENTRE, RADIUS, L, _setup
+from paper_1912_05371_gb300.workloads import random_graded_leaves
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def A():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1912_05371_gb300 import acm
+    acm.lib()
+    return acm
+
+
+def _gpu_forest(A, S, delta, seed=41, n_target=18):
+    grid = dict(nroot=(2, 1, 1), root_len=1.0, Bs=9, g=4, Jmin=1, Jmax=2, precision=64, max_blocks=256,
+                fd_scheme=1)
+    phys = dict(nu=1e-2, c0=3.0, C_eta=1e-2, C_gamma=0.5, C_sp=0.05, u_inf=(1.0, 0.0, 0.0), p_inf=0.0,
+                sponge=1, sponge_L=L, sponge_width=0.2, sponge_delta=delta)
+    f = A.Forest(grid, phys)
+    f.set_leaves(random_graded_leaves(seed, nroot=(2, 1, 1), J0=1, Jmax=2, n_target=n_target))
+    f.set_mask(A.ACM_MASK_SPHERE, (*CENTRE, RADIUS, delta))
+    f.write_fields(block_order_fields(S))
+    return f
+
+
+def _per_point(fo, blocks, Jmax):
+    """Sum block-order arrays (n, 4, Bs, Bs, Bs) over the copies of each physical point."""
+    M = fo.M
+    Nf = np.array(fo.npoints(Jmax))
+    keys, vals = [], []
+    i = np.arange(M + 1)
+    for r, (J, gx, gy, gz) in enumerate(fo.sorted_leaves()):
+        sc = 1 << (Jmax - J)
+        Z, Y, X = np.meshgrid(i, i, i, indexing="ij")
+        gxi = np.mod((gx * M + X) * sc, Nf[0])
+        gyi = np.mod((gy * M + Y) * sc, Nf[1])
+        gzi = np.mod((gz * M + Z) * sc, Nf[2])
+        keys.append(((gzi * Nf[1] + gyi) * Nf[0] + gxi).ravel())
+        vals.append(blocks[r].reshape(4, -1))
+    keys = np.concatenate(keys)
+    vals = np.concatenate(vals, axis=1)
+    uk, inv = np.unique(keys, return_inverse=True)
+    out = np.zeros((4, uk.size))
+    for c in range(4):
+        np.add.at(out[c], inv.ravel(), vals[c])
+    return out
+
+
+def test_adjoint_matches_the_oracle(A):
+    S, delta = _setup()
+    dt, N, c = 2e-3, 4, 2
+    f = _gpu_forest(A, S, delta)
+    before = f.read_fields().copy()
+    J, gth, gU = f.adjoint_sphere(N, dt, ckpt_every=c, w_energy=0.1)
+    assert np.array_equal(f.read_fields(), before)
+    adj = FrozenGridAdjoint(S, CENTRE, RADIUS, delta, dt=dt, nsteps=N, checkpoint_every=c)
+    Jo, gUo, gtho = adj.gradient(S.U.copy())
+    fo = S.fo
+    go = np.stack([gUo[fo.leaves[l]] for l in fo.sorted_leaves()])
+    a, b = _per_point(fo, gU, 2), _per_point(fo, go, 2)
+    info = (J, Jo, gth, gtho, [float(np.abs(a[k] - b[k]).max() / np.abs(b).max()) for k in range(4)])
+    assert abs(J - Jo) <= 1e-12 * abs(Jo), info
+    assert np.abs(gth - gtho).max() <= 1e-10 * np.abs(gtho).max(), info
+    assert np.abs(a - b).max() <= 1e-10 * np.abs(b).max(), info
+
+
+def test_adjoint_through_autograd(A):
+    import torch
+    S, delta = _setup()
+    f = _gpu_forest(A, S, delta)
+    Fn = A.sphere_objective_function()
+    U0 = torch.tensor(block_order_fields(S), dtype=torch.float64, requires_grad=True)
+    th = torch.tensor([*CENTRE, RADIUS, delta], dtype=torch.float64, requires_grad=True)
+    J = Fn.apply(f, U0, th, 3, 2e-3, 2, 0.1)
+    J.backward()
+    J2, gth, gU = f.adjoint_sphere(3, 2e-3, ckpt_every=2, w_energy=0.1)
+    # the scatter and the parameter sums add with FP64 atomics: equal up to their order
+    assert float(J.detach()) == J2
+    assert np.allclose(th.grad.numpy()[:4], gth, rtol=0, atol=1e-12 * np.abs(gth).max())
+    assert th.grad.numpy()[4] == 0.0
+    assert np.allclose(U0.grad.numpy(), gU, rtol=0, atol=1e-12 * np.abs(gU).max())
