@@ -264,6 +264,40 @@ def wavelet_comparison(A, stream, precision, Jmax, max_blocks, nsteps=10, warmup
             "blocks_evolved_mean": float(np.mean(nev)), "blocks_after_coarsening": nb}
 
 
+def adjoint_measurement(A, stream, nsteps=100, ckpt_every=10, w_energy=0.1):
+    """The adjoint workload: the sphere case at levels 2..4 in FP64 on its initial grid (frozen),
+    nsteps RK4 steps of one fixed dt; CUDA-event time of the forward steps alone and of the whole
+    adjoint call (forward with checkpoints every ckpt_every steps, recomputation, backward sweep)."""
+    import torch
+    grid, phys, mask, ic, _ = sphere_setup(Jmax=4, precision=64, max_blocks=2048)
+    f = A.Forest(grid, phys, stream=stream)
+    f.set_mask(A.ACM_MASK_SPHERE, mask)
+    f.init_grid(A.ACM_IC_UNIFORM, ic)
+    dt = f.rk4_step(0.0)
+    U0 = f.read_fields().copy()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(nsteps):
+        f.rk4_step(dt)
+    e1.record(stream)
+    e1.synchronize()
+    fwd = e0.elapsed_time(e1)
+    f.write_fields(U0)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    J, gth, _ = f.adjoint_sphere(nsteps, dt, ckpt_every, w_energy)
+    e1.record(stream)
+    e1.synchronize()
+    adj = e0.elapsed_time(e1)
+    nb = f.n_blocks()
+    f.close()
+    return {"workload": f"sphere, levels 2..4, frozen grid of {nb} blocks of 17^3, FP64, {nsteps} steps, "
+                        f"checkpoints every {ckpt_every}", "forward_ms_per_step": fwd / nsteps,
+            "adjoint_ms_per_step": adj / nsteps, "adjoint_over_forward": adj / fwd, "J": J,
+            "dJ_dtheta": [float(v) for v in gth]}
+
+
 def batched_comparison(A, precision, seed=0, n=64, nsteps=10):
     """The batched workload: n independent instances (periodic unit cubes, N_b ~ U{8..512} blocks
     of 17^3 on random graded layouts over levels 2..5, pulse + vortex ring, seeded), nsteps RK4
@@ -384,6 +418,7 @@ def main():
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--no-uniform", action="store_true")
     ap.add_argument("--no-cdf44", action="store_true")
+    ap.add_argument("--adjoint", action="store_true", help="also time the adjoint workload (FP64)")
     ap.add_argument("--wavelet", type=int, default=40, choices=[40, 44],
                     help="wavelet of the main line: 40 = CDF 4/0 (default), 44 = CDF 4/4")
     args = ap.parse_args()
@@ -505,6 +540,7 @@ def main():
         batched = batched_comparison(A, args.precision) if rank == 0 and not args.no_batched else None
         cdf44 = (wavelet_comparison(A, stream, args.precision, args.Jmax, args.max_blocks)
                  if rank == 0 and not args.no_cdf44 and args.wavelet == 40 else None)
+        adjoint = adjoint_measurement(A, stream) if rank == 0 and args.adjoint else None
 
         cpu = None
         if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -546,6 +582,7 @@ def main():
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "rk4_graph": graph,
             "batched": batched,
             "cdf44": cdf44,
+            "adjoint": adjoint,
             "uniform_roofline": uniform,
             "autotune": {"fine_wins_ctas_per_sm": tuned[0], "slab_ctas_per_sm": tuned[1]},
             "clocks": clk,
