@@ -1014,8 +1014,8 @@ acm_status force_energy(acm_forest* f, double* Fx, double* E) {
   return ACM_OK;
 }
 
-acm_status adjoint_sphere(acm_forest* f, int nsteps, double dt, int c, double wE, void* ws, size_t ws_bytes,
-                          double* J_out, double* dtheta, void* dU0, int64_t n_elems, int on_device) {
+acm_status adjoint_sweep(acm_forest* f, int nsteps, double dt, int c, double wE, void* ws, size_t ws_bytes,
+                         double* J_out, double* dtheta, void* dU0, int64_t n_elems, int on_device) {
   if (f->gp.precision != 64) return fail(f, ACM_EINVAL, "the adjoint runs on FP64 forests");
   if (!f->mask_on || f->mask.kind != 1) return fail(f, ACM_EINVAL, "the adjoint needs the sphere mask");
   if (nsteps < 1 || c < 1 || !(dt > 0) || !ws || !J_out || !dtheta) return fail(f, ACM_EINVAL, "bad arguments");
@@ -1128,6 +1128,24 @@ acm_status adjoint_sphere(acm_forest* f, int nsteps, double dt, int c, double wE
     CK(cudaStreamSynchronize(f->st));
   }
   return ACM_OK;
+}
+
+// The sweep above, with the forest's state and time put back if it stops on an error after the
+// first step (checkpoint 0 holds the initial state).
+acm_status adjoint_sphere(acm_forest* f, int nsteps, double dt, int c, double wE, void* ws, size_t ws_bytes,
+                          double* J_out, double* dtheta, void* dU0, int64_t n_elems, int on_device) {
+  const double t0 = f->time;
+  const acm_status s = adjoint_sweep(f, nsteps, dt, c, wE, ws, ws_bytes, J_out, dtheta, dU0, n_elems, on_device);
+  if (s != ACM_OK && s != ACM_EINVAL && s != ACM_ENOMEM && f->time != t0) {
+    const AdjLayout L = adj_layout(f, nsteps, c);
+    char* base = reinterpret_cast<char*>(((uintptr_t)ws + 255) & ~(uintptr_t)255);
+    acm::launch_copy_blocks<double>(f->gp.Bs, reinterpret_cast<const double*>(base + L.ck),
+                                    reinterpret_cast<double*>(f->U), f->d_blist, 1, (int64_t)f->order.size(), f->st);
+    cudaStreamSynchronize(f->st);
+    f->time = t0;
+    f->norms_fresh = false;
+  }
+  return s;
 }
 
 }  // namespace
