@@ -117,8 +117,17 @@ typedef struct {
 enum { ACM_IC_TAYLOR_GREEN = 1, ACM_IC_UNIFORM = 2, ACM_IC_PULSE = 3, ACM_IC_PULSE_RING = 4 };
 
 /* Masks for acm_set_mask: ACM_MASK_NONE; ACM_MASK_SPHERE: cx, cy, cz, R, delta with
- * chi = (1 - tanh(d/delta))/2, d the signed distance to the sphere (Sec. 2.2 smoothed mask). */
-enum { ACM_MASK_NONE = 0, ACM_MASK_SPHERE = 1 };
+ * chi = (1 - tanh(d/delta))/2, d the signed distance to the sphere (Sec. 2.2 smoothed mask);
+ * ACM_MASK_PLATE: a rigid plate flapping about a pivot (Sec. 2.2 with a moving body; no
+ * counterpart workload in the paper): chord, span, thickness, stroke amplitude phi_m, pitch
+ * amplitude alpha_m (radians), frequency f, pivot x0, y0, z0, delta.  The plate is the box
+ * |x_b| <= chord/2, 0 <= y_b <= span, |z_b| <= thickness/2 of its body frame; x = x0 + R(t) x_b
+ * with R = R_z(phi) R_y(alpha), phi = phi_m sin(2 pi f t), alpha = alpha_m cos(2 pi f t); chi is
+ * the same tanh profile of the box's signed distance and u_s = omega x (x - x0).  Its pose
+ * follows the forest's simulated time: chi is evaluated at every RK4 stage time and the
+ * penalization uses u_s; acm_rk4_steps and acm_rk4_steps_batch refuse a moving mask
+ * (ACM_EINVAL); the force of acm_diagnostics integrates chi (u - u_s).  Not yet run on a GPU. */
+enum { ACM_MASK_NONE = 0, ACM_MASK_SPHERE = 1, ACM_MASK_PLATE = 2 };
 
 /* Register ids for acm_sync_ghosts / acm_read_fields (U is the solution). */
 enum { ACM_REG_U = 0 };
@@ -153,8 +162,8 @@ acm_status acm_set_leaves(acm_forest* f, const int32_t* level, const int32_t* gx
 acm_status acm_set_ic(acm_forest* f, int ic_kind, const double* params, int n_params);
 
 /* Set the obstacle mask chi (Sec. 2.2), evaluated analytically on every block now and after
- * every grid change; u_s = 0.  kind ACM_MASK_NONE removes it.  t is reserved for moving
- * bodies. */
+ * every grid change; u_s = 0 except for the moving plate (see ACM_MASK_PLATE, whose pose
+ * follows the forest's time).  kind ACM_MASK_NONE removes it.  t is unused. */
 acm_status acm_set_mask(acm_forest* f, int kind, const double* params, int n_params, double t);
 
 /* Initial grid (Sec. 3.5, last paragraph): start from the uniform Jmin grid and repeat

@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_lib", "libacm.so")
 
 ACM_IC_TAYLOR_GREEN, ACM_IC_UNIFORM, ACM_IC_PULSE, ACM_IC_PULSE_RING = 1, 2, 3, 4
-ACM_MASK_NONE, ACM_MASK_SPHERE = 0, 1
+ACM_MASK_NONE, ACM_MASK_SPHERE, ACM_MASK_PLATE = 0, 1, 2
 ACM_REG_U = 0
 
 

@@ -1135,6 +1135,21 @@ __global__ void __launch_bounds__(ColCfg<BS>::NT) k_mask(T* chi, const int32_t* 
         if (sqrt(dmin2) - m.p[3] > 40.0 * m.p[4]) uniform = 0;
         else if (sqrt(dmax2) - m.p[3] < -40.0 * m.p[4]) uniform = 1;
       }
+    } else if (m.kind == 2) {
+      // rigid box: outside the sphere of radius p[22] around the pivot by more than 40 delta
+      uniform = -1;
+      const double lo[3] = {(double)bi.y * M * h, (double)bi.z * M * h, (double)bi.w * M * h};
+      const double L[3] = {ph.nroot[0] * ph.root_len, ph.nroot[1] * ph.root_len, ph.nroot[2] * ph.root_len};
+      bool seam = false;
+      double dmin2 = 0.0;
+      for (int a = 0; a < 3; ++a) {
+        const double hi = lo[a] + M * h;
+        if (hi >= L[a]) seam = true;
+        const double c = m.p[9 + a];
+        const double near = c < lo[a] ? lo[a] - c : (c > hi ? c - hi : 0.0);
+        dmin2 += near * near;
+      }
+      if (!seam && sqrt(dmin2) - m.p[22] > 40.0 * m.p[18]) uniform = 0;
     }
     s_uniform = uniform;
   }
@@ -1147,6 +1162,37 @@ __global__ void __launch_bounds__(ColCfg<BS>::NT) k_mask(T* chi, const int32_t* 
   if (uniform >= 0) {
 #pragma unroll
     for (int iz = 0; iz < BS; ++iz) out[L::idx(ix, iy, iz)] = T(uniform);
+    return;
+  }
+  if (m.kind == 2) {
+    // signed distance to the box in the body frame, in the field precision
+    const T hT = T(h);
+    T Rm[9], x0[3], cb[3], hb[3];
+    for (int k = 0; k < 9; ++k) Rm[k] = T(m.p[k]);
+    for (int a = 0; a < 3; ++a) {
+      x0[a] = T(m.p[9 + a]);
+      cb[a] = T(m.p[12 + a]);
+      hb[a] = T(m.p[15 + a]);
+    }
+    const T dl = T(m.p[18]);
+    const T cut = T(sizeof(T) == 4 ? 10.0 : 20.0) * dl;
+    const T rx = T(lattice(ph, bi, 0, ix, M)) * hT - x0[0], ry = T(lattice(ph, bi, 1, iy, M)) * hT - x0[1];
+    for (int iz = 0; iz < BS; ++iz) {
+      const T rz = T(lattice(ph, bi, 2, iz, M)) * hT - x0[2];
+      T out2 = T(0), qmax = T(-1e30);
+      for (int k = 0; k < 3; ++k) {
+        const T xb = Rm[k] * rx + Rm[3 + k] * ry + Rm[6 + k] * rz;     // (R^T r)_k
+        const T q = (xb - cb[k] < T(0) ? cb[k] - xb : xb - cb[k]) - hb[k];
+        if (q > T(0)) out2 += q * q;
+        qmax = q > qmax ? q : qmax;
+      }
+      const T d = tsqrt(out2) + (qmax < T(0) ? qmax : T(0));
+      T c;
+      if (d > cut) c = T(0);
+      else if (d < -cut) c = T(1);
+      else c = T(0.5) * (T(1) - ttanh(d / dl));
+      out[L::idx(ix, iy, iz)] = c;
+    }
     return;
   }
   // evaluated in the field precision: FP64 fields in double, FP32 fields in float; the
@@ -1171,6 +1217,73 @@ __global__ void __launch_bounds__(ColCfg<BS>::NT) k_mask(T* chi, const int32_t* 
 }
 
 // ---- (9) diagnostics: raw per-block sums over the half-open points [0, M-1]^3 -----------------
+// Penalization source of a rotating rigid body (mask kind 2): S = chi (omega x (x - x_0)) / C_eta,
+// added to the stage outputs (out += c_out S, acc += c_acc S).  FP64 arithmetic per point is
+// avoided for FP32 fields: the pose arrives in double and is converted once.
+template <typename T, int BS>
+__global__ void __launch_bounds__(kNT) k_solid_source(T* out, T* acc, const T* chi, const int32_t* blist,
+                                                      const int4* binfo, const PhysK ph, const MaskK m, double c_out,
+                                                      double c_acc, int acc_too) {
+  using L = Lay<T, BS>;
+  constexpr int M = L::M;
+  const int slot = blist[blockIdx.x];
+  const int4 bi = binfo[blockIdx.x];
+  const T hT = T(ph.h[bi.x]);
+  const T w0 = T(m.p[19]), w1 = T(m.p[20]), w2 = T(m.p[21]);
+  const T x0 = T(m.p[9]), y0 = T(m.p[10]), z0 = T(m.p[11]);
+  const T ci = T(ph.inv_ceta), co = T(c_out), ca = T(c_acc);
+  const size_t base = (size_t)slot * L::BLK;
+  for (int t = threadIdx.x; t < BS * BS * BS; t += kNT) {
+    const int x = t % BS, y = (t / BS) % BS, z = t / (BS * BS);
+    const int pi = L::idx(x, y, z);
+    const T c = chi[(size_t)slot * L::FS + pi];
+    if (c == T(0)) continue;
+    const T rx = T(lattice(ph, bi, 0, x, M)) * hT - x0;
+    const T ry = T(lattice(ph, bi, 1, y, M)) * hT - y0;
+    const T rz = T(lattice(ph, bi, 2, z, M)) * hT - z0;
+    const T s[3] = {c * ci * (w1 * rz - w2 * ry), c * ci * (w2 * rx - w0 * rz), c * ci * (w0 * ry - w1 * rx)};
+    for (int a = 0; a < 3; ++a) {
+      out[base + (size_t)a * L::FS + pi] += co * s[a];
+      if (acc_too) acc[base + (size_t)a * L::FS + pi] += ca * s[a];
+    }
+  }
+}
+
+// Per block sums over the half-open points of chi u_s (force of a moving body, Sec. 2.2).
+template <typename T, int BS>
+__global__ void __launch_bounds__(kNT) k_solid_moment(const T* chi, const int32_t* blist, const int4* binfo,
+                                                      const PhysK ph, const MaskK m, double* out) {
+  using L = Lay<T, BS>;
+  constexpr int M = L::M;
+  const int slot = blist[blockIdx.x];
+  const int4 bi = binfo[blockIdx.x];
+  const double h = ph.h[bi.x];
+  double s[3] = {0.0, 0.0, 0.0};
+  for (int i = threadIdx.x; i < M * M * M; i += kNT) {
+    const int x = i % M, y = (i / M) % M, z = i / (M * M);
+    const double c = chi[(size_t)slot * L::FS + L::idx(x, y, z)];
+    if (c == 0.0) continue;
+    const double rx = lattice(ph, bi, 0, x, M) * h - m.p[9];
+    const double ry = lattice(ph, bi, 1, y, M) * h - m.p[10];
+    const double rz = lattice(ph, bi, 2, z, M) * h - m.p[11];
+    s[0] += c * (m.p[20] * rz - m.p[21] * ry);
+    s[1] += c * (m.p[21] * rx - m.p[19] * rz);
+    s[2] += c * (m.p[19] * ry - m.p[20] * rx);
+  }
+  __shared__ double red[3][kNT / 32];
+  for (int k = 0; k < 3; ++k)
+    for (int o = 16; o > 0; o >>= 1) s[k] += __shfl_xor_sync(0xffffffffu, s[k], o);
+  if ((threadIdx.x & 31) == 0)
+    for (int k = 0; k < 3; ++k) red[k][threadIdx.x >> 5] = s[k];
+  __syncthreads();
+  if (threadIdx.x < 4) {
+    double t = 0.0;
+    if (threadIdx.x < 3)
+      for (int w = 0; w < kNT / 32; ++w) t += red[threadIdx.x][w];
+    out[(size_t)blockIdx.x * 4 + threadIdx.x] = t;
+  }
+}
+
 template <typename T, int BS>
 __global__ void __launch_bounds__(kNT) k_diag(const T* reg, const T* chi, const int32_t* blist, double* out) {
   using L = Lay<T, BS>;
@@ -1367,6 +1480,18 @@ void launch_mask(int Bs, T* chi, const int32_t* blist, const int32_t* ranks, int
   else k_mask<T, 9><<<grid1(n), ColCfg<9>::NT, 0, st>>>(chi, blist, ranks, binfo, p, m);
 }
 template <typename T>
+void launch_solid_source(int Bs, T* out, T* acc, const T* chi, const int32_t* blist, const int4* binfo, int64_t n,
+                         const PhysK& p, const MaskK& m, double c_out, double c_acc, int acc_too, cudaStream_t st) {
+  if (n <= 0) return;
+  ACM_BS_DISPATCH(Bs, k_solid_source, <<<grid1(n), kNT, 0, st>>>(out, acc, chi, blist, binfo, p, m, c_out, c_acc, acc_too));
+}
+template <typename T>
+void launch_solid_moment(int Bs, const T* chi, const int32_t* blist, const int4* binfo, int64_t n, const PhysK& p,
+                         const MaskK& m, double* out, cudaStream_t st) {
+  if (n <= 0) return;
+  ACM_BS_DISPATCH(Bs, k_solid_moment, <<<grid1(n), kNT, 0, st>>>(chi, blist, binfo, p, m, out));
+}
+template <typename T>
 void launch_diag(int Bs, const T* reg, const T* chi, const int32_t* blist, int64_t n, double* out, cudaStream_t st) {
   if (n <= 0) return;
   ACM_BS_DISPATCH(Bs, k_diag, <<<grid1(n), kNT, 0, st>>>(reg, chi, blist, out));
@@ -1397,6 +1522,8 @@ void launch_scatter(int Bs, const T* dense, T* reg, const int32_t* blist, int64_
   template void launch_ic<T>(int, T*, const int32_t*, const int32_t*, int64_t, const int4*, const PhysK&, const IcK&, cudaStream_t); \
   template void launch_mask<T>(int, T*, const int32_t*, const int32_t*, int64_t, const int4*, const PhysK&, const MaskK&, cudaStream_t); \
   template void launch_diag<T>(int, const T*, const T*, const int32_t*, int64_t, double*, cudaStream_t);   \
+  template void launch_solid_source<T>(int, T*, T*, const T*, const int32_t*, const int4*, int64_t, const PhysK&, const MaskK&, double, double, int, cudaStream_t); \
+  template void launch_solid_moment<T>(int, const T*, const int32_t*, const int4*, int64_t, const PhysK&, const MaskK&, double*, cudaStream_t); \
   template void launch_gather<T>(int, const T*, T*, const int32_t*, int64_t, int, cudaStream_t);          \
   template void launch_scatter<T>(int, const T*, T*, const int32_t*, int64_t, cudaStream_t);
 ACM_INST(float)

@@ -103,6 +103,10 @@ struct acm_forest {
 
   bool mask_on = false;
   acm::MaskK mask{};
+  // moving rigid plate (mask kind 2): chord, span, thickness, stroke and pitch amplitudes (rad),
+  // frequency, pivot x, y, z, delta; its pose follows the simulated time
+  bool moving = false;
+  double plate[10] = {};
   acm::PhysK phk{};
   double time = 0.0;
   std::string err;
@@ -402,10 +406,42 @@ double cfl_dt(const acm_forest* f, double u_max) {
   return dt;
 }
 
+// Pose of the moving plate at time t into the mask parameters (kind 2): the plate is the box
+// |x_b| <= c/2, 0 <= y_b <= b, |z_b| <= thickness/2 of its body frame, x = x_0 + R(t) x_b with
+// R = R_z(phi) R_y(alpha), phi = phi_m sin(2 pi f t) (stroke about the vertical), alpha =
+// alpha_m cos(2 pi f t) (pitch about the span axis), and u_s = omega x (x - x_0) with
+// omega = phi' e_z + alpha' R_z(phi) e_y (Sec. 2.2 mask and solid velocity of a rigid body).
+void plate_pose(acm_forest* f, double t) {
+  const double* q = f->plate;
+  const double w = 2.0 * 3.14159265358979323846 * q[5];
+  const double phi = q[3] * std::sin(w * t), alpha = q[4] * std::cos(w * t);
+  const double dphi = q[3] * w * std::cos(w * t), dalpha = -q[4] * w * std::sin(w * t);
+  const double cp = std::cos(phi), sp = std::sin(phi), ca = std::cos(alpha), sa = std::sin(alpha);
+  // R_z(phi) R_y(alpha), row-major
+  const double R[9] = {cp * ca, -sp, cp * sa, sp * ca, cp, sp * sa, -sa, 0.0, ca};
+  acm::MaskK& m = f->mask;
+  m.kind = 2;
+  for (int k = 0; k < 9; ++k) m.p[k] = R[k];
+  for (int a = 0; a < 3; ++a) m.p[9 + a] = q[6 + a];
+  m.p[12] = 0.0;
+  m.p[13] = 0.5 * q[1];
+  m.p[14] = 0.0;
+  m.p[15] = 0.5 * q[0];
+  m.p[16] = 0.5 * q[1];
+  m.p[17] = 0.5 * q[2];
+  m.p[18] = q[9];
+  // omega = phi' e_z + alpha' R_z(phi) e_y, R_z(phi) e_y = (-sin phi, cos phi, 0)
+  m.p[19] = -dalpha * sp;
+  m.p[20] = dalpha * cp;
+  m.p[21] = dphi;
+  m.p[22] = std::sqrt(0.25 * q[0] * q[0] + q[1] * q[1] + 0.25 * q[2] * q[2]);
+}
+
 // Mask on every block, or only on the blocks whose slots are in `fresh` (new blocks).
 template <typename T>
 acm_status eval_mask(acm_forest* f, const std::vector<int32_t>* fresh = nullptr) {
   if (!f->mask_on) return ACM_OK;
+  if (f->moving) plate_pose(f, f->time);
   const int32_t* ranks = nullptr;
   int64_t n = (int64_t)f->order.size();
   std::vector<int32_t> rl;
@@ -449,6 +485,16 @@ acm_status rk4(acm_forest* f, double dt, double* dt_used, T* const* save = nullp
     // stage 1 looks up the slabs' source points and caches them for stages 2-4 (same grid)
     acm_status st = sync_stage<T>(f, in, s > 1);
     if (st) return st;
+    const double cs_out = s == 1 || s == 2 ? dt / 2.0 : (s == 3 ? dt : dt / 6.0);
+    const double cs_acc = s == 1 ? dt / 6.0 : dt / 3.0;
+    if (f->moving) {
+      // the plate's mask at the stage time (RK4 nodes t, t + dt/2, t + dt/2, t + dt)
+      plate_pose(f, f->time + (s == 1 ? 0.0 : (s == 4 ? dt : 0.5 * dt)));
+      acm::launch_mask<T>(f->gp.Bs, reinterpret_cast<T*>(f->CHI), f->d_blist, nullptr, (int64_t)f->order.size(),
+                          f->d_binfo, f->phk, f->mask, f->st);
+      CKL();
+      ++f->launches;
+    }
     if (save) {
       acm::launch_copy_blocks<T>(f->gp.Bs, in, save[s - 1], f->d_blist, 1, (int64_t)f->order.size(), f->st);
       CKL();
@@ -473,11 +519,22 @@ acm_status rk4(acm_forest* f, double dt, double* dt_used, T* const* save = nullp
     acm::launch_stage<T>(s, f->gp.Bs, a, t, f->phk, f->d_err, f->st);
     CKL();
     ++f->launches;
+    if (f->moving) {
+      // + chi u_s / C_eta, the part of the penalization the stage kernel leaves out (u_s = 0 there)
+      acm::launch_solid_source<T>(f->gp.Bs, out, ACC, reinterpret_cast<const T*>(f->CHI), f->d_blist, f->d_binfo,
+                                  (int64_t)f->order.size(), f->phk, f->mask, cs_out, cs_acc, s < 4, f->st);
+      CKL();
+      ++f->launches;
+    }
     if (f->timing) CK(cudaEventRecord(f->ev[3 * (s - 1) + 2], f->st));
   }
   CK(cudaMemcpyAsync(f->h_err, f->d_err, sizeof(int), cudaMemcpyDeviceToHost, f->st));
-  f->norms_fresh = true;
+  f->norms_fresh = !f->moving;
   f->time += dt;
+  if (f->moving) {
+    acm_status st = eval_mask<T>(f);
+    if (st) return st;
+  }
   // algorithmic bytes of the four stage kernels: per point 64 words (registers Y, U, acc in and
   // out, see stage.cu) plus one word of mask per stage when a mask is set
   const double npts = (double)f->order.size() * f->gp.Bs * f->gp.Bs * f->gp.Bs;
@@ -860,6 +917,20 @@ acm_status diagnostics(acm_forest* f, acm_diag* out) {
     for (int i = 0; i < 3; ++i) out->force[i] += part[4 * r + i] * h3 / f->pp.C_eta;
     out->energy += 0.5 * part[4 * r + 3] * h3;
     out->blocks_per_level[f->order[r].J]++;
+  }
+  if (f->moving) {
+    // the force of a moving body integrates chi (u - u_s): subtract the sums of chi u_s
+    plate_pose(f, f->time);
+    acm::launch_solid_moment<T>(f->gp.Bs, reinterpret_cast<const T*>(f->CHI), f->d_blist, f->d_binfo, (int64_t)n,
+                                f->phk, f->mask, f->d_diag, f->st);
+    CKL();
+    ++f->launches;
+    CK(cudaMemcpyAsync(part.data(), f->d_diag, n * 4 * 8, cudaMemcpyDeviceToHost, f->st));
+    CK(cudaStreamSynchronize(f->st));
+    for (size_t r = 0; r < n; ++r) {
+      const double h = h_of(f, f->order[r].J);
+      for (int i = 0; i < 3; ++i) out->force[i] -= part[4 * r + i] * h * h * h / f->pp.C_eta;
+    }
   }
   out->u_max = m[4];
   for (int k = 0; k < 4; ++k) out->norms[k] = m[k];
@@ -1286,11 +1357,20 @@ acm_status acm_set_mask(acm_forest* f, int kind, const double* params, int n, do
   if (!f) return ACM_EINVAL;
   if (kind == ACM_MASK_NONE) {
     f->mask_on = false;
+    f->moving = false;
   } else if (kind == ACM_MASK_SPHERE) {
     if (!params || n < 5 || !(params[4] > 0)) return fail(f, ACM_EINVAL, "sphere mask needs cx, cy, cz, R, delta>0");
     f->mask_on = true;
+    f->moving = false;
     f->mask.kind = 1;
     for (int i = 0; i < 5; ++i) f->mask.p[i] = params[i];
+  } else if (kind == ACM_MASK_PLATE) {
+    if (!params || n < 10 || !(params[0] > 0) || !(params[1] > 0) || !(params[2] > 0) || !(params[9] > 0))
+      return fail(f, ACM_EINVAL, "plate mask needs chord, span, thickness > 0, phi_m, alpha_m, f, x0, y0, z0, delta > 0");
+    f->mask_on = true;
+    f->moving = true;
+    for (int i = 0; i < 10; ++i) f->plate[i] = params[i];
+    plate_pose(f, f->time);
   } else {
     return fail(f, ACM_EINVAL, "unknown mask kind");
   }
@@ -1342,6 +1422,7 @@ acm_status acm_rk4_step(acm_forest* f, double dt, double* dt_used) {
 }
 
 acm_status acm_rk4_steps(acm_forest* f, int nsteps, double dt, int use_graph, double* t_end, int* graph_used) {
+  if (f && f->moving) return fail(f, ACM_EINVAL, "a moving mask needs acm_rk4_step (its pose changes per stage)");
   if (!f) return ACM_EINVAL;
   acm_status s = DISPATCH(f, rk4_steps, f, nsteps, dt, use_graph, graph_used);
   if (s) return s;
@@ -1356,6 +1437,7 @@ acm_status acm_rk4_steps_batch(acm_forest* const* forests, int n, int nsteps, do
   for (int i = 0; i < n; ++i) {
     if (!forests[i]) return ACM_EINVAL;
     if (forests[i]->order.empty()) return fail(forests[i], ACM_EINVAL, "empty forest");
+    if (forests[i]->moving) return fail(forests[i], ACM_EINVAL, "a moving mask needs acm_rk4_step");
     for (int j = 0; j < i; ++j)
       if (forests[j] == forests[i]) return fail(forests[i], ACM_EINVAL, "forest listed twice");
   }

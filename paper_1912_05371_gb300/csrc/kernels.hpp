@@ -161,13 +161,28 @@ template <typename T>
 void launch_ic(int Bs, T* reg, const int32_t* blist, const int32_t* ranks, int64_t n, const int4* binfo,
                const PhysK& p, const IcK& ic, cudaStream_t st);
 
+// kind 1 (sphere): p = cx, cy, cz, R, delta.  kind 2 (rigid box, e.g. the moving plate, at one
+// time): p[0..8] = R (body to world, row-major), p[9..11] = pivot x_0, p[12..14] = box centre and
+// p[15..17] = half extents in the body frame, p[18] = delta, p[19..21] = angular velocity omega,
+// p[22] = radius around x_0 that contains the box.  Body coordinates x_b = R^T (x - x_0).
 struct MaskK {
   int kind;
-  double p[8];
+  double p[24];
 };
 template <typename T>
 void launch_mask(int Bs, T* chi, const int32_t* blist, const int32_t* ranks, int64_t n, const int4* binfo,
                  const PhysK& p, const MaskK& m, cudaStream_t st);
+
+// Solid velocity of a rotating rigid body (mask kind 2), u_s = omega x (x - x_0): adds the
+// penalization's source chi u_s / C_eta of the stage to the stage outputs, out += c_out S and,
+// if acc_too, acc += c_acc S (the stage kernel has applied -chi u / C_eta).
+template <typename T>
+void launch_solid_source(int Bs, T* out, T* acc, const T* chi, const int32_t* blist, const int4* binfo, int64_t n,
+                         const PhysK& p, const MaskK& m, double c_out, double c_acc, int acc_too, cudaStream_t st);
+// Per block sums over the half-open points of chi u_s (3 components): out[n][4].
+template <typename T>
+void launch_solid_moment(int Bs, const T* chi, const int32_t* blist, const int4* binfo, int64_t n, const PhysK& p,
+                         const MaskK& m, double* out, cudaStream_t st);
 
 // Per block raw sums over the half-open points: [sum chi u, sum chi v, sum chi w, sum |u|^2].
 template <typename T>
