@@ -265,11 +265,12 @@ def wavelet_comparison(A, stream, precision, Jmax, max_blocks, nsteps=10, warmup
 
 
 def adjoint_measurement(A, stream, nsteps=100, ckpt_every=10, w_energy=0.1):
-    """The adjoint workload: the sphere case at levels 2..4 in FP64 on its initial grid (frozen),
-    nsteps RK4 steps of one fixed dt; CUDA-event time of the forward steps alone and of the whole
-    adjoint call (forward with checkpoints every ckpt_every steps, recomputation, backward sweep)."""
+    """The adjoint workload: the sphere case at levels 2..4, FP32 fields and FP64 adjoint, on its
+    initial grid (frozen), nsteps RK4 steps of one fixed dt; CUDA-event time of the forward steps
+    alone and of the whole adjoint call (forward with checkpoints every ckpt_every steps,
+    recomputation, backward sweep)."""
     import torch
-    grid, phys, mask, ic, _ = sphere_setup(Jmax=4, precision=64, max_blocks=2048)
+    grid, phys, mask, ic, _ = sphere_setup(Jmax=4, precision=32, max_blocks=2048)
     f = A.Forest(grid, phys, stream=stream)
     f.set_mask(A.ACM_MASK_SPHERE, mask)
     f.init_grid(A.ACM_IC_UNIFORM, ic)
@@ -292,7 +293,7 @@ def adjoint_measurement(A, stream, nsteps=100, ckpt_every=10, w_energy=0.1):
     adj = e0.elapsed_time(e1)
     nb = f.n_blocks()
     f.close()
-    return {"workload": f"sphere, levels 2..4, frozen grid of {nb} blocks of 17^3, FP64, {nsteps} steps, "
+    return {"workload": f"sphere, levels 2..4, frozen grid of {nb} blocks of 17^3, FP32 forward, FP64 adjoint, {nsteps} steps, "
                         f"checkpoints every {ckpt_every}", "forward_ms_per_step": fwd / nsteps,
             "adjoint_ms_per_step": adj / nsteps, "adjoint_over_forward": adj / fwd, "J": J,
             "dJ_dtheta": [float(v) for v in gth]}

@@ -220,9 +220,10 @@ acm_status acm_autotune(acm_forest* f, int* fw_ctas, int* slab_ctas);
  * differentiable), the objective J = (1/N) sum_{n=1..N} [F_x(U_n) + w_energy E(U_n)] with the
  * force and energy of Sec. 2.2, and its gradient with respect to the sphere mask's centre and
  * radius (dJ_dtheta[0..3] = d/dcx, d/dcy, d/dcz, d/dR, host) and the initial state (dJ_dU0,
- * block order, fields layout of acm_read_fields, n_elems = n_blocks*4*Bs^3; device pointer if
- * on_device, else host; may be NULL).  FP64 forests with the sphere mask only (ACM_EINVAL
- * otherwise).  The states at every ckpt_every-th step are kept and each segment is recomputed
+ * FP64 values whatever the forest's precision, block order, fields layout of acm_read_fields,
+ * n_elems = n_blocks*4*Bs^3; device pointer if on_device, else host; may be NULL).  FP32 or
+ * FP64 forests with the sphere mask (ACM_EINVAL otherwise): the forward steps run in the
+ * forest's precision, every adjoint variable and sum in FP64.  The states at every ckpt_every-th step are kept and each segment is recomputed
  * in the backward sweep.  ws: caller device buffer of at least acm_adjoint_bytes(f, nsteps,
  * ckpt_every) bytes (ACM_ENOMEM if smaller).  The forest's state and time are unchanged on
  * return; the call synchronises the stream.  ACM_EGRADING if a ghost point's source is

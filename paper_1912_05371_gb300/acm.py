@@ -258,7 +258,8 @@ class Forest:
     def adjoint_sphere(self, nsteps, dt, ckpt_every=10, w_energy=0.1):
         """J = (1/N) sum_n [F_x(U_n) + w_energy E(U_n)] over nsteps fixed-dt RK4 steps on the frozen
         grid, and its gradient: returns (J, dJ/d(cx, cy, cz, R) (4,), dJ/dU_0 in the layout of
-        read_fields).  FP64 forests with the sphere mask; the forest's state is unchanged."""
+        read_fields, float64).  The forward runs in the forest's precision, the adjoint in FP64;
+        the sphere mask must be set; the forest's state is unchanged."""
         import torch
         nbytes = int(self.L.acm_adjoint_bytes(self.h, int(nsteps), int(ckpt_every)))
         ws = torch.empty(nbytes, dtype=torch.uint8, device=self.pool.device)

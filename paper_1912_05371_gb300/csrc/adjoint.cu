@@ -1,4 +1,6 @@
-// Discrete adjoint of the RK4 steps on a frozen grid (FP64 registers): kernels of libacm.
+// Discrete adjoint of the RK4 steps on a frozen grid: kernels of libacm.  The forward state and
+// the mask are in the forest's precision T; every adjoint variable, coefficient and sum is FP64
+// (indexed like a register of T: same block, component and point offsets).
 //
 // One RK4 step (Sec. 2.3) maps U to U' = V + dt/6 (K1 + 2 K2 + 2 K3 + K4), V = W U, with
 // K_s = G(Y_s) the right-hand side of eqs. (u_eqn-1, p_eqn-1) (Sec. 2.1-2.2) of the synchronised
@@ -48,12 +50,12 @@ __device__ __forceinline__ double sponge_at(const PhysK& ph, int4 bi, int x, int
 
 // Value of the stage state at local point (x, y, z) of a block: its own point inside, else the
 // ghost value (finest leaf holding it, else the DD-4 prediction).
-template <int BS>
-__device__ __forceinline__ double yval(const double* Y, const int* nbh, size_t own, int x, int y, int z, int f) {
-  using L = Lay<double, BS>;
+template <typename T, int BS>
+__device__ __forceinline__ double yval(const T* Y, const int* nbh, size_t own, int x, int y, int z, int f) {
+  using L = Lay<T, BS>;
   constexpr int M = L::M;
-  if (x >= 0 && x <= M && y >= 0 && y <= M && z >= 0 && z <= M) return Y[own + (size_t)f * L::FS + L::idx(x, y, z)];
-  return point_value<double, BS>(Y, nbh, x, y, z, f);
+  if (x >= 0 && x <= M && y >= 0 && y <= M && z >= 0 && z <= M) return (double)Y[own + (size_t)f * L::FS + L::idx(x, y, z)];
+  return (double)point_value<T, BS>(Y, nbh, x, y, z, f);
 }
 
 // Coefficients of loc^T at each interior point p of block `rank` (kappa: the adjoint stage
@@ -65,11 +67,11 @@ __device__ __forceinline__ double yval(const double* Y, const int* nbh, size_t o
 //   [16 + j]  pointwise term of field j: -sum_i kappa_i D1_j u_i - (chi/C_eta + chi_sp/C_sp) kappa_j,
 //             and for p: -(C_gamma + chi_sp/C_sp) kappa_p
 // The mask sensitivity -sum_i kappa_i u_i / C_eta is added to gchi.
-template <int BS>
-__global__ void __launch_bounds__(kNA) k_adj_weights(const double* Y, const double* kap, const double* chi,
+template <typename T, int BS>
+__global__ void __launch_bounds__(kNA) k_adj_weights(const T* Y, const double* kap, const T* chi,
                                                      double* gchi, double* wgt, const int32_t* blist,
                                                      const int4* binfo, const int32_t* nbh_all, const PhysK ph) {
-  using L = Lay<double, BS>;
+  using L = Lay<T, BS>;
   constexpr int M = L::M, N3 = BS * BS * BS;
   __shared__ int nbh[kNbhStride];
   const int rank = blockIdx.x;
@@ -85,18 +87,19 @@ __global__ void __launch_bounds__(kNA) k_adj_weights(const double* Y, const doub
     const int x = t % BS, y = (t / BS) % BS, z = t / (BS * BS);
     const int pi = L::idx(x, y, z);
     double u[3], k[4], du[3][3];
-    for (int f = 0; f < 3; ++f) u[f] = Y[own + (size_t)f * L::FS + pi];
+    for (int f = 0; f < 3; ++f) u[f] = (double)Y[own + (size_t)f * L::FS + pi];
     for (int f = 0; f < 4; ++f) k[f] = kap[own + (size_t)f * L::FS + pi];
     for (int i = 0; i < 3; ++i)
       for (int j = 0; j < 3; ++j) {
         double s = 0.0;
         for (int m = 1; m <= 3; ++m) {
           const int dx = j == 0 ? m : 0, dy = j == 1 ? m : 0, dz = j == 2 ? m : 0;
-          s += a[m - 1] * (yval<BS>(Y, nbh, own, x + dx, y + dy, z + dz, i) - yval<BS>(Y, nbh, own, x - dx, y - dy, z - dz, i));
+          s += a[m - 1] * (yval<T, BS>(Y, nbh, own, x + dx, y + dy, z + dz, i) -
+                           yval<T, BS>(Y, nbh, own, x - dx, y - dy, z - dz, i));
         }
         du[i][j] = s * ih;
       }
-    const double c = ph.mask ? chi[(size_t)slot * L::FS + pi] : 0.0;
+    const double c = ph.mask ? (double)chi[(size_t)slot * L::FS + pi] : 0.0;
     const double cs = ph.sponge ? sponge_at(ph, bi, x, y, z, M, h) : 0.0;
     for (int i = 0; i < 3; ++i)
       for (int j = 0; j < 3; ++j) w[(size_t)(3 * i + j) * N3 + t] = -u[j] * k[i];
@@ -118,11 +121,11 @@ __global__ void __launch_bounds__(kNA) k_adj_weights(const double* Y, const doub
 // loc^T and E^T: for every point q of block `rank`'s extended region (interior and the six face
 // halos of depth 3) and component f, the sum of the stencil terms of the interior points that
 // read q, added to q's source in `nu` (FP64 atomics: several blocks reach one point).
-template <int BS>
+template <typename T, int BS>
 __global__ void __launch_bounds__(kNA) k_adj_scatter(const double* wgt, double* nu, const int32_t* blist,
                                                      const int4* binfo, const int32_t* nbh_all, const PhysK ph,
                                                      int* err) {
-  using L = Lay<double, BS>;
+  using L = Lay<T, BS>;
   constexpr int M = L::M, N3 = BS * BS * BS, NH = 6 * 3 * BS * BS;
   __shared__ int nbh[kNbhStride];
   const int rank = blockIdx.x;
@@ -183,7 +186,7 @@ __global__ void __launch_bounds__(kNA) k_adj_scatter(const double* wgt, double* 
       continue;
     }
     if (de == 0.0) continue;
-    const long long o = direct_offset<double, BS>(nbh, q[0], q[1], q[2], f);
+    const long long o = direct_offset<T, BS>(nbh, q[0], q[1], q[2], f);
     if (o >= 0) {
       atomicAdd(&nu[o], de);
       continue;
@@ -199,7 +202,7 @@ __global__ void __launch_bounds__(kNA) k_adj_scatter(const double* wgt, double* 
           const int yy = ny == 4 ? q[1] + off[ky] : q[1];
           const int zz = nz == 4 ? q[2] + off[kz] : q[2];
           const double wt = (nx == 4 ? wd[kx] : 1.0) * (ny == 4 ? wd[ky] : 1.0) * (nz == 4 ? wd[kz] : 1.0);
-          const long long o2 = direct_offset<double, BS>(nbh, xx, yy, zz, f);
+          const long long o2 = direct_offset<T, BS>(nbh, xx, yy, zz, f);
           if (o2 < 0) {
             atomicOr(err, 8);
             continue;
@@ -212,10 +215,10 @@ __global__ void __launch_bounds__(kNA) k_adj_scatter(const double* wgt, double* 
 // W^T on register r: a boundary point of block `rank` that a finer leaf holds (the first refined
 // box among those containing it, in the order the forward search uses) adds its value to that
 // leaf's point and is cleared.
-template <int BS>
+template <typename T, int BS>
 __global__ void __launch_bounds__(kNA) k_adj_fw_T(double* r, const int32_t* blist, const int32_t* nbh_all,
                                                   const uint8_t* finer) {
-  using L = Lay<double, BS>;
+  using L = Lay<T, BS>;
   constexpr int M = L::M, N3 = BS * BS * BS;
   const int rank = blockIdx.x;
   if (!finer[rank]) return;
@@ -259,10 +262,10 @@ __global__ void __launch_bounds__(kNA) k_adj_fw_T(double* r, const int32_t* blis
 }
 
 // out = a x + b y over the blocks of the list (whole block strides); y may be null.
-template <int BS>
+template <typename T, int BS>
 __global__ void __launch_bounds__(kNA) k_adj_lin(double* out, double a, const double* x, double b, const double* y,
                                                  const int32_t* blist) {
-  using L = Lay<double, BS>;
+  using L = Lay<T, BS>;
   const size_t base = (size_t)blist[blockIdx.x] * L::BLK;
   for (int i = threadIdx.x; i < L::BLK; i += kNA)
     out[base + i] = a * x[base + i] + (y ? b * y[base + i] : 0.0);
@@ -270,31 +273,32 @@ __global__ void __launch_bounds__(kNA) k_adj_lin(double* out, double a, const do
 
 // Direct terms of (1/N) [F_x(U) + w_E E(U)] (Sec. 2.2, half-open points, weight h^3): into lam
 // and, for the mask, into gchi.
-template <int BS>
-__global__ void __launch_bounds__(kNA) k_adj_objective(const double* U, const double* chi, double* lam, double* gchi,
+template <typename T, int BS>
+__global__ void __launch_bounds__(kNA) k_adj_objective(const T* U, const T* chi, double* lam, double* gchi,
                                                        const int32_t* blist, const int4* binfo, const PhysK ph,
                                                        double wN, double wE) {
-  using L = Lay<double, BS>;
+  using L = Lay<T, BS>;
   constexpr int M = L::M;
   const int slot = blist[blockIdx.x];
   const double h = ph.h[binfo[blockIdx.x].x], h3 = h * h * h;
   const size_t own = (size_t)slot * L::BLK;
   for (int t = threadIdx.x; t < M * M * M; t += kNA) {
     const int pi = L::idx(t % M, (t / M) % M, t / (M * M));
-    const double u = U[own + pi];
-    const double c = ph.mask ? chi[(size_t)slot * L::FS + pi] : 0.0;
+    const double u = (double)U[own + pi];
+    const double c = ph.mask ? (double)chi[(size_t)slot * L::FS + pi] : 0.0;
     lam[own + pi] += wN * (c * ph.inv_ceta + wE * u) * h3;
-    for (int f = 1; f < 3; ++f) lam[own + (size_t)f * L::FS + pi] += wN * wE * U[own + (size_t)f * L::FS + pi] * h3;
+    for (int f = 1; f < 3; ++f)
+      lam[own + (size_t)f * L::FS + pi] += wN * wE * (double)U[own + (size_t)f * L::FS + pi] * h3;
     if (ph.mask) gchi[(size_t)slot * L::FS + pi] += wN * u * h3 * ph.inv_ceta;
   }
 }
 
 // sum over all points of gchi * d chi / d (cx, cy, cz, R) for the sphere mask
 // chi = (1 - tanh((|x - c| - R)/delta))/2 (Sec. 2.2), into out[0..3].
-template <int BS>
+template <typename T, int BS>
 __global__ void __launch_bounds__(kNA) k_adj_theta(const double* gchi, const int32_t* blist, const int4* binfo,
                                                    const PhysK ph, const MaskK m, double* out) {
-  using L = Lay<double, BS>;
+  using L = Lay<T, BS>;
   constexpr int M = L::M, N3 = BS * BS * BS;
   const int slot = blist[blockIdx.x];
   const int4 bi = binfo[blockIdx.x];
@@ -329,49 +333,87 @@ __global__ void __launch_bounds__(kNA) k_adj_theta(const double* gchi, const int
   }
 }
 
+// Block-order copy of an FP64 register indexed like a register of T: dense[rank][f][z][y][x].
+template <typename T, int BS>
+__global__ void __launch_bounds__(kNA) k_adj_gather(const double* r, double* dense, const int32_t* blist) {
+  using L = Lay<T, BS>;
+  constexpr int N3 = BS * BS * BS;
+  const size_t own = (size_t)blist[blockIdx.x] * L::BLK;
+  double* d = dense + (size_t)blockIdx.x * 4 * N3;
+  for (int t = threadIdx.x; t < 4 * N3; t += kNA) {
+    const int f = t / N3, r3 = t % N3;
+    d[t] = r[own + (size_t)f * L::FS + L::idx(r3 % BS, (r3 / BS) % BS, r3 / (BS * BS))];
+  }
+}
+
 inline dim3 g1(int64_t n) { return dim3((unsigned)n); }
 
 #define ACM_ADJ_BS(Bs, KERNEL, ...)                      \
   do {                                                   \
-    if ((Bs) == 17) { KERNEL<17> __VA_ARGS__; }          \
-    else { KERNEL<9> __VA_ARGS__; }                      \
+    if ((Bs) == 17) { KERNEL<T, 17> __VA_ARGS__; }       \
+    else { KERNEL<T, 9> __VA_ARGS__; }                   \
   } while (0)
 
 }  // namespace
 
 size_t adj_weight_doubles(int Bs, int64_t nblocks) { return (size_t)kNW * Bs * Bs * Bs * (size_t)nblocks; }
 
-void launch_adj_jgt(int Bs, const double* Y, const double* kap, const double* chi, double* gchi, double* wgt,
-                    double* nu, const int32_t* blist, const int4* binfo, const int32_t* nbh, const uint8_t* finer,
-                    int64_t n, const PhysK& ph, int* err, cudaStream_t st) {
+template <typename T>
+void launch_adj_jgt(int Bs, const T* Y, const double* kap, const T* chi, double* gchi, double* wgt, double* nu,
+                    const int32_t* blist, const int4* binfo, const int32_t* nbh, const uint8_t* finer, int64_t n,
+                    const PhysK& ph, int* err, cudaStream_t st) {
   if (n <= 0) return;
   ACM_ADJ_BS(Bs, k_adj_weights, <<<g1(n), kNA, 0, st>>>(Y, kap, chi, gchi, wgt, blist, binfo, nbh, ph));
   ACM_ADJ_BS(Bs, k_adj_scatter, <<<g1(n), kNA, 0, st>>>(wgt, nu, blist, binfo, nbh, ph, err));
   ACM_ADJ_BS(Bs, k_adj_fw_T, <<<g1(n), kNA, 0, st>>>(nu, blist, nbh, finer));
 }
 
+template <typename T>
 void launch_adj_fw_T(int Bs, double* r, const int32_t* blist, const int32_t* nbh, const uint8_t* finer, int64_t n,
                      cudaStream_t st) {
   if (n <= 0) return;
   ACM_ADJ_BS(Bs, k_adj_fw_T, <<<g1(n), kNA, 0, st>>>(r, blist, nbh, finer));
 }
 
+template <typename T>
 void launch_adj_lin(int Bs, double* out, double a, const double* x, double b, const double* y, const int32_t* blist,
                     int64_t n, cudaStream_t st) {
   if (n <= 0) return;
   ACM_ADJ_BS(Bs, k_adj_lin, <<<g1(n), kNA, 0, st>>>(out, a, x, b, y, blist));
 }
 
-void launch_adj_objective(int Bs, const double* U, const double* chi, double* lam, double* gchi, const int32_t* blist,
+template <typename T>
+void launch_adj_objective(int Bs, const T* U, const T* chi, double* lam, double* gchi, const int32_t* blist,
                           const int4* binfo, int64_t n, const PhysK& ph, double wN, double wE, cudaStream_t st) {
   if (n <= 0) return;
   ACM_ADJ_BS(Bs, k_adj_objective, <<<g1(n), kNA, 0, st>>>(U, chi, lam, gchi, blist, binfo, ph, wN, wE));
 }
 
+template <typename T>
 void launch_adj_theta(int Bs, const double* gchi, const int32_t* blist, const int4* binfo, int64_t n, const PhysK& ph,
                       const MaskK& m, double* out, cudaStream_t st) {
   if (n <= 0) return;
   ACM_ADJ_BS(Bs, k_adj_theta, <<<g1(n), kNA, 0, st>>>(gchi, blist, binfo, ph, m, out));
 }
+
+template <typename T>
+void launch_adj_gather(int Bs, const double* r, double* dense, const int32_t* blist, int64_t n, cudaStream_t st) {
+  if (n <= 0) return;
+  ACM_ADJ_BS(Bs, k_adj_gather, <<<g1(n), kNA, 0, st>>>(r, dense, blist));
+}
+
+#define ACM_ADJ_INST(T)                                                                                        \
+  template void launch_adj_jgt<T>(int, const T*, const double*, const T*, double*, double*, double*, const int32_t*, \
+                                  const int4*, const int32_t*, const uint8_t*, int64_t, const PhysK&, int*, cudaStream_t); \
+  template void launch_adj_fw_T<T>(int, double*, const int32_t*, const int32_t*, const uint8_t*, int64_t, cudaStream_t); \
+  template void launch_adj_lin<T>(int, double*, double, const double*, double, const double*, const int32_t*, int64_t, \
+                                  cudaStream_t);                                                              \
+  template void launch_adj_objective<T>(int, const T*, const T*, double*, double*, const int32_t*, const int4*, int64_t, \
+                                        const PhysK&, double, double, cudaStream_t);                          \
+  template void launch_adj_theta<T>(int, const double*, const int32_t*, const int4*, int64_t, const PhysK&,   \
+                                    const MaskK&, double*, cudaStream_t);                                     \
+  template void launch_adj_gather<T>(int, const double*, double*, const int32_t*, int64_t, cudaStream_t);
+ACM_ADJ_INST(float)
+ACM_ADJ_INST(double)
 
 }  // namespace acm

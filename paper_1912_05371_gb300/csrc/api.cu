@@ -1039,23 +1039,26 @@ acm_status autotune(acm_forest* f, int* fw_ctas, int* slab_ctas) {
 // ceil(N / c) checkpoints, the mask sensitivity (one component), the loc^T coefficients and the
 // 4 parameter sums.
 struct AdjLayout {
-  size_t lam, kap, nu, sum, y[4], seg, ck, gchi, wgt, theta, total, reg;
+  size_t lam, kap, nu, sum, y[4], seg, ck, gchi, wgt, theta, total;
+  size_t reg;    // bytes of an FP64 adjoint register (indexed like a register of the forest)
+  size_t sreg;   // bytes of a state register in the forest's precision
   int nck;
 };
 
 AdjLayout adj_layout(const acm_forest* f, int nsteps, int c) {
   AdjLayout L{};
   L.reg = (size_t)f->gp.max_blocks * (size_t)f->lay.BLK * 8;
+  L.sreg = (size_t)f->gp.max_blocks * (size_t)f->lay.BLK * f->esz;
   size_t o = 0;
   auto take = [&](size_t b) { const size_t r = o; o = (o + b + 255) & ~(size_t)255; return r; };
   L.lam = take(L.reg);
   L.kap = take(L.reg);
   L.nu = take(L.reg);
   L.sum = take(L.reg);
-  for (int s = 0; s < 4; ++s) L.y[s] = take(L.reg);
-  L.seg = take(L.reg * (size_t)(c + 1));
+  for (int s = 0; s < 4; ++s) L.y[s] = take(L.sreg);
+  L.seg = take(L.sreg * (size_t)(c + 1));
   L.nck = (nsteps - 1) / c + 1;
-  L.ck = take(L.reg * (size_t)L.nck);
+  L.ck = take(L.sreg * (size_t)L.nck);
   L.gchi = take((size_t)f->gp.max_blocks * (size_t)f->lay.FS * 8);
   L.wgt = take(acm::adj_weight_doubles(f->gp.Bs, f->gp.max_blocks) * 8);
   L.theta = take(64);
@@ -1064,11 +1067,12 @@ AdjLayout adj_layout(const acm_forest* f, int nsteps, int c) {
 }
 
 // F_x and E of the current state (Sec. 2.2), as acm_diagnostics sums them.
+template <typename T>
 acm_status force_energy(acm_forest* f, double* Fx, double* E) {
   const size_t n = f->order.size();
-  acm::launch_diag<double>(f->gp.Bs, reinterpret_cast<const double*>(f->U),
-                           f->mask_on ? reinterpret_cast<const double*>(f->CHI) : nullptr, f->d_blist, (int64_t)n,
-                           f->d_diag, f->st);
+  acm::launch_diag<T>(f->gp.Bs, reinterpret_cast<const T*>(f->U),
+                      f->mask_on ? reinterpret_cast<const T*>(f->CHI) : nullptr, f->d_blist, (int64_t)n, f->d_diag,
+                      f->st);
   CKL();
   ++f->launches;
   std::vector<double> part(n * 4);
@@ -1085,9 +1089,9 @@ acm_status force_energy(acm_forest* f, double* Fx, double* E) {
   return ACM_OK;
 }
 
+template <typename T>
 acm_status adjoint_sweep(acm_forest* f, int nsteps, double dt, int c, double wE, void* ws, size_t ws_bytes,
                          double* J_out, double* dtheta, void* dU0, int64_t n_elems, int on_device) {
-  if (f->gp.precision != 64) return fail(f, ACM_EINVAL, "the adjoint runs on FP64 forests");
   if (!f->mask_on || f->mask.kind != 1) return fail(f, ACM_EINVAL, "the adjoint needs the sphere mask");
   if (nsteps < 1 || c < 1 || !(dt > 0) || !ws || !J_out || !dtheta) return fail(f, ACM_EINVAL, "bad arguments");
   if (f->order.empty()) return fail(f, ACM_EINVAL, "empty forest");
@@ -1098,39 +1102,41 @@ acm_status adjoint_sweep(acm_forest* f, int nsteps, double dt, int c, double wE,
     return fail(f, ACM_EINVAL, "element count does not match n_blocks*4*Bs^3");
   char* base = reinterpret_cast<char*>(((uintptr_t)ws + 255) & ~(uintptr_t)255);
   auto R = [&](size_t off) { return reinterpret_cast<double*>(base + off); };
+  auto S = [&](size_t off) { return reinterpret_cast<T*>(base + off); };
   double* LAM = R(L.lam);
   double* KAP = R(L.kap);
   double* NU = R(L.nu);
   double* SUM = R(L.sum);
-  double* Y[4] = {R(L.y[0]), R(L.y[1]), R(L.y[2]), R(L.y[3])};
+  T* Y[4] = {S(L.y[0]), S(L.y[1]), S(L.y[2]), S(L.y[3])};
   double* GCHI = R(L.gchi);
   double* WGT = R(L.wgt);
   double* TH = R(L.theta);
-  auto SEG = [&](int k) { return R(L.seg + (size_t)k * L.reg); };
-  auto CKP = [&](int k) { return R(L.ck + (size_t)k * L.reg); };
+  auto SEG = [&](int k) { return S(L.seg + (size_t)k * L.sreg); };
+  auto CKP = [&](int k) { return S(L.ck + (size_t)k * L.sreg); };
   const int Bs = f->gp.Bs;
-  double* U = reinterpret_cast<double*>(f->U);
-  const double* CHI = reinterpret_cast<const double*>(f->CHI);
+  T* U = reinterpret_cast<T*>(f->U);
+  const T* CHI = reinterpret_cast<const T*>(f->CHI);
   const double t0 = f->time;
-  auto copy = [&](const double* src, double* dst) {
-    acm::launch_copy_blocks<double>(Bs, src, dst, f->d_blist, 1, nb, f->st);
+  auto copy = [&](const T* src, T* dst) {
+    acm::launch_copy_blocks<T>(Bs, src, dst, f->d_blist, 1, nb, f->st);
     ++f->launches;
     return cudaGetLastError();
   };
   auto lin = [&](double* out, double a, const double* x, double b, const double* y) {
-    acm::launch_adj_lin(Bs, out, a, x, b, y, f->d_blist, nb, f->st);
+    acm::launch_adj_lin<T>(Bs, out, a, x, b, y, f->d_blist, nb, f->st);
     ++f->launches;
   };
   // nu = J_G(Y)^T kappa (and the mask sensitivity of this stage into gchi)
-  auto jgt = [&](const double* Ys) {
+  auto jgt = [&](const T* Ys) {
     CK(cudaMemsetAsync(NU, 0, L.reg, f->st));
-    acm::launch_adj_jgt(Bs, Ys, KAP, CHI, GCHI, WGT, NU, f->d_blist, f->d_binfo, f->d_nbh, f->d_finer, nb, f->phk,
-                        f->d_err, f->st);
+    acm::launch_adj_jgt<T>(Bs, Ys, KAP, CHI, GCHI, WGT, NU, f->d_blist, f->d_binfo, f->d_nbh, f->d_finer, nb, f->phk,
+                           f->d_err, f->st);
     f->launches += 3;
     return cudaGetLastError() == cudaSuccess ? ACM_OK : fail(f, ACM_ECUDA, "adjoint kernel launch failed");
   };
-  auto objective = [&](const double* Us) {
-    acm::launch_adj_objective(Bs, Us, CHI, LAM, GCHI, f->d_blist, f->d_binfo, nb, f->phk, 1.0 / nsteps, wE, f->st);
+  auto objective = [&](const T* Us) {
+    acm::launch_adj_objective<T>(Bs, Us, CHI, LAM, GCHI, f->d_blist, f->d_binfo, nb, f->phk, 1.0 / nsteps, wE,
+                                 f->st);
     ++f->launches;
   };
   acm_status s;
@@ -1138,9 +1144,9 @@ acm_status adjoint_sweep(acm_forest* f, int nsteps, double dt, int c, double wE,
   CK(copy(U, CKP(0)));
   double J = 0.0;
   for (int k = 1; k <= nsteps; ++k) {
-    if ((s = rk4<double>(f, dt, nullptr))) return s;
+    if ((s = rk4<T>(f, dt, nullptr))) return s;
     double Fx, E;
-    if ((s = force_energy(f, &Fx, &E))) return s;
+    if ((s = force_energy<T>(f, &Fx, &E))) return s;
     J += (Fx + wE * E) / nsteps;
     if (k % c == 0 && k < nsteps) CK(copy(U, CKP(k / c)));
   }
@@ -1153,13 +1159,13 @@ acm_status adjoint_sweep(acm_forest* f, int nsteps, double dt, int c, double wE,
     CK(copy(CKP(a / c), SEG(0)));
     for (int k = a; k < b; ++k) {
       CK(copy(SEG(k - a), U));
-      if ((s = rk4<double>(f, dt, nullptr))) return s;
+      if ((s = rk4<T>(f, dt, nullptr))) return s;
       CK(copy(U, SEG(k - a + 1)));
     }
     if (b == nsteps) objective(SEG(b - a));
     for (int k = b - 1; k >= a; --k) {
       CK(copy(SEG(k - a), U));
-      if ((s = rk4<double>(f, dt, nullptr, Y))) return s;
+      if ((s = rk4<T>(f, dt, nullptr, Y))) return s;
       lin(KAP, dt / 6.0, LAM, 0.0, nullptr);
       if ((s = jgt(Y[3]))) return s;
       lin(SUM, 1.0, NU, 0.0, nullptr);
@@ -1173,12 +1179,12 @@ acm_status adjoint_sweep(acm_forest* f, int nsteps, double dt, int c, double wE,
       if ((s = jgt(Y[0]))) return s;
       lin(SUM, 1.0, SUM, 1.0, NU);
       lin(LAM, 1.0, LAM, 1.0, SUM);
-      acm::launch_adj_fw_T(Bs, LAM, f->d_blist, f->d_nbh, f->d_finer, nb, f->st);
+      acm::launch_adj_fw_T<T>(Bs, LAM, f->d_blist, f->d_nbh, f->d_finer, nb, f->st);
       ++f->launches;
       if (k >= 1) objective(SEG(k - a));
     }
   }
-  acm::launch_adj_theta(Bs, GCHI, f->d_blist, f->d_binfo, nb, f->phk, f->mask, TH, f->st);
+  acm::launch_adj_theta<T>(Bs, GCHI, f->d_blist, f->d_binfo, nb, f->phk, f->mask, TH, f->st);
   ++f->launches;
   CKL();
   CK(cudaMemcpyAsync(dtheta, TH, 4 * sizeof(double), cudaMemcpyDeviceToHost, f->st));
@@ -1191,8 +1197,9 @@ acm_status adjoint_sweep(acm_forest* f, int nsteps, double dt, int c, double wE,
   if ((s = device_error(f))) return s;
   *J_out = J;
   if (dU0) {
-    void* dense = on_device ? dU0 : f->DENSE;
-    acm::launch_gather<double>(Bs, LAM, reinterpret_cast<double*>(dense), f->d_blist, nb, 4, f->st);
+    // FP64 gradient in block order; a host copy goes through the workspace's second register
+    void* dense = on_device ? dU0 : reinterpret_cast<void*>(KAP);
+    acm::launch_adj_gather<T>(Bs, LAM, reinterpret_cast<double*>(dense), f->d_blist, nb, f->st);
     CKL();
     ++f->launches;
     if (!on_device) CK(cudaMemcpyAsync(dU0, dense, (size_t)n_elems * 8, cudaMemcpyDeviceToHost, f->st));
@@ -1206,12 +1213,17 @@ acm_status adjoint_sweep(acm_forest* f, int nsteps, double dt, int c, double wE,
 acm_status adjoint_sphere(acm_forest* f, int nsteps, double dt, int c, double wE, void* ws, size_t ws_bytes,
                           double* J_out, double* dtheta, void* dU0, int64_t n_elems, int on_device) {
   const double t0 = f->time;
-  const acm_status s = adjoint_sweep(f, nsteps, dt, c, wE, ws, ws_bytes, J_out, dtheta, dU0, n_elems, on_device);
+  const acm_status s = DISPATCH(f, adjoint_sweep, f, nsteps, dt, c, wE, ws, ws_bytes, J_out, dtheta, dU0, n_elems,
+                                on_device);
   if (s != ACM_OK && s != ACM_EINVAL && s != ACM_ENOMEM && f->time != t0) {
     const AdjLayout L = adj_layout(f, nsteps, c);
     char* base = reinterpret_cast<char*>(((uintptr_t)ws + 255) & ~(uintptr_t)255);
-    acm::launch_copy_blocks<double>(f->gp.Bs, reinterpret_cast<const double*>(base + L.ck),
-                                    reinterpret_cast<double*>(f->U), f->d_blist, 1, (int64_t)f->order.size(), f->st);
+    if (f->gp.precision == 64)
+      acm::launch_copy_blocks<double>(f->gp.Bs, reinterpret_cast<const double*>(base + L.ck),
+                                      reinterpret_cast<double*>(f->U), f->d_blist, 1, (int64_t)f->order.size(), f->st);
+    else
+      acm::launch_copy_blocks<float>(f->gp.Bs, reinterpret_cast<const float*>(base + L.ck),
+                                     reinterpret_cast<float*>(f->U), f->d_blist, 1, (int64_t)f->order.size(), f->st);
     cudaStreamSynchronize(f->st);
     f->time = t0;
     f->norms_fresh = false;

@@ -197,25 +197,33 @@ template <typename T>
 void launch_scatter(int Bs, const T* dense, T* reg, const int32_t* blist, int64_t n,
                     cudaStream_t st);
 
-// ---- discrete adjoint (adjoint.cu), FP64 registers ------------------------------------------
-// Doubles of the loc^T coefficient scratch for n blocks.
+// ---- discrete adjoint (adjoint.cu): forward state and mask in T, adjoint variables FP64 ------------
+// (FP64 arrays are indexed like registers of T.)  Doubles of the loc^T coefficient scratch.
 size_t adj_weight_doubles(int Bs, int64_t nblocks);
 // nu += W^T E^T loc(E W Y)^T kappa for the blocks 0..n-1 (nu zeroed by the caller); the stage's
 // mask sensitivity is added to gchi.  err |= 8 if a ghost point's source is missing.
-void launch_adj_jgt(int Bs, const double* Y, const double* kap, const double* chi, double* gchi, double* wgt,
-                    double* nu, const int32_t* blist, const int4* binfo, const int32_t* nbh, const uint8_t* finer,
-                    int64_t n, const PhysK& ph, int* err, cudaStream_t st);
+template <typename T>
+void launch_adj_jgt(int Bs, const T* Y, const double* kap, const T* chi, double* gchi, double* wgt, double* nu,
+                    const int32_t* blist, const int4* binfo, const int32_t* nbh, const uint8_t* finer, int64_t n,
+                    const PhysK& ph, int* err, cudaStream_t st);
 // W^T applied to register r in place.
+template <typename T>
 void launch_adj_fw_T(int Bs, double* r, const int32_t* blist, const int32_t* nbh, const uint8_t* finer, int64_t n,
                      cudaStream_t st);
 // out = a x + b y over every element of the listed blocks (y may be null).
+template <typename T>
 void launch_adj_lin(int Bs, double* out, double a, const double* x, double b, const double* y, const int32_t* blist,
                     int64_t n, cudaStream_t st);
 // Direct terms of wN (F_x(U) + wE E(U)) into lam and gchi.
-void launch_adj_objective(int Bs, const double* U, const double* chi, double* lam, double* gchi, const int32_t* blist,
+template <typename T>
+void launch_adj_objective(int Bs, const T* U, const T* chi, double* lam, double* gchi, const int32_t* blist,
                           const int4* binfo, int64_t n, const PhysK& ph, double wN, double wE, cudaStream_t st);
 // out[0..3] += sum gchi d chi / d (centre, radius) for the sphere mask m.
+template <typename T>
 void launch_adj_theta(int Bs, const double* gchi, const int32_t* blist, const int4* binfo, int64_t n, const PhysK& ph,
                       const MaskK& m, double* out, cudaStream_t st);
+// Block-order copy (n, 4, Bs^3) of an FP64 register.
+template <typename T>
+void launch_adj_gather(int Bs, const double* r, double* dense, const int32_t* blist, int64_t n, cudaStream_t st);
 
 }  // namespace acm

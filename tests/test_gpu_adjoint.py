@@ -25,8 +25,8 @@ def A():
     return acm
 
 
-def _gpu_forest(A, S, delta, seed=41, n_target=18):
-    grid = dict(nroot=(2, 1, 1), root_len=1.0, Bs=9, g=4, Jmin=1, Jmax=2, precision=64, max_blocks=256,
+def _gpu_forest(A, S, delta, seed=41, n_target=18, precision=64):
+    grid = dict(nroot=(2, 1, 1), root_len=1.0, Bs=9, g=4, Jmin=1, Jmax=2, precision=precision, max_blocks=256,
                 fd_scheme=1)
     phys = dict(nu=1e-2, c0=3.0, C_eta=1e-2, C_gamma=0.5, C_sp=0.05, u_inf=(1.0, 0.0, 0.0), p_inf=0.0,
                 sponge=1, sponge_L=L, sponge_width=0.2, sponge_delta=delta)
@@ -60,22 +60,33 @@ def _per_point(fo, blocks, Jmax):
     return out
 
 
-def test_adjoint_matches_the_oracle(A):
+DT, N, C = 2e-3, 4, 2
+
+
+@pytest.fixture(scope="module")
+def oracle_gradient():
     S, delta = _setup()
-    dt, N, c = 2e-3, 4, 2
-    f = _gpu_forest(A, S, delta)
-    before = f.read_fields().copy()
-    J, gth, gU = f.adjoint_sphere(N, dt, ckpt_every=c, w_energy=0.1)
-    assert np.array_equal(f.read_fields(), before)
-    adj = FrozenGridAdjoint(S, CENTRE, RADIUS, delta, dt=dt, nsteps=N, checkpoint_every=c)
+    adj = FrozenGridAdjoint(S, CENTRE, RADIUS, delta, dt=DT, nsteps=N, checkpoint_every=C)
     Jo, gUo, gtho = adj.gradient(S.U.copy())
+    return S, delta, Jo, gUo, gtho
+
+
+@pytest.mark.parametrize("prec,tol_J,tol_g", [(64, 1e-12, 1e-10), (32, 1e-5, 1e-4)])
+def test_adjoint_matches_the_oracle(A, oracle_gradient, prec, tol_J, tol_g):
+    """FP64: the same arithmetic up to rounding.  FP32 forward states (the adjoint variables
+    and sums stay FP64): within the FP32 rounding of the states the coefficients come from."""
+    S, delta, Jo, gUo, gtho = oracle_gradient
+    f = _gpu_forest(A, S, delta, precision=prec)
+    before = f.read_fields().copy()
+    J, gth, gU = f.adjoint_sphere(N, DT, ckpt_every=C, w_energy=0.1)
+    assert np.array_equal(f.read_fields(), before)
     fo = S.fo
     go = np.stack([gUo[fo.leaves[l]] for l in fo.sorted_leaves()])
     a, b = _per_point(fo, gU, 2), _per_point(fo, go, 2)
     info = (J, Jo, gth, gtho, [float(np.abs(a[k] - b[k]).max() / np.abs(b).max()) for k in range(4)])
-    assert abs(J - Jo) <= 1e-12 * abs(Jo), info
-    assert np.abs(gth - gtho).max() <= 1e-10 * np.abs(gtho).max(), info
-    assert np.abs(a - b).max() <= 1e-10 * np.abs(b).max(), info
+    assert abs(J - Jo) <= tol_J * abs(Jo), info
+    assert np.abs(gth - gtho).max() <= tol_g * np.abs(gtho).max(), info
+    assert np.abs(a - b).max() <= tol_g * np.abs(b).max(), info
 
 
 def test_adjoint_through_autograd(A):
