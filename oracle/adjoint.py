@@ -212,9 +212,10 @@ def d2_T(w, out, g, M, h, axis):
         _sh_add(out, g, axis, k, M, a * c * w)
 
 
-def rhs_block_vjp(e, g, M, h, ph, kappa, chi=None, chisp=None):
+def rhs_block_vjp(e, g, M, h, ph, kappa, chi=None, chisp=None, us=None, with_us=False):
     """Transposed Jacobian of ``acm.rhs_block`` at the extended state e (4, ne, ne, ne) applied
-    to kappa (4, M+1, M+1, M+1): (d e (4, ne, ne, ne), d chi (M+1,)^3 or None).  u_s = 0."""
+    to kappa (4, M+1, M+1, M+1): (d e (4, ne, ne, ne), d chi (M+1,)^3 or None), and with
+    ``with_us`` also d u_s (3, M+1, M+1, M+1) (the solid velocity us, default 0)."""
     a = acm.d1_coeffs(ph.scheme)
     u = [acm._sh(e[f], g, 0, 0, M) for f in range(4)]
     du = [[acm.d1(e[f], g, M, h, ax, a) for ax in range(3)] for f in range(4)]
@@ -233,8 +234,9 @@ def rhs_block_vjp(e, g, M, h, ph, kappa, chi=None, chisp=None):
         for ax in range(3):
             d2_T(ph.nu * k, de[i], g, M, h, ax)
         if chi is not None:
+            usi = 0.0 if us is None else us[i]
             dint[i] -= chi / ph.C_eta * k
-            dchi -= u[i] / ph.C_eta * k
+            dchi -= (u[i] - usi) / ph.C_eta * k
         if chisp is not None:
             dint[i] -= chisp / ph.C_sp * k
     k = kappa[3]
@@ -245,6 +247,12 @@ def rhs_block_vjp(e, g, M, h, ph, kappa, chi=None, chisp=None):
         dint[3] -= chisp / ph.C_sp * k
     for f in range(4):
         _sh_add(de[f], g, 0, 0, M, dint[f])
+    if with_us:
+        dus = np.zeros((3, M + 1, M + 1, M + 1))
+        if chi is not None:
+            for i in range(3):
+                dus[i] = chi / ph.C_eta * kappa[i]
+        return de, dchi, dus
     return de, dchi
 
 

@@ -27,6 +27,7 @@ import numpy as np
 
 from . import acm
 from .adapt import Solver
+from .adjoint import rhs_block_vjp
 from .sync import sync
 
 
@@ -139,3 +140,188 @@ class MovingSolver(Solver):
             for i in range(3):
                 F[i] += float((chi * (u[i] - self.us[s][i][:M, :M, :M])).sum()) * h3 / self.ph.C_eta
         return F, E
+
+
+# ---- adjoint of the moving case: the gradient with respect to the pitch amplitude ---------------
+
+def box_sdf_grad(P, lo, hi):
+    """Gradient of ``box_sdf`` (..., 3): outside the box the unit vector from the nearest box
+    point, inside the outward normal of the nearest face (undefined on the measure-zero set of
+    points equidistant from several faces or on the box edges)."""
+    c = 0.5 * (np.asarray(lo) + np.asarray(hi))
+    h = 0.5 * (np.asarray(hi) - np.asarray(lo))
+    sgn = np.where(P - c >= 0.0, 1.0, -1.0)
+    q = np.abs(P - c) - h
+    qp = np.maximum(q, 0.0)
+    n = np.sqrt((qp ** 2).sum(axis=-1, keepdims=True))
+    outside = n > 0.0
+    onehot = (q == q.max(axis=-1, keepdims=True)).astype(np.float64)
+    return np.where(outside, qp / np.where(outside, n, 1.0), onehot) * sgn
+
+
+def plate_alpha_derivatives(plate, X, Y, Z, t):
+    """d chi / d alpha_m (...) and d u_s / d alpha_m (3, ...) of ``Plate.fields`` at world points
+    and time t.  alpha = alpha_m cos(w t), so dR/dalpha_m = R_z(phi) R_y'(alpha) cos(w t), and
+    d omega / d alpha_m = -w sin(w t) R_z(phi) e_y."""
+    phi, alpha, _, _ = plate.angles(t)
+    w = 2.0 * math.pi * plate.f
+    ca, sa = math.cos(alpha), math.sin(alpha)
+    dRy = np.array([[-sa, 0.0, ca], [0.0, 0.0, 0.0], [-ca, 0.0, -sa]])
+    dR = rot_z(phi) @ dRy * math.cos(w * t)
+    R = plate.rotation(t)
+    r = np.stack([X - plate.root[0], Y - plate.root[1], Z - plate.root[2]], axis=-1)
+    xb = r @ R
+    dxb = r @ dR
+    d = box_sdf(xb, plate.lo, plate.hi)
+    dchi_dd = -0.5 / plate.delta * (1.0 - np.tanh(d / plate.delta) ** 2)
+    dchi = dchi_dd * (box_sdf_grad(xb, plate.lo, plate.hi) * dxb).sum(axis=-1)
+    domega = -w * math.sin(w * t) * (rot_z(phi) @ np.array([0.0, 1.0, 0.0]))
+    dus = np.moveaxis(np.cross(domega, r), -1, 0)
+    return dchi, dus
+
+
+class MovingPlateAdjoint:
+    """Gradient of J = (1/N) sum_{n=1..N} [F_x(U_n, t_n) + w E(U_n)] for N fixed-dt RK4 steps of a
+    ``MovingSolver`` on its frozen grid, with respect to the initial state and the pitch
+    amplitude alpha_m.  F_x integrates chi (u - u_s) at the step's time.  The forward step is
+    the solver's (mask and solid velocity at each stage time); the adjoint step is that of
+    ``oracle.adjoint`` with the stage's mask and solid velocity, whose sensitivities are turned
+    into d/d alpha_m with ``plate_alpha_derivatives`` at the stage time."""
+
+    def __init__(self, solver, dt, nsteps, checkpoint_every=10, w_energy=0.1):
+        from .adjoint import G_RHS, SyncMatrices
+        self.S = solver
+        self.fo = solver.fo
+        self.ph = solver.ph
+        self.dt, self.N, self.c, self.we = dt, nsteps, checkpoint_every, w_energy
+        self.g = G_RHS
+        self.mats = SyncMatrices(self.fo)
+        M = self.fo.M
+        self.half = np.zeros((M + 1,) * 3)
+        self.half[:M, :M, :M] = 1.0
+        self.t0 = solver.t
+
+    def _fields(self, t):
+        chi, us = {}, {}
+        for leaf, s in self.fo.leaves.items():
+            X, Y, Z = acm.block_coords(self.fo, leaf)
+            chi[s], us[s] = self.S.plate.fields(X, Y, Z, t)
+        return chi, us
+
+    def _step(self, U, t):
+        """The solver's step from (U, t): (U', [ext_s], [(chi_s, us_s)], [t_s])."""
+        dt = self.dt
+        V = U.copy()
+        Ks, exts, fields, times = [], [], [], []
+        for st, ts in enumerate((t, t + 0.5 * dt, t + 0.5 * dt, t + dt)):
+            Y = V if st == 0 else V + (dt if st == 3 else 0.5 * dt) * Ks[-1]
+            chi, us = self._fields(ts)
+            ext = sync(self.fo, Y, self.g, "faces")
+            K = np.zeros_like(Y)
+            for leaf, s in self.fo.leaves.items():
+                K[s] = acm.rhs_block(ext[s], self.g, self.fo.M, self.fo.h(leaf[0]), self.ph, chi=chi[s],
+                                     us=us[s], chisp=self.S.chisp.get(s))
+            Ks.append(K)
+            exts.append(ext)
+            fields.append((chi, us))
+            times.append(ts)
+        return V + dt / 6.0 * (Ks[0] + 2.0 * Ks[1] + 2.0 * Ks[2] + Ks[3]), exts, fields, times
+
+    def _objective_terms(self, U, t):
+        chi, us = self._fields(t)
+        F = E = 0.0
+        for leaf, s in self.fo.leaves.items():
+            h3 = self.fo.h(leaf[0]) ** 3
+            u = U[s]
+            E += 0.5 * float(((u[0] ** 2 + u[1] ** 2 + u[2] ** 2) * self.half).sum()) * h3
+            F += float((chi[s] * (u[0] - us[s][0]) * self.half).sum()) * h3 / self.ph.C_eta
+        return F, E
+
+    def _alpha_from(self, gchi, gus, t):
+        """sum over blocks of <gchi, d chi/d alpha_m> + <gus, d u_s/d alpha_m> at time t."""
+        out = 0.0
+        for leaf, s in self.fo.leaves.items():
+            X, Y, Z = acm.block_coords(self.fo, leaf)
+            dchi, dus = plate_alpha_derivatives(self.S.plate, X, Y, Z, t)
+            out += float((gchi[s] * dchi).sum()) + float((gus[s] * dus).sum())
+        return out
+
+    def _direct(self, U, t, lam):
+        """Direct terms of (1/N)(F_x + w E) at (U, t): into lam; returns their d/d alpha_m."""
+        chi, us = self._fields(t)
+        wN = 1.0 / self.N
+        gchi, gus = {}, {}
+        for leaf, s in self.fo.leaves.items():
+            h3 = self.fo.h(leaf[0]) ** 3
+            u = U[s]
+            lam[s, 0] += wN * (chi[s] / self.ph.C_eta + self.we * u[0]) * self.half * h3
+            lam[s, 1] += wN * self.we * u[1] * self.half * h3
+            lam[s, 2] += wN * self.we * u[2] * self.half * h3
+            gchi[s] = wN * (u[0] - us[s][0]) * self.half * h3 / self.ph.C_eta
+            gus[s] = np.zeros((3,) + u[0].shape)
+            gus[s][0] = -wN * chi[s] * self.half * h3 / self.ph.C_eta
+        return self._alpha_from(gchi, gus, t)
+
+    def _G_T(self, ext, kappa, chi, us):
+        """(J_G^T kappa in the register layout, d/d alpha_m contribution is returned by the caller
+        from the mask and solid-velocity sensitivities (gchi, gus))."""
+        m = self.mats
+        M, g = self.fo.M, self.g
+        de = np.zeros((4, m.nb, m.ne, m.ne, m.ne))
+        gchi, gus = {}, {}
+        for leaf, s in self.fo.leaves.items():
+            e = np.nan_to_num(ext[s], nan=0.0)
+            d, dc, du = rhs_block_vjp(e, g, M, self.fo.h(leaf[0]), self.ph, kappa[s], chi=chi[s],
+                                      chisp=self.S.chisp.get(s), us=us[s], with_us=True)
+            de[:, m.pos[s]] = d
+            gchi[s], gus[s] = dc, du
+        flat = de.reshape(4, -1)
+        v = np.stack([m.S.T @ flat[f] for f in range(4)])
+        return m.to_reg(v, np.zeros_like(kappa)), gchi, gus
+
+    def _step_adjoint(self, U, t, lam):
+        """lam = dJ/dU' -> (dJ/dU, d/d alpha_m through this step)."""
+        dt = self.dt
+        _, exts, fields, times = self._step(U, t)
+        ga = 0.0
+        kap = dt / 6.0 * lam
+        nus = []
+        for st, coef in ((3, None), (2, dt), (1, 0.5 * dt), (0, 0.5 * dt)):
+            if st < 3:
+                base = (dt / 3.0 if st > 0 else dt / 6.0) * lam
+                kap = base + coef * nus[-1]
+            nu, gchi, gus = self._G_T(exts[st], kap, *fields[st])
+            ga += self._alpha_from(gchi, gus, times[st])
+            nus.append(nu)
+        m = self.mats
+        tot = m.to_vec(lam + nus[0] + nus[1] + nus[2] + nus[3])
+        v = np.stack([m.W.T @ tot[f] for f in range(4)])
+        return m.to_reg(v, np.zeros_like(lam)), ga
+
+    def gradient(self, U0):
+        """(J, dJ/dU_0 in the register layout, dJ/d alpha_m)."""
+        dt, N, c = self.dt, self.N, self.c
+        U = U0.copy()
+        ckpt = {0: U.copy()}
+        J = 0.0
+        for n in range(1, N + 1):
+            U = self._step(U, self.t0 + (n - 1) * dt)[0]
+            F, E = self._objective_terms(U, self.t0 + n * dt)
+            J += (F + self.we * E) / N
+            if n % c == 0 and n < N:
+                ckpt[n] = U.copy()
+        lam = np.zeros_like(U0)
+        ga = 0.0
+        starts = sorted(ckpt)
+        for a, b in reversed(list(zip(starts, starts[1:] + [N]))):
+            states = [ckpt[a]]
+            for k in range(a, b):
+                states.append(self._step(states[-1], self.t0 + k * dt)[0])
+            if b == N:
+                ga += self._direct(states[-1], self.t0 + N * dt, lam)
+            for n in range(b - 1, a - 1, -1):
+                lam, g_step = self._step_adjoint(states[n - a], self.t0 + n * dt, lam)
+                ga += g_step
+                if n >= 1:
+                    ga += self._direct(states[n - a], self.t0 + n * dt, lam)
+        return J, lam, ga
