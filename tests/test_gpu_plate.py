@@ -32,7 +32,7 @@ DT, NSTEPS = 2e-3, 3
 
 @pytest.fixture(scope="module")
 def oracle_run():
-    fo = oracle_forest(GRID, J=2)
+    fo = oracle_forest(GRID, J=2, max_blocks=256)
     S = MovingSolver(fo, oacm.Physics(nu=1e-2, c0=5.0, C_eta=1e-2, C_gamma=0.5), Plate(**PLATE),
                      ic=lambda X, Y, Z: oacm.ic_taylor_green(X, Y, Z))
     S.eval_ic()
