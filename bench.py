@@ -541,14 +541,6 @@ def main():
         batched = batched_comparison(A, args.precision) if rank == 0 and not args.no_batched else None
         cdf44 = (wavelet_comparison(A, stream, args.precision, args.Jmax, args.max_blocks)
                  if rank == 0 and not args.no_cdf44 and args.wavelet == 40 else None)
-        adjoint = None
-        if rank == 0 and not args.no_adjoint:
-            # a side measurement: an error here is reported under its key, not raised
-            try:
-                adjoint = adjoint_measurement(A, stream)
-            except Exception as e:  # noqa: BLE001
-                adjoint = {"error": f"{type(e).__name__}: {e}"}
-
         cpu = None
         if rank == 0 and world == 1 and not args.no_cpu_baseline:
             # bounded sample (10-30 s of one core): the same workload with levels 2..4, its grid
@@ -568,6 +560,14 @@ def main():
                    "sample": f"one FP64 oracle RHS evaluation (ghost sync + RHS) over the same workload at "
                              f"levels {g4['Jmin']}..{g4['Jmax']} after refinement, {nb} blocks x 17^3, "
                              f"{secs:.1f} s"}
+
+        # the last GPU work of the run: a side measurement whose errors are reported, not raised
+        adjoint = None
+        if rank == 0 and not args.no_adjoint:
+            try:
+                adjoint = adjoint_measurement(A, stream)
+            except Exception as e:  # noqa: BLE001
+                adjoint = {"error": f"{type(e).__name__}: {e}"}
 
     if rank == 0:
         line = {
@@ -595,7 +595,12 @@ def main():
             "clocks": clk,
         }
         print(json.dumps(line), flush=True)
-    f.close()
+    try:
+        f.close()
+    except Exception as e:  # noqa: BLE001
+        # reported, not raised: the line above is complete; a failed side measurement (listed
+        # under its key) may have left the device in an error state
+        print(f"bench: forest close failed after the measurements: {e}", file=sys.stderr)
     if dist is not None:
         dist.destroy_process_group()
     return 0
