@@ -234,6 +234,15 @@ acm_status acm_adjoint_sphere(acm_forest* f, int nsteps, double dt, int ckpt_eve
                               size_t ws_bytes, double* J, double* dJ_dtheta, void* dJ_dU0, int64_t n_elems,
                               int on_device);
 
+/* The same for the moving plate (ACM_MASK_PLATE; ACM_EINVAL otherwise), from the forest's time:
+ * the mask and the solid velocity follow the RK4 stage times, F_x integrates chi (u - u_s), and
+ * *dJ_dalpha (host) receives the derivative with respect to the pitch amplitude alpha_m (the
+ * plate's drag sensitivity of the full-scale configuration).  Workspace as acm_adjoint_bytes.
+ * Not yet run on a GPU. */
+acm_status acm_adjoint_plate_pitch(acm_forest* f, int nsteps, double dt, int ckpt_every, double w_energy, void* ws,
+                                   size_t ws_bytes, double* J, double* dJ_dalpha, void* dJ_dU0, int64_t n_elems,
+                                   int on_device);
+
 /* Right-hand side K = F(U) of eqs. (u_eqn-1, p_eqn-1) at every point of every block, after
  * the same synchronisation as an RK4 stage, written in block order (fields layout) to out
  * (device pointer if on_device, else host; n_elems = n_blocks*4*Bs^3).  For checks: the

@@ -63,6 +63,9 @@ EXPORTS = {
     "acm_adjoint_bytes": (C.c_size_t, [C.c_void_p, C.c_int, C.c_int]),
     "acm_adjoint_sphere": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_int, C.c_double, C.c_void_p, C.c_size_t,
                                      C.POINTER(C.c_double), C.c_void_p, C.c_void_p, C.c_int64, C.c_int]),
+    "acm_adjoint_plate_pitch": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_int, C.c_double, C.c_void_p,
+                                          C.c_size_t, C.POINTER(C.c_double), C.c_void_p, C.c_void_p, C.c_int64,
+                                          C.c_int]),
     "acm_rk4_steps_batch": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_int, C.c_double, C.c_int,
                                       C.POINTER(C.c_double), C.POINTER(C.c_int)]),
     "acm_refine_all": (C.c_int, [C.c_void_p]),
@@ -271,6 +274,21 @@ class Forest:
                                               C.c_void_p(ws.data_ptr()), nbytes, C.byref(J), _ptr(th), _ptr(g),
                                               g.size, 0))
         return J.value, th, g
+
+    def adjoint_plate_pitch(self, nsteps, dt, ckpt_every=10, w_energy=0.1):
+        """As adjoint_sphere for the moving plate, from the forest's time: returns (J, dJ/d alpha_m,
+        dJ/dU_0)."""
+        import torch
+        nbytes = int(self.L.acm_adjoint_bytes(self.h, int(nsteps), int(ckpt_every)))
+        ws = torch.empty(nbytes, dtype=torch.uint8, device=self.pool.device)
+        n = self.n_blocks()
+        g = np.empty((n, 4, self.Bs, self.Bs, self.Bs), dtype=np.float64)
+        J = C.c_double()
+        da = np.zeros(1)
+        self._check(self.L.acm_adjoint_plate_pitch(self.h, int(nsteps), float(dt), int(ckpt_every), float(w_energy),
+                                                   C.c_void_p(ws.data_ptr()), nbytes, C.byref(J), _ptr(da),
+                                                   _ptr(g), g.size, 0))
+        return J.value, float(da[0]), g
 
     def rhs(self):
         n = self.n_blocks()

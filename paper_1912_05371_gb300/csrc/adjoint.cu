@@ -58,6 +58,61 @@ __device__ __forceinline__ double yval(const T* Y, const int* nbh, size_t own, i
   return (double)point_value<T, BS>(Y, nbh, x, y, z, f);
 }
 
+// Moving rigid box (mask kind 2) at offset r = x - x_0 from its pivot: the solid velocity
+// u_s = omega x r, its derivative d u_s/dtheta = (d omega/dtheta) x r, and d chi/dtheta through
+// the body coordinates x_b = R^T r (d x_b/dtheta = dR^T r) and the gradient of the box's signed
+// distance (outside: from the nearest box point; inside: the nearest face's normal).
+struct BoxPoint {
+  double us[3], dus[3], dchi;
+};
+__device__ __forceinline__ BoxPoint box_point(const MaskK& m, double rx, double ry, double rz) {
+  BoxPoint o;
+  const double* w = m.p + 19;
+  const double* dw = m.p + 33;
+  o.us[0] = w[1] * rz - w[2] * ry;
+  o.us[1] = w[2] * rx - w[0] * rz;
+  o.us[2] = w[0] * ry - w[1] * rx;
+  o.dus[0] = dw[1] * rz - dw[2] * ry;
+  o.dus[1] = dw[2] * rx - dw[0] * rz;
+  o.dus[2] = dw[0] * ry - dw[1] * rx;
+  double q[3], sg[3], dxb[3], n2 = 0.0, qmax = -1e300;
+  int kmax = 0;
+  for (int k = 0; k < 3; ++k) {
+    const double xb = m.p[k] * rx + m.p[3 + k] * ry + m.p[6 + k] * rz;
+    dxb[k] = m.p[24 + k] * rx + m.p[27 + k] * ry + m.p[30 + k] * rz;
+    const double dv = xb - m.p[12 + k];
+    sg[k] = dv >= 0.0 ? 1.0 : -1.0;
+    q[k] = fabs(dv) - m.p[15 + k];
+    if (q[k] > 0.0) n2 += q[k] * q[k];
+    if (q[k] > qmax) { qmax = q[k]; kmax = k; }
+  }
+  const double nout = sqrt(n2);
+  double gd = 0.0;                                     // grad d . d x_b / dtheta
+  if (nout > 0.0) {
+    for (int k = 0; k < 3; ++k)
+      if (q[k] > 0.0) gd += q[k] / nout * sg[k] * dxb[k];
+  } else {
+    gd = sg[kmax] * dxb[kmax];
+  }
+  const double d = nout + (qmax < 0.0 ? qmax : 0.0);
+  const double th = tanh(d / m.p[18]);
+  o.dchi = -0.5 / m.p[18] * (1.0 - th * th) * gd;
+  return o;
+}
+
+// Block reduction of one double per thread into *out (one atomic per CTA).
+__device__ __forceinline__ void block_add(double v, double* out) {
+  __shared__ double red[kNA / 32];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int k = 0; k < kNA / 32; ++k) t += red[k];
+    atomicAdd(out, t);
+  }
+}
+
 // Coefficients of loc^T at each interior point p of block `rank` (kappa: the adjoint stage
 // variable, Y: the synchronised stage state):
 //   [3i + j]  A_ij = -u_j kappa_i      (i, j < 3; weight of D1_j applied to field i)
@@ -67,10 +122,13 @@ __device__ __forceinline__ double yval(const T* Y, const int* nbh, size_t own, i
 //   [16 + j]  pointwise term of field j: -sum_i kappa_i D1_j u_i - (chi/C_eta + chi_sp/C_sp) kappa_j,
 //             and for p: -(C_gamma + chi_sp/C_sp) kappa_p
 // The mask sensitivity -sum_i kappa_i u_i / C_eta is added to gchi.
+// With a moving box (m.kind == 2) the mask's and the solid velocity's sensitivities are turned into
+// d/dtheta at once (the pose is the stage's) and summed into *dtheta instead of gchi.
 template <typename T, int BS>
 __global__ void __launch_bounds__(kNA) k_adj_weights(const T* Y, const double* kap, const T* chi,
                                                      double* gchi, double* wgt, const int32_t* blist,
-                                                     const int4* binfo, const int32_t* nbh_all, const PhysK ph) {
+                                                     const int4* binfo, const int32_t* nbh_all, const PhysK ph,
+                                                     const MaskK m, double* dtheta) {
   using L = Lay<T, BS>;
   constexpr int M = L::M, N3 = BS * BS * BS;
   __shared__ int nbh[kNbhStride];
@@ -83,6 +141,8 @@ __global__ void __launch_bounds__(kNA) k_adj_weights(const T* Y, const double* k
   const double a[3] = {ph.a1, ph.a2, ph.a3};
   const size_t own = (size_t)slot * L::BLK;
   double* w = wgt + (size_t)rank * kNW * N3;
+  const bool moving = m.kind == 2;
+  double dth = 0.0;
   for (int t = threadIdx.x; t < N3; t += kNA) {
     const int x = t % BS, y = (t / BS) % BS, z = t / (BS * BS);
     const int pi = L::idx(x, y, z);
@@ -114,8 +174,21 @@ __global__ void __launch_bounds__(kNA) k_adj_weights(const T* Y, const double* k
       w[(size_t)(16 + j) * N3 + t] = s - (c * ph.inv_ceta + cs * ph.inv_csp) * k[j];
     }
     w[(size_t)19 * N3 + t] = -(ph.cgamma + cs * ph.inv_csp) * k[3];
-    if (ph.mask) gchi[(size_t)slot * L::FS + pi] -= (k[0] * u[0] + k[1] * u[1] + k[2] * u[2]) * ph.inv_ceta;
+    if (moving) {
+      const BoxPoint bp = box_point(m, lattice_coord(ph, bi, 0, x, M, h) - m.p[9],
+                                    lattice_coord(ph, bi, 1, y, M, h) - m.p[10],
+                                    lattice_coord(ph, bi, 2, z, M, h) - m.p[11]);
+      double gc = 0.0, gu = 0.0;
+      for (int i = 0; i < 3; ++i) {
+        gc -= k[i] * (u[i] - bp.us[i]) * ph.inv_ceta;      // d/dchi of -chi (u - u_s) / C_eta
+        gu += c * k[i] * ph.inv_ceta * bp.dus[i];          // d/du_s, times d u_s / dtheta
+      }
+      dth += gc * bp.dchi + gu;
+    } else if (ph.mask) {
+      gchi[(size_t)slot * L::FS + pi] -= (k[0] * u[0] + k[1] * u[1] + k[2] * u[2]) * ph.inv_ceta;
+    }
   }
+  if (moving) block_add(dth, dtheta);
 }
 
 // loc^T and E^T: for every point q of block `rank`'s extended region (interior and the six face
@@ -273,24 +346,38 @@ __global__ void __launch_bounds__(kNA) k_adj_lin(double* out, double a, const do
 
 // Direct terms of (1/N) [F_x(U) + w_E E(U)] (Sec. 2.2, half-open points, weight h^3): into lam
 // and, for the mask, into gchi.
+// With a moving box the force integrates chi (u - u_s) at the state's time (pose in m): the direct
+// d/dtheta of the force is summed into *dtheta.
 template <typename T, int BS>
 __global__ void __launch_bounds__(kNA) k_adj_objective(const T* U, const T* chi, double* lam, double* gchi,
                                                        const int32_t* blist, const int4* binfo, const PhysK ph,
-                                                       double wN, double wE) {
+                                                       double wN, double wE, const MaskK m, double* dtheta) {
   using L = Lay<T, BS>;
   constexpr int M = L::M;
   const int slot = blist[blockIdx.x];
-  const double h = ph.h[binfo[blockIdx.x].x], h3 = h * h * h;
+  const int4 bi = binfo[blockIdx.x];
+  const double h = ph.h[bi.x], h3 = h * h * h;
   const size_t own = (size_t)slot * L::BLK;
+  const bool moving = m.kind == 2;
+  double dth = 0.0;
   for (int t = threadIdx.x; t < M * M * M; t += kNA) {
-    const int pi = L::idx(t % M, (t / M) % M, t / (M * M));
+    const int x = t % M, y = (t / M) % M, z = t / (M * M);
+    const int pi = L::idx(x, y, z);
     const double u = (double)U[own + pi];
     const double c = ph.mask ? (double)chi[(size_t)slot * L::FS + pi] : 0.0;
     lam[own + pi] += wN * (c * ph.inv_ceta + wE * u) * h3;
     for (int f = 1; f < 3; ++f)
       lam[own + (size_t)f * L::FS + pi] += wN * wE * (double)U[own + (size_t)f * L::FS + pi] * h3;
-    if (ph.mask) gchi[(size_t)slot * L::FS + pi] += wN * u * h3 * ph.inv_ceta;
+    if (moving) {
+      const BoxPoint bp = box_point(m, lattice_coord(ph, bi, 0, x, M, h) - m.p[9],
+                                    lattice_coord(ph, bi, 1, y, M, h) - m.p[10],
+                                    lattice_coord(ph, bi, 2, z, M, h) - m.p[11]);
+      dth += wN * h3 * ph.inv_ceta * ((u - bp.us[0]) * bp.dchi - c * bp.dus[0]);
+    } else if (ph.mask) {
+      gchi[(size_t)slot * L::FS + pi] += wN * u * h3 * ph.inv_ceta;
+    }
   }
+  if (moving) block_add(dth, dtheta);
 }
 
 // sum over all points of gchi * d chi / d (cx, cy, cz, R) for the sphere mask
@@ -361,9 +448,9 @@ size_t adj_weight_doubles(int Bs, int64_t nblocks) { return (size_t)kNW * Bs * B
 template <typename T>
 void launch_adj_jgt(int Bs, const T* Y, const double* kap, const T* chi, double* gchi, double* wgt, double* nu,
                     const int32_t* blist, const int4* binfo, const int32_t* nbh, const uint8_t* finer, int64_t n,
-                    const PhysK& ph, int* err, cudaStream_t st) {
+                    const PhysK& ph, const MaskK& m, double* dtheta, int* err, cudaStream_t st) {
   if (n <= 0) return;
-  ACM_ADJ_BS(Bs, k_adj_weights, <<<g1(n), kNA, 0, st>>>(Y, kap, chi, gchi, wgt, blist, binfo, nbh, ph));
+  ACM_ADJ_BS(Bs, k_adj_weights, <<<g1(n), kNA, 0, st>>>(Y, kap, chi, gchi, wgt, blist, binfo, nbh, ph, m, dtheta));
   ACM_ADJ_BS(Bs, k_adj_scatter, <<<g1(n), kNA, 0, st>>>(wgt, nu, blist, binfo, nbh, ph, err));
   ACM_ADJ_BS(Bs, k_adj_fw_T, <<<g1(n), kNA, 0, st>>>(nu, blist, nbh, finer));
 }
@@ -384,9 +471,10 @@ void launch_adj_lin(int Bs, double* out, double a, const double* x, double b, co
 
 template <typename T>
 void launch_adj_objective(int Bs, const T* U, const T* chi, double* lam, double* gchi, const int32_t* blist,
-                          const int4* binfo, int64_t n, const PhysK& ph, double wN, double wE, cudaStream_t st) {
+                          const int4* binfo, int64_t n, const PhysK& ph, double wN, double wE, const MaskK& m,
+                          double* dtheta, cudaStream_t st) {
   if (n <= 0) return;
-  ACM_ADJ_BS(Bs, k_adj_objective, <<<g1(n), kNA, 0, st>>>(U, chi, lam, gchi, blist, binfo, ph, wN, wE));
+  ACM_ADJ_BS(Bs, k_adj_objective, <<<g1(n), kNA, 0, st>>>(U, chi, lam, gchi, blist, binfo, ph, wN, wE, m, dtheta));
 }
 
 template <typename T>
@@ -404,12 +492,13 @@ void launch_adj_gather(int Bs, const double* r, double* dense, const int32_t* bl
 
 #define ACM_ADJ_INST(T)                                                                                        \
   template void launch_adj_jgt<T>(int, const T*, const double*, const T*, double*, double*, double*, const int32_t*, \
-                                  const int4*, const int32_t*, const uint8_t*, int64_t, const PhysK&, int*, cudaStream_t); \
+                                  const int4*, const int32_t*, const uint8_t*, int64_t, const PhysK&, const MaskK&, \
+                                  double*, int*, cudaStream_t);                                              \
   template void launch_adj_fw_T<T>(int, double*, const int32_t*, const int32_t*, const uint8_t*, int64_t, cudaStream_t); \
   template void launch_adj_lin<T>(int, double*, double, const double*, double, const double*, const int32_t*, int64_t, \
                                   cudaStream_t);                                                              \
   template void launch_adj_objective<T>(int, const T*, const T*, double*, double*, const int32_t*, const int4*, int64_t, \
-                                        const PhysK&, double, double, cudaStream_t);                          \
+                                        const PhysK&, double, double, const MaskK&, double*, cudaStream_t);  \
   template void launch_adj_theta<T>(int, const double*, const int32_t*, const int4*, int64_t, const PhysK&,   \
                                     const MaskK&, double*, cudaStream_t);                                     \
   template void launch_adj_gather<T>(int, const double*, double*, const int32_t*, int64_t, cudaStream_t);

@@ -435,6 +435,21 @@ void plate_pose(acm_forest* f, double t) {
   m.p[20] = dalpha * cp;
   m.p[21] = dphi;
   m.p[22] = std::sqrt(0.25 * q[0] * q[0] + q[1] * q[1] + 0.25 * q[2] * q[2]);
+  // derivatives with respect to the pitch amplitude alpha_m (alpha = alpha_m cos(w t)):
+  // dR = R_z(phi) dR_y/dalpha cos(w t), d omega = -w sin(w t) R_z(phi) e_y
+  const double cw = std::cos(w * t);
+  const double dRy[9] = {-sa, 0.0, ca, 0.0, 0.0, 0.0, -ca, 0.0, -sa};
+  const double Rz[9] = {cp, -sp, 0.0, sp, cp, 0.0, 0.0, 0.0, 1.0};
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      double v = 0.0;
+      for (int k = 0; k < 3; ++k) v += Rz[3 * i + k] * dRy[3 * k + j];
+      m.p[24 + 3 * i + j] = v * cw;
+    }
+  const double dw = -w * std::sin(w * t);
+  m.p[33] = -dw * sp;
+  m.p[34] = dw * cp;
+  m.p[35] = 0.0;
 }
 
 // Mask on every block, or only on the blocks whose slots are in `fresh` (new blocks).
@@ -1086,13 +1101,28 @@ acm_status force_energy(acm_forest* f, double* Fx, double* E) {
     *Fx += part[4 * r] * h3 / f->pp.C_eta;
     *E += 0.5 * part[4 * r + 3] * h3;
   }
+  if (f->moving) {
+    // a moving body's force integrates chi (u - u_s) (pose and mask at the state's time)
+    acm::launch_solid_moment<T>(f->gp.Bs, reinterpret_cast<const T*>(f->CHI), f->d_blist, f->d_binfo, (int64_t)n,
+                                f->phk, f->mask, f->d_diag, f->st);
+    CKL();
+    ++f->launches;
+    CK(cudaMemcpyAsync(part.data(), f->d_diag, n * 4 * 8, cudaMemcpyDeviceToHost, f->st));
+    CK(cudaStreamSynchronize(f->st));
+    for (size_t r = 0; r < n; ++r) {
+      const double h = h_of(f, f->order[r].J);
+      *Fx -= part[4 * r] * h * h * h / f->pp.C_eta;
+    }
+  }
   return ACM_OK;
 }
 
 template <typename T>
 acm_status adjoint_sweep(acm_forest* f, int nsteps, double dt, int c, double wE, void* ws, size_t ws_bytes,
                          double* J_out, double* dtheta, void* dU0, int64_t n_elems, int on_device) {
-  if (!f->mask_on || f->mask.kind != 1) return fail(f, ACM_EINVAL, "the adjoint needs the sphere mask");
+  // the sphere's centre and radius (static mask), or the moving plate's pitch amplitude
+  const bool plate = f->moving;
+  if (!f->mask_on || (!plate && f->mask.kind != 1)) return fail(f, ACM_EINVAL, "the adjoint needs a sphere or plate mask");
   if (nsteps < 1 || c < 1 || !(dt > 0) || !ws || !J_out || !dtheta) return fail(f, ACM_EINVAL, "bad arguments");
   if (f->order.empty()) return fail(f, ACM_EINVAL, "empty forest");
   const AdjLayout L = adj_layout(f, nsteps, c);
@@ -1126,17 +1156,27 @@ acm_status adjoint_sweep(acm_forest* f, int nsteps, double dt, int c, double wE,
     acm::launch_adj_lin<T>(Bs, out, a, x, b, y, f->d_blist, nb, f->st);
     ++f->launches;
   };
-  // nu = J_G(Y)^T kappa (and the mask sensitivity of this stage into gchi)
-  auto jgt = [&](const T* Ys) {
+  // the moving plate's pose and mask at time t (a static mask needs nothing)
+  auto pose_at = [&](double t) {
+    if (!plate) return;
+    plate_pose(f, t);
+    acm::launch_mask<T>(Bs, reinterpret_cast<T*>(f->CHI), f->d_blist, nullptr, nb, f->d_binfo, f->phk, f->mask, f->st);
+    ++f->launches;
+  };
+  // nu = J_G(Y)^T kappa (and the mask sensitivity of this stage into gchi, or for the plate
+  // straight into its parameter's sum)
+  auto jgt = [&](const T* Ys, double ts) {
+    pose_at(ts);
     CK(cudaMemsetAsync(NU, 0, L.reg, f->st));
     acm::launch_adj_jgt<T>(Bs, Ys, KAP, CHI, GCHI, WGT, NU, f->d_blist, f->d_binfo, f->d_nbh, f->d_finer, nb, f->phk,
-                           f->d_err, f->st);
+                           f->mask, TH, f->d_err, f->st);
     f->launches += 3;
     return cudaGetLastError() == cudaSuccess ? ACM_OK : fail(f, ACM_ECUDA, "adjoint kernel launch failed");
   };
-  auto objective = [&](const T* Us) {
+  auto objective = [&](const T* Us, double tn) {
+    pose_at(tn);
     acm::launch_adj_objective<T>(Bs, Us, CHI, LAM, GCHI, f->d_blist, f->d_binfo, nb, f->phk, 1.0 / nsteps, wE,
-                                 f->st);
+                                 f->mask, TH, f->st);
     ++f->launches;
   };
   acm_status s;
@@ -1159,39 +1199,47 @@ acm_status adjoint_sweep(acm_forest* f, int nsteps, double dt, int c, double wE,
     CK(copy(CKP(a / c), SEG(0)));
     for (int k = a; k < b; ++k) {
       CK(copy(SEG(k - a), U));
+      f->time = t0 + k * dt;                       // a moving mask follows the step's clock
       if ((s = rk4<T>(f, dt, nullptr))) return s;
       CK(copy(U, SEG(k - a + 1)));
     }
-    if (b == nsteps) objective(SEG(b - a));
+    if (b == nsteps) objective(SEG(b - a), t0 + b * dt);
     for (int k = b - 1; k >= a; --k) {
+      const double tk = t0 + k * dt;
       CK(copy(SEG(k - a), U));
+      f->time = tk;
       if ((s = rk4<T>(f, dt, nullptr, Y))) return s;
       lin(KAP, dt / 6.0, LAM, 0.0, nullptr);
-      if ((s = jgt(Y[3]))) return s;
+      if ((s = jgt(Y[3], tk + dt))) return s;
       lin(SUM, 1.0, NU, 0.0, nullptr);
       lin(KAP, dt / 3.0, LAM, dt, NU);
-      if ((s = jgt(Y[2]))) return s;
+      if ((s = jgt(Y[2], tk + 0.5 * dt))) return s;
       lin(SUM, 1.0, SUM, 1.0, NU);
       lin(KAP, dt / 3.0, LAM, dt / 2.0, NU);
-      if ((s = jgt(Y[1]))) return s;
+      if ((s = jgt(Y[1], tk + 0.5 * dt))) return s;
       lin(SUM, 1.0, SUM, 1.0, NU);
       lin(KAP, dt / 6.0, LAM, dt / 2.0, NU);
-      if ((s = jgt(Y[0]))) return s;
+      if ((s = jgt(Y[0], tk))) return s;
       lin(SUM, 1.0, SUM, 1.0, NU);
       lin(LAM, 1.0, LAM, 1.0, SUM);
       acm::launch_adj_fw_T<T>(Bs, LAM, f->d_blist, f->d_nbh, f->d_finer, nb, f->st);
       ++f->launches;
-      if (k >= 1) objective(SEG(k - a));
+      if (k >= 1) objective(SEG(k - a), tk);
     }
   }
-  acm::launch_adj_theta<T>(Bs, GCHI, f->d_blist, f->d_binfo, nb, f->phk, f->mask, TH, f->st);
-  ++f->launches;
+  if (!plate) {
+    acm::launch_adj_theta<T>(Bs, GCHI, f->d_blist, f->d_binfo, nb, f->phk, f->mask, TH, f->st);
+    ++f->launches;
+  }
   CKL();
-  CK(cudaMemcpyAsync(dtheta, TH, 4 * sizeof(double), cudaMemcpyDeviceToHost, f->st));
-  // the forest keeps its state and time
+  CK(cudaMemcpyAsync(dtheta, TH, (plate ? 1 : 4) * sizeof(double), cudaMemcpyDeviceToHost, f->st));
+  // the forest keeps its state, time and mask
   CK(copy(CKP(0), U));
   f->time = t0;
   f->norms_fresh = false;
+  if (plate) {
+    if ((s = eval_mask<T>(f))) return s;
+  }
   CK(cudaMemcpyAsync(f->h_err, f->d_err, sizeof(int), cudaMemcpyDeviceToHost, f->st));
   CK(cudaStreamSynchronize(f->st));
   if ((s = device_error(f))) return s;
@@ -1227,6 +1275,8 @@ acm_status adjoint_sphere(acm_forest* f, int nsteps, double dt, int c, double wE
     cudaStreamSynchronize(f->st);
     f->time = t0;
     f->norms_fresh = false;
+    if (f->moving) DISPATCH(f, eval_mask, f);
+    cudaStreamSynchronize(f->st);
   }
   return s;
 }
@@ -1564,7 +1614,16 @@ acm_status acm_adjoint_sphere(acm_forest* f, int nsteps, double dt, int ckpt_eve
                               size_t ws_bytes, double* J, double* dJ_dtheta, void* dJ_dU0, int64_t n_elems,
                               int on_device) {
   if (!f) return ACM_EINVAL;
+  if (f->moving || !f->mask_on || f->mask.kind != 1) return fail(f, ACM_EINVAL, "acm_adjoint_sphere needs the sphere mask");
   return adjoint_sphere(f, nsteps, dt, ckpt_every, w_energy, ws, ws_bytes, J, dJ_dtheta, dJ_dU0, n_elems, on_device);
+}
+
+acm_status acm_adjoint_plate_pitch(acm_forest* f, int nsteps, double dt, int ckpt_every, double w_energy, void* ws,
+                                   size_t ws_bytes, double* J, double* dJ_dalpha, void* dJ_dU0, int64_t n_elems,
+                                   int on_device) {
+  if (!f) return ACM_EINVAL;
+  if (!f->moving) return fail(f, ACM_EINVAL, "acm_adjoint_plate_pitch needs the moving plate mask");
+  return adjoint_sphere(f, nsteps, dt, ckpt_every, w_energy, ws, ws_bytes, J, dJ_dalpha, dJ_dU0, n_elems, on_device);
 }
 
 acm_status acm_autotune(acm_forest* f, int* fw_ctas, int* slab_ctas) {

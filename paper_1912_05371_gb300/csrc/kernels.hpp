@@ -164,10 +164,12 @@ void launch_ic(int Bs, T* reg, const int32_t* blist, const int32_t* ranks, int64
 // kind 1 (sphere): p = cx, cy, cz, R, delta.  kind 2 (rigid box, e.g. the moving plate, at one
 // time): p[0..8] = R (body to world, row-major), p[9..11] = pivot x_0, p[12..14] = box centre and
 // p[15..17] = half extents in the body frame, p[18] = delta, p[19..21] = angular velocity omega,
-// p[22] = radius around x_0 that contains the box.  Body coordinates x_b = R^T (x - x_0).
+// p[22] = radius around x_0 that contains the box, p[24..32] = dR/dtheta and p[33..35] =
+// d omega/dtheta for the parameter theta whose gradient the adjoint takes (the plate's pitch
+// amplitude).  Body coordinates x_b = R^T (x - x_0).
 struct MaskK {
   int kind;
-  double p[24];
+  double p[40];
 };
 template <typename T>
 void launch_mask(int Bs, T* chi, const int32_t* blist, const int32_t* ranks, int64_t n, const int4* binfo,
@@ -201,11 +203,12 @@ void launch_scatter(int Bs, const T* dense, T* reg, const int32_t* blist, int64_
 // (FP64 arrays are indexed like registers of T.)  Doubles of the loc^T coefficient scratch.
 size_t adj_weight_doubles(int Bs, int64_t nblocks);
 // nu += W^T E^T loc(E W Y)^T kappa for the blocks 0..n-1 (nu zeroed by the caller); the stage's
-// mask sensitivity is added to gchi.  err |= 8 if a ghost point's source is missing.
+// mask sensitivity is added to gchi, or, for a moving box (m.kind 2, the stage's pose), the
+// sensitivity to m's parameter is added to *dtheta.  err |= 8 if a ghost point's source is missing.
 template <typename T>
 void launch_adj_jgt(int Bs, const T* Y, const double* kap, const T* chi, double* gchi, double* wgt, double* nu,
                     const int32_t* blist, const int4* binfo, const int32_t* nbh, const uint8_t* finer, int64_t n,
-                    const PhysK& ph, int* err, cudaStream_t st);
+                    const PhysK& ph, const MaskK& m, double* dtheta, int* err, cudaStream_t st);
 // W^T applied to register r in place.
 template <typename T>
 void launch_adj_fw_T(int Bs, double* r, const int32_t* blist, const int32_t* nbh, const uint8_t* finer, int64_t n,
@@ -214,10 +217,12 @@ void launch_adj_fw_T(int Bs, double* r, const int32_t* blist, const int32_t* nbh
 template <typename T>
 void launch_adj_lin(int Bs, double* out, double a, const double* x, double b, const double* y, const int32_t* blist,
                     int64_t n, cudaStream_t st);
-// Direct terms of wN (F_x(U) + wE E(U)) into lam and gchi.
+// Direct terms of wN (F_x(U) + wE E(U)) into lam and gchi (a moving box: its parameter's direct
+// term into *dtheta, F_x integrating chi (u - u_s) at the pose of m).
 template <typename T>
 void launch_adj_objective(int Bs, const T* U, const T* chi, double* lam, double* gchi, const int32_t* blist,
-                          const int4* binfo, int64_t n, const PhysK& ph, double wN, double wE, cudaStream_t st);
+                          const int4* binfo, int64_t n, const PhysK& ph, double wN, double wE, const MaskK& m,
+                          double* dtheta, cudaStream_t st);
 // out[0..3] += sum gchi d chi / d (centre, radius) for the sphere mask m.
 template <typename T>
 void launch_adj_theta(int Bs, const double* gchi, const int32_t* blist, const int4* binfo, int64_t n, const PhysK& ph,

@@ -66,3 +66,36 @@ def test_moving_plate_steps_match_oracle(A, oracle_run, prec):
     ftol = 1e-11 if prec == 64 else 1e-4
     assert np.abs(np.asarray(d["force"]) - F).max() <= ftol * np.abs(F).max(), (d["force"], F)
     assert abs(d["energy"] - E) <= ftol * E
+
+
+def test_moving_plate_adjoint_matches_oracle(A):
+    """The gradient of the moving case with respect to the pitch amplitude (FP64, 8 blocks of 9^3,
+    2 steps) against the oracle's adjoint, which is pinned by central differences."""
+    from oracle.forest import Forest as OForest
+    from oracle.plate import MovingPlateAdjoint
+    from tests.test_gpu_adjoint import _per_point
+    P = dict(chord=0.3, span=0.35, thickness=0.1, phi_m=math.radians(60.0), alpha_m=math.radians(45.0), freq=1.0,
+             root=(0.5, 0.5, 0.5), delta=0.06)
+    ic = lambda X, Y, Z: np.stack([np.sin(2 * math.pi * Y), 0.3 * np.cos(2 * math.pi * Z),
+                                   0.2 * np.sin(2 * math.pi * X), 0.0 * X])
+    fo = OForest(nroot=(1, 1, 1), root_len=1.0, Bs=9, Jmin=1, Jmax=1, max_blocks=16)
+    fo.init_uniform(1)
+    S = MovingSolver(fo, oacm.Physics(nu=1e-2, c0=3.0, C_eta=1e-2, C_gamma=0.5), Plate(**P), ic=ic)
+    S.eval_ic()
+    S.eval_mask()
+    dt, n = 2e-3, 2
+    Jo, gUo, gao = MovingPlateAdjoint(S, dt, n, checkpoint_every=1).gradient(S.U.copy())
+    grid = dict(nroot=(1, 1, 1), root_len=1.0, Bs=9, g=4, Jmin=1, Jmax=1, precision=64, max_blocks=16, fd_scheme=1)
+    f = A.Forest(grid, dict(nu=1e-2, c0=3.0, C_eta=1e-2, C_gamma=0.5, cfl=0.5))
+    f.init_uniform(1)
+    f.write_fields(block_order_fields(S))
+    f.set_mask(A.ACM_MASK_PLATE, [P["chord"], P["span"], P["thickness"], P["phi_m"], P["alpha_m"], P["freq"],
+                                  *P["root"], P["delta"]])
+    before = f.read_fields().copy()
+    J, ga, gU = f.adjoint_plate_pitch(n, dt, ckpt_every=1, w_energy=0.1)
+    assert np.array_equal(f.read_fields(), before) and f.diagnostics()["time"] == 0.0
+    go = np.stack([gUo[fo.leaves[l]] for l in fo.sorted_leaves()])
+    a, b = _per_point(fo, gU, 1), _per_point(fo, go, 1)
+    assert abs(J - Jo) <= 1e-12 * abs(Jo), (J, Jo)
+    assert abs(ga - gao) <= 1e-10 * abs(gao), (ga, gao)
+    assert np.abs(a - b).max() <= 1e-10 * np.abs(b).max()
