@@ -60,7 +60,8 @@ def test_moving_plate_steps_match_oracle(A, oracle_run, prec):
     err = rel_linf(f.read_fields().astype(np.float64), block_order_fields(S))
     assert max(err) < tol, err
     chi = np.stack([S.chi[fo.leaves[l]] for l in fo.sorted_leaves()])
-    assert np.abs(f.read_mask().astype(np.float64) - chi).max() < (1e-14 if prec == 64 else 1e-6)
+    # FP32: the signed distance carries ~1e-7 absolute rounding, i.e. ~3e-6 of d/delta at delta = 0.03
+    assert np.abs(f.read_mask().astype(np.float64) - chi).max() < (1e-14 if prec == 64 else 1e-5)
     d = f.diagnostics()
     F, E = S.diagnostics()
     ftol = 1e-11 if prec == 64 else 1e-4
