@@ -46,3 +46,23 @@ def test_binding_covers_the_header_and_pool_size_is_host_only(libpath):
     g.Bs = 12
     assert L.acm_pool_bytes(ctypes.byref(g)) == 0  # invalid block size is rejected
     assert L.acm_status_string(3) == b"block pool exhausted"
+
+
+def test_host_only_argument_checks(libpath):
+    """Calls that are refused before any device work: an unknown wavelet, and the adjoint entry
+    points without a forest."""
+    from paper_1912_05371_gb300 import acm
+    L = acm.lib()
+    g = acm.GridParams()
+    g.nroot = (ctypes.c_int * 3)(2, 1, 1)
+    g.root_len, g.Bs, g.g, g.Jmin, g.Jmax, g.precision, g.max_blocks, g.fd_scheme = 2.0, 17, 4, 2, 5, 32, 1000, 1
+    sizes = {}
+    for w in (0, 40, 44, 43):
+        g.wavelet = w
+        sizes[w] = L.acm_pool_bytes(ctypes.byref(g))
+    assert sizes[0] == sizes[40] == sizes[44] > 0 and sizes[43] == 0
+    assert L.acm_adjoint_bytes(None, 10, 2) == 0
+    J = ctypes.c_double()
+    einval = 1
+    assert L.acm_adjoint_sphere(None, 4, 1e-3, 2, 0.1, None, 0, ctypes.byref(J), None, None, 0, 0) == einval
+    assert L.acm_adjoint_plate_pitch(None, 4, 1e-3, 2, 0.1, None, 0, ctypes.byref(J), None, None, 0, 0) == einval
