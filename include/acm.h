@@ -5,7 +5,10 @@
  * multiscale simulation of turbulent flows in flying insects" (arXiv:1912.05371): the
  * per-RK4-stage update over all cubic blocks of an adaptive block grid (ghost synchronisation,
  * fused ACM right-hand side, RK4 combination) and the per-step wavelet detail thresholding
- * that refines and coarsens the grid.
+ * that refines and coarsens the grid.  Beyond that path: RK4 steps replayed from CUDA graphs and
+ * many instances per graph (acm_rk4_steps, acm_rk4_steps_batch), an autotuner (acm_autotune),
+ * the lifted CDF 4/4 wavelet for coarsening (acm_grid_params.wavelet), a moving rigid plate
+ * (ACM_MASK_PLATE) and a discrete adjoint on a frozen grid (acm_adjoint_*).
  *
  * Conventions (all entry points):
  *  - Every call returns an acm_status; nothing throws across the ABI.  On an error the forest
