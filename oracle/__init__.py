@@ -19,6 +19,8 @@ Modules, each following the paper section it cites:
                  (Sec. 2.1-2.3; the adjoint itself is an extension, not in the paper)
 * ``plate``   -- moving rigid plate: box signed distance, stroke/pitch kinematics,
                  solid velocity, RK4 with the mask evaluated at every stage time (Sec. 2.2)
+* ``checkpointing`` -- binomial checkpointing of the adjoint's reverse sweep (Griewank's
+                 recursion, brute-force optimal splits; an extension, not in the paper)
 
 Parity status: every function is pinned by a ``-m "not gpu"`` test against a closed form,
 an invariant, a brute-force computation or a value the paper prints; none is "parity unpinned".

@@ -31,7 +31,9 @@ and the mask collects sum_s (dG/dchi)(Y_s)^T kappa_s.  The paper has no adjoint;
   steps on the grid a forward run uses (recorded and replayed), here one fixed grid.
 * dt is fixed (recorded), not differentiated through the CFL rule; the mask is static.
 * Checkpointing keeps the state at every c-th step; the backward sweep over a segment recomputes
-  the states inside it from its checkpoint (the one-level recompute pattern of revolve).
+  the states inside it from its checkpoint (one level of recompute).  Alternatively S snapshots
+  and binomial checkpointing (``oracle.checkpointing``) recompute the fewest steps for that
+  memory; the arithmetic of every step is the same, so all schedules give the same gradient.
 """
 from __future__ import annotations
 
@@ -39,6 +41,7 @@ import numpy as np
 import scipy.sparse as sp
 
 from . import acm
+from .checkpointing import reverse
 from .sync import PointValues, local_points, sync
 
 W_DD4 = np.array([-1.0, 9.0, 9.0, -1.0]) / 16.0
@@ -375,9 +378,13 @@ class FrozenGridAdjoint:
                 ckpt[n] = U.copy()
         return J, ckpt
 
-    def gradient(self, U0, store_all=False):
+    def gradient(self, U0, store_all=False, snapshots=None):
         """(J, dJ/dU_0 in the register layout, dJ/d(cx, cy, cz, R)).  store_all keeps every
-        state instead of recomputing segments (the same arithmetic, for comparison)."""
+        state instead of recomputing segments (the same arithmetic, for comparison); snapshots
+        = S reverses with S stored states by binomial checkpointing (``oracle.checkpointing``;
+        the count of recomputed steps is left in ``last_advances``)."""
+        if snapshots is not None:
+            return self._gradient_binomial(U0, snapshots)
         c = 1 if store_all else self.c
         saved_c, self.c = self.c, c
         J, ckpt = self.forward(U0)
@@ -397,9 +404,44 @@ class FrozenGridAdjoint:
                 lam = self._step_adjoint(states[n - a], lam, gchi)
                 if n >= 1:
                     self._dJ_dU(states[n - a], lam, gchi)
+        return J, lam, self._theta(gchi)
+
+    def _theta(self, gchi):
+        """dJ/d(cx, cy, cz, R) from the mask gradient."""
         gtheta = np.zeros(4)
         for leaf, s in self.fo.leaves.items():
             X, Y, Z = acm.block_coords(self.fo, leaf)
             dchi = sphere_mask_grad(X, Y, Z, self.centre, self.R, self.delta)
             gtheta += (dchi * gchi[s]).reshape(4, -1).sum(axis=1)
-        return J, lam, gtheta
+        return gtheta
+
+    def _gradient_binomial(self, U0, snapshots):
+        """The gradient with the states recomputed by binomial checkpointing: the objective's
+        terms are summed when a state is first reached (U_1 .. U_N in order), the adjoint steps
+        run N-1 .. 0 as in the segment sweep."""
+        N = self.N
+        gchi = {s: np.zeros_like(self.S.chi[s]) for s in self.fo.leaves.values()}
+        st = {"lam": np.zeros_like(U0), "J": 0.0, "hi": 0}
+
+        def reached(U, k):
+            if k > st["hi"]:
+                F, E = self.objective_terms(U)
+                st["J"] += (F + self.we * E) / N
+                st["hi"] = k
+
+        def advance(U, k):
+            U1 = self._step(U)[0]
+            reached(U1, k + 1)
+            return U1
+
+        def turn(U, k):
+            if k == N - 1:
+                UN = self._step(U)[0]
+                reached(UN, N)
+                self._dJ_dU(UN, st["lam"], gchi)
+            st["lam"] = self._step_adjoint(U, st["lam"], gchi)
+            if k >= 1:
+                self._dJ_dU(U, st["lam"], gchi)
+
+        self.last_advances = reverse(N, snapshots, U0, advance, turn)
+        return st["J"], st["lam"], self._theta(gchi)

@@ -28,6 +28,7 @@ import numpy as np
 from . import acm
 from .adapt import Solver
 from .adjoint import rhs_block_vjp
+from .checkpointing import reverse
 from .sync import sync
 
 
@@ -298,8 +299,11 @@ class MovingPlateAdjoint:
         v = np.stack([m.W.T @ tot[f] for f in range(4)])
         return m.to_reg(v, np.zeros_like(lam)), ga
 
-    def gradient(self, U0):
-        """(J, dJ/dU_0 in the register layout, dJ/d alpha_m)."""
+    def gradient(self, U0, snapshots=None):
+        """(J, dJ/dU_0 in the register layout, dJ/d alpha_m).  snapshots = S recomputes the
+        states by binomial checkpointing with S stored states instead of segments."""
+        if snapshots is not None:
+            return self._gradient_binomial(U0, snapshots)
         dt, N, c = self.dt, self.N, self.c
         U = U0.copy()
         ckpt = {0: U.copy()}
@@ -325,3 +329,33 @@ class MovingPlateAdjoint:
                 if n >= 1:
                     ga += self._direct(states[n - a], self.t0 + n * dt, lam)
         return J, lam, ga
+
+    def _gradient_binomial(self, U0, snapshots):
+        """As ``gradient``, the states recomputed by ``oracle.checkpointing.reverse``; the
+        objective's terms are summed when a state is first reached."""
+        dt, N = self.dt, self.N
+        st = {"lam": np.zeros_like(U0), "J": 0.0, "ga": 0.0, "hi": 0}
+
+        def reached(U, k):
+            if k > st["hi"]:
+                F, E = self._objective_terms(U, self.t0 + k * dt)
+                st["J"] += (F + self.we * E) / N
+                st["hi"] = k
+
+        def advance(U, k):
+            U1 = self._step(U, self.t0 + k * dt)[0]
+            reached(U1, k + 1)
+            return U1
+
+        def turn(U, k):
+            if k == N - 1:
+                UN = self._step(U, self.t0 + k * dt)[0]
+                reached(UN, N)
+                st["ga"] += self._direct(UN, self.t0 + N * dt, st["lam"])
+            st["lam"], g_step = self._step_adjoint(U, self.t0 + k * dt, st["lam"])
+            st["ga"] += g_step
+            if k >= 1:
+                st["ga"] += self._direct(U, self.t0 + k * dt, st["lam"])
+
+        self.last_advances = reverse(N, snapshots, U0, advance, turn)
+        return st["J"], st["lam"], st["ga"]

@@ -196,3 +196,7 @@ def test_checkpointing_reproduces_the_stored_state_sweep(grad_case):
     S, delta, dt, N, adj, U0, J, gU, gth = grad_case
     J2, gU2, gth2 = adj.gradient(U0, store_all=True)
     assert J2 == J and np.array_equal(gU2, gU) and np.array_equal(gth2, gth)
+    # binomial checkpointing with 2 snapshots: 4 recomputed steps (the closed form 2*4 - C(4,1))
+    J3, gU3, gth3 = adj.gradient(U0, snapshots=2)
+    assert adj.last_advances == 4
+    assert J3 == J and np.array_equal(gU3, gU) and np.array_equal(gth3, gth)

@@ -211,3 +211,8 @@ def test_moving_adjoint_against_central_differences():
     # checkpointing every 2 steps recomputes the same arithmetic
     J2, gU2, ga2 = MovingPlateAdjoint(_moving_case(), dt, n, checkpoint_every=2).gradient(U0)
     assert J2 == J and np.array_equal(gU2, gU) and ga2 == ga
+    # and so does binomial checkpointing with U_0 as the only snapshot (1 recomputed step)
+    adj1 = MovingPlateAdjoint(_moving_case(), dt, n)
+    J3, gU3, ga3 = adj1.gradient(U0, snapshots=1)
+    assert adj1.last_advances == 1
+    assert J3 == J and np.array_equal(gU3, gU) and ga3 == ga
