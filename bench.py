@@ -264,11 +264,13 @@ def wavelet_comparison(A, stream, precision, Jmax, max_blocks, nsteps=10, warmup
             "blocks_evolved_mean": float(np.mean(nev)), "blocks_after_coarsening": nb}
 
 
-def adjoint_measurement(A, stream, nsteps=100, ckpt_every=10, w_energy=0.1):
+def adjoint_measurement(A, stream, nsteps=100, ckpt_every=10, w_energy=0.1, binomial_snapshots=4):
     """The adjoint workload: the sphere case at levels 2..4, FP32 fields and FP64 adjoint, on its
     initial grid (frozen), nsteps RK4 steps of one fixed dt; CUDA-event time of the forward steps
     alone and of the whole adjoint call (forward with checkpoints every ckpt_every steps,
-    recomputation, backward sweep)."""
+    recomputation, backward sweep), then of the same call with binomial checkpointing in
+    binomial_snapshots stored states."""
+    import numpy as np
     import torch
     grid, phys, mask, ic, _ = sphere_setup(Jmax=4, precision=32, max_blocks=2048)
     f = A.Forest(grid, phys, stream=stream)
@@ -291,12 +293,25 @@ def adjoint_measurement(A, stream, nsteps=100, ckpt_every=10, w_energy=0.1):
     e1.record(stream)
     e1.synchronize()
     adj = e0.elapsed_time(e1)
+    # the same gradient with binomial checkpointing in 4 snapshots: less memory, more recomputation
+    e0.record(stream)
+    J4, gth4, _ = f.adjoint_sphere(nsteps, dt, w_energy=w_energy, snapshots=binomial_snapshots)
+    e1.record(stream)
+    e1.synchronize()
+    adj4 = e0.elapsed_time(e1)
     nb = f.n_blocks()
     f.close()
+    eq = A.checkpoint_schedule(nsteps, ckpt_every=ckpt_every)
+    bi = A.checkpoint_schedule(nsteps, snapshots=binomial_snapshots)
     return {"workload": f"sphere, levels 2..4, frozen grid of {nb} blocks of 17^3, FP32 forward, FP64 adjoint, "
                         f"{nsteps} steps, checkpoints every {ckpt_every}", "forward_ms_per_step": fwd / nsteps,
             "adjoint_ms_per_step": adj / nsteps, "adjoint_over_forward": adj / fwd, "J": J,
-            "dJ_dtheta": [float(v) for v in gth]}
+            "dJ_dtheta": [float(v) for v in gth], "snapshots": eq["snapshots"],
+            "recomputed_steps": eq["advances"],
+            "binomial": {"snapshots": bi["snapshots"], "recomputed_steps": bi["advances"],
+                         "adjoint_ms_per_step": adj4 / nsteps, "adjoint_over_forward": adj4 / fwd,
+                         "rel_diff_J": abs(J4 - J) / abs(J),
+                         "rel_diff_dJ_dtheta": float(np.abs(gth4 - gth).max() / np.abs(gth).max())}}
 
 
 def batched_comparison(A, precision, seed=0, n=64, nsteps=10):

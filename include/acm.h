@@ -226,14 +226,21 @@ acm_status acm_autotune(acm_forest* f, int* fw_ctas, int* slab_ctas);
  * FP64 values whatever the forest's precision, block order, fields layout of acm_read_fields,
  * n_elems = n_blocks*4*Bs^3; device pointer if on_device, else host; may be NULL).  FP32 or
  * FP64 forests with the sphere mask (ACM_EINVAL otherwise): the forward steps run in the
- * forest's precision, every adjoint variable and sum in FP64.  The states at every ckpt_every-th step are kept and each segment is recomputed
- * in the backward sweep.  ws: caller device buffer of at least acm_adjoint_bytes(f, nsteps,
- * ckpt_every) bytes (ACM_ENOMEM if smaller).  The forest's state and time are unchanged on
- * return; the call synchronises the stream.  ACM_EGRADING if a ghost point's source is
- * missing.  The gradient with respect to U_0 is that of the forward map as computed: a point
- * shared by several blocks carries its sensitivity in the copy the forward map reads. */
-size_t acm_adjoint_bytes(const acm_forest* f, int nsteps, int ckpt_every);
-acm_status acm_adjoint_sphere(acm_forest* f, int nsteps, double dt, int ckpt_every, double w_energy, void* ws,
+ * forest's precision, every adjoint variable and sum in FP64.  States are recomputed from
+ * snapshots by the schedule of acm_checkpoint_schedule(nsteps, ckpt): ckpt > 0 keeps the state
+ * at every ckpt-th step and recomputes each segment with its states stored; ckpt < 0 is binomial
+ * checkpointing with -ckpt snapshots (the fewest recomputed steps for that memory).  Every
+ * schedule takes the same steps in the same arithmetic, so the result does not depend on it
+ * (up to the order of FP64 atomic sums).  ws: caller device buffer of at least
+ * acm_adjoint_bytes(f, nsteps, ckpt) bytes (ACM_ENOMEM if smaller): four FP64 registers, the
+ * snapshots and five state registers in the forest's precision, and the mask's sensitivity.
+ * acm_adjoint_bytes returns 0 for an invalid ckpt (0) or nsteps outside [1, 2^20].  The
+ * forest's state and time are unchanged on return, also when the sweep stops on an error; the
+ * call synchronises the stream.  ACM_EGRADING if a ghost point's source is missing.  The
+ * gradient with respect to U_0 is that of the forward map as computed: a point shared by
+ * several blocks carries its sensitivity in the copy the forward map reads. */
+size_t acm_adjoint_bytes(const acm_forest* f, int nsteps, int ckpt);
+acm_status acm_adjoint_sphere(acm_forest* f, int nsteps, double dt, int ckpt, double w_energy, void* ws,
                               size_t ws_bytes, double* J, double* dJ_dtheta, void* dJ_dU0, int64_t n_elems,
                               int on_device);
 
@@ -242,9 +249,26 @@ acm_status acm_adjoint_sphere(acm_forest* f, int nsteps, double dt, int ckpt_eve
  * *dJ_dalpha (host) receives the derivative with respect to the pitch amplitude alpha_m (the
  * plate's drag sensitivity of the full-scale configuration).  Workspace as acm_adjoint_bytes.
  * Not yet run on a GPU. */
-acm_status acm_adjoint_plate_pitch(acm_forest* f, int nsteps, double dt, int ckpt_every, double w_energy, void* ws,
+acm_status acm_adjoint_plate_pitch(acm_forest* f, int nsteps, double dt, int ckpt, double w_energy, void* ws,
                                    size_t ws_bytes, double* J, double* dJ_dalpha, void* dJ_dU0, int64_t n_elems,
                                    int on_device);
+
+/* The adjoint's checkpoint schedule (host only: no forest, no device work).  The reverse sweep
+ * over nsteps steps takes the steps' adjoints in the order nsteps-1, ..., 0, each from its own
+ * state, recomputed from snapshots.  ckpt > 0: equidistant, U_k kept for every multiple k of
+ * ckpt, ceil(nsteps/ckpt) + max(ckpt - 2, 0) snapshots (ckpt capped at nsteps).  ckpt < 0: binomial
+ * checkpointing (Griewank's revolve) with S = -ckpt snapshots (capped at nsteps): the fewest
+ * recomputed steps for S stored states, r n - C(S + r, r - 1) with r the least integer with
+ * C(S + r, S) >= n.  Writes the snapshots used and the recomputed (plain forward) steps, the n
+ * steps taken with their adjoint not counted (either pointer may be NULL) and the number of
+ * actions.  With ops and args (both non-NULL, cap entries) it also writes the actions in order:
+ * op 0 STORE j (current state into snapshot j), 1 RESTORE j (snapshot j becomes current),
+ * 2 ADVANCE k (plain step k -> k+1 from U_k), 3 TURN k (step k with its adjoint, from U_k; the
+ * current state is used up); args holds j or k.  The first action stores U_0 in snapshot 0,
+ * which is never written again.  ACM_EINVAL for nsteps outside [1, 2^20], ckpt = 0, or cap
+ * below the number of actions (which is still written). */
+acm_status acm_checkpoint_schedule(int nsteps, int ckpt, int32_t* snapshots, int64_t* advances, int8_t* ops,
+                                   int32_t* args, int64_t cap, int64_t* n_actions);
 
 /* Right-hand side K = F(U) of eqs. (u_eqn-1, p_eqn-1) at every point of every block, after
  * the same synchronisation as an RK4 stage, written in block order (fields layout) to out

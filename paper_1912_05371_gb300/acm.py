@@ -66,6 +66,8 @@ EXPORTS = {
     "acm_adjoint_plate_pitch": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_int, C.c_double, C.c_void_p,
                                           C.c_size_t, C.POINTER(C.c_double), C.c_void_p, C.c_void_p, C.c_int64,
                                           C.c_int]),
+    "acm_checkpoint_schedule": (C.c_int, [C.c_int, C.c_int, C.POINTER(C.c_int32), C.POINTER(C.c_int64), C.c_void_p,
+                                          C.c_void_p, C.c_int64, C.POINTER(C.c_int64)]),
     "acm_rk4_steps_batch": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_int, C.c_double, C.c_int,
                                       C.POINTER(C.c_double), C.POINTER(C.c_int)]),
     "acm_refine_all": (C.c_int, [C.c_void_p]),
@@ -258,34 +260,41 @@ class Forest:
         self._check(self.L.acm_autotune(self.h, C.byref(a), C.byref(b)))
         return a.value, b.value
 
-    def adjoint_sphere(self, nsteps, dt, ckpt_every=10, w_energy=0.1):
+    def _adjoint_workspace(self, nsteps, policy):
+        import torch
+        nbytes = int(self.L.acm_adjoint_bytes(self.h, int(nsteps), policy))
+        if nbytes == 0:
+            raise ValueError(f"invalid checkpointing ({policy}) or step count ({nsteps})")
+        return torch.empty(nbytes, dtype=torch.uint8, device=self.pool.device), nbytes
+
+    def adjoint_sphere(self, nsteps, dt, ckpt_every=10, w_energy=0.1, snapshots=None):
         """J = (1/N) sum_n [F_x(U_n) + w_energy E(U_n)] over nsteps fixed-dt RK4 steps on the frozen
         grid, and its gradient: returns (J, dJ/d(cx, cy, cz, R) (4,), dJ/dU_0 in the layout of
         read_fields, float64).  The forward runs in the forest's precision, the adjoint in FP64;
-        the sphere mask must be set; the forest's state is unchanged."""
-        import torch
-        nbytes = int(self.L.acm_adjoint_bytes(self.h, int(nsteps), int(ckpt_every)))
-        ws = torch.empty(nbytes, dtype=torch.uint8, device=self.pool.device)
+        the sphere mask must be set; the forest's state is unchanged.  States are recomputed from
+        a checkpoint every ckpt_every steps, or with snapshots=S by binomial checkpointing with S
+        stored states (see checkpoint_schedule)."""
+        policy = checkpoint_policy(ckpt_every, snapshots)
+        ws, nbytes = self._adjoint_workspace(nsteps, policy)
         n = self.n_blocks()
         g = np.empty((n, 4, self.Bs, self.Bs, self.Bs), dtype=np.float64)
         J = C.c_double()
         th = np.zeros(4)
-        self._check(self.L.acm_adjoint_sphere(self.h, int(nsteps), float(dt), int(ckpt_every), float(w_energy),
+        self._check(self.L.acm_adjoint_sphere(self.h, int(nsteps), float(dt), policy, float(w_energy),
                                               C.c_void_p(ws.data_ptr()), nbytes, C.byref(J), _ptr(th), _ptr(g),
                                               g.size, 0))
         return J.value, th, g
 
-    def adjoint_plate_pitch(self, nsteps, dt, ckpt_every=10, w_energy=0.1):
+    def adjoint_plate_pitch(self, nsteps, dt, ckpt_every=10, w_energy=0.1, snapshots=None):
         """As adjoint_sphere for the moving plate, from the forest's time: returns (J, dJ/d alpha_m,
         dJ/dU_0)."""
-        import torch
-        nbytes = int(self.L.acm_adjoint_bytes(self.h, int(nsteps), int(ckpt_every)))
-        ws = torch.empty(nbytes, dtype=torch.uint8, device=self.pool.device)
+        policy = checkpoint_policy(ckpt_every, snapshots)
+        ws, nbytes = self._adjoint_workspace(nsteps, policy)
         n = self.n_blocks()
         g = np.empty((n, 4, self.Bs, self.Bs, self.Bs), dtype=np.float64)
         J = C.c_double()
         da = np.zeros(1)
-        self._check(self.L.acm_adjoint_plate_pitch(self.h, int(nsteps), float(dt), int(ckpt_every), float(w_energy),
+        self._check(self.L.acm_adjoint_plate_pitch(self.h, int(nsteps), float(dt), policy, float(w_energy),
                                                    C.c_void_p(ws.data_ptr()), nbytes, C.byref(J), _ptr(da),
                                                    _ptr(g), g.size, 0))
         return J.value, float(da[0]), g
@@ -376,6 +385,39 @@ class Forest:
 
     def launch_count(self):
         return self.L.acm_launch_count(self.h)
+
+
+CKPT_OPS = ("store", "restore", "advance", "turn")
+
+
+def checkpoint_policy(ckpt_every=10, snapshots=None):
+    """The library's checkpointing argument: ckpt_every > 0, or -snapshots for binomial."""
+    if snapshots is not None:
+        if int(snapshots) < 1:
+            raise ValueError("binomial checkpointing needs at least one snapshot")
+        return -int(snapshots)
+    if int(ckpt_every) < 1:
+        raise ValueError("ckpt_every must be positive")
+    return int(ckpt_every)
+
+
+def checkpoint_schedule(nsteps, ckpt_every=10, snapshots=None):
+    """The adjoint's checkpoint schedule as the library runs it (host only): a dict with the
+    snapshots used, the recomputed (plain forward) steps and the actions, a list of (op, arg)
+    with op in CKPT_OPS."""
+    L = lib()
+    policy = checkpoint_policy(ckpt_every, snapshots)
+    ns, adv, na = C.c_int32(), C.c_int64(), C.c_int64()
+    st = L.acm_checkpoint_schedule(int(nsteps), policy, C.byref(ns), C.byref(adv), None, None, 0, C.byref(na))
+    if st != 0:
+        raise AcmError(f"acm_checkpoint_schedule: {L.acm_status_string(st).decode()}")
+    ops = np.empty(na.value, dtype=np.int8)
+    args = np.empty(na.value, dtype=np.int32)
+    st = L.acm_checkpoint_schedule(int(nsteps), policy, None, None, _ptr(ops), _ptr(args), na.value, C.byref(na))
+    if st != 0:
+        raise AcmError(f"acm_checkpoint_schedule: {L.acm_status_string(st).decode()}")
+    return dict(snapshots=ns.value, advances=adv.value,
+                actions=[(CKPT_OPS[o], int(a)) for o, a in zip(ops.tolist(), args.tolist())])
 
 
 def sphere_objective_function():

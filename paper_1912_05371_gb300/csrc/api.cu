@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "../../include/acm.h"
+#include "checkpoint.hpp"
 #include "common.cuh"
 #include "forest.hpp"
 #include "kernels.hpp"
@@ -1054,14 +1055,18 @@ acm_status autotune(acm_forest* f, int* fw_ctas, int* slab_ctas) {
 // ceil(N / c) checkpoints, the mask sensitivity (one component), the loc^T coefficients and the
 // 4 parameter sums.
 struct AdjLayout {
-  size_t lam, kap, nu, sum, y[4], seg, ck, gchi, wgt, theta, total;
+  size_t lam, kap, nu, sum, y[4], tape, ck, gchi, wgt, theta, total;
   size_t reg;    // bytes of an FP64 adjoint register (indexed like a register of the forest)
   size_t sreg;   // bytes of a state register in the forest's precision
-  int nck;
+  int64_t nslots;   // snapshots of the checkpoint schedule (ck: snapshot 0, 1, ...)
 };
 
-AdjLayout adj_layout(const acm_forest* f, int nsteps, int c) {
+// policy > 0: equidistant checkpoints every policy steps; policy < 0: binomial checkpointing with
+// -policy snapshots.  total = 0 for an invalid policy or step count.
+AdjLayout adj_layout(const acm_forest* f, int nsteps, int policy) {
   AdjLayout L{};
+  L.nslots = acm::ckpt::snapshots_needed(nsteps, policy);
+  if (L.nslots < 1) return L;
   L.reg = (size_t)f->gp.max_blocks * (size_t)f->lay.BLK * 8;
   L.sreg = (size_t)f->gp.max_blocks * (size_t)f->lay.BLK * f->esz;
   size_t o = 0;
@@ -1071,9 +1076,8 @@ AdjLayout adj_layout(const acm_forest* f, int nsteps, int c) {
   L.nu = take(L.reg);
   L.sum = take(L.reg);
   for (int s = 0; s < 4; ++s) L.y[s] = take(L.sreg);
-  L.seg = take(L.sreg * (size_t)(c + 1));
-  L.nck = (nsteps - 1) / c + 1;
-  L.ck = take(L.sreg * (size_t)L.nck);
+  L.tape = take(L.sreg);
+  L.ck = take(L.sreg * (size_t)L.nslots);
   L.gchi = take((size_t)f->gp.max_blocks * (size_t)f->lay.FS * 8);
   L.wgt = take(acm::adj_weight_doubles(f->gp.Bs, f->gp.max_blocks) * 8);
   L.theta = take(64);
@@ -1119,13 +1123,14 @@ acm_status force_energy(acm_forest* f, double* Fx, double* E) {
 
 template <typename T>
 acm_status adjoint_sweep(acm_forest* f, int nsteps, double dt, int c, double wE, void* ws, size_t ws_bytes,
-                         double* J_out, double* dtheta, void* dU0, int64_t n_elems, int on_device) {
+                         double* J_out, double* dtheta, void* dU0, int64_t n_elems, int on_device, bool* saved) {
   // the sphere's centre and radius (static mask), or the moving plate's pitch amplitude
   const bool plate = f->moving;
   if (!f->mask_on || (!plate && f->mask.kind != 1)) return fail(f, ACM_EINVAL, "the adjoint needs a sphere or plate mask");
-  if (nsteps < 1 || c < 1 || !(dt > 0) || !ws || !J_out || !dtheta) return fail(f, ACM_EINVAL, "bad arguments");
+  if (nsteps < 1 || c == 0 || !(dt > 0) || !ws || !J_out || !dtheta) return fail(f, ACM_EINVAL, "bad arguments");
   if (f->order.empty()) return fail(f, ACM_EINVAL, "empty forest");
   const AdjLayout L = adj_layout(f, nsteps, c);
+  if (L.total == 0) return fail(f, ACM_EINVAL, "bad checkpoint policy");
   if (ws_bytes < L.total) return fail(f, ACM_ENOMEM, "adjoint workspace too small");
   const int64_t nb = (int64_t)f->order.size();
   if (dU0 && n_elems != nb * 4 * (int64_t)f->gp.Bs * f->gp.Bs * f->gp.Bs)
@@ -1141,7 +1146,6 @@ acm_status adjoint_sweep(acm_forest* f, int nsteps, double dt, int c, double wE,
   double* GCHI = R(L.gchi);
   double* WGT = R(L.wgt);
   double* TH = R(L.theta);
-  auto SEG = [&](int k) { return S(L.seg + (size_t)k * L.sreg); };
   auto CKP = [&](int k) { return S(L.ck + (size_t)k * L.sreg); };
   const int Bs = f->gp.Bs;
   T* U = reinterpret_cast<T*>(f->U);
@@ -1179,53 +1183,66 @@ acm_status adjoint_sweep(acm_forest* f, int nsteps, double dt, int c, double wE,
                                  f->mask, TH, f->st);
     ++f->launches;
   };
-  acm_status s;
-  // forward: the objective and the checkpoints
-  CK(copy(U, CKP(0)));
-  double J = 0.0;
-  for (int k = 1; k <= nsteps; ++k) {
-    if ((s = rk4<T>(f, dt, nullptr))) return s;
-    double Fx, E;
-    if ((s = force_energy<T>(f, &Fx, &E))) return s;
-    J += (Fx + wE * E) / nsteps;
-    if (k % c == 0 && k < nsteps) CK(copy(U, CKP(k / c)));
-  }
-  // backward sweep, one checkpoint segment at a time (its states recomputed)
+  acm::ckpt::Schedule sched;
+  if (!acm::ckpt::build(nsteps, c, &sched) || sched.slots > L.nslots)
+    return fail(f, ACM_EINVAL, "bad checkpoint policy");
+  T* TAPE = S(L.tape);
   CK(cudaMemsetAsync(LAM, 0, L.reg, f->st));
   CK(cudaMemsetAsync(GCHI, 0, (size_t)f->gp.max_blocks * f->lay.FS * 8, f->st));
   CK(cudaMemsetAsync(TH, 0, 64, f->st));
-  for (int a = ((nsteps - 1) / c) * c; a >= 0; a -= c) {
-    const int b = std::min(a + c, nsteps);
-    CK(copy(CKP(a / c), SEG(0)));
-    for (int k = a; k < b; ++k) {
-      CK(copy(SEG(k - a), U));
-      f->time = t0 + k * dt;                       // a moving mask follows the step's clock
+  acm_status s;
+  // J's terms are summed when a state is first reached (U_1, ..., U_N in that order)
+  double J = 0.0;
+  int hi = 0;
+  auto reached = [&](int k) -> acm_status {
+    if (k <= hi) return ACM_OK;
+    double Fx, E;
+    const acm_status r = force_energy<T>(f, &Fx, &E);
+    if (r) return r;
+    J += (Fx + wE * E) / nsteps;
+    hi = k;
+    return ACM_OK;
+  };
+  // the schedule's actions: snapshots are copies of U; a turn takes step k from U_k with its
+  // stage inputs kept and then the step's adjoint (lam' -> lam)
+  for (const acm::ckpt::Action& act : sched.act) {
+    const int k = act.arg;
+    if (act.op == acm::ckpt::STORE || act.op == acm::ckpt::RESTORE) {
+      if (k < 0 || k >= L.nslots) return fail(f, ACM_EINVAL, "snapshot index outside the workspace");
+      T* snap = CKP(k);
+      CK(act.op == acm::ckpt::STORE ? copy(U, snap) : copy(snap, U));
+      if (k == 0) *saved = true;                   // snapshot 0 holds U_0 from here on
+      continue;
+    }
+    if (k < 0 || k >= nsteps) return fail(f, ACM_EINVAL, "step index outside the sweep");
+    const double tk = t0 + k * dt;
+    if (act.op == acm::ckpt::ADVANCE) {
+      f->time = tk;                                // a moving mask follows the step's clock
       if ((s = rk4<T>(f, dt, nullptr))) return s;
-      CK(copy(U, SEG(k - a + 1)));
+      if ((s = reached(k + 1))) return s;
+      continue;
     }
-    if (b == nsteps) objective(SEG(b - a), t0 + b * dt);
-    for (int k = b - 1; k >= a; --k) {
-      const double tk = t0 + k * dt;
-      CK(copy(SEG(k - a), U));
-      f->time = tk;
-      if ((s = rk4<T>(f, dt, nullptr, Y))) return s;
-      lin(KAP, dt / 6.0, LAM, 0.0, nullptr);
-      if ((s = jgt(Y[3], tk + dt))) return s;
-      lin(SUM, 1.0, NU, 0.0, nullptr);
-      lin(KAP, dt / 3.0, LAM, dt, NU);
-      if ((s = jgt(Y[2], tk + 0.5 * dt))) return s;
-      lin(SUM, 1.0, SUM, 1.0, NU);
-      lin(KAP, dt / 3.0, LAM, dt / 2.0, NU);
-      if ((s = jgt(Y[1], tk + 0.5 * dt))) return s;
-      lin(SUM, 1.0, SUM, 1.0, NU);
-      lin(KAP, dt / 6.0, LAM, dt / 2.0, NU);
-      if ((s = jgt(Y[0], tk))) return s;
-      lin(SUM, 1.0, SUM, 1.0, NU);
-      lin(LAM, 1.0, LAM, 1.0, SUM);
-      acm::launch_adj_fw_T<T>(Bs, LAM, f->d_blist, f->d_nbh, f->d_finer, nb, f->st);
-      ++f->launches;
-      if (k >= 1) objective(SEG(k - a), tk);
-    }
+    CK(copy(U, TAPE));
+    f->time = tk;
+    if ((s = rk4<T>(f, dt, nullptr, Y))) return s;
+    if ((s = reached(k + 1))) return s;
+    if (k == nsteps - 1) objective(U, t0 + nsteps * dt);
+    lin(KAP, dt / 6.0, LAM, 0.0, nullptr);
+    if ((s = jgt(Y[3], tk + dt))) return s;
+    lin(SUM, 1.0, NU, 0.0, nullptr);
+    lin(KAP, dt / 3.0, LAM, dt, NU);
+    if ((s = jgt(Y[2], tk + 0.5 * dt))) return s;
+    lin(SUM, 1.0, SUM, 1.0, NU);
+    lin(KAP, dt / 3.0, LAM, dt / 2.0, NU);
+    if ((s = jgt(Y[1], tk + 0.5 * dt))) return s;
+    lin(SUM, 1.0, SUM, 1.0, NU);
+    lin(KAP, dt / 6.0, LAM, dt / 2.0, NU);
+    if ((s = jgt(Y[0], tk))) return s;
+    lin(SUM, 1.0, SUM, 1.0, NU);
+    lin(LAM, 1.0, LAM, 1.0, SUM);
+    acm::launch_adj_fw_T<T>(Bs, LAM, f->d_blist, f->d_nbh, f->d_finer, nb, f->st);
+    ++f->launches;
+    if (k >= 1) objective(TAPE, tk);
   }
   if (!plate) {
     acm::launch_adj_theta<T>(Bs, GCHI, f->d_blist, f->d_binfo, nb, f->phk, f->mask, TH, f->st);
@@ -1256,14 +1273,15 @@ acm_status adjoint_sweep(acm_forest* f, int nsteps, double dt, int c, double wE,
   return ACM_OK;
 }
 
-// The sweep above, with the forest's state and time put back if it stops on an error after the
-// first step (checkpoint 0 holds the initial state).
+// The sweep above, with the forest's state and time put back if it stops on an error once
+// U_0 is in snapshot 0 (the first action of every schedule; no step runs before it).
 acm_status adjoint_sphere(acm_forest* f, int nsteps, double dt, int c, double wE, void* ws, size_t ws_bytes,
                           double* J_out, double* dtheta, void* dU0, int64_t n_elems, int on_device) {
   const double t0 = f->time;
+  bool saved = false;
   const acm_status s = DISPATCH(f, adjoint_sweep, f, nsteps, dt, c, wE, ws, ws_bytes, J_out, dtheta, dU0, n_elems,
-                                on_device);
-  if (s != ACM_OK && s != ACM_EINVAL && s != ACM_ENOMEM && f->time != t0) {
+                                on_device, &saved);
+  if (s != ACM_OK && saved) {
     const AdjLayout L = adj_layout(f, nsteps, c);
     char* base = reinterpret_cast<char*>(((uintptr_t)ws + 255) & ~(uintptr_t)255);
     if (f->gp.precision == 64)
@@ -1605,25 +1623,42 @@ acm_status acm_rk4_steps_batch(acm_forest* const* forests, int n, int nsteps, do
   return ACM_OK;
 }
 
-size_t acm_adjoint_bytes(const acm_forest* f, int nsteps, int ckpt_every) {
-  if (!f || nsteps < 1 || ckpt_every < 1) return 0;
-  return adj_layout(f, nsteps, ckpt_every).total;
+size_t acm_adjoint_bytes(const acm_forest* f, int nsteps, int ckpt) {
+  if (!f) return 0;
+  return adj_layout(f, nsteps, ckpt).total;
 }
 
-acm_status acm_adjoint_sphere(acm_forest* f, int nsteps, double dt, int ckpt_every, double w_energy, void* ws,
+acm_status acm_checkpoint_schedule(int nsteps, int ckpt, int32_t* snapshots, int64_t* advances, int8_t* ops,
+                                   int32_t* args, int64_t cap, int64_t* n_actions) {
+  acm::ckpt::Schedule sched;
+  if (!acm::ckpt::build(nsteps, ckpt, &sched)) return ACM_EINVAL;
+  if (snapshots) *snapshots = sched.slots;
+  if (advances) *advances = sched.advances;
+  const int64_t n = (int64_t)sched.act.size();
+  if (n_actions) *n_actions = n;
+  if (!ops && !args) return ACM_OK;
+  if (!ops || !args || cap < n) return ACM_EINVAL;
+  for (int64_t i = 0; i < n; ++i) {
+    ops[i] = sched.act[(size_t)i].op;
+    args[i] = sched.act[(size_t)i].arg;
+  }
+  return ACM_OK;
+}
+
+acm_status acm_adjoint_sphere(acm_forest* f, int nsteps, double dt, int ckpt, double w_energy, void* ws,
                               size_t ws_bytes, double* J, double* dJ_dtheta, void* dJ_dU0, int64_t n_elems,
                               int on_device) {
   if (!f) return ACM_EINVAL;
   if (f->moving || !f->mask_on || f->mask.kind != 1) return fail(f, ACM_EINVAL, "acm_adjoint_sphere needs the sphere mask");
-  return adjoint_sphere(f, nsteps, dt, ckpt_every, w_energy, ws, ws_bytes, J, dJ_dtheta, dJ_dU0, n_elems, on_device);
+  return adjoint_sphere(f, nsteps, dt, ckpt, w_energy, ws, ws_bytes, J, dJ_dtheta, dJ_dU0, n_elems, on_device);
 }
 
-acm_status acm_adjoint_plate_pitch(acm_forest* f, int nsteps, double dt, int ckpt_every, double w_energy, void* ws,
+acm_status acm_adjoint_plate_pitch(acm_forest* f, int nsteps, double dt, int ckpt, double w_energy, void* ws,
                                    size_t ws_bytes, double* J, double* dJ_dalpha, void* dJ_dU0, int64_t n_elems,
                                    int on_device) {
   if (!f) return ACM_EINVAL;
   if (!f->moving) return fail(f, ACM_EINVAL, "acm_adjoint_plate_pitch needs the moving plate mask");
-  return adjoint_sphere(f, nsteps, dt, ckpt_every, w_energy, ws, ws_bytes, J, dJ_dalpha, dJ_dU0, n_elems, on_device);
+  return adjoint_sphere(f, nsteps, dt, ckpt, w_energy, ws, ws_bytes, J, dJ_dalpha, dJ_dU0, n_elems, on_device);
 }
 
 acm_status acm_autotune(acm_forest* f, int* fw_ctas, int* slab_ctas) {

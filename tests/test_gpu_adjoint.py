@@ -89,6 +89,25 @@ def test_adjoint_matches_the_oracle(A, oracle_gradient, prec, tol_J, tol_g):
     assert np.abs(a - b).max() <= tol_g * np.abs(b).max(), info
 
 
+@pytest.mark.parametrize("ckpt", [dict(snapshots=1), dict(snapshots=2), dict(snapshots=3), dict(ckpt_every=1),
+                                  dict(ckpt_every=3), dict(ckpt_every=8)])
+def test_every_checkpoint_schedule_gives_the_oracles_gradient(A, oracle_gradient, ckpt):
+    """Binomial checkpointing with 1-3 snapshots and equidistant checkpoints at other spacings
+    take the same steps in the same arithmetic (FP64): the oracle's gradient, which is itself
+    the same for every schedule, and the forest's state and time unchanged."""
+    S, delta, Jo, gUo, gtho = oracle_gradient
+    f = _gpu_forest(A, S, delta, precision=64)
+    before = f.read_fields().copy()
+    J, gth, gU = f.adjoint_sphere(N, DT, w_energy=0.1, **ckpt)
+    assert np.array_equal(f.read_fields(), before) and f.diagnostics()["time"] == 0.0
+    fo = S.fo
+    go = np.stack([gUo[fo.leaves[l]] for l in fo.sorted_leaves()])
+    a, b = _per_point(fo, gU, 2), _per_point(fo, go, 2)
+    assert abs(J - Jo) <= 1e-12 * abs(Jo), (J, Jo)
+    assert np.abs(gth - gtho).max() <= 1e-10 * np.abs(gtho).max(), (gth, gtho)
+    assert np.abs(a - b).max() <= 1e-10 * np.abs(b).max()
+
+
 def test_adjoint_through_autograd(A):
     import torch
     S, delta = _setup()

@@ -69,9 +69,11 @@ def test_moving_plate_steps_match_oracle(A, oracle_run, prec):
     assert abs(d["energy"] - E) <= ftol * E
 
 
-def test_moving_plate_adjoint_matches_oracle(A):
+@pytest.mark.parametrize("ckpt", [dict(ckpt_every=1), dict(snapshots=1)])
+def test_moving_plate_adjoint_matches_oracle(A, ckpt):
     """The gradient of the moving case with respect to the pitch amplitude (FP64, 8 blocks of 9^3,
-    2 steps) against the oracle's adjoint, which is pinned by central differences."""
+    2 steps) against the oracle's adjoint, which is pinned by central differences; equidistant
+    checkpoints, or binomial checkpointing with U_0 as the only snapshot."""
     from oracle.forest import Forest as OForest
     from oracle.plate import MovingPlateAdjoint
     from tests.test_gpu_adjoint import _per_point
@@ -93,7 +95,7 @@ def test_moving_plate_adjoint_matches_oracle(A):
     f.set_mask(A.ACM_MASK_PLATE, [P["chord"], P["span"], P["thickness"], P["phi_m"], P["alpha_m"], P["freq"],
                                   *P["root"], P["delta"]])
     before = f.read_fields().copy()
-    J, ga, gU = f.adjoint_plate_pitch(n, dt, ckpt_every=1, w_energy=0.1)
+    J, ga, gU = f.adjoint_plate_pitch(n, dt, w_energy=0.1, **ckpt)
     assert np.array_equal(f.read_fields(), before) and f.diagnostics()["time"] == 0.0
     go = np.stack([gUo[fo.leaves[l]] for l in fo.sorted_leaves()])
     a, b = _per_point(fo, gU, 1), _per_point(fo, go, 1)
