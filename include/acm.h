@@ -53,6 +53,11 @@ typedef enum {
   ACM_EGRADING = 7    /* a supplied layout is not 2:1 graded / does not tile the domain     */
 } acm_status;
 
+/* ACM_ENUMERIC comes from the max-norm reduction, which propagates NaN and infinity: acm_rk4_step
+ * with dt <= 0 and acm_diagnostics report a non-finite state before changing anything, acm_step
+ * with dt <= 0 after its refinement.  acm_rk4_steps and the batched steps take the time step on
+ * the device from the last stage's norms and do not check. */
+
 /* Grid of cubic blocks (Sec. 4.1).  nroot[3] roots of side root_len tile the periodic box
  * [0, nroot*root_len]; a block at level J has side root_len/2^J and spacing
  * h_J = root_len / (2^J (Bs-1)).  Bs must be 9 or 17.  g is the ghost depth reported by

@@ -452,8 +452,11 @@ __global__ void __launch_bounds__(kNT) k_maxnorm(const T* reg, const int32_t* bl
   const int slot = blist[blockIdx.x];
   const T* b = reg + (size_t)slot * L::BLK;
   // arithmetic in the field precision (an FP32 field gives an FP32 norm, stored as double);
-  // m[4] holds the squared magnitude, its root is taken once at the end
+  // m[4] holds the squared magnitude, its root is taken once at the end.  The maxima propagate
+  // NaN (a comparison with NaN is false, so a plain maximum would drop it): a non-finite state
+  // reaches the host as a non-finite norm.
   T m[5] = {T(0), T(0), T(0), T(0), T(0)};
+  auto keep = [](T a, T m) { return (a > m || a != a) ? a : m; };
   constexpr int N = BS * BS * BS, U = 4;
   for (int base = threadIdx.x; base < N; base += kNT * U) {
     T v[U][4];
@@ -468,27 +471,22 @@ __global__ void __launch_bounds__(kNT) k_maxnorm(const T* reg, const int32_t* bl
     for (int k = 0; k < U; ++k) {
 #pragma unroll
       for (int f = 0; f < 4; ++f) {
-        const T a = tabs(v[k][f]);
-        m[f] = a > m[f] ? a : m[f];
+        m[f] = keep(tabs(v[k][f]), m[f]);
       }
-      const T m2 = mag2(v[k][0], v[k][1], v[k][2]);
-      m[4] = m2 > m[4] ? m2 : m[4];
+      m[4] = keep(mag2(v[k][0], v[k][1], v[k][2]), m[4]);
     }
   }
   __shared__ T red[5][kNT / 32];
 #pragma unroll
   for (int k = 0; k < 5; ++k) {
     T mk = m[k];
-    for (int o = 16; o > 0; o >>= 1) {
-      const T t = __shfl_xor_sync(0xffffffffu, mk, o);
-      mk = t > mk ? t : mk;
-    }
+    for (int o = 16; o > 0; o >>= 1) mk = keep(__shfl_xor_sync(0xffffffffu, mk, o), mk);
     if ((threadIdx.x & 31) == 0) red[k][threadIdx.x >> 5] = mk;
   }
   __syncthreads();
   if (threadIdx.x < 5) {
     T mk = T(0);
-    for (int w = 0; w < kNT / 32; ++w) mk = red[threadIdx.x][w] > mk ? red[threadIdx.x][w] : mk;
+    for (int w = 0; w < kNT / 32; ++w) mk = keep(red[threadIdx.x][w], mk);
     const double d = threadIdx.x == 4 ? (double)tsqrt(mk) : (double)mk;
     atomicMax(out + threadIdx.x, (unsigned long long)__double_as_longlong(d));
   }
