@@ -201,6 +201,7 @@ void launch_scatter(int Bs, const T* dense, T* reg, const int32_t* blist, int64_
 
 // ---- discrete adjoint (adjoint.cu): forward state and mask in T, adjoint variables FP64 ------------
 // (FP64 arrays are indexed like registers of T.)  Doubles of the loc^T coefficient scratch.
+constexpr int kAdjWeightsPerPoint = 20;
 size_t adj_weight_doubles(int Bs, int64_t nblocks);
 // nu += W^T E^T loc(E W Y)^T kappa for the blocks 0..n-1 (nu zeroed by the caller); the stage's
 // mask sensitivity is added to gchi, or, for a moving box (m.kind 2, the stage's pose), the
