@@ -258,6 +258,23 @@ acm_status acm_adjoint_plate_pitch(acm_forest* f, int nsteps, double dt, int ckp
                                    size_t ws_bytes, double* J, double* dJ_dalpha, void* dJ_dU0, int64_t n_elems,
                                    int on_device);
 
+/* Restart files (the paper's runs resume from saved states across job limits, Sec. 4).
+ * acm_save_state writes to path: a header (8 bytes "ACMSTATE", int32 version 1, precision,
+ * sizeof(acm_grid_params), sizeof(acm_phys_params), mask kind, 0, the mask's 10 parameters as
+ * acm_set_mask takes them (unused ones 0), the time, int64 n_blocks), the forest's
+ * acm_grid_params and acm_phys_params, the leaves' level, x, y and z (int32 arrays of n_blocks,
+ * block order) and the interior fields of U as acm_read_fields returns them; host byte order.
+ * acm_read_state_header (host only, no forest) returns a file's parameters, block count and
+ * time, so a caller can create a matching forest.  acm_load_state replaces a forest's grid,
+ * state, physics parameters, mask and time with the file's; the forest's acm_grid_params must
+ * equal the file's except max_blocks, which must hold its blocks (ACM_ECAPACITY), and the file is
+ * read whole before anything changes.  ACM_EINVAL for a missing, foreign, truncated or
+ * inconsistent file, or a different grid.  Save and load synchronise the stream. */
+acm_status acm_save_state(acm_forest* f, const char* path);
+acm_status acm_read_state_header(const char* path, acm_grid_params* grid, acm_phys_params* phys, int64_t* n_blocks,
+                                 double* time);
+acm_status acm_load_state(acm_forest* f, const char* path);
+
 /* The adjoint's checkpoint schedule (host only: no forest, no device work).  The reverse sweep
  * over nsteps steps takes the steps' adjoints in the order nsteps-1, ..., 0, each from its own
  * state, recomputed from snapshots.  ckpt > 0: equidistant, U_k kept for every multiple k of

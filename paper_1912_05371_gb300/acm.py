@@ -68,6 +68,10 @@ EXPORTS = {
                                           C.c_int]),
     "acm_checkpoint_schedule": (C.c_int, [C.c_int, C.c_int, C.POINTER(C.c_int32), C.POINTER(C.c_int64), C.c_void_p,
                                           C.c_void_p, C.c_int64, C.POINTER(C.c_int64)]),
+    "acm_save_state": (C.c_int, [C.c_void_p, C.c_char_p]),
+    "acm_read_state_header": (C.c_int, [C.c_char_p, C.POINTER(GridParams), C.POINTER(PhysParams),
+                                        C.POINTER(C.c_int64), C.POINTER(C.c_double)]),
+    "acm_load_state": (C.c_int, [C.c_void_p, C.c_char_p]),
     "acm_rk4_steps_batch": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_int, C.c_double, C.c_int,
                                       C.POINTER(C.c_double), C.POINTER(C.c_int)]),
     "acm_refine_all": (C.c_int, [C.c_void_p]),
@@ -308,6 +312,26 @@ class Forest:
     def refine_all(self):
         self._check(self.L.acm_refine_all(self.h))
 
+    # ---- restart files --------------------------------------------------------------------------
+    def save(self, path):
+        """Write the grid, state, parameters, mask and time to a restart file."""
+        self._check(self.L.acm_save_state(self.h, os.fsencode(path)))
+
+    def load(self, path):
+        """Replace this forest's grid, state, parameters, mask and time with a restart file's
+        (its grid parameters must equal this forest's, max_blocks large enough)."""
+        self._check(self.L.acm_load_state(self.h, os.fsencode(path)))
+
+    @classmethod
+    def from_file(cls, path, max_blocks=None, stream=None, device=None):
+        """A new forest resumed from a restart file (max_blocks defaults to the saving forest's)."""
+        grid, phys, _, _ = read_state_header(path)
+        if max_blocks is not None:
+            grid["max_blocks"] = int(max_blocks)
+        f = cls(grid, phys, stream=stream, device=device)
+        f.load(path)
+        return f
+
     def coarsen(self):
         n, p = C.c_int64(), C.c_int()
         self._check(self.L.acm_coarsen(self.h, C.byref(n), C.byref(p)))
@@ -385,6 +409,26 @@ class Forest:
 
     def launch_count(self):
         return self.L.acm_launch_count(self.h)
+
+
+def _fields_dict(st):
+    out = {}
+    for name, _ in st._fields_:
+        v = getattr(st, name)
+        out[name] = tuple(v) if isinstance(v, C.Array) else v
+    return out
+
+
+def read_state_header(path):
+    """(grid dict, phys dict, n_blocks, time) of a restart file (host only); the dicts are what
+    Forest takes."""
+    L = lib()
+    g, p = GridParams(), PhysParams()
+    n, t = C.c_int64(), C.c_double()
+    st = L.acm_read_state_header(os.fsencode(path), C.byref(g), C.byref(p), C.byref(n), C.byref(t))
+    if st != 0:
+        raise AcmError(f"acm_read_state_header: {L.acm_status_string(st).decode()} ({path})")
+    return _fields_dict(g), _fields_dict(p), n.value, t.value
 
 
 CKPT_OPS = ("store", "restore", "advance", "turn")

@@ -1783,6 +1783,148 @@ static acm_status copy_fields(acm_forest* f, void* buf, int64_t n_elems, int on_
   return device_error(f);
 }
 
+// ---- restart files -------------------------------------------------------------------------------
+// Header, then acm_grid_params, acm_phys_params, the leaves' level, x, y, z (int32, block order)
+// and the interior fields of U (block order, the forest's precision).  Host byte order.
+namespace {
+
+struct StateHeader {
+  char magic[8];
+  int32_t version;
+  int32_t precision;
+  int32_t grid_bytes;
+  int32_t phys_bytes;
+  int32_t mask_kind;
+  int32_t reserved;
+  double mask_params[10];
+  double time;
+  int64_t n_blocks;
+};
+constexpr char kStateMagic[8] = {'A', 'C', 'M', 'S', 'T', 'A', 'T', 'E'};
+constexpr int32_t kStateVersion = 1;
+
+struct File {
+  FILE* p = nullptr;
+  explicit File(FILE* q) : p(q) {}
+  ~File() {
+    if (p) fclose(p);
+  }
+};
+
+// Reads and checks the header and both parameter blocks.
+acm_status read_state_head(acm_forest* f, FILE* in, StateHeader* h, acm_grid_params* g, acm_phys_params* ph) {
+  if (fread(h, sizeof(*h), 1, in) != 1 || std::memcmp(h->magic, kStateMagic, 8) != 0)
+    return fail(f, ACM_EINVAL, "not a restart file");
+  if (h->version != kStateVersion || h->grid_bytes != (int32_t)sizeof(acm_grid_params) ||
+      h->phys_bytes != (int32_t)sizeof(acm_phys_params))
+    return fail(f, ACM_EINVAL, "restart file of another version or build");
+  if (fread(g, sizeof(*g), 1, in) != 1 || fread(ph, sizeof(*ph), 1, in) != 1)
+    return fail(f, ACM_EINVAL, "truncated restart file");
+  if (h->n_blocks < 1 || h->n_blocks > g->max_blocks || (h->precision != 32 && h->precision != 64) ||
+      h->precision != g->precision || h->mask_kind < ACM_MASK_NONE || h->mask_kind > ACM_MASK_PLATE)
+    return fail(f, ACM_EINVAL, "inconsistent restart file header");
+  return ACM_OK;
+}
+
+}  // namespace
+
+acm_status acm_save_state(acm_forest* f, const char* path) {
+  if (!f || !path) return fail(f, ACM_EINVAL, "bad arguments");
+  const int64_t n = (int64_t)f->order.size();
+  if (n < 1) return fail(f, ACM_EINVAL, "empty forest");
+  StateHeader h{};
+  std::memcpy(h.magic, kStateMagic, 8);
+  h.version = kStateVersion;
+  h.precision = f->gp.precision;
+  h.grid_bytes = (int32_t)sizeof(acm_grid_params);
+  h.phys_bytes = (int32_t)sizeof(acm_phys_params);
+  if (f->mask_on && f->moving) {
+    h.mask_kind = ACM_MASK_PLATE;
+    for (int i = 0; i < 10; ++i) h.mask_params[i] = f->plate[i];
+  } else if (f->mask_on) {
+    h.mask_kind = ACM_MASK_SPHERE;
+    for (int i = 0; i < 5; ++i) h.mask_params[i] = f->mask.p[i];
+  }
+  h.time = f->time;
+  h.n_blocks = n;
+  std::vector<int32_t> leaves((size_t)(4 * n));
+  for (int64_t r = 0; r < n; ++r) {
+    const BoxKey& b = f->order[(size_t)r];
+    leaves[(size_t)r] = b.J;
+    leaves[(size_t)(n + r)] = b.x;
+    leaves[(size_t)(2 * n + r)] = b.y;
+    leaves[(size_t)(3 * n + r)] = b.z;
+  }
+  const int64_t ne = n * 4 * (int64_t)f->gp.Bs * f->gp.Bs * f->gp.Bs;
+  std::vector<char> fields((size_t)ne * f->esz);
+  acm_status s = copy_fields(f, fields.data(), ne, 0, false, 4, f->U);
+  if (s) return s;
+  File out(fopen(path, "wb"));
+  if (!out.p) return fail(f, ACM_EINVAL, std::string("cannot open ") + path);
+  if (fwrite(&h, sizeof(h), 1, out.p) != 1 || fwrite(&f->gp, sizeof(f->gp), 1, out.p) != 1 ||
+      fwrite(&f->pp, sizeof(f->pp), 1, out.p) != 1 ||
+      fwrite(leaves.data(), sizeof(int32_t), leaves.size(), out.p) != leaves.size() ||
+      fwrite(fields.data(), 1, fields.size(), out.p) != fields.size())
+    return fail(f, ACM_EINVAL, std::string("cannot write ") + path);
+  if (fclose(out.p) != 0) {
+    out.p = nullptr;
+    return fail(f, ACM_EINVAL, std::string("cannot write ") + path);
+  }
+  out.p = nullptr;
+  return ACM_OK;
+}
+
+acm_status acm_read_state_header(const char* path, acm_grid_params* grid, acm_phys_params* phys, int64_t* n_blocks,
+                                 double* time) {
+  if (!path) return ACM_EINVAL;
+  File in(fopen(path, "rb"));
+  if (!in.p) return ACM_EINVAL;
+  StateHeader h{};
+  acm_grid_params g{};
+  acm_phys_params ph{};
+  if (read_state_head(nullptr, in.p, &h, &g, &ph)) return ACM_EINVAL;
+  if (grid) *grid = g;
+  if (phys) *phys = ph;
+  if (n_blocks) *n_blocks = h.n_blocks;
+  if (time) *time = h.time;
+  return ACM_OK;
+}
+
+acm_status acm_load_state(acm_forest* f, const char* path) {
+  if (!f || !path) return fail(f, ACM_EINVAL, "bad arguments");
+  File in(fopen(path, "rb"));
+  if (!in.p) return fail(f, ACM_EINVAL, std::string("cannot open ") + path);
+  StateHeader h{};
+  acm_grid_params g{};
+  acm_phys_params ph{};
+  acm_status s = read_state_head(f, in.p, &h, &g, &ph);
+  if (s) return s;
+  const acm_grid_params& me = f->gp;
+  if (g.wavelet == 0) g.wavelet = 40;
+  if (g.nroot[0] != me.nroot[0] || g.nroot[1] != me.nroot[1] || g.nroot[2] != me.nroot[2] ||
+      g.root_len != me.root_len || g.Bs != me.Bs || g.g != me.g || g.Jmin != me.Jmin || g.Jmax != me.Jmax ||
+      g.precision != me.precision || g.fd_scheme != me.fd_scheme || g.wavelet != me.wavelet)
+    return fail(f, ACM_EINVAL, "restart file of a different grid");
+  if (h.n_blocks > me.max_blocks) return fail(f, ACM_ECAPACITY, "restart file has more blocks than max_blocks");
+  // everything is read before the forest changes
+  const int64_t n = h.n_blocks;
+  std::vector<int32_t> leaves((size_t)(4 * n));
+  const int64_t ne = n * 4 * (int64_t)me.Bs * me.Bs * me.Bs;
+  std::vector<char> fields((size_t)ne * f->esz);
+  if (fread(leaves.data(), sizeof(int32_t), leaves.size(), in.p) != leaves.size() ||
+      fread(fields.data(), 1, fields.size(), in.p) != fields.size())
+    return fail(f, ACM_EINVAL, "truncated restart file");
+  s = acm_set_leaves(f, leaves.data(), leaves.data() + n, leaves.data() + 2 * n, leaves.data() + 3 * n, n);
+  if (s) return s;
+  s = copy_fields(f, fields.data(), ne, 0, true, 4, f->U);
+  if (s) return s;
+  f->pp = ph;
+  f->time = h.time;
+  f->norms_fresh = false;
+  const int np = h.mask_kind == ACM_MASK_PLATE ? 10 : (h.mask_kind == ACM_MASK_SPHERE ? 5 : 0);
+  return acm_set_mask(f, h.mask_kind, np ? h.mask_params : nullptr, np, h.time);
+}
+
 acm_status acm_read_fields(acm_forest* f, int reg, void* out, int64_t n_elems, int on_device) {
   if (!f || !out || reg != ACM_REG_U) return fail(f, ACM_EINVAL, "bad arguments");
   return copy_fields(f, out, n_elems, on_device, false, 4, f->U);
