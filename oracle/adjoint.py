@@ -406,6 +406,26 @@ class FrozenGridAdjoint:
                     self._dJ_dU(states[n - a], lam, gchi)
         return J, lam, self._theta(gchi)
 
+    def vjp(self, U0, lamN, snapshots=None):
+        """The vector-Jacobian product of the N-step map U_0 -> U_N: for L = <lamN, U_N> (lamN in
+        the register layout) returns (U_N, dL/dU_0, dL/d(cx, cy, cz, R)).  The backward sweep is
+        the gradient's without the objective's direct terms, from lam = lamN; the states are
+        recomputed with `snapshots` stored states (default: all of them)."""
+        N = self.N
+        gchi = {s: np.zeros_like(self.S.chi[s]) for s in self.fo.leaves.values()}
+        st = {"lam": lamN.copy(), "UN": None}
+
+        def advance(U, k):
+            return self._step(U)[0]
+
+        def turn(U, k):
+            if k == N - 1:
+                st["UN"] = self._step(U)[0]
+            st["lam"] = self._step_adjoint(U, st["lam"], gchi)
+
+        self.last_advances = reverse(N, snapshots or N, U0, advance, turn)
+        return st["UN"], st["lam"], self._theta(gchi)
+
     def _theta(self, gchi):
         """dJ/d(cx, cy, cz, R) from the mask gradient."""
         gtheta = np.zeros(4)

@@ -200,3 +200,45 @@ def test_checkpointing_reproduces_the_stored_state_sweep(grad_case):
     J3, gU3, gth3 = adj.gradient(U0, snapshots=2)
     assert adj.last_advances == 4
     assert J3 == J and np.array_equal(gU3, gU) and np.array_equal(gth3, gth)
+
+
+def test_vector_jacobian_product_against_central_differences():
+    """L = <lam, U_N> over 3 steps for a random lam: the oracle's vector-Jacobian product against
+    central differences of L through the oracle solver's own steps, in a random direction of U_0
+    and in the sphere's centre and radius; binomial checkpointing gives it bitwise."""
+    S, delta = _setup()
+    dt, N = 2e-3, 3
+    adj = FrozenGridAdjoint(S, CENTRE, RADIUS, delta, dt=dt, nsteps=N)
+    U0 = S.U.copy()
+    sl = adj.mats.slots
+    rng = np.random.default_rng(12)
+    lam = np.zeros_like(U0)
+    lam[sl] = rng.normal(size=lam[sl].shape)
+    UN, g, gth = adj.vjp(U0, lam)
+
+    def L(T):
+        for _ in range(N):
+            T.rk4(dt)
+        return float((lam[sl] * T.U[sl]).sum())
+
+    assert L(_setup()[0]) == float((lam[sl] * UN[sl]).sum())
+    h = 1e-4
+    v = np.zeros_like(U0)
+    v[sl] = rng.normal(size=v[sl].shape)
+    vals = []
+    for sgn in (1, -1):
+        T, _ = _setup()
+        T.U = U0 + sgn * h * v
+        vals.append(L(T))
+    fd = (vals[0] - vals[1]) / (2 * h)
+    assert abs(fd - float((g * v).sum())) <= 1e-7 * abs(fd)
+    theta = list(CENTRE) + [RADIUS]
+    for a in range(4):
+        tp, tm = list(theta), list(theta)
+        tp[a] += h
+        tm[a] -= h
+        fd = (L(_setup(centre=tp[:3], R=tp[3])[0]) - L(_setup(centre=tm[:3], R=tm[3])[0])) / (2 * h)
+        assert abs(fd - gth[a]) <= 2e-4 * np.abs(gth).max(), (a, fd, gth[a])
+    UN2, g2, gth2 = adj.vjp(U0, lam, snapshots=1)
+    assert adj.last_advances == 3
+    assert np.array_equal(UN2, UN) and np.array_equal(g2, g) and np.array_equal(gth2, gth)
