@@ -258,6 +258,21 @@ acm_status acm_adjoint_plate_pitch(acm_forest* f, int nsteps, double dt, int ckp
                                    size_t ws_bytes, double* J, double* dJ_dalpha, void* dJ_dU0, int64_t n_elems,
                                    int on_device);
 
+/* Vector-Jacobian product of the N-step map U_0 -> U_N (nsteps RK4 steps of fixed dt from the
+ * current state and time on the frozen grid, the forward map and checkpointing of
+ * acm_adjoint_sphere, sphere or moving-plate mask required): for any L with dL_dUN = dL/dU_N
+ * (FP64, block order, layout of acm_read_fields, n_elems = n_blocks*4*Bs^3, one value per copy
+ * of a redundant point), writes dL_dU0 = dL/dU_0 (same layout; both arrays on the device if
+ * on_device, else host) and, if dL_dtheta is not NULL, dL/d(cx, cy, cz, R) of the sphere (4
+ * values) or dL/d alpha_m of the plate (1 value).  Workspace, restoration of the forest's state
+ * and time, and errors as acm_adjoint_sphere.  With it a caller composes the solver with any
+ * loss of the final state (the Python binding's step_map_function does so for torch.autograd). */
+acm_status acm_adjoint_vjp(acm_forest* f, int nsteps, double dt, int ckpt, void* ws, size_t ws_bytes,
+                           const void* dL_dUN, void* dL_dU0, int64_t n_elems, int on_device, double* dL_dtheta);
+
+/* Set the simulated time (a moving mask is evaluated at it).  ACM_EINVAL for a non-finite t. */
+acm_status acm_set_time(acm_forest* f, double t);
+
 /* Restart files (the paper's runs resume from saved states across job limits, Sec. 4).
  * acm_save_state writes to path: a header (8 bytes "ACMSTATE", int32 version 1, precision,
  * sizeof(acm_grid_params), sizeof(acm_phys_params), mask kind, 0, the mask's 10 parameters as

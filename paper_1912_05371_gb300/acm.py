@@ -68,6 +68,9 @@ EXPORTS = {
                                           C.c_int]),
     "acm_checkpoint_schedule": (C.c_int, [C.c_int, C.c_int, C.POINTER(C.c_int32), C.POINTER(C.c_int64), C.c_void_p,
                                           C.c_void_p, C.c_int64, C.POINTER(C.c_int64)]),
+    "acm_adjoint_vjp": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_int, C.c_void_p, C.c_size_t, C.c_void_p,
+                                  C.c_void_p, C.c_int64, C.c_int, C.c_void_p]),
+    "acm_set_time": (C.c_int, [C.c_void_p, C.c_double]),
     "acm_save_state": (C.c_int, [C.c_void_p, C.c_char_p]),
     "acm_read_state_header": (C.c_int, [C.c_char_p, C.POINTER(GridParams), C.POINTER(PhysParams),
                                         C.POINTER(C.c_int64), C.POINTER(C.c_double)]),
@@ -303,6 +306,32 @@ class Forest:
                                                    _ptr(g), g.size, 0))
         return J.value, float(da[0]), g
 
+    def adjoint_vjp(self, nsteps, dt, dL_dUN, ckpt_every=10, snapshots=None):
+        """Vector-Jacobian product of nsteps fixed-dt RK4 steps from the current state and time:
+        dL_dUN (n_blocks, 4, Bs, Bs, Bs) float64, numpy or a CUDA tensor -> (dL/dU_0 of the same
+        kind, dL/d(cx, cy, cz, R) for the sphere; for the plate element 0 is dL/d alpha_m)."""
+        import torch
+        policy = checkpoint_policy(ckpt_every, snapshots)
+        ws, nbytes = self._adjoint_workspace(nsteps, policy)
+        n = self.n_blocks()
+        shape = (n, 4, self.Bs, self.Bs, self.Bs)
+        on_dev = int(hasattr(dL_dUN, "data_ptr") and dL_dUN.is_cuda)
+        if on_dev:
+            src = dL_dUN.detach().to(torch.float64).contiguous()
+            out = torch.empty(shape, dtype=torch.float64, device=src.device)
+        else:
+            src = np.ascontiguousarray(dL_dUN, dtype=np.float64)
+            out = np.empty(shape, dtype=np.float64)
+        if tuple(src.shape) != shape:
+            raise ValueError(f"dL_dUN must have shape {shape}")
+        th = np.zeros(4)
+        self._check(self.L.acm_adjoint_vjp(self.h, int(nsteps), float(dt), policy, C.c_void_p(ws.data_ptr()), nbytes,
+                                           _ptr(src), _ptr(out), int(np.prod(shape)), on_dev, _ptr(th)))
+        return out, th
+
+    def set_time(self, t):
+        self._check(self.L.acm_set_time(self.h, float(t)))
+
     def rhs(self):
         n = self.n_blocks()
         out = np.empty((n, 4, self.Bs, self.Bs, self.Bs), dtype=self.dtype)
@@ -429,6 +458,43 @@ def read_state_header(path):
     if st != 0:
         raise AcmError(f"acm_read_state_header: {L.acm_status_string(st).decode()} ({path})")
     return _fields_dict(g), _fields_dict(p), n.value, t.value
+
+
+def step_map_function():
+    """A torch.autograd.Function for the N-step map: forward(forest, U0, theta, nsteps, dt,
+    ckpt_every=10, snapshots=None) writes U0 (block order, read_fields layout, float64) and the
+    sphere mask theta = (cx, cy, cz, R, delta) into the forest, takes nsteps fixed-dt RK4 steps on
+    its frozen grid and returns U_N (float64), leaving the forest at U0 and its start time;
+    backward returns dL/dU0 and dL/d(cx, cy, cz, R) (none for delta) from the library's
+    vector-Jacobian product, so any loss of U_N can be differentiated."""
+    import torch
+
+    class StepMap(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, forest, U0, theta, nsteps, dt, ckpt_every=10, snapshots=None):
+            u0 = U0.detach().cpu().numpy()
+            t0 = forest.diagnostics()["time"] if forest.n_blocks() else 0.0
+            forest.write_fields(u0)
+            forest.set_mask(ACM_MASK_SPHERE, [float(v) for v in theta.detach().cpu()])
+            for _ in range(int(nsteps)):
+                forest.rk4_step(float(dt))
+            UN = forest.read_fields().astype(np.float64)
+            forest.write_fields(u0)
+            forest.set_time(t0)
+            ctx.forest, ctx.u0 = forest, u0
+            ctx.args = (int(nsteps), float(dt), ckpt_every, snapshots)
+            ctx.devices = (U0.device, theta.device)
+            return torch.from_numpy(UN).to(U0.device)
+
+        @staticmethod
+        def backward(ctx, gUN):
+            nsteps, dt, ckpt_every, snapshots = ctx.args
+            ctx.forest.write_fields(ctx.u0)
+            gU0, gth = ctx.forest.adjoint_vjp(nsteps, dt, gUN.detach().cpu().numpy(), ckpt_every, snapshots)
+            gtheta = torch.tensor(list(gth[:4]) + [0.0], dtype=torch.float64, device=ctx.devices[1])
+            return None, torch.from_numpy(gU0).to(ctx.devices[0]), gtheta, None, None, None, None
+
+    return StepMap
 
 
 CKPT_OPS = ("store", "restore", "advance", "turn")

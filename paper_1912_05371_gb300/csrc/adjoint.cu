@@ -26,6 +26,8 @@ void theta(const double* gchi, const int32_t* blist, const int4* binfo, int64_t 
            double* out, cudaStream_t st);
 template <typename T, int BS>
 void gather(const double* r, double* dense, const int32_t* blist, int64_t n, cudaStream_t st);
+template <typename T, int BS>
+void put(const double* dense, double* r, const int32_t* blist, int64_t n, cudaStream_t st);
 
 }  // namespace adj
 
@@ -82,6 +84,12 @@ void launch_adj_gather(int Bs, const double* r, double* dense, const int32_t* bl
   ACM_ADJ_BS(Bs, gather, r, dense, blist, n, st);
 }
 
+template <typename T>
+void launch_adj_put(int Bs, const double* dense, double* r, const int32_t* blist, int64_t n, cudaStream_t st) {
+  if (n <= 0) return;
+  ACM_ADJ_BS(Bs, put, dense, r, blist, n, st);
+}
+
 #define ACM_ADJ_INST(T)                                                                                        \
   template void launch_adj_jgt<T>(int, const T*, const double*, const T*, double*, double*, double*, const int32_t*, \
                                   const int4*, const int32_t*, const uint8_t*, int64_t, const PhysK&, const MaskK&, \
@@ -93,7 +101,8 @@ void launch_adj_gather(int Bs, const double* r, double* dense, const int32_t* bl
                                         const PhysK&, double, double, const MaskK&, double*, cudaStream_t);  \
   template void launch_adj_theta<T>(int, const double*, const int32_t*, const int4*, int64_t, const PhysK&,   \
                                     const MaskK&, double*, cudaStream_t);                                     \
-  template void launch_adj_gather<T>(int, const double*, double*, const int32_t*, int64_t, cudaStream_t);
+  template void launch_adj_gather<T>(int, const double*, double*, const int32_t*, int64_t, cudaStream_t);         \
+  template void launch_adj_put<T>(int, const double*, double*, const int32_t*, int64_t, cudaStream_t);
 ACM_ADJ_INST(float)
 ACM_ADJ_INST(double)
 

@@ -439,6 +439,20 @@ __global__ void __launch_bounds__(kNA) k_adj_gather(const double* r, double* den
   }
 }
 
+// The inverse copy: dense[rank][f][z][y][x] into the register's interior points (the register's
+// padding is left as it is).
+template <typename T, int BS>
+__global__ void __launch_bounds__(kNA) k_adj_put(const double* dense, double* r, const int32_t* blist) {
+  using L = Lay<T, BS>;
+  constexpr int N3 = BS * BS * BS;
+  const size_t own = (size_t)blist[blockIdx.x] * L::BLK;
+  const double* d = dense + (size_t)blockIdx.x * 4 * N3;
+  for (int t = threadIdx.x; t < 4 * N3; t += kNA) {
+    const int f = t / N3, r3 = t % N3;
+    r[own + (size_t)f * L::FS + L::idx(r3 % BS, (r3 / BS) % BS, r3 / (BS * BS))] = d[t];
+  }
+}
+
 inline dim3 g1(int64_t n) { return dim3((unsigned)n); }
 
 }  // namespace
@@ -482,6 +496,11 @@ void gather(const double* r, double* dense, const int32_t* blist, int64_t n, cud
   k_adj_gather<T, BS><<<g1(n), kNA, 0, st>>>(r, dense, blist);
 }
 
+template <typename T, int BS>
+void put(const double* dense, double* r, const int32_t* blist, int64_t n, cudaStream_t st) {
+  k_adj_put<T, BS><<<g1(n), kNA, 0, st>>>(dense, r, blist);
+}
+
 }  // namespace adj
 }  // namespace acm
 
@@ -500,5 +519,6 @@ void gather(const double* r, double* dense, const int32_t* blist, int64_t n, cud
   template void theta<T, BS>(const double*, const int32_t*, const int4*, int64_t, const PhysK&, const MaskK&,        \
                              double*, cudaStream_t);                                                               \
   template void gather<T, BS>(const double*, double*, const int32_t*, int64_t, cudaStream_t);                        \
+  template void put<T, BS>(const double*, double*, const int32_t*, int64_t, cudaStream_t);                           \
   }                                                                                                                \
   }

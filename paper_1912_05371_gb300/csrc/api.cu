@@ -1123,17 +1123,22 @@ acm_status force_energy(acm_forest* f, double* Fx, double* E) {
 
 template <typename T>
 acm_status adjoint_sweep(acm_forest* f, int nsteps, double dt, int c, double wE, void* ws, size_t ws_bytes,
-                         double* J_out, double* dtheta, void* dU0, int64_t n_elems, int on_device, bool* saved) {
+                         double* J_out, double* dtheta, void* dU0, int64_t n_elems, int on_device, const void* lamN,
+                         bool* saved) {
   // the sphere's centre and radius (static mask), or the moving plate's pitch amplitude
   const bool plate = f->moving;
+  // with lamN (dL/dU_N, block order, FP64, on the device if on_device) the sweep is the
+  // vector-Jacobian product of the N-step map: lam starts from lamN, no objective terms
+  const bool vjp = lamN != nullptr;
   if (!f->mask_on || (!plate && f->mask.kind != 1)) return fail(f, ACM_EINVAL, "the adjoint needs a sphere or plate mask");
-  if (nsteps < 1 || c == 0 || !(dt > 0) || !ws || !J_out || !dtheta) return fail(f, ACM_EINVAL, "bad arguments");
+  if (nsteps < 1 || c == 0 || !(dt > 0) || !ws || !dtheta || (!vjp && !J_out) || (vjp && !dU0))
+    return fail(f, ACM_EINVAL, "bad arguments");
   if (f->order.empty()) return fail(f, ACM_EINVAL, "empty forest");
   const AdjLayout L = adj_layout(f, nsteps, c);
   if (L.total == 0) return fail(f, ACM_EINVAL, "bad checkpoint policy");
   if (ws_bytes < L.total) return fail(f, ACM_ENOMEM, "adjoint workspace too small");
   const int64_t nb = (int64_t)f->order.size();
-  if (dU0 && n_elems != nb * 4 * (int64_t)f->gp.Bs * f->gp.Bs * f->gp.Bs)
+  if ((dU0 || vjp) && n_elems != nb * 4 * (int64_t)f->gp.Bs * f->gp.Bs * f->gp.Bs)
     return fail(f, ACM_EINVAL, "element count does not match n_blocks*4*Bs^3");
   char* base = reinterpret_cast<char*>(((uintptr_t)ws + 255) & ~(uintptr_t)255);
   auto R = [&](size_t off) { return reinterpret_cast<double*>(base + off); };
@@ -1190,12 +1195,20 @@ acm_status adjoint_sweep(acm_forest* f, int nsteps, double dt, int c, double wE,
   CK(cudaMemsetAsync(LAM, 0, L.reg, f->st));
   CK(cudaMemsetAsync(GCHI, 0, (size_t)f->gp.max_blocks * f->lay.FS * 8, f->st));
   CK(cudaMemsetAsync(TH, 0, 64, f->st));
+  if (vjp) {
+    // lam_N into LAM's interior points (a host array is staged in KAP, free until the first turn)
+    const double* src = on_device ? reinterpret_cast<const double*>(lamN) : KAP;
+    if (!on_device) CK(cudaMemcpyAsync(KAP, lamN, (size_t)n_elems * 8, cudaMemcpyHostToDevice, f->st));
+    acm::launch_adj_put<T>(Bs, src, LAM, f->d_blist, nb, f->st);
+    CKL();
+    ++f->launches;
+  }
   acm_status s;
   // J's terms are summed when a state is first reached (U_1, ..., U_N in that order)
   double J = 0.0;
   int hi = 0;
   auto reached = [&](int k) -> acm_status {
-    if (k <= hi) return ACM_OK;
+    if (vjp || k <= hi) return ACM_OK;
     double Fx, E;
     const acm_status r = force_energy<T>(f, &Fx, &E);
     if (r) return r;
@@ -1226,7 +1239,7 @@ acm_status adjoint_sweep(acm_forest* f, int nsteps, double dt, int c, double wE,
     f->time = tk;
     if ((s = rk4<T>(f, dt, nullptr, Y))) return s;
     if ((s = reached(k + 1))) return s;
-    if (k == nsteps - 1) objective(U, t0 + nsteps * dt);
+    if (k == nsteps - 1 && !vjp) objective(U, t0 + nsteps * dt);
     lin(KAP, dt / 6.0, LAM, 0.0, nullptr);
     if ((s = jgt(Y[3], tk + dt))) return s;
     lin(SUM, 1.0, NU, 0.0, nullptr);
@@ -1242,7 +1255,7 @@ acm_status adjoint_sweep(acm_forest* f, int nsteps, double dt, int c, double wE,
     lin(LAM, 1.0, LAM, 1.0, SUM);
     acm::launch_adj_fw_T<T>(Bs, LAM, f->d_blist, f->d_nbh, f->d_finer, nb, f->st);
     ++f->launches;
-    if (k >= 1) objective(TAPE, tk);
+    if (k >= 1 && !vjp) objective(TAPE, tk);
   }
   if (!plate) {
     acm::launch_adj_theta<T>(Bs, GCHI, f->d_blist, f->d_binfo, nb, f->phk, f->mask, TH, f->st);
@@ -1260,7 +1273,7 @@ acm_status adjoint_sweep(acm_forest* f, int nsteps, double dt, int c, double wE,
   CK(cudaMemcpyAsync(f->h_err, f->d_err, sizeof(int), cudaMemcpyDeviceToHost, f->st));
   CK(cudaStreamSynchronize(f->st));
   if ((s = device_error(f))) return s;
-  *J_out = J;
+  if (J_out) *J_out = J;
   if (dU0) {
     // FP64 gradient in block order; a host copy goes through the workspace's second register
     void* dense = on_device ? dU0 : reinterpret_cast<void*>(KAP);
@@ -1276,11 +1289,12 @@ acm_status adjoint_sweep(acm_forest* f, int nsteps, double dt, int c, double wE,
 // The sweep above, with the forest's state and time put back if it stops on an error once
 // U_0 is in snapshot 0 (the first action of every schedule; no step runs before it).
 acm_status adjoint_sphere(acm_forest* f, int nsteps, double dt, int c, double wE, void* ws, size_t ws_bytes,
-                          double* J_out, double* dtheta, void* dU0, int64_t n_elems, int on_device) {
+                          double* J_out, double* dtheta, void* dU0, int64_t n_elems, int on_device,
+                          const void* lamN = nullptr) {
   const double t0 = f->time;
   bool saved = false;
   const acm_status s = DISPATCH(f, adjoint_sweep, f, nsteps, dt, c, wE, ws, ws_bytes, J_out, dtheta, dU0, n_elems,
-                                on_device, &saved);
+                                on_device, lamN, &saved);
   if (s != ACM_OK && saved) {
     const AdjLayout L = adj_layout(f, nsteps, c);
     char* base = reinterpret_cast<char*>(((uintptr_t)ws + 255) & ~(uintptr_t)255);
@@ -1626,6 +1640,30 @@ acm_status acm_rk4_steps_batch(acm_forest* const* forests, int n, int nsteps, do
 size_t acm_adjoint_bytes(const acm_forest* f, int nsteps, int ckpt) {
   if (!f) return 0;
   return adj_layout(f, nsteps, ckpt).total;
+}
+
+acm_status acm_adjoint_vjp(acm_forest* f, int nsteps, double dt, int ckpt, void* ws, size_t ws_bytes,
+                           const void* dL_dUN, void* dL_dU0, int64_t n_elems, int on_device, double* dL_dtheta) {
+  if (!f) return ACM_EINVAL;
+  if (!dL_dUN || !dL_dU0) return fail(f, ACM_EINVAL, "bad arguments");
+  double th[4] = {0.0, 0.0, 0.0, 0.0};
+  const acm_status s = adjoint_sphere(f, nsteps, dt, ckpt, 0.0, ws, ws_bytes, nullptr, th, dL_dU0, n_elems,
+                                      on_device, dL_dUN);
+  if (s == ACM_OK && dL_dtheta)
+    for (int i = 0; i < (f->moving ? 1 : 4); ++i) dL_dtheta[i] = th[i];
+  return s;
+}
+
+acm_status acm_set_time(acm_forest* f, double t) {
+  if (!f || !std::isfinite(t)) return fail(f, ACM_EINVAL, "bad time");
+  f->time = t;
+  if (f->moving && !f->order.empty()) {
+    f->norms_fresh = false;
+    acm_status s = DISPATCH(f, eval_mask, f);
+    if (s) return s;
+    CK(cudaStreamSynchronize(f->st));
+  }
+  return ACM_OK;
 }
 
 acm_status acm_checkpoint_schedule(int nsteps, int ckpt, int32_t* snapshots, int64_t* advances, int8_t* ops,

@@ -228,8 +228,10 @@ void launch_adj_objective(int Bs, const T* U, const T* chi, double* lam, double*
 template <typename T>
 void launch_adj_theta(int Bs, const double* gchi, const int32_t* blist, const int4* binfo, int64_t n, const PhysK& ph,
                       const MaskK& m, double* out, cudaStream_t st);
-// Block-order copy (n, 4, Bs^3) of an FP64 register.
+// Block-order copy (n, 4, Bs^3) of an FP64 register, and its inverse (interior points only).
 template <typename T>
 void launch_adj_gather(int Bs, const double* r, double* dense, const int32_t* blist, int64_t n, cudaStream_t st);
+template <typename T>
+void launch_adj_put(int Bs, const double* dense, double* r, const int32_t* blist, int64_t n, cudaStream_t st);
 
 }  // namespace acm

@@ -123,3 +123,61 @@ def test_adjoint_through_autograd(A):
     assert np.allclose(th.grad.numpy()[:4], gth, rtol=0, atol=1e-12 * np.abs(gth).max())
     assert th.grad.numpy()[4] == 0.0
     assert np.allclose(U0.grad.numpy(), gU, rtol=0, atol=1e-12 * np.abs(gU).max())
+
+
+NV = 3
+
+
+@pytest.fixture(scope="module")
+def oracle_vjp():
+    S, delta = _setup()
+    fo = S.fo
+    order = fo.sorted_leaves()
+    rng = np.random.default_rng(23)
+    lamB = rng.normal(size=(len(order), 4, fo.M + 1, fo.M + 1, fo.M + 1))
+    lam = np.zeros_like(S.U)
+    for r, l in enumerate(order):
+        lam[fo.leaves[l]] = lamB[r]
+    adj = FrozenGridAdjoint(S, CENTRE, RADIUS, delta, dt=DT, nsteps=NV)
+    UN, g, gth = adj.vjp(S.U.copy(), lam)
+    return S, delta, lamB, UN, g, gth
+
+
+@pytest.mark.parametrize("ckpt", [dict(ckpt_every=2), dict(snapshots=1)])
+def test_vjp_matches_the_oracle(A, oracle_vjp, ckpt):
+    """dL/dU_0 and dL/d(centre, radius) of L = <lam, U_N> (3 steps, FP64, lam random on every
+    copy of every point) against the oracle's vector-Jacobian product, which is pinned by central
+    differences; the forest's state is unchanged."""
+    S, delta, lamB, UNo, go, gtho = oracle_vjp
+    f = _gpu_forest(A, S, delta, precision=64)
+    before = f.read_fields().copy()
+    gU, gth = f.adjoint_vjp(NV, DT, lamB, **ckpt)
+    assert np.array_equal(f.read_fields(), before) and f.diagnostics()["time"] == 0.0
+    fo = S.fo
+    gob = np.stack([go[fo.leaves[l]] for l in fo.sorted_leaves()])
+    a, b = _per_point(fo, gU, 2), _per_point(fo, gob, 2)
+    assert np.abs(a - b).max() <= 1e-10 * np.abs(b).max()
+    assert np.abs(gth - gtho).max() <= 1e-10 * np.abs(gtho).max(), (gth, gtho)
+
+
+def test_step_map_through_autograd(A, oracle_vjp):
+    """U_N of the autograd step map equals the forest's own steps and the oracle's; the gradient
+    of a loss of U_N equals the direct vector-Jacobian product (up to the order of FP64 atomic
+    sums); the forest is left at U_0 and time 0."""
+    import torch
+    S, delta, lamB, UNo, go, gtho = oracle_vjp
+    f = _gpu_forest(A, S, delta, precision=64)
+    Fn = A.step_map_function()
+    U0 = torch.tensor(block_order_fields(S), dtype=torch.float64, requires_grad=True)
+    th = torch.tensor([*CENTRE, RADIUS, delta], dtype=torch.float64, requires_grad=True)
+    W = torch.tensor(lamB)
+    UN = Fn.apply(f, U0, th, NV, DT, 2)
+    fo = S.fo
+    UNob = np.stack([UNo[fo.leaves[l]] for l in fo.sorted_leaves()])
+    assert np.abs(UN.detach().numpy() - UNob).max() <= 1e-12 * np.abs(UNob).max()
+    assert np.array_equal(f.read_fields(), block_order_fields(S)) and f.diagnostics()["time"] == 0.0
+    (UN * W).sum().backward()
+    gU, gth = f.adjoint_vjp(NV, DT, lamB, ckpt_every=2)
+    assert np.allclose(U0.grad.numpy(), gU, rtol=0, atol=1e-12 * np.abs(gU).max())
+    assert np.allclose(th.grad.numpy()[:4], gth, rtol=0, atol=1e-12 * np.abs(gth).max())
+    assert th.grad.numpy()[4] == 0.0
