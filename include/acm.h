@@ -260,11 +260,11 @@ acm_status acm_adjoint_plate_pitch(acm_forest* f, int nsteps, double dt, int ckp
 
 /* Vector-Jacobian product of the N-step map U_0 -> U_N (nsteps RK4 steps of fixed dt from the
  * current state and time on the frozen grid, the forward map and checkpointing of
- * acm_adjoint_sphere, sphere or moving-plate mask required): for any L with dL_dUN = dL/dU_N
+ * acm_adjoint_sphere; a sphere, a moving plate or no mask): for any L with dL_dUN = dL/dU_N
  * (FP64, block order, layout of acm_read_fields, n_elems = n_blocks*4*Bs^3, one value per copy
  * of a redundant point), writes dL_dU0 = dL/dU_0 (same layout; both arrays on the device if
  * on_device, else host) and, if dL_dtheta is not NULL, dL/d(cx, cy, cz, R) of the sphere (4
- * values) or dL/d alpha_m of the plate (1 value).  Workspace, restoration of the forest's state
+ * values), dL/d alpha_m of the plate (1 value) or 4 zeros without a mask.  Workspace, restoration of the forest's state
  * and time, and errors as acm_adjoint_sphere.  With it a caller composes the solver with any
  * loss of the final state (the Python binding's step_map_function does so for torch.autograd). */
 acm_status acm_adjoint_vjp(acm_forest* f, int nsteps, double dt, int ckpt, void* ws, size_t ws_bytes,

@@ -283,7 +283,8 @@ class FrozenGridAdjoint:
         self.S = solver
         self.fo = solver.fo
         self.ph = solver.ph
-        self.centre, self.R, self.delta = tuple(centre), R, delta
+        self.centre = None if centre is None else tuple(centre)
+        self.R, self.delta = R, delta
         self.dt, self.N, self.c, self.we = dt, nsteps, checkpoint_every, w_energy
         self.mats = SyncMatrices(self.fo)
         M = self.fo.M
@@ -412,7 +413,7 @@ class FrozenGridAdjoint:
         the gradient's without the objective's direct terms, from lam = lamN; the states are
         recomputed with `snapshots` stored states (default: all of them)."""
         N = self.N
-        gchi = {s: np.zeros_like(self.S.chi[s]) for s in self.fo.leaves.values()}
+        gchi = {s: np.zeros_like(U0[s][0]) for s in self.fo.leaves.values()}
         st = {"lam": lamN.copy(), "UN": None}
 
         def advance(U, k):
@@ -427,8 +428,10 @@ class FrozenGridAdjoint:
         return st["UN"], st["lam"], self._theta(gchi)
 
     def _theta(self, gchi):
-        """dJ/d(cx, cy, cz, R) from the mask gradient."""
+        """dJ/d(cx, cy, cz, R) from the mask gradient (zero without a sphere: centre None)."""
         gtheta = np.zeros(4)
+        if self.centre is None:
+            return gtheta
         for leaf, s in self.fo.leaves.items():
             X, Y, Z = acm.block_coords(self.fo, leaf)
             dchi = sphere_mask_grad(X, Y, Z, self.centre, self.R, self.delta)

@@ -1130,7 +1130,11 @@ acm_status adjoint_sweep(acm_forest* f, int nsteps, double dt, int c, double wE,
   // with lamN (dL/dU_N, block order, FP64, on the device if on_device) the sweep is the
   // vector-Jacobian product of the N-step map: lam starts from lamN, no objective terms
   const bool vjp = lamN != nullptr;
-  if (!f->mask_on || (!plate && f->mask.kind != 1)) return fail(f, ACM_EINVAL, "the adjoint needs a sphere or plate mask");
+  // the objective's force needs a body; the vector-Jacobian product also runs without a mask
+  if ((!vjp && !f->mask_on) || (f->mask_on && !plate && f->mask.kind != 1))
+    return fail(f, ACM_EINVAL, "the adjoint needs a sphere or plate mask");
+  acm::MaskK mk = f->mask;
+  if (!f->mask_on) mk.kind = 0;                    // no body: no mask parameter to differentiate
   if (nsteps < 1 || c == 0 || !(dt > 0) || !ws || !dtheta || (!vjp && !J_out) || (vjp && !dU0))
     return fail(f, ACM_EINVAL, "bad arguments");
   if (f->order.empty()) return fail(f, ACM_EINVAL, "empty forest");
@@ -1178,14 +1182,14 @@ acm_status adjoint_sweep(acm_forest* f, int nsteps, double dt, int c, double wE,
     pose_at(ts);
     CK(cudaMemsetAsync(NU, 0, L.reg, f->st));
     acm::launch_adj_jgt<T>(Bs, Ys, KAP, CHI, GCHI, WGT, NU, f->d_blist, f->d_binfo, f->d_nbh, f->d_finer, nb, f->phk,
-                           f->mask, TH, f->d_err, f->st);
+                           mk, TH, f->d_err, f->st);
     f->launches += 3;
     return cudaGetLastError() == cudaSuccess ? ACM_OK : fail(f, ACM_ECUDA, "adjoint kernel launch failed");
   };
   auto objective = [&](const T* Us, double tn) {
     pose_at(tn);
     acm::launch_adj_objective<T>(Bs, Us, CHI, LAM, GCHI, f->d_blist, f->d_binfo, nb, f->phk, 1.0 / nsteps, wE,
-                                 f->mask, TH, f->st);
+                                 mk, TH, f->st);
     ++f->launches;
   };
   acm::ckpt::Schedule sched;
@@ -1257,8 +1261,8 @@ acm_status adjoint_sweep(acm_forest* f, int nsteps, double dt, int c, double wE,
     ++f->launches;
     if (k >= 1 && !vjp) objective(TAPE, tk);
   }
-  if (!plate) {
-    acm::launch_adj_theta<T>(Bs, GCHI, f->d_blist, f->d_binfo, nb, f->phk, f->mask, TH, f->st);
+  if (!plate && f->mask_on) {
+    acm::launch_adj_theta<T>(Bs, GCHI, f->d_blist, f->d_binfo, nb, f->phk, mk, TH, f->st);
     ++f->launches;
   }
   CKL();
@@ -1650,7 +1654,7 @@ acm_status acm_adjoint_vjp(acm_forest* f, int nsteps, double dt, int ckpt, void*
   const acm_status s = adjoint_sphere(f, nsteps, dt, ckpt, 0.0, ws, ws_bytes, nullptr, th, dL_dU0, n_elems,
                                       on_device, dL_dUN);
   if (s == ACM_OK && dL_dtheta)
-    for (int i = 0; i < (f->moving ? 1 : 4); ++i) dL_dtheta[i] = th[i];
+    for (int i = 0; i < (f->moving ? 1 : 4); ++i) dL_dtheta[i] = f->mask_on ? th[i] : 0.0;
   return s;
 }
 

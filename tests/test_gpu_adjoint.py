@@ -181,3 +181,38 @@ def test_step_map_through_autograd(A, oracle_vjp):
     assert np.allclose(U0.grad.numpy(), gU, rtol=0, atol=1e-12 * np.abs(gU).max())
     assert np.allclose(th.grad.numpy()[:4], gth, rtol=0, atol=1e-12 * np.abs(gth).max())
     assert th.grad.numpy()[4] == 0.0
+
+
+def test_vjp_without_a_mask_matches_the_oracle(A):
+    """The vector-Jacobian product of a flow without a body (sponge only; 2 steps, FP64) against
+    the oracle's, which is pinned by central differences."""
+    from oracle import acm as oacm
+    from oracle.adapt import Solver
+    from oracle.forest import Forest as OForest
+    from tests.test_oracle_adjoint import _field
+    leaves = random_graded_leaves(41, nroot=(2, 1, 1), J0=1, Jmax=2, n_target=18)
+    fo = OForest(nroot=(2, 1, 1), root_len=1.0, Bs=9, Jmin=1, Jmax=2, max_blocks=256)
+    fo.set_leaves(leaves)
+    delta = 1.5 * fo.h(2)
+    S = Solver(fo, oacm.Physics(nu=1e-2, c0=3.0, C_eta=1e-2, C_gamma=0.5, C_sp=0.05, u_inf=(1.0, 0.0, 0.0)),
+               ic=lambda X, Y, Z: _field(X, Y, Z, 41),
+               sponge=lambda X, Y, Z: oacm.sponge_mask(X, Y, Z, L, 0.2, delta))
+    S.eval_ic()
+    S.eval_mask()
+    order = fo.sorted_leaves()
+    lamB = np.random.default_rng(29).normal(size=(len(order), 4, 9, 9, 9))
+    lam = np.zeros_like(S.U)
+    for r, l in enumerate(order):
+        lam[fo.leaves[l]] = lamB[r]
+    _, go, _ = FrozenGridAdjoint(S, None, None, None, dt=DT, nsteps=2).vjp(S.U.copy(), lam)
+    grid = dict(nroot=(2, 1, 1), root_len=1.0, Bs=9, g=4, Jmin=1, Jmax=2, precision=64, max_blocks=256, fd_scheme=1)
+    phys = dict(nu=1e-2, c0=3.0, C_eta=1e-2, C_gamma=0.5, C_sp=0.05, u_inf=(1.0, 0.0, 0.0), p_inf=0.0,
+                sponge=1, sponge_L=L, sponge_width=0.2, sponge_delta=delta)
+    f = A.Forest(grid, phys)
+    f.set_leaves(leaves)
+    f.write_fields(block_order_fields(S))
+    gU, gth = f.adjoint_vjp(2, DT, lamB, snapshots=1)
+    assert not gth.any()
+    gob = np.stack([go[fo.leaves[l]] for l in order])
+    a, b = _per_point(fo, gU, 2), _per_point(fo, gob, 2)
+    assert np.abs(a - b).max() <= 1e-10 * np.abs(b).max()

@@ -242,3 +242,43 @@ def test_vector_jacobian_product_against_central_differences():
     UN2, g2, gth2 = adj.vjp(U0, lam, snapshots=1)
     assert adj.last_advances == 3
     assert np.array_equal(UN2, UN) and np.array_equal(g2, g) and np.array_equal(gth2, gth)
+
+
+def test_vector_jacobian_product_without_a_mask():
+    """The same product for a flow without a body (sponge only): central differences of
+    L = <lam, U_N> in a random direction of U_0."""
+    leaves = random_graded_leaves(41, nroot=(2, 1, 1), J0=1, Jmax=2, n_target=18)
+    fo = Forest(nroot=(2, 1, 1), root_len=1.0, Bs=9, Jmin=1, Jmax=2, max_blocks=256)
+    fo.set_leaves(leaves)
+    delta = 1.5 * fo.h(2)
+    ph = acm.Physics(nu=1e-2, c0=3.0, C_eta=1e-2, C_gamma=0.5, C_sp=0.05, u_inf=(1.0, 0.0, 0.0))
+
+    def make():
+        S = Solver(fo, ph, ic=lambda X, Y, Z: _field(X, Y, Z, 41),
+                   sponge=lambda X, Y, Z: acm.sponge_mask(X, Y, Z, L, 0.2, delta))
+        S.eval_ic()
+        S.eval_mask()
+        return S
+
+    S = make()
+    dt, N = 2e-3, 2
+    adj = FrozenGridAdjoint(S, None, None, None, dt=dt, nsteps=N)
+    U0 = S.U.copy()
+    sl = adj.mats.slots
+    rng = np.random.default_rng(13)
+    lam = np.zeros_like(U0)
+    lam[sl] = rng.normal(size=lam[sl].shape)
+    _, g, gth = adj.vjp(U0, lam)
+    assert not gth.any()
+    h = 1e-4
+    v = np.zeros_like(U0)
+    v[sl] = rng.normal(size=v[sl].shape)
+    vals = []
+    for sgn in (1, -1):
+        T = make()
+        T.U = U0 + sgn * h * v
+        for _ in range(N):
+            T.rk4(dt)
+        vals.append(float((lam[sl] * T.U[sl]).sum()))
+    fd = (vals[0] - vals[1]) / (2 * h)
+    assert abs(fd - float((g * v).sum())) <= 1e-7 * abs(fd)
