@@ -365,3 +365,41 @@ def test_refine_then_cdf44_coarsen_restores_any_field(A, prec, Bs):
     err = np.abs(f.read_fields().astype(np.float64) - before).max() / np.abs(before).max()
     # FP32: rounding amplified by the summed weights of the prediction and the low-pass (~8 in 3D)
     assert err < (1e-13 if prec == 64 else 5e-6), err
+
+
+@pytest.mark.parametrize("prec,Bs", [(64, 9), (64, 17), (32, 9)])
+def test_single_block_is_its_own_neighbour(A, prec, Bs):
+    """The degenerate grid of one root at level 0: every one of the only block's 26 periodic
+    neighbours is the block itself.  Neighbour table, two RK4 steps with a sphere mask, refinement
+    to 8 blocks and coarsening back to the single block (dealiasing tags every finest block),
+    against the oracle."""
+    grid = _grid(Bs=Bs, nroot=(1, 1, 1), Jmin=0, Jmax=1, precision=prec, max_blocks=16)
+    phys = _phys(eps=1e30, dealias=1)
+    mask = (0.45, 0.5, 0.55, 0.2, 0.1)
+    f = A.Forest(grid, phys)
+    f.set_leaves([(0, 0, 0, 0)])
+    fo = oracle_forest(grid, leaves=[(0, 0, 0, 0)], max_blocks=16)
+    S = oracle_solver(fo, phys, mask=sphere_fn(mask))
+    fill_from_function(S, lambda X, Y, Z: smooth_field(X, Y, Z, (1.0, 1.0, 1.0), 21))
+    S.eval_mask()
+    f.set_mask(A.ACM_MASK_SPHERE, mask)
+    f.write_fields(block_order_fields(S))
+    t = f.topology()
+    tc, lv, sl, nbr, rel = fo.topology()
+    assert np.array_equal(t["nbr"], nbr) and np.array_equal(t["rel"], rel)
+    dt = 2e-3 if Bs == 9 else 1e-3
+    for _ in range(2):
+        f.rk4_step(dt)
+        S.rk4(dt)
+    err = rel_linf(f.read_fields().astype(np.float64), block_order_fields(S))
+    assert max(err) < TOL[prec], err
+    f.refine_all()
+    S.refine_all()
+    assert f.n_blocks() == len(S.fo.leaves) == 8
+    err = rel_linf(f.read_fields().astype(np.float64), block_order_fields(S))
+    assert max(err) < TOL[prec], err
+    nb, npass = f.coarsen()
+    S.coarsen()
+    assert nb == len(S.fo.leaves) == 1 and npass == 1
+    err = rel_linf(f.read_fields().astype(np.float64), block_order_fields(S))
+    assert max(err) < TOL[prec], err
