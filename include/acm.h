@@ -8,7 +8,9 @@
  * that refines and coarsens the grid.  Beyond that path: RK4 steps replayed from CUDA graphs and
  * many instances per graph (acm_rk4_steps, acm_rk4_steps_batch), an autotuner (acm_autotune),
  * the lifted CDF 4/4 wavelet for coarsening (acm_grid_params.wavelet), a moving rigid plate
- * (ACM_MASK_PLATE) and a discrete adjoint on a frozen grid (acm_adjoint_*).
+ * (ACM_MASK_PLATE), a discrete adjoint on a frozen grid (acm_adjoint_*, with equidistant or
+ * binomial checkpointing, acm_checkpoint_schedule, and a vector-Jacobian product of the step
+ * map) and restart files (acm_save_state, acm_load_state).
  *
  * Conventions (all entry points):
  *  - Every call returns an acm_status; nothing throws across the ABI.  On an error the forest
@@ -23,6 +25,10 @@
  *    that return host-visible results (dt, diagnostics, topology, indicators) synchronise
  *    that stream before returning; the others may return while their kernels still run, and
  *    a device error then surfaces at the next synchronising call.
+ *  - Devices: a forest belongs to the CUDA device current when it is created (its pool and
+ *    stream must be on that device); every call on it must be made with that device current.
+ *    The library never switches devices.  Forests on several devices may coexist in one
+ *    process.
  *  - Pointers passed in are borrowed for the duration of the call only.
  *  - Layouts: "block order" is ascending (treecode, level); a field array is block-major,
  *    then component (u, v, w, p), then z, y, x with x fastest, Bs^3 points per block, in the

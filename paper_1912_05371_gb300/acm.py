@@ -154,7 +154,9 @@ def max_norms_noalloc(fields, n_blocks, Bs, precision, norms_out, stream=None):
 
 class Forest:
     """One forest of the C library.  ``pool`` is a torch uint8 CUDA tensor (allocated here from
-    the size the library asks for) kept alive for the forest's lifetime."""
+    the size the library asks for) kept alive for the forest's lifetime.  The forest belongs to
+    ``device`` (default: the current one); call its methods with that device current
+    (``torch.cuda.device(...)``), as the library uses the current device."""
 
     def __init__(self, grid: dict, phys: dict, stream=None, device=None):
         import torch
@@ -198,8 +200,9 @@ class Forest:
         self.stream = stream if stream is not None else torch.cuda.current_stream(dev)
         self.pool = torch.empty(nbytes, dtype=torch.uint8, device=dev)
         h = C.c_void_p()
-        self._check(self.L.acm_create_forest(C.byref(g), C.byref(p), C.c_void_p(self.stream.cuda_stream),
-                                             C.c_void_p(self.pool.data_ptr()), nbytes, C.byref(h)), None)
+        with torch.cuda.device(dev):
+            self._check(self.L.acm_create_forest(C.byref(g), C.byref(p), C.c_void_p(self.stream.cuda_stream),
+                                                 C.c_void_p(self.pool.data_ptr()), nbytes, C.byref(h)), None)
         self.h = h
 
     def _check(self, st, h="self"):

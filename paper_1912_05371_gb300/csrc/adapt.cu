@@ -5,6 +5,7 @@
 // (refine by prediction, coarsen by merging sister blocks), Sec. 4.2 (ghost synchronisation:
 // restrict or predict, then copy), Sec. 2.2 (smoothed mask, force by midpoint rule).
 #include <algorithm>
+#include <atomic>
 
 #include "common.cuh"
 #include "kernels.hpp"
@@ -14,6 +15,18 @@ namespace acm {
 namespace {
 
 constexpr int kNT = 256;
+
+// Opt `kernel` in to `bytes` of dynamic shared memory (above the default 48 KB) on the current
+// device, once per device (the attribute belongs to the device's context).
+template <typename K>
+void smem_opt_in(K kernel, size_t bytes, std::atomic<unsigned long long>& done) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
+  const unsigned long long bit = 1ull << dev;
+  if (done.load(std::memory_order_relaxed) & bit) return;
+  cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  done.fetch_or(bit);
+}
 
 template <typename T>
 __device__ __forceinline__ T tabs(T v) { return v < T(0) ? -v : v; }
@@ -1374,11 +1387,8 @@ void launch_fine_wins(int Bs, T* reg, const int2* tasks, const int32_t* ntasks, 
 template <typename T, int BS>
 void launch_coarse_slabs_bs(const T* reg, T* slab, const int4* tasks, const int32_t* ntasks, int64_t max_tasks,
                             const int32_t* nbh, uint32_t* offc, int use_cache, int ctas_per_sm, cudaStream_t st) {
-  static bool attr = false;             // opt in to more than 48 KB of dynamic shared memory once
-  if (!attr) {
-    cudaFuncSetAttribute(k_coarse_slabs<T, BS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SlabSmem<T, BS>::bytes);
-    attr = true;
-  }
+  static std::atomic<unsigned long long> opted{0};   // devices whose context has the opt-in
+  smem_opt_in(k_coarse_slabs<T, BS>, SlabSmem<T, BS>::bytes, opted);
   // CTAs walking the task list: ctas_per_sm per SM (at most 3 are resident for Bs = 17)
   const int64_t g = std::min<int64_t>(max_tasks, (int64_t)std::max(1, ctas_per_sm) * sm_count());
   k_coarse_slabs<T, BS><<<grid1(g), SlabSmem<T, BS>::NT, SlabSmem<T, BS>::bytes, st>>>(reg, slab, tasks, ntasks, nbh,
@@ -1400,11 +1410,8 @@ void launch_sync_ext(int Bs, const T* reg, T* out, int g, const int32_t* list, i
 template <typename T, int BS>
 void launch_details_bs(const T* reg, const T* chi, const int32_t* blist, const int32_t* ranks, const int32_t* nbh,
                        int64_t n, const unsigned long long* norm_bits, double* ind, double* chirange, cudaStream_t st) {
-  static bool attr = false;             // opt in to more than 48 KB of dynamic shared memory once
-  if (!attr) {
-    cudaFuncSetAttribute(k_details<T, BS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DetSmem<T, BS>::bytes);
-    attr = true;
-  }
+  static std::atomic<unsigned long long> opted{0};   // devices whose context has the opt-in
+  smem_opt_in(k_details<T, BS>, DetSmem<T, BS>::bytes, opted);
   k_details<T, BS><<<grid1(n), DetSmem<T, BS>::NT, DetSmem<T, BS>::bytes, st>>>(reg, chi, blist, ranks, nbh,
                                                                               norm_bits, ind, chirange);
 }
@@ -1424,11 +1431,8 @@ void launch_maxnorm(int Bs, const T* reg, const int32_t* blist, int64_t n, unsig
 template <typename T, int BS>
 void launch_refine_bs(const T* src, T* dst, const int32_t* tasks, int64_t n, const int32_t* blist,
                       const int32_t* nbh, cudaStream_t st) {
-  static bool attr = false;             // opt in to more than 48 KB of dynamic shared memory once
-  if (!attr) {
-    cudaFuncSetAttribute(k_refine<T, BS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RefSmem<T, BS>::bytes);
-    attr = true;
-  }
+  static std::atomic<unsigned long long> opted{0};   // devices whose context has the opt-in
+  smem_opt_in(k_refine<T, BS>, RefSmem<T, BS>::bytes, opted);
   k_refine<T, BS><<<grid1(4 * n), RefSmem<T, BS>::NT, RefSmem<T, BS>::bytes, st>>>(src, dst, tasks, blist, nbh);
 }
 template <typename T>
@@ -1446,11 +1450,8 @@ void launch_coarsen(int Bs, const T* src, T* dst, const int32_t* tasks, int64_t 
 }
 template <typename T, int BS>
 void launch_coarsen44_bs(const T* src, T* dst, const int32_t* tasks, int64_t n, const int32_t* nbh, cudaStream_t st) {
-  static bool attr = false;             // opt in to more than 48 KB of dynamic shared memory once
-  if (!attr) {
-    cudaFuncSetAttribute(k_coarsen44<T, BS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C44Smem<T, BS>::bytes);
-    attr = true;
-  }
+  static std::atomic<unsigned long long> opted{0};   // devices whose context has the opt-in
+  smem_opt_in(k_coarsen44<T, BS>, C44Smem<T, BS>::bytes, opted);
   k_coarsen44<T, BS><<<grid1(n), C44Smem<T, BS>::NT, C44Smem<T, BS>::bytes, st>>>(src, dst, tasks, nbh);
 }
 template <typename T>
