@@ -330,6 +330,25 @@ class MovingPlateAdjoint:
                     ga += self._direct(states[n - a], self.t0 + n * dt, lam)
         return J, lam, ga
 
+    def vjp(self, U0, lamN, snapshots=None):
+        """For L = <lamN, U_N> (lamN in the register layout): (U_N, dL/dU_0, dL/d alpha_m), the
+        gradient's sweep without the objective's direct terms, from lam = lamN; the states are
+        recomputed with `snapshots` stored states (default: all of them)."""
+        dt, N = self.dt, self.N
+        st = {"lam": lamN.copy(), "ga": 0.0, "UN": None}
+
+        def advance(U, k):
+            return self._step(U, self.t0 + k * dt)[0]
+
+        def turn(U, k):
+            if k == N - 1:
+                st["UN"] = self._step(U, self.t0 + k * dt)[0]
+            st["lam"], g_step = self._step_adjoint(U, self.t0 + k * dt, st["lam"])
+            st["ga"] += g_step
+
+        self.last_advances = reverse(N, snapshots or N, U0, advance, turn)
+        return st["UN"], st["lam"], st["ga"]
+
     def _gradient_binomial(self, U0, snapshots):
         """As ``gradient``, the states recomputed by ``oracle.checkpointing.reverse``; the
         objective's terms are summed when a state is first reached."""

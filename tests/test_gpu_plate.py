@@ -102,3 +102,41 @@ def test_moving_plate_adjoint_matches_oracle(A, ckpt):
     assert abs(J - Jo) <= 1e-12 * abs(Jo), (J, Jo)
     assert abs(ga - gao) <= 1e-10 * abs(gao), (ga, gao)
     assert np.abs(a - b).max() <= 1e-10 * np.abs(b).max()
+
+
+def test_moving_plate_vjp_matches_oracle(A):
+    """The vector-Jacobian product of 2 steps of the moving case (FP64, 8 blocks of 9^3, random
+    lam on every copy of every point, binomial checkpointing with one snapshot): dL/dU_0 per
+    physical point and dL/d alpha_m against the oracle's product, which is pinned by central
+    differences."""
+    from oracle.forest import Forest as OForest
+    from oracle.plate import MovingPlateAdjoint
+    from tests.test_gpu_adjoint import _per_point
+    P = dict(chord=0.3, span=0.35, thickness=0.1, phi_m=math.radians(60.0), alpha_m=math.radians(45.0), freq=1.0,
+             root=(0.5, 0.5, 0.5), delta=0.06)
+    ic = lambda X, Y, Z: np.stack([np.sin(2 * math.pi * Y), 0.3 * np.cos(2 * math.pi * Z),
+                                   0.2 * np.sin(2 * math.pi * X), 0.0 * X])
+    fo = OForest(nroot=(1, 1, 1), root_len=1.0, Bs=9, Jmin=1, Jmax=1, max_blocks=16)
+    fo.init_uniform(1)
+    S = MovingSolver(fo, oacm.Physics(nu=1e-2, c0=3.0, C_eta=1e-2, C_gamma=0.5), Plate(**P), ic=ic)
+    S.eval_ic()
+    S.eval_mask()
+    order = fo.sorted_leaves()
+    lamB = np.random.default_rng(31).normal(size=(len(order), 4, 9, 9, 9))
+    lam = np.zeros_like(S.U)
+    for r, l in enumerate(order):
+        lam[fo.leaves[l]] = lamB[r]
+    dt, n = 2e-3, 2
+    _, go, gao = MovingPlateAdjoint(S, dt, n).vjp(S.U.copy(), lam)
+    grid = dict(nroot=(1, 1, 1), root_len=1.0, Bs=9, g=4, Jmin=1, Jmax=1, precision=64, max_blocks=16, fd_scheme=1)
+    f = A.Forest(grid, dict(nu=1e-2, c0=3.0, C_eta=1e-2, C_gamma=0.5, cfl=0.5))
+    f.init_uniform(1)
+    f.write_fields(block_order_fields(S))
+    f.set_mask(A.ACM_MASK_PLATE, [P["chord"], P["span"], P["thickness"], P["phi_m"], P["alpha_m"], P["freq"],
+                                  *P["root"], P["delta"]])
+    gU, gth = f.adjoint_vjp(n, dt, lamB, snapshots=1)
+    assert f.diagnostics()["time"] == 0.0
+    gob = np.stack([go[fo.leaves[l]] for l in order])
+    a, b = _per_point(fo, gU, 1), _per_point(fo, gob, 1)
+    assert np.abs(a - b).max() <= 1e-10 * np.abs(b).max()
+    assert abs(gth[0] - gao) <= 1e-10 * abs(gao), (gth[0], gao)

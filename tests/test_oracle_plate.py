@@ -216,3 +216,41 @@ def test_moving_adjoint_against_central_differences():
     J3, gU3, ga3 = adj1.gradient(U0, snapshots=1)
     assert adj1.last_advances == 1
     assert J3 == J and np.array_equal(gU3, gU) and ga3 == ga
+
+
+def test_moving_vector_jacobian_product_against_central_differences():
+    """L = <lam, U_N> over 2 steps of the moving case, random lam: the oracle's product against
+    central differences of L through the moving solver's own steps, in the pitch amplitude and
+    in a random direction of U_0; binomial checkpointing gives it bitwise."""
+    from oracle.plate import MovingPlateAdjoint
+    dt, n = 2e-3, 2
+    S = _moving_case()
+    adj = MovingPlateAdjoint(S, dt, n)
+    U0 = S.U.copy()
+    sl = sorted(S.fo.leaves.values())
+    rng = np.random.default_rng(17)
+    lam = np.zeros_like(U0)
+    lam[sl] = rng.normal(size=lam[sl].shape)
+    UN, g, ga = adj.vjp(U0, lam)
+
+    def L(T):
+        for _ in range(n):
+            T.rk4(dt)
+        return float((lam[sl] * T.U[sl]).sum())
+
+    assert L(_moving_case()) == float((lam[sl] * UN[sl]).sum())
+    h = 1e-4
+    a0 = math.radians(45.0)
+    fd = (L(_moving_case(a0 + h)) - L(_moving_case(a0 - h))) / (2 * h)
+    assert abs(fd - ga) <= 1e-6 * abs(fd), (fd, ga)             # agreement 1.7e-8
+    d = np.zeros_like(U0)
+    d[sl] = rng.normal(size=d[sl].shape)
+    vals = []
+    for sgn in (1, -1):
+        T = _moving_case()
+        T.U = U0 + sgn * h * d
+        vals.append(L(T))
+    fdu = (vals[0] - vals[1]) / (2 * h)
+    assert abs(fdu - float((g * d).sum())) <= 1e-7 * abs(fdu)
+    UN2, g2, ga2 = MovingPlateAdjoint(_moving_case(), dt, n).vjp(U0, lam, snapshots=1)
+    assert np.array_equal(UN2, UN) and np.array_equal(g2, g) and ga2 == ga
