@@ -104,6 +104,11 @@ typedef struct {
   double sponge_L[3];     /* periodic box lengths used by the sponge profile               */
   double sponge_width;    /* L_sp: sponge thickness at each box face                        */
   double sponge_delta;    /* smoothing length of the sponge profile                         */
+  int coarsen_everywhere; /* 0: tags by thresholds (Sec. 3.3); 1: the performance cycle of
+                             Sec. 5.4 ("coarsen everywhere" on random data): every block made by
+                             the last acm_refine_all is tagged and the thresholds are ignored,
+                             so acm_coarsen restores the grid the step started from (the
+                             indicators are still computed; acm_init_grid always thresholds) */
 } acm_phys_params;
 
 /* Per-step diagnostics (Sec. 2.2 force by midpoint rule; every physical point counted once:

@@ -37,9 +37,14 @@ class Solver:
     """State of one simulation: forest, register U (slot-indexed) and the analytic mask."""
 
     def __init__(self, forest: Forest, ph: acm.Physics, eps=1e-3, dealias=True,
-                 mask_thr=1e-5, ic=None, mask=None, sponge=None, wavelet="cdf40"):
+                 mask_thr=1e-5, ic=None, mask=None, sponge=None, wavelet="cdf40", coarsen_everywhere=False):
         assert wavelet in ("cdf40", "cdf44")
         self.wavelet = wavelet
+        # the performance cycle of Sec. 5.4 ("coarsen everywhere" on random data): instead of
+        # thresholding, every block made by the last refine_all is tagged, so coarsening
+        # restores the grid the step started from (reading: a block goes back at most one level)
+        self.coarsen_everywhere = coarsen_everywhere
+        self.last_refined = set()
         self.fo = forest
         self.ph = ph
         self.eps, self.dealias, self.mask_thr = eps, dealias, mask_thr
@@ -206,8 +211,13 @@ class Solver:
         norms = self.norms()
         npass = 0
         for _ in range(max_passes):
-            ind, ext = self.indicators(norms)
-            groups = self.coarsenable_groups(self.tags(ind))
+            if self.coarsen_everywhere:
+                tags = {l: l[0] > 0 and (l[0] - 1, l[1] >> 1, l[2] >> 1, l[3] >> 1) in self.last_refined
+                        for l in self.fo.leaves}
+            else:
+                ind, ext = self.indicators(norms)
+                tags = self.tags(ind)
+            groups = self.coarsenable_groups(tags)
             if not groups:
                 break
             src = self.U.copy()
@@ -223,6 +233,7 @@ class Solver:
         M = fo.M
         half = M // 2
         parents = [l for l in fo.sorted_leaves() if l[0] < fo.Jmax]
+        self.last_refined = set(parents)
         if not parents:
             return
         g = 2

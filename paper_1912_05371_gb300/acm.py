@@ -30,7 +30,8 @@ class PhysParams(C.Structure):
                 ("C_sp", C.c_double), ("u_inf", C.c_double * 3), ("p_inf", C.c_double),
                 ("cfl", C.c_double), ("cfl_eta", C.c_double), ("cfl_nu", C.c_double), ("eps", C.c_double),
                 ("dealias", C.c_int), ("mask_range_thr", C.c_double), ("sponge", C.c_int),
-                ("sponge_L", C.c_double * 3), ("sponge_width", C.c_double), ("sponge_delta", C.c_double)]
+                ("sponge_L", C.c_double * 3), ("sponge_width", C.c_double), ("sponge_delta", C.c_double),
+                ("coarsen_everywhere", C.c_int)]
 
 
 class Diag(C.Structure):
@@ -190,6 +191,7 @@ class Forest:
         p.sponge_L = (C.c_double * 3)(*phys.get("sponge_L", (1.0, 1.0, 1.0)))
         p.sponge_width = phys.get("sponge_width", 0.0)
         p.sponge_delta = phys.get("sponge_delta", 1.0)
+        p.coarsen_everywhere = int(phys.get("coarsen_everywhere", 0))
         self.grid, self.phys = g, p
         self.Bs = g.Bs
         self.dtype = np.float64 if g.precision == 64 else np.float32

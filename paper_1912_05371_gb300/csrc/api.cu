@@ -11,6 +11,7 @@
 #include <cstring>
 #include <memory>
 #include <string>
+#include <unordered_set>
 #include <vector>
 
 #include "../../include/acm.h"
@@ -94,6 +95,8 @@ struct acm_forest {
   std::vector<int32_t> slot_rank;     // slot -> rank (-1: free)
   std::vector<double> ind_slot, chr_slot;   // indicators of the current coarsening, by slot
   bool leaves_stale = false;          // fo->leaves lags behind (order, blist)
+  // parents refined by the last acm_refine_all (tags of the coarsen-everywhere cycle)
+  std::unordered_set<BoxKey, acm::BoxKeyHash> last_refined;
   int4* h_binfo = nullptr;
   int32_t* h_blist = nullptr;
   uint8_t* h_finer = nullptr;
@@ -682,12 +685,14 @@ acm_status refine_all(acm_forest* f) {
       prank.push_back((int32_t)r);
       pslot.push_back(f->blist[r]);
     }
+  f->last_refined.clear();
   if (prank.empty()) return ACM_OK;
   // children in ascending key order (each parent's children 0..7 in turn) take the lowest free
   // slots once the parents' slots are released
   std::vector<int32_t> new_slot;
   if (!fo.take_slots(pslot, prank.size() * 8, &new_slot))
     return fail(f, ACM_ECAPACITY, "block pool too small to refine");
+  for (int32_t r : prank) f->last_refined.insert(f->order[(size_t)r]);
   std::vector<int32_t> tasks(prank.size() * 9);
   for (size_t i = 0; i < prank.size(); ++i) {
     tasks[9 * i] = prank[i];
@@ -812,7 +817,9 @@ acm_status coarsen(acm_forest* f, int64_t* n_blocks, int* n_passes) {
     for (size_t r = 0; r < n; ++r) {
       const BoxKey& b = f->order[r];
       bool t = false;
-      if (b.J > fo.Jmin) {
+      if (f->pp.coarsen_everywhere) {
+        t = b.J > 0 && f->last_refined.count(BoxKey{b.J - 1, b.x >> 1, b.y >> 1, b.z >> 1}) > 0;
+      } else if (b.J > fo.Jmin) {
         if (f->pp.dealias && b.J == fo.Jmax) t = true;
         else t = (ind[r] < f->pp.eps) && !(chr[r] > f->pp.mask_range_thr);
       }
@@ -1409,6 +1416,7 @@ acm_status acm_set_leaves(acm_forest* f, const int32_t* level, const int32_t* gx
   if (!f || !level || !gx || !gy || !gz || n <= 0) return fail(f, ACM_EINVAL, "bad leaves");
   if (n > f->gp.max_blocks) return fail(f, ACM_ECAPACITY, "more leaves than max_blocks");
   f->norms_fresh = false;
+  f->last_refined.clear();
   acm::Forest trial(f->gp.nroot, f->gp.Bs, f->gp.Jmin, f->gp.Jmax, f->gp.max_blocks);
   std::vector<BoxKey> created((size_t)n);
   for (int64_t i = 0; i < n; ++i) {
@@ -1727,8 +1735,8 @@ acm_status acm_step(acm_forest* f, double dt, double* dt_used, int64_t* n_blocks
   return acm_coarsen(f, n_blocks, nullptr);
 }
 
-acm_status acm_init_grid(acm_forest* f, int ic_kind, const double* params, int n, int64_t* n_blocks) {
-  if (!f) return ACM_EINVAL;
+static acm_status init_grid_thresholded(acm_forest* f, int ic_kind, const double* params, int n,
+                                        int64_t* n_blocks) {
   acm_status s = acm_init_uniform(f, f->gp.Jmin);
   if (s) return s;
   s = acm_set_ic(f, ic_kind, params, n);
@@ -1749,6 +1757,16 @@ acm_status acm_init_grid(acm_forest* f, int ic_kind, const double* params, int n
     }
   }
   return fail(f, ACM_EINVAL, "initial grid did not converge");
+}
+
+acm_status acm_init_grid(acm_forest* f, int ic_kind, const double* params, int n, int64_t* n_blocks) {
+  if (!f) return ACM_EINVAL;
+  // the initial grid follows the thresholds whatever the coarsening mode
+  const int everywhere = f->pp.coarsen_everywhere;
+  f->pp.coarsen_everywhere = 0;
+  const acm_status s = init_grid_thresholded(f, ic_kind, params, n, n_blocks);
+  f->pp.coarsen_everywhere = everywhere;
+  return s;
 }
 
 acm_status acm_block_indicators(acm_forest* f, double* ind, double* chirange, int64_t n) {

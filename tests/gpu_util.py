@@ -47,7 +47,8 @@ def oracle_solver(fo, phys, ic=None, mask=None, sponge=None, wavelet=40):
     ph = oracle_physics(phys)
     S = Solver(fo, ph, eps=phys.get("eps", 1e-3), dealias=bool(phys.get("dealias", 0)),
                mask_thr=phys.get("mask_range_thr", 1e-5), ic=ic, mask=mask, sponge=sponge,
-               wavelet={40: "cdf40", 44: "cdf44"}[wavelet])
+               wavelet={40: "cdf40", 44: "cdf44"}[wavelet],
+               coarsen_everywhere=bool(phys.get("coarsen_everywhere", 0)))
     return S
 
 

@@ -403,3 +403,29 @@ def test_single_block_is_its_own_neighbour(A, prec, Bs):
     assert nb == len(S.fo.leaves) == 1 and npass == 1
     err = rel_linf(f.read_fields().astype(np.float64), block_order_fields(S))
     assert max(err) < TOL[prec], err
+
+
+@pytest.mark.parametrize("prec,Bs", [(64, 9), (32, 17)])
+def test_coarsen_everywhere_restores_the_step_grid(A, prec, Bs):
+    """The performance cycle's coarsening (coarsen_everywhere = 1): after refine-all, every block
+    the refinement made merges back, in as many passes as the grading needs, to the starting
+    layout with bit-exact topology against the oracle's and, with CDF 4/0, the state bitwise."""
+    from oracle.sync import fine_wins
+    leaves = random_graded_leaves(51, nroot=(2, 1, 1), J0=1, Jmax=3, n_target=60)
+    grid = _grid(Bs=Bs, precision=prec, Jmax=4)
+    phys = _phys(coarsen_everywhere=1)
+    f, S = _pair(A, grid, phys, leaves, fn_seed=51)
+    f.sync_ghosts()                                       # fine wins on U, as refinement does
+    fine_wins(S.fo, S.U)
+    before = f.read_fields().copy()
+    t0 = f.topology()
+    f.refine_all()
+    S.refine_all()
+    nb, npass = f.coarsen()
+    opass = S.coarsen()
+    assert nb == len(leaves) == len(S.fo.leaves) and npass == opass >= 2
+    t = f.topology()
+    tc, lv, sl, nbr, rel = S.fo.topology()
+    assert np.array_equal(t["treecode"], tc) and np.array_equal(t["slot"], sl) and np.array_equal(t["nbr"], nbr)
+    assert np.array_equal(t["treecode"], t0["treecode"]) and np.array_equal(t["level"], t0["level"])
+    assert np.array_equal(f.read_fields(), before)

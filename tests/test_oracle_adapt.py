@@ -2,6 +2,7 @@
 import math
 
 import numpy as np
+import pytest
 
 from oracle import acm
 from oracle.adapt import Solver
@@ -145,3 +146,31 @@ def test_adaptive_run_stays_within_the_threshold_error_of_the_uniform_run():
             err = max(err, float(np.abs(ua - sub).max()))
     assert err <= steps * eps * scale, (err, steps * eps * scale)
     assert err > 0.0
+
+
+@pytest.mark.parametrize("seed", [51])
+def test_coarsen_everywhere_restores_the_step_grid(seed):
+    """The performance cycle of Sec. 5.4 with coarsening forced everywhere (reading: every block
+    made by the step's refinement is tagged, thresholds ignored): refine-all then coarsening
+    restores the starting layout, and with CDF 4/0 the state bitwise (prediction copies the
+    coincident points to the children, decimation copies them back); over full steps
+    (refine, RK4, coarsen) the layout stays the same."""
+    from oracle.sync import fine_wins
+    from tests.gpu_util import fill_from_function, oracle_forest, smooth_field
+    leaves = random_graded_leaves(seed, nroot=(2, 1, 1), J0=1, Jmax=3, n_target=60)
+    grid = dict(nroot=(2, 1, 1), root_len=1.0, Bs=9, g=4, Jmin=1, Jmax=4)
+    fo = oracle_forest(grid, leaves=leaves, max_blocks=4096)
+    S = Solver(fo, acm.Physics(nu=1e-2, c0=3.0, C_eta=1e-2, C_gamma=0.5), coarsen_everywhere=True)
+    fill_from_function(S, lambda X, Y, Z: smooth_field(X, Y, Z, (2.0, 1.0, 1.0), seed))
+    S.eval_mask()
+    fine_wins(fo, S.U)
+    before = {l: S.U[s].copy() for l, s in fo.leaves.items()}
+    S.refine_all()
+    assert len(fo.leaves) > len(before)
+    assert S.coarsen() >= 2                                    # finest groups first (grading)
+    assert set(fo.leaves) == set(before)
+    assert all(np.array_equal(S.U[s], before[l]) for l, s in fo.leaves.items())
+    S.refine_all()
+    S.rk4(1e-3)
+    S.coarsen()
+    assert set(fo.leaves) == set(before)
