@@ -372,6 +372,70 @@ def reduce_over_ranks(ms, point_updates, dist=None, device="cpu"):
     return float(t.item()), float(p.item())
 
 
+def random_grid_sweep(args):
+    """The paper's performance study (Sec. 5.4) on one GPU: for each N_b a random 2:1-graded grid
+    of about N_b blocks of 17^3 (periodic unit cube, levels 3..Jmax), Taylor-Green data, `steps`
+    refine-evolve-coarsen steps with the coarsening forced everywhere (every block the step's
+    refinement made merges back, so the grid is the same at every step), FP32.  Per N_b: device
+    time per step (CUDA events on the forest's stream) and per evolved point and RHS evaluation,
+    the paper's unit.  Grids grow until the 32-bit element offsets (2^32 / (72 Bs^2) blocks after
+    refinement) or the memory cap would be exceeded.  Prints one JSON line."""
+    import numpy as np
+    import torch
+
+    from paper_1912_05371_gb300 import acm as A
+    from paper_1912_05371_gb300 import workloads as W
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    Bs, steps, warm = 17, args.steps, args.warmup
+    limit = (1 << 32) // (72 * Bs * Bs)
+    rows = []
+    sampler = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    sampler.start()
+    for nb in (int(v) for v in args.sweep_blocks.split(",")):
+        J = 5 if nb <= 2000 else (6 if nb <= 16000 else 7)
+        leaves = W.random_graded_leaves(nb, nroot=(1, 1, 1), J0=2, Jmax=J, n_target=nb)
+        evolved = sum(8 if l[0] < J + 1 else 1 for l in leaves)
+        grid = dict(nroot=(1, 1, 1), root_len=1.0, Bs=Bs, g=4, Jmin=2, Jmax=J + 1, precision=args.precision,
+                    max_blocks=evolved + 64, fd_scheme=1)
+        if grid["max_blocks"] > limit:
+            break
+        phys = dict(nu=1e-3, c0=10.0, C_gamma=1.0, cfl=0.5, eps=1e-3, dealias=0, coarsen_everywhere=1)
+        stream = torch.cuda.Stream()
+        with torch.cuda.stream(stream):
+            f = A.Forest(grid, phys, stream=stream)
+            if f.pool.numel() > args.sweep_max_gb * 1e9:
+                f.close()
+                break
+            f.set_leaves(leaves)
+            f.set_ic(A.ACM_IC_TAYLOR_GREEN, [2 * math.pi, 1.0])
+            for _ in range(warm):
+                f.step(0.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(steps):
+                _, n_after = f.step(0.0)
+            e1.record(stream)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1) / steps
+            assert n_after == len(leaves)
+            gb = f.pool.numel() / 1e9
+            f.close()
+        del f
+        torch.cuda.empty_cache()
+        pts = evolved * Bs ** 3 * 4
+        rows.append({"n_blocks": len(leaves), "evolved_blocks": evolved, "ms_per_step": ms,
+                     "ns_per_point_rhs": ms * 1e6 / pts, "point_updates_per_s": pts / (ms * 1e-3), "pool_gb": gb})
+    clocks = sampler.stop()
+    print(json.dumps({"metric": "device time per evolved point and RHS evaluation (random grids, Sec. 5.4)",
+                      "unit": "ns", "higher_is_better": False, "n_gpus": 1, "steps": steps, "warmup": warm,
+                      "dtype": "f32" if args.precision == 32 else "f64", "data": "synthetic",
+                      "config": {"workload": "random 2:1-graded grids of blocks of 17^3, periodic unit cube, "
+                                             "Taylor-Green, refine-evolve-coarsen with coarsening forced "
+                                             "everywhere (the grid is fixed)"},
+                      "sweep": rows, "clocks": clocks}))
+
+
 def run_reference(args):
     """Reference arm: the FP64 CPU oracle as it stands, timed on the host cores, on a bounded
     sample of the same workload: the sphere case built by the oracle's own initial-grid
@@ -437,10 +501,18 @@ def main():
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint workload")
     ap.add_argument("--wavelet", type=int, default=40, choices=[40, 44],
                     help="wavelet of the main line: 40 = CDF 4/0 (default), 44 = CDF 4/4")
+    ap.add_argument("--sweep", action="store_true",
+                    help="run the random-grid performance study (Sec. 5.4) instead of the benchmark")
+    ap.add_argument("--sweep-blocks", default="1000,2000,4000,8000,16000,24000")
+    ap.add_argument("--sweep-max-gb", type=float, default=150.0)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
         return run_reference(args)
+    if args.sweep:
+        if not any(a.startswith("--steps") for a in sys.argv[1:]):
+            args.steps = 15
+        return random_grid_sweep(args)
 
     import numpy as np
     import torch
