@@ -379,7 +379,9 @@ def random_grid_sweep(args):
     refinement made merges back, so the grid is the same at every step), FP32.  Per N_b: device
     time per step (CUDA events on the forest's stream) and per evolved point and RHS evaluation,
     the paper's unit.  Grids grow until the 32-bit element offsets (2^32 / (72 Bs^2) blocks after
-    refinement) or the memory cap would be exceeded.  Prints one JSON line."""
+    refinement) or the memory cap would be exceeded.  The fractions of the step spent refining,
+    evolving and coarsening (Fig. 5D) come from events between the three calls.  Prints one JSON
+    line."""
     import numpy as np
     import torch
 
@@ -410,22 +412,30 @@ def random_grid_sweep(args):
             f.set_ic(A.ACM_IC_TAYLOR_GREEN, [2 * math.pi, 1.0])
             for _ in range(warm):
                 f.step(0.0)
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            # the step's three phases (refine, evolve, coarsen) between events on the stream
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(3 * steps + 1)]
             torch.cuda.synchronize()
-            e0.record(stream)
-            for _ in range(steps):
-                _, n_after = f.step(0.0)
-            e1.record(stream)
-            e1.synchronize()
-            ms = e0.elapsed_time(e1) / steps
+            ev[0].record(stream)
+            for k in range(steps):
+                f.refine_all()
+                ev[3 * k + 1].record(stream)
+                f.rk4_step(0.0)
+                ev[3 * k + 2].record(stream)
+                n_after, _ = f.coarsen()
+                ev[3 * k + 3].record(stream)
+            ev[-1].synchronize()
+            ms = ev[0].elapsed_time(ev[-1]) / steps
+            phase = [sum(ev[3 * k + q].elapsed_time(ev[3 * k + q + 1]) for k in range(steps)) for q in range(3)]
             assert n_after == len(leaves)
             gb = f.pool.numel() / 1e9
             f.close()
         del f
         torch.cuda.empty_cache()
         pts = evolved * Bs ** 3 * 4
+        tot = sum(phase)
         rows.append({"n_blocks": len(leaves), "evolved_blocks": evolved, "ms_per_step": ms,
-                     "ns_per_point_rhs": ms * 1e6 / pts, "point_updates_per_s": pts / (ms * 1e-3), "pool_gb": gb})
+                     "ns_per_point_rhs": ms * 1e6 / pts, "point_updates_per_s": pts / (ms * 1e-3), "pool_gb": gb,
+                     "fractions": {"refine": phase[0] / tot, "evolve": phase[1] / tot, "coarsen": phase[2] / tot}})
     clocks = sampler.stop()
     print(json.dumps({"metric": "device time per evolved point and RHS evaluation (random grids, Sec. 5.4)",
                       "unit": "ns", "higher_is_better": False, "n_gpus": 1, "steps": steps, "warmup": warm,
