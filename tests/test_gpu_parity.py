@@ -414,7 +414,12 @@ def test_coarsen_everywhere_restores_the_step_grid(A, prec, Bs):
     leaves = random_graded_leaves(51, nroot=(2, 1, 1), J0=1, Jmax=3, n_target=60)
     grid = _grid(Bs=Bs, precision=prec, Jmax=4)
     phys = _phys(coarsen_everywhere=1)
-    f, S = _pair(A, grid, phys, leaves, fn_seed=51)
+    f = A.Forest(grid, phys)
+    f.set_leaves(leaves)
+    S = oracle_solver(oracle_forest(grid, leaves=leaves, max_blocks=grid["max_blocks"]), phys)
+    fill_from_function(S, lambda X, Y, Z: smooth_field(X, Y, Z, (2.0, 1.0, 1.0), 51))
+    S.eval_mask()
+    f.write_fields(block_order_fields(S))
     f.sync_ghosts()                                       # fine wins on U, as refinement does
     fine_wins(S.fo, S.U)
     before = f.read_fields().copy()
