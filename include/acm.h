@@ -250,7 +250,8 @@ acm_status acm_autotune(acm_forest* f, int* fw_ctas, int* slab_ctas);
  * (up to the order of FP64 atomic sums).  ws: caller device buffer of at least
  * acm_adjoint_bytes(f, nsteps, ckpt) bytes (ACM_ENOMEM if smaller): four FP64 registers, the
  * snapshots and five state registers in the forest's precision, and the mask's sensitivity.
- * acm_adjoint_bytes returns 0 for an invalid ckpt (0) or nsteps outside [1, 2^20].  The
+ * acm_adjoint_bytes returns 0 for an invalid ckpt (0), nsteps outside [1, 2^20] or a refused
+ * binomial schedule (see acm_checkpoint_schedule).  The
  * forest's state and time are unchanged on return, also when the sweep stops on an error; the
  * call synchronises the stream.  ACM_EGRADING if a ghost point's source is missing.  The
  * gradient with respect to U_0 is that of the forward map as computed: a point shared by
@@ -313,8 +314,9 @@ acm_status acm_load_state(acm_forest* f, const char* path);
  * op 0 STORE j (current state into snapshot j), 1 RESTORE j (snapshot j becomes current),
  * 2 ADVANCE k (plain step k -> k+1 from U_k), 3 TURN k (step k with its adjoint, from U_k; the
  * current state is used up); args holds j or k.  The first action stores U_0 in snapshot 0,
- * which is never written again.  ACM_EINVAL for nsteps outside [1, 2^20], ckpt = 0, or cap
- * below the number of actions (which is still written). */
+ * which is never written again.  ACM_EINVAL for nsteps outside [1, 2^20], ckpt = 0, a binomial
+ * schedule of more than 2^26 recomputed steps, or cap below the number of actions (which is
+ * still written). */
 acm_status acm_checkpoint_schedule(int nsteps, int ckpt, int32_t* snapshots, int64_t* advances, int8_t* ops,
                                    int32_t* args, int64_t cap, int64_t* n_actions);
 

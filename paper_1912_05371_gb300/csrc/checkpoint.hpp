@@ -13,7 +13,7 @@
 //
 // equidistant(n, c): U_k is kept for every multiple k of c; in the backward sweep each segment
 // of c steps is recomputed from its checkpoint with its states stored, then reversed (the last
-// segment's states are stored on the first pass).  ceil(n/c) + c - 2 snapshots.
+// segment's states are stored on the first pass).  ceil(n/c) + max(c - 2, 0) snapshots.
 //
 // binomial(n, S): binomial checkpointing (Griewank 1992; Griewank and Walther, revolve, 2000)
 // with S snapshots: to reverse steps a..b-1 from U_a with F further free snapshots, advance to
@@ -44,6 +44,9 @@ struct Schedule {
 };
 
 constexpr int32_t kMaxSteps = 1 << 20;
+// A schedule holds one action per recomputed step; longer ones are refused (few snapshots for
+// very many steps: 2^20 steps with 2 snapshots would need about 1.5e9).
+constexpr int64_t kMaxAdvances = int64_t(1) << 26;
 
 // Fewest advances that reverse n steps with S snapshots (U_0's included).
 inline int64_t binomial_advances(int64_t n, int64_t S) {
@@ -66,8 +69,8 @@ inline int64_t snapshots_needed(int64_t n, int64_t policy) {
     const int64_t nck = (n - 1) / c + 1;
     return nck + (c > 2 ? c - 2 : 0);
   }
-  const int64_t S = -policy;
-  return S < n ? S : n;
+  const int64_t S = -policy < n ? -policy : n;
+  return binomial_advances(n, S) > kMaxAdvances ? 0 : S;
 }
 
 inline void push(Schedule& s, Op op, int64_t arg) {
@@ -113,6 +116,7 @@ inline bool equidistant(int64_t n, int64_t policy, Schedule* out) {
 inline bool binomial(int64_t n, int64_t policy, Schedule* out) {
   if (n < 1 || n > kMaxSteps || policy > -1) return false;
   const int64_t S = (-policy < n) ? -policy : n;
+  if (binomial_advances(n, S) > kMaxAdvances) return false;
   Schedule s;
   std::vector<int32_t> free_slots;                       // a stack; slot 1 is taken first
   for (int64_t j = S - 1; j >= 1; --j) free_slots.push_back((int32_t)j);

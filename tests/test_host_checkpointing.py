@@ -95,3 +95,6 @@ def test_invalid_requests(A):
     assert na.value > 4
     with pytest.raises(ValueError):
         A.checkpoint_schedule(10, snapshots=0)
+    # too many recomputed steps for the memory given: refused at once, not built
+    assert L.acm_checkpoint_schedule(1 << 20, -2, None, None, None, None, 0, C.byref(na)) == 1
+    assert A.checkpoint_schedule(1 << 20, snapshots=64)["advances"] < (1 << 26)
