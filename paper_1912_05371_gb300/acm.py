@@ -207,6 +207,15 @@ class Forest:
                                                  C.c_void_p(self.pool.data_ptr()), nbytes, C.byref(h)), None)
         self.h = h
 
+    def _after_producer(self, t):
+        """Make the forest's stream wait for the caller's current stream, which made the device
+        tensor t (torch's convention); the library's calls synchronise their own stream before
+        returning, so outputs need no wait."""
+        import torch
+        cur = torch.cuda.current_stream(t.device)
+        if cur.cuda_stream != self.stream.cuda_stream:
+            self.stream.wait_stream(cur)
+
     def _check(self, st, h="self"):
         if st != 0:
             msg = self.L.acm_status_string(st).decode()
@@ -324,6 +333,7 @@ class Forest:
         if on_dev:
             src = dL_dUN.detach().to(torch.float64).contiguous()
             out = torch.empty(shape, dtype=torch.float64, device=src.device)
+            self._after_producer(src)
         else:
             src = np.ascontiguousarray(dL_dUN, dtype=np.float64)
             out = np.empty(shape, dtype=np.float64)
@@ -389,6 +399,8 @@ class Forest:
     def write_fields(self, arr):
         n = self.n_blocks()
         on_dev = int(hasattr(arr, "data_ptr") and arr.is_cuda)
+        if on_dev:
+            self._after_producer(arr)
         if not hasattr(arr, "data_ptr"):
             arr = np.ascontiguousarray(arr, dtype=self.dtype)
         self._check(self.L.acm_write_fields(self.h, _ptr(arr), n * 4 * self.Bs ** 3, on_dev))
