@@ -45,7 +45,8 @@ def _phys(**kw):
 def _pair(A, grid, phys, leaves, fn_seed=1, mask=None):
     f = A.Forest(grid, phys)
     f.set_leaves(leaves)
-    fo = oracle_forest(grid, leaves=leaves)
+    # the oracle's pool is the forest's: slots follow the same rule and fit the same capacity
+    fo = oracle_forest(grid, leaves=leaves, max_blocks=grid["max_blocks"])
     S = oracle_solver(fo, phys, mask=sphere_fn(mask) if mask else None,
                       sponge=sponge_fn(phys) if phys.get("sponge") else None, wavelet=grid.get("wavelet", 40))
     L = tuple(n * grid["root_len"] for n in grid["nroot"])
