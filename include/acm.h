@@ -61,8 +61,8 @@ typedef enum {
 
 /* ACM_ENUMERIC comes from the max-norm reduction, which propagates NaN and infinity: acm_rk4_step
  * with dt <= 0 and acm_diagnostics report a non-finite state before changing anything, acm_step
- * with dt <= 0 after its refinement.  acm_rk4_steps and the batched steps take the time step on
- * the device from the last stage's norms and do not check. */
+ * with dt <= 0 after its refinement, acm_rk4_steps after its steps (the state and time are then
+ * those the steps left).  The batched steps (acm_rk4_steps_batch) do not check. */
 
 /* Grid of cubic blocks (Sec. 4.1).  nroot[3] roots of side root_len tile the periodic box
  * [0, nroot*root_len]; a block at level J has side root_len/2^J and spacing

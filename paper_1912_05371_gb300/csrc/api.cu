@@ -671,7 +671,11 @@ acm_status rk4_steps(acm_forest* f, int nsteps, double dt, int use_graph, int* g
   CK(cudaStreamSynchronize(f->st));
   f->time = f->h_scal[1];
   f->norms_fresh = true;
-  return device_error(f);
+  if (acm_status e = device_error(f)) return e;
+  // a non-finite state is reported here: the last stage's fused norms pass NaN over, the
+  // reduction of max_norms does not (for a finite state it leaves the same norms)
+  double m[5];
+  return max_norms<T>(f, m);
 }
 
 template <typename T>

@@ -49,6 +49,19 @@ def test_non_finite_state_is_reported(A, prec, bad):
     f.close()
 
 
+@pytest.mark.parametrize("graph", [False, True])
+def test_non_finite_state_is_reported_by_device_dt_steps(A, graph):
+    """Steps with the time step on the device (plain launches or a CUDA graph) report a NaN
+    planted in the state after their steps."""
+    f = _forest(A, 32)
+    planted = f.read_fields().copy()
+    planted[5, 0, 3, 3, 3] = math.nan
+    f.write_fields(planted)
+    with pytest.raises(A.AcmError, match="status 6"):
+        f.rk4_steps(3, 0.0, graph=graph)
+    f.close()
+
+
 @pytest.mark.parametrize("prec", [64, 32])
 def test_refinement_beyond_the_pool_is_refused_and_changes_nothing(A, prec):
     f = _forest(A, prec)
