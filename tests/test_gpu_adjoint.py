@@ -143,21 +143,23 @@ def oracle_vjp():
     return S, delta, lamB, UN, g, gth
 
 
-@pytest.mark.parametrize("ckpt", [dict(ckpt_every=2), dict(snapshots=1)])
-def test_vjp_matches_the_oracle(A, oracle_vjp, ckpt):
-    """dL/dU_0 and dL/d(centre, radius) of L = <lam, U_N> (3 steps, FP64, lam random on every
-    copy of every point) against the oracle's vector-Jacobian product, which is pinned by central
-    differences; the forest's state is unchanged."""
+@pytest.mark.parametrize("prec,tol,ckpt", [(64, 1e-10, dict(ckpt_every=2)), (64, 1e-10, dict(snapshots=1)),
+                                           (32, 1e-4, dict(snapshots=2))])
+def test_vjp_matches_the_oracle(A, oracle_vjp, prec, tol, ckpt):
+    """dL/dU_0 and dL/d(centre, radius) of L = <lam, U_N> (3 steps, lam random on every copy of
+    every point) against the oracle's vector-Jacobian product, which is pinned by central
+    differences: FP64 to rounding; an FP32 forward (FP64 adjoint) within the FP32 rounding of the
+    states its coefficients come from.  The forest's state is unchanged."""
     S, delta, lamB, UNo, go, gtho = oracle_vjp
-    f = _gpu_forest(A, S, delta, precision=64)
+    f = _gpu_forest(A, S, delta, precision=prec)
     before = f.read_fields().copy()
     gU, gth = f.adjoint_vjp(NV, DT, lamB, **ckpt)
     assert np.array_equal(f.read_fields(), before) and f.diagnostics()["time"] == 0.0
     fo = S.fo
     gob = np.stack([go[fo.leaves[l]] for l in fo.sorted_leaves()])
     a, b = _per_point(fo, gU, 2), _per_point(fo, gob, 2)
-    assert np.abs(a - b).max() <= 1e-10 * np.abs(b).max()
-    assert np.abs(gth - gtho).max() <= 1e-10 * np.abs(gtho).max(), (gth, gtho)
+    assert np.abs(a - b).max() <= tol * np.abs(b).max()
+    assert np.abs(gth - gtho).max() <= tol * np.abs(gtho).max(), (gth, gtho)
 
 
 def test_step_map_through_autograd(A, oracle_vjp):
