@@ -145,8 +145,13 @@ enum { ACM_IC_TAYLOR_GREEN = 1, ACM_IC_UNIFORM = 2, ACM_IC_PULSE = 3, ACM_IC_PUL
  * the same tanh profile of the box's signed distance and u_s = omega x (x - x0).  Its pose
  * follows the forest's simulated time: chi is evaluated at every RK4 stage time and the
  * penalization uses u_s; acm_rk4_steps and acm_rk4_steps_batch refuse a moving mask
- * (ACM_EINVAL); the force of acm_diagnostics integrates chi (u - u_s).  Not yet run on a GPU. */
-enum { ACM_MASK_NONE = 0, ACM_MASK_SPHERE = 1, ACM_MASK_PLATE = 2 };
+ * (ACM_EINVAL); the force of acm_diagnostics integrates chi (u - u_s).  Not yet run on a GPU.
+ * ACM_MASK_FIELD (no parameters): chi is the caller's field (any geometry, e.g. a mask made
+ * from a surface), written with acm_write_mask and 0 until then; u_s = 0.  It belongs to the
+ * grid it was written for: acm_set_leaves, acm_init_uniform, acm_init_grid, acm_refine_all,
+ * acm_coarsen and acm_step return ACM_EINVAL while it is set (set another mask first).  The
+ * vector-Jacobian product (acm_adjoint_vjp) accepts it, with no parameter gradient. */
+enum { ACM_MASK_NONE = 0, ACM_MASK_SPHERE = 1, ACM_MASK_PLATE = 2, ACM_MASK_FIELD = 3 };
 
 /* Register ids for acm_sync_ghosts / acm_read_fields (U is the solution). */
 enum { ACM_REG_U = 0 };
@@ -272,11 +277,11 @@ acm_status acm_adjoint_plate_pitch(acm_forest* f, int nsteps, double dt, int ckp
 
 /* Vector-Jacobian product of the N-step map U_0 -> U_N (nsteps RK4 steps of fixed dt from the
  * current state and time on the frozen grid, the forward map and checkpointing of
- * acm_adjoint_sphere; a sphere, a moving plate or no mask): for any L with dL_dUN = dL/dU_N
+ * acm_adjoint_sphere; a sphere, a moving plate, a field mask or none): for any L with dL_dUN = dL/dU_N
  * (FP64, block order, layout of acm_read_fields, n_elems = n_blocks*4*Bs^3, one value per copy
  * of a redundant point), writes dL_dU0 = dL/dU_0 (same layout; both arrays on the device if
  * on_device, else host) and, if dL_dtheta is not NULL, dL/d(cx, cy, cz, R) of the sphere (4
- * values), dL/d alpha_m of the plate (1 value) or 4 zeros without a mask.  Workspace, restoration of the forest's state
+ * values), dL/d alpha_m of the plate (1 value) or 4 zeros without a mask or with a field mask.  Workspace, restoration of the forest's state
  * and time, and errors as acm_adjoint_sphere.  With it a caller composes the solver with any
  * loss of the final state (the Python binding's step_map_function does so for torch.autograd). */
 acm_status acm_adjoint_vjp(acm_forest* f, int nsteps, double dt, int ckpt, void* ws, size_t ws_bytes,
@@ -285,12 +290,18 @@ acm_status acm_adjoint_vjp(acm_forest* f, int nsteps, double dt, int ckpt, void*
 /* Set the simulated time (a moving mask is evaluated at it).  ACM_EINVAL for a non-finite t. */
 acm_status acm_set_time(acm_forest* f, double t);
 
+/* Write the field mask chi (ACM_MASK_FIELD only, ACM_EINVAL otherwise): block order, Bs^3 values
+ * per block (layout of acm_read_mask), forest precision, n_elems = n_blocks*Bs^3, device
+ * pointer if on_device, else host.  Synchronises the stream. */
+acm_status acm_write_mask(acm_forest* f, const void* chi, int64_t n_elems, int on_device);
+
 /* Restart files (the paper's runs resume from saved states across job limits, Sec. 4).
  * acm_save_state writes to path: a header (8 bytes "ACMSTATE", int32 version 1, precision,
  * sizeof(acm_grid_params), sizeof(acm_phys_params), mask kind, 0, the mask's 10 parameters as
  * acm_set_mask takes them (unused ones 0), the time, int64 n_blocks), the forest's
  * acm_grid_params and acm_phys_params, the leaves' level, x, y and z (int32 arrays of n_blocks,
- * block order) and the interior fields of U as acm_read_fields returns them; host byte order.
+ * block order), the interior fields of U as acm_read_fields returns them and, for a field mask,
+ * chi as acm_read_mask returns it; host byte order.
  * acm_read_state_header (host only, no forest) returns a file's parameters, block count and
  * time, so a caller can create a matching forest.  acm_load_state replaces a forest's grid,
  * state, physics parameters, mask and time with the file's; the forest's acm_grid_params must

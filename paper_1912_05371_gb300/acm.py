@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_lib", "libacm.so")
 
 ACM_IC_TAYLOR_GREEN, ACM_IC_UNIFORM, ACM_IC_PULSE, ACM_IC_PULSE_RING = 1, 2, 3, 4
-ACM_MASK_NONE, ACM_MASK_SPHERE, ACM_MASK_PLATE = 0, 1, 2
+ACM_MASK_NONE, ACM_MASK_SPHERE, ACM_MASK_PLATE, ACM_MASK_FIELD = 0, 1, 2, 3
 ACM_REG_U = 0
 
 
@@ -89,6 +89,7 @@ EXPORTS = {
     "acm_read_fields": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int64, C.c_int]),
     "acm_write_fields": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int]),
     "acm_read_mask": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int]),
+    "acm_write_mask": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int]),
     "acm_enable_timing": (C.c_int, [C.c_void_p, C.c_int]),
     "acm_last_step_stats": (C.c_int, [C.c_void_p, C.POINTER(StepStats)]),
     "acm_launch_count": (C.c_int64, [C.c_void_p]),
@@ -404,6 +405,16 @@ class Forest:
         if not hasattr(arr, "data_ptr"):
             arr = np.ascontiguousarray(arr, dtype=self.dtype)
         self._check(self.L.acm_write_fields(self.h, _ptr(arr), n * 4 * self.Bs ** 3, on_dev))
+
+    def write_mask(self, chi):
+        """The field mask's chi (ACM_MASK_FIELD): (n_blocks, Bs, Bs, Bs), numpy or a CUDA tensor."""
+        n = self.n_blocks()
+        on_dev = int(hasattr(chi, "data_ptr") and chi.is_cuda)
+        if on_dev:
+            self._after_producer(chi)
+        else:
+            chi = np.ascontiguousarray(chi, dtype=self.dtype)
+        self._check(self.L.acm_write_mask(self.h, _ptr(chi), n * self.Bs ** 3, on_dev))
 
     def read_mask(self):
         n = self.n_blocks()

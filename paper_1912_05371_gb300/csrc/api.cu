@@ -459,7 +459,7 @@ void plate_pose(acm_forest* f, double t) {
 // Mask on every block, or only on the blocks whose slots are in `fresh` (new blocks).
 template <typename T>
 acm_status eval_mask(acm_forest* f, const std::vector<int32_t>* fresh = nullptr) {
-  if (!f->mask_on) return ACM_OK;
+  if (!f->mask_on || f->mask.kind == 3) return ACM_OK;   // a field mask is the caller's
   if (f->moving) plate_pose(f, f->time);
   const int32_t* ranks = nullptr;
   int64_t n = (int64_t)f->order.size();
@@ -1142,7 +1142,7 @@ acm_status adjoint_sweep(acm_forest* f, int nsteps, double dt, int c, double wE,
   // vector-Jacobian product of the N-step map: lam starts from lamN, no objective terms
   const bool vjp = lamN != nullptr;
   // the objective's force needs a body; the vector-Jacobian product also runs without a mask
-  if ((!vjp && !f->mask_on) || (f->mask_on && !plate && f->mask.kind != 1))
+  if ((!vjp && !f->mask_on) || (f->mask_on && !plate && f->mask.kind != 1 && !(vjp && f->mask.kind == 3)))
     return fail(f, ACM_EINVAL, "the adjoint needs a sphere or plate mask");
   acm::MaskK mk = f->mask;
   if (!f->mask_on) mk.kind = 0;                    // no body: no mask parameter to differentiate
@@ -1272,7 +1272,7 @@ acm_status adjoint_sweep(acm_forest* f, int nsteps, double dt, int c, double wE,
     ++f->launches;
     if (k >= 1 && !vjp) objective(TAPE, tk);
   }
-  if (!plate && f->mask_on) {
+  if (!plate && f->mask_on && f->mask.kind == 1) {
     acm::launch_adj_theta<T>(Bs, GCHI, f->d_blist, f->d_binfo, nb, f->phk, mk, TH, f->st);
     ++f->launches;
   }
@@ -1417,6 +1417,7 @@ acm_status acm_init_uniform(acm_forest* f, int J) {
 
 acm_status acm_set_leaves(acm_forest* f, const int32_t* level, const int32_t* gx, const int32_t* gy,
                           const int32_t* gz, int64_t n) {
+  if (f && f->mask_on && f->mask.kind == 3) return fail(f, ACM_EINVAL, "a field mask belongs to its grid: set another mask first");
   if (!f || !level || !gx || !gy || !gz || n <= 0) return fail(f, ACM_EINVAL, "bad leaves");
   if (n > f->gp.max_blocks) return fail(f, ACM_ECAPACITY, "more leaves than max_blocks");
   f->norms_fresh = false;
@@ -1474,6 +1475,11 @@ acm_status acm_set_mask(acm_forest* f, int kind, const double* params, int n, do
     f->moving = false;
     f->mask.kind = 1;
     for (int i = 0; i < 5; ++i) f->mask.p[i] = params[i];
+  } else if (kind == ACM_MASK_FIELD) {
+    f->mask_on = true;
+    f->moving = false;
+    f->mask.kind = 3;
+    CK(cudaMemsetAsync(f->CHI, 0, (size_t)f->gp.max_blocks * f->lay.FS * f->esz, f->st));
   } else if (kind == ACM_MASK_PLATE) {
     if (!params || n < 10 || !(params[0] > 0) || !(params[1] > 0) || !(params[2] > 0) || !(params[9] > 0))
       return fail(f, ACM_EINVAL, "plate mask needs chord, span, thickness > 0, phi_m, alpha_m, f, x0, y0, z0, delta > 0");
@@ -1722,11 +1728,13 @@ acm_status acm_autotune(acm_forest* f, int* fw_ctas, int* slab_ctas) {
 
 acm_status acm_refine_all(acm_forest* f) {
   if (!f) return ACM_EINVAL;
+  if (f->mask_on && f->mask.kind == 3) return fail(f, ACM_EINVAL, "a field mask belongs to its grid: no refinement");
   return DISPATCH(f, refine_all, f);
 }
 
 acm_status acm_coarsen(acm_forest* f, int64_t* n_blocks, int* n_passes) {
   if (!f) return ACM_EINVAL;
+  if (f->mask_on && f->mask.kind == 3) return fail(f, ACM_EINVAL, "a field mask belongs to its grid: no coarsening");
   return DISPATCH(f, coarsen, f, n_blocks, n_passes);
 }
 
@@ -1885,7 +1893,7 @@ acm_status read_state_head(acm_forest* f, FILE* in, StateHeader* h, acm_grid_par
   if (fread(g, sizeof(*g), 1, in) != 1 || fread(ph, sizeof(*ph), 1, in) != 1)
     return fail(f, ACM_EINVAL, "truncated restart file");
   if (h->n_blocks < 1 || h->n_blocks > g->max_blocks || (h->precision != 32 && h->precision != 64) ||
-      h->precision != g->precision || h->mask_kind < ACM_MASK_NONE || h->mask_kind > ACM_MASK_PLATE)
+      h->precision != g->precision || h->mask_kind < ACM_MASK_NONE || h->mask_kind > ACM_MASK_FIELD)
     return fail(f, ACM_EINVAL, "inconsistent restart file header");
   return ACM_OK;
 }
@@ -1905,6 +1913,8 @@ acm_status acm_save_state(acm_forest* f, const char* path) {
   if (f->mask_on && f->moving) {
     h.mask_kind = ACM_MASK_PLATE;
     for (int i = 0; i < 10; ++i) h.mask_params[i] = f->plate[i];
+  } else if (f->mask_on && f->mask.kind == 3) {
+    h.mask_kind = ACM_MASK_FIELD;
   } else if (f->mask_on) {
     h.mask_kind = ACM_MASK_SPHERE;
     for (int i = 0; i < 5; ++i) h.mask_params[i] = f->mask.p[i];
@@ -1923,12 +1933,18 @@ acm_status acm_save_state(acm_forest* f, const char* path) {
   std::vector<char> fields((size_t)ne * f->esz);
   acm_status s = copy_fields(f, fields.data(), ne, 0, false, 4, f->U);
   if (s) return s;
+  std::vector<char> chi;
+  if (h.mask_kind == ACM_MASK_FIELD) {
+    chi.resize((size_t)(ne / 4) * f->esz);
+    if ((s = copy_fields(f, chi.data(), ne / 4, 0, false, 1, f->CHI))) return s;
+  }
   File out(fopen(path, "wb"));
   if (!out.p) return fail(f, ACM_EINVAL, std::string("cannot open ") + path);
   if (fwrite(&h, sizeof(h), 1, out.p) != 1 || fwrite(&f->gp, sizeof(f->gp), 1, out.p) != 1 ||
       fwrite(&f->pp, sizeof(f->pp), 1, out.p) != 1 ||
       fwrite(leaves.data(), sizeof(int32_t), leaves.size(), out.p) != leaves.size() ||
-      fwrite(fields.data(), 1, fields.size(), out.p) != fields.size())
+      fwrite(fields.data(), 1, fields.size(), out.p) != fields.size() ||
+      fwrite(chi.data(), 1, chi.size(), out.p) != chi.size())
     return fail(f, ACM_EINVAL, std::string("cannot write ") + path);
   if (fclose(out.p) != 0) {
     out.p = nullptr;
@@ -1975,9 +1991,12 @@ acm_status acm_load_state(acm_forest* f, const char* path) {
   std::vector<int32_t> leaves((size_t)(4 * n));
   const int64_t ne = n * 4 * (int64_t)me.Bs * me.Bs * me.Bs;
   std::vector<char> fields((size_t)ne * f->esz);
+  std::vector<char> chi(h.mask_kind == ACM_MASK_FIELD ? (size_t)(ne / 4) * f->esz : 0);
   if (fread(leaves.data(), sizeof(int32_t), leaves.size(), in.p) != leaves.size() ||
-      fread(fields.data(), 1, fields.size(), in.p) != fields.size())
+      fread(fields.data(), 1, fields.size(), in.p) != fields.size() ||
+      fread(chi.data(), 1, chi.size(), in.p) != chi.size())
     return fail(f, ACM_EINVAL, "truncated restart file");
+  if (f->mask_on && f->mask.kind == 3) f->mask_on = false;   // the file's mask replaces it below
   s = acm_set_leaves(f, leaves.data(), leaves.data() + n, leaves.data() + 2 * n, leaves.data() + 3 * n, n);
   if (s) return s;
   s = copy_fields(f, fields.data(), ne, 0, true, 4, f->U);
@@ -1986,7 +2005,9 @@ acm_status acm_load_state(acm_forest* f, const char* path) {
   f->time = h.time;
   f->norms_fresh = false;
   const int np = h.mask_kind == ACM_MASK_PLATE ? 10 : (h.mask_kind == ACM_MASK_SPHERE ? 5 : 0);
-  return acm_set_mask(f, h.mask_kind, np ? h.mask_params : nullptr, np, h.time);
+  s = acm_set_mask(f, h.mask_kind, np ? h.mask_params : nullptr, np, h.time);
+  if (s || h.mask_kind != ACM_MASK_FIELD) return s;
+  return copy_fields(f, chi.data(), ne / 4, 0, true, 1, f->CHI);
 }
 
 acm_status acm_read_fields(acm_forest* f, int reg, void* out, int64_t n_elems, int on_device) {
@@ -1997,6 +2018,13 @@ acm_status acm_read_fields(acm_forest* f, int reg, void* out, int64_t n_elems, i
 acm_status acm_write_fields(acm_forest* f, const void* in, int64_t n_elems, int on_device) {
   if (!f || !in) return fail(f, ACM_EINVAL, "bad arguments");
   return copy_fields(f, const_cast<void*>(in), n_elems, on_device, true, 4, f->U);
+}
+
+acm_status acm_write_mask(acm_forest* f, const void* chi, int64_t n_elems, int on_device) {
+  if (!f || !chi) return fail(f, ACM_EINVAL, "bad arguments");
+  if (!f->mask_on || f->mask.kind != 3) return fail(f, ACM_EINVAL, "acm_write_mask needs the field mask");
+  f->norms_fresh = false;
+  return copy_fields(f, const_cast<void*>(chi), n_elems, on_device, true, 1, f->CHI);
 }
 
 acm_status acm_read_mask(acm_forest* f, void* out, int64_t n_elems, int on_device) {
