@@ -68,4 +68,5 @@ def test_host_only_argument_checks(libpath):
     assert L.acm_adjoint_plate_pitch(None, 4, 1e-3, 2, 0.1, None, 0, ctypes.byref(J), None, None, 0, 0) == einval
     assert L.acm_adjoint_vjp(None, 4, 1e-3, 2, None, 0, None, None, 0, 0, None) == einval
     assert L.acm_set_time(None, 0.0) == einval
+    assert L.acm_write_mask(None, None, 0, 0) == einval
     assert L.acm_load_state(None, b"missing.acm") == einval and L.acm_save_state(None, b"x.acm") == einval
