@@ -424,7 +424,9 @@ int64_t acm_launch_count(const acm_forest* f);
  * fields: device array in block order as written by acm_read_fields (n_blocks x 4 components
  * x Bs^3, x fastest), float for precision 32, double for 64.  norms_out: device array of 5
  * doubles receiving max|u|, max|v|, max|w|, max|p| and max |(u,v,w)| (arithmetic in the field
- * precision, as inside acm_diagnostics).  stream: cudaStream_t (NULL = legacy default stream);
+ * precision, as inside acm_diagnostics; a NaN or an infinity in a component is carried into its
+ * norm, NaN before infinity, as acm_diagnostics reports a non-finite state).  stream:
+ * cudaStream_t (NULL = legacy default stream);
  * the call is asynchronous on it.
  * Returns ACM_EINVAL for bad arguments (Bs other than 9 or 17, precision other than 32 or 64,
  * NULL pointers, n_blocks < 1), ACM_ECAPACITY if n_blocks > ACM_NOALLOC_MAX_BLOCKS (nothing is

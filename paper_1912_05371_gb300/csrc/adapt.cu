@@ -1342,14 +1342,14 @@ __global__ void __launch_bounds__(kNT) k_gather(const T* reg, T* dense, const in
 }
 
 template <typename T, int BS>
-__global__ void __launch_bounds__(kNT) k_scatter(const T* dense, T* reg, const int32_t* blist) {
+__global__ void __launch_bounds__(kNT) k_scatter(const T* dense, T* reg, const int32_t* blist, int ncomp, int comp_stride_blk) {
   using L = Lay<T, BS>;
   const int slot = blist[blockIdx.x];
-  const int n = 4 * BS * BS * BS;
+  const int n = ncomp * BS * BS * BS;
   for (int i = threadIdx.x; i < n; i += kNT) {
     const int f = i / (BS * BS * BS), r = i % (BS * BS * BS);
     const int x = r % BS, y = (r / BS) % BS, z = r / (BS * BS);
-    reg[(size_t)slot * L::BLK + (size_t)f * L::FS + L::idx(x, y, z)] = dense[(size_t)blockIdx.x * n + i];
+    reg[(size_t)slot * comp_stride_blk + (size_t)f * L::FS + L::idx(x, y, z)] = dense[(size_t)blockIdx.x * n + i];
   }
 }
 
@@ -1503,9 +1503,12 @@ void launch_gather(int Bs, const T* reg, T* dense, const int32_t* blist, int64_t
   ACM_BS_DISPATCH(Bs, k_gather, <<<grid1(n), kNT, 0, st>>>(reg, dense, blist, ncomp, cstride));
 }
 template <typename T>
-void launch_scatter(int Bs, const T* dense, T* reg, const int32_t* blist, int64_t n, cudaStream_t st) {
+void launch_scatter(int Bs, const T* dense, T* reg, const int32_t* blist, int64_t n, int ncomp, cudaStream_t st) {
   if (n <= 0) return;
-  ACM_BS_DISPATCH(Bs, k_scatter, <<<grid1(n), kNT, 0, st>>>(dense, reg, blist));
+  // a one-component register (the mask) has one component per slot, like launch_gather's
+  const int stride = (int)layout_info(sizeof(T) == 8 ? 64 : 32, Bs).BLK;
+  const int cstride = ncomp == 1 ? (int)layout_info(sizeof(T) == 8 ? 64 : 32, Bs).FS : stride;
+  ACM_BS_DISPATCH(Bs, k_scatter, <<<grid1(n), kNT, 0, st>>>(dense, reg, blist, ncomp, cstride));
 }
 
 #define ACM_INST(T)                                                                                        \
@@ -1524,7 +1527,7 @@ void launch_scatter(int Bs, const T* dense, T* reg, const int32_t* blist, int64_
   template void launch_solid_source<T>(int, T*, T*, const T*, const int32_t*, const int4*, int64_t, const PhysK&, const MaskK&, double, double, int, cudaStream_t); \
   template void launch_solid_moment<T>(int, const T*, const int32_t*, const int4*, int64_t, const PhysK&, const MaskK&, double*, cudaStream_t); \
   template void launch_gather<T>(int, const T*, T*, const int32_t*, int64_t, int, cudaStream_t);          \
-  template void launch_scatter<T>(int, const T*, T*, const int32_t*, int64_t, cudaStream_t);
+  template void launch_scatter<T>(int, const T*, T*, const int32_t*, int64_t, int, cudaStream_t);
 ACM_INST(float)
 ACM_INST(double)
 

@@ -1144,8 +1144,13 @@ acm_status adjoint_sweep(acm_forest* f, int nsteps, double dt, int c, double wE,
   // the objective's force needs a body; the vector-Jacobian product also runs without a mask
   if ((!vjp && !f->mask_on) || (f->mask_on && !plate && f->mask.kind != 1 && !(vjp && f->mask.kind == 3)))
     return fail(f, ACM_EINVAL, "the adjoint needs a sphere or plate mask");
-  acm::MaskK mk = f->mask;
-  if (!f->mask_on) mk.kind = 0;                    // no body: no mask parameter to differentiate
+  // the mask the adjoint kernels see: the forest's current one (a moving plate's pose changes at
+  // every stage time), with kind 0 when no body is set (no mask parameter to differentiate)
+  auto cur_mask = [&]() {
+    acm::MaskK m = f->mask;
+    if (!f->mask_on) m.kind = 0;
+    return m;
+  };
   if (nsteps < 1 || c == 0 || !(dt > 0) || !ws || !dtheta || (!vjp && !J_out) || (vjp && !dU0))
     return fail(f, ACM_EINVAL, "bad arguments");
   if (f->order.empty()) return fail(f, ACM_EINVAL, "empty forest");
@@ -1193,14 +1198,14 @@ acm_status adjoint_sweep(acm_forest* f, int nsteps, double dt, int c, double wE,
     pose_at(ts);
     CK(cudaMemsetAsync(NU, 0, L.reg, f->st));
     acm::launch_adj_jgt<T>(Bs, Ys, KAP, CHI, GCHI, WGT, NU, f->d_blist, f->d_binfo, f->d_nbh, f->d_finer, nb, f->phk,
-                           mk, TH, f->d_err, f->st);
+                           cur_mask(), TH, f->d_err, f->st);
     f->launches += 3;
     return cudaGetLastError() == cudaSuccess ? ACM_OK : fail(f, ACM_ECUDA, "adjoint kernel launch failed");
   };
   auto objective = [&](const T* Us, double tn) {
     pose_at(tn);
     acm::launch_adj_objective<T>(Bs, Us, CHI, LAM, GCHI, f->d_blist, f->d_binfo, nb, f->phk, 1.0 / nsteps, wE,
-                                 mk, TH, f->st);
+                                 cur_mask(), TH, f->st);
     ++f->launches;
   };
   acm::ckpt::Schedule sched;
@@ -1273,7 +1278,7 @@ acm_status adjoint_sweep(acm_forest* f, int nsteps, double dt, int c, double wE,
     if (k >= 1 && !vjp) objective(TAPE, tk);
   }
   if (!plate && f->mask_on && f->mask.kind == 1) {
-    acm::launch_adj_theta<T>(Bs, GCHI, f->d_blist, f->d_binfo, nb, f->phk, mk, TH, f->st);
+    acm::launch_adj_theta<T>(Bs, GCHI, f->d_blist, f->d_binfo, nb, f->phk, cur_mask(), TH, f->st);
     ++f->launches;
   }
   CKL();
@@ -1839,9 +1844,9 @@ static acm_status copy_fields(acm_forest* f, void* buf, int64_t n_elems, int on_
     f->norms_fresh = false;
     if (!on_device) CK(cudaMemcpyAsync(dense, buf, bytes, cudaMemcpyHostToDevice, f->st));
     if (f->gp.precision == 64)
-      acm::launch_scatter<double>(f->gp.Bs, (const double*)dense, (double*)reg, f->d_blist, nb, f->st);
+      acm::launch_scatter<double>(f->gp.Bs, (const double*)dense, (double*)reg, f->d_blist, nb, ncomp, f->st);
     else
-      acm::launch_scatter<float>(f->gp.Bs, (const float*)dense, (float*)reg, f->d_blist, nb, f->st);
+      acm::launch_scatter<float>(f->gp.Bs, (const float*)dense, (float*)reg, f->d_blist, nb, ncomp, f->st);
   } else {
     if (f->gp.precision == 64)
       acm::launch_gather<double>(f->gp.Bs, (const double*)reg, (double*)dense, f->d_blist, nb, ncomp, f->st);
@@ -1996,9 +2001,16 @@ acm_status acm_load_state(acm_forest* f, const char* path) {
       fread(fields.data(), 1, fields.size(), in.p) != fields.size() ||
       fread(chi.data(), 1, chi.size(), in.p) != chi.size())
     return fail(f, ACM_EINVAL, "truncated restart file");
-  if (f->mask_on && f->mask.kind == 3) f->mask_on = false;   // the file's mask replaces it below
+  // the file's mask replaces a field mask below; a field mask would make acm_set_leaves refuse
+  // the grid change, so it is switched off for that call and back on if the call fails (the
+  // forest is then unchanged)
+  const bool had_field_mask = f->mask_on && f->mask.kind == 3;
+  if (had_field_mask) f->mask_on = false;
   s = acm_set_leaves(f, leaves.data(), leaves.data() + n, leaves.data() + 2 * n, leaves.data() + 3 * n, n);
-  if (s) return s;
+  if (s) {
+    if (had_field_mask) f->mask_on = true;
+    return s;
+  }
   s = copy_fields(f, fields.data(), ne, 0, true, 4, f->U);
   if (s) return s;
   f->pp = ph;

@@ -196,7 +196,7 @@ template <typename T>
 void launch_gather(int Bs, const T* reg, T* dense, const int32_t* blist, int64_t n, int ncomp,
                    cudaStream_t st);
 template <typename T>
-void launch_scatter(int Bs, const T* dense, T* reg, const int32_t* blist, int64_t n,
+void launch_scatter(int Bs, const T* dense, T* reg, const int32_t* blist, int64_t n, int ncomp,
                     cudaStream_t st);
 
 // ---- discrete adjoint (adjoint.cu): forward state and mask in T, adjoint variables FP64 ------------

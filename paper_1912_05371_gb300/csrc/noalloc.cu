@@ -28,35 +28,51 @@ __device__ __forceinline__ T absval(T v) { return v < T(0) ? -v : v; }
 __device__ __forceinline__ float root(float v) { return sqrtf(v); }
 __device__ __forceinline__ double root(double v) { return sqrt(v); }
 
+// Maximum that keeps NaN: a comparison with NaN is false, so a plain maximum (or fmax) would
+// drop it; with this one a non-finite state gives a non-finite norm, as in the forest's own
+// reduction, and NaN wins over infinity once it is in m.
+template <typename T>
+__device__ __forceinline__ T keep_max(T a, T m) { return (a > m || a != a) ? a : m; }
+
+// Squared velocity magnitude in the same rounding sequence as the forest's max norm (u*u, then
+// fma(v, v, .), then fma(w, w, .)), so both give bitwise the same largest magnitude.
+template <typename T>
+__device__ __forceinline__ T speed2(T u, T v, T w) {
+  T s = u * u;
+  s = fma(v, v, s);
+  return fma(w, w, s);
+}
+
 // One CTA per block of the dense block-order array (component-major, then z, y, x).
 template <typename T>
 __global__ void __launch_bounds__(kNT) k_block_max(const T* __restrict__ fields, int Bs, double* partials) {
   const int n3 = Bs * Bs * Bs;
   const T* b = fields + (size_t)blockIdx.x * 4 * n3;
+  // m[4] holds the squared speed; its root is taken once per block, in the field precision
   T m[5] = {T(0), T(0), T(0), T(0), T(0)};
   for (int i = threadIdx.x; i < n3; i += kNT) {
     T v[4];
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
       v[f] = b[(size_t)f * n3 + i];
-      const T a = absval(v[f]);
-      m[f] = a > m[f] ? a : m[f];
+      m[f] = keep_max(absval(v[f]), m[f]);
     }
-    const T mag = root(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
-    m[4] = mag > m[4] ? mag : m[4];
+    m[4] = keep_max(speed2(v[0], v[1], v[2]), m[4]);
   }
-  __shared__ double red[5][kNT / 32];
+  __shared__ T red[5][kNT / 32];
 #pragma unroll
   for (int k = 0; k < 5; ++k) {
-    double mk = (double)m[k];
-    for (int o = 16; o > 0; o >>= 1) mk = fmax(mk, __shfl_xor_sync(0xffffffffu, mk, o));
+    T mk = m[k];
+    for (int o = 16; o > 0; o >>= 1) mk = keep_max(__shfl_xor_sync(0xffffffffu, mk, o), mk);
     if ((threadIdx.x & 31) == 0) red[k][threadIdx.x >> 5] = mk;
   }
   __syncthreads();
   if (threadIdx.x < 5) {
-    double mk = 0.0;
-    for (int w = 0; w < kNT / 32; ++w) mk = fmax(mk, red[threadIdx.x][w]);
-    partials[(size_t)blockIdx.x * 5 + threadIdx.x] = mk;
+    T mk = T(0);
+    for (int w = 0; w < kNT / 32; ++w) mk = keep_max(red[threadIdx.x][w], mk);
+    // the root is monotone and correctly rounded: the root of the largest square is the
+    // largest root
+    partials[(size_t)blockIdx.x * 5 + threadIdx.x] = threadIdx.x == 4 ? (double)root(mk) : (double)mk;
   }
 }
 
@@ -65,16 +81,16 @@ __global__ void __launch_bounds__(1024) k_final_max(const double* partials, int 
   double m[5] = {0, 0, 0, 0, 0};
   for (int b = threadIdx.x; b < n; b += blockDim.x)
 #pragma unroll
-    for (int k = 0; k < 5; ++k) m[k] = fmax(m[k], partials[(size_t)b * 5 + k]);
+    for (int k = 0; k < 5; ++k) m[k] = keep_max(partials[(size_t)b * 5 + k], m[k]);
 #pragma unroll
   for (int k = 0; k < 5; ++k) {
-    for (int o = 16; o > 0; o >>= 1) m[k] = fmax(m[k], __shfl_xor_sync(0xffffffffu, m[k], o));
+    for (int o = 16; o > 0; o >>= 1) m[k] = keep_max(__shfl_xor_sync(0xffffffffu, m[k], o), m[k]);
     if ((threadIdx.x & 31) == 0) red[k][threadIdx.x >> 5] = m[k];
   }
   __syncthreads();
   if (threadIdx.x < 5) {
     double mk = 0.0;
-    for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) mk = fmax(mk, red[threadIdx.x][w]);
+    for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) mk = keep_max(red[threadIdx.x][w], mk);
     out[threadIdx.x] = mk;
   }
 }

@@ -47,6 +47,19 @@ def test_no_alloc_norms_match_the_forest_norms(precision):
         assert np.all(np.isfinite(got))
         assert np.all(np.abs(got - ref) <= tol * np.abs(ref).max()), (call, got, ref)
 
+    # a NaN and an infinity in the state reach the norms as they reach the forest's own: here
+    # an infinity in v and a NaN in p (at other points), so |v| and the speed are infinite
+    # and |p| is NaN, while |u| and |w| stay finite
+    host = dense.view(n, 4, Bs, Bs, Bs)
+    host[n // 2, 1, 3, 4, 5] = float("inf")
+    host[n - 1, 3, 6, 2, 1] = float("nan")
+    out = torch.zeros(5, dtype=torch.float64, device="cuda")
+    assert A.max_norms_noalloc(dense, n, Bs, precision, out, stream) == 0
+    torch.cuda.synchronize()
+    got = out.cpu().numpy()
+    assert np.isfinite(got[0]) and np.isfinite(got[2]), got
+    assert got[1] == np.inf and got[4] == np.inf and np.isnan(got[3]), got
+
     # sizes beyond the scratch capacity are refused before anything is launched
     big = A.NOALLOC_MAX_BLOCKS + 1
     out = torch.zeros(5, dtype=torch.float64, device="cuda")
