@@ -551,6 +551,7 @@ def main():
         # autotune the launch knobs on the evolved (refined) grid, then finish that step
         f.refine_all()
         tuned = f.autotune()
+        tuning = f.tuning()
         f.rk4_step(0.0)
         f.coarsen()
         f.enable_timing(True)
@@ -688,7 +689,10 @@ def main():
             "cdf44": cdf44,
             "adjoint": adjoint,
             "uniform_roofline": uniform,
-            "autotune": {"fine_wins_ctas_per_sm": tuned[0], "slab_ctas_per_sm": tuned[1]},
+            "autotune": {"fine_wins_ctas_per_sm": tuned[0], "slab_ctas_per_sm": tuned[1],
+                         "stage_kernel": {0: "pair (2 points/thread, packed f32x2)",
+                                          1: "point (1 point/thread)"}[tuning["stage_variant"]],
+                         "stage2_ms": {"pair": tuning["stage_ms"][0], "point": tuning["stage_ms"][1]}},
             "clocks": clk,
         }
         print(json.dumps(line), flush=True)

@@ -234,10 +234,33 @@ acm_status acm_rk4_steps_batch(acm_forest* const* forests, int n, int nsteps, do
 /* Autotuner: on the current grid, time the two task-list kernels of the per-stage ghost
  * synchronisation -- fine wins and the coarse-face halo slabs -- for each number of CTAs per SM
  * walking the list (fine wins 2, 4, 8, 16; slabs 1, 2, 3) and keep the fastest of each for this
- * forest (either output may be NULL).  Like every synchronisation it first lets finer leaves'
- * values win on shared boundary points of U; nothing else of the state changes.  Synchronises
+ * forest (either output may be NULL).  FP32 forests also time the two work layouts of the fused
+ * stage kernel (ACM_STAGE_PAIR, ACM_STAGE_POINT below) on one RK stage of the live grid and keep
+ * the faster.  Like every synchronisation it first lets finer leaves' values win on shared
+ * boundary points of U; nothing else of the state changes (the stage timing writes only the
+ * accumulator and a stage register, which every step rewrites before reading).  Synchronises
  * the stream.  No counterpart in the paper. */
 acm_status acm_autotune(acm_forest* f, int* fw_ctas, int* slab_ctas);
+
+/* Work layouts of the fused right-hand side + RK4 stage kernel (Sec. 2.1-2.3): ACM_STAGE_POINT,
+ * one point per thread (the default), or ACM_STAGE_PAIR, two x-adjacent points per thread with
+ * packed FP32x2 arithmetic (FP32 forests only: fewer instructions, half the resident threads).
+ * Both compute every point by the same formula; their FP32 results differ only in rounding
+ * order.  FP64 forests always use ACM_STAGE_POINT. */
+#define ACM_STAGE_PAIR 0
+#define ACM_STAGE_POINT 1
+/* Force the stage kernel's work layout (until the next acm_autotune); drops a captured graph.
+ * ACM_EINVAL for another value. */
+acm_status acm_set_stage_variant(acm_forest* f, int variant);
+
+/* The launch knobs in use: CTAs per SM of the fine-wins and slab kernels, the stage kernel's
+ * work layout, and the autotuner's median times (ms) of one stage launch in each layout
+ * (stage_ms[ACM_STAGE_PAIR], stage_ms[ACM_STAGE_POINT]; 0 until it has timed them). */
+typedef struct {
+  int fw_ctas_per_sm, slab_ctas_per_sm, stage_variant;
+  float stage_ms[2];
+} acm_tuning;
+acm_status acm_get_tuning(const acm_forest* f, acm_tuning* out);
 
 /* Discrete adjoint (an extension; the paper has none).  For nsteps RK4 steps of fixed dt from
  * the current state on the current grid, frozen (no adaptation: adaptation is not

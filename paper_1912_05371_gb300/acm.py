@@ -16,6 +16,7 @@ LIB_PATH = os.path.join(HERE, "_lib", "libacm.so")
 
 ACM_IC_TAYLOR_GREEN, ACM_IC_UNIFORM, ACM_IC_PULSE, ACM_IC_PULSE_RING = 1, 2, 3, 4
 ACM_MASK_NONE, ACM_MASK_SPHERE, ACM_MASK_PLATE, ACM_MASK_FIELD = 0, 1, 2, 3
+ACM_STAGE_PAIR, ACM_STAGE_POINT = 0, 1
 ACM_REG_U = 0
 
 
@@ -40,6 +41,11 @@ class Diag(C.Structure):
                 ("time", C.c_double)]
 
 
+class Tuning(C.Structure):
+    _fields_ = [("fw_ctas_per_sm", C.c_int), ("slab_ctas_per_sm", C.c_int), ("stage_variant", C.c_int),
+                ("stage_ms", C.c_float * 2)]
+
+
 class StepStats(C.Structure):
     _fields_ = [("stage_ms", C.c_double), ("sync_ms", C.c_double), ("stage_bytes", C.c_double),
                 ("n_launches", C.c_int64), ("host_topology_ms", C.c_double), ("host_tree_ms", C.c_double),
@@ -61,6 +67,8 @@ EXPORTS = {
     "acm_rk4_steps": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_int, C.POINTER(C.c_double),
                                 C.POINTER(C.c_int)]),
     "acm_autotune": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    "acm_set_stage_variant": (C.c_int, [C.c_void_p, C.c_int]),
+    "acm_get_tuning": (C.c_int, [C.c_void_p, C.c_void_p]),
     "acm_adjoint_bytes": (C.c_size_t, [C.c_void_p, C.c_int, C.c_int]),
     "acm_adjoint_sphere": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_int, C.c_double, C.c_void_p, C.c_size_t,
                                      C.POINTER(C.c_double), C.c_void_p, C.c_void_p, C.c_int64, C.c_int]),
@@ -281,6 +289,18 @@ class Forest:
         a, b = C.c_int(), C.c_int()
         self._check(self.L.acm_autotune(self.h, C.byref(a), C.byref(b)))
         return a.value, b.value
+
+    def set_stage_variant(self, variant):
+        """Force the stage kernel's work layout: ACM_STAGE_PAIR (two points per thread, FP32) or
+        ACM_STAGE_POINT (one point per thread)."""
+        self._check(self.L.acm_set_stage_variant(self.h, int(variant)))
+
+    def tuning(self):
+        """The launch knobs in use (see acm_get_tuning)."""
+        t = Tuning()
+        self._check(self.L.acm_get_tuning(self.h, C.byref(t)))
+        return dict(fw_ctas_per_sm=t.fw_ctas_per_sm, slab_ctas_per_sm=t.slab_ctas_per_sm,
+                    stage_variant=t.stage_variant, stage_ms=tuple(t.stage_ms))
 
     def _adjoint_workspace(self, nsteps, policy):
         import torch

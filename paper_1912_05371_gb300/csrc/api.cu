@@ -87,6 +87,8 @@ struct acm_forest {
   // launch knobs chosen by acm_autotune (defaults until it runs)
   int tune_fw_ctas = 8;            // fine-wins kernel: CTAs per SM walking the task list
   int tune_slab_ctas = 3;          // coarse-face slab kernel: CTAs per SM walking the task list
+  int stage_variant = acm::kStagePoint;  // FP32 stage kernel: one point per thread, or two
+  float tune_stage_ms[2] = {0.f, 0.f};   // the autotuner's times of the two (FP32)
 
   // host side of the current topology (the neighbourhood tables are built on the device from
   // the block list; the host leaf map is brought up to date only when a host query needs it)
@@ -535,7 +537,7 @@ acm_status rk4(acm_forest* f, double dt, double* dt_used, T* const* save = nullp
       CK(cudaMemsetAsync(f->d_maxbits, 0, 8 * sizeof(unsigned long long), f->st));
       a.norms = f->d_maxbits;
     }
-    acm::launch_stage<T>(s, f->gp.Bs, a, t, f->phk, f->d_err, f->st);
+    acm::launch_stage<T>(s, f->gp.Bs, a, t, f->phk, f->d_err, f->st, f->stage_variant);
     CKL();
     ++f->launches;
     if (f->moving) {
@@ -609,7 +611,7 @@ acm_status enqueue_rk4_device_dt(acm_forest* f, double dt) {
       CK(cudaMemsetAsync(f->d_maxbits, 0, 8 * sizeof(unsigned long long), f->st));
       a.norms = f->d_maxbits;
     }
-    acm::launch_stage<T>(s, f->gp.Bs, a, t, f->phk, f->d_err, f->st);
+    acm::launch_stage<T>(s, f->gp.Bs, a, t, f->phk, f->d_err, f->st, f->stage_variant);
     CKL();
     ++f->launches;
   }
@@ -1020,7 +1022,11 @@ acm_status time_launches(acm_forest* f, F&& launch, int reps, float* ms_out) {
 // synchronisation for each number of CTAs per SM walking the list (fine wins: 2, 4, 8, 16; coarse
 // faces: 1, 2, 3 -- at most 3 are resident) and keep the fastest of each.  Fine wins rewrites
 // stored boundary points with the values of finer leaves (what every synchronisation does first);
-// the slab kernel writes only the slab buffer.
+// the slab kernel writes only the slab buffer.  FP32 forests also time the two work layouts of
+// the fused stage kernel (two points per thread with packed arithmetic, or one point per thread)
+// on RK stage 2 of the live grid (reading U, the first stage register and the accumulator,
+// writing the accumulator and the second stage register: registers a step rewrites before it
+// reads them) and keep the faster.
 template <typename T>
 acm_status autotune(acm_forest* f, int* fw_ctas, int* slab_ctas) {
   if (f->order.empty()) return fail(f, ACM_EINVAL, "empty forest");
@@ -1048,6 +1054,31 @@ acm_status autotune(acm_forest* f, int* fw_ctas, int* slab_ctas) {
     if (s) return s;
     f->launches += 6;
     if (ms < best) { best = ms; best_sc = c; }
+  }
+  if constexpr (sizeof(T) == 4) {
+    const acm::TopoK t = topo(f);
+    acm::StageK<T> a{};
+    a.in = reinterpret_cast<const T*>(f->YA);
+    a.U = U;
+    a.acc = reinterpret_cast<T*>(f->ACC);
+    a.out = reinterpret_cast<T*>(f->YB);
+    a.chi = f->mask_on ? reinterpret_cast<const T*>(f->CHI) : nullptr;
+    a.slab = reinterpret_cast<const T*>(f->SLAB);
+    a.c_acc = 0.0;
+    a.c_out = 0.0;
+    best = 1e30f;
+    int best_v = f->stage_variant;
+    for (int v : {acm::kStagePair, acm::kStagePoint}) {
+      float ms = 0.f;
+      acm_status s = time_launches(f, [&]() {
+        acm::launch_stage<T>(2, f->gp.Bs, a, t, f->phk, f->d_err, f->st, v);
+      }, 5, &ms);
+      if (s) return s;
+      f->launches += 6;
+      f->tune_stage_ms[v] = ms;
+      if (ms < best) { best = ms; best_v = v; }
+    }
+    f->stage_variant = best_v;
   }
   f->tune_fw_ctas = best_fw;
   f->tune_slab_ctas = best_sc;
@@ -1731,6 +1762,27 @@ acm_status acm_autotune(acm_forest* f, int* fw_ctas, int* slab_ctas) {
   return DISPATCH(f, autotune, f, fw_ctas, slab_ctas);
 }
 
+acm_status acm_set_stage_variant(acm_forest* f, int variant) {
+  if (!f) return ACM_EINVAL;
+  if (variant != ACM_STAGE_PAIR && variant != ACM_STAGE_POINT) return fail(f, ACM_EINVAL, "unknown stage kernel");
+  f->stage_variant = variant == ACM_STAGE_PAIR ? acm::kStagePair : acm::kStagePoint;
+  // a captured graph holds the old kernel
+  if (f->gexec) { cudaGraphExecDestroy(f->gexec); f->gexec = nullptr; }
+  if (f->graph) { cudaGraphDestroy(f->graph); f->graph = nullptr; }
+  return ACM_OK;
+}
+
+acm_status acm_get_tuning(const acm_forest* f, acm_tuning* out) {
+  if (!f || !out) return ACM_EINVAL;
+  out->fw_ctas_per_sm = f->tune_fw_ctas;
+  out->slab_ctas_per_sm = f->tune_slab_ctas;
+  out->stage_variant = f->gp.precision == 64 ? ACM_STAGE_POINT
+                       : (f->stage_variant == acm::kStagePair ? ACM_STAGE_PAIR : ACM_STAGE_POINT);
+  out->stage_ms[0] = f->tune_stage_ms[acm::kStagePair];
+  out->stage_ms[1] = f->tune_stage_ms[acm::kStagePoint];
+  return ACM_OK;
+}
+
 acm_status acm_refine_all(acm_forest* f) {
   if (!f) return ACM_EINVAL;
   if (f->mask_on && f->mask.kind == 3) return fail(f, ACM_EINVAL, "a field mask belongs to its grid: no refinement");
@@ -2055,13 +2107,13 @@ acm_status acm_rhs(acm_forest* f, void* out, int64_t n_elems, int on_device) {
     if (s) return s;
     acm::StageK<double> a{(const double*)f->U, (const double*)f->U, (double*)f->ACC, (double*)f->YA,
                           f->mask_on ? (const double*)f->CHI : nullptr, (const double*)f->SLAB, 0.0, 0.0};
-    acm::launch_stage<double>(0, f->gp.Bs, a, t, f->phk, f->d_err, f->st);
+    acm::launch_stage<double>(0, f->gp.Bs, a, t, f->phk, f->d_err, f->st, f->stage_variant);
   } else {
     acm_status s = sync_stage<float>(f, (float*)f->U);
     if (s) return s;
     acm::StageK<float> a{(const float*)f->U, (const float*)f->U, (float*)f->ACC, (float*)f->YA,
                          f->mask_on ? (const float*)f->CHI : nullptr, (const float*)f->SLAB, 0.0, 0.0};
-    acm::launch_stage<float>(0, f->gp.Bs, a, t, f->phk, f->d_err, f->st);
+    acm::launch_stage<float>(0, f->gp.Bs, a, t, f->phk, f->d_err, f->st, f->stage_variant);
   }
   CKL();
   ++f->launches;

@@ -90,9 +90,23 @@ struct RkK {
 void launch_rk_coefs(const unsigned long long* maxbits, const RkK& p, double* rk, cudaStream_t st);
 
 // err: device int set to 1 if a bounded wait inside the kernel expired (never cleared here).
+// variant kStagePair: FP32 fields take the two-points-per-thread kernel (stage_pair.cu);
+// otherwise, and always for FP64 fields, the one-point kernel (stage.cu).
+constexpr int kStagePair = 0, kStagePoint = 1;
 template <typename T>
 void launch_stage(int stage, int Bs, const StageK<T>& s, const TopoK& t, const PhysK& p, int* err,
-                  cudaStream_t st);
+                  cudaStream_t st, int variant = kStagePair);
+
+// Constants of the FP32 pair kernel (kernel parameters, read from the constant bank): equal
+// pairs (v, v) for the packed operations, plain floats for the rest.
+struct PairConst {
+  float2 a1, a2, a3, k16, km90, mcgam, minv_ceta, minv_csp, uinf0, uinf1, uinf2, pinf;
+  float nu, c0sq, c_acc, c_out;
+  float ih[kMaxLevel + 1];     // 1 / h_J
+  float ih2[kMaxLevel + 1];    // 1 / (12 h_J^2)
+};
+void launch_stage_pair(int stage, int Bs, const StageK<float>& s, const TopoK& t, const PhysK& p,
+                       cudaStream_t st);
 
 // The per-stage synchronisation kernels walk a task list whose length the device holds
 // (*ntasks, written by launch_topology); max_tasks bounds it and sizes the grid, with

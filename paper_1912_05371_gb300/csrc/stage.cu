@@ -18,8 +18,7 @@
 // neighbour's stored interior (same level: copy; finer: decimation, Sec. 3.1 restriction) or,
 // across a face to a coarser neighbour, from the halo slab that the coarse-face kernel
 // predicted for this stage.  No ghost layer is written to HBM.
-#include "common.cuh"
-#include "kernels.hpp"
+#include "stage_common.cuh"
 
 namespace acm {
 
@@ -39,58 +38,6 @@ struct Cfg {
   static_assert(4 * PW < 0x8000, "plane buffer offsets must fit 15 bits");
 };
 
-
-// faces: 0 -x, 1 +x, 2 -y, 3 +y, 4 -z, 5 +z ; box index of the face neighbour
-__constant__ int kFaceBox[6] = {12, 14, 10, 16, 4, 22};
-
-template <typename T>
-__device__ __forceinline__ void cp_async_elem(T* dst, const T* src) {
-  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-  if constexpr (sizeof(T) == 4) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
-  } else {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
-  }
-}
-template <typename T>
-__device__ __forceinline__ T tmax(T a, T b) { return a > b ? a : b; }
-// Bulk prefetch of a contiguous range into L2 (address and size multiples of 16 bytes).
-__device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
-  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(p), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
-
-// Address of one halo value: face F, distance l = 1..3 from the face plane, tangential
-// coordinates (t0, t1) = (y, z) for x-faces, (x, z) for y-faces, (x, y) for z-faces.
-template <typename T, int BS>
-__device__ __forceinline__ const T* halo_ptr(const int (&ftype)[6], const int (&fs)[6][4],
-                                             const T* __restrict__ in, const T* __restrict__ slab,
-                                             int F, int l, int t0, int t1, int f) {
-  using L = Lay<T, BS>;
-  constexpr int M = L::M;
-  const int ax = F >> 1;
-  const bool plus = F & 1;
-  const int ty = ftype[F];
-  int s, nl, u0 = t0, u1 = t1;
-  if (ty == kTypeLeaf) {
-    s = fs[F][0];
-    nl = plus ? l : M - l;
-  } else if (ty == kTypeRefined) {
-    const int c0 = t0 > M / 2, c1 = t1 > M / 2;
-    s = fs[F][c0 + 2 * c1];
-    nl = plus ? 2 * l : M - 2 * l;
-    u0 = 2 * t0 - c0 * M;
-    u1 = 2 * t1 - c1 * M;
-  } else {
-    return slab + ((((size_t)fs[F][0] * 4 + f) * 3 + (l - 1)) * BS + t1) * BS + t0;
-  }
-  int x, y, z;
-  if (ax == 0) { x = nl; y = u0; z = u1; }
-  else if (ax == 1) { x = u0; y = nl; z = u1; }
-  else { x = u0; y = u1; z = nl; }
-  return in + (size_t)s * L::BLK + (size_t)f * L::FS + L::idx(x, y, z);
-}
 
 template <typename T, int BS, int STAGE>
 __global__ void __launch_bounds__(Cfg<T, BS>::NT, sizeof(T) == 4 ? 3 : 1)
@@ -115,41 +62,8 @@ k_stage(const StageK<T> a, const TopoK tp, const PhysK ph, int* err) {
   const int4 bi = tp.binfo[blockIdx.x];
   const int* nbh = tp.nbh + (size_t)blockIdx.x * kNbhStride;
 
-  if (tid < 24) {
-    const int F = tid >> 2, j = tid & 3;
-    const int c0 = j & 1, c1 = j >> 1;
-    const int d = kFaceBox[F];
-    int ty = nbh[kNbhType + d] & 15;
-    int s;
-    if (ty == kTypeLeaf) {
-      s = nbh[8 * d];
-    } else if (ty == kTypeRefined) {
-      const int nbit = (F & 1) ? 0 : 1;
-      const int ax = F >> 1;
-      int c;
-      if (ax == 0) c = nbit | (c0 << 1) | (c1 << 2);
-      else if (ax == 1) c = c0 | (nbit << 1) | (c1 << 2);
-      else c = c0 | (c1 << 1) | (nbit << 2);
-      s = nbh[8 * d + c];
-    } else {
-      ty = kTypeCoarser;                 // halo slab predicted by the coarse-face kernel
-      s = tp.slabidx[(size_t)blockIdx.x * 8 + F];
-    }
-    fs[F][j] = s;
-    if (j == 0) ftype[F] = ty;
-  }
-  if (ph.sponge && tid < 3 * BS) {
-    const double h = ph.h[bi.x];
-    const int ax = tid / BS, i = tid % BS;
-    const int g = ax == 0 ? bi.y : (ax == 1 ? bi.z : bi.w);
-    const long long N = ((long long)ph.nroot[ax] << bi.x) * M;
-    long long gi = (long long)g * M + i;        // in [0, N]; the seam x = L is taken as 0
-    if (gi >= N) gi -= N;
-    const double c = (double)gi * h;
-    // the profile in the field precision (FP32 fields keep tanh off the FP64 pipe)
-    const T dist = T(fmin(c, ph.sp_L[ax] - c));
-    sp[ax][i] = T(0.5) * (T(1) - ttanh((dist - T(ph.sp_width)) / T(ph.sp_delta)));
-  }
+  stage_faces(tid, nbh, tp.slabidx, blockIdx.x, ftype, fs);
+  stage_sponge<T, BS>(tid, ph, bi, sp);
   __syncthreads();
 
   // model and RK constants are read from the kernel parameters (constant bank), not registers;
@@ -421,7 +335,13 @@ void launch_stage_bs(int stage, const StageK<T>& s, const TopoK& t, const PhysK&
 
 template <typename T>
 void launch_stage(int stage, int Bs, const StageK<T>& s, const TopoK& t, const PhysK& p, int* err,
-                  cudaStream_t st) {
+                  cudaStream_t st, int variant) {
+  if constexpr (sizeof(T) == 4) {
+    if (variant == kStagePair) {
+      launch_stage_pair(stage, Bs, s, t, p, st);
+      return;
+    }
+  }
   StageK<T> a = s;
   StageConst<T>& c = a.kc;
   c.a1 = T(p.a1); c.a2 = T(p.a2); c.a3 = T(p.a3);
@@ -442,7 +362,7 @@ void launch_rk_coefs(const unsigned long long* maxbits, const RkK& p, double* rk
   k_rk_coefs<<<1, 32, 0, st>>>(maxbits, p, rk);
 }
 
-template void launch_stage<float>(int, int, const StageK<float>&, const TopoK&, const PhysK&, int*, cudaStream_t);
-template void launch_stage<double>(int, int, const StageK<double>&, const TopoK&, const PhysK&, int*, cudaStream_t);
+template void launch_stage<float>(int, int, const StageK<float>&, const TopoK&, const PhysK&, int*, cudaStream_t, int);
+template void launch_stage<double>(int, int, const StageK<double>&, const TopoK&, const PhysK&, int*, cudaStream_t, int);
 
 }  // namespace acm

@@ -54,8 +54,10 @@ def test_full_size_sphere_rhs_matches_oracle(A, prec):
     Ko = S.rhs(S.U.copy())
     ref = np.stack([Ko[fo.leaves[l]] for l in order])
     err = rel_linf(K, ref)
-    # FP32: one derivative evaluation of FP32 data (see test_fused_rhs_matches_oracle)
-    assert max(err) < (1e-12 if prec == 64 else 1e-4), err
+    print(f"full-size rhs FP{prec} rel. Linf per field", err)
+    # the oracle evaluates the right-hand side of the forest's own (FP32-rounded) state, so the
+    # difference is the FP32 arithmetic of one evaluation
+    assert max(err) < (1e-12 if prec == 64 else 2e-5), err
 
 
 def check_cdf44_parents(grid, pre_leaves, pre_U, post_leaves, post_U, nsample=4, tol=2e-5):

@@ -97,30 +97,50 @@ def test_sync_ghosts_matches_oracle(A, prec, Bs, seed):
     assert max(err) < (1e-13 if prec == 64 else 1e-6), err
 
 
-@pytest.mark.parametrize("prec,Bs,seed,masked,sponge", [(64, 9, 7, True, True), (64, 17, 8, False, False),
-                                                        (32, 9, 9, True, True), (64, 9, 10, False, True)])
-def test_fused_rhs_matches_oracle(A, prec, Bs, seed, masked, sponge):
+PAIR, POINT = 0, 1     # the stage kernel's work layouts (FP32: two points per thread, or one)
+
+
+@pytest.mark.parametrize("prec,Bs,seed,masked,sponge,variant", [
+    (64, 9, 7, True, True, POINT), (64, 17, 8, False, False, POINT), (32, 9, 9, True, True, PAIR),
+    (32, 9, 9, True, True, POINT), (32, 17, 14, True, True, PAIR), (32, 17, 14, True, True, POINT),
+    (64, 9, 10, False, True, POINT)])
+def test_fused_rhs_matches_oracle(A, prec, Bs, seed, masked, sponge, variant):
     leaves = random_graded_leaves(seed, nroot=(2, 1, 1), J0=1, Jmax=3, n_target=70)
     grid = _grid(Bs=Bs, precision=prec)
     phys = _phys(sponge=int(sponge), C_sp=0.05, u_inf=(0.4, -0.1, 0.2), p_inf=0.1,
                  sponge_L=(2.0, 1.0, 1.0), sponge_width=0.2, sponge_delta=0.05)
     mask = (0.8, 0.5, 0.5, 0.2, 0.04) if masked else None
     f, S = _pair(A, grid, phys, leaves, fn_seed=seed, mask=mask)
+    f.set_stage_variant(variant)
     gpu = f.rhs().astype(np.float64)
     K = S.rhs(S.U.copy())
     ref = np.stack([K[S.fo.leaves[l]] for l in S.fo.sorted_leaves()])
     err = rel_linf(gpu, ref)
-    # FP32: the stencils difference neighbouring values, losing about log2(1/(k h)) bits
-    assert max(err) < (1e-12 if prec == 64 else 1e-4), err
+    if prec == 64:
+        assert max(err) < 1e-12, err
+        return
+    # FP32 against the oracle on the same state rounded to FP32: the rounding of the kernel's own
+    # arithmetic, within the FP32 field tolerance
+    U32 = S.U.astype(np.float32).astype(np.float64)
+    K32 = S.rhs(U32)
+    ref32 = np.stack([K32[S.fo.leaves[l]] for l in S.fo.sorted_leaves()])
+    err32 = rel_linf(gpu, ref32)
+    print("fp32 rhs err vs fp64 state", err, "vs rounded state", err32)
+    assert max(err32) < 2e-5, err32
+    # against the unrounded FP64 state too (the stencils amplify the input's own rounding by
+    # about 1/(k h); measured about 1e-6 here)
+    assert max(err) < 2e-5, err
 
 
-@pytest.mark.parametrize("prec,Bs,seed", [(64, 9, 11), (64, 17, 12), (32, 17, 13)])
-def test_rk4_steps_match_oracle(A, prec, Bs, seed):
+@pytest.mark.parametrize("prec,Bs,seed,variant", [(64, 9, 11, POINT), (64, 17, 12, POINT), (32, 17, 13, PAIR),
+                                                  (32, 17, 13, POINT), (32, 9, 15, PAIR)])
+def test_rk4_steps_match_oracle(A, prec, Bs, seed, variant):
     leaves = random_graded_leaves(seed, nroot=(2, 1, 1), J0=1, Jmax=3, n_target=70)
     grid = _grid(Bs=Bs, precision=prec)
     phys = _phys()
     mask = (1.2, 0.5, 0.5, 0.15, 0.05)
     f, S = _pair(A, grid, phys, leaves, fn_seed=seed, mask=mask)
+    f.set_stage_variant(variant)
     dt = 2e-3 if Bs == 9 else 1e-3
     for _ in range(2):
         f.rk4_step(dt)
