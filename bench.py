@@ -161,6 +161,157 @@ def oracle_rhs_sample(leaves, U_blocks, grid, phys, mask):
     return n * grid["Bs"] ** 3 / dt, dt, n
 
 
+def _oracle_worker(path, grid, phys, mask, steps, warmup, barrier):
+    """One host process of the all-core oracle timing: builds the oracle solver on the sample
+    saved at `path`, waits for every worker, then times `steps` RHS evaluations."""
+    import numpy as np
+
+    from oracle import acm as oacm
+    from oracle.adapt import Solver
+    from oracle.forest import Forest as OForest
+    d = np.load(path, allow_pickle=False)
+    leaves = [tuple(int(v) for v in r) for r in d["leaves"]]
+    fo = OForest(nroot=grid["nroot"], root_len=grid["root_len"], Bs=grid["Bs"], Jmin=grid["Jmin"],
+                 Jmax=grid["Jmax"], max_blocks=len(leaves) + 8)
+    fo.set_leaves(leaves)
+    ph = oacm.Physics(nu=phys["nu"], c0=phys["c0"], C_eta=phys["C_eta"], C_gamma=phys["C_gamma"],
+                      C_sp=phys["C_sp"], u_inf=phys["u_inf"], p_inf=phys["p_inf"])
+    cx, cy, cz, R, dl = mask
+    S = Solver(fo, ph, mask=lambda X, Y, Z: oacm.sphere_mask(X, Y, Z, (cx, cy, cz), R, dl),
+               sponge=lambda X, Y, Z: oacm.sponge_mask(X, Y, Z, phys["sponge_L"], phys["sponge_width"],
+                                                       phys["sponge_delta"]))
+    for i, l in enumerate(fo.sorted_leaves()):
+        S.U[fo.leaves[l]] = d["U"][i]
+    S.eval_mask()
+    for _ in range(warmup):
+        S.rhs(S.U)
+    barrier.wait()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        S.rhs(S.U)
+    return time.perf_counter() - t0
+
+
+def oracle_all_cores(leaves, U_blocks, grid, phys, mask, cores, steps=1, warmup=0):
+    """The oracle as it stands on `cores` host processes at once, each evaluating the RHS of its
+    own copy of the sample (processes started with spawn, after the GPU work; they never touch
+    the GPU).  Returns (point-updates/s of all processes together, seconds of the slowest)."""
+    import multiprocessing as mp
+    import tempfile
+
+    import numpy as np
+    ctx = mp.get_context("spawn")
+    with tempfile.TemporaryDirectory() as tmp:
+        path = os.path.join(tmp, "sample.npz")
+        np.savez(path, leaves=np.asarray(leaves, dtype=np.int64), U=np.asarray(U_blocks, dtype=np.float64))
+        with ctx.Manager() as mgr:
+            bar = mgr.Barrier(cores)
+            with ctx.Pool(cores) as pool:
+                secs = pool.starmap(_oracle_worker, [(path, grid, phys, mask, steps, warmup, bar)] * cores)
+    n = len(leaves)
+    slowest = max(secs)
+    return cores * steps * n * grid["Bs"] ** 3 / slowest, slowest
+
+
+def adaptive_run(A, stream, precision, Jmax, max_blocks, nsteps=200):
+    """Config 2 as stated: the sphere workload from its initial grid through 200 adaptive steps
+    (refine, RK4 at the CFL time step, coarsen), the block count after every step (N_b(t)), the
+    share of the step time spent refining, evolving and coarsening (events between the three
+    calls, as the paper splits its step, Sec. 5.4), and the clocks sampled during the run."""
+    import torch
+    grid, phys, mask, ic, _ = sphere_setup(Jmax=Jmax, precision=precision, max_blocks=max_blocks)
+    f = A.Forest(grid, phys, stream=stream)
+    f.set_mask(A.ACM_MASK_SPHERE, mask)
+    n0 = f.init_grid(A.ACM_IC_UNIFORM, ic)
+    Bs3 = grid["Bs"] ** 3
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3 * nsteps + 1)]
+    nev, nst, t = [], [], 0.0
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    for k in range(nsteps):
+        f.refine_all()
+        ev[3 * k + 1].record(stream)
+        nev.append(f.n_blocks())
+        t += f.rk4_step(0.0)
+        ev[3 * k + 2].record(stream)
+        n_after, _ = f.coarsen()
+        nst.append(n_after)
+        ev[3 * k + 3].record(stream)
+    ev[-1].synchronize()
+    clk = clocks.stop()
+    ms = ev[0].elapsed_time(ev[-1])
+    phase = [sum(ev[3 * k + q].elapsed_time(ev[3 * k + q + 1]) for k in range(nsteps)) for q in range(3)]
+    f.close()
+    tot = sum(phase)
+    pu = 4 * Bs3 * sum(nev)
+    return {"workload": "the sphere workload from its initial grid, 200 adaptive steps at the CFL time step",
+            "precision": f"fp{precision}", "steps": nsteps, "t_end": t, "ms_per_step": ms / nsteps,
+            "value": pu / (ms * 1e-3), "unit": UNIT, "blocks_initial": n0,
+            "n_blocks": {"evolved": nev, "after_coarsening": nst},
+            "phase_fractions": {"refine": phase[0] / tot, "evolve": phase[1] / tot, "coarsen": phase[2] / tot},
+            "clocks": clk}
+
+
+def fp64_measurement(A, stream, Jmax, max_blocks, nsteps=20, warmup=3):
+    """The sphere workload with FP64 fields (config 2 asks for both precisions): whole steps
+    timed by CUDA events as in the main line, the stage kernel's launch time, and its roofline
+    against both bounds -- HBM (136 B per point-update) and the FP64 pipe (224 flops per
+    point-update, counted from the kernel: 12 first derivatives at 8, 3 Laplacians at 20, the
+    right-hand side 52, the RK combination 16 -- over the FMA rate of this GPU measured by the
+    library's own kernel)."""
+    import numpy as np
+    import torch
+    grid, phys, mask, ic, _ = sphere_setup(Jmax=Jmax, precision=64, max_blocks=max_blocks)
+    f = A.Forest(grid, phys, stream=stream)
+    f.set_mask(A.ACM_MASK_SPHERE, mask)
+    f.init_grid(A.ACM_IC_UNIFORM, ic)
+    for _ in range(warmup):
+        f.step(0.0)
+    Bs3 = grid["Bs"] ** 3
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f.enable_timing(True)
+    pu, nev, st_ms, st_b = 0, [], 0.0, 0.0
+    e0.record(stream)
+    for _ in range(nsteps):
+        f.refine_all()
+        n_ev = f.n_blocks()
+        f.rk4_step(0.0)
+        st = f.last_step_stats()
+        st_ms += st["stage_ms"]
+        st_b += st["stage_bytes"]
+        f.coarsen()
+        pu += 4 * n_ev * Bs3
+        nev.append(n_ev)
+    e1.record(stream)
+    e1.synchronize()
+    f.enable_timing(False)
+    ms = e0.elapsed_time(e1)
+    f.close()
+    fma64 = A.fma_rate(64, stream)
+    fma32 = A.fma_rate(32, stream)
+    peak, kind = measured_peaks()
+    pts_per_launch = float(np.mean(nev)) * Bs3
+    launch_s = st_ms * 1e-3 / (4 * nsteps)
+    flops = 224.0 * pts_per_launch / launch_s
+    gbs = st_b / (st_ms * 1e-3) / 1e9
+    return {"workload": "the sphere workload above with FP64 fields", "precision": "fp64", "steps": nsteps,
+            "ms_per_step": ms / nsteps, "value": pu / (ms * 1e-3), "unit": UNIT,
+            "blocks_evolved_mean": float(np.mean(nev)),
+            "stage_ms_per_launch": launch_s * 1e3,
+            "fma_rate_tflops": {"fp64": fma64 / 1e12, "fp32": fma32 / 1e12,
+                                "how": "acm_fma_rate: 8 independent FMA chains per thread, 8 CTAs of 256 "
+                                       "threads per SM, median of 5 launches"},
+            "roofline": {"alu": {"bound": "alu", "achieved": flops / 1e12, "peak": fma64 / 1e12,
+                                 "unit": "TFLOP/s", "frac": flops / fma64,
+                                 "flops_per_point_update": 224},
+                         "hbm": {"achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+                                 "bytes_per_point_update": 136, "peak_kind": kind}},
+            "ceilings_point_updates_per_s": {"fp64_pipe": fma64 / 224.0, "hbm": peak * 1e9 / 136.0}}
+
+
 def graph_comparison(A, stream, precision, nsteps=200):
     """RK4 steps on config 1's grid (periodic unit cube, 4x4x4 blocks of 17^3, Taylor-Green,
     nu = 1e-2, c0 = 10, CFL 0.5), three ways: one C-ABI call per step with the time step on the
@@ -447,10 +598,12 @@ def random_grid_sweep(args):
 
 
 def run_reference(args):
-    """Reference arm: the FP64 CPU oracle as it stands, timed on the host cores, on a bounded
-    sample of the same workload: the sphere case built by the oracle's own initial-grid
-    procedure with levels 2..3, refined once; one step = one oracle RHS evaluation (ghost sync
-    + right-hand side of every block)."""
+    """Reference arm: the FP64 CPU oracle as it stands, on all host cores at once (one spawned
+    process per core, each evaluating the RHS of its own copy of the sample), on a bounded sample
+    of the same workload: the sphere case built by the oracle's own initial-grid procedure with
+    levels 2..3, refined once (1024 blocks), or -- when K + W evaluations of that would exceed
+    about 150 s -- the initial grid itself; one step = one oracle RHS evaluation (ghost sync +
+    right-hand side of every block) in every process."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
@@ -469,24 +622,29 @@ def run_reference(args):
                sponge=lambda X, Y, Z: oacm.sponge_mask(X, Y, Z, phys["sponge_L"], phys["sponge_width"],
                                                        phys["sponge_delta"]))
     S.initial_grid()
+    initial = (list(fo.sorted_leaves()), [S.U[fo.leaves[l]].copy() for l in fo.sorted_leaves()])
     S.refine_all()
-    n = len(fo.leaves)
-    for _ in range(args.warmup):
-        S.rhs(S.U)
+    refined = (list(fo.sorted_leaves()), [S.U[fo.leaves[l]].copy() for l in fo.sorted_leaves()])
+    # one RHS evaluation of the refined sample on one core decides the sample size
     t0 = time.perf_counter()
-    for _ in range(args.steps):
-        S.rhs(S.U)
-    dt = time.perf_counter() - t0
-    value = n * grid["Bs"] ** 3 * args.steps / dt
+    S.rhs(S.U)
+    t1 = time.perf_counter() - t0
+    leaves, U, kind = (refined + ("refined once",)) if (args.steps + args.warmup) * t1 <= 150.0 else \
+        (initial + ("initial grid",))
+    cores = args.cpu_cores or os.cpu_count() or 1
+    value, slowest = oracle_all_cores(leaves, U, grid, phys, mask, cores, steps=args.steps, warmup=args.warmup)
+    n = len(leaves)
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * slowest / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": workload_name(grid), "sample": f"levels 2..3, {n} blocks of 17^3 after one "
-                   "refinement; one step = one oracle RHS evaluation (sync + RHS of every block)"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"{n} blocks x 17^3, {args.steps} RHS evaluations"},
+        "config": {"workload": workload_name(grid), "sample": f"levels 2..3, {kind}: {n} blocks of 17^3; one step = "
+                   f"one oracle RHS evaluation (sync + RHS of every block) in each of {cores} processes"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{n} blocks x 17^3, {args.steps} RHS evaluations per process, {cores} processes "
+                                   f"(nproc = {os.cpu_count()}); one core alone: {n * grid['Bs'] ** 3 / t1:.4g} "
+                                   f"point-updates/s"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -509,6 +667,10 @@ def main():
     ap.add_argument("--no-uniform", action="store_true")
     ap.add_argument("--no-cdf44", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint workload")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 run of the sphere workload")
+    ap.add_argument("--no-run200", action="store_true", help="skip the 200-step adaptive run of the sphere workload")
+    ap.add_argument("--cpu-cores", type=int, default=0,
+                    help="host cores for the oracle's all-core figure (default: all, os.cpu_count())")
     ap.add_argument("--wavelet", type=int, default=40, choices=[40, 44],
                     help="wavelet of the main line: 40 = CDF 4/0 (default), 44 = CDF 4/4")
     ap.add_argument("--sweep", action="store_true",
@@ -569,21 +731,36 @@ def main():
         h0 = f.last_step_stats()
         pu = 0
         stage_ms = 0.0
+        sync_ms = 0.0
         stage_bytes = 0.0
-        nev = []
+        nev, nst = [], []
+        # events between the step's three phases (refine, evolve, coarsen), as the paper splits
+        # its step time (Sec. 5.4)
+        pev = [torch.cuda.Event(enable_timing=True) for _ in range(3 * args.steps)]
         ev0.record(stream)
-        for _ in range(args.steps):
+        for k in range(args.steps):
             f.refine_all()
+            pev[3 * k].record(stream)
             n_ev = f.n_blocks()
             f.rk4_step(0.0)
-            f.coarsen()
+            pev[3 * k + 1].record(stream)
+            n_after, _ = f.coarsen()
+            pev[3 * k + 2].record(stream)
             st = f.last_step_stats()
             stage_ms += st["stage_ms"]
+            sync_ms += st["sync_ms"]
             stage_bytes += st["stage_bytes"]
             pu += 4 * n_ev * Bs3
             nev.append(n_ev)
+            nst.append(n_after)
         ev1.record(stream)
         barrier()
+        ph_ms = [0.0, 0.0, 0.0]
+        prev = ev0
+        for k in range(args.steps):
+            for q in range(3):
+                ph_ms[q] += prev.elapsed_time(pev[3 * k + q])
+                prev = pev[3 * k + q]
         launches = f.launch_count() - l0
         h1 = f.last_step_stats()
         ms = ev0.elapsed_time(ev1)
@@ -604,7 +781,16 @@ def main():
                 "avg_launch_ms": stage_ms / launches_stage,
                 "traffic": (traffic_ppu * float(np.mean(nev)) * Bs3 if traffic_ppu is not None else None),
                 "traffic_capture": capture,
-                "stage_share_of_step": round(stage_ms / t_max, 4)}
+                "stage_share_of_step": round(stage_ms / t_max, 4),
+                # the fused RHS + ghost-sync path: the stage kernels' algorithmic bytes over the
+                # time of the stage kernels and the per-stage synchronisation (fine wins and the
+                # coarse-face slabs) together
+                "path": {"achieved": round(stage_bytes / ((stage_ms + sync_ms) * 1e-3) / 1e9, 1),
+                         "frac": round(stage_bytes / ((stage_ms + sync_ms) * 1e-3) / 1e9 / peak, 4),
+                         "sync_ms_per_stage": sync_ms / launches_stage,
+                         "stage_ms_per_stage": stage_ms / launches_stage}}
+        roof["kernel"] = {0: "k_stage_pair<17> (fused RHS + RK4 stage, 2 points per thread)",
+                          1: "k_stage<float,17> (fused RHS + RK4 stage)"}[tuning["stage_variant"]]
 
         # end to end through the C-ABI with host buffers: write state, step, read state
         e2e = None
@@ -639,6 +825,14 @@ def main():
         batched = batched_comparison(A, args.precision) if rank == 0 and not args.no_batched else None
         cdf44 = (wavelet_comparison(A, stream, args.precision, args.Jmax, args.max_blocks)
                  if rank == 0 and not args.no_cdf44 and args.wavelet == 40 else None)
+        run200 = (adaptive_run(A, stream, args.precision, args.Jmax, args.max_blocks)
+                  if rank == 0 and not args.no_run200 else None)
+        fp64 = None
+        if rank == 0 and not args.no_fp64 and args.precision == 32:
+            try:
+                fp64 = fp64_measurement(A, stream, args.Jmax, args.max_blocks)
+            except Exception as e:  # noqa: BLE001
+                fp64 = {"error": f"{type(e).__name__}: {e}"}
         cpu = None
         if rank == 0 and world == 1 and not args.no_cpu_baseline:
             # bounded sample (10-30 s of one core): the same workload with levels 2..4, its grid
@@ -654,10 +848,18 @@ def main():
             U = f4.read_fields().astype(np.float64)
             del f4
             v, secs, nb = oracle_rhs_sample(leaves, U, g4, p4, m4)
-            cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+            cores = args.cpu_cores or os.cpu_count() or 1
+            try:
+                vall, sall = oracle_all_cores(leaves, U, g4, p4, m4, cores)
+            except Exception as e:  # noqa: BLE001
+                vall, sall = None, f"{type(e).__name__}: {e}"
+            cpu = {"value": vall if vall is not None else v, "unit": UNIT,
+                   "cores": cores if vall is not None else 1, "kind": "oracle",
                    "sample": f"one FP64 oracle RHS evaluation (ghost sync + RHS) over the same workload at "
-                             f"levels {g4['Jmin']}..{g4['Jmax']} after refinement, {nb} blocks x 17^3, "
-                             f"{secs:.1f} s"}
+                             f"levels {g4['Jmin']}..{g4['Jmax']} after refinement, {nb} blocks x 17^3, on each of "
+                             f"{cores} host processes at once (value: all together; nproc = {os.cpu_count()})",
+                   "all_cores_seconds": sall,
+                   "single_core": {"value": v, "cores": 1, "seconds": secs}}
 
         # the last GPU work of the run: a side measurement whose errors are reported, not raised
         adjoint = None
@@ -679,14 +881,21 @@ def main():
                        "points_evolved_mean": float(np.mean(nev)) * Bs3,
                        "l2": f"inputs larger than L2: state {4 * float(np.mean(nev)) * Bs3 * 4 * (args.precision // 8) / 1e9:.2f} GB per RK register x 4 registers",
                        "parallelism": f"replicas x{world}"},
+            "n_blocks_over_time": {"evolved": nev[::10], "after_coarsening": nst[::10], "every": 10,
+                                   "evolved_min_max": [min(nev), max(nev)]},
+            "phase_fractions": {"refine": ph_ms[0] / sum(ph_ms), "evolve": ph_ms[1] / sum(ph_ms),
+                                "coarsen": ph_ms[2] / sum(ph_ms)},
             "step_breakdown_ms": {
                 "stage_kernels": stage_ms / args.steps,
+                "sync_kernels": sync_ms / args.steps,
                 "host_topology": (h1["host_topology_ms"] - h0["host_topology_ms"]) / args.steps,
                 "host_tree": (h1["host_tree_ms"] - h0["host_tree_ms"]) / args.steps,
                 "total": t_max / args.steps},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "rk4_graph": graph,
             "batched": batched,
             "cdf44": cdf44,
+            "fp64": fp64,
+            "adaptive_200_steps": run200,
             "adjoint": adjoint,
             "uniform_roofline": uniform,
             "autotune": {"fine_wins_ctas_per_sm": tuned[0], "slab_ctas_per_sm": tuned[1],

@@ -145,7 +145,7 @@ enum { ACM_IC_TAYLOR_GREEN = 1, ACM_IC_UNIFORM = 2, ACM_IC_PULSE = 3, ACM_IC_PUL
  * the same tanh profile of the box's signed distance and u_s = omega x (x - x0).  Its pose
  * follows the forest's simulated time: chi is evaluated at every RK4 stage time and the
  * penalization uses u_s; acm_rk4_steps and acm_rk4_steps_batch refuse a moving mask
- * (ACM_EINVAL); the force of acm_diagnostics integrates chi (u - u_s).  Not yet run on a GPU.
+ * (ACM_EINVAL); the force of acm_diagnostics integrates chi (u - u_s).
  * ACM_MASK_FIELD (no parameters): chi is the caller's field (any geometry, e.g. a mask made
  * from a surface), written with acm_write_mask and 0 until then; u_s = 0.  It belongs to the
  * grid it was written for: acm_set_leaves, acm_init_uniform, acm_init_grid, acm_refine_all,
@@ -292,8 +292,7 @@ acm_status acm_adjoint_sphere(acm_forest* f, int nsteps, double dt, int ckpt, do
 /* The same for the moving plate (ACM_MASK_PLATE; ACM_EINVAL otherwise), from the forest's time:
  * the mask and the solid velocity follow the RK4 stage times, F_x integrates chi (u - u_s), and
  * *dJ_dalpha (host) receives the derivative with respect to the pitch amplitude alpha_m (the
- * plate's drag sensitivity of the full-scale configuration).  Workspace as acm_adjoint_bytes.
- * Not yet run on a GPU. */
+ * plate's drag sensitivity of the full-scale configuration).  Workspace as acm_adjoint_bytes. */
 acm_status acm_adjoint_plate_pitch(acm_forest* f, int nsteps, double dt, int ckpt, double w_energy, void* ws,
                                    size_t ws_bytes, double* J, double* dJ_dalpha, void* dJ_dU0, int64_t n_elems,
                                    int on_device);
@@ -427,6 +426,14 @@ typedef struct {
 } acm_step_stats;
 acm_status acm_enable_timing(acm_forest* f, int on);
 acm_status acm_last_step_stats(acm_forest* f, acm_step_stats* out);
+
+/* Fused multiply-add rate of the current device in flop/s (2 per FMA), measured by a kernel of
+ * this library: independent chains of dependent FMAs in FP64 (precision 64) or FP32 (32) on every
+ * SM, the median CUDA-event time of five launches after a warm-up, on `stream` (cudaStream_t,
+ * NULL = legacy default); synchronises the stream.  The FP64 stage kernel's roofline denominator
+ * (GB300's FP64 pipe, not HBM, bounds FP64 fields).  ACM_EINVAL for another precision or a NULL
+ * output, ACM_ECUDA if a launch fails.  No counterpart in the paper. */
+acm_status acm_fma_rate(int precision, double* flops_out, void* stream);
 
 /* Total kernel launches since creation (every launch of this library). */
 int64_t acm_launch_count(const acm_forest* f);

@@ -68,6 +68,7 @@ EXPORTS = {
                                 C.POINTER(C.c_int)]),
     "acm_autotune": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "acm_set_stage_variant": (C.c_int, [C.c_void_p, C.c_int]),
+    "acm_fma_rate": (C.c_int, [C.c_int, C.POINTER(C.c_double), C.c_void_p]),
     "acm_get_tuning": (C.c_int, [C.c_void_p, C.c_void_p]),
     "acm_adjoint_bytes": (C.c_size_t, [C.c_void_p, C.c_int, C.c_int]),
     "acm_adjoint_sphere": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_int, C.c_double, C.c_void_p, C.c_size_t,
@@ -151,6 +152,16 @@ def rk4_steps_batch(forests, nsteps, dt=0.0, graph=True):
         msg = lib().acm_status_string(st).decode()
         raise AcmError(f"libacm status {st}: {msg}")
     return list(t), bool(g.value)
+
+
+def fma_rate(precision, stream=None):
+    """Fused multiply-add rate of the current GPU in flop/s, measured by the library's own kernel
+    (acm_fma_rate)."""
+    v = C.c_double()
+    st = lib().acm_fma_rate(int(precision), C.byref(v), C.c_void_p(0 if stream is None else stream.cuda_stream))
+    if st != 0:
+        raise AcmError(f"libacm status {st}: {lib().acm_status_string(st).decode()}")
+    return v.value
 
 
 def max_norms_noalloc(fields, n_blocks, Bs, precision, norms_out, stream=None):
