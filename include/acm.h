@@ -269,15 +269,17 @@ acm_status acm_get_tuning(const acm_forest* f, acm_tuning* out);
  * radius (dJ_dtheta[0..3] = d/dcx, d/dcy, d/dcz, d/dR, host) and the initial state (dJ_dU0,
  * FP64 values whatever the forest's precision, block order, fields layout of acm_read_fields,
  * n_elems = n_blocks*4*Bs^3; device pointer if on_device, else host; may be NULL).  FP32 or
- * FP64 forests with the sphere mask (ACM_EINVAL otherwise): the forward steps run in the
- * forest's precision, every adjoint variable and sum in FP64.  States are recomputed from
+ * FP64 forests with the sphere mask (ACM_EINVAL otherwise): the forward steps and the adjoint
+ * variables are in the forest's precision, the sums onto the mask parameters (and the returned
+ * gradients) in FP64.  States are recomputed from
  * snapshots by the schedule of acm_checkpoint_schedule(nsteps, ckpt): ckpt > 0 keeps the state
  * at every ckpt-th step and recomputes each segment with its states stored; ckpt < 0 is binomial
  * checkpointing with -ckpt snapshots (the fewest recomputed steps for that memory).  Every
  * schedule takes the same steps in the same arithmetic, so the result does not depend on it
- * (up to the order of FP64 atomic sums).  ws: caller device buffer of at least
- * acm_adjoint_bytes(f, nsteps, ckpt) bytes (ACM_ENOMEM if smaller): four FP64 registers, the
- * snapshots and five state registers in the forest's precision, and the mask's sensitivity.
+ * (up to the order of floating-point atomic sums).  ws: caller device buffer of at least
+ * acm_adjoint_bytes(f, nsteps, ckpt) bytes (ACM_ENOMEM if smaller): nine registers and the
+ * snapshots in the forest's precision, the mask's sensitivity and one FP64 array of
+ * n_blocks x 4 x Bs^3 values (all sized for max_blocks).
  * acm_adjoint_bytes returns 0 for an invalid ckpt (0), nsteps outside [1, 2^20] or a refused
  * binomial schedule (see acm_checkpoint_schedule).  The
  * forest's state and time are unchanged on return, also when the sweep stops on an error; the

@@ -1,21 +1,24 @@
-// Discrete adjoint of the RK4 steps on a frozen grid: kernels of libacm.  The forward state and
-// the mask are in the forest's precision T; every adjoint variable, coefficient and sum is FP64
-// (indexed like a register of T: same block, component and point offsets).
+// Discrete adjoint of the RK4 steps on a frozen grid: kernels of libacm.  The forward state, the
+// mask and the adjoint variables are in the forest's precision T; the sums over the grid that make
+// the gradient with respect to the mask parameters are FP64, and so is the gradient with respect
+// to U_0 handed to the caller.
 //
 // One RK4 step (Sec. 2.3) maps U to U' = V + dt/6 (K1 + 2 K2 + 2 K3 + K4), V = W U, with
 // K_s = G(Y_s) the right-hand side of eqs. (u_eqn-1, p_eqn-1) (Sec. 2.1-2.2) of the synchronised
 // stage state.  G(Y) = loc(E W Y): W is fine wins on the block boundaries, E fills each block's
 // face halos (3 layers) from the finest leaf holding a point, else by the tensor DD-4 prediction
-// (Sec. 3.1, 4.2), and loc is the block-local stencil arithmetic.  Its transpose applied to an
-// adjoint stage variable kappa is built in three launches:
-//   k_adj_weights   per interior point the coefficients of loc^T (from Y's values and kappa),
-//   k_adj_scatter   per halo or interior point of every block the sum of the stencil terms that
-//                   read it (loc^T), added to the point's source in the register (E^T: the
-//                   block's own point, the leaf holding it, or the DD-4 stencil's sources),
-//   k_adj_fw_T      W^T: a boundary point held by a finer leaf passes its value to that leaf's
-//                   point and is cleared.
-// The elementwise RK4 adjoint combination, the objective's direct terms and the reduction of the
-// mask sensitivity onto the sphere's centre and radius complete the step (host side in api.cu).
+// (Sec. 3.1, 4.2), and loc is the block-local stencil arithmetic.  The adjoint of one stage,
+// nu = W^T E^T loc^T kappa with kappa = c_lam lam + c_nu nu' (the RK4 adjoint combination), takes
+// three launches:
+//   k_adj_stage  loc^T at every block's own interior points, in gather form (a z-march like the
+//                forward stage kernel), with the combination for kappa, the running sum of the
+//                stage nus and the mask sensitivity fused in;
+//   k_adj_halo   loc^T at the face-halo points and E^T: added to the points they were read from
+//                (the finest leaf holding the point, or its DD-4 prediction's even points);
+//   k_adj_fw_T   W^T: a boundary point held by a finer leaf passes its value to that leaf's point
+//                and is cleared.
+// The objective's direct terms and the reduction of the mask sensitivity onto the sphere's centre
+// and radius complete the sweep (host side in api.cu).
 //
 // This header holds the kernels and one launcher per kernel and (T, BS); each of the
 // translation units adjoint_{f,d}{9,17}.cu instantiates one pair (they compile in parallel),
@@ -25,43 +28,18 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
-#include "common.cuh"
-#include "kernels.hpp"
+#include "stage_common.cuh"
 
 namespace acm {
 namespace {
 
 constexpr int kNA = 256;
-constexpr int kNW = kAdjWeightsPerPoint;   // loc^T coefficients per interior point (layout in k_adj_weights)
 
 __device__ __forceinline__ double lattice_coord(const PhysK& ph, int4 bi, int a, int i, int M, double h) {
   const int g = a == 0 ? bi.y : (a == 1 ? bi.z : bi.w);
   const long long N = ((long long)ph.nroot[a] << bi.x) * M;
   const long long gi = (long long)g * M + i;              // in [0, N]; the seam x = L is taken as 0
   return (double)(gi >= N ? gi - N : gi) * h;
-}
-
-// Sponge profile (the stage kernel's, in FP64): the largest of the three axis profiles.
-__device__ __forceinline__ double sponge_at(const PhysK& ph, int4 bi, int x, int y, int z, int M, double h) {
-  const int q[3] = {x, y, z};
-  double s = 0.0;
-  for (int a = 0; a < 3; ++a) {
-    const double c = lattice_coord(ph, bi, a, q[a], M, h);
-    const double dist = fmin(c, ph.sp_L[a] - c);
-    const double v = 0.5 * (1.0 - tanh((dist - ph.sp_width) / ph.sp_delta));
-    s = v > s ? v : s;
-  }
-  return s;
-}
-
-// Value of the stage state at local point (x, y, z) of a block: its own point inside, else the
-// ghost value (finest leaf holding it, else the DD-4 prediction).
-template <typename T, int BS>
-__device__ __forceinline__ double yval(const T* Y, const int* nbh, size_t own, int x, int y, int z, int f) {
-  using L = Lay<T, BS>;
-  constexpr int M = L::M;
-  if (x >= 0 && x <= M && y >= 0 && y <= M && z >= 0 && z <= M) return (double)Y[own + (size_t)f * L::FS + L::idx(x, y, z)];
-  return (double)point_value<T, BS>(Y, nbh, x, y, z, f);
 }
 
 // Moving rigid box (mask kind 2) at offset r = x - x_0 from its pivot: the solid velocity
@@ -106,6 +84,20 @@ __device__ __forceinline__ BoxPoint box_point(const MaskK& m, double rx, double 
   return o;
 }
 
+// Block reduction of one double per thread of an NT-thread CTA into *out (one atomic per CTA).
+template <int NT>
+__device__ __forceinline__ void block_add_n(double v, double* out) {
+  __shared__ double red[NT / 32];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int k = 0; k < NT / 32; ++k) t += red[k];
+    atomicAdd(out, t);
+  }
+}
+
 // Block reduction of one double per thread into *out (one atomic per CTA).
 __device__ __forceinline__ void block_add(double v, double* out) {
   __shared__ double red[kNA / 32];
@@ -119,159 +111,344 @@ __device__ __forceinline__ void block_add(double v, double* out) {
   }
 }
 
-// Coefficients of loc^T at each interior point p of block `rank` (kappa: the adjoint stage
-// variable, Y: the synchronised stage state):
-//   [3i + j]  A_ij = -u_j kappa_i      (i, j < 3; weight of D1_j applied to field i)
-//   [9]       P    = -c0^2 kappa_p     (weight of D1_j applied to field j, from the p equation)
-//   [10 + i]  V_i  = nu kappa_i        (weight of every D2 applied to field i)
-//   [13 + i]  G_i  = -kappa_i          (weight of D1_i applied to p)
-//   [16 + j]  pointwise term of field j: -sum_i kappa_i D1_j u_i - (chi/C_eta + chi_sp/C_sp) kappa_j,
-//             and for p: -(C_gamma + chi_sp/C_sp) kappa_p
-// The mask sensitivity -sum_i kappa_i u_i / C_eta is added to gchi.
-// With a moving box (m.kind == 2) the mask's and the solid velocity's sensitivities are turned into
-// d/dtheta at once (the pose is the stage's) and summed into *dtheta instead of gchi.
+// ---- the adjoint of one RK stage: nu = W^T E^T loc(E W Y)^T kappa ------------------------------------
+// loc^T kappa at a target point q, for the weights at the block's interior sources p (zero
+// outside the interior; h-free first differences Dt_j g(q) = sum_m a_m [g(q - m e_j) - g(q + m e_j)],
+// the symmetric second difference D2_j g(q) = sum_k d2_k g(q + k e_j), d2 = (-1, 16, -30, 16, -1)):
+//   nu_i(q) = -1/h [sum_j Dt_j(u_j kappa_i) + c0^2 Dt_i(kappa_p)] + nu/(12 h^2) sum_j D2_j(kappa_i)
+//             - 1/h sum_k kappa_k(q) Dh_i u_k(q) - (chi/C_eta + chi_sp/C_sp) kappa_i(q)      (i < 3)
+//   nu_p(q) = -1/h sum_j Dt_j(kappa_j) - (C_gamma + chi_sp/C_sp) kappa_p(q)
+// (Dh_i: the forward's h-free first difference along i, of the stage state with its ghost values).
+// The first two lines are the transposed stencils of the convective, pressure, divergence and
+// viscous terms, the last ones the pointwise terms of the linearisation.
+//
+// k_adj_stage evaluates this at the block's own interior targets in gather form (one CTA per
+// block, a thread per (x, y) pencil marching in z, as the forward stage kernel): kappa and u of
+// the current plane in shared memory with a zero halo (sources outside the interior weigh
+// nothing), kappa and u of the planes z - 3 .. z + 3 in a register ring, and for the pointwise
+// term the stage state's x/y halos by cp.async from the neighbours (copy or decimation) or from
+// the coarse-face slabs, as the forward reads them.  kappa = c_lam lam + c_nu nu' is formed as it
+// is read (nu': the next RK stage's nu), and the running sum of the stage nus is updated from nu'
+// in the same pass.  The own targets are stored with plain writes; the targets in the face halos
+// (k_adj_halo) go to other blocks' points through E^T afterwards.
 template <typename T, int BS>
-__global__ void __launch_bounds__(kNA) k_adj_weights(const T* Y, const double* kap, const T* chi,
-                                                     double* gchi, double* wgt, const int32_t* blist,
-                                                     const int4* binfo, const int32_t* nbh_all, const PhysK ph,
-                                                     const MaskK m, double* dtheta) {
+struct AdjCfg {
+  static constexpr int NT = ((BS * BS + 31) / 32) * 32;
+  static constexpr int H = BS + 6;
+  static constexpr int W = sizeof(T) == 4 ? BS + 32 : BS + 6;   // bank-conflict-free rows (FP32)
+  static constexpr int PW = H * W;
+  static constexpr int NC = 7;                                   // planes: u, v, w, kappa_0..3
+  static constexpr int NH = 36 * BS;                             // x/y halo values of u, v, w per plane
+  static constexpr int HPT = (NH + NT - 1) / NT;
+  static constexpr size_t BUF = (size_t)2 * NC * PW * sizeof(T);
+  static constexpr size_t bytes = BUF + (size_t)NH * 12;
+  static constexpr int MINB = sizeof(T) == 4 ? 2 : 1;
+  static_assert(NC * PW < 0x8000, "plane buffer offsets must fit 15 bits");
+};
+
+template <typename T, int BS>
+__global__ void __launch_bounds__(AdjCfg<T, BS>::NT, AdjCfg<T, BS>::MINB)
+k_adj_stage(const AdjStageK<T> a, const TopoK tp, const PhysK ph, const MaskK m) {
   using L = Lay<T, BS>;
-  constexpr int M = L::M, N3 = BS * BS * BS;
-  __shared__ int nbh[kNbhStride];
+  using C = AdjCfg<T, BS>;
+  constexpr int M = L::M;
+  constexpr int NT = C::NT, W = C::W, PW = C::PW, NH = C::NH, HPT = C::HPT;
+  extern __shared__ __align__(16) unsigned char smem[];
+  T* buf = reinterpret_cast<T*>(smem);                                       // [2][7][PW]
+  unsigned* hlo = reinterpret_cast<unsigned*>(smem + C::BUF);
+  unsigned* hhi = hlo + NH;
+  unsigned* hzd = hhi + NH;
+  __shared__ int ftype[6];
+  __shared__ int fs[6][4];
+  __shared__ T sp[3][BS];
+
+  const int tid = threadIdx.x;
   const int rank = blockIdx.x;
-  for (int i = threadIdx.x; i < kNbhStride; i += kNA) nbh[i] = nbh_all[(size_t)rank * kNbhStride + i];
+  const int slot = tp.blist[rank];
+  const int4 bi = tp.binfo[rank];
+  const int* nbh = tp.nbh + (size_t)rank * kNbhStride;
+  stage_faces(tid, nbh, tp.slabidx, rank, ftype, fs);
+  stage_sponge<T, BS>(tid, ph, bi, sp);
+  // the kappa planes' halos stay zero (sources outside the block weigh nothing)
+  for (int i = tid; i < 2 * C::NC * PW; i += NT) buf[i] = T(0);
   __syncthreads();
-  const int slot = blist[rank];
-  const int4 bi = binfo[rank];
-  const double h = ph.h[bi.x], ih = 1.0 / h;
-  const double a[3] = {ph.a1, ph.a2, ph.a3};
-  const size_t own = (size_t)slot * L::BLK;
-  double* w = wgt + (size_t)rank * kNW * N3;
-  const bool moving = m.kind == 2;
-  double dth = 0.0;
-  for (int t = threadIdx.x; t < N3; t += kNA) {
-    const int x = t % BS, y = (t / BS) % BS, z = t / (BS * BS);
-    const int pi = L::idx(x, y, z);
-    double u[3], k[4], du[3][3];
-    for (int f = 0; f < 3; ++f) u[f] = (double)Y[own + (size_t)f * L::FS + pi];
-    for (int f = 0; f < 4; ++f) k[f] = kap[own + (size_t)f * L::FS + pi];
-    for (int i = 0; i < 3; ++i)
-      for (int j = 0; j < 3; ++j) {
-        double s = 0.0;
-        for (int m = 1; m <= 3; ++m) {
-          const int dx = j == 0 ? m : 0, dy = j == 1 ? m : 0, dz = j == 2 ? m : 0;
-          s += a[m - 1] * (yval<T, BS>(Y, nbh, own, x + dx, y + dy, z + dz, i) -
-                           yval<T, BS>(Y, nbh, own, x - dx, y - dy, z - dz, i));
-        }
-        du[i][j] = s * ih;
+
+  const T a1 = T(ph.a1), a2 = T(ph.a2), a3 = T(ph.a3);
+  const T ih = T(1.0 / ph.h[bi.x]);
+  const T nu_ih2 = T(ph.nu / (12.0 * ph.h[bi.x] * ph.h[bi.x]));
+  const T c0sq = T(ph.c0sq), inv_ceta = T(ph.inv_ceta), inv_csp = T(ph.inv_csp), cgam = T(ph.cgamma);
+  const T c_lam = T(a.c_lam), c_nu = T(a.c_nu);
+  const bool act = tid < BS * BS;
+  const int x = act ? tid % BS : 0, y = act ? tid / BS : 0;
+  const size_t bo = (size_t)slot * L::BLK;
+  const T* __restrict__ Yb = a.Y + bo;
+
+  auto y_value = [&](int zz, int f) -> T {
+    if (zz >= 0 && zz <= M) return Yb[(size_t)f * L::FS + L::idx(x, y, zz)];
+    if (zz < 0) return *halo_ptr<T, BS>(ftype, fs, a.Y, a.slab, 4, -zz, x, y, f);
+    return *halo_ptr<T, BS>(ftype, fs, a.Y, a.slab, 5, zz - M, x, y, f);
+  };
+  auto kappa = [&](int zz, int f) -> T {
+    if (zz < 0 || zz > M) return T(0);
+    const size_t o = bo + (size_t)f * L::FS + L::idx(x, y, zz);
+    T k = c_lam * a.lam[o];
+    if (a.nup) k += c_nu * a.nup[o];
+    return k;
+  };
+
+  // x/y halo values of u, v, w of every plane as affine functions of z (the forward kernel's
+  // table): entry i is read at (z <= M/2 ? lo : hi) + z * stride from Y (or the slab buffer,
+  // flag bit 15) and lands at dst: hzd = stride << 16 | slab << 15 | dst.
+#pragma unroll
+  for (int k = 0; k < HPT; ++k) {
+    const int i = tid + k * NT;
+    if (i < NH) {
+      const int g = i / (3 * BS), el = i % (3 * BS);
+      const int F = g & 3, f = g >> 2;
+      int l, t;
+      if (F < 2) { l = el % 3 + 1; t = el / 3; }
+      else { t = el % BS; l = el / BS + 1; }
+      int hx, hy;
+      if (F == 0) { hx = -l; hy = t; }
+      else if (F == 1) { hx = M + l; hy = t; }
+      else if (F == 2) { hx = t; hy = -l; }
+      else { hx = t; hy = M + l; }
+      const unsigned dst = (unsigned)(f * PW + (hy + 3) * W + hx + 3);
+      const int ty = ftype[F];
+      const bool plus = F & 1;
+      const int ax = F >> 1;
+      if (ty == kTypeCoarser) {
+        const unsigned o = (unsigned)((((size_t)fs[F][0] * 4 + f) * 3 + (l - 1)) * BS * BS + t);
+        hlo[i] = o; hhi[i] = o; hzd[i] = ((unsigned)BS << 16) | 0x8000u | dst;
+      } else if (ty == kTypeLeaf) {
+        const int nl = plus ? l : M - l;
+        const int xx = ax == 0 ? nl : t, yy = ax == 0 ? t : nl;
+        const unsigned o = (unsigned)((size_t)fs[F][0] * L::BLK + (size_t)f * L::FS + L::idx(xx, yy, 0));
+        hlo[i] = o; hhi[i] = o; hzd[i] = ((unsigned)L::PP << 16) | dst;
+      } else {
+        const int c0 = t > M / 2;
+        const int nl = plus ? 2 * l : M - 2 * l;
+        const int u0 = 2 * t - c0 * M;
+        const int xx = ax == 0 ? nl : u0, yy = ax == 0 ? u0 : nl;
+        const unsigned lo = (unsigned)((size_t)fs[F][c0] * L::BLK + (size_t)f * L::FS + L::idx(xx, yy, 0));
+        const unsigned hi = (unsigned)((size_t)fs[F][c0 + 2] * L::BLK + (size_t)f * L::FS + L::idx(xx, yy, 0)) -
+                            (unsigned)(M * L::PP);
+        hlo[i] = lo; hhi[i] = hi; hzd[i] = ((unsigned)(2 * L::PP) << 16) | dst;
       }
-    const double c = ph.mask ? (double)chi[(size_t)slot * L::FS + pi] : 0.0;
-    const double cs = ph.sponge ? sponge_at(ph, bi, x, y, z, M, h) : 0.0;
-    for (int i = 0; i < 3; ++i)
-      for (int j = 0; j < 3; ++j) w[(size_t)(3 * i + j) * N3 + t] = -u[j] * k[i];
-    w[(size_t)9 * N3 + t] = -ph.c0sq * k[3];
-    for (int i = 0; i < 3; ++i) {
-      w[(size_t)(10 + i) * N3 + t] = ph.nu * k[i];
-      w[(size_t)(13 + i) * N3 + t] = -k[i];
-    }
-    for (int j = 0; j < 3; ++j) {
-      double s = 0.0;
-      for (int i = 0; i < 3; ++i) s -= k[i] * du[i][j];
-      w[(size_t)(16 + j) * N3 + t] = s - (c * ph.inv_ceta + cs * ph.inv_csp) * k[j];
-    }
-    w[(size_t)19 * N3 + t] = -(ph.cgamma + cs * ph.inv_csp) * k[3];
-    if (moving) {
-      const BoxPoint bp = box_point(m, lattice_coord(ph, bi, 0, x, M, h) - m.p[9],
-                                    lattice_coord(ph, bi, 1, y, M, h) - m.p[10],
-                                    lattice_coord(ph, bi, 2, z, M, h) - m.p[11]);
-      double gc = 0.0, gu = 0.0;
-      for (int i = 0; i < 3; ++i) {
-        gc -= k[i] * (u[i] - bp.us[i]) * ph.inv_ceta;      // d/dchi of -chi (u - u_s) / C_eta
-        gu += c * k[i] * ph.inv_ceta * bp.dus[i];          // d/du_s, times d u_s / dtheta
-      }
-      dth += gc * bp.dchi + gu;
-    } else if (ph.mask) {
-      gchi[(size_t)slot * L::FS + pi] -= (k[0] * u[0] + k[1] * u[1] + k[2] * u[2]) * ph.inv_ceta;
     }
   }
-  if (moving) block_add(dth, dtheta);
+  auto issue_halos = [&](int zz, T* B) {
+#pragma unroll
+    for (int k = 0; k < HPT; ++k) {
+      const int i = tid + k * NT;
+      if (i < NH) {
+        const unsigned zd = hzd[i];
+        const unsigned off = (zz > M / 2 ? hhi[i] : hlo[i]) + (unsigned)zz * (zd >> 16);
+        cp_async_elem(B + (zd & 0x7fffu), ((zd & 0x8000u) ? a.slab : a.Y) + (size_t)off);
+      }
+    }
+    cp_async_commit();
+  };
+
+  // register rings: qy[c][k] = u_c of plane z + k - 3, qk[f][k] = kappa_f of plane z + k - 3
+  T qy[3][8], qk[4][8];
+#pragma unroll
+  for (int k = 0; k < 7; ++k) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) qy[c][k] = act ? y_value(k - 3, c) : T(0);
+#pragma unroll
+    for (int f = 0; f < 4; ++f) qk[f][k] = act ? kappa(k - 3, f) : T(0);
+  }
+#pragma unroll
+  for (int f = 0; f < 4; ++f) qk[f][7] = T(0);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) qy[c][7] = T(0);
+  __syncthreads();
+  issue_halos(0, buf);
+
+  const int ci = (y + 3) * W + x + 3;
+  const bool moving = m.kind == 2;
+  double dth = 0.0;
+  const double hd = ph.h[bi.x];
+  for (int z = 0; z <= M; ++z) {
+    T* B = buf + (z & 1) * C::NC * PW;
+    if (act) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) B[c * PW + ci] = qy[c][3];
+#pragma unroll
+      for (int f = 0; f < 4; ++f) B[(3 + f) * PW + ci] = qk[f][3];
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    if (z < M) issue_halos(z + 1, buf + ((z + 1) & 1) * C::NC * PW);
+    if (act) {
+      if (z + 4 <= M + 3) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) qy[c][7] = y_value(z + 4, c);
+#pragma unroll
+        for (int f = 0; f < 4; ++f) qk[f][7] = kappa(z + 4, f);
+      }
+      const size_t pi = (size_t)L::idx(x, y, z);
+      // h-free first differences Dh_j u_i of the stage state (with its ghost values)
+      T du[3][3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const T* s = B + c * PW;
+        du[c][0] = a1 * (s[ci + 1] - s[ci - 1]) + a2 * (s[ci + 2] - s[ci - 2]) + a3 * (s[ci + 3] - s[ci - 3]);
+        du[c][1] = a1 * (s[ci + W] - s[ci - W]) + a2 * (s[ci + 2 * W] - s[ci - 2 * W]) +
+                   a3 * (s[ci + 3 * W] - s[ci - 3 * W]);
+        du[c][2] = a1 * (qy[c][4] - qy[c][2]) + a2 * (qy[c][5] - qy[c][1]) + a3 * (qy[c][6] - qy[c][0]);
+      }
+      // transposed first differences of the products u_j kappa_i and of kappa, and the second
+      // differences of kappa, along x (shared plane), y (shared plane) and z (register rings)
+      T tconv[3] = {T(0), T(0), T(0)};     // sum_j Dt_j(u_j kappa_i)
+      T tk[4];                              // Dt_j(kappa_f) along j = f (f < 3); for p: sum_j Dt_j(kappa_j)
+      T d2k[3] = {T(0), T(0), T(0)};       // sum_j D2_j(kappa_i)
+      T tkp[3];                             // Dt_i(kappa_p)
+      tk[3] = T(0);
+      const T* su = B;
+      const T* sk[4] = {B + 3 * PW, B + 4 * PW, B + 5 * PW, B + 6 * PW};
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        // tap values at offsets -3..3 (index o + 3) along direction j
+        T uj[7], kf[4][7];
+#pragma unroll
+        for (int o = -3; o <= 3; ++o) {
+          if (j < 2) {
+            const int st = j == 0 ? o : o * W;
+            uj[o + 3] = su[j * PW + ci + st];
+#pragma unroll
+            for (int f = 0; f < 4; ++f) kf[f][o + 3] = sk[f][ci + st];
+          } else {
+            uj[o + 3] = qy[2][o + 3];
+#pragma unroll
+            for (int f = 0; f < 4; ++f) kf[f][o + 3] = qk[f][o + 3];
+          }
+        }
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          const T g1 = uj[2] * kf[i][2] - uj[4] * kf[i][4];
+          const T g2 = uj[1] * kf[i][1] - uj[5] * kf[i][5];
+          const T g3 = uj[0] * kf[i][0] - uj[6] * kf[i][6];
+          tconv[i] += a1 * g1 + a2 * g2 + a3 * g3;
+          d2k[i] += T(16) * (kf[i][2] + kf[i][4]) - (kf[i][1] + kf[i][5]) - T(30) * kf[i][3];
+        }
+        tkp[j] = a1 * (kf[3][2] - kf[3][4]) + a2 * (kf[3][1] - kf[3][5]) + a3 * (kf[3][0] - kf[3][6]);
+        tk[3] += a1 * (kf[j][2] - kf[j][4]) + a2 * (kf[j][1] - kf[j][5]) + a3 * (kf[j][0] - kf[j][6]);
+      }
+      const T k0 = qk[0][3], k1 = qk[1][3], k2 = qk[2][3], k3 = qk[3][3];
+      const T chiv = ph.mask ? a.chi[(size_t)slot * L::FS + pi] : T(0);
+      const T cs = ph.sponge ? tmax(tmax(sp[0][x], sp[1][y]), sp[2][z]) : T(0);
+      const T damp = chiv * inv_ceta + cs * inv_csp;
+      T out[4];
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+        out[i] = -ih * (tconv[i] + c0sq * tkp[i]) + nu_ih2 * d2k[i] -
+                 ih * (k0 * du[0][i] + k1 * du[1][i] + k2 * du[2][i]) - damp * qk[i][3];
+      out[3] = -ih * tk[3] - (cgam + cs * inv_csp) * k3;
+#pragma unroll
+      for (int f = 0; f < 4; ++f) {
+        const size_t o = bo + (size_t)f * L::FS + pi;
+        a.nu[o] = out[f];
+        if (a.sum_mode == 1) a.sum[o] = a.nup[o];
+        else if (a.sum_mode == 2) a.sum[o] += a.nup[o];
+      }
+      const T u = qy[0][3], v = qy[1][3], w = qy[2][3];
+      if (moving) {
+        const BoxPoint bp = box_point(m, lattice_coord(ph, bi, 0, x, M, hd) - m.p[9],
+                                      lattice_coord(ph, bi, 1, y, M, hd) - m.p[10],
+                                      lattice_coord(ph, bi, 2, z, M, hd) - m.p[11]);
+        const double kk[3] = {(double)k0, (double)k1, (double)k2}, uu[3] = {(double)u, (double)v, (double)w};
+        double gc = 0.0, gu = 0.0;
+        for (int i = 0; i < 3; ++i) {
+          gc -= kk[i] * (uu[i] - bp.us[i]) * ph.inv_ceta;     // d/dchi of -chi (u - u_s) / C_eta
+          gu += (double)chiv * kk[i] * ph.inv_ceta * bp.dus[i]; // d/du_s, times d u_s / dtheta
+        }
+        dth += gc * bp.dchi + gu;
+      } else if (ph.mask && a.gchi) {
+        a.gchi[(size_t)slot * L::FS + pi] -= (k0 * u + k1 * v + k2 * w) * inv_ceta;
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 7; ++k) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) qy[c][k] = qy[c][k + 1];
+#pragma unroll
+      for (int f = 0; f < 4; ++f) qk[f][k] = qk[f][k + 1];
+    }
+  }
+  if (moving) {
+    __syncthreads();
+    block_add_n<AdjCfg<T, BS>::NT>(dth, a.dtheta);
+  }
 }
 
-// loc^T and E^T: for every point q of block `rank`'s extended region (interior and the six face
-// halos of depth 3) and component f, the sum of the stencil terms of the interior points that
-// read q, added to q's source in `nu` (FP64 atomics: several blocks reach one point).
+// The targets of loc^T in block `rank`'s face halos (3 layers beyond each face): only sources
+// along the face normal are inside the block, so a halo point q at distance l gets
+//   nu_i(q) = -1/h sum_{m=l..3} (+-a_m) [u_n kappa_i + delta_{in} c0^2 kappa_p](q -+ m e_n)
+//             + nu/(12 h^2) sum_{k=l..2} d2_k kappa_i(q -+ k e_n)                      (i < 3)
+//   nu_p(q) = -1/h sum_{m=l..3} (+-a_m) kappa_n(q -+ m e_n)
+// (n the normal axis, the sign that of the face), added through E^T to the point's source: the
+// finest leaf holding q, else the even points of its tensor DD-4 prediction (FP atomics: several
+// blocks reach one point).  Runs after k_adj_stage, which stored the own targets.
 template <typename T, int BS>
-__global__ void __launch_bounds__(kNA) k_adj_scatter(const double* wgt, double* nu, const int32_t* blist,
-                                                     const int4* binfo, const int32_t* nbh_all, const PhysK ph,
-                                                     int* err) {
+__global__ void __launch_bounds__(kNA) k_adj_halo(const AdjStageK<T> a, const TopoK tp, const PhysK ph, int* err) {
   using L = Lay<T, BS>;
-  constexpr int M = L::M, N3 = BS * BS * BS, NH = 6 * 3 * BS * BS;
+  constexpr int M = L::M, NQ = 6 * 3 * BS * BS;
   __shared__ int nbh[kNbhStride];
   const int rank = blockIdx.x;
-  for (int i = threadIdx.x; i < kNbhStride; i += kNA) nbh[i] = nbh_all[(size_t)rank * kNbhStride + i];
+  for (int i = threadIdx.x; i < kNbhStride; i += kNA) nbh[i] = tp.nbh[(size_t)rank * kNbhStride + i];
   __syncthreads();
-  const int slot = blist[rank];
-  const int4 bi = binfo[rank];
-  const double h = ph.h[bi.x], ih = 1.0 / h, ih2 = 1.0 / (12.0 * h * h);
-  const double a[3] = {ph.a1, ph.a2, ph.a3};
-  const double d2[5] = {-1.0, 16.0, -30.0, 16.0, -1.0};
-  const double* w = wgt + (size_t)rank * kNW * N3;
-  const size_t own = (size_t)slot * L::BLK;
-  auto inside = [](int x, int y, int z) { return x >= 0 && x <= M && y >= 0 && y <= M && z >= 0 && z <= M; };
-  auto wat = [&](int k, int x, int y, int z) { return w[(size_t)k * N3 + (z * BS + y) * BS + x]; };
-  for (int t = threadIdx.x; t < 4 * (N3 + NH); t += kNA) {
-    const int f = t / (N3 + NH), r = t % (N3 + NH);
+  const size_t bo = (size_t)tp.blist[rank] * L::BLK;
+  const int4 bi = tp.binfo[rank];
+  const T ih = T(1.0 / ph.h[bi.x]);
+  const T nu_ih2 = T(ph.nu / (12.0 * ph.h[bi.x] * ph.h[bi.x]));
+  const T c0sq = T(ph.c0sq);
+  const T am[3] = {T(ph.a1), T(ph.a2), T(ph.a3)};
+  const T d2[2] = {T(16), T(-1)};
+  const T c_lam = T(a.c_lam), c_nu = T(a.c_nu);
+  auto kappa = [&](const int (&p)[3], int f) -> T {
+    const size_t o = bo + (size_t)f * L::FS + L::idx(p[0], p[1], p[2]);
+    T k = c_lam * a.lam[o];
+    if (a.nup) k += c_nu * a.nup[o];
+    return k;
+  };
+  for (int t = threadIdx.x; t < 4 * NQ; t += kNA) {
+    const int f = t / NQ, e = t % NQ;
+    const int F = e / (3 * BS * BS), l = (e / (BS * BS)) % 3 + 1, uv = e % (BS * BS);
+    const int ax = F >> 1, side = F & 1;
+    const int o1 = (ax + 1) % 3, o2 = (ax + 2) % 3;
     int q[3];
-    if (r < N3) {
-      q[0] = r % BS; q[1] = (r / BS) % BS; q[2] = r / (BS * BS);
-    } else {
-      const int e = r - N3, F = e / (3 * BS * BS), l = (e / (BS * BS)) % 3, uv = e % (BS * BS);
-      const int ax = F >> 1, side = F & 1;
-      const int o1 = (ax + 1) % 3, o2 = (ax + 2) % 3;
-      q[ax] = side ? M + 1 + l : -1 - l;
-      q[o1] = uv % BS;
-      q[o2] = uv / BS;
-    }
-    double de = 0.0;
-    for (int j = 0; j < 3; ++j) {
-      // D1_j: point p = q - m e_j reads q with +a_m/h, p = q + m e_j with -a_m/h
-      const int kidx = f < 3 ? 3 * f + j : 13 + j;
-      for (int m = 1; m <= 3; ++m) {
-        int p[3] = {q[0], q[1], q[2]};
-        p[j] = q[j] - m;
-        if (inside(p[0], p[1], p[2])) {
-          double wv = wat(kidx, p[0], p[1], p[2]);
-          if (f < 3 && f == j) wv += wat(9, p[0], p[1], p[2]);
-          de += a[m - 1] * ih * wv;
-        }
-        p[j] = q[j] + m;
-        if (inside(p[0], p[1], p[2])) {
-          double wv = wat(kidx, p[0], p[1], p[2]);
-          if (f < 3 && f == j) wv += wat(9, p[0], p[1], p[2]);
-          de -= a[m - 1] * ih * wv;
-        }
+    q[ax] = side ? M + l : -l;
+    q[o1] = uv % BS;
+    q[o2] = uv / BS;
+    // sources p = q - dir m e_n inside the block (m >= l), dir = +1 beyond the upper face
+    const int dir = side ? 1 : -1;
+    const T sg = side ? T(1) : T(-1);
+    T de = T(0), dd = T(0);
+    for (int mm = l; mm <= 3; ++mm) {
+      int p[3] = {q[0], q[1], q[2]};
+      p[ax] -= dir * mm;
+      T wv;
+      if (f < 3) {
+        const T un = a.Y[bo + (size_t)ax * L::FS + L::idx(p[0], p[1], p[2])];
+        wv = un * kappa(p, f);
+        if (f == ax) wv += c0sq * kappa(p, 3);
+        if (mm <= 2) dd += d2[mm - 1] * kappa(p, f);
+      } else {
+        wv = kappa(p, ax);
       }
-      // D2_j on the velocity: p = q - k e_j reads q with d2[k + 2]
-      if (f < 3)
-        for (int kk = -2; kk <= 2; ++kk) {
-          int p[3] = {q[0], q[1], q[2]};
-          p[j] = q[j] - kk;
-          if (inside(p[0], p[1], p[2])) de += d2[kk + 2] * ih2 * wat(10 + f, p[0], p[1], p[2]);
-        }
+      de += sg * am[mm - 1] * wv;
     }
-    if (r < N3) {
-      de += wat(16 + f, q[0], q[1], q[2]);
-      atomicAdd(&nu[own + (size_t)f * L::FS + L::idx(q[0], q[1], q[2])], de);
-      continue;
-    }
-    if (de == 0.0) continue;
+    de = -ih * de + (f < 3 ? nu_ih2 * dd : T(0));
+    if (de == T(0)) continue;
     const long long o = direct_offset<T, BS>(nbh, q[0], q[1], q[2], f);
     if (o >= 0) {
-      atomicAdd(&nu[o], de);
+      atomicAdd(&a.nu[o], de);
       continue;
     }
     // predicted ghost: the tensor DD-4 weights (x, then y, then z) of its even stencil points
-    const double wd[4] = {-1.0 / 16.0, 9.0 / 16.0, 9.0 / 16.0, -1.0 / 16.0};
+    const T wd[4] = {T(-1) / T(16), T(9) / T(16), T(9) / T(16), T(-1) / T(16)};
     const int off[4] = {-3, -1, 1, 3};
     const int nx = (q[0] & 1) ? 4 : 1, ny = (q[1] & 1) ? 4 : 1, nz = (q[2] & 1) ? 4 : 1;
     for (int kz = 0; kz < nz; ++kz)
@@ -280,13 +457,13 @@ __global__ void __launch_bounds__(kNA) k_adj_scatter(const double* wgt, double* 
           const int xx = nx == 4 ? q[0] + off[kx] : q[0];
           const int yy = ny == 4 ? q[1] + off[ky] : q[1];
           const int zz = nz == 4 ? q[2] + off[kz] : q[2];
-          const double wt = (nx == 4 ? wd[kx] : 1.0) * (ny == 4 ? wd[ky] : 1.0) * (nz == 4 ? wd[kz] : 1.0);
+          const T wt = (nx == 4 ? wd[kx] : T(1)) * (ny == 4 ? wd[ky] : T(1)) * (nz == 4 ? wd[kz] : T(1));
           const long long o2 = direct_offset<T, BS>(nbh, xx, yy, zz, f);
           if (o2 < 0) {
             atomicOr(err, 8);
             continue;
           }
-          atomicAdd(&nu[o2], wt * de);
+          atomicAdd(&a.nu[o2], wt * de);
         }
   }
 }
@@ -295,7 +472,7 @@ __global__ void __launch_bounds__(kNA) k_adj_scatter(const double* wgt, double* 
 // box among those containing it, in the order the forward search uses) adds its value to that
 // leaf's point and is cleared.
 template <typename T, int BS>
-__global__ void __launch_bounds__(kNA) k_adj_fw_T(double* r, const int32_t* blist, const int32_t* nbh_all,
+__global__ void __launch_bounds__(kNA) k_adj_fw_T(T* r, const int32_t* blist, const int32_t* nbh_all,
                                                   const uint8_t* finer) {
   using L = Lay<T, BS>;
   constexpr int M = L::M, N3 = BS * BS * BS;
@@ -333,21 +510,19 @@ __global__ void __launch_bounds__(kNA) k_adj_fw_T(double* r, const int32_t* blis
     if (src < 0) continue;
     for (int f = 0; f < 4; ++f) {
       const size_t o = own + (size_t)f * L::FS + L::idx(p[0], p[1], p[2]);
-      const double v = r[o];
-      r[o] = 0.0;
-      if (v != 0.0) atomicAdd(&r[(size_t)src + (size_t)f * L::FS], v);
+      const T v = r[o];
+      r[o] = T(0);
+      if (v != T(0)) atomicAdd(&r[(size_t)src + (size_t)f * L::FS], v);
     }
   }
 }
 
-// out = a x + b y over the blocks of the list (whole block strides); y may be null.
+// out = x + y + z over the blocks of the list (whole block strides).
 template <typename T, int BS>
-__global__ void __launch_bounds__(kNA) k_adj_lin(double* out, double a, const double* x, double b, const double* y,
-                                                 const int32_t* blist) {
+__global__ void __launch_bounds__(kNA) k_adj_sum3(T* out, const T* x, const T* y, const T* z, const int32_t* blist) {
   using L = Lay<T, BS>;
   const size_t base = (size_t)blist[blockIdx.x] * L::BLK;
-  for (int i = threadIdx.x; i < L::BLK; i += kNA)
-    out[base + i] = a * x[base + i] + (y ? b * y[base + i] : 0.0);
+  for (int i = threadIdx.x; i < L::BLK; i += kNA) out[base + i] = x[base + i] + y[base + i] + z[base + i];
 }
 
 // Direct terms of (1/N) [F_x(U) + w_E E(U)] (Sec. 2.2, half-open points, weight h^3): into lam
@@ -355,7 +530,7 @@ __global__ void __launch_bounds__(kNA) k_adj_lin(double* out, double a, const do
 // With a moving box the force integrates chi (u - u_s) at the state's time (pose in m): the direct
 // d/dtheta of the force is summed into *dtheta.
 template <typename T, int BS>
-__global__ void __launch_bounds__(kNA) k_adj_objective(const T* U, const T* chi, double* lam, double* gchi,
+__global__ void __launch_bounds__(kNA) k_adj_objective(const T* U, const T* chi, T* lam, T* gchi,
                                                        const int32_t* blist, const int4* binfo, const PhysK ph,
                                                        double wN, double wE, const MaskK m, double* dtheta) {
   using L = Lay<T, BS>;
@@ -371,16 +546,16 @@ __global__ void __launch_bounds__(kNA) k_adj_objective(const T* U, const T* chi,
     const int pi = L::idx(x, y, z);
     const double u = (double)U[own + pi];
     const double c = ph.mask ? (double)chi[(size_t)slot * L::FS + pi] : 0.0;
-    lam[own + pi] += wN * (c * ph.inv_ceta + wE * u) * h3;
+    lam[own + pi] += T(wN * (c * ph.inv_ceta + wE * u) * h3);
     for (int f = 1; f < 3; ++f)
-      lam[own + (size_t)f * L::FS + pi] += wN * wE * (double)U[own + (size_t)f * L::FS + pi] * h3;
+      lam[own + (size_t)f * L::FS + pi] += T(wN * wE * (double)U[own + (size_t)f * L::FS + pi] * h3);
     if (moving) {
       const BoxPoint bp = box_point(m, lattice_coord(ph, bi, 0, x, M, h) - m.p[9],
                                     lattice_coord(ph, bi, 1, y, M, h) - m.p[10],
                                     lattice_coord(ph, bi, 2, z, M, h) - m.p[11]);
       dth += wN * h3 * ph.inv_ceta * ((u - bp.us[0]) * bp.dchi - c * bp.dus[0]);
     } else if (ph.mask) {
-      gchi[(size_t)slot * L::FS + pi] += wN * u * h3 * ph.inv_ceta;
+      gchi[(size_t)slot * L::FS + pi] += T(wN * u * h3 * ph.inv_ceta);
     }
   }
   if (moving) block_add(dth, dtheta);
@@ -389,7 +564,7 @@ __global__ void __launch_bounds__(kNA) k_adj_objective(const T* U, const T* chi,
 // sum over all points of gchi * d chi / d (cx, cy, cz, R) for the sphere mask
 // chi = (1 - tanh((|x - c| - R)/delta))/2 (Sec. 2.2), into out[0..3].
 template <typename T, int BS>
-__global__ void __launch_bounds__(kNA) k_adj_theta(const double* gchi, const int32_t* blist, const int4* binfo,
+__global__ void __launch_bounds__(kNA) k_adj_theta(const T* gchi, const int32_t* blist, const int4* binfo,
                                                    const PhysK ph, const MaskK m, double* out) {
   using L = Lay<T, BS>;
   constexpr int M = L::M, N3 = BS * BS * BS;
@@ -399,7 +574,7 @@ __global__ void __launch_bounds__(kNA) k_adj_theta(const double* gchi, const int
   double s[4] = {0.0, 0.0, 0.0, 0.0};
   for (int t = threadIdx.x; t < N3; t += kNA) {
     const int x = t % BS, y = (t / BS) % BS, z = t / (BS * BS);
-    const double g = gchi[(size_t)slot * L::FS + L::idx(x, y, z)];
+    const double g = (double)gchi[(size_t)slot * L::FS + L::idx(x, y, z)];
     if (g == 0.0) continue;
     const double rx = lattice_coord(ph, bi, 0, x, M, h) - m.p[0];
     const double ry = lattice_coord(ph, bi, 1, y, M, h) - m.p[1];
@@ -428,28 +603,28 @@ __global__ void __launch_bounds__(kNA) k_adj_theta(const double* gchi, const int
 
 // Block-order copy of an FP64 register indexed like a register of T: dense[rank][f][z][y][x].
 template <typename T, int BS>
-__global__ void __launch_bounds__(kNA) k_adj_gather(const double* r, double* dense, const int32_t* blist) {
+__global__ void __launch_bounds__(kNA) k_adj_gather(const T* r, double* dense, const int32_t* blist) {
   using L = Lay<T, BS>;
   constexpr int N3 = BS * BS * BS;
   const size_t own = (size_t)blist[blockIdx.x] * L::BLK;
   double* d = dense + (size_t)blockIdx.x * 4 * N3;
   for (int t = threadIdx.x; t < 4 * N3; t += kNA) {
     const int f = t / N3, r3 = t % N3;
-    d[t] = r[own + (size_t)f * L::FS + L::idx(r3 % BS, (r3 / BS) % BS, r3 / (BS * BS))];
+    d[t] = (double)r[own + (size_t)f * L::FS + L::idx(r3 % BS, (r3 / BS) % BS, r3 / (BS * BS))];
   }
 }
 
 // The inverse copy: dense[rank][f][z][y][x] into the register's interior points (the register's
 // padding is left as it is).
 template <typename T, int BS>
-__global__ void __launch_bounds__(kNA) k_adj_put(const double* dense, double* r, const int32_t* blist) {
+__global__ void __launch_bounds__(kNA) k_adj_put(const double* dense, T* r, const int32_t* blist) {
   using L = Lay<T, BS>;
   constexpr int N3 = BS * BS * BS;
   const size_t own = (size_t)blist[blockIdx.x] * L::BLK;
   const double* d = dense + (size_t)blockIdx.x * 4 * N3;
   for (int t = threadIdx.x; t < 4 * N3; t += kNA) {
     const int f = t / N3, r3 = t % N3;
-    r[own + (size_t)f * L::FS + L::idx(r3 % BS, (r3 / BS) % BS, r3 / (BS * BS))] = d[t];
+    r[own + (size_t)f * L::FS + L::idx(r3 % BS, (r3 / BS) % BS, r3 / (BS * BS))] = T(d[t]);
   }
 }
 
@@ -460,44 +635,44 @@ inline dim3 g1(int64_t n) { return dim3((unsigned)n); }
 namespace adj {
 
 template <typename T, int BS>
-void jgt(const T* Y, const double* kap, const T* chi, double* gchi, double* wgt, double* nu, const int32_t* blist,
-         const int4* binfo, const int32_t* nbh, const uint8_t* finer, int64_t n, const PhysK& ph, const MaskK& m,
-         double* dtheta, int* err, cudaStream_t st) {
-  k_adj_weights<T, BS><<<g1(n), kNA, 0, st>>>(Y, kap, chi, gchi, wgt, blist, binfo, nbh, ph, m, dtheta);
-  k_adj_scatter<T, BS><<<g1(n), kNA, 0, st>>>(wgt, nu, blist, binfo, nbh, ph, err);
-  k_adj_fw_T<T, BS><<<g1(n), kNA, 0, st>>>(nu, blist, nbh, finer);
+void stage(const AdjStageK<T>& a, const TopoK& t, const PhysK& ph, const MaskK& m, const uint8_t* finer, int* err,
+           cudaStream_t st) {
+  static std::atomic<unsigned long long> opted{0};
+  smem_opt_in_stage(k_adj_stage<T, BS>, AdjCfg<T, BS>::bytes, opted);
+  k_adj_stage<T, BS><<<g1(t.n), AdjCfg<T, BS>::NT, AdjCfg<T, BS>::bytes, st>>>(a, t, ph, m);
+  k_adj_halo<T, BS><<<g1(t.n), kNA, 0, st>>>(a, t, ph, err);
+  k_adj_fw_T<T, BS><<<g1(t.n), kNA, 0, st>>>(a.nu, t.blist, t.nbh, finer);
 }
 
 template <typename T, int BS>
-void fw_T(double* r, const int32_t* blist, const int32_t* nbh, const uint8_t* finer, int64_t n, cudaStream_t st) {
+void fw_T(T* r, const int32_t* blist, const int32_t* nbh, const uint8_t* finer, int64_t n, cudaStream_t st) {
   k_adj_fw_T<T, BS><<<g1(n), kNA, 0, st>>>(r, blist, nbh, finer);
 }
 
 template <typename T, int BS>
-void lin(double* out, double a, const double* x, double b, const double* y, const int32_t* blist, int64_t n,
-         cudaStream_t st) {
-  k_adj_lin<T, BS><<<g1(n), kNA, 0, st>>>(out, a, x, b, y, blist);
+void sum3(T* out, const T* x, const T* y, const T* z, const int32_t* blist, int64_t n, cudaStream_t st) {
+  k_adj_sum3<T, BS><<<g1(n), kNA, 0, st>>>(out, x, y, z, blist);
 }
 
 template <typename T, int BS>
-void objective(const T* U, const T* chi, double* lam, double* gchi, const int32_t* blist, const int4* binfo,
+void objective(const T* U, const T* chi, T* lam, T* gchi, const int32_t* blist, const int4* binfo,
                int64_t n, const PhysK& ph, double wN, double wE, const MaskK& m, double* dtheta, cudaStream_t st) {
   k_adj_objective<T, BS><<<g1(n), kNA, 0, st>>>(U, chi, lam, gchi, blist, binfo, ph, wN, wE, m, dtheta);
 }
 
 template <typename T, int BS>
-void theta(const double* gchi, const int32_t* blist, const int4* binfo, int64_t n, const PhysK& ph, const MaskK& m,
+void theta(const T* gchi, const int32_t* blist, const int4* binfo, int64_t n, const PhysK& ph, const MaskK& m,
            double* out, cudaStream_t st) {
   k_adj_theta<T, BS><<<g1(n), kNA, 0, st>>>(gchi, blist, binfo, ph, m, out);
 }
 
 template <typename T, int BS>
-void gather(const double* r, double* dense, const int32_t* blist, int64_t n, cudaStream_t st) {
+void gather(const T* r, double* dense, const int32_t* blist, int64_t n, cudaStream_t st) {
   k_adj_gather<T, BS><<<g1(n), kNA, 0, st>>>(r, dense, blist);
 }
 
 template <typename T, int BS>
-void put(const double* dense, double* r, const int32_t* blist, int64_t n, cudaStream_t st) {
+void put(const double* dense, T* r, const int32_t* blist, int64_t n, cudaStream_t st) {
   k_adj_put<T, BS><<<g1(n), kNA, 0, st>>>(dense, r, blist);
 }
 
@@ -508,17 +683,15 @@ void put(const double* dense, double* r, const int32_t* blist, int64_t n, cudaSt
 #define ACM_ADJ_INSTANTIATE(T, BS)                                                                                 \
   namespace acm {                                                                                                  \
   namespace adj {                                                                                                  \
-  template void jgt<T, BS>(const T*, const double*, const T*, double*, double*, double*, const int32_t*, const int4*, \
-                           const int32_t*, const uint8_t*, int64_t, const PhysK&, const MaskK&, double*, int*,       \
-                           cudaStream_t);                                                                          \
-  template void fw_T<T, BS>(double*, const int32_t*, const int32_t*, const uint8_t*, int64_t, cudaStream_t);         \
-  template void lin<T, BS>(double*, double, const double*, double, const double*, const int32_t*, int64_t,           \
-                           cudaStream_t);                                                                          \
-  template void objective<T, BS>(const T*, const T*, double*, double*, const int32_t*, const int4*, int64_t,         \
+  template void stage<T, BS>(const AdjStageK<T>&, const TopoK&, const PhysK&, const MaskK&, const uint8_t*, int*,   \
+                             cudaStream_t);                                                                        \
+  template void fw_T<T, BS>(T*, const int32_t*, const int32_t*, const uint8_t*, int64_t, cudaStream_t);              \
+  template void sum3<T, BS>(T*, const T*, const T*, const T*, const int32_t*, int64_t, cudaStream_t);                \
+  template void objective<T, BS>(const T*, const T*, T*, T*, const int32_t*, const int4*, int64_t,                   \
                                  const PhysK&, double, double, const MaskK&, double*, cudaStream_t);               \
-  template void theta<T, BS>(const double*, const int32_t*, const int4*, int64_t, const PhysK&, const MaskK&,        \
+  template void theta<T, BS>(const T*, const int32_t*, const int4*, int64_t, const PhysK&, const MaskK&,             \
                              double*, cudaStream_t);                                                               \
-  template void gather<T, BS>(const double*, double*, const int32_t*, int64_t, cudaStream_t);                        \
-  template void put<T, BS>(const double*, double*, const int32_t*, int64_t, cudaStream_t);                           \
+  template void gather<T, BS>(const T*, double*, const int32_t*, int64_t, cudaStream_t);                             \
+  template void put<T, BS>(const double*, T*, const int32_t*, int64_t, cudaStream_t);                                \
   }                                                                                                                \
   }

@@ -1092,14 +1092,15 @@ acm_status autotune(acm_forest* f, int* fw_ctas, int* slab_ctas) {
 }
 
 // ---- discrete adjoint of RK4 steps on the frozen grid (FP64 forests) ------------------------------
-// Workspace (caller-provided, 256-byte aligned regions): registers lam, kappa, nu, sum of nu, the 4
-// stage states of the step being differentiated, the c + 1 states of a checkpoint segment, the
-// ceil(N / c) checkpoints, the mask sensitivity (one component), the loc^T coefficients and the
-// 4 parameter sums.
+// Workspace (caller-provided, 256-byte aligned regions), all adjoint registers in the forest's
+// precision and indexed like its registers: lam, the nu of two consecutive RK stages, the running
+// sum of the stage nus, the 4 stage states of the step being differentiated, the step's starting
+// state, the snapshots of the checkpoint schedule, the mask sensitivity (one component), a dense
+// FP64 array (n_blocks x 4 x Bs^3: the caller's dL/dU_N coming in, dJ/dU_0 going out) and the 4
+// parameter sums (FP64).
 struct AdjLayout {
-  size_t lam, kap, nu, sum, y[4], tape, ck, gchi, wgt, theta, total;
-  size_t reg;    // bytes of an FP64 adjoint register (indexed like a register of the forest)
-  size_t sreg;   // bytes of a state register in the forest's precision
+  size_t lam, nu[2], sum, y[4], tape, ck, gchi, dense, theta, total;
+  size_t reg;    // bytes of a register in the forest's precision
   int64_t nslots;   // snapshots of the checkpoint schedule (ck: snapshot 0, 1, ...)
 };
 
@@ -1109,19 +1110,18 @@ AdjLayout adj_layout(const acm_forest* f, int nsteps, int policy) {
   AdjLayout L{};
   L.nslots = acm::ckpt::snapshots_needed(nsteps, policy);
   if (L.nslots < 1) return L;
-  L.reg = (size_t)f->gp.max_blocks * (size_t)f->lay.BLK * 8;
-  L.sreg = (size_t)f->gp.max_blocks * (size_t)f->lay.BLK * f->esz;
+  L.reg = (size_t)f->gp.max_blocks * (size_t)f->lay.BLK * f->esz;
   size_t o = 0;
   auto take = [&](size_t b) { const size_t r = o; o = (o + b + 255) & ~(size_t)255; return r; };
   L.lam = take(L.reg);
-  L.kap = take(L.reg);
-  L.nu = take(L.reg);
+  L.nu[0] = take(L.reg);
+  L.nu[1] = take(L.reg);
   L.sum = take(L.reg);
-  for (int s = 0; s < 4; ++s) L.y[s] = take(L.sreg);
-  L.tape = take(L.sreg);
-  L.ck = take(L.sreg * (size_t)L.nslots);
-  L.gchi = take((size_t)f->gp.max_blocks * (size_t)f->lay.FS * 8);
-  L.wgt = take(acm::adj_weight_doubles(f->gp.Bs, f->gp.max_blocks) * 8);
+  for (int s = 0; s < 4; ++s) L.y[s] = take(L.reg);
+  L.tape = take(L.reg);
+  L.ck = take(L.reg * (size_t)L.nslots);
+  L.gchi = take((size_t)f->gp.max_blocks * (size_t)f->lay.FS * f->esz);
+  L.dense = take((size_t)f->gp.max_blocks * 4 * (size_t)f->gp.Bs * f->gp.Bs * f->gp.Bs * 8);
   L.theta = take(64);
   L.total = o + 256;
   return L;
@@ -1192,29 +1192,24 @@ acm_status adjoint_sweep(acm_forest* f, int nsteps, double dt, int c, double wE,
   if ((dU0 || vjp) && n_elems != nb * 4 * (int64_t)f->gp.Bs * f->gp.Bs * f->gp.Bs)
     return fail(f, ACM_EINVAL, "element count does not match n_blocks*4*Bs^3");
   char* base = reinterpret_cast<char*>(((uintptr_t)ws + 255) & ~(uintptr_t)255);
-  auto R = [&](size_t off) { return reinterpret_cast<double*>(base + off); };
   auto S = [&](size_t off) { return reinterpret_cast<T*>(base + off); };
-  double* LAM = R(L.lam);
-  double* KAP = R(L.kap);
-  double* NU = R(L.nu);
-  double* SUM = R(L.sum);
+  T* LAM = S(L.lam);
+  T* NUR[2] = {S(L.nu[0]), S(L.nu[1])};
+  T* SUM = S(L.sum);
   T* Y[4] = {S(L.y[0]), S(L.y[1]), S(L.y[2]), S(L.y[3])};
-  double* GCHI = R(L.gchi);
-  double* WGT = R(L.wgt);
-  double* TH = R(L.theta);
-  auto CKP = [&](int k) { return S(L.ck + (size_t)k * L.sreg); };
+  T* GCHI = S(L.gchi);
+  double* DENSE = reinterpret_cast<double*>(base + L.dense);
+  double* TH = reinterpret_cast<double*>(base + L.theta);
+  auto CKP = [&](int k) { return S(L.ck + (size_t)k * L.reg); };
   const int Bs = f->gp.Bs;
   T* U = reinterpret_cast<T*>(f->U);
   const T* CHI = reinterpret_cast<const T*>(f->CHI);
+  T* SLAB = reinterpret_cast<T*>(f->SLAB);
   const double t0 = f->time;
   auto copy = [&](const T* src, T* dst) {
     acm::launch_copy_blocks<T>(Bs, src, dst, f->d_blist, 1, nb, f->st);
     ++f->launches;
     return cudaGetLastError();
-  };
-  auto lin = [&](double* out, double a, const double* x, double b, const double* y) {
-    acm::launch_adj_lin<T>(Bs, out, a, x, b, y, f->d_blist, nb, f->st);
-    ++f->launches;
   };
   // the moving plate's pose and mask at time t (a static mask needs nothing)
   auto pose_at = [&](double t) {
@@ -1223,14 +1218,31 @@ acm_status adjoint_sweep(acm_forest* f, int nsteps, double dt, int c, double wE,
     acm::launch_mask<T>(Bs, reinterpret_cast<T*>(f->CHI), f->d_blist, nullptr, nb, f->d_binfo, f->phk, f->mask, f->st);
     ++f->launches;
   };
-  // nu = J_G(Y)^T kappa (and the mask sensitivity of this stage into gchi, or for the plate
-  // straight into its parameter's sum)
-  auto jgt = [&](const T* Ys, double ts) {
+  // one RK stage's adjoint: nu_out = J_G(Y_s)^T kappa with kappa = c_lam lam + c_nu nup, the
+  // running sum of the stage nus updated from nup (sum_mode), the stage's mask sensitivity into
+  // gchi (or for the plate straight into its parameter's sum).  The stage state's halo slabs
+  // toward coarser neighbours are predicted first, as the forward's synchronisation does (the
+  // slab kernel's source lookups were cached by the forward's first stage on this grid).
+  const acm::TopoK tk_topo = topo(f);
+  auto astage = [&](const T* Ys, double ts, const T* nup, double c_lam, double c_nu, T* nu_out, int sum_mode) {
     pose_at(ts);
-    CK(cudaMemsetAsync(NU, 0, L.reg, f->st));
-    acm::launch_adj_jgt<T>(Bs, Ys, KAP, CHI, GCHI, WGT, NU, f->d_blist, f->d_binfo, f->d_nbh, f->d_finer, nb, f->phk,
-                           cur_mask(), TH, f->d_err, f->st);
-    f->launches += 3;
+    acm::launch_coarse_slabs<T>(Bs, Ys, SLAB, f->d_slabt, f->d_counts + 1, 6 * nb, f->d_nbh, f->d_slaboffc, 1,
+                                f->tune_slab_ctas, f->st);
+    acm::AdjStageK<T> a{};
+    a.Y = Ys;
+    a.slab = SLAB;
+    a.chi = CHI;
+    a.lam = LAM;
+    a.nup = nup;
+    a.c_lam = c_lam;
+    a.c_nu = c_nu;
+    a.nu = nu_out;
+    a.sum = SUM;
+    a.sum_mode = sum_mode;
+    a.gchi = GCHI;
+    a.dtheta = TH;
+    acm::launch_adj_stage<T>(Bs, a, tk_topo, f->phk, cur_mask(), f->d_finer, f->d_err, f->st);
+    f->launches += 4;
     return cudaGetLastError() == cudaSuccess ? ACM_OK : fail(f, ACM_ECUDA, "adjoint kernel launch failed");
   };
   auto objective = [&](const T* Us, double tn) {
@@ -1244,12 +1256,15 @@ acm_status adjoint_sweep(acm_forest* f, int nsteps, double dt, int c, double wE,
     return fail(f, ACM_EINVAL, "bad checkpoint policy");
   T* TAPE = S(L.tape);
   CK(cudaMemsetAsync(LAM, 0, L.reg, f->st));
-  CK(cudaMemsetAsync(GCHI, 0, (size_t)f->gp.max_blocks * f->lay.FS * 8, f->st));
+  CK(cudaMemsetAsync(NUR[0], 0, L.reg, f->st));
+  CK(cudaMemsetAsync(NUR[1], 0, L.reg, f->st));
+  CK(cudaMemsetAsync(SUM, 0, L.reg, f->st));
+  CK(cudaMemsetAsync(GCHI, 0, (size_t)f->gp.max_blocks * f->lay.FS * f->esz, f->st));
   CK(cudaMemsetAsync(TH, 0, 64, f->st));
   if (vjp) {
-    // lam_N into LAM's interior points (a host array is staged in KAP, free until the first turn)
-    const double* src = on_device ? reinterpret_cast<const double*>(lamN) : KAP;
-    if (!on_device) CK(cudaMemcpyAsync(KAP, lamN, (size_t)n_elems * 8, cudaMemcpyHostToDevice, f->st));
+    // lam_N into LAM's interior points (a host array is staged in the dense region)
+    const double* src = on_device ? reinterpret_cast<const double*>(lamN) : DENSE;
+    if (!on_device) CK(cudaMemcpyAsync(DENSE, lamN, (size_t)n_elems * 8, cudaMemcpyHostToDevice, f->st));
     acm::launch_adj_put<T>(Bs, src, LAM, f->d_blist, nb, f->st);
     CKL();
     ++f->launches;
@@ -1291,21 +1306,16 @@ acm_status adjoint_sweep(acm_forest* f, int nsteps, double dt, int c, double wE,
     if ((s = rk4<T>(f, dt, nullptr, Y))) return s;
     if ((s = reached(k + 1))) return s;
     if (k == nsteps - 1 && !vjp) objective(U, t0 + nsteps * dt);
-    lin(KAP, dt / 6.0, LAM, 0.0, nullptr);
-    if ((s = jgt(Y[3], tk + dt))) return s;
-    lin(SUM, 1.0, NU, 0.0, nullptr);
-    lin(KAP, dt / 3.0, LAM, dt, NU);
-    if ((s = jgt(Y[2], tk + 0.5 * dt))) return s;
-    lin(SUM, 1.0, SUM, 1.0, NU);
-    lin(KAP, dt / 3.0, LAM, dt / 2.0, NU);
-    if ((s = jgt(Y[1], tk + 0.5 * dt))) return s;
-    lin(SUM, 1.0, SUM, 1.0, NU);
-    lin(KAP, dt / 6.0, LAM, dt / 2.0, NU);
-    if ((s = jgt(Y[0], tk))) return s;
-    lin(SUM, 1.0, SUM, 1.0, NU);
-    lin(LAM, 1.0, LAM, 1.0, SUM);
+    // the step's adjoint, RK stages 4, 3, 2, 1 (kappa_4 = dt/6 lam, kappa_3 = dt/3 lam + dt nu_4,
+    // kappa_2 = dt/3 lam + dt/2 nu_3, kappa_1 = dt/6 lam + dt/2 nu_2), then
+    // lam <- W^T (lam + nu_4 + nu_3 + nu_2 + nu_1)
+    if ((s = astage(Y[3], tk + dt, nullptr, dt / 6.0, 0.0, NUR[0], 0))) return s;
+    if ((s = astage(Y[2], tk + 0.5 * dt, NUR[0], dt / 3.0, dt, NUR[1], 1))) return s;
+    if ((s = astage(Y[1], tk + 0.5 * dt, NUR[1], dt / 3.0, dt / 2.0, NUR[0], 2))) return s;
+    if ((s = astage(Y[0], tk, NUR[0], dt / 6.0, dt / 2.0, NUR[1], 2))) return s;
+    acm::launch_adj_sum3<T>(Bs, LAM, LAM, SUM, NUR[1], f->d_blist, nb, f->st);
     acm::launch_adj_fw_T<T>(Bs, LAM, f->d_blist, f->d_nbh, f->d_finer, nb, f->st);
-    ++f->launches;
+    f->launches += 2;
     if (k >= 1 && !vjp) objective(TAPE, tk);
   }
   if (!plate && f->mask_on && f->mask.kind == 1) {
@@ -1326,8 +1336,8 @@ acm_status adjoint_sweep(acm_forest* f, int nsteps, double dt, int c, double wE,
   if ((s = device_error(f))) return s;
   if (J_out) *J_out = J;
   if (dU0) {
-    // FP64 gradient in block order; a host copy goes through the workspace's second register
-    void* dense = on_device ? dU0 : reinterpret_cast<void*>(KAP);
+    // FP64 gradient in block order; a host copy goes through the dense region
+    void* dense = on_device ? dU0 : reinterpret_cast<void*>(DENSE);
     acm::launch_adj_gather<T>(Bs, LAM, reinterpret_cast<double*>(dense), f->d_blist, nb, f->st);
     CKL();
     ++f->launches;

@@ -213,39 +213,53 @@ template <typename T>
 void launch_scatter(int Bs, const T* dense, T* reg, const int32_t* blist, int64_t n, int ncomp,
                     cudaStream_t st);
 
-// ---- discrete adjoint (adjoint.cu): forward state and mask in T, adjoint variables FP64 ------------
-// (FP64 arrays are indexed like registers of T.)  Doubles of the loc^T coefficient scratch.
-constexpr int kAdjWeightsPerPoint = 20;
-size_t adj_weight_doubles(int Bs, int64_t nblocks);
-// nu += W^T E^T loc(E W Y)^T kappa for the blocks 0..n-1 (nu zeroed by the caller); the stage's
-// mask sensitivity is added to gchi, or, for a moving box (m.kind 2, the stage's pose), the
-// sensitivity to m's parameter is added to *dtheta.  err |= 8 if a ghost point's source is missing.
+// ---- discrete adjoint (adjoint.cu): state, mask and adjoint variables in T; the sums onto the
+// mask parameters and the U_0 gradient handed out in FP64 ------------------------------------------
+// One RK stage's adjoint: nu = W^T E^T loc(E W Y)^T kappa, kappa = c_lam lam + c_nu nup (nup may be
+// null: kappa = c_lam lam).  Y: the stage's synchronised state; slab: its coarse-face halo slabs.
+// sum_mode 1: sum = nup; 2: sum += nup (at interior points).  The stage's mask sensitivity is added
+// to gchi (sphere; null: none), or for a moving box (m.kind 2, the stage's pose) its parameter's
+// sensitivity to *dtheta.
 template <typename T>
-void launch_adj_jgt(int Bs, const T* Y, const double* kap, const T* chi, double* gchi, double* wgt, double* nu,
-                    const int32_t* blist, const int4* binfo, const int32_t* nbh, const uint8_t* finer, int64_t n,
-                    const PhysK& ph, const MaskK& m, double* dtheta, int* err, cudaStream_t st);
+struct AdjStageK {
+  const T* Y;
+  const T* slab;
+  const T* chi;
+  const T* lam;
+  const T* nup;
+  double c_lam, c_nu;
+  T* nu;
+  T* sum;
+  int sum_mode;
+  T* gchi;
+  double* dtheta;
+};
+// err |= 8 if a ghost point's source is missing.
+template <typename T>
+void launch_adj_stage(int Bs, const AdjStageK<T>& a, const TopoK& t, const PhysK& ph, const MaskK& m,
+                      const uint8_t* finer, int* err, cudaStream_t st);
 // W^T applied to register r in place.
 template <typename T>
-void launch_adj_fw_T(int Bs, double* r, const int32_t* blist, const int32_t* nbh, const uint8_t* finer, int64_t n,
+void launch_adj_fw_T(int Bs, T* r, const int32_t* blist, const int32_t* nbh, const uint8_t* finer, int64_t n,
                      cudaStream_t st);
-// out = a x + b y over every element of the listed blocks (y may be null).
+// out = x + y + z over every element of the listed blocks.
 template <typename T>
-void launch_adj_lin(int Bs, double* out, double a, const double* x, double b, const double* y, const int32_t* blist,
-                    int64_t n, cudaStream_t st);
+void launch_adj_sum3(int Bs, T* out, const T* x, const T* y, const T* z, const int32_t* blist, int64_t n,
+                     cudaStream_t st);
 // Direct terms of wN (F_x(U) + wE E(U)) into lam and gchi (a moving box: its parameter's direct
 // term into *dtheta, F_x integrating chi (u - u_s) at the pose of m).
 template <typename T>
-void launch_adj_objective(int Bs, const T* U, const T* chi, double* lam, double* gchi, const int32_t* blist,
+void launch_adj_objective(int Bs, const T* U, const T* chi, T* lam, T* gchi, const int32_t* blist,
                           const int4* binfo, int64_t n, const PhysK& ph, double wN, double wE, const MaskK& m,
                           double* dtheta, cudaStream_t st);
 // out[0..3] += sum gchi d chi / d (centre, radius) for the sphere mask m.
 template <typename T>
-void launch_adj_theta(int Bs, const double* gchi, const int32_t* blist, const int4* binfo, int64_t n, const PhysK& ph,
+void launch_adj_theta(int Bs, const T* gchi, const int32_t* blist, const int4* binfo, int64_t n, const PhysK& ph,
                       const MaskK& m, double* out, cudaStream_t st);
-// Block-order copy (n, 4, Bs^3) of an FP64 register, and its inverse (interior points only).
+// Block-order copy (n, 4, Bs^3, FP64) of an adjoint register, and its inverse (interior points only).
 template <typename T>
-void launch_adj_gather(int Bs, const double* r, double* dense, const int32_t* blist, int64_t n, cudaStream_t st);
+void launch_adj_gather(int Bs, const T* r, double* dense, const int32_t* blist, int64_t n, cudaStream_t st);
 template <typename T>
-void launch_adj_put(int Bs, const double* dense, double* r, const int32_t* blist, int64_t n, cudaStream_t st);
+void launch_adj_put(int Bs, const double* dense, T* r, const int32_t* blist, int64_t n, cudaStream_t st);
 
 }  // namespace acm
