@@ -454,7 +454,7 @@ def adjoint_measurement(A, stream, nsteps=100, ckpt_every=10, w_energy=0.1, bino
     f.close()
     eq = A.checkpoint_schedule(nsteps, ckpt_every=ckpt_every)
     bi = A.checkpoint_schedule(nsteps, snapshots=binomial_snapshots)
-    return {"workload": f"sphere, levels 2..4, frozen grid of {nb} blocks of 17^3, FP32 forward, FP64 adjoint, "
+    return {"workload": f"sphere, levels 2..4, frozen grid of {nb} blocks of 17^3, FP32 forward and adjoint, "
                         f"{nsteps} steps, checkpoints every {ckpt_every}", "forward_ms_per_step": fwd / nsteps,
             "adjoint_ms_per_step": adj / nsteps, "adjoint_over_forward": adj / fwd, "J": J,
             "dJ_dtheta": [float(v) for v in gth], "snapshots": eq["snapshots"],
@@ -463,6 +463,42 @@ def adjoint_measurement(A, stream, nsteps=100, ckpt_every=10, w_energy=0.1, bino
                          "adjoint_ms_per_step": adj4 / nsteps, "adjoint_over_forward": adj4 / fwd,
                          "rel_diff_J": abs(J4 - J) / abs(J),
                          "rel_diff_dJ_dtheta": float(np.abs(gth4 - gth).max() / np.abs(gth).max())}}
+
+
+def adjoint_at_scale(A, stream, nsteps=10, ckpt_every=5, w_energy=0.1):
+    """The adjoint on the main line's grid: the sphere workload refined to its evolved grid
+    (levels 2..5, 4608 blocks of 17^3), frozen, FP32; forward and adjoint time per step as in the
+    adjoint workload (which has 184 blocks, too few to fill the GPU)."""
+    import torch
+    grid, phys, mask, ic, _ = sphere_setup(Jmax=5, precision=32, max_blocks=6000)
+    f = A.Forest(grid, phys, stream=stream)
+    f.set_mask(A.ACM_MASK_SPHERE, mask)
+    f.init_grid(A.ACM_IC_UNIFORM, ic)
+    f.step(0.0)
+    f.refine_all()
+    dt = f.rk4_step(0.0)
+    U0 = f.read_fields().copy()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(nsteps):
+        f.rk4_step(dt)
+    e1.record(stream)
+    e1.synchronize()
+    fwd = e0.elapsed_time(e1)
+    f.write_fields(U0)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    J, gth, _ = f.adjoint_sphere(nsteps, dt, ckpt_every, w_energy)
+    e1.record(stream)
+    e1.synchronize()
+    adj = e0.elapsed_time(e1)
+    nb = f.n_blocks()
+    f.close()
+    return {"workload": f"sphere, the evolved grid of {nb} blocks of 17^3 (levels 2..5), frozen, FP32, {nsteps} "
+                        f"steps, checkpoints every {ckpt_every}", "forward_ms_per_step": fwd / nsteps,
+            "adjoint_ms_per_step": adj / nsteps, "adjoint_over_forward": adj / fwd, "J": J,
+            "dJ_dtheta": [float(v) for v in gth]}
 
 
 def batched_comparison(A, precision, seed=0, n=64, nsteps=10):
@@ -866,6 +902,7 @@ def main():
         if rank == 0 and not args.no_adjoint:
             try:
                 adjoint = adjoint_measurement(A, stream)
+                adjoint["at_scale"] = adjoint_at_scale(A, stream)
             except Exception as e:  # noqa: BLE001
                 adjoint = {"error": f"{type(e).__name__}: {e}"}
 

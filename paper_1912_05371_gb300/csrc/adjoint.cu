@@ -10,10 +10,10 @@ namespace acm {
 namespace adj {
 
 template <typename T, int BS>
-void stage(const AdjStageK<T>& a, const TopoK& t, const PhysK& ph, const MaskK& m, const uint8_t* finer, int* err,
+void stage(const AdjStageK<T>& a, const TopoK& t, const PhysK& ph, const MaskK& m, const FwTasks& fw, int* err,
            cudaStream_t st);
 template <typename T, int BS>
-void fw_T(T* r, const int32_t* blist, const int32_t* nbh, const uint8_t* finer, int64_t n, cudaStream_t st);
+void fw_T(T* r, const FwTasks& fw, const int32_t* blist, const int32_t* nbh, cudaStream_t st);
 template <typename T, int BS>
 void sum3(T* out, const T* x, const T* y, const T* z, const int32_t* blist, int64_t n, cudaStream_t st);
 template <typename T, int BS>
@@ -37,16 +37,16 @@ void put(const double* dense, T* r, const int32_t* blist, int64_t n, cudaStream_
 
 template <typename T>
 void launch_adj_stage(int Bs, const AdjStageK<T>& a, const TopoK& t, const PhysK& ph, const MaskK& m,
-                      const uint8_t* finer, int* err, cudaStream_t st) {
+                      const FwTasks& fw, int* err, cudaStream_t st) {
   if (t.n <= 0) return;
-  ACM_ADJ_BS(Bs, stage, a, t, ph, m, finer, err, st);
+  ACM_ADJ_BS(Bs, stage, a, t, ph, m, fw, err, st);
 }
 
 template <typename T>
-void launch_adj_fw_T(int Bs, T* r, const int32_t* blist, const int32_t* nbh, const uint8_t* finer, int64_t n,
+void launch_adj_fw_T(int Bs, T* r, const FwTasks& fw, const int32_t* blist, const int32_t* nbh, int64_t n,
                      cudaStream_t st) {
   if (n <= 0) return;
-  ACM_ADJ_BS(Bs, fw_T, r, blist, nbh, finer, n, st);
+  ACM_ADJ_BS(Bs, fw_T, r, fw, blist, nbh, st);
 }
 
 template <typename T>
@@ -85,8 +85,8 @@ void launch_adj_put(int Bs, const double* dense, T* r, const int32_t* blist, int
 
 #define ACM_ADJ_INST(T)                                                                                        \
   template void launch_adj_stage<T>(int, const AdjStageK<T>&, const TopoK&, const PhysK&, const MaskK&,         \
-                                    const uint8_t*, int*, cudaStream_t);                                      \
-  template void launch_adj_fw_T<T>(int, T*, const int32_t*, const int32_t*, const uint8_t*, int64_t, cudaStream_t); \
+                                    const FwTasks&, int*, cudaStream_t);                                      \
+  template void launch_adj_fw_T<T>(int, T*, const FwTasks&, const int32_t*, const int32_t*, int64_t, cudaStream_t); \
   template void launch_adj_sum3<T>(int, T*, const T*, const T*, const T*, const int32_t*, int64_t, cudaStream_t); \
   template void launch_adj_objective<T>(int, const T*, const T*, T*, T*, const int32_t*, const int4*, int64_t,  \
                                         const PhysK&, double, double, const MaskK&, double*, cudaStream_t);  \

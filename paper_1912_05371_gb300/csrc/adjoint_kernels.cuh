@@ -388,17 +388,39 @@ k_adj_stage(const AdjStageK<T> a, const TopoK tp, const PhysK ph, const MaskK m)
 //   nu_i(q) = -1/h sum_{m=l..3} (+-a_m) [u_n kappa_i + delta_{in} c0^2 kappa_p](q -+ m e_n)
 //             + nu/(12 h^2) sum_{k=l..2} d2_k kappa_i(q -+ k e_n)                      (i < 3)
 //   nu_p(q) = -1/h sum_{m=l..3} (+-a_m) kappa_n(q -+ m e_n)
-// (n the normal axis, the sign that of the face), added through E^T to the point's source: the
-// finest leaf holding q, else the even points of its tensor DD-4 prediction (FP atomics: several
-// blocks reach one point).  Runs after k_adj_stage, which stored the own targets.
+// (n the normal axis, the sign that of the face), added through E^T to the point q was read from.
+// One CTA per (block, face).  Across a same-level face that is the neighbour's point, across a
+// finer face the child's coinciding point (the forward's copy and decimation); fine wins' copies
+// between leaves are W's part (k_adj_fw_T).  Across a coarser face, q is held by a leaf if it lies
+// on one's lattice (its point gets the value), else it was predicted by the tensor DD-4 from the
+// even points of the 5 x (M/2 + 3)^2 coarse patch around the face: the transposed prediction is
+// summed per patch point in shared memory first, then each patch point goes to the leaf holding
+// it.  FP atomics: several blocks reach one point.  Runs after k_adj_stage.
+template <typename T, int BS>
+struct HaloCfg {
+  static constexpr int M = BS - 1;
+  static constexpr int NTG = M / 2 + 3;               // even fine tangential coordinates -2 .. M + 2
+  static constexpr int NPATCH = 5 * NTG * NTG;        // normal: 5 even fine coordinates beyond the face
+};
+
 template <typename T, int BS>
 __global__ void __launch_bounds__(kNA) k_adj_halo(const AdjStageK<T> a, const TopoK tp, const PhysK ph, int* err) {
   using L = Lay<T, BS>;
-  constexpr int M = L::M, NQ = 6 * 3 * BS * BS;
+  using H = HaloCfg<T, BS>;
+  constexpr int M = L::M, NTG = H::NTG, NP = H::NPATCH;
   __shared__ int nbh[kNbhStride];
-  const int rank = blockIdx.x;
+  __shared__ T acc[4 * NP];
+  const int rank = blockIdx.x / 6, F = blockIdx.x % 6;
   for (int i = threadIdx.x; i < kNbhStride; i += kNA) nbh[i] = tp.nbh[(size_t)rank * kNbhStride + i];
   __syncthreads();
+  const int ax = F >> 1, side = F & 1;
+  const int d = kFaceBox[F];
+  const int ty = nbh[kNbhType + d] & 15;
+  const bool coarse = ty != kTypeLeaf && ty != kTypeRefined;
+  if (coarse) {
+    for (int i = threadIdx.x; i < 4 * NP; i += kNA) acc[i] = T(0);
+    __syncthreads();
+  }
   const size_t bo = (size_t)tp.blist[rank] * L::BLK;
   const int4 bi = tp.binfo[rank];
   const T ih = T(1.0 / ph.h[bi.x]);
@@ -407,112 +429,194 @@ __global__ void __launch_bounds__(kNA) k_adj_halo(const AdjStageK<T> a, const To
   const T am[3] = {T(ph.a1), T(ph.a2), T(ph.a3)};
   const T d2[2] = {T(16), T(-1)};
   const T c_lam = T(a.c_lam), c_nu = T(a.c_nu);
-  auto kappa = [&](const int (&p)[3], int f) -> T {
-    const size_t o = bo + (size_t)f * L::FS + L::idx(p[0], p[1], p[2]);
-    T k = c_lam * a.lam[o];
-    if (a.nup) k += c_nu * a.nup[o];
-    return k;
+  // threads run along the tangential axis with the smaller memory stride (x for y and z faces)
+  const int o1 = ax == 0 ? 1 : 0, o2 = 3 - ax - o1;
+  const int dir = side ? 1 : -1;
+  const T sg = side ? T(1) : T(-1);
+  const T wd[4] = {T(-1) / T(16), T(9) / T(16), T(9) / T(16), T(-1) / T(16)};
+  // E^T of one halo target q of component f with value de
+  auto scatter = [&](const int (&q)[3], int f, int l, T de) {
+    if (!coarse) {
+      int s, lc[3];
+      if (ty == kTypeLeaf) {
+        s = nbh[8 * d];
+        lc[ax] = side ? l : M - l;
+        lc[o1] = q[o1];
+        lc[o2] = q[o2];
+      } else {
+        int c = (side ? 0 : 1) << ax;
+        const int b1 = q[o1] > M / 2, b2 = q[o2] > M / 2;
+        c |= (b1 << o1) | (b2 << o2);
+        s = nbh[8 * d + c];
+        lc[ax] = side ? 2 * l : M - 2 * l;
+        lc[o1] = 2 * q[o1] - b1 * M;
+        lc[o2] = 2 * q[o2] - b2 * M;
+      }
+      if (s < 0) {
+        atomicOr(err, 8);
+        return;
+      }
+      if (de != T(0)) atomicAdd(&a.nu[(size_t)s * L::BLK + (size_t)f * L::FS + L::idx(lc[0], lc[1], lc[2])], de);
+      return;
+    }
+    if (de == T(0)) return;
+    if (ty != kTypeCoarser || q[o1] == 0 || q[o1] == M || q[o2] == 0 || q[o2] == M) {
+      // on the face's boundary lines a leaf of this level or finer may hold q
+      const long long o = direct_offset<T, BS>(nbh, q[0], q[1], q[2], f);
+      if (o >= 0) {
+        atomicAdd(&a.nu[o], de);
+        return;
+      }
+    } else if (!((q[0] | q[1] | q[2]) & 1)) {
+      // strictly inside the face's box only the coarser leaf holds q, on its lattice here
+      const int oct = nbh[kNbhType + d] >> 4;
+      int lc[3];
+#pragma unroll
+      for (int ac = 0; ac < 3; ++ac) {
+        const int qb = q[ac] - (ac == ax ? (side ? M : -M) : 0);      // in box d's frame
+        lc[ac] = (((oct >> ac) & 1) * M + qb) >> 1;
+      }
+      const int s = nbh[8 * d];
+      if (s < 0) {
+        atomicOr(err, 8);
+        return;
+      }
+      atomicAdd(&a.nu[(size_t)s * L::BLK + (size_t)f * L::FS + L::idx(lc[0], lc[1], lc[2])], de);
+      return;
+    }
+    // predicted ghost: transposed tensor DD-4 (even points: weight 1, odd: -1, 9, 9, -1 over 16
+    // at -3, -1, 1, 3) onto the coarse patch (normal index from the face, tangential (c + 2) / 2)
+    const int nn = (q[ax] & 1) ? 4 : 1, n1 = (q[o1] & 1) ? 4 : 1, n2 = (q[o2] & 1) ? 4 : 1;
+    const int off[4] = {-3, -1, 1, 3};
+    const int nbase = side ? M - 2 : -6;
+    for (int kn = 0; kn < nn; ++kn) {
+      const int cn = nn == 4 ? q[ax] + off[kn] : q[ax];
+      const T wn = nn == 4 ? wd[kn] : T(1);
+      for (int k2 = 0; k2 < n2; ++k2) {
+        const int c2 = n2 == 4 ? q[o2] + off[k2] : q[o2];
+        const T w2 = n2 == 4 ? wd[k2] : T(1);
+        for (int k1 = 0; k1 < n1; ++k1) {
+          const int c1 = n1 == 4 ? q[o1] + off[k1] : q[o1];
+          const T w1 = n1 == 4 ? wd[k1] : T(1);
+          const int pi = (((cn - nbase) >> 1) * NTG + ((c2 + 2) >> 1)) * NTG + ((c1 + 2) >> 1);
+          atomicAdd(&acc[f * NP + pi], wn * w2 * w1 * de);
+        }
+      }
+    }
   };
-  for (int t = threadIdx.x; t < 4 * NQ; t += kNA) {
-    const int f = t / NQ, e = t % NQ;
-    const int F = e / (3 * BS * BS), l = (e / (BS * BS)) % 3 + 1, uv = e % (BS * BS);
-    const int ax = F >> 1, side = F & 1;
-    const int o1 = (ax + 1) % 3, o2 = (ax + 2) % 3;
-    int q[3];
-    q[ax] = side ? M + l : -l;
+  // a thread per (component, tangential point): the three halo layers from the three sources
+  // next to the face, p_k at normal distance k = 0, 1, 2 inside it (q at layer l reads p_k with
+  // weight a_{l+k}, and its second difference d2_{l+k} for l + k <= 2)
+  for (int t = threadIdx.x; t < 4 * BS * BS; t += kNA) {
+    const int f = t / (BS * BS), uv = t % (BS * BS);
+    int q[3] = {0, 0, 0};
     q[o1] = uv % BS;
     q[o2] = uv / BS;
-    // sources p = q - dir m e_n inside the block (m >= l), dir = +1 beyond the upper face
-    const int dir = side ? 1 : -1;
-    const T sg = side ? T(1) : T(-1);
-    T de = T(0), dd = T(0);
-    for (int mm = l; mm <= 3; ++mm) {
+    T Wk[3], Kk[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
       int p[3] = {q[0], q[1], q[2]};
-      p[ax] -= dir * mm;
-      T wv;
+      p[ax] = side ? M - k : k;
+      const size_t po = bo + L::idx(p[0], p[1], p[2]);
+      auto kappa = [&](int g) -> T {
+        T kv = c_lam * a.lam[po + (size_t)g * L::FS];
+        if (a.nup) kv += c_nu * a.nup[po + (size_t)g * L::FS];
+        return kv;
+      };
       if (f < 3) {
-        const T un = a.Y[bo + (size_t)ax * L::FS + L::idx(p[0], p[1], p[2])];
-        wv = un * kappa(p, f);
-        if (f == ax) wv += c0sq * kappa(p, 3);
-        if (mm <= 2) dd += d2[mm - 1] * kappa(p, f);
+        Kk[k] = kappa(f);
+        Wk[k] = a.Y[po + (size_t)ax * L::FS] * Kk[k];
+        if (f == ax) Wk[k] += c0sq * kappa(3);
       } else {
-        wv = kappa(p, ax);
+        Kk[k] = T(0);
+        Wk[k] = kappa(ax);
       }
-      de += sg * am[mm - 1] * wv;
     }
-    de = -ih * de + (f < 3 ? nu_ih2 * dd : T(0));
-    if (de == T(0)) continue;
-    const long long o = direct_offset<T, BS>(nbh, q[0], q[1], q[2], f);
-    if (o >= 0) {
-      atomicAdd(&a.nu[o], de);
+#pragma unroll
+    for (int l = 1; l <= 3; ++l) {
+      T de = T(0), dd = T(0);
+#pragma unroll
+      for (int k = 0; k + l <= 3; ++k) {
+        de += sg * am[l + k - 1] * Wk[k];
+        if (l + k <= 2) dd += d2[l + k - 1] * Kk[k];
+      }
+      de = -ih * de + (f < 3 ? nu_ih2 * dd : T(0));
+      q[ax] = side ? M + l : -l;
+      scatter(q, f, l, de);
+    }
+  }
+  if (!coarse) return;
+  __syncthreads();
+  // each patch point to the leaf holding it (the prediction's sources are held directly)
+  for (int i = threadIdx.x; i < 4 * NP; i += kNA) {
+    const T v = acc[i];
+    if (v == T(0)) continue;
+    const int f = i / NP, r = i % NP;
+    const int kn = r / (NTG * NTG), k2 = (r / NTG) % NTG, k1 = r % NTG;
+    int c[3];
+    c[ax] = (side ? M - 2 : -6) + 2 * kn;
+    c[o2] = 2 * k2 - 2;
+    c[o1] = 2 * k1 - 2;
+    const long long o = direct_offset<T, BS>(nbh, c[0], c[1], c[2], f);
+    if (o < 0) {
+      atomicOr(err, 8);
       continue;
     }
-    // predicted ghost: the tensor DD-4 weights (x, then y, then z) of its even stencil points
-    const T wd[4] = {T(-1) / T(16), T(9) / T(16), T(9) / T(16), T(-1) / T(16)};
-    const int off[4] = {-3, -1, 1, 3};
-    const int nx = (q[0] & 1) ? 4 : 1, ny = (q[1] & 1) ? 4 : 1, nz = (q[2] & 1) ? 4 : 1;
-    for (int kz = 0; kz < nz; ++kz)
-      for (int ky = 0; ky < ny; ++ky)
-        for (int kx = 0; kx < nx; ++kx) {
-          const int xx = nx == 4 ? q[0] + off[kx] : q[0];
-          const int yy = ny == 4 ? q[1] + off[ky] : q[1];
-          const int zz = nz == 4 ? q[2] + off[kz] : q[2];
-          const T wt = (nx == 4 ? wd[kx] : T(1)) * (ny == 4 ? wd[ky] : T(1)) * (nz == 4 ? wd[kz] : T(1));
-          const long long o2 = direct_offset<T, BS>(nbh, xx, yy, zz, f);
-          if (o2 < 0) {
-            atomicOr(err, 8);
-            continue;
-          }
-          atomicAdd(&a.nu[o2], wt * de);
-        }
+    atomicAdd(&a.nu[o], v);
   }
 }
 
-// W^T on register r: a boundary point of block `rank` that a finer leaf holds (the first refined
-// box among those containing it, in the order the forward search uses) adds its value to that
-// leaf's point and is cleared.
+// W^T on register r, over the forward's fine-wins task list (rank, refined box d): every boundary
+// point of block `rank` that the forward overwrote with the value of a point of box d's child
+// hands its value to that point and is cleared.  A point on an edge or corner may appear in two
+// tasks (the forward wrote it twice, the same value): the atomic exchange gives it to the first
+// task that reaches it, the other moves zero.  CTAs walk the list, whose length is on the device.
+template <typename T>
+__device__ __forceinline__ T exch_zero(T* p) {
+  if constexpr (sizeof(T) == 4) {
+    return __int_as_float(atomicExch(reinterpret_cast<int*>(p), 0));
+  } else {
+    return __longlong_as_double(
+        (long long)atomicExch(reinterpret_cast<unsigned long long*>(p), 0ull));
+  }
+}
+
 template <typename T, int BS>
-__global__ void __launch_bounds__(kNA) k_adj_fw_T(T* r, const int32_t* blist, const int32_t* nbh_all,
-                                                  const uint8_t* finer) {
+__global__ void __launch_bounds__(kNA) k_adj_fw_T(T* r, const int2* tasks, const int32_t* ntasks,
+                                                  const int32_t* nbh_all, const int32_t* blist) {
   using L = Lay<T, BS>;
-  constexpr int M = L::M, N3 = BS * BS * BS;
-  const int rank = blockIdx.x;
-  if (!finer[rank]) return;
-  __shared__ int nbh[kNbhStride];
-  for (int i = threadIdx.x; i < kNbhStride; i += kNA) nbh[i] = nbh_all[(size_t)rank * kNbhStride + i];
-  __syncthreads();
-  const size_t own = (size_t)blist[rank] * L::BLK;
-  for (int t = threadIdx.x; t < N3; t += kNA) {
-    const int p[3] = {t % BS, (t / BS) % BS, t / (BS * BS)};
-    if (p[0] != 0 && p[0] != M && p[1] != 0 && p[1] != M && p[2] != 0 && p[2] != M) continue;
-    int lo[3], hi[3];
+  constexpr int M = L::M;
+  const int nt = *ntasks;
+  for (int ti = blockIdx.x; ti < nt; ti += gridDim.x) {
+    const int2 tk = tasks[ti];
+    const int* nbh = nbh_all + (size_t)tk.x * kNbhStride;
+    const int me = blist[tk.x];
+    const int d = tk.y;
+    const int dd[3] = {d % 3 - 1, (d / 3) % 3 - 1, d / 9 - 1};
+    int n[3], o[3];
+#pragma unroll
     for (int a = 0; a < 3; ++a) {
-      lo[a] = p[a] == 0 ? -1 : 0;
-      hi[a] = p[a] == M ? 1 : 0;
+      n[a] = dd[a] == 0 ? BS : 1;
+      o[a] = dd[a] < 0 ? 0 : (dd[a] > 0 ? M : 0);
     }
-    long long src = -1;
-    for (int dz = lo[2]; dz <= hi[2] && src < 0; ++dz)
-      for (int dy = lo[1]; dy <= hi[1] && src < 0; ++dy)
-        for (int dx = lo[0]; dx <= hi[0] && src < 0; ++dx) {
-          const int d = box_index(dx, dy, dz);
-          if ((nbh[kNbhType + d] & 15) != kTypeRefined) continue;
-          const int bd[3] = {dx, dy, dz};
-          int c = 0, l[3];
-          for (int a = 0; a < 3; ++a) {
-            const int qa = p[a] - bd[a] * M;                 // in [0, M] inside box d
-            const int ca = qa > M / 2 ? 1 : (qa < M / 2 ? 0 : (bd[a] < 0 ? 1 : 0));
-            c |= ca << a;
-            l[a] = 2 * qa - ca * M;
-          }
-          const int s = nbh[8 * d + c];
-          if (s >= 0) src = (long long)s * L::BLK + L::idx(l[0], l[1], l[2]);
-        }
-    if (src < 0) continue;
-    for (int f = 0; f < 4; ++f) {
-      const size_t o = own + (size_t)f * L::FS + L::idx(p[0], p[1], p[2]);
-      const T v = r[o];
-      r[o] = T(0);
-      if (v != T(0)) atomicAdd(&r[(size_t)src + (size_t)f * L::FS], v);
+    const int tot = n[0] * n[1] * n[2];
+    for (int i = threadIdx.x; i < tot; i += kNA) {
+      const int p[3] = {o[0] + i % n[0], o[1] + (i / n[0]) % n[1], o[2] + i / (n[0] * n[1])};
+      int c = 0, l[3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const int q = p[a] - dd[a] * M;
+        const int ca = q > M / 2 ? 1 : (q < M / 2 ? 0 : (dd[a] < 0 ? 1 : 0));
+        c |= ca << a;
+        l[a] = 2 * q - ca * M;
+      }
+      const int s = nbh[8 * d + c];
+      if (s < 0) continue;
+#pragma unroll
+      for (int f = 0; f < 4; ++f) {
+        const T v = exch_zero(&r[(size_t)me * L::BLK + (size_t)f * L::FS + L::idx(p[0], p[1], p[2])]);
+        if (v != T(0)) atomicAdd(&r[(size_t)s * L::BLK + (size_t)f * L::FS + L::idx(l[0], l[1], l[2])], v);
+      }
     }
   }
 }
@@ -634,19 +738,25 @@ inline dim3 g1(int64_t n) { return dim3((unsigned)n); }
 
 namespace adj {
 
+// CTAs of the task-list kernel: enough to fill the GPU, at most one per task.
+inline unsigned fw_ctas(int64_t max_tasks) {
+  const int64_t c = (int64_t)sm_count() * 8;
+  return (unsigned)(max_tasks < c ? (max_tasks > 0 ? max_tasks : 1) : c);
+}
+
 template <typename T, int BS>
-void stage(const AdjStageK<T>& a, const TopoK& t, const PhysK& ph, const MaskK& m, const uint8_t* finer, int* err,
+void stage(const AdjStageK<T>& a, const TopoK& t, const PhysK& ph, const MaskK& m, const FwTasks& fw, int* err,
            cudaStream_t st) {
   static std::atomic<unsigned long long> opted{0};
   smem_opt_in_stage(k_adj_stage<T, BS>, AdjCfg<T, BS>::bytes, opted);
   k_adj_stage<T, BS><<<g1(t.n), AdjCfg<T, BS>::NT, AdjCfg<T, BS>::bytes, st>>>(a, t, ph, m);
-  k_adj_halo<T, BS><<<g1(t.n), kNA, 0, st>>>(a, t, ph, err);
-  k_adj_fw_T<T, BS><<<g1(t.n), kNA, 0, st>>>(a.nu, t.blist, t.nbh, finer);
+  k_adj_halo<T, BS><<<g1(6 * t.n), kNA, 0, st>>>(a, t, ph, err);
+  k_adj_fw_T<T, BS><<<fw_ctas(fw.max_tasks), kNA, 0, st>>>(a.nu, fw.tasks, fw.ntasks, t.nbh, t.blist);
 }
 
 template <typename T, int BS>
-void fw_T(T* r, const int32_t* blist, const int32_t* nbh, const uint8_t* finer, int64_t n, cudaStream_t st) {
-  k_adj_fw_T<T, BS><<<g1(n), kNA, 0, st>>>(r, blist, nbh, finer);
+void fw_T(T* r, const FwTasks& fw, const int32_t* blist, const int32_t* nbh, cudaStream_t st) {
+  k_adj_fw_T<T, BS><<<fw_ctas(fw.max_tasks), kNA, 0, st>>>(r, fw.tasks, fw.ntasks, nbh, blist);
 }
 
 template <typename T, int BS>
@@ -683,9 +793,9 @@ void put(const double* dense, T* r, const int32_t* blist, int64_t n, cudaStream_
 #define ACM_ADJ_INSTANTIATE(T, BS)                                                                                 \
   namespace acm {                                                                                                  \
   namespace adj {                                                                                                  \
-  template void stage<T, BS>(const AdjStageK<T>&, const TopoK&, const PhysK&, const MaskK&, const uint8_t*, int*,   \
+  template void stage<T, BS>(const AdjStageK<T>&, const TopoK&, const PhysK&, const MaskK&, const FwTasks&, int*,  \
                              cudaStream_t);                                                                        \
-  template void fw_T<T, BS>(T*, const int32_t*, const int32_t*, const uint8_t*, int64_t, cudaStream_t);              \
+  template void fw_T<T, BS>(T*, const FwTasks&, const int32_t*, const int32_t*, cudaStream_t);                       \
   template void sum3<T, BS>(T*, const T*, const T*, const T*, const int32_t*, int64_t, cudaStream_t);                \
   template void objective<T, BS>(const T*, const T*, T*, T*, const int32_t*, const int4*, int64_t,                   \
                                  const PhysK&, double, double, const MaskK&, double*, cudaStream_t);               \

@@ -1224,6 +1224,7 @@ acm_status adjoint_sweep(acm_forest* f, int nsteps, double dt, int c, double wE,
   // toward coarser neighbours are predicted first, as the forward's synchronisation does (the
   // slab kernel's source lookups were cached by the forward's first stage on this grid).
   const acm::TopoK tk_topo = topo(f);
+  const acm::FwTasks fwt{f->d_fw, f->d_counts, 26 * nb};
   auto astage = [&](const T* Ys, double ts, const T* nup, double c_lam, double c_nu, T* nu_out, int sum_mode) {
     pose_at(ts);
     acm::launch_coarse_slabs<T>(Bs, Ys, SLAB, f->d_slabt, f->d_counts + 1, 6 * nb, f->d_nbh, f->d_slaboffc, 1,
@@ -1241,7 +1242,7 @@ acm_status adjoint_sweep(acm_forest* f, int nsteps, double dt, int c, double wE,
     a.sum_mode = sum_mode;
     a.gchi = GCHI;
     a.dtheta = TH;
-    acm::launch_adj_stage<T>(Bs, a, tk_topo, f->phk, cur_mask(), f->d_finer, f->d_err, f->st);
+    acm::launch_adj_stage<T>(Bs, a, tk_topo, f->phk, cur_mask(), fwt, f->d_err, f->st);
     f->launches += 4;
     return cudaGetLastError() == cudaSuccess ? ACM_OK : fail(f, ACM_ECUDA, "adjoint kernel launch failed");
   };
@@ -1314,7 +1315,7 @@ acm_status adjoint_sweep(acm_forest* f, int nsteps, double dt, int c, double wE,
     if ((s = astage(Y[1], tk + 0.5 * dt, NUR[1], dt / 3.0, dt / 2.0, NUR[0], 2))) return s;
     if ((s = astage(Y[0], tk, NUR[0], dt / 6.0, dt / 2.0, NUR[1], 2))) return s;
     acm::launch_adj_sum3<T>(Bs, LAM, LAM, SUM, NUR[1], f->d_blist, nb, f->st);
-    acm::launch_adj_fw_T<T>(Bs, LAM, f->d_blist, f->d_nbh, f->d_finer, nb, f->st);
+    acm::launch_adj_fw_T<T>(Bs, LAM, fwt, f->d_blist, f->d_nbh, nb, f->st);
     f->launches += 2;
     if (k >= 1 && !vjp) objective(TAPE, tk);
   }

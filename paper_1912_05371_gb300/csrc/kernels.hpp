@@ -234,13 +234,19 @@ struct AdjStageK {
   T* gchi;
   double* dtheta;
 };
+// The forward's fine-wins task list (rank, refined box), its device-held length and its bound.
+struct FwTasks {
+  const int2* tasks;
+  const int32_t* ntasks;
+  int64_t max_tasks;
+};
 // err |= 8 if a ghost point's source is missing.
 template <typename T>
 void launch_adj_stage(int Bs, const AdjStageK<T>& a, const TopoK& t, const PhysK& ph, const MaskK& m,
-                      const uint8_t* finer, int* err, cudaStream_t st);
-// W^T applied to register r in place.
+                      const FwTasks& fw, int* err, cudaStream_t st);
+// W^T applied to register r in place (n: blocks of the grid).
 template <typename T>
-void launch_adj_fw_T(int Bs, T* r, const int32_t* blist, const int32_t* nbh, const uint8_t* finer, int64_t n,
+void launch_adj_fw_T(int Bs, T* r, const FwTasks& fw, const int32_t* blist, const int32_t* nbh, int64_t n,
                      cudaStream_t st);
 // out = x + y + z over every element of the listed blocks.
 template <typename T>
