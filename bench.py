@@ -416,7 +416,7 @@ def wavelet_comparison(A, stream, precision, Jmax, max_blocks, nsteps=10, warmup
 
 
 def adjoint_measurement(A, stream, nsteps=100, ckpt_every=10, w_energy=0.1, binomial_snapshots=4):
-    """The adjoint workload: the sphere case at levels 2..4, FP32 fields and FP64 adjoint, on its
+    """The adjoint workload: the sphere case at levels 2..4, FP32 fields and adjoint, on its
     initial grid (frozen), nsteps RK4 steps of one fixed dt; CUDA-event time of the forward steps
     alone and of the whole adjoint call (forward with checkpoints every ckpt_every steps,
     recomputation, backward sweep), then of the same call with binomial checkpointing in
@@ -499,6 +499,86 @@ def adjoint_at_scale(A, stream, nsteps=10, ckpt_every=5, w_energy=0.1):
                         f"steps, checkpoints every {ckpt_every}", "forward_ms_per_step": fwd / nsteps,
             "adjoint_ms_per_step": adj / nsteps, "adjoint_over_forward": adj / fwd, "J": J,
             "dJ_dtheta": [float(v) for v in gth]}
+
+
+def fullscale_plate(A, stream, Jmax=8, max_blocks=120000, nsteps=20, adj_Jmax=6, adj_steps=10, adj_ckpt=5):
+    """The full-scale case: the flapping plate (chord 1, span 3, thickness 0.05; stroke +-60 deg,
+    pitch +-45 deg, frequency 1) in the periodic box 8^3, fluid at rest, nu = 1/2000, C_eta = 1e-4,
+    c0 = 30, C_eps = 1e-3, Bs = 17 at levels 2..Jmax, FP32: its initial grid by the paper's
+    procedure, then nsteps adaptive steps (refine, RK4 at the CFL time step with the mask and solid
+    velocity at every stage time, coarsen) timed by CUDA events, with the block count after every
+    step and the device memory the forest holds.  Then the adjoint workload of this case -- the
+    gradient of J = (1/N) sum [F_x + 0.1 E] with respect to the pitch amplitude on the frozen
+    initial grid of the levels 2..adj_Jmax twin (the level-Jmax grid's workspace would not fit
+    beside it) -- forward and adjoint time per step."""
+    import numpy as np
+    import torch
+    from paper_1912_05371_gb300 import workloads as W
+
+    def make(J, mb):
+        cfg = W.plate_fullscale(Jmax=J)
+        pl = cfg["plate"]
+        grid = dict(cfg["grid"], precision=32, max_blocks=mb, fd_scheme=1)
+        phys = dict(cfg["phys"], eps=cfg["eps"], dealias=1, mask_range_thr=cfg["mask_thr"])
+        f = A.Forest(grid, phys, stream=stream)
+        f.set_mask(A.ACM_MASK_PLATE, [pl["chord"], pl["span"], pl["thickness"], pl["phi_m"], pl["alpha_m"],
+                                      pl["freq"], *pl["root"], pl["delta"]])
+        n0 = f.init_grid(A.ACM_IC_UNIFORM, [0.0, 0.0, 0.0, 0.0])
+        return f, n0, grid
+
+    f, n0, grid = make(Jmax, max_blocks)
+    Bs3 = grid["Bs"] ** 3
+    gb = f.pool.numel() / 1e9
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(nsteps + 1)]
+    nev, nst, t = [], [], 0.0
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    for k in range(nsteps):
+        f.refine_all()
+        nev.append(f.n_blocks())
+        t += f.rk4_step(0.0)
+        n_after, _ = f.coarsen()
+        nst.append(n_after)
+        ev[k + 1].record(stream)
+    ev[-1].synchronize()
+    ms = ev[0].elapsed_time(ev[-1])
+    f.close()
+    del f
+    torch.cuda.empty_cache()
+    out = {"workload": f"flapping plate in the box 8^3, Bs = 17, levels 2..{Jmax}, FP32, {nsteps} adaptive steps",
+           "blocks_initial": n0, "n_blocks": {"evolved": nev, "after_coarsening": nst},
+           "points_evolved_max": max(nev) * Bs3, "pool_gb": gb, "t_end": t, "ms_per_step": ms / nsteps,
+           "value": 4 * Bs3 * sum(nev) / (ms * 1e-3), "unit": UNIT,
+           "note": "pool sized for max_blocks; 32-bit element offsets bound a register at 2^32 elements "
+                   "(206,000 blocks of 17^3)"}
+    # adjoint of the pitch amplitude on the twin's frozen initial grid
+    f, n0a, _ = make(adj_Jmax, 16384)
+    dt = f.rk4_step(0.0)
+    f.set_time(0.0)
+    U0 = f.read_fields().copy()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(adj_steps):
+        f.rk4_step(dt)
+    e1.record(stream)
+    e1.synchronize()
+    fwd = e0.elapsed_time(e1)
+    f.write_fields(U0)
+    f.set_time(0.0)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    J, dJ, _ = f.adjoint_plate_pitch(adj_steps, dt, ckpt_every=adj_ckpt, w_energy=0.1)
+    e1.record(stream)
+    e1.synchronize()
+    adj = e0.elapsed_time(e1)
+    f.close()
+    out["adjoint"] = {"workload": f"the plate case at levels 2..{adj_Jmax}: {n0a} blocks of 17^3 frozen, FP32, "
+                                 f"{adj_steps} steps of dt = {dt:.3e}, checkpoints every {adj_ckpt}",
+                      "forward_ms_per_step": fwd / adj_steps, "adjoint_ms_per_step": adj / adj_steps,
+                      "adjoint_over_forward": adj / fwd, "J": J, "dJ_dalpha_m": float(dJ),
+                      "point_updates_per_s_adjoint": 4 * Bs3 * n0a * adj_steps / (adj * 1e-3)}
+    return out
 
 
 def batched_comparison(A, precision, seed=0, n=64, nsteps=10):
@@ -705,6 +785,7 @@ def main():
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint workload")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 run of the sphere workload")
     ap.add_argument("--no-run200", action="store_true", help="skip the 200-step adaptive run of the sphere workload")
+    ap.add_argument("--no-fullscale", action="store_true", help="skip the full-scale plate case")
     ap.add_argument("--cpu-cores", type=int, default=0,
                     help="host cores for the oracle's all-core figure (default: all, os.cpu_count())")
     ap.add_argument("--wavelet", type=int, default=40, choices=[40, 44],
@@ -863,6 +944,12 @@ def main():
                  if rank == 0 and not args.no_cdf44 and args.wavelet == 40 else None)
         run200 = (adaptive_run(A, stream, args.precision, args.Jmax, args.max_blocks)
                   if rank == 0 and not args.no_run200 else None)
+        fullscale = None
+        if rank == 0 and not args.no_fullscale and args.precision == 32:
+            try:
+                fullscale = fullscale_plate(A, stream)
+            except Exception as e:  # noqa: BLE001
+                fullscale = {"error": f"{type(e).__name__}: {e}"}
         fp64 = None
         if rank == 0 and not args.no_fp64 and args.precision == 32:
             try:
@@ -933,6 +1020,7 @@ def main():
             "cdf44": cdf44,
             "fp64": fp64,
             "adaptive_200_steps": run200,
+            "fullscale": fullscale,
             "adjoint": adjoint,
             "uniform_roofline": uniform,
             "autotune": {"fine_wins_ctas_per_sm": tuned[0], "slab_ctas_per_sm": tuned[1],

@@ -15,6 +15,10 @@ available, so these synthetic cases stand in for them, with the sizes of its run
   faces with C_sp = L_sp / (c0 tau), tau = 20, u_inf = (1, 0, 0), C_gamma = 0.
 * ``random_forest``: the paper's performance method (Sec. 5.4) draws random graded grids of a
   prescribed block count; :func:`random_graded_leaves` does this with a seed.
+* ``plate_fullscale``: the full-scale case -- a rigid plate (chord 1, span 3, thickness 0.05)
+  flapping with stroke +-60 deg and pitch +-45 deg at frequency 1 about its root at the centre
+  of the periodic box 8^3 (one root of side 8), fluid at rest, nu = 1/2000, C_eta = 1e-4,
+  c0 = 30, C_eps = 1e-3, levels 2..Jmax, the mask's layer 1.5 dx at Jmax.
 """
 from __future__ import annotations
 
@@ -44,6 +48,20 @@ def sphere(Jmax=5, Jmin=2):
         mask=("sphere", dict(centre=(1.0, 1.0, 1.0), R=0.25, delta=1.5 * dx_max)),
         sponge=dict(L=(4.0, 2.0, 2.0), L_sp=L_sp, delta=1.5 * dx_max),
         steps=200, eps=1e-3, dealias=True, mask_thr=1e-5,
+    )
+
+
+def plate_fullscale(Jmax=7, Jmin=2, Bs=17):
+    root_len = 8.0
+    dx_max = root_len / ((1 << Jmax) * (Bs - 1))
+    return dict(
+        grid=dict(nroot=(1, 1, 1), root_len=root_len, Bs=Bs, g=4, Jmin=Jmin, Jmax=Jmax),
+        phys=dict(nu=1.0 / 2000.0, c0=30.0, C_eta=1e-4, C_gamma=0.0, cfl=0.5, cfl_eta=1.0, cfl_nu=0.25),
+        ic=("uniform", dict(u0=(0.0, 0.0, 0.0), p0=0.0)),
+        # chord, span, thickness, stroke and pitch amplitudes (rad), frequency, root, layer width
+        plate=dict(chord=1.0, span=3.0, thickness=0.05, phi_m=math.radians(60.0), alpha_m=math.radians(45.0),
+                   freq=1.0, root=(4.0, 4.0, 4.0), delta=1.5 * dx_max),
+        eps=1e-3, dealias=True, mask_thr=1e-5,
     )
 
 
