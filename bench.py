@@ -907,7 +907,8 @@ def main():
                          "sync_ms_per_stage": sync_ms / launches_stage,
                          "stage_ms_per_stage": stage_ms / launches_stage}}
         roof["kernel"] = {0: "k_stage_pair<17> (fused RHS + RK4 stage, 2 points per thread)",
-                          1: "k_stage<float,17> (fused RHS + RK4 stage)"}[tuning["stage_variant"]]
+                          1: "k_stage<float,17> (fused RHS + RK4 stage)",
+                          2: "k_stage<float,17,TMA> (fused RHS + RK4 stage, bulk-copy staging)"}[tuning["stage_variant"]]
 
         # end to end through the C-ABI with host buffers: write state, step, read state
         e2e = None
@@ -1025,8 +1026,10 @@ def main():
             "uniform_roofline": uniform,
             "autotune": {"fine_wins_ctas_per_sm": tuned[0], "slab_ctas_per_sm": tuned[1],
                          "stage_kernel": {0: "pair (2 points/thread, packed f32x2)",
-                                          1: "point (1 point/thread)"}[tuning["stage_variant"]],
-                         "stage2_ms": {"pair": tuning["stage_ms"][0], "point": tuning["stage_ms"][1]}},
+                                          1: "point (1 point/thread)",
+                                          2: "point, bulk-copy (TMA) staging of U/acc/chi"}[tuning["stage_variant"]],
+                         "stage2_ms": {"pair": tuning["stage_ms"][0], "point": tuning["stage_ms"][1],
+                                       "point_tma": tuning["stage_ms"][2]}},
             "clocks": clk,
         }
         print(json.dumps(line), flush=True)

@@ -242,23 +242,27 @@ acm_status acm_rk4_steps_batch(acm_forest* const* forests, int n, int nsteps, do
  * the stream.  No counterpart in the paper. */
 acm_status acm_autotune(acm_forest* f, int* fw_ctas, int* slab_ctas);
 
-/* Work layouts of the fused right-hand side + RK4 stage kernel (Sec. 2.1-2.3): ACM_STAGE_POINT,
- * one point per thread (the default), or ACM_STAGE_PAIR, two x-adjacent points per thread with
- * packed FP32x2 arithmetic (FP32 forests only: fewer instructions, half the resident threads).
- * Both compute every point by the same formula; their FP32 results differ only in rounding
- * order.  FP64 forests always use ACM_STAGE_POINT. */
+/* Forms of the fused right-hand side + RK4 stage kernel (Sec. 2.1-2.3): ACM_STAGE_POINT, one
+ * point per thread (the default); ACM_STAGE_PAIR, two x-adjacent points per thread with packed
+ * FP32x2 arithmetic (FP32 forests only: fewer instructions, half the resident threads);
+ * ACM_STAGE_POINT_TMA, one point per thread with the planes of U, the RK accumulator and the mask
+ * brought into a shared-memory ring by mbarrier-tracked bulk copies one plane ahead (FP32 forests
+ * only).  All compute every point by the same formula; ACM_STAGE_POINT and ACM_STAGE_POINT_TMA
+ * give bitwise equal results, ACM_STAGE_PAIR differs in FP32 rounding order.  FP64 forests always
+ * use ACM_STAGE_POINT. */
 #define ACM_STAGE_PAIR 0
 #define ACM_STAGE_POINT 1
-/* Force the stage kernel's work layout (until the next acm_autotune); drops a captured graph.
+#define ACM_STAGE_POINT_TMA 2
+/* Force the stage kernel's form (until the next acm_autotune); drops a captured graph.
  * ACM_EINVAL for another value. */
 acm_status acm_set_stage_variant(acm_forest* f, int variant);
 
 /* The launch knobs in use: CTAs per SM of the fine-wins and slab kernels, the stage kernel's
- * work layout, and the autotuner's median times (ms) of one stage launch in each layout
- * (stage_ms[ACM_STAGE_PAIR], stage_ms[ACM_STAGE_POINT]; 0 until it has timed them). */
+ * form, and the autotuner's median times (ms) of one stage launch in each form (indexed by
+ * ACM_STAGE_*; 0 until it has timed them). */
 typedef struct {
   int fw_ctas_per_sm, slab_ctas_per_sm, stage_variant;
-  float stage_ms[2];
+  float stage_ms[3];
 } acm_tuning;
 acm_status acm_get_tuning(const acm_forest* f, acm_tuning* out);
 

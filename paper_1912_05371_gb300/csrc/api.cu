@@ -88,7 +88,7 @@ struct acm_forest {
   int tune_fw_ctas = 8;            // fine-wins kernel: CTAs per SM walking the task list
   int tune_slab_ctas = 3;          // coarse-face slab kernel: CTAs per SM walking the task list
   int stage_variant = acm::kStagePoint;  // FP32 stage kernel: one point per thread, or two
-  float tune_stage_ms[2] = {0.f, 0.f};   // the autotuner's times of the two (FP32)
+  float tune_stage_ms[3] = {0.f, 0.f, 0.f};   // the autotuner's times of the three (FP32)
 
   // host side of the current topology (the neighbourhood tables are built on the device from
   // the block list; the host leaf map is brought up to date only when a host query needs it)
@@ -1022,8 +1022,9 @@ acm_status time_launches(acm_forest* f, F&& launch, int reps, float* ms_out) {
 // synchronisation for each number of CTAs per SM walking the list (fine wins: 2, 4, 8, 16; coarse
 // faces: 1, 2, 3 -- at most 3 are resident) and keep the fastest of each.  Fine wins rewrites
 // stored boundary points with the values of finer leaves (what every synchronisation does first);
-// the slab kernel writes only the slab buffer.  FP32 forests also time the two work layouts of
-// the fused stage kernel (two points per thread with packed arithmetic, or one point per thread)
+// the slab kernel writes only the slab buffer.  FP32 forests also time the three forms of the
+// fused stage kernel (two points per thread with packed arithmetic, one point per thread, one
+// point per thread with U, the accumulator and chi staged by bulk copies)
 // on RK stage 2 of the live grid (reading U, the first stage register and the accumulator,
 // writing the accumulator and the second stage register: registers a step rewrites before it
 // reads them) and keep the faster.
@@ -1068,7 +1069,7 @@ acm_status autotune(acm_forest* f, int* fw_ctas, int* slab_ctas) {
     a.c_out = 0.0;
     best = 1e30f;
     int best_v = f->stage_variant;
-    for (int v : {acm::kStagePair, acm::kStagePoint}) {
+    for (int v : {acm::kStagePair, acm::kStagePoint, acm::kStagePointTMA}) {
       float ms = 0.f;
       acm_status s = time_launches(f, [&]() {
         acm::launch_stage<T>(2, f->gp.Bs, a, t, f->phk, f->d_err, f->st, v);
@@ -1775,8 +1776,10 @@ acm_status acm_autotune(acm_forest* f, int* fw_ctas, int* slab_ctas) {
 
 acm_status acm_set_stage_variant(acm_forest* f, int variant) {
   if (!f) return ACM_EINVAL;
-  if (variant != ACM_STAGE_PAIR && variant != ACM_STAGE_POINT) return fail(f, ACM_EINVAL, "unknown stage kernel");
-  f->stage_variant = variant == ACM_STAGE_PAIR ? acm::kStagePair : acm::kStagePoint;
+  if (variant != ACM_STAGE_PAIR && variant != ACM_STAGE_POINT && variant != ACM_STAGE_POINT_TMA)
+    return fail(f, ACM_EINVAL, "unknown stage kernel");
+  f->stage_variant = variant == ACM_STAGE_PAIR ? acm::kStagePair
+                     : (variant == ACM_STAGE_POINT ? acm::kStagePoint : acm::kStagePointTMA);
   // a captured graph holds the old kernel
   if (f->gexec) { cudaGraphExecDestroy(f->gexec); f->gexec = nullptr; }
   if (f->graph) { cudaGraphDestroy(f->graph); f->graph = nullptr; }
@@ -1788,9 +1791,11 @@ acm_status acm_get_tuning(const acm_forest* f, acm_tuning* out) {
   out->fw_ctas_per_sm = f->tune_fw_ctas;
   out->slab_ctas_per_sm = f->tune_slab_ctas;
   out->stage_variant = f->gp.precision == 64 ? ACM_STAGE_POINT
-                       : (f->stage_variant == acm::kStagePair ? ACM_STAGE_PAIR : ACM_STAGE_POINT);
-  out->stage_ms[0] = f->tune_stage_ms[acm::kStagePair];
-  out->stage_ms[1] = f->tune_stage_ms[acm::kStagePoint];
+                       : (f->stage_variant == acm::kStagePair ? ACM_STAGE_PAIR
+                          : (f->stage_variant == acm::kStagePoint ? ACM_STAGE_POINT : ACM_STAGE_POINT_TMA));
+  out->stage_ms[ACM_STAGE_PAIR] = f->tune_stage_ms[acm::kStagePair];
+  out->stage_ms[ACM_STAGE_POINT] = f->tune_stage_ms[acm::kStagePoint];
+  out->stage_ms[ACM_STAGE_POINT_TMA] = f->tune_stage_ms[acm::kStagePointTMA];
   return ACM_OK;
 }
 

@@ -39,7 +39,18 @@ struct Cfg {
 };
 
 
-template <typename T, int BS, int STAGE>
+// Planes of U, the accumulator and chi a stage reads besides its input (TMA variant: staged in
+// shared memory by bulk copies).
+template <int STAGE>
+__host__ __device__ constexpr int staged_planes(bool mask) {
+  return (STAGE == 2 || STAGE == 3 ? 8 : (STAGE == 4 ? 4 : 0)) + (mask ? 1 : 0);
+}
+
+// TMA = true: the planes of U, the accumulator and chi of plane z + 1 are brought into a
+// two-slot shared-memory ring by 1D bulk copies (one thread issues them after the plane
+// barrier of iteration z, completion on an mbarrier per slot), instead of per-thread loads at
+// the point of use.
+template <typename T, int BS, int STAGE, bool TMA = false>
 __global__ void __launch_bounds__(Cfg<T, BS>::NT, sizeof(T) == 4 ? 3 : 1)
 k_stage(const StageK<T> a, const TopoK tp, const PhysK ph, int* err) {
   using L = Lay<T, BS>;
@@ -149,6 +160,38 @@ k_stage(const StageK<T> a, const TopoK tp, const PhysK ph, int* err) {
     cp_async_commit();
   };
 
+  // TMA ring: stg[slot][k][PP], component k of the staged arrays (U 0..3 and acc 4..7 in stages
+  // 2, 3; acc 0..3 in stage 4; chi last if a mask is set)
+  extern __shared__ __align__(128) unsigned char dsm[];
+  T* stg = reinterpret_cast<T*>(dsm);
+  __shared__ __align__(8) unsigned long long mbar[2];
+  const int nstg = staged_planes<STAGE>(ph.mask != 0);
+  auto stage_src = [&](int k) -> const T* {
+    if (STAGE == 2 || STAGE == 3) {
+      if (k < 4) return a.U + bo + (size_t)k * L::FS;
+      if (k < 8) return a.acc + bo + (size_t)(k - 4) * L::FS;
+    } else if (STAGE == 4) {
+      if (k < 4) return a.acc + bo + (size_t)k * L::FS;
+    }
+    return a.chi + (size_t)slot * L::FS;
+  };
+  auto issue_staged = [&](int zz) {          // thread 0 only
+    const int sl = zz & 1;
+    constexpr unsigned pb = (unsigned)(L::PP * sizeof(T));
+    mbar_expect_tx(&mbar[sl], pb * (unsigned)nstg);
+    for (int k = 0; k < nstg; ++k)
+      bulk_g2s(stg + ((size_t)sl * nstg + k) * L::PP, stage_src(k) + (size_t)zz * L::PP, pb, &mbar[sl]);
+  };
+  if (TMA && nstg > 0) {
+    if (tid == 0) {
+      mbar_init(&mbar[0], 1);
+      mbar_init(&mbar[1], 1);
+      mbar_init_fence();
+    }
+    __syncthreads();
+    if (tid == 0) issue_staged(0);
+  }
+
   T nm[5] = {T(0), T(0), T(0), T(0), T(0)};   // stage 4: max |u|,|v|,|w|,|p|, |(u,v,w)|^2
   // L2 prefetch of the planes an iteration reads kPf iterations ahead: one thread per array
   // (stage input planes z + 4 + kPf, U, acc and chi planes z + kPf), one bulk request each
@@ -187,7 +230,13 @@ k_stage(const StageK<T> a, const TopoK tp, const PhysK ph, int* err) {
     cp_async_wait_all();
     __syncthreads();
     if (z < M) issue_halos(z + 1, &buf[(z + 1) & 1][0][0]);
+    if (TMA && nstg > 0 && tid == 0 && z < M) {
+      // the slot of plane z + 1 held plane z - 1, which every thread finished before the barrier
+      fence_async_shared();
+      issue_staged(z + 1);
+    }
     prefetch_planes(z + 4 + kPf, z + kPf);
+    if (TMA && nstg > 0) mbar_wait(&mbar[z & 1], (unsigned)((z >> 1) & 1), err);
     if (act) {
       if (z + 4 <= M + 3) {
 #pragma unroll
@@ -195,15 +244,29 @@ k_stage(const StageK<T> a, const TopoK tp, const PhysK ph, int* err) {
       }
       const size_t pi = (size_t)L::idx(x, y, z);
       T Uv[4], Av[4], chiv = T(0);
-      if (STAGE == 2 || STAGE == 3) {
+      if constexpr (TMA) {
+        const T* sg = stg + (size_t)(z & 1) * nstg * L::PP + (size_t)L::idx(x, y, 0);
+        if (STAGE == 2 || STAGE == 3) {
 #pragma unroll
-        for (int f = 0; f < 4; ++f) Uv[f] = a.U[bo + (size_t)f * L::FS + pi];
-      }
-      if (STAGE != 1) {
+          for (int f = 0; f < 4; ++f) Uv[f] = sg[(size_t)f * L::PP];
 #pragma unroll
-        for (int f = 0; f < 4; ++f) Av[f] = a.acc[bo + (size_t)f * L::FS + pi];
+          for (int f = 0; f < 4; ++f) Av[f] = sg[(size_t)(4 + f) * L::PP];
+        } else if (STAGE == 4) {
+#pragma unroll
+          for (int f = 0; f < 4; ++f) Av[f] = sg[(size_t)f * L::PP];
+        }
+        if (ph.mask) chiv = sg[(size_t)(nstg - 1) * L::PP];
+      } else {
+        if (STAGE == 2 || STAGE == 3) {
+#pragma unroll
+          for (int f = 0; f < 4; ++f) Uv[f] = a.U[bo + (size_t)f * L::FS + pi];
+        }
+        if (STAGE != 1) {
+#pragma unroll
+          for (int f = 0; f < 4; ++f) Av[f] = a.acc[bo + (size_t)f * L::FS + pi];
+        }
+        if (ph.mask) chiv = a.chi[(size_t)slot * L::FS + pi];
       }
-      if (ph.mask) chiv = a.chi[(size_t)slot * L::FS + pi];
 
       T dx[4], dy[4], dz[4], lap[3];
 #pragma unroll
@@ -318,16 +381,28 @@ __global__ void k_rk_coefs(const unsigned long long* maxbits, RkK p, double* rk)
   rk[8] = dt / 3.0; rk[9] = dt / 6.0;
 }
 
-template <typename T, int BS>
+template <typename T, int BS, int STAGE, bool TMA>
+void launch_one(const StageK<T>& s, const TopoK& t, const PhysK& p, int* err, cudaStream_t st) {
+  const dim3 grid((unsigned)t.n), block(Cfg<T, BS>::NT);
+  const size_t dyn = TMA ? (size_t)2 * staged_planes<STAGE>(p.mask != 0) * Lay<T, BS>::PP * sizeof(T) : 0;
+  if (TMA) {
+    // the ring comes on top of the kernel's static shared memory: opt in to its largest size
+    static std::atomic<unsigned long long> opted{0};
+    smem_opt_in_stage(k_stage<T, BS, STAGE, TMA>, (size_t)2 * staged_planes<STAGE>(true) * Lay<T, BS>::PP * sizeof(T),
+                      opted);
+  }
+  k_stage<T, BS, STAGE, TMA><<<grid, block, dyn, st>>>(s, t, p, err);
+}
+
+template <typename T, int BS, bool TMA>
 void launch_stage_bs(int stage, const StageK<T>& s, const TopoK& t, const PhysK& p, int* err, cudaStream_t st) {
   if (t.n <= 0) return;
-  const dim3 grid((unsigned)t.n), block(Cfg<T, BS>::NT);
   switch (stage) {
-    case 0: k_stage<T, BS, 0><<<grid, block, 0, st>>>(s, t, p, err); break;
-    case 1: k_stage<T, BS, 1><<<grid, block, 0, st>>>(s, t, p, err); break;
-    case 2: k_stage<T, BS, 2><<<grid, block, 0, st>>>(s, t, p, err); break;
-    case 3: k_stage<T, BS, 3><<<grid, block, 0, st>>>(s, t, p, err); break;
-    default: k_stage<T, BS, 4><<<grid, block, 0, st>>>(s, t, p, err); break;
+    case 0: launch_one<T, BS, 0, TMA>(s, t, p, err, st); break;
+    case 1: launch_one<T, BS, 1, TMA>(s, t, p, err, st); break;
+    case 2: launch_one<T, BS, 2, TMA>(s, t, p, err, st); break;
+    case 3: launch_one<T, BS, 3, TMA>(s, t, p, err, st); break;
+    default: launch_one<T, BS, 4, TMA>(s, t, p, err, st); break;
   }
 }
 
@@ -354,8 +429,15 @@ void launch_stage(int stage, int Bs, const StageK<T>& s, const TopoK& t, const P
     c.ih[J] = T(1.0 / p.h[J]);
     c.ih2[J] = T(1.0 / (12.0 * p.h[J] * p.h[J]));
   }
-  if (Bs == 17) launch_stage_bs<T, 17>(stage, a, t, p, err, st);
-  else launch_stage_bs<T, 9>(stage, a, t, p, err, st);
+  if constexpr (sizeof(T) == 4) {
+    if (variant == kStagePointTMA) {
+      if (Bs == 17) launch_stage_bs<T, 17, true>(stage, a, t, p, err, st);
+      else launch_stage_bs<T, 9, true>(stage, a, t, p, err, st);
+      return;
+    }
+  }
+  if (Bs == 17) launch_stage_bs<T, 17, false>(stage, a, t, p, err, st);
+  else launch_stage_bs<T, 9, false>(stage, a, t, p, err, st);
 }
 
 void launch_rk_coefs(const unsigned long long* maxbits, const RkK& p, double* rk, cudaStream_t st) {
