@@ -584,9 +584,11 @@ def fullscale_plate(A, stream, Jmax=8, max_blocks=120000, nsteps=20, adj_Jmax=6,
 def batched_comparison(A, precision, seed=0, n=64, nsteps=10):
     """The batched workload: n independent instances (periodic unit cubes, N_b ~ U{8..512} blocks
     of 17^3 on random graded layouts over levels 2..5, pulse + vortex ring, seeded), nsteps RK4
-    steps each, three ways: one C-ABI call per instance and step (time step on the host), all
-    instances' steps as plain launches on their own streams (time step on the device), and one
-    CUDA graph per step holding every instance as a parallel branch."""
+    steps each, four ways: one C-ABI call per instance and step (time step on the host), all
+    instances' steps as plain launches on their own streams (time step on the device), one CUDA
+    graph per step holding every instance as a parallel branch, and the persistent form (per RK
+    stage the instances' synchronisation as parallel branches and one stage launch whose CTAs walk
+    the blocks of all instances, in one graph per step)."""
     import torch
     from paper_1912_05371_gb300 import workloads as W
     insts = W.batched_instances(seed=seed, n=n)
@@ -603,14 +605,14 @@ def batched_comparison(A, precision, seed=0, n=64, nsteps=10):
     nb = sum(len(i["leaves"]) for i in insts)
     pts = nb * 17 ** 3 * 4 * nsteps
     out = {}
-    for mode in ("per_instance_calls", "streams", "graph"):
+    for mode in ("per_instance_calls", "streams", "graph", "persistent"):
         def run(k):
             if mode == "per_instance_calls":
                 for _ in range(k):
                     for f in forests:
                         f.rk4_step(0.0)
             else:
-                A.rk4_steps_batch(forests, k, 0.0, graph=(mode == "graph"))
+                A.rk4_steps_batch(forests, k, 0.0, graph={"streams": 0, "graph": 1, "persistent": 2}[mode])
         run(2)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -623,7 +625,8 @@ def batched_comparison(A, precision, seed=0, n=64, nsteps=10):
                         f"pulse + vortex ring, seed {seed}", "precision": f"fp{precision}", "steps": nsteps,
             "ms_per_step": {k: round(1e3 * v / nsteps, 4) for k, v in out.items()},
             "point_updates_per_s": {k: pts / v for k, v in out.items()},
-            "graph_speedup_vs_per_instance_calls": out["per_instance_calls"] / out["graph"]}
+            "graph_speedup_vs_per_instance_calls": out["per_instance_calls"] / out["graph"],
+            "persistent_speedup_vs_per_instance_calls": out["per_instance_calls"] / out["persistent"]}
 
 
 def reduce_over_ranks(ms, point_updates, dist=None, device="cpu"):

@@ -225,9 +225,17 @@ acm_status acm_rk4_steps(acm_forest* f, int nsteps, double dt, int use_graph, do
  * stream): every step enqueues each instance's step on its stream, so the instances run side by
  * side.  use_graph = 1: the second step of all instances is captured into ONE CUDA graph (each
  * instance a parallel branch forked from forests[0]'s stream) and replayed for the remaining
- * steps.  Synchronises every stream at the end; t_end (may be NULL) receives n simulated times.
- * Errors are reported on the forest concerned (forests[0] for capture errors).  No counterpart
- * in the paper. */
+ * steps.  use_graph = 2, the persistent form: per RK stage every instance's synchronisation (and
+ * its time step) runs as a parallel branch, then ONE launch of the fused stage kernel whose CTAs
+ * walk the (instance, block) pairs of all instances; the first step runs as plain launches, the
+ * second is captured into one CUDA graph and replayed.  It needs forests of one precision and
+ * block size with identical physics and grid spacings, and uses forests[0]'s staging buffer
+ * (the one acm_read_fields/acm_write_fields use) for its instance table and work list; otherwise
+ * the call takes use_graph = 1.  *graph_used receives 0 (plain launches), 1 or 2.  The persistent
+ * form computes every block's update bitwise as the other forms do.  Synchronises every stream at
+ * the end; t_end (may be NULL) receives n simulated times.  Errors are reported on the forest
+ * concerned (forests[0] for capture errors and the persistent stage launches).  No counterpart in
+ * the paper. */
 acm_status acm_rk4_steps_batch(acm_forest* const* forests, int n, int nsteps, double dt, int use_graph,
                                double* t_end, int* graph_used);
 

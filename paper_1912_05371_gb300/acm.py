@@ -142,16 +142,19 @@ NOALLOC_MAX_BLOCKS = 16384
 
 def rk4_steps_batch(forests, nsteps, dt=0.0, graph=True):
     """nsteps RK4 steps of several independent forests (each on its own stream), optionally as
-    one CUDA graph per step; returns (list of simulated times, whether a graph ran)."""
+    one CUDA graph per step (graph=True or 1) or in the persistent form (graph=2: one stage launch
+    walking the blocks of all instances, inside one graph per step); returns (list of simulated
+    times, the form that ran: 0 plain launches, 1 graph, 2 persistent)."""
     n = len(forests)
     hs = (C.c_void_p * n)(*[f.h for f in forests])
     t = (C.c_double * n)()
     g = C.c_int()
-    st = lib().acm_rk4_steps_batch(hs, n, int(nsteps), float(dt), int(bool(graph)), t, C.byref(g))
+    mode = graph if (isinstance(graph, int) and not isinstance(graph, bool)) else int(bool(graph))
+    st = lib().acm_rk4_steps_batch(hs, n, int(nsteps), float(dt), int(mode), t, C.byref(g))
     if st != 0:
         msg = lib().acm_status_string(st).decode()
         raise AcmError(f"libacm status {st}: {msg}")
-    return list(t), bool(g.value)
+    return list(t), int(g.value)
 
 
 def fma_rate(precision, stream=None):

@@ -141,6 +141,11 @@ acm_status fail(acm_forest* f, acm_status s, const std::string& msg) {
       return fail(f, ACM_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));           \
   } while (0)
 
+#define CK_F(g, call)                                                                          \
+  do {                                                                                         \
+    const cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess) return fail((g), ACM_ECUDA, cudaGetErrorString(e_));                 \
+  } while (0)
 #define CKL()                                                                                  \
   do {                                                                                         \
     cudaError_t e_ = cudaGetLastError();                                                       \
@@ -571,8 +576,7 @@ acm_status rk4(acm_forest* f, double dt, double* dt_used, T* const* save = nullp
 // One RK4 step with the time step computed on the device (no host synchronisation): the
 // time-step kernel, then 4 x (synchronisation, stage kernel reading its coefficients from device
 // memory); stage 4 reduces the max norms of U^{n+1}, which the next step's time step reads.
-template <typename T>
-acm_status enqueue_rk4_device_dt(acm_forest* f, double dt) {
+acm::RkK rk_params(const acm_forest* f, double dt) {
   acm::RkK rp;
   rp.dt_fixed = dt;
   rp.h = h_of(f, f->Jtop);
@@ -583,7 +587,12 @@ acm_status enqueue_rk4_device_dt(acm_forest* f, double dt) {
   rp.cfl_nu = f->pp.cfl_nu;
   rp.nu = f->pp.nu;
   rp.mask = f->mask_on ? 1 : 0;
-  acm::launch_rk_coefs(f->d_maxbits, rp, f->d_rk, f->st);
+  return rp;
+}
+
+template <typename T>
+acm_status enqueue_rk4_device_dt(acm_forest* f, double dt) {
+  acm::launch_rk_coefs(f->d_maxbits, rk_params(f, dt), f->d_rk, f->st);
   CKL();
   ++f->launches;
   T* U = reinterpret_cast<T*>(f->U);
@@ -1594,6 +1603,113 @@ acm_status acm_rk4_steps(acm_forest* f, int nsteps, double dt, int use_graph, do
   return ACM_OK;
 }
 
+extern "C++" {
+namespace {
+
+// The persistent form of the batched steps: per RK stage, every instance's synchronisation (and
+// at the first stage its time step on the device) on its own stream, joined into the origin
+// stream, then one launch of the stage kernel whose CTAs walk the (instance, rank) pairs of all
+// instances.  The per-stage instance descriptors and the work list live in forests[0]'s dense
+// staging buffer (free during steps).
+template <typename T>
+struct BatchPersistent {
+  acm_forest* const* forests = nullptr;
+  int n = 0;
+  int64_t nwork = 0;
+  const acm::StageInst<T>* desc = nullptr;   // [4][n] on the device
+  const int2* work = nullptr;                // [nwork] on the device
+  std::vector<cudaEvent_t> ev;               // fork, then one join event per instance
+
+  // ACM_EINVAL (nothing changed) if the instances cannot share one launch
+  acm_status setup(acm_forest* const* fs, int nn) {
+    forests = fs;
+    n = nn;
+    acm_forest* f0 = fs[0];
+    for (int i = 0; i < n; ++i) {
+      const acm_forest* g = fs[i];
+      if (g->gp.precision != f0->gp.precision || g->gp.Bs != f0->gp.Bs || !g->st ||
+          std::memcmp(&g->phk, &f0->phk, sizeof(acm::PhysK)) != 0)
+        return ACM_EINVAL;
+      nwork += (int64_t)g->order.size();
+    }
+    const size_t dbytes = (size_t)4 * n * sizeof(acm::StageInst<T>);
+    const size_t wofs = (dbytes + 255) & ~(size_t)255;
+    const size_t need = wofs + (size_t)nwork * sizeof(int2);
+    const size_t cap = (size_t)f0->gp.max_blocks * 4 * f0->gp.Bs * f0->gp.Bs * f0->gp.Bs * f0->esz;
+    if (need > cap) return ACM_EINVAL;
+    std::vector<acm::StageInst<T>> hd((size_t)4 * n);
+    std::vector<int2> hw;
+    hw.reserve((size_t)nwork);
+    for (int i = 0; i < n; ++i) {
+      acm_forest* g = fs[i];
+      T* U = reinterpret_cast<T*>(g->U);
+      T* YA = reinterpret_cast<T*>(g->YA);
+      T* YB = reinterpret_cast<T*>(g->YB);
+      for (int st = 1; st <= 4; ++st) {
+        acm::StageInst<T>& d = hd[(size_t)(st - 1) * n + i];
+        d.p.in = st == 1 ? U : (st == 2 ? YA : (st == 3 ? YB : YA));
+        d.p.out = st == 1 ? YA : (st == 2 ? YB : (st == 3 ? YA : U));
+        d.p.U = U;
+        d.p.acc = reinterpret_cast<T*>(g->ACC);
+        d.p.chi = g->mask_on ? reinterpret_cast<const T*>(g->CHI) : nullptr;
+        d.p.slab = reinterpret_cast<const T*>(g->SLAB);
+        d.p.norms = st == 4 ? g->d_maxbits : nullptr;
+        d.p.coefp = g->d_rk + 2;
+        d.tp = topo(g);
+      }
+      for (int64_t r = 0; r < (int64_t)g->order.size(); ++r) hw.push_back(make_int2(i, (int)r));
+    }
+    char* base = reinterpret_cast<char*>(f0->DENSE);
+    if (cudaMemcpyAsync(base, hd.data(), dbytes, cudaMemcpyHostToDevice, f0->st) != cudaSuccess ||
+        cudaMemcpyAsync(base + wofs, hw.data(), hw.size() * sizeof(int2), cudaMemcpyHostToDevice, f0->st) != cudaSuccess ||
+        cudaStreamSynchronize(f0->st) != cudaSuccess)
+      return fail(f0, ACM_ECUDA, "persistent batch: descriptor upload");
+    desc = reinterpret_cast<const acm::StageInst<T>*>(base);
+    work = reinterpret_cast<const int2*>(base + wofs);
+    ev.assign((size_t)n + 1, nullptr);
+    for (auto& e : ev)
+      if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return fail(f0, ACM_ECUDA, "event");
+    return ACM_OK;
+  }
+  ~BatchPersistent() {
+    for (cudaEvent_t e : ev)
+      if (e) cudaEventDestroy(e);
+  }
+
+  // one RK4 step of every instance, ordered after the origin stream's work and before its later work
+  acm_status enqueue(double dt) {
+    acm_forest* f0 = forests[0];
+    cudaStream_t origin = f0->st;
+    for (int st = 1; st <= 4; ++st) {
+      CK_F(f0, cudaEventRecord(ev[0], origin));
+      for (int i = 1; i < n; ++i) CK_F(f0, cudaStreamWaitEvent(forests[i]->st, ev[0], 0));
+      for (int i = 0; i < n; ++i) {
+        acm_forest* g = forests[i];
+        if (st == 1) {
+          acm::launch_rk_coefs(g->d_maxbits, rk_params(g, dt), g->d_rk, g->st);
+          ++g->launches;
+        }
+        T* in = reinterpret_cast<T*>(st == 1 ? g->U : (st == 2 ? g->YA : (st == 3 ? g->YB : g->YA)));
+        acm_status s = sync_stage<T>(g, in, st > 1);
+        if (s) return s;
+        if (st == 4) CK_F(g, cudaMemsetAsync(g->d_maxbits, 0, 8 * sizeof(unsigned long long), g->st));
+      }
+      for (int i = 1; i < n; ++i) {
+        CK_F(f0, cudaEventRecord(ev[i], forests[i]->st));
+        CK_F(f0, cudaStreamWaitEvent(origin, ev[i], 0));
+      }
+      acm::launch_stage_multi<T>(st, f0->gp.Bs, f0->phk, desc + (size_t)(st - 1) * n, work, nwork,
+                                 acm::sm_count() * 3, f0->d_err, origin);
+      CK_F(f0, cudaGetLastError());
+      ++f0->launches;
+    }
+    return ACM_OK;
+  }
+};
+
+}  // namespace
+}  // extern "C++"
+
 acm_status acm_rk4_steps_batch(acm_forest* const* forests, int n, int nsteps, double dt, int use_graph,
                                double* t_end, int* graph_used) {
   if (!forests || n <= 0 || nsteps < 0) return ACM_EINVAL;
@@ -1624,6 +1740,17 @@ acm_status acm_rk4_steps_batch(acm_forest* const* forests, int n, int nsteps, do
     if (!forests[i]->st) can_graph = false;
   acm_forest* f = forests[0];             // for CK: errors are reported on the first forest
   cudaStream_t origin = f->st;
+  // use_graph = 2: the persistent form (falls back to the graph of per-instance launches if the
+  // instances cannot share one stage launch)
+  BatchPersistent<float> pf;
+  BatchPersistent<double> pd;
+  bool persistent = false;
+  if (use_graph == 2 && can_graph) {
+    const acm_status ps = f->gp.precision == 64 ? pd.setup(forests, n) : pf.setup(forests, n);
+    if (ps == ACM_OK) persistent = true;
+    else if (ps != ACM_EINVAL) return ps;
+  }
+  auto combined = [&]() { return f->gp.precision == 64 ? pd.enqueue(dt) : pf.enqueue(dt); };
   std::vector<cudaEvent_t> ev((size_t)n + 1, nullptr);
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t gexec = nullptr;
@@ -1641,7 +1768,32 @@ acm_status acm_rk4_steps_batch(acm_forest* const* forests, int n, int nsteps, do
   for (int k = 0; k < nsteps && !rs; ++k) {
     if (!can_graph || k == 0) {
       // plain launches, every instance on its own stream (they run side by side)
-      for (int i = 0; i < n && !rs; ++i) rs = step(forests[i]);
+      if (persistent) rs = combined();
+      else
+        for (int i = 0; i < n && !rs; ++i) rs = step(forests[i]);
+      continue;
+    }
+    if (persistent && !gexec) {
+      // capture one combined step (its fork and join events tie the instances' streams in)
+      for (int i = 1; i < n; ++i) {
+        cudaEventRecord(ev[i], forests[i]->st);
+        cudaStreamWaitEvent(origin, ev[i], 0);
+      }
+      if (cudaStreamBeginCapture(origin, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cleanup();
+        return fail(f, ACM_ECUDA, "graph capture could not start");
+      }
+      for (int i = 0; i < n; ++i) per_step[i] = forests[i]->launches;
+      rs = combined();
+      for (int i = 0; i < n; ++i) per_step[i] = forests[i]->launches - per_step[i];
+      const cudaError_t ec = cudaStreamEndCapture(origin, &graph);
+      if (rs) break;
+      if (ec != cudaSuccess || cudaGraphInstantiate(&gexec, graph, 0) != cudaSuccess) {
+        cleanup();
+        return fail(f, ACM_ECUDA, std::string("graph capture: ") + cudaGetErrorString(ec));
+      }
+      if (graph_used) *graph_used = 2;
+      if (cudaGraphLaunch(gexec, origin) != cudaSuccess) { cleanup(); return fail(f, ACM_ECUDA, "graph launch"); }
       continue;
     }
     if (!gexec) {
@@ -1678,8 +1830,8 @@ acm_status acm_rk4_steps_batch(acm_forest* const* forests, int n, int nsteps, do
     }
     if (cudaGraphLaunch(gexec, origin) != cudaSuccess) { cleanup(); return fail(f, ACM_ECUDA, "graph launch"); }
   }
-  if (gexec) {
-    // the instances' streams continue after the last replay
+  if (gexec || persistent) {
+    // the instances' streams continue after the last replay (or the last combined step)
     cudaEventRecord(ev[n], origin);
     for (int i = 1; i < n; ++i) cudaStreamWaitEvent(forests[i]->st, ev[n], 0);
   }

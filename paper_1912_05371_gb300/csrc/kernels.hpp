@@ -81,6 +81,34 @@ struct StageK {
   const double* coefp;
 };
 
+// The arrays one stage update of one block reads and writes (see StageK).
+template <typename T>
+struct StagePtrs {
+  const T* in;
+  const T* U;
+  T* acc;
+  T* out;
+  const T* chi;
+  const T* slab;
+  unsigned long long* norms;
+  const double* coefp;
+};
+
+// One instance of the persistent multi-instance stage launch: its arrays and its topology.
+template <typename T>
+struct StageInst {
+  StagePtrs<T> p;
+  TopoK tp;
+};
+
+// One RK stage of several independent instances in one persistent launch (ctas CTAs walking the
+// nwork (instance, rank) pairs of work); the instances share PhysK and take their stage
+// coefficients from their own p.coefp (the time step on the device).  desc and work are device
+// arrays.
+template <typename T>
+void launch_stage_multi(int stage, int Bs, const PhysK& p, const StageInst<T>* desc, const int2* work, int64_t nwork,
+                        int ctas, int* err, cudaStream_t st);
+
 // Parameters of the device time step (Sec. 2.3): CFL rule as on the host; h = finest spacing.
 struct RkK {
   double dt_fixed;          // > 0: use it

@@ -18,6 +18,8 @@
 // neighbour's stored interior (same level: copy; finer: decimation, Sec. 3.1 restriction) or,
 // across a face to a coarser neighbour, from the halo slab that the coarse-face kernel
 // predicted for this stage.  No ghost layer is written to HBM.
+#include <algorithm>
+
 #include "stage_common.cuh"
 
 namespace acm {
@@ -50,9 +52,10 @@ __host__ __device__ constexpr int staged_planes(bool mask) {
 // two-slot shared-memory ring by 1D bulk copies (one thread issues them after the plane
 // barrier of iteration z, completion on an mbarrier per slot), instead of per-thread loads at
 // the point of use.
-template <typename T, int BS, int STAGE, bool TMA = false>
-__global__ void __launch_bounds__(Cfg<T, BS>::NT, sizeof(T) == 4 ? 3 : 1)
-k_stage(const StageK<T> a, const TopoK tp, const PhysK ph, int* err) {
+// The update of one block (rank `rank` of the topology tp); a: the arrays, kc: the constants.
+template <typename T, int BS, int STAGE, bool TMA>
+__device__ __forceinline__ void stage_block(const StagePtrs<T>& a, const StageConst<T>& kc, const TopoK& tp,
+                                            const PhysK& ph, int* err, const int rank) {
   using L = Lay<T, BS>;
   constexpr int M = L::M;
   constexpr int NT = Cfg<T, BS>::NT;
@@ -69,17 +72,16 @@ k_stage(const StageK<T> a, const TopoK tp, const PhysK ph, int* err) {
   __shared__ unsigned hlo[NH], hhi[NH], hzd[NH];
 
   const int tid = threadIdx.x;
-  const int slot = tp.blist[blockIdx.x];
-  const int4 bi = tp.binfo[blockIdx.x];
-  const int* nbh = tp.nbh + (size_t)blockIdx.x * kNbhStride;
+  const int slot = tp.blist[rank];
+  const int4 bi = tp.binfo[rank];
+  const int* nbh = tp.nbh + (size_t)rank * kNbhStride;
 
-  stage_faces(tid, nbh, tp.slabidx, blockIdx.x, ftype, fs);
+  stage_faces(tid, nbh, tp.slabidx, rank, ftype, fs);
   stage_sponge<T, BS>(tid, ph, bi, sp);
   __syncthreads();
 
   // model and RK constants are read from the kernel parameters (constant bank), not registers;
   // so are the level's 1/h and 1/(12 h^2) (no per-thread FP64 division)
-  const StageConst<T>& kc = a.kc;
   // 1/h is applied once per right-hand side term, not to every difference
   const T ih = kc.ih[bi.x], nu_ih2 = kc.nu * kc.ih2[bi.x], c0sq_ih = kc.c0sq * ih;
   // RK coefficients: kernel parameters, or (steps with the time step on the device) the values
@@ -359,6 +361,28 @@ k_stage(const StageK<T> a, const TopoK tp, const PhysK ph, int* err) {
   }
 }
 
+template <typename T, int BS, int STAGE, bool TMA = false>
+__global__ void __launch_bounds__(Cfg<T, BS>::NT, sizeof(T) == 4 ? 3 : 1)
+k_stage(const StageK<T> a, const TopoK tp, const PhysK ph, int* err) {
+  const StagePtrs<T> p{a.in, a.U, a.acc, a.out, a.chi, a.slab, a.norms, a.coefp};
+  stage_block<T, BS, STAGE, TMA>(p, a.kc, tp, ph, err, blockIdx.x);
+}
+
+// Persistent form over several independent instances: the CTAs walk the work list of
+// (instance, rank) pairs, each instance with its own arrays and topology (desc) and the same
+// physics and constants; every block gets bitwise the update k_stage gives it.
+template <typename T, int BS, int STAGE>
+__global__ void __launch_bounds__(Cfg<T, BS>::NT, sizeof(T) == 4 ? 3 : 1)
+k_stage_multi(const StageConst<T> kc, const PhysK ph, const StageInst<T>* desc, const int2* work, int nwork,
+              int* err) {
+  for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
+    const int2 it = work[w];
+    const StageInst<T> d = desc[it.x];
+    stage_block<T, BS, STAGE, false>(d.p, kc, d.tp, ph, err, it.y);
+    __syncthreads();                   // the next block reuses the shared arrays
+  }
+}
+
 // Time step of one RK4 step on the device (Sec. 2.3): dt_fixed if > 0, else the CFL rule from the
 // velocity max norm of the last reduction (maxbits[4]); writes rk[0] = dt, rk[1] += dt (time)
 // and the stage coefficients rk[2..9] = (c_acc, c_out) of stages 1..4, in double, by the same
@@ -409,6 +433,48 @@ void launch_stage_bs(int stage, const StageK<T>& s, const TopoK& t, const PhysK&
 }  // namespace
 
 template <typename T>
+StageConst<T> stage_constants(const PhysK& p, double c_acc, double c_out) {
+  StageConst<T> c{};
+  c.a1 = T(p.a1); c.a2 = T(p.a2); c.a3 = T(p.a3);
+  c.nu = T(p.nu); c.c0sq = T(p.c0sq); c.cgam = T(p.cgamma);
+  c.inv_ceta = T(p.inv_ceta); c.inv_csp = T(p.inv_csp);
+  for (int i = 0; i < 3; ++i) c.uinf[i] = T(p.uinf[i]);
+  c.pinf = T(p.pinf);
+  c.c_acc = T(c_acc); c.c_out = T(c_out);
+  for (int J = 0; J <= kMaxLevel; ++J) {
+    c.ih[J] = T(1.0 / p.h[J]);
+    c.ih2[J] = T(1.0 / (12.0 * p.h[J] * p.h[J]));
+  }
+  return c;
+}
+
+template <typename T>
+void launch_stage_multi(int stage, int Bs, const PhysK& p, const StageInst<T>* desc, const int2* work, int64_t nwork,
+                        int ctas, int* err, cudaStream_t st) {
+  if (nwork <= 0) return;
+  const StageConst<T> kc = stage_constants<T>(p, 0.0, 0.0);
+  const int nb = (int)std::min<int64_t>(nwork, (int64_t)std::max(ctas, 1));
+  auto go = [&](auto kern, int nt) { kern<<<nb, nt, 0, st>>>(kc, p, desc, work, (int)nwork, err); };
+  if (Bs == 17) {
+    constexpr int NT = Cfg<T, 17>::NT;
+    switch (stage) {
+      case 1: go(k_stage_multi<T, 17, 1>, NT); break;
+      case 2: go(k_stage_multi<T, 17, 2>, NT); break;
+      case 3: go(k_stage_multi<T, 17, 3>, NT); break;
+      default: go(k_stage_multi<T, 17, 4>, NT); break;
+    }
+  } else {
+    constexpr int NT = Cfg<T, 9>::NT;
+    switch (stage) {
+      case 1: go(k_stage_multi<T, 9, 1>, NT); break;
+      case 2: go(k_stage_multi<T, 9, 2>, NT); break;
+      case 3: go(k_stage_multi<T, 9, 3>, NT); break;
+      default: go(k_stage_multi<T, 9, 4>, NT); break;
+    }
+  }
+}
+
+template <typename T>
 void launch_stage(int stage, int Bs, const StageK<T>& s, const TopoK& t, const PhysK& p, int* err,
                   cudaStream_t st, int variant) {
   if constexpr (sizeof(T) == 4) {
@@ -418,17 +484,7 @@ void launch_stage(int stage, int Bs, const StageK<T>& s, const TopoK& t, const P
     }
   }
   StageK<T> a = s;
-  StageConst<T>& c = a.kc;
-  c.a1 = T(p.a1); c.a2 = T(p.a2); c.a3 = T(p.a3);
-  c.nu = T(p.nu); c.c0sq = T(p.c0sq); c.cgam = T(p.cgamma);
-  c.inv_ceta = T(p.inv_ceta); c.inv_csp = T(p.inv_csp);
-  for (int i = 0; i < 3; ++i) c.uinf[i] = T(p.uinf[i]);
-  c.pinf = T(p.pinf);
-  c.c_acc = T(s.c_acc); c.c_out = T(s.c_out);
-  for (int J = 0; J <= kMaxLevel; ++J) {
-    c.ih[J] = T(1.0 / p.h[J]);
-    c.ih2[J] = T(1.0 / (12.0 * p.h[J] * p.h[J]));
-  }
+  a.kc = stage_constants<T>(p, s.c_acc, s.c_out);
   if constexpr (sizeof(T) == 4) {
     if (variant == kStagePointTMA) {
       if (Bs == 17) launch_stage_bs<T, 17, true>(stage, a, t, p, err, st);
@@ -445,6 +501,10 @@ void launch_rk_coefs(const unsigned long long* maxbits, const RkK& p, double* rk
 }
 
 template void launch_stage<float>(int, int, const StageK<float>&, const TopoK&, const PhysK&, int*, cudaStream_t, int);
+template void launch_stage_multi<float>(int, int, const PhysK&, const StageInst<float>*, const int2*, int64_t, int, int*,
+                                        cudaStream_t);
+template void launch_stage_multi<double>(int, int, const PhysK&, const StageInst<double>*, const int2*, int64_t, int,
+                                         int*, cudaStream_t);
 template void launch_stage<double>(int, int, const StageK<double>&, const TopoK&, const PhysK&, int*, cudaStream_t, int);
 
 }  // namespace acm

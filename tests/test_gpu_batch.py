@@ -69,14 +69,17 @@ def test_instance_rk4_steps_match_oracle(A):
     assert max(err) < 1e-12, err
 
 
-@pytest.mark.parametrize("prec,Bs", [(64, 9), (32, 17)])
-def test_batched_graph_equals_instance_by_instance(A, prec, Bs):
+@pytest.mark.parametrize("prec,Bs,mode", [(64, 9, 1), (32, 17, 1), (32, 17, 2), (64, 9, 2), (32, 9, 2)])
+def test_batched_graph_equals_instance_by_instance(A, prec, Bs, mode):
+    """The batched steps -- one graph of per-instance launch sequences (mode 1), or the persistent
+    form with one stage launch walking the blocks of every instance (mode 2) -- give every instance
+    bitwise the steps it takes alone."""
     import torch
     insts = W.batched_instances(seed=5, n=3, nb_range=(8, 80), Jmax=3)
     streams = [torch.cuda.Stream() for _ in insts]
     batch = [_forest(A, i, prec, Bs, 3, stream=s) for i, s in zip(insts, streams)]
-    times, used = A.rk4_steps_batch(batch, 4, 0.0, graph=True)
-    assert used
+    times, used = A.rk4_steps_batch(batch, 4, 0.0, graph=mode)
+    assert used == mode
     for inst, s, tb, fb in zip(insts, streams, times, batch):
         f = _forest(A, inst, prec, Bs, 3, stream=s)
         t, _ = f.rk4_steps(4, 0.0, graph=False)
