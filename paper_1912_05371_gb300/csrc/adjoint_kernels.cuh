@@ -9,14 +9,17 @@
 // face halos (3 layers) from the finest leaf holding a point, else by the tensor DD-4 prediction
 // (Sec. 3.1, 4.2), and loc is the block-local stencil arithmetic.  The adjoint of one stage,
 // nu = W^T E^T loc^T kappa with kappa = c_lam lam + c_nu nu' (the RK4 adjoint combination), takes
-// three launches:
-//   k_adj_stage  loc^T at every block's own interior points, in gather form (a z-march like the
-//                forward stage kernel), with the combination for kappa, the running sum of the
-//                stage nus and the mask sensitivity fused in;
-//   k_adj_halo   loc^T at the face-halo points and E^T: added to the points they were read from
-//                (the finest leaf holding the point, or its DD-4 prediction's even points);
-//   k_adj_fw_T   W^T: a boundary point held by a finer leaf passes its value to that leaf's point
-//                and is cleared.
+// four launches:
+//   k_adj_stage      loc^T at every block's own interior points, in gather form (a z-march like
+//                    the forward stage kernel), with the combination for kappa, the running sum
+//                    of the stage nus and the mask sensitivity fused in;
+//   k_adj_samelevel  E^T of the face-halo targets that same-level neighbours read from a block,
+//                    gathered by that block (no atomics);
+//   k_adj_halo       loc^T at the face-halo points toward finer and coarser faces and E^T: added
+//                    to the points they were read from (the finest leaf holding the point, or its
+//                    DD-4 prediction's even points);
+//   k_adj_fw_T       W^T: a boundary point held by a finer leaf passes its value to that leaf's
+//                    point and is cleared.
 // The objective's direct terms and the reduction of the mask sensitivity onto the sphere's centre
 // and radius complete the sweep (host side in api.cu).
 //
@@ -389,13 +392,96 @@ k_adj_stage(const AdjStageK<T> a, const TopoK tp, const PhysK ph, const MaskK m)
 //             + nu/(12 h^2) sum_{k=l..2} d2_k kappa_i(q -+ k e_n)                      (i < 3)
 //   nu_p(q) = -1/h sum_{m=l..3} (+-a_m) kappa_n(q -+ m e_n)
 // (n the normal axis, the sign that of the face), added through E^T to the point q was read from.
-// One CTA per (block, face).  Across a same-level face that is the neighbour's point, across a
-// finer face the child's coinciding point (the forward's copy and decimation); fine wins' copies
+// One CTA per (block, face); faces toward a same-level neighbour are left to that neighbour,
+// which gathers them (k_adj_samelevel).  Across a finer face q goes to the child's coinciding
+// point (the forward's decimation); fine wins' copies
 // between leaves are W's part (k_adj_fw_T).  Across a coarser face, q is held by a leaf if it lies
 // on one's lattice (its point gets the value), else it was predicted by the tensor DD-4 from the
 // even points of the 5 x (M/2 + 3)^2 coarse patch around the face: the transposed prediction is
 // summed per patch point in shared memory first, then each patch point goes to the leaf holding
 // it.  FP atomics: several blocks reach one point.  Runs after k_adj_stage.
+//
+// E^T across same-level faces in gather form: block A adds to its own points the face-halo
+// targets of its same-level face neighbours that the forward read from A (the neighbour N's
+// halo point at distance l beyond the shared face is A's point at distance l inside it), each
+// computed from N's sources next to the face as k_adj_halo computes a halo target.  One CTA per
+// block walks its six faces in turn (a point near an edge takes one face's value at a time), so
+// the additions need no atomics; it runs after k_adj_stage and before k_adj_halo's atomics.
+template <typename T, int BS>
+__global__ void __launch_bounds__(kNA) k_adj_samelevel(const AdjStageK<T> a, const TopoK tp, const PhysK ph, int* err) {
+  using L = Lay<T, BS>;
+  constexpr int M = L::M;
+  __shared__ int types[6], slots[6];
+  const int rank = blockIdx.x;
+  if (threadIdx.x < 6) {
+    const int d = kFaceBox[threadIdx.x];
+    const int* nbh = tp.nbh + (size_t)rank * kNbhStride;
+    types[threadIdx.x] = nbh[kNbhType + d] & 15;
+    slots[threadIdx.x] = nbh[8 * d];
+  }
+  __syncthreads();
+  const size_t bo = (size_t)tp.blist[rank] * L::BLK;
+  const int4 bi = tp.binfo[rank];
+  const T ih = T(1.0 / ph.h[bi.x]);
+  const T nu_ih2 = T(ph.nu / (12.0 * ph.h[bi.x] * ph.h[bi.x]));
+  const T c0sq = T(ph.c0sq);
+  const T am[3] = {T(ph.a1), T(ph.a2), T(ph.a3)};
+  const T d2[2] = {T(16), T(-1)};
+  const T c_lam = T(a.c_lam), c_nu = T(a.c_nu);
+  for (int F = 0; F < 6; ++F) {
+    if (types[F] != kTypeLeaf) continue;                        // uniform over the CTA
+    if (slots[F] < 0) {
+      if (threadIdx.x == 0) atomicOr(err, 8);
+      continue;
+    }
+    const int ax = F >> 1, side = F & 1;
+    const int o1 = ax == 0 ? 1 : 0, o2 = 3 - ax - o1;
+    const size_t nb = (size_t)slots[F] * L::BLK;
+    // the shared face is the neighbour's opposite face: its sources at distance k inside it sit
+    // at neighbour coordinate k (this block's upper face) or M - k (its lower face), and its
+    // halo stencils take the sign of that face
+    const T sg = side ? T(-1) : T(1);
+    for (int t = threadIdx.x; t < 4 * BS * BS; t += kNA) {
+      const int f = t / (BS * BS), uv = t % (BS * BS);
+      int p[3] = {0, 0, 0};
+      p[o1] = uv % BS;
+      p[o2] = uv / BS;
+      T Wk[3], Kk[3];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        p[ax] = side ? k : M - k;
+        const size_t po = nb + L::idx(p[0], p[1], p[2]);
+        auto kappa = [&](int g) -> T {
+          T kv = c_lam * a.lam[po + (size_t)g * L::FS];
+          if (a.nup) kv += c_nu * a.nup[po + (size_t)g * L::FS];
+          return kv;
+        };
+        if (f < 3) {
+          Kk[k] = kappa(f);
+          Wk[k] = a.Y[po + (size_t)ax * L::FS] * Kk[k];
+          if (f == ax) Wk[k] += c0sq * kappa(3);
+        } else {
+          Kk[k] = T(0);
+          Wk[k] = kappa(ax);
+        }
+      }
+#pragma unroll
+      for (int l = 1; l <= 3; ++l) {
+        T de = T(0), dd = T(0);
+#pragma unroll
+        for (int k = 0; k + l <= 3; ++k) {
+          de += sg * am[l + k - 1] * Wk[k];
+          if (l + k <= 2) dd += d2[l + k - 1] * Kk[k];
+        }
+        de = -ih * de + (f < 3 ? nu_ih2 * dd : T(0));
+        p[ax] = side ? M - l : l;
+        a.nu[bo + (size_t)f * L::FS + L::idx(p[0], p[1], p[2])] += de;
+      }
+    }
+    __syncthreads();
+  }
+}
+
 template <typename T, int BS>
 struct HaloCfg {
   static constexpr int M = BS - 1;
@@ -416,6 +502,8 @@ __global__ void __launch_bounds__(kNA) k_adj_halo(const AdjStageK<T> a, const To
   const int ax = F >> 1, side = F & 1;
   const int d = kFaceBox[F];
   const int ty = nbh[kNbhType + d] & 15;
+  // a same-level neighbour gathers these targets itself (k_adj_samelevel)
+  if (ty == kTypeLeaf) return;
   const bool coarse = ty != kTypeLeaf && ty != kTypeRefined;
   if (coarse) {
     for (int i = threadIdx.x; i < 4 * NP; i += kNA) acc[i] = T(0);
@@ -644,22 +732,24 @@ __global__ void __launch_bounds__(kNA) k_adj_objective(const T* U, const T* chi,
   const double h = ph.h[bi.x], h3 = h * h * h;
   const size_t own = (size_t)slot * L::BLK;
   const bool moving = m.kind == 2;
+  // the terms' weights of this block in FP64, the per-point products in the field precision
+  const T a_chi = T(wN * h3 * ph.inv_ceta), a_e = T(wN * wE * h3);
   double dth = 0.0;
   for (int t = threadIdx.x; t < M * M * M; t += kNA) {
     const int x = t % M, y = (t / M) % M, z = t / (M * M);
     const int pi = L::idx(x, y, z);
-    const double u = (double)U[own + pi];
-    const double c = ph.mask ? (double)chi[(size_t)slot * L::FS + pi] : 0.0;
-    lam[own + pi] += T(wN * (c * ph.inv_ceta + wE * u) * h3);
-    for (int f = 1; f < 3; ++f)
-      lam[own + (size_t)f * L::FS + pi] += T(wN * wE * (double)U[own + (size_t)f * L::FS + pi] * h3);
+    const T uT = U[own + pi];
+    const T cT = ph.mask ? chi[(size_t)slot * L::FS + pi] : T(0);
+    lam[own + pi] += a_chi * cT + a_e * uT;
+    for (int f = 1; f < 3; ++f) lam[own + (size_t)f * L::FS + pi] += a_e * U[own + (size_t)f * L::FS + pi];
     if (moving) {
+      const double u = (double)uT, c = (double)cT;
       const BoxPoint bp = box_point(m, lattice_coord(ph, bi, 0, x, M, h) - m.p[9],
                                     lattice_coord(ph, bi, 1, y, M, h) - m.p[10],
                                     lattice_coord(ph, bi, 2, z, M, h) - m.p[11]);
       dth += wN * h3 * ph.inv_ceta * ((u - bp.us[0]) * bp.dchi - c * bp.dus[0]);
     } else if (ph.mask) {
-      gchi[(size_t)slot * L::FS + pi] += T(wN * u * h3 * ph.inv_ceta);
+      gchi[(size_t)slot * L::FS + pi] += a_chi * uT;
     }
   }
   if (moving) block_add(dth, dtheta);
@@ -750,6 +840,7 @@ void stage(const AdjStageK<T>& a, const TopoK& t, const PhysK& ph, const MaskK& 
   static std::atomic<unsigned long long> opted{0};
   smem_opt_in_stage(k_adj_stage<T, BS>, AdjCfg<T, BS>::bytes, opted);
   k_adj_stage<T, BS><<<g1(t.n), AdjCfg<T, BS>::NT, AdjCfg<T, BS>::bytes, st>>>(a, t, ph, m);
+  k_adj_samelevel<T, BS><<<g1(t.n), kNA, 0, st>>>(a, t, ph, err);
   k_adj_halo<T, BS><<<g1(6 * t.n), kNA, 0, st>>>(a, t, ph, err);
   k_adj_fw_T<T, BS><<<fw_ctas(fw.max_tasks), kNA, 0, st>>>(a.nu, fw.tasks, fw.ntasks, t.nbh, t.blist);
 }

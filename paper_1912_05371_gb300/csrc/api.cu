@@ -1253,7 +1253,7 @@ acm_status adjoint_sweep(acm_forest* f, int nsteps, double dt, int c, double wE,
     a.gchi = GCHI;
     a.dtheta = TH;
     acm::launch_adj_stage<T>(Bs, a, tk_topo, f->phk, cur_mask(), fwt, f->d_err, f->st);
-    f->launches += 4;
+    f->launches += 5;
     return cudaGetLastError() == cudaSuccess ? ACM_OK : fail(f, ACM_ECUDA, "adjoint kernel launch failed");
   };
   auto objective = [&](const T* Us, double tn) {
