@@ -66,11 +66,15 @@ typedef enum {
 
 /* Grid of cubic blocks (Sec. 4.1).  nroot[3] roots of side root_len tile the periodic box
  * [0, nroot*root_len]; a block at level J has side root_len/2^J and spacing
- * h_J = root_len / (2^J (Bs-1)).  Bs must be 9 or 17.  g is the ghost depth reported by
+ * h_J = root_len / (2^J (Bs-1)).  Bs is 9, 17 or 33; Bs = 33 takes precision 32 and the CDF 4/0
+ * wavelet (ACM_EINVAL otherwise), and its forests have no adjoint (acm_adjoint_* return
+ * ACM_EINVAL) and no persistent batched form (acm_rk4_steps_batch falls back to the graph of
+ * per-instance launches).  g is the ghost depth reported by
  * acm_sync_ghosts (1..4).  precision is 32 or 64.  fd_scheme: 1 = Tam-Webb optimised first
  * derivative (Sec. 2.3, the paper's choice), 0 = classical (8,-1)/12.  Levels obey
- * 0 <= Jmin <= Jmax <= 18 (Sec. 3.5).  max_blocks (the block pool) is at most
- * 2^32 / (72 Bs^2) blocks (206,000 at Bs = 17): device offsets into the pool are 32-bit.
+ * 0 <= Jmin <= Jmax <= 18 (Sec. 3.5).  max_blocks (the block pool) is below 2^32 divided by
+ * the larger of a block's padded element count and 72 Bs^2 (about 206,000 blocks at Bs = 17,
+ * 29,700 at Bs = 33): device offsets into the pool are 32-bit.
  * wavelet (Sec. 3.2): 40 = CDF 4/0, the interpolating wavelet (a merged parent is the decimated
  * children); 44 = CDF 4/4, its lifted form (Sec. 3.2.1): a merged parent's interior points take
  * the lifted analysis low-pass of the children's level and the 4 fine points around them, its
@@ -472,7 +476,7 @@ int64_t acm_launch_count(const acm_forest* f);
  * norm, NaN before infinity, as acm_diagnostics reports a non-finite state).  stream:
  * cudaStream_t (NULL = legacy default stream);
  * the call is asynchronous on it.
- * Returns ACM_EINVAL for bad arguments (Bs other than 9 or 17, precision other than 32 or 64,
+ * Returns ACM_EINVAL for bad arguments (Bs other than 9, 17 or 33, precision other than 32 or 64,
  * NULL pointers, n_blocks < 1), ACM_ECAPACITY if n_blocks > ACM_NOALLOC_MAX_BLOCKS (nothing is
  * launched), ACM_ECUDA if a launch or the set-up fails.
  * Scratch: a fixed array compiled into the library (per-block partial maxima).  The first call

@@ -113,7 +113,10 @@ __global__ void __launch_bounds__(kNT) k_fine_wins(T* reg, const int2* tasks, co
 // Dynamic shared memory: P, A, B below in T, then the neighbourhood.
 template <typename T, int BS>
 struct SlabSmem {
-  static constexpr int NT = ((BS * BS + 31) / 32) * 32;
+  // a thread per halo column (t0, t1); above 1024 columns (Bs = 33) a thread takes two
+  static constexpr int NT = BS * BS <= 1024 ? ((BS * BS + 31) / 32) * 32 : 1024;
+  static constexpr bool ONE = BS * BS <= NT;        // one column per thread
+  static constexpr int MINB = BS <= 17 ? 3 : 1;     // CTAs per SM
   static constexpr int M = BS - 1;
   static constexpr int NC = M / 2 + 3;              // coarse samples along the face: -2..M+2 step 2
   static constexpr int NN = 5;                      // coarse planes across the face
@@ -136,9 +139,9 @@ __device__ __forceinline__ int edge_index(int t0, int t1) {
 }
 
 template <typename T, int BS>
-__global__ void __launch_bounds__(SlabSmem<T, BS>::NT, 3) k_coarse_slabs(const T* reg, T* slab, const int4* tasks,
-                                                                       const int32_t* ntasks, const int32_t* nbh_all,
-                                                                       uint32_t* offc, int use_cache) {
+__global__ void __launch_bounds__(SlabSmem<T, BS>::NT, SlabSmem<T, BS>::MINB)
+k_coarse_slabs(const T* reg, T* slab, const int4* tasks, const int32_t* ntasks, const int32_t* nbh_all, uint32_t* offc,
+               int use_cache) {
   using L = Lay<T, BS>;
   using S = SlabSmem<T, BS>;
   constexpr int M = L::M, NT = S::NT, NC = S::NC, NN = S::NN;
@@ -167,26 +170,35 @@ __global__ void __launch_bounds__(SlabSmem<T, BS>::NT, 3) k_coarse_slabs(const T
     else if (ax == 1) { *x = t0; *y = nl; *z = t1; }
     else { *x = t0; *y = t1; *z = nl; }
   };
-  const bool col = tid < BS * BS;
-  const int t0 = col ? tid % BS : 0, t1 = col ? tid / BS : 0;
-  const bool edge = col && (t0 == 0 || t0 == M || t1 == 0 || t1 == M);
-  // leaf lookups (component 0 offsets; component f is FS further), then all loads at once
-  long long eo[3] = {-1, -1, -1};
-  const int ei = edge ? edge_index<BS>(t0, t1) : 0;
-  if (edge) {
+  // leaf lookups of the halo column (t0, t1) on the face's boundary lines (component 0
+  // offsets; component f is FS further), and its values
+  auto edge_values = [&](int t0, int t1, long long (&eo)[3], T (&ev)[3][4]) {
+    eo[0] = eo[1] = eo[2] = -1;
+    if (t0 == 0 || t0 == M || t1 == 0 || t1 == M) {
+      const int ei = edge_index<BS>(t0, t1);
 #pragma unroll
-    for (int l = 1; l <= 3; ++l) {
-      if (cached) {
-        const uint32_t v = oc[NP3 + 3 * ei + l - 1];
-        eo[l - 1] = v == 0xffffffffu ? -1 : (long long)v;
-      } else {
-        int x, y, z;
-        place(plus ? M + l : -l, t0, t1, &x, &y, &z);
-        eo[l - 1] = direct_offset<T, BS>(nbh, x, y, z, 0);
-        if (oc) oc[NP3 + 3 * ei + l - 1] = eo[l - 1] < 0 ? 0xffffffffu : (uint32_t)eo[l - 1];
+      for (int l = 1; l <= 3; ++l) {
+        if (cached) {
+          const uint32_t v = oc[NP3 + 3 * ei + l - 1];
+          eo[l - 1] = v == 0xffffffffu ? -1 : (long long)v;
+        } else {
+          int x, y, z;
+          place(plus ? M + l : -l, t0, t1, &x, &y, &z);
+          eo[l - 1] = direct_offset<T, BS>(nbh, x, y, z, 0);
+          if (oc) oc[NP3 + 3 * ei + l - 1] = eo[l - 1] < 0 ? 0xffffffffu : (uint32_t)eo[l - 1];
+        }
       }
     }
-  }
+#pragma unroll
+    for (int l = 0; l < 3; ++l)
+#pragma unroll
+      for (int f = 0; f < 4; ++f) ev[l][f] = eo[l] >= 0 ? reg[eo[l] + (long long)f * L::FS] : T(0);
+  };
+  // with one column per thread its edge values are loaded with the patch, before the passes
+  const bool col = tid < BS * BS;
+  long long eo[3];
+  T ev[3][4];
+  if (S::ONE && col) edge_values(tid % BS, tid / BS, eo, ev);
   constexpr int U = (NP3 + NT - 1) / NT;
   long long off[U];
 #pragma unroll
@@ -206,11 +218,6 @@ __global__ void __launch_bounds__(SlabSmem<T, BS>::NT, 3) k_coarse_slabs(const T
       }
     }
   }
-  T ev[3][4];
-#pragma unroll
-  for (int l = 0; l < 3; ++l)
-#pragma unroll
-    for (int f = 0; f < 4; ++f) ev[l][f] = eo[l] >= 0 ? reg[eo[l] + (long long)f * L::FS] : T(0);
   T pv[U][4];
 #pragma unroll
   for (int k = 0; k < U; ++k)
@@ -240,7 +247,8 @@ __global__ void __launch_bounds__(SlabSmem<T, BS>::NT, 3) k_coarse_slabs(const T
     for (int i = 0; i < BS; ++i) B[(fn * BS + i) * BS + l0] = dd4_line<T, BS>(cv, i);
   }
   __syncthreads();
-  if (col) {                                        // across the face: column (t0, t1)
+  // across the face: column (t0, t1)
+  auto column_out = [&](int t0, int t1, const long long (&eo)[3], const T (&ev)[3][4]) {
     const T w[4] = {T(-1) / T(16), T(9) / T(16), T(9) / T(16), T(-1) / T(16)};
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
@@ -265,6 +273,14 @@ __global__ void __launch_bounds__(SlabSmem<T, BS>::NT, 3) k_coarse_slabs(const T
         }
         slab[((((size_t)tk.z * 4 + f) * 3 + (l - 1)) * BS + t1) * BS + t0] = v;
       }
+    }
+  };
+  if (S::ONE) {
+    if (col) column_out(tid % BS, tid / BS, eo, ev);
+  } else {
+    for (int c = tid; c < BS * BS; c += NT) {
+      edge_values(c % BS, c / BS, eo, ev);
+      column_out(c % BS, c / BS, eo, ev);
     }
   }
   }
@@ -458,6 +474,134 @@ __global__ void __launch_bounds__(DetSmem<T, BS>::NT) k_details(const T* reg, co
   }
 }
 
+// Block indicators of Bs = 33 blocks: the same passes with one component's coarse samples in
+// shared memory at a time (four would not fit beside px and py); the leaf lookups are done once
+// and kept in shared memory as 32-bit offsets (the pool's element offsets fit 32 bits, checked at
+// forest creation).  A thread owns up to two columns in the mask range and the z-pass, and reads
+// the block's values there as it compares them.  Same values as k_details.
+template <typename T, int BS>
+struct DetBigSmem {
+  static constexpr int NT = 1024;
+  static constexpr int NC = (BS - 1) / 2 + 3;
+  static constexpr int NC3 = NC * NC * NC;
+  static constexpr int PX = NC * NC * BS, PY = NC * BS * BS;
+  static constexpr size_t bytes = (size_t)(NC3 + PX + PY) * sizeof(T) + (size_t)NC3 * sizeof(uint32_t) +
+                                  kNbhStride * sizeof(int);
+};
+
+template <typename T, int BS>
+__global__ void __launch_bounds__(DetBigSmem<T, BS>::NT, 1)
+k_details_big(const T* reg, const T* chi, const int32_t* blist, const int32_t* ranks, const int32_t* nbh_all,
+              const unsigned long long* norm_bits, double* ind, double* chirange) {
+  using L = Lay<T, BS>;
+  using S = DetBigSmem<T, BS>;
+  constexpr int M = L::M;
+  constexpr int NT = S::NT, NC = S::NC, NC3 = S::NC3;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* cs = reinterpret_cast<T*>(smem_raw);       // c[zc][yc][xc] of one component
+  T* px = cs + NC3;                             // px[zc][yc][x]
+  T* py = px + S::PX;                           // py[zc][y][x]
+  uint32_t* offs = reinterpret_cast<uint32_t*>(py + S::PY);
+  int* nbh = reinterpret_cast<int*>(offs + NC3);
+  __shared__ T red[6][NT / 32];
+  const int tid = threadIdx.x;
+  const int rank = ranks ? ranks[blockIdx.x] : (int)blockIdx.x;
+  const int slot = blist[rank];
+  const int wid = tid >> 5, lane = tid & 31;
+  const T* bb = reg + (size_t)slot * L::BLK;
+  T tmin = T(1e30), tmax = T(-1e30);
+  if (chi) {
+    const T* cb = chi + (size_t)slot * L::FS;
+    for (int c = tid; c < BS * BS; c += NT) {
+      for (int z = 0; z < BS; ++z) {
+        const T v = cb[L::idx(c % BS, c / BS, z)];
+        tmin = v < tmin ? v : tmin;
+        tmax = v > tmax ? v : tmax;
+      }
+    }
+  }
+  for (int i = tid; i < kNbhStride; i += NT) nbh[i] = nbh_all[(size_t)rank * kNbhStride + i];
+  __syncthreads();
+  for (int i = tid; i < NC3; i += NT) {
+    const int cx = 2 * (i % NC) - 2, cy = 2 * ((i / NC) % NC) - 2, cz = 2 * (i / (NC * NC)) - 2;
+    long long off;
+    if (cx >= 0 && cx <= M && cy >= 0 && cy <= M && cz >= 0 && cz <= M)
+      off = (long long)slot * L::BLK + L::idx(cx, cy, cz);
+    else
+      off = direct_offset<T, BS>(nbh, cx, cy, cz, 0);
+    offs[i] = off < 0 ? 0xffffffffu : (uint32_t)off;
+  }
+  __syncthreads();
+  for (int f = 0; f < 4; ++f) {
+    for (int i = tid; i < NC3; i += NT) {
+      const uint32_t o = offs[i];
+      cs[i] = o == 0xffffffffu ? T(__longlong_as_double(0x7ff8000000000000ll)) : reg[(size_t)o + (size_t)f * L::FS];
+    }
+    __syncthreads();                            // cs complete (py free: the last z-pass is done)
+    if (tid < NC * NC) {                        // x-pass: line (yc, zc)
+      T cv[NC];
+#pragma unroll
+      for (int k = 0; k < NC; ++k) cv[k] = cs[tid * NC + k];
+#pragma unroll
+      for (int i = 0; i < BS; ++i) px[tid * BS + i] = dd4_line<T, BS>(cv, i);
+    }
+    __syncthreads();
+    if (tid < NC * BS) {                        // y-pass: line (x, zc)
+      const int lx = tid % BS, zc = tid / BS;
+      T cv[NC];
+#pragma unroll
+      for (int k = 0; k < NC; ++k) cv[k] = px[(zc * NC + k) * BS + lx];
+#pragma unroll
+      for (int i = 0; i < BS; ++i) py[(zc * BS + i) * BS + lx] = dd4_line<T, BS>(cv, i);
+    }
+    __syncthreads();
+    T dmax = T(0);
+    for (int c = tid; c < BS * BS; c += NT) {   // z-pass: column (x, y), compared with the block
+      const int x = c % BS, y = c / BS;
+      T cv[NC];
+#pragma unroll
+      for (int k = 0; k < NC; ++k) cv[k] = py[(k * BS + y) * BS + x];
+#pragma unroll
+      for (int z = 0; z < BS; ++z) {
+        const T dv = tabs(bb[(size_t)f * L::FS + L::idx(x, y, z)] - dd4_line<T, BS>(cv, z));
+        dmax = dv > dmax ? dv : dmax;
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const T t = __shfl_xor_sync(0xffffffffu, dmax, o);
+      dmax = t > dmax ? t : dmax;
+    }
+    if (lane == 0) red[f][wid] = dmax;
+    __syncthreads();                            // the z-pass is done with py before the next x-pass
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const T a = __shfl_xor_sync(0xffffffffu, tmin, o), b = __shfl_xor_sync(0xffffffffu, tmax, o);
+    tmin = a < tmin ? a : tmin;
+    tmax = b > tmax ? b : tmax;
+  }
+  if (lane == 0) { red[4][wid] = tmin; red[5][wid] = tmax; }
+  __syncthreads();
+  if (tid == 0) {
+    double best = 0.0;
+    for (int f = 0; f < 4; ++f) {
+      const double nf = __longlong_as_double((long long)norm_bits[f]);
+      const double inv = nf > 0.0 ? 1.0 / nf : 0.0;
+      if (inv == 0.0) continue;
+      T m = red[f][0];
+      for (int k = 1; k < NT / 32; ++k) m = red[f][k] > m ? red[f][k] : m;
+      const double r = (double)m * inv;
+      best = r > best ? r : best;
+    }
+    T mn = red[4][0], mx = red[5][0];
+    for (int k = 1; k < NT / 32; ++k) {
+      mn = red[4][k] < mn ? red[4][k] : mn;
+      mx = red[5][k] > mx ? red[5][k] : mx;
+    }
+    ind[rank] = best;
+    chirange[rank] = chi ? (double)mx - (double)mn : 0.0;
+  }
+}
+
 // ---- (5) max norms (Sec. 2.3 u_max, Sec. 3.4 normalisation) ------------------------------------
 template <typename T, int BS>
 __global__ void __launch_bounds__(kNT) k_maxnorm(const T* reg, const int32_t* blist, unsigned long long* out) {
@@ -528,6 +672,33 @@ struct RefSmem {
   static constexpr int NSHELL = PP - BS * BS * BS;  // ghost-shell points
   static constexpr size_t bytes = (size_t)(PP + EQ + QY) * sizeof(T) + kNbhStride * sizeof(int);
 };
+
+// Tensor DD-4 prediction at local point (gx, gy, gz) from the even lattice -4..M+4 in ev
+// (NEV points per axis): z outer, then y, then x.
+template <typename T, int NEV>
+__device__ __forceinline__ T predict_from_even(const T* ev, int gx, int gy, int gz) {
+  const int p[3] = {gx, gy, gz};
+  const T w[4] = {T(-1) / T(16), T(9) / T(16), T(9) / T(16), T(-1) / T(16)};
+  const int o4[4] = {-3, -1, 1, 3};
+  int cnt[3];
+  for (int a = 0; a < 3; ++a) cnt[a] = (p[a] & 1) ? 4 : 1;
+  T accz = T(0);
+  for (int kz = 0; kz < cnt[2]; ++kz) {
+    const int zz = ((cnt[2] == 4 ? gz + o4[kz] : gz) + 4) >> 1;
+    T accy = T(0);
+    for (int ky = 0; ky < cnt[1]; ++ky) {
+      const int yy = ((cnt[1] == 4 ? gy + o4[ky] : gy) + 4) >> 1;
+      T accx = T(0);
+      for (int kx = 0; kx < cnt[0]; ++kx) {
+        const int xx = ((cnt[0] == 4 ? gx + o4[kx] : gx) + 4) >> 1;
+        accx = accx + (cnt[0] == 4 ? w[kx] : T(1)) * ev[(zz * NEV + yy) * NEV + xx];
+      }
+      accy = accy + (cnt[1] == 4 ? w[ky] : T(1)) * accx;
+    }
+    accz = accz + (cnt[2] == 4 ? w[kz] : T(1)) * accy;
+  }
+  return accz;
+}
 
 template <typename T, int BS>
 __global__ void __launch_bounds__(RefSmem<T, BS>::NT, sizeof(T) == 4 ? 3 : 2)
@@ -625,30 +796,8 @@ k_refine(const T* src, T* dst, const int32_t* tasks, const int32_t* blist, const
     for (int k = 0; k < U; ++k) {
       if (gi[k] < 0) continue;
       if (off[k] < 0) {
-        // tensor DD-4 prediction from the even lattice (z outer, then y, then x)
         const int i = gi[k];
-        const int gx = i % NPP - 1, gy = (i / NPP) % NPP - 1, gz = i / (NPP * NPP) - 1;
-        const int p[3] = {gx, gy, gz};
-        const T w[4] = {T(-1) / T(16), T(9) / T(16), T(9) / T(16), T(-1) / T(16)};
-        const int o4[4] = {-3, -1, 1, 3};
-        int cnt[3];
-        for (int a = 0; a < 3; ++a) cnt[a] = (p[a] & 1) ? 4 : 1;
-        T accz = T(0);
-        for (int kz = 0; kz < cnt[2]; ++kz) {
-          const int zz = ((cnt[2] == 4 ? gz + o4[kz] : gz) + 4) >> 1;
-          T accy = T(0);
-          for (int ky = 0; ky < cnt[1]; ++ky) {
-            const int yy = ((cnt[1] == 4 ? gy + o4[ky] : gy) + 4) >> 1;
-            T accx = T(0);
-            for (int kx = 0; kx < cnt[0]; ++kx) {
-              const int xx = ((cnt[0] == 4 ? gx + o4[kx] : gx) + 4) >> 1;
-              accx = accx + (cnt[0] == 4 ? w[kx] : T(1)) * eq[(zz * NEV + yy) * NEV + xx];
-            }
-            accy = accy + (cnt[1] == 4 ? w[ky] : T(1)) * accx;
-          }
-          accz = accz + (cnt[2] == 4 ? w[kz] : T(1)) * accy;
-        }
-        v[k] = accz;
+        v[k] = predict_from_even<T, NEV>(eq, i % NPP - 1, (i / NPP) % NPP - 1, i / (NPP * NPP) - 1);
       }
       pp[gi[k]] = v[k];
     }
@@ -691,15 +840,110 @@ k_refine(const T* src, T* dst, const int32_t* tasks, const int32_t* blist, const
   }
 }
 
+// Refinement of Bs = 33 blocks: the parent with its shell, 35^3 values of one component, does
+// not fit beside the passes' buffers, so a CTA predicts one child of one component from the
+// parent samples that child uses (local [o, o + M/2 + 2]^3, o = -1 or M/2 - 1 per axis): the
+// parent's points where it has them, a shell point from the finest leaf holding it, else the
+// tensor DD-4 prediction from the even lattice.  Same values as k_refine (the same expressions
+// in the same order).  One CTA per (parent, component, child).
+template <typename T, int BS>
+struct RefBigSmem {
+  static constexpr int NT = 1024;
+  static constexpr int M = BS - 1;
+  static constexpr int NEV = M / 2 + 5;             // even lattice per axis: -4..M+4
+  static constexpr int NP = M / 2 + 3;              // samples per axis one child uses
+  static constexpr int SUB = NP * NP * NP;
+  static constexpr int EQ = (NEV * NEV * NEV > NP * NP * BS) ? NEV * NEV * NEV : NP * NP * BS;
+  static constexpr int QY = NP * BS * BS;
+  static constexpr size_t bytes = (size_t)(SUB + EQ + QY) * sizeof(T) + kNbhStride * sizeof(int);
+};
+
+template <typename T, int BS>
+__global__ void __launch_bounds__(RefBigSmem<T, BS>::NT, 1)
+k_refine_child(const T* src, T* dst, const int32_t* tasks, const int32_t* blist, const int32_t* nbh_all) {
+  using L = Lay<T, BS>;
+  using S = RefBigSmem<T, BS>;
+  constexpr int M = L::M, NEV = S::NEV, NP = S::NP, NT = S::NT;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sub = reinterpret_cast<T*>(smem_raw);
+  T* eq = sub + S::SUB;                         // even lattice ev, later the x-pass qx
+  T* qy = eq + S::EQ;
+  int* nbh = reinterpret_cast<int*>(qy + S::QY);
+  const int tid = threadIdx.x;
+  const int32_t* tk = tasks + (size_t)(blockIdx.x >> 5) * 9;
+  const int f = (blockIdx.x >> 3) & 3, c = blockIdx.x & 7;
+  const int prank = tk[0];
+  const int pslot = blist[prank];
+  const int o[3] = {(c & 1) * (M / 2) - 1, ((c >> 1) & 1) * (M / 2) - 1, ((c >> 2) & 1) * (M / 2) - 1};
+  const T NaN = T(__longlong_as_double(0x7ff8000000000000ll));
+  const T* pb = src + (size_t)pslot * L::BLK + (size_t)f * L::FS;
+  for (int i = tid; i < kNbhStride; i += NT) nbh[i] = nbh_all[(size_t)prank * kNbhStride + i];
+  __syncthreads();
+  const int coarser = __syncthreads_or(tid < 27 && tid != 13 && (nbh[kNbhType + tid] & 15) == kTypeCoarser);
+  if (coarser) {
+    for (int i = tid; i < NEV * NEV * NEV; i += NT) {
+      const int ex = 2 * (i % NEV) - 4, ey = 2 * ((i / NEV) % NEV) - 4, ez = 2 * (i / (NEV * NEV)) - 4;
+      long long off;
+      if (ex >= 0 && ex <= M && ey >= 0 && ey <= M && ez >= 0 && ez <= M)
+        off = (long long)pslot * L::BLK + (long long)f * L::FS + L::idx(ex, ey, ez);
+      else
+        off = direct_offset<T, BS>(nbh, ex, ey, ez, f);
+      eq[i] = off >= 0 ? src[off] : NaN;
+    }
+    __syncthreads();
+  }
+  for (int i = tid; i < S::SUB; i += NT) {
+    const int gx = o[0] + i % NP, gy = o[1] + (i / NP) % NP, gz = o[2] + i / (NP * NP);
+    T v;
+    if (gx >= 0 && gx <= M && gy >= 0 && gy <= M && gz >= 0 && gz <= M) {
+      v = pb[L::idx(gx, gy, gz)];
+    } else {
+      const long long off = direct_offset<T, BS>(nbh, gx, gy, gz, f);
+      v = off >= 0 ? src[off] : predict_from_even<T, NEV>(eq, gx, gy, gz);
+    }
+    sub[i] = v;
+  }
+  __syncthreads();
+  T* qx = eq;
+  if (tid < NP * NP) {                          // x-pass: line (yy, zz)
+    const int yy = tid % NP, zz = tid / NP;
+    T cv[NP];
+#pragma unroll
+    for (int k = 0; k < NP; ++k) cv[k] = sub[(zz * NP + yy) * NP + k];
+#pragma unroll
+    for (int i = 0; i < BS; ++i) qx[(zz * NP + yy) * BS + i] = dd4_line<T, BS>(cv, i);
+  }
+  __syncthreads();
+  if (tid < NP * BS) {                          // y-pass: line (ix, zz)
+    const int ix = tid % BS, zz = tid / BS;
+    T cv[NP];
+#pragma unroll
+    for (int k = 0; k < NP; ++k) cv[k] = qx[(zz * NP + k) * BS + ix];
+#pragma unroll
+    for (int i = 0; i < BS; ++i) qy[(zz * BS + i) * BS + ix] = dd4_line<T, BS>(cv, i);
+  }
+  __syncthreads();
+  T* out = dst + (size_t)tk[1 + c] * L::BLK + (size_t)f * L::FS;
+  for (int col = tid; col < BS * BS; col += NT) {   // z-pass: column (x, y), written to the child
+    const int x = col % BS, y = col / BS;
+    T cv[NP];
+#pragma unroll
+    for (int k = 0; k < NP; ++k) cv[k] = qy[(k * BS + y) * BS + x];
+#pragma unroll
+    for (int z = 0; z < BS; ++z) out[L::idx(x, y, z)] = dd4_line<T, BS>(cv, z);
+  }
+}
+
 // ---- (7) coarsening: parent by decimation of its 8 children (Sec. 3.1 R, Sec. 3.5 step 3) ----
 // task = [new parent slot, old child slots 0..7]; dst is a register other than src (a parent
 // may take a slot freed by a child that another CTA is still reading): the parents are copied
 // into the state afterwards.
-// One CTA per (task, component); a thread owns one z-column of the parent and has all its loads
-// in flight before it stores.
+// One CTA per (task, component); a thread owns one z-column of the parent (two for Bs = 33)
+// and has all its loads in flight before it stores.
 template <int BS>
 struct ColCfg {
-  static constexpr int NT = ((BS * BS + 31) / 32) * 32;
+  // a thread per (x, y) column; above 1024 columns (Bs = 33) a thread takes two
+  static constexpr int NT = BS * BS <= 1024 ? ((BS * BS + 31) / 32) * 32 : ((BS * BS / 2 + 32) / 32) * 32;
 };
 
 template <typename T, int BS>
@@ -708,19 +952,19 @@ __global__ void __launch_bounds__(ColCfg<BS>::NT) k_coarsen(const T* src, T* dst
   constexpr int M = L::M;
   const int32_t* tk = tasks + (size_t)(blockIdx.x >> 2) * 9;
   const int f = blockIdx.x & 3;
-  const int tid = threadIdx.x;
-  if (tid >= BS * BS) return;
-  const int x = tid % BS, y = tid / BS;
-  const int cx = x > M / 2, cy = y > M / 2;
-  const int lx = 2 * x - cx * M, ly = 2 * y - cy * M;
-  const T* c0 = src + (size_t)tk[1 + (cx | (cy << 1))] * L::BLK + (size_t)f * L::FS;       // cz = 0
-  const T* c1 = src + (size_t)tk[1 + (cx | (cy << 1) | 4)] * L::BLK + (size_t)f * L::FS;   // cz = 1
-  T v[BS];
+  for (int col = threadIdx.x; col < BS * BS; col += ColCfg<BS>::NT) {
+    const int x = col % BS, y = col / BS;
+    const int cx = x > M / 2, cy = y > M / 2;
+    const int lx = 2 * x - cx * M, ly = 2 * y - cy * M;
+    const T* c0 = src + (size_t)tk[1 + (cx | (cy << 1))] * L::BLK + (size_t)f * L::FS;       // cz = 0
+    const T* c1 = src + (size_t)tk[1 + (cx | (cy << 1) | 4)] * L::BLK + (size_t)f * L::FS;   // cz = 1
+    T v[BS];
 #pragma unroll
-  for (int z = 0; z < BS; ++z) v[z] = z <= M / 2 ? c0[L::idx(lx, ly, 2 * z)] : c1[L::idx(lx, ly, 2 * z - M)];
-  T* out = dst + (size_t)tk[0] * L::BLK + (size_t)f * L::FS;
+    for (int z = 0; z < BS; ++z) v[z] = z <= M / 2 ? c0[L::idx(lx, ly, 2 * z)] : c1[L::idx(lx, ly, 2 * z - M)];
+    T* out = dst + (size_t)tk[0] * L::BLK + (size_t)f * L::FS;
 #pragma unroll
-  for (int z = 0; z < BS; ++z) out[L::idx(x, y, z)] = v[z];
+    for (int z = 0; z < BS; ++z) out[L::idx(x, y, z)] = v[z];
+  }
 }
 
 // ---- (7b) CDF 4/4 coarsening (Sec. 3.2.1 lifted wavelet, Sec. 3.5 step 3) ------------------------
@@ -1111,65 +1355,12 @@ __global__ void __launch_bounds__(kNT) k_ic(T* reg, const int32_t* blist, const 
   }
 }
 
+// chi along the z-column (ix, iy) of one block (out: the block's mask component).
 template <typename T, int BS>
-__global__ void __launch_bounds__(ColCfg<BS>::NT) k_mask(T* chi, const int32_t* blist, const int32_t* ranks,
-                                                         const int4* binfo, const PhysK ph, const MaskK m) {
+__device__ __forceinline__ void mask_column(T* out, const int ix, const int iy, const int uniform, const int4 bi,
+                                            const PhysK& ph, const MaskK& m, const double h) {
   using L = Lay<T, BS>;
   constexpr int M = L::M;
-  const int rank = ranks ? ranks[blockIdx.x] : (int)blockIdx.x;
-  const int slot = blist[rank];
-  const int4 bi = binfo[rank];
-  const double h = ph.h[bi.x];
-  // A block that lies entirely farther than 40 delta from the sphere surface has tanh(d/delta)
-  // = +-1 exactly in double precision at all its points (1 - tanh(40) < 1e-34): chi is exactly
-  // 0 or 1 there and needs no transcendental.  Blocks on the periodic seam are evaluated fully.
-  // One thread decides (FP64), the block reads the answer.
-  __shared__ int s_uniform;
-  if (threadIdx.x == 0) {
-    int uniform = 0;
-    if (m.kind == 1) {
-      uniform = -1;
-      const double lo[3] = {(double)bi.y * M * h, (double)bi.z * M * h, (double)bi.w * M * h};
-      const double L[3] = {ph.nroot[0] * ph.root_len, ph.nroot[1] * ph.root_len, ph.nroot[2] * ph.root_len};
-      bool seam = false;
-      double dmin2 = 0.0, dmax2 = 0.0;
-      for (int a = 0; a < 3; ++a) {
-        const double hi = lo[a] + M * h;
-        if (hi >= L[a]) seam = true;
-        const double c = m.p[a];
-        const double near = c < lo[a] ? lo[a] - c : (c > hi ? c - hi : 0.0);
-        const double far = fmax(fabs(c - lo[a]), fabs(hi - c));
-        dmin2 += near * near;
-        dmax2 += far * far;
-      }
-      if (!seam) {
-        if (sqrt(dmin2) - m.p[3] > 40.0 * m.p[4]) uniform = 0;
-        else if (sqrt(dmax2) - m.p[3] < -40.0 * m.p[4]) uniform = 1;
-      }
-    } else if (m.kind == 2) {
-      // rigid box: outside the sphere of radius p[22] around the pivot by more than 40 delta
-      uniform = -1;
-      const double lo[3] = {(double)bi.y * M * h, (double)bi.z * M * h, (double)bi.w * M * h};
-      const double L[3] = {ph.nroot[0] * ph.root_len, ph.nroot[1] * ph.root_len, ph.nroot[2] * ph.root_len};
-      bool seam = false;
-      double dmin2 = 0.0;
-      for (int a = 0; a < 3; ++a) {
-        const double hi = lo[a] + M * h;
-        if (hi >= L[a]) seam = true;
-        const double c = m.p[9 + a];
-        const double near = c < lo[a] ? lo[a] - c : (c > hi ? c - hi : 0.0);
-        dmin2 += near * near;
-      }
-      if (!seam && sqrt(dmin2) - m.p[22] > 40.0 * m.p[18]) uniform = 0;
-    }
-    s_uniform = uniform;
-  }
-  __syncthreads();
-  const int uniform = s_uniform;
-  const int tid = threadIdx.x;
-  if (tid >= BS * BS) return;
-  const int ix = tid % BS, iy = tid / BS;
-  T* out = chi + (size_t)slot * L::FS;
   if (uniform >= 0) {
 #pragma unroll
     for (int iz = 0; iz < BS; ++iz) out[L::idx(ix, iy, iz)] = T(uniform);
@@ -1225,6 +1416,65 @@ __global__ void __launch_bounds__(ColCfg<BS>::NT) k_mask(T* chi, const int32_t* 
     else c = T(0.5) * (T(1) - ttanh(d / dl));
     out[L::idx(ix, iy, iz)] = c;
   }
+}
+
+template <typename T, int BS>
+__global__ void __launch_bounds__(ColCfg<BS>::NT) k_mask(T* chi, const int32_t* blist, const int32_t* ranks,
+                                                         const int4* binfo, const PhysK ph, const MaskK m) {
+  using L = Lay<T, BS>;
+  constexpr int M = L::M;
+  const int rank = ranks ? ranks[blockIdx.x] : (int)blockIdx.x;
+  const int slot = blist[rank];
+  const int4 bi = binfo[rank];
+  const double h = ph.h[bi.x];
+  // A block that lies entirely farther than 40 delta from the sphere surface has tanh(d/delta)
+  // = +-1 exactly in double precision at all its points (1 - tanh(40) < 1e-34): chi is exactly
+  // 0 or 1 there and needs no transcendental.  Blocks on the periodic seam are evaluated fully.
+  // One thread decides (FP64), the block reads the answer.
+  __shared__ int s_uniform;
+  if (threadIdx.x == 0) {
+    int uniform = 0;
+    if (m.kind == 1) {
+      uniform = -1;
+      const double lo[3] = {(double)bi.y * M * h, (double)bi.z * M * h, (double)bi.w * M * h};
+      const double L[3] = {ph.nroot[0] * ph.root_len, ph.nroot[1] * ph.root_len, ph.nroot[2] * ph.root_len};
+      bool seam = false;
+      double dmin2 = 0.0, dmax2 = 0.0;
+      for (int a = 0; a < 3; ++a) {
+        const double hi = lo[a] + M * h;
+        if (hi >= L[a]) seam = true;
+        const double c = m.p[a];
+        const double near = c < lo[a] ? lo[a] - c : (c > hi ? c - hi : 0.0);
+        const double far = fmax(fabs(c - lo[a]), fabs(hi - c));
+        dmin2 += near * near;
+        dmax2 += far * far;
+      }
+      if (!seam) {
+        if (sqrt(dmin2) - m.p[3] > 40.0 * m.p[4]) uniform = 0;
+        else if (sqrt(dmax2) - m.p[3] < -40.0 * m.p[4]) uniform = 1;
+      }
+    } else if (m.kind == 2) {
+      // rigid box: outside the sphere of radius p[22] around the pivot by more than 40 delta
+      uniform = -1;
+      const double lo[3] = {(double)bi.y * M * h, (double)bi.z * M * h, (double)bi.w * M * h};
+      const double L[3] = {ph.nroot[0] * ph.root_len, ph.nroot[1] * ph.root_len, ph.nroot[2] * ph.root_len};
+      bool seam = false;
+      double dmin2 = 0.0;
+      for (int a = 0; a < 3; ++a) {
+        const double hi = lo[a] + M * h;
+        if (hi >= L[a]) seam = true;
+        const double c = m.p[9 + a];
+        const double near = c < lo[a] ? lo[a] - c : (c > hi ? c - hi : 0.0);
+        dmin2 += near * near;
+      }
+      if (!seam && sqrt(dmin2) - m.p[22] > 40.0 * m.p[18]) uniform = 0;
+    }
+    s_uniform = uniform;
+  }
+  __syncthreads();
+  const int uniform = s_uniform;
+  for (int col = threadIdx.x; col < BS * BS; col += ColCfg<BS>::NT)
+    mask_column<T, BS>(chi + (size_t)slot * L::FS, col % BS, col / BS, uniform, bi, ph, m, h);
 }
 
 // ---- (9) diagnostics: raw per-block sums over the half-open points [0, M-1]^3 -----------------
@@ -1363,18 +1613,21 @@ LayoutInfo layout_info(int precision, int Bs) {
   li.PP = Lay<T, B>::PP; li.FS = Lay<T, B>::FS; li.BLK = Lay<T, B>::BLK; li.NE = Lay<T, B>::NE;  \
   li.NE3 = Lay<T, B>::NE3; li.EBLK = Lay<T, B>::EBLK;
   if (precision == 64) {
-    if (Bs == 17) { ACM_FILL(double, 17) } else { ACM_FILL(double, 9) }
+    if (Bs == 33) { ACM_FILL(double, 33) } else if (Bs == 17) { ACM_FILL(double, 17) } else { ACM_FILL(double, 9) }
   } else {
-    if (Bs == 17) { ACM_FILL(float, 17) } else { ACM_FILL(float, 9) }
+    if (Bs == 33) { ACM_FILL(float, 33) } else if (Bs == 17) { ACM_FILL(float, 17) } else { ACM_FILL(float, 9) }
   }
 #undef ACM_FILL
   return li;
 }
 
-#define ACM_BS_DISPATCH(Bs, KERNEL, ...)                 \
-  do {                                                   \
-    if ((Bs) == 17) { KERNEL<T, 17> __VA_ARGS__; }       \
-    else { KERNEL<T, 9> __VA_ARGS__; }                   \
+// Bs = 33 blocks are FP32 only (the forest refuses FP64 with them).
+#define ACM_BS_DISPATCH(Bs, KERNEL, ...)                                      \
+  do {                                                                        \
+    if ((Bs) == 33) {                                                         \
+      if constexpr (sizeof(T) == 4) { KERNEL<T, 33> __VA_ARGS__; }            \
+    } else if ((Bs) == 17) { KERNEL<T, 17> __VA_ARGS__; }                     \
+    else { KERNEL<T, 9> __VA_ARGS__; }                                        \
   } while (0)
 
 template <typename T>
@@ -1398,10 +1651,19 @@ template <typename T>
 void launch_coarse_slabs(int Bs, const T* reg, T* slab, const int4* tasks, const int32_t* ntasks, int64_t max_tasks,
                          const int32_t* nbh, uint32_t* offc, int use_cache, int ctas_per_sm, cudaStream_t st) {
   if (max_tasks <= 0) return;
-  if (Bs == 17) launch_coarse_slabs_bs<T, 17>(reg, slab, tasks, ntasks, max_tasks, nbh, offc, use_cache, ctas_per_sm, st);
-  else launch_coarse_slabs_bs<T, 9>(reg, slab, tasks, ntasks, max_tasks, nbh, offc, use_cache, ctas_per_sm, st);
+  if (Bs == 33) {
+    // one CTA per SM is resident (166 KB of shared memory)
+    if constexpr (sizeof(T) == 4)
+      launch_coarse_slabs_bs<T, 33>(reg, slab, tasks, ntasks, max_tasks, nbh, offc, use_cache, 1, st);
+  } else if (Bs == 17) {
+    launch_coarse_slabs_bs<T, 17>(reg, slab, tasks, ntasks, max_tasks, nbh, offc, use_cache, ctas_per_sm, st);
+  } else {
+    launch_coarse_slabs_bs<T, 9>(reg, slab, tasks, ntasks, max_tasks, nbh, offc, use_cache, ctas_per_sm, st);
+  }
 }
-size_t slab_offset_words(int Bs) { return Bs == 17 ? SlabSmem<float, 17>::NOFF : SlabSmem<float, 9>::NOFF; }
+size_t slab_offset_words(int Bs) {
+  return Bs == 33 ? SlabSmem<float, 33>::NOFF : (Bs == 17 ? SlabSmem<float, 17>::NOFF : SlabSmem<float, 9>::NOFF);
+}
 template <typename T>
 void launch_sync_ext(int Bs, const T* reg, T* out, int g, const int32_t* list, int64_t n, const int32_t* nbh, int by_rank, cudaStream_t st) {
   if (n <= 0) return;
@@ -1420,8 +1682,18 @@ void launch_details(int Bs, const T* reg, const T* chi, const int32_t* blist, co
                     const int32_t* nbh, int64_t n, const unsigned long long* norm_bits, double* ind,
                     double* chirange, cudaStream_t st) {
   if (n <= 0) return;
-  if (Bs == 17) launch_details_bs<T, 17>(reg, chi, blist, ranks, nbh, n, norm_bits, ind, chirange, st);
-  else launch_details_bs<T, 9>(reg, chi, blist, ranks, nbh, n, norm_bits, ind, chirange, st);
+  if (Bs == 33) {
+    if constexpr (sizeof(T) == 4) {
+      static std::atomic<unsigned long long> opted{0};
+      smem_opt_in(k_details_big<T, 33>, DetBigSmem<T, 33>::bytes, opted);
+      k_details_big<T, 33><<<grid1(n), DetBigSmem<T, 33>::NT, DetBigSmem<T, 33>::bytes, st>>>(
+          reg, chi, blist, ranks, nbh, norm_bits, ind, chirange);
+    }
+  } else if (Bs == 17) {
+    launch_details_bs<T, 17>(reg, chi, blist, ranks, nbh, n, norm_bits, ind, chirange, st);
+  } else {
+    launch_details_bs<T, 9>(reg, chi, blist, ranks, nbh, n, norm_bits, ind, chirange, st);
+  }
 }
 template <typename T>
 void launch_maxnorm(int Bs, const T* reg, const int32_t* blist, int64_t n, unsigned long long* out, cudaStream_t st) {
@@ -1439,14 +1711,29 @@ template <typename T>
 void launch_refine(int Bs, const T* src, T* dst, const int32_t* tasks, int64_t n, const int32_t* blist,
                    const int32_t* nbh, cudaStream_t st) {
   if (n <= 0) return;
-  if (Bs == 17) launch_refine_bs<T, 17>(src, dst, tasks, n, blist, nbh, st);
-  else launch_refine_bs<T, 9>(src, dst, tasks, n, blist, nbh, st);
+  if (Bs == 33) {
+    if constexpr (sizeof(T) == 4) {
+      static std::atomic<unsigned long long> opted{0};
+      smem_opt_in(k_refine_child<T, 33>, RefBigSmem<T, 33>::bytes, opted);
+      k_refine_child<T, 33><<<grid1(32 * n), RefBigSmem<T, 33>::NT, RefBigSmem<T, 33>::bytes, st>>>(src, dst, tasks,
+                                                                                                    blist, nbh);
+    }
+  } else if (Bs == 17) {
+    launch_refine_bs<T, 17>(src, dst, tasks, n, blist, nbh, st);
+  } else {
+    launch_refine_bs<T, 9>(src, dst, tasks, n, blist, nbh, st);
+  }
 }
 template <typename T>
 void launch_coarsen(int Bs, const T* src, T* dst, const int32_t* tasks, int64_t n, cudaStream_t st) {
   if (n <= 0) return;
-  if (Bs == 17) k_coarsen<T, 17><<<grid1(4 * n), ColCfg<17>::NT, 0, st>>>(src, dst, tasks);
-  else k_coarsen<T, 9><<<grid1(4 * n), ColCfg<9>::NT, 0, st>>>(src, dst, tasks);
+  if (Bs == 33) {
+    if constexpr (sizeof(T) == 4) k_coarsen<T, 33><<<grid1(4 * n), ColCfg<33>::NT, 0, st>>>(src, dst, tasks);
+  } else if (Bs == 17) {
+    k_coarsen<T, 17><<<grid1(4 * n), ColCfg<17>::NT, 0, st>>>(src, dst, tasks);
+  } else {
+    k_coarsen<T, 9><<<grid1(4 * n), ColCfg<9>::NT, 0, st>>>(src, dst, tasks);
+  }
 }
 template <typename T, int BS>
 void launch_coarsen44_bs(const T* src, T* dst, const int32_t* tasks, int64_t n, const int32_t* nbh, cudaStream_t st) {
@@ -1456,7 +1743,7 @@ void launch_coarsen44_bs(const T* src, T* dst, const int32_t* tasks, int64_t n, 
 }
 template <typename T>
 void launch_coarsen44(int Bs, const T* src, T* dst, const int32_t* tasks, int64_t n, const int32_t* nbh, cudaStream_t st) {
-  if (n <= 0) return;
+  if (n <= 0 || Bs == 33) return;     // CDF 4/4 merging is built for Bs 9 and 17 (refused above)
   if (Bs == 17) launch_coarsen44_bs<T, 17>(src, dst, tasks, n, nbh, st);
   else launch_coarsen44_bs<T, 9>(src, dst, tasks, n, nbh, st);
 }
@@ -1475,8 +1762,13 @@ template <typename T>
 void launch_mask(int Bs, T* chi, const int32_t* blist, const int32_t* ranks, int64_t n, const int4* binfo,
                  const PhysK& p, const MaskK& m, cudaStream_t st) {
   if (n <= 0) return;
-  if (Bs == 17) k_mask<T, 17><<<grid1(n), ColCfg<17>::NT, 0, st>>>(chi, blist, ranks, binfo, p, m);
-  else k_mask<T, 9><<<grid1(n), ColCfg<9>::NT, 0, st>>>(chi, blist, ranks, binfo, p, m);
+  if (Bs == 33) {
+    if constexpr (sizeof(T) == 4) k_mask<T, 33><<<grid1(n), ColCfg<33>::NT, 0, st>>>(chi, blist, ranks, binfo, p, m);
+  } else if (Bs == 17) {
+    k_mask<T, 17><<<grid1(n), ColCfg<17>::NT, 0, st>>>(chi, blist, ranks, binfo, p, m);
+  } else {
+    k_mask<T, 9><<<grid1(n), ColCfg<9>::NT, 0, st>>>(chi, blist, ranks, binfo, p, m);
+  }
 }
 template <typename T>
 void launch_solid_source(int Bs, T* out, T* acc, const T* chi, const int32_t* blist, const int4* binfo, int64_t n,

@@ -182,10 +182,12 @@ struct Carve {
 
 bool valid_grid(const acm_grid_params* g) {
   if (!g) return false;
-  if (g->Bs != 9 && g->Bs != 17) return false;
+  if (g->Bs != 9 && g->Bs != 17 && g->Bs != 33) return false;
   if (g->precision != 32 && g->precision != 64) return false;
   if (g->g < 1 || g->g > 4) return false;
   if (g->wavelet != 0 && g->wavelet != 40 && g->wavelet != 44) return false;
+  // Bs = 33 blocks: FP32 fields and the CDF 4/0 merge (the kernels built for that size)
+  if (g->Bs == 33 && (g->precision != 32 || g->wavelet == 44)) return false;
   if (g->Jmin < 0 || g->Jmax < g->Jmin || g->Jmax > 18) return false;
   if (g->max_blocks < 1 || g->max_blocks > (int64_t)1 << 30) return false;
   if (!(g->root_len > 0)) return false;
@@ -1079,6 +1081,7 @@ acm_status autotune(acm_forest* f, int* fw_ctas, int* slab_ctas) {
     best = 1e30f;
     int best_v = f->stage_variant;
     for (int v : {acm::kStagePair, acm::kStagePoint, acm::kStagePointTMA}) {
+      if (f->gp.Bs == 33 && v != acm::kStagePoint) continue;   // the one form for 33^3 blocks
       float ms = 0.f;
       acm_status s = time_launches(f, [&]() {
         acm::launch_stage<T>(2, f->gp.Bs, a, t, f->phk, f->d_err, f->st, v);
@@ -1363,6 +1366,7 @@ acm_status adjoint_sweep(acm_forest* f, int nsteps, double dt, int c, double wE,
 acm_status adjoint_sphere(acm_forest* f, int nsteps, double dt, int c, double wE, void* ws, size_t ws_bytes,
                           double* J_out, double* dtheta, void* dU0, int64_t n_elems, int on_device,
                           const void* lamN = nullptr) {
+  if (f->gp.Bs == 33) return fail(f, ACM_EINVAL, "the adjoint kernels are built for Bs 9 and 17");
   const double t0 = f->time;
   bool saved = false;
   const acm_status s = DISPATCH(f, adjoint_sweep, f, nsteps, dt, c, wE, ws, ws_bytes, J_out, dtheta, dU0, n_elems,
@@ -1627,7 +1631,7 @@ struct BatchPersistent {
     acm_forest* f0 = fs[0];
     for (int i = 0; i < n; ++i) {
       const acm_forest* g = fs[i];
-      if (g->gp.precision != f0->gp.precision || g->gp.Bs != f0->gp.Bs || !g->st ||
+      if (g->gp.precision != f0->gp.precision || g->gp.Bs != f0->gp.Bs || g->gp.Bs == 33 || !g->st ||
           std::memcmp(&g->phk, &f0->phk, sizeof(acm::PhysK)) != 0)
         return ACM_EINVAL;
       nwork += (int64_t)g->order.size();
@@ -1942,7 +1946,7 @@ acm_status acm_get_tuning(const acm_forest* f, acm_tuning* out) {
   if (!f || !out) return ACM_EINVAL;
   out->fw_ctas_per_sm = f->tune_fw_ctas;
   out->slab_ctas_per_sm = f->tune_slab_ctas;
-  out->stage_variant = f->gp.precision == 64 ? ACM_STAGE_POINT
+  out->stage_variant = f->gp.precision == 64 || f->gp.Bs == 33 ? ACM_STAGE_POINT
                        : (f->stage_variant == acm::kStagePair ? ACM_STAGE_PAIR
                           : (f->stage_variant == acm::kStagePoint ? ACM_STAGE_POINT : ACM_STAGE_POINT_TMA));
   out->stage_ms[ACM_STAGE_PAIR] = f->tune_stage_ms[acm::kStagePair];

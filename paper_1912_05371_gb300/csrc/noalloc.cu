@@ -100,7 +100,7 @@ __global__ void __launch_bounds__(1024) k_final_max(const double* partials, int 
 extern "C" acm_status acm_max_norms_noalloc(const void* fields, int64_t n_blocks, int Bs, int precision,
                                             double* norms_out, void* stream) {
   if (!fields || !norms_out || n_blocks < 1) return ACM_EINVAL;
-  if (Bs != 9 && Bs != 17) return ACM_EINVAL;
+  if (Bs != 9 && Bs != 17 && Bs != 33) return ACM_EINVAL;
   if (precision != 32 && precision != 64) return ACM_EINVAL;
   if (n_blocks > ACM_NOALLOC_MAX_BLOCKS) return ACM_ECAPACITY;
   int dev = 0;

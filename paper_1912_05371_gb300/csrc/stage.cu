@@ -11,7 +11,9 @@
 //   stage 4:                    out = acc + dt/6 K  (= U^{n+1})
 //   stage 0 (checks only):      acc = K
 //
-// Work layout: a thread owns one (x, y) pencil of the block and marches in z.  The z-stencil
+// Work layout: a thread owns one (x, y) pencil of the block and marches in z (a block of up to
+// 17^3 points is one CTA; a 33^3 block is split by rows over three CTAs, which read the rows
+// next to their own from the block like a halo).  The z-stencil
 // (7 points) lives in a register queue fed one plane ahead from global memory; the x/y
 // stencils read a shared-memory plane with a 3-point halo on each side, double-buffered, whose
 // halo is brought in by cp.async one plane ahead.  Halo points come straight from the
@@ -28,16 +30,25 @@ namespace {
 
 template <typename T, int BS>
 struct Cfg {
-  static constexpr int NT = ((BS * BS + 31) / 32) * 32;
-  static constexpr int H = BS + 6;       // plane rows: 3 halo rows each side
+  // rows (y) of the block one CTA updates: all of them up to Bs = 17; a CTA may have at most
+  // 1024 threads, so a Bs = 33 block goes to three CTAs of 11 rows
+  static constexpr int RY = BS <= 17 ? BS : 11;
+  static constexpr int NS = (BS + RY - 1) / RY;    // CTAs per block
+  static constexpr int NT = ((BS * RY + 31) / 32) * 32;
+  static constexpr int H = RY + 6;       // plane rows: 3 halo rows each side
   // row stride: a warp covers consecutive pencils of about two rows; with a stride congruent
   // to BS modulo the bank count (32 words for FP32) the second row continues on the next
-  // banks and the plane is read without bank conflicts
-  static constexpr int W = sizeof(T) == 4 ? BS + 32 : BS + 6;
+  // banks and the plane is read without bank conflicts (Bs = 33 keeps the narrow stride: a
+  // warp is one row there, and the wide one would not fit the static shared memory)
+  static constexpr int W = sizeof(T) == 4 && BS <= 17 ? BS + 32 : BS + 6;
   static constexpr int PW = H * W;
-  static constexpr int NH = 48 * BS;     // x/y halo values per plane: 4 comp x 4 faces x 3 x BS
+  // x/y halo values per plane and component: x faces 2 x 3 x RY, y faces 2 x 3 x BS
+  static constexpr int NHC = 6 * (RY + BS);
+  static constexpr int NH = 4 * NHC;
   static constexpr int HPT = (NH + NT - 1) / NT;   // halo values per thread
+  static constexpr int MINB = sizeof(T) == 4 ? (NT <= 352 ? 3 : 2) : 1;   // CTAs per SM
   static_assert(4 * PW < 0x8000, "plane buffer offsets must fit 15 bits");
+  static_assert(NS == 1 || sizeof(T) == 4, "row-split blocks are FP32 only");
 };
 
 
@@ -52,13 +63,16 @@ __host__ __device__ constexpr int staged_planes(bool mask) {
 // two-slot shared-memory ring by 1D bulk copies (one thread issues them after the plane
 // barrier of iteration z, completion on an mbarrier per slot), instead of per-thread loads at
 // the point of use.
-// The update of one block (rank `rank` of the topology tp); a: the arrays, kc: the constants.
+// The update of one block (rank `rank` of the topology tp), rows part * RY .. of it; a: the
+// arrays, kc: the constants.
 template <typename T, int BS, int STAGE, bool TMA>
 __device__ __forceinline__ void stage_block(const StagePtrs<T>& a, const StageConst<T>& kc, const TopoK& tp,
-                                            const PhysK& ph, int* err, const int rank) {
+                                            const PhysK& ph, int* err, const int rank, const int part) {
   using L = Lay<T, BS>;
   constexpr int M = L::M;
   constexpr int NT = Cfg<T, BS>::NT;
+  constexpr int RY = Cfg<T, BS>::RY, NHC = Cfg<T, BS>::NHC;
+  static_assert(!TMA || Cfg<T, BS>::NS == 1, "the bulk-copy ring stages whole planes");
   constexpr int W = Cfg<T, BS>::W;
   constexpr int PW = Cfg<T, BS>::PW;
   constexpr int HPT = Cfg<T, BS>::HPT;
@@ -91,8 +105,9 @@ __device__ __forceinline__ void stage_block(const StagePtrs<T>& a, const StageCo
     c_acc = T(a.coefp[2 * (STAGE - 1)]);
     c_out = T(a.coefp[2 * (STAGE - 1) + 1]);
   }
-  const bool act = tid < BS * BS;
-  const int x = act ? tid % BS : 0, y = act ? tid / BS : 0;
+  const int y0 = part * RY, ny = BS - y0 < RY ? BS - y0 : RY;   // this CTA's rows
+  const bool act = tid < BS * ny;
+  const int x = act ? tid % BS : 0, y = y0 + (act ? tid / BS : 0);
   (void)err;   // this kernel has no waits that can expire
   const T* __restrict__ inb = a.in + (size_t)slot * L::BLK;
   const size_t bo = (size_t)slot * L::BLK;
@@ -107,27 +122,45 @@ __device__ __forceinline__ void stage_block(const StagePtrs<T>& a, const StageCo
   // (z <= M/2 ? lo : hi) + z * hz from the state (or from the slab buffer, flag bit 15) and
   // lands at dst of the plane buffer: hzd = hz << 16 | slab << 15 | dst.  The offsets are
   // element indices (32-bit: pool and slab sizes are checked at forest creation); hi differs
-  // from lo for the upper child of a finer face.  Thread tid owns entries tid + k NT.
+  // from lo for the upper child of a finer face.  Thread tid owns entries tid + k NT.  A CTA
+  // holding part of the rows reads the rows beyond its own from the block itself, and its
+  // x-face entries past its last row are unused (hzd = 0; every used dst is at least 3).
 #pragma unroll
   for (int k = 0; k < HPT; ++k) {
     const int i = tid + k * NT;
     if (i < NH) {
-      const int g = i / (3 * BS), el = i % (3 * BS);
-      const int F = g & 3, f = g >> 2;
-      int l, t;
+      const int f = i / NHC;
+      int el = i % NHC, F, l, t;
       // x-faces take the 3 layers of a row as consecutive elements (one sector), y-faces a row
-      if (F < 2) { l = el % 3 + 1; t = el / 3; }
-      else { t = el % BS; l = el / BS + 1; }
-      int hx, hy;
-      if (F == 0) { hx = -l; hy = t; }
-      else if (F == 1) { hx = M + l; hy = t; }
+      if (el < 6 * RY) {
+        F = el / (3 * RY);
+        el %= 3 * RY;
+        l = el % 3 + 1;
+        t = y0 + el / 3;
+      } else {
+        el -= 6 * RY;
+        F = 2 + el / (3 * BS);
+        el %= 3 * BS;
+        t = el % BS;
+        l = el / BS + 1;
+      }
+      int hx, hy;                                   // plane coordinates, rows from y0
+      if (F == 0) { hx = -l; hy = t - y0; }
+      else if (F == 1) { hx = M + l; hy = t - y0; }
       else if (F == 2) { hx = t; hy = -l; }
-      else { hx = t; hy = M + l; }
+      else { hx = t; hy = ny - 1 + l; }
       const unsigned dst = (unsigned)(f * PW + (hy + 3) * W + hx + 3);
       const int ty = ftype[F];
       const bool plus = F & 1;
       const int ax = F >> 1;
-      if (ty == kTypeCoarser) {
+      if (F < 2 && t >= y0 + ny) {
+        hlo[i] = 0; hhi[i] = 0; hzd[i] = 0;
+      } else if ((F == 2 && y0 > 0) || (F == 3 && y0 + ny - 1 < M)) {
+        // a row of this block held by the CTA next to this one
+        const int yy = F == 2 ? y0 - l : y0 + ny - 1 + l;
+        const unsigned o = (unsigned)(bo + (size_t)f * L::FS + L::idx(t, yy, 0));
+        hlo[i] = o; hhi[i] = o; hzd[i] = ((unsigned)L::PP << 16) | dst;
+      } else if (ty == kTypeCoarser) {
         const unsigned o = (unsigned)((((size_t)fs[F][0] * 4 + f) * 3 + (l - 1)) * BS * BS + t);
         hlo[i] = o; hhi[i] = o; hzd[i] = ((unsigned)BS << 16) | 0x8000u | dst;
       } else if (ty == kTypeLeaf) {
@@ -155,6 +188,7 @@ __device__ __forceinline__ void stage_block(const StagePtrs<T>& a, const StageCo
       const int i = tid + k * NT;
       if (i < NH) {
         const unsigned zd = hzd[i];
+        if (Cfg<T, BS>::NS > 1 && zd == 0) continue;
         const unsigned off = (zz > M / 2 ? hhi[i] : hlo[i]) + (unsigned)zz * (zd >> 16);
         cp_async_elem(B + (zd & 0x7fffu), ((zd & 0x8000u) ? a.slab : a.in) + (size_t)off);
       }
@@ -197,18 +231,22 @@ __device__ __forceinline__ void stage_block(const StagePtrs<T>& a, const StageCo
   T nm[5] = {T(0), T(0), T(0), T(0), T(0)};   // stage 4: max |u|,|v|,|w|,|p|, |(u,v,w)|^2
   // L2 prefetch of the planes an iteration reads kPf iterations ahead: one thread per array
   // (stage input planes z + 4 + kPf, U, acc and chi planes z + kPf), one bulk request each
+  // (this CTA's rows of the plane, widened to 16-byte boundaries inside the padded plane)
   constexpr int kPf = 2;
-  constexpr unsigned kPlaneBytes = (unsigned)(L::PP * sizeof(T));
+  const int pf0 = Cfg<T, BS>::NS == 1 ? 0 : ((y0 * BS) & ~(L::VEC - 1));
+  const int pf1 = Cfg<T, BS>::NS == 1 ? L::PP : (((y0 + ny) * BS + L::VEC - 1) & ~(L::VEC - 1));
+  const unsigned kPlaneBytes = (unsigned)((pf1 - pf0) * sizeof(T));
   auto prefetch_planes = [&](int zin, int zo) {
+    const size_t pz = (size_t)zin * L::PP + pf0, po = (size_t)zo * L::PP + pf0;
     if (tid < 4) {
-      if (zin <= M) prefetch_l2(inb + (size_t)tid * L::FS + (size_t)zin * L::PP, kPlaneBytes);
+      if (zin <= M) prefetch_l2(inb + (size_t)tid * L::FS + pz, kPlaneBytes);
     } else if (tid < 8) {
       if ((STAGE == 2 || STAGE == 3) && zo <= M)
-        prefetch_l2(a.U + bo + (size_t)(tid - 4) * L::FS + (size_t)zo * L::PP, kPlaneBytes);
+        prefetch_l2(a.U + bo + (size_t)(tid - 4) * L::FS + po, kPlaneBytes);
     } else if (tid < 12) {
-      if (STAGE >= 2 && zo <= M) prefetch_l2(a.acc + bo + (size_t)(tid - 8) * L::FS + (size_t)zo * L::PP, kPlaneBytes);
+      if (STAGE >= 2 && zo <= M) prefetch_l2(a.acc + bo + (size_t)(tid - 8) * L::FS + po, kPlaneBytes);
     } else if (tid == 12) {
-      if (ph.mask && zo <= M) prefetch_l2(a.chi + (size_t)slot * L::FS + (size_t)zo * L::PP, kPlaneBytes);
+      if (ph.mask && zo <= M) prefetch_l2(a.chi + (size_t)slot * L::FS + po, kPlaneBytes);
     }
   };
   for (int k = 0; k < kPf; ++k) prefetch_planes(4 + k, k);
@@ -221,7 +259,7 @@ __device__ __forceinline__ void stage_block(const StagePtrs<T>& a, const StageCo
   for (int f = 0; f < 4; ++f) q[f][7] = T(0);
   issue_halos(0, &buf[0][0][0]);
 
-  const int ci = (y + 3) * W + x + 3;
+  const int ci = (y - y0 + 3) * W + x + 3;
   const T sp_xy = ph.sponge ? tmax(sp[0][x], sp[1][y]) : T(0);   // the sponge profile's x/y part
   for (int z = 0; z <= M; ++z) {
     T(*B)[PW] = buf[z & 1];
@@ -362,23 +400,24 @@ __device__ __forceinline__ void stage_block(const StagePtrs<T>& a, const StageCo
 }
 
 template <typename T, int BS, int STAGE, bool TMA = false>
-__global__ void __launch_bounds__(Cfg<T, BS>::NT, sizeof(T) == 4 ? 3 : 1)
+__global__ void __launch_bounds__(Cfg<T, BS>::NT, Cfg<T, BS>::MINB)
 k_stage(const StageK<T> a, const TopoK tp, const PhysK ph, int* err) {
   const StagePtrs<T> p{a.in, a.U, a.acc, a.out, a.chi, a.slab, a.norms, a.coefp};
-  stage_block<T, BS, STAGE, TMA>(p, a.kc, tp, ph, err, blockIdx.x);
+  constexpr int NS = Cfg<T, BS>::NS;
+  stage_block<T, BS, STAGE, TMA>(p, a.kc, tp, ph, err, blockIdx.x / NS, blockIdx.x % NS);
 }
 
 // Persistent form over several independent instances: the CTAs walk the work list of
 // (instance, rank) pairs, each instance with its own arrays and topology (desc) and the same
 // physics and constants; every block gets bitwise the update k_stage gives it.
 template <typename T, int BS, int STAGE>
-__global__ void __launch_bounds__(Cfg<T, BS>::NT, sizeof(T) == 4 ? 3 : 1)
+__global__ void __launch_bounds__(Cfg<T, BS>::NT, Cfg<T, BS>::MINB)
 k_stage_multi(const StageConst<T> kc, const PhysK ph, const StageInst<T>* desc, const int2* work, int nwork,
               int* err) {
   for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
     const int2 it = work[w];
     const StageInst<T> d = desc[it.x];
-    stage_block<T, BS, STAGE, false>(d.p, kc, d.tp, ph, err, it.y);
+    stage_block<T, BS, STAGE, false>(d.p, kc, d.tp, ph, err, it.y, 0);
     __syncthreads();                   // the next block reuses the shared arrays
   }
 }
@@ -407,7 +446,7 @@ __global__ void k_rk_coefs(const unsigned long long* maxbits, RkK p, double* rk)
 
 template <typename T, int BS, int STAGE, bool TMA>
 void launch_one(const StageK<T>& s, const TopoK& t, const PhysK& p, int* err, cudaStream_t st) {
-  const dim3 grid((unsigned)t.n), block(Cfg<T, BS>::NT);
+  const dim3 grid((unsigned)(t.n * Cfg<T, BS>::NS)), block(Cfg<T, BS>::NT);
   const size_t dyn = TMA ? (size_t)2 * staged_planes<STAGE>(p.mask != 0) * Lay<T, BS>::PP * sizeof(T) : 0;
   if (TMA) {
     // the ring comes on top of the kernel's static shared memory: opt in to its largest size
@@ -451,7 +490,7 @@ StageConst<T> stage_constants(const PhysK& p, double c_acc, double c_out) {
 template <typename T>
 void launch_stage_multi(int stage, int Bs, const PhysK& p, const StageInst<T>* desc, const int2* work, int64_t nwork,
                         int ctas, int* err, cudaStream_t st) {
-  if (nwork <= 0) return;
+  if (nwork <= 0 || Bs == 33) return;     // the persistent form takes whole blocks (Bs <= 17)
   const StageConst<T> kc = stage_constants<T>(p, 0.0, 0.0);
   const int nb = (int)std::min<int64_t>(nwork, (int64_t)std::max(ctas, 1));
   auto go = [&](auto kern, int nt) { kern<<<nb, nt, 0, st>>>(kc, p, desc, work, (int)nwork, err); };
@@ -478,7 +517,7 @@ template <typename T>
 void launch_stage(int stage, int Bs, const StageK<T>& s, const TopoK& t, const PhysK& p, int* err,
                   cudaStream_t st, int variant) {
   if constexpr (sizeof(T) == 4) {
-    if (variant == kStagePair) {
+    if (variant == kStagePair && Bs != 33) {
       launch_stage_pair(stage, Bs, s, t, p, st);
       return;
     }
@@ -486,6 +525,10 @@ void launch_stage(int stage, int Bs, const StageK<T>& s, const TopoK& t, const P
   StageK<T> a = s;
   a.kc = stage_constants<T>(p, s.c_acc, s.c_out);
   if constexpr (sizeof(T) == 4) {
+    if (Bs == 33) {              // the point form, rows split over three CTAs
+      launch_stage_bs<T, 33, false>(stage, a, t, p, err, st);
+      return;
+    }
     if (variant == kStagePointTMA) {
       if (Bs == 17) launch_stage_bs<T, 17, true>(stage, a, t, p, err, st);
       else launch_stage_bs<T, 9, true>(stage, a, t, p, err, st);
