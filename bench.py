@@ -501,33 +501,49 @@ def adjoint_at_scale(A, stream, nsteps=10, ckpt_every=5, w_energy=0.1):
             "dJ_dtheta": [float(v) for v in gth]}
 
 
-def fullscale_plate(A, stream, Jmax=8, max_blocks=120000, nsteps=20, adj_Jmax=6, adj_steps=10, adj_ckpt=5):
+def fullscale_plate(A, stream, Bs=33, Jmax=7, max_blocks=29000, nsteps=20, adj_Bs=33, adj_Jmax=7, adj_steps=10,
+                    adj_ckpt=5):
     """The full-scale case: the flapping plate (chord 1, span 3, thickness 0.05; stroke +-60 deg,
     pitch +-45 deg, frequency 1) in the periodic box 8^3, fluid at rest, nu = 1/2000, C_eta = 1e-4,
-    c0 = 30, C_eps = 1e-3, Bs = 17 at levels 2..Jmax, FP32: its initial grid by the paper's
+    c0 = 30, C_eps = 1e-3, blocks of Bs^3 at levels 2..Jmax, FP32 (the pool sized at max_blocks, at
+    Bs = 33 the most that 32-bit element offsets address): its initial grid by the paper's
     procedure, then nsteps adaptive steps (refine, RK4 at the CFL time step with the mask and solid
     velocity at every stage time, coarsen) timed by CUDA events, with the block count after every
     step and the device memory the forest holds.  Then the adjoint workload of this case -- the
     gradient of J = (1/N) sum [F_x + 0.1 E] with respect to the pitch amplitude on the frozen
-    initial grid of the levels 2..adj_Jmax twin (the level-Jmax grid's workspace would not fit
-    beside it) -- forward and adjoint time per step."""
+    initial grid of the case at levels 2..adj_Jmax with blocks of adj_Bs^3 (a forest of its own,
+    made after the adaptive run's pool is freed) -- forward and adjoint time per step."""
     import numpy as np
     import torch
     from paper_1912_05371_gb300 import workloads as W
 
-    def make(J, mb):
-        cfg = W.plate_fullscale(Jmax=J)
+    def make(J, mb, bs, leaves=None):
+        """The case's forest: its initial grid by the paper's procedure, or the given leaves
+        with the fluid at rest."""
+        cfg = W.plate_fullscale(Jmax=J, Bs=bs)
         pl = cfg["plate"]
         grid = dict(cfg["grid"], precision=32, max_blocks=mb, fd_scheme=1)
         phys = dict(cfg["phys"], eps=cfg["eps"], dealias=1, mask_range_thr=cfg["mask_thr"])
         f = A.Forest(grid, phys, stream=stream)
-        f.set_mask(A.ACM_MASK_PLATE, [pl["chord"], pl["span"], pl["thickness"], pl["phi_m"], pl["alpha_m"],
-                                      pl["freq"], *pl["root"], pl["delta"]])
-        n0 = f.init_grid(A.ACM_IC_UNIFORM, [0.0, 0.0, 0.0, 0.0])
+        params = [pl["chord"], pl["span"], pl["thickness"], pl["phi_m"], pl["alpha_m"], pl["freq"], *pl["root"],
+                  pl["delta"]]
+        f.set_mask(A.ACM_MASK_PLATE, params)
+        if leaves is None:
+            n0 = f.init_grid(A.ACM_IC_UNIFORM, [0.0, 0.0, 0.0, 0.0])
+        else:
+            f.set_leaves(leaves)
+            f.set_ic(A.ACM_IC_UNIFORM, [0.0, 0.0, 0.0, 0.0])
+            f.set_mask(A.ACM_MASK_PLATE, params)
+            n0 = len(leaves)
         return f, n0, grid
 
-    f, n0, grid = make(Jmax, max_blocks)
-    Bs3 = grid["Bs"] ** 3
+    def leaves_of(f):
+        t = f.topology()
+        return list(zip(t["level"].tolist(), t["gx"].tolist(), t["gy"].tolist(), t["gz"].tolist()))
+
+    f, n0, grid = make(Jmax, max_blocks, Bs)
+    leaves0 = leaves_of(f)
+    Bs3 = Bs ** 3
     gb = f.pool.numel() / 1e9
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(nsteps + 1)]
     nev, nst, t = [], [], 0.0
@@ -545,14 +561,24 @@ def fullscale_plate(A, stream, Jmax=8, max_blocks=120000, nsteps=20, adj_Jmax=6,
     f.close()
     del f
     torch.cuda.empty_cache()
-    out = {"workload": f"flapping plate in the box 8^3, Bs = 17, levels 2..{Jmax}, FP32, {nsteps} adaptive steps",
+    out = {"workload": f"flapping plate in the box 8^3, Bs = {Bs}, levels 2..{Jmax}, FP32, {nsteps} adaptive steps",
            "blocks_initial": n0, "n_blocks": {"evolved": nev, "after_coarsening": nst},
            "points_evolved_max": max(nev) * Bs3, "pool_gb": gb, "t_end": t, "ms_per_step": ms / nsteps,
            "value": 4 * Bs3 * sum(nev) / (ms * 1e-3), "unit": UNIT,
-           "note": "pool sized for max_blocks; 32-bit element offsets bound a register at 2^32 elements "
-                   "(206,000 blocks of 17^3)"}
-    # adjoint of the pitch amplitude on the twin's frozen initial grid
-    f, n0a, _ = make(adj_Jmax, 16384)
+           "note": f"pool sized for {max_blocks} blocks; 32-bit element offsets bound a register at 2^32 "
+                   "elements (29,700 blocks of 33^3, 206,000 of 17^3)"}
+    # adjoint of the pitch amplitude on a frozen initial grid, in a forest sized for it (the
+    # adjoint's workspace is some twelve registers of the pool's size)
+    Bs3 = adj_Bs ** 3
+    if (adj_Jmax, adj_Bs) == (Jmax, Bs):
+        leaves_a = leaves0
+    else:
+        g0, _, _ = make(adj_Jmax, max_blocks, adj_Bs)
+        leaves_a = leaves_of(g0)
+        g0.close()
+        del g0
+        torch.cuda.empty_cache()
+    f, n0a, _ = make(adj_Jmax, len(leaves_a) + 64, adj_Bs, leaves=leaves_a)
     dt = f.rk4_step(0.0)
     f.set_time(0.0)
     U0 = f.read_fields().copy()
@@ -573,7 +599,7 @@ def fullscale_plate(A, stream, Jmax=8, max_blocks=120000, nsteps=20, adj_Jmax=6,
     e1.synchronize()
     adj = e0.elapsed_time(e1)
     f.close()
-    out["adjoint"] = {"workload": f"the plate case at levels 2..{adj_Jmax}: {n0a} blocks of 17^3 frozen, FP32, "
+    out["adjoint"] = {"workload": f"the plate case at levels 2..{adj_Jmax}: {n0a} blocks of {adj_Bs}^3 frozen, FP32, "
                                  f"{adj_steps} steps of dt = {dt:.3e}, checkpoints every {adj_ckpt}",
                       "forward_ms_per_step": fwd / adj_steps, "adjoint_ms_per_step": adj / adj_steps,
                       "adjoint_over_forward": adj / fwd, "J": J, "dJ_dalpha_m": float(dJ),

@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libacm.so")
-SOURCES = ["adjoint_d17.cu", "adjoint_f17.cu", "adjoint_d9.cu", "adjoint_f9.cu", "adapt.cu", "stage.cu", "stage_pair.cu", "api.cu",
+SOURCES = ["adjoint_f33.cu", "adjoint_d17.cu", "adjoint_f17.cu", "adjoint_d9.cu", "adjoint_f9.cu", "adapt.cu", "stage.cu", "stage_pair.cu", "api.cu",
            "topo.cu", "adjoint.cu", "forest.cpp", "noalloc.cu", "peak.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -29,10 +29,16 @@ void put(const double* dense, T* r, const int32_t* blist, int64_t n, cudaStream_
 
 }  // namespace adj
 
-#define ACM_ADJ_BS(Bs, FN, ...)            \
-  do {                                     \
-    if ((Bs) == 17) adj::FN<T, 17>(__VA_ARGS__); \
-    else adj::FN<T, 9>(__VA_ARGS__);       \
+// Blocks of 33^3 are FP32 only (the forest refuses FP64 with them).
+#define ACM_ADJ_BS(Bs, FN, ...)                                       \
+  do {                                                                \
+    if ((Bs) == 33) {                                                 \
+      if constexpr (sizeof(T) == 4) adj::FN<T, 33>(__VA_ARGS__);      \
+    } else if ((Bs) == 17) {                                          \
+      adj::FN<T, 17>(__VA_ARGS__);                                    \
+    } else {                                                          \
+      adj::FN<T, 9>(__VA_ARGS__);                                     \
+    }                                                                 \
   } while (0)
 
 template <typename T>

@@ -134,19 +134,25 @@ __device__ __forceinline__ void block_add(double v, double* out) {
 // is read (nu': the next RK stage's nu), and the running sum of the stage nus is updated from nu'
 // in the same pass.  The own targets are stored with plain writes; the targets in the face halos
 // (k_adj_halo) go to other blocks' points through E^T afterwards.
+// A block of 33^3 points is split by rows over three CTAs (as the forward stage kernel): the
+// kappa rows of the CTA next to this one are sources inside the block, loaded like a halo.
 template <typename T, int BS>
 struct AdjCfg {
-  static constexpr int NT = ((BS * BS + 31) / 32) * 32;
-  static constexpr int H = BS + 6;
-  static constexpr int W = sizeof(T) == 4 ? BS + 32 : BS + 6;   // bank-conflict-free rows (FP32)
+  static constexpr int RY = BS <= 17 ? BS : 11;                  // rows (y) per CTA
+  static constexpr int NS = (BS + RY - 1) / RY;                  // CTAs per block
+  static constexpr int NT = ((BS * RY + 31) / 32) * 32;
+  static constexpr int H = RY + 6;
+  static constexpr int W = sizeof(T) == 4 && BS <= 17 ? BS + 32 : BS + 6;   // bank-conflict-free rows (FP32)
   static constexpr int PW = H * W;
   static constexpr int NC = 7;                                   // planes: u, v, w, kappa_0..3
-  static constexpr int NH = 36 * BS;                             // x/y halo values of u, v, w per plane
+  static constexpr int NHC = 6 * (RY + BS);                      // x/y halo values of one component
+  static constexpr int NH = 3 * NHC;                             // x/y halo values of u, v, w per plane
   static constexpr int HPT = (NH + NT - 1) / NT;
   static constexpr size_t BUF = (size_t)2 * NC * PW * sizeof(T);
   static constexpr size_t bytes = BUF + (size_t)NH * 12;
   static constexpr int MINB = sizeof(T) == 4 ? 2 : 1;
   static_assert(NC * PW < 0x8000, "plane buffer offsets must fit 15 bits");
+  static_assert(NS == 1 || sizeof(T) == 4, "row-split blocks are FP32 only");
 };
 
 template <typename T, int BS>
@@ -165,11 +171,13 @@ k_adj_stage(const AdjStageK<T> a, const TopoK tp, const PhysK ph, const MaskK m)
   __shared__ int fs[6][4];
   __shared__ T sp[3][BS];
 
+  constexpr int RY = C::RY, NHC = C::NHC;
   const int tid = threadIdx.x;
-  const int rank = blockIdx.x;
+  const int rank = blockIdx.x / C::NS, part = blockIdx.x % C::NS;
   const int slot = tp.blist[rank];
   const int4 bi = tp.binfo[rank];
   const int* nbh = tp.nbh + (size_t)rank * kNbhStride;
+  const int y0 = part * RY, ny = BS - y0 < RY ? BS - y0 : RY;    // this CTA's rows
   stage_faces(tid, nbh, tp.slabidx, rank, ftype, fs);
   stage_sponge<T, BS>(tid, ph, bi, sp);
   // the kappa planes' halos stay zero (sources outside the block weigh nothing)
@@ -181,8 +189,8 @@ k_adj_stage(const AdjStageK<T> a, const TopoK tp, const PhysK ph, const MaskK m)
   const T nu_ih2 = T(ph.nu / (12.0 * ph.h[bi.x] * ph.h[bi.x]));
   const T c0sq = T(ph.c0sq), inv_ceta = T(ph.inv_ceta), inv_csp = T(ph.inv_csp), cgam = T(ph.cgamma);
   const T c_lam = T(a.c_lam), c_nu = T(a.c_nu);
-  const bool act = tid < BS * BS;
-  const int x = act ? tid % BS : 0, y = act ? tid / BS : 0;
+  const bool act = tid < BS * ny;
+  const int x = act ? tid % BS : 0, y = y0 + (act ? tid / BS : 0);
   const size_t bo = (size_t)slot * L::BLK;
   const T* __restrict__ Yb = a.Y + bo;
 
@@ -201,26 +209,41 @@ k_adj_stage(const AdjStageK<T> a, const TopoK tp, const PhysK ph, const MaskK m)
 
   // x/y halo values of u, v, w of every plane as affine functions of z (the forward kernel's
   // table): entry i is read at (z <= M/2 ? lo : hi) + z * stride from Y (or the slab buffer,
-  // flag bit 15) and lands at dst: hzd = stride << 16 | slab << 15 | dst.
+  // flag bit 15) and lands at dst: hzd = stride << 16 | slab << 15 | dst (0: unused entry).
 #pragma unroll
   for (int k = 0; k < HPT; ++k) {
     const int i = tid + k * NT;
     if (i < NH) {
-      const int g = i / (3 * BS), el = i % (3 * BS);
-      const int F = g & 3, f = g >> 2;
-      int l, t;
-      if (F < 2) { l = el % 3 + 1; t = el / 3; }
-      else { t = el % BS; l = el / BS + 1; }
-      int hx, hy;
-      if (F == 0) { hx = -l; hy = t; }
-      else if (F == 1) { hx = M + l; hy = t; }
+      const int f = i / NHC;
+      int el = i % NHC, F, l, t;
+      if (el < 6 * RY) {
+        F = el / (3 * RY);
+        el %= 3 * RY;
+        l = el % 3 + 1;
+        t = y0 + el / 3;
+      } else {
+        el -= 6 * RY;
+        F = 2 + el / (3 * BS);
+        el %= 3 * BS;
+        t = el % BS;
+        l = el / BS + 1;
+      }
+      int hx, hy;                                   // plane coordinates, rows from y0
+      if (F == 0) { hx = -l; hy = t - y0; }
+      else if (F == 1) { hx = M + l; hy = t - y0; }
       else if (F == 2) { hx = t; hy = -l; }
-      else { hx = t; hy = M + l; }
+      else { hx = t; hy = ny - 1 + l; }
       const unsigned dst = (unsigned)(f * PW + (hy + 3) * W + hx + 3);
       const int ty = ftype[F];
       const bool plus = F & 1;
       const int ax = F >> 1;
-      if (ty == kTypeCoarser) {
+      if (F < 2 && t >= y0 + ny) {
+        hlo[i] = 0; hhi[i] = 0; hzd[i] = 0;
+      } else if ((F == 2 && y0 > 0) || (F == 3 && y0 + ny - 1 < M)) {
+        const int yy = F == 2 ? y0 - l : y0 + ny - 1 + l;       // a row of this block
+        const unsigned o = (unsigned)(bo + (size_t)f * L::FS + L::idx(t, yy, 0));
+        hlo[i] = o; hhi[i] = o; hzd[i] = ((unsigned)L::PP << 16) | dst;
+      } else if (ty == kTypeCoarser) {
         const unsigned o = (unsigned)((((size_t)fs[F][0] * 4 + f) * 3 + (l - 1)) * BS * BS + t);
         hlo[i] = o; hhi[i] = o; hzd[i] = ((unsigned)BS << 16) | 0x8000u | dst;
       } else if (ty == kTypeLeaf) {
@@ -246,11 +269,29 @@ k_adj_stage(const AdjStageK<T> a, const TopoK tp, const PhysK ph, const MaskK m)
       const int i = tid + k * NT;
       if (i < NH) {
         const unsigned zd = hzd[i];
+        if (C::NS > 1 && zd == 0) continue;
         const unsigned off = (zz > M / 2 ? hhi[i] : hlo[i]) + (unsigned)zz * (zd >> 16);
         cp_async_elem(B + (zd & 0x7fffu), ((zd & 0x8000u) ? a.slab : a.Y) + (size_t)off);
       }
     }
     cp_async_commit();
+  };
+  // kappa of plane zz in the rows the CTAs next to this one own (3 each side that has one)
+  auto fill_kappa_rows = [&](int zz, T* B) {
+    if constexpr (C::NS > 1) {
+      for (int j = tid; j < 2 * 3 * BS; j += NT) {
+        const int side = j / (3 * BS), l = (j / BS) % 3 + 1, t = j % BS;
+        if (side == 0 ? y0 == 0 : y0 + ny - 1 == M) continue;
+        const int yy = side == 0 ? y0 - l : y0 + ny - 1 + l, hy = side == 0 ? -l : ny - 1 + l;
+        const size_t o = bo + L::idx(t, yy, zz);
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+          T k = c_lam * a.lam[o + (size_t)f * L::FS];
+          if (a.nup) k += c_nu * a.nup[o + (size_t)f * L::FS];
+          B[(3 + f) * PW + (hy + 3) * W + t + 3] = k;
+        }
+      }
+    }
   };
 
   // register rings: qy[c][k] = u_c of plane z + k - 3, qk[f][k] = kappa_f of plane z + k - 3
@@ -266,10 +307,11 @@ k_adj_stage(const AdjStageK<T> a, const TopoK tp, const PhysK ph, const MaskK m)
   for (int f = 0; f < 4; ++f) qk[f][7] = T(0);
 #pragma unroll
   for (int c = 0; c < 3; ++c) qy[c][7] = T(0);
+  fill_kappa_rows(0, buf);
   __syncthreads();
   issue_halos(0, buf);
 
-  const int ci = (y + 3) * W + x + 3;
+  const int ci = (y - y0 + 3) * W + x + 3;
   const bool moving = m.kind == 2;
   double dth = 0.0;
   const double hd = ph.h[bi.x];
@@ -283,7 +325,10 @@ k_adj_stage(const AdjStageK<T> a, const TopoK tp, const PhysK ph, const MaskK m)
     }
     cp_async_wait_all();
     __syncthreads();
-    if (z < M) issue_halos(z + 1, buf + ((z + 1) & 1) * C::NC * PW);
+    if (z < M) {
+      issue_halos(z + 1, buf + ((z + 1) & 1) * C::NC * PW);
+      fill_kappa_rows(z + 1, buf + ((z + 1) & 1) * C::NC * PW);
+    }
     if (act) {
       if (z + 4 <= M + 3) {
 #pragma unroll
@@ -839,7 +884,7 @@ void stage(const AdjStageK<T>& a, const TopoK& t, const PhysK& ph, const MaskK& 
            cudaStream_t st) {
   static std::atomic<unsigned long long> opted{0};
   smem_opt_in_stage(k_adj_stage<T, BS>, AdjCfg<T, BS>::bytes, opted);
-  k_adj_stage<T, BS><<<g1(t.n), AdjCfg<T, BS>::NT, AdjCfg<T, BS>::bytes, st>>>(a, t, ph, m);
+  k_adj_stage<T, BS><<<g1(t.n * AdjCfg<T, BS>::NS), AdjCfg<T, BS>::NT, AdjCfg<T, BS>::bytes, st>>>(a, t, ph, m);
   k_adj_samelevel<T, BS><<<g1(t.n), kNA, 0, st>>>(a, t, ph, err);
   k_adj_halo<T, BS><<<g1(6 * t.n), kNA, 0, st>>>(a, t, ph, err);
   k_adj_fw_T<T, BS><<<fw_ctas(fw.max_tasks), kNA, 0, st>>>(a.nu, fw.tasks, fw.ntasks, t.nbh, t.blist);

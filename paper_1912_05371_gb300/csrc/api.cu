@@ -1366,7 +1366,6 @@ acm_status adjoint_sweep(acm_forest* f, int nsteps, double dt, int c, double wE,
 acm_status adjoint_sphere(acm_forest* f, int nsteps, double dt, int c, double wE, void* ws, size_t ws_bytes,
                           double* J_out, double* dtheta, void* dU0, int64_t n_elems, int on_device,
                           const void* lamN = nullptr) {
-  if (f->gp.Bs == 33) return fail(f, ACM_EINVAL, "the adjoint kernels are built for Bs 9 and 17");
   const double t0 = f->time;
   bool saved = false;
   const acm_status s = DISPATCH(f, adjoint_sweep, f, nsteps, dt, c, wE, ws, ws_bytes, J_out, dtheta, dU0, n_elems,

@@ -166,3 +166,43 @@ def test_bs33_adaptive_step_matches_oracle(A):
     _same_topology(f, fo)
     err = rel_linf(f.read_fields().astype(np.float64), block_order_fields(S))
     assert max(err) < 2e-5, err
+
+
+def test_bs33_vjp_matches_the_oracle(A):
+    """The discrete adjoint on 33^3 blocks (the adjoint stage kernel split by rows, as the
+    forward one): dL/dU_0 and dL/d(centre, radius) of L = <lam, U_1> (one RK4 step, sphere and
+    sponge, lam random on every copy of every point) against the oracle's vector-Jacobian
+    product, which is pinned by central differences; FP32 within 1e-4 as at Bs 17."""
+    from oracle.adapt import Solver
+    from oracle.adjoint import FrozenGridAdjoint
+    from oracle.forest import Forest as OForest
+    from tests.test_gpu_adjoint import _per_point
+    from tests.test_oracle_adjoint import L, _field
+    fo = OForest(nroot=(2, 1, 1), root_len=1.0, Bs=33, Jmin=0, Jmax=1, max_blocks=96)
+    fo.set_leaves(LEAVES)
+    delta = 1.5 * fo.h(1)
+    centre, R, dt = (1.3, 0.5, 0.5), 0.2, 1e-3
+    ph = oacm.Physics(nu=1e-2, c0=3.0, C_eta=1e-2, C_gamma=0.5, C_sp=0.05, u_inf=(1.0, 0.0, 0.0))
+    S = Solver(fo, ph, ic=lambda X, Y, Z: _field(X, Y, Z, 41),
+               mask=lambda X, Y, Z: oacm.sphere_mask(X, Y, Z, centre, R, delta),
+               sponge=lambda X, Y, Z: oacm.sponge_mask(X, Y, Z, L, 0.2, delta))
+    S.eval_ic()
+    S.eval_mask()
+    order = fo.sorted_leaves()
+    rng = np.random.default_rng(23)
+    lamB = rng.normal(size=(len(order), 4, 33, 33, 33))
+    lam = np.zeros_like(S.U)
+    for r, l in enumerate(order):
+        lam[fo.leaves[l]] = lamB[r]
+    _, go, gtho = FrozenGridAdjoint(S, centre, R, delta, dt=dt, nsteps=1).vjp(S.U.copy(), lam)
+    phys = dict(nu=1e-2, c0=3.0, C_eta=1e-2, C_gamma=0.5, C_sp=0.05, u_inf=(1.0, 0.0, 0.0), p_inf=0.0,
+                sponge=1, sponge_L=L, sponge_width=0.2, sponge_delta=delta)
+    f = A.Forest(_grid(), phys)
+    f.set_leaves(LEAVES)
+    f.set_mask(A.ACM_MASK_SPHERE, (*centre, R, delta))
+    f.write_fields(block_order_fields(S))
+    gU, gth = f.adjoint_vjp(1, dt, lamB, ckpt_every=1)
+    gob = np.stack([go[fo.leaves[l]] for l in order])
+    a, b = _per_point(fo, gU, 1), _per_point(fo, gob, 1)
+    assert np.abs(a - b).max() <= 1e-4 * np.abs(b).max()
+    assert np.abs(gth - gtho).max() <= 1e-4 * np.abs(gtho).max(), (gth, gtho)
