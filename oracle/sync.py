@@ -176,8 +176,9 @@ def sync(forest, F, g, which="cube"):
     pv = PointValues(forest, F)
     Pl = local_points(M, g, which)
     n = M + 1 + 2 * g
-    ext = np.full((F.shape[0], F.shape[1], n, n, n), np.nan)
     leaves = list(forest.leaves.items())
+    nslot = max(s for _, s in leaves) + 1 if leaves else 0
+    ext = np.full((nslot, F.shape[1], n, n, n), np.nan)
     # batch all blocks of one level together
     for J in sorted({l[0][0] for l in leaves}):
         blk = [(l, s) for l, s in leaves if l[0] == J]

@@ -16,7 +16,7 @@ def _poly(C, X, Y, Z):
 
 
 def _solver(leaves, nroot=(2, 2, 2), Jmin=1, Jmax=3, ic=None, **kw):
-    fo = Forest(nroot=nroot, root_len=1.0, Bs=9, Jmin=Jmin, Jmax=Jmax, max_blocks=1 << 14)
+    fo = Forest(nroot=nroot, root_len=1.0, Bs=9, Jmin=Jmin, Jmax=Jmax, max_blocks=1 << 12)
     fo.set_leaves(leaves)
     S = Solver(fo, acm.Physics(), ic=ic, **kw)
     S.eval_ic()
@@ -48,7 +48,7 @@ def test_refine_predicts_cubics_exactly_and_coarsen_restores():
     assert nchk > 10
     # uniform level-2 grid, J_min = 2: with every detail below a huge threshold, coarsening
     # undoes the refinement exactly (R o P = Id)
-    fo = Forest(nroot=(1, 1, 1), root_len=1.0, Bs=9, Jmin=2, Jmax=3, max_blocks=1 << 12)
+    fo = Forest(nroot=(1, 1, 1), root_len=1.0, Bs=9, Jmin=2, Jmax=3, max_blocks=1 << 10)
     fo.init_uniform(2)
     S = Solver(fo, acm.Physics(), ic=lambda X, Y, Z: _poly(C, X, Y, Z), eps=1e3, dealias=False)
     S.eval_ic()
@@ -92,7 +92,7 @@ def test_coarsen_refine_error_below_threshold_and_grid_invariants():
 def test_initial_grid_tracks_the_mask_interface():
     delta = 1.5 / (8 * 8)
     for dealias, top in ((True, 2), (False, 3)):
-        fo = Forest(nroot=(1, 1, 1), root_len=1.0, Bs=9, Jmin=1, Jmax=3, max_blocks=1 << 12)
+        fo = Forest(nroot=(1, 1, 1), root_len=1.0, Bs=9, Jmin=1, Jmax=3, max_blocks=1 << 10)
         S = Solver(fo, acm.Physics(), eps=1e-3, dealias=dealias,
                    ic=lambda X, Y, Z: acm.ic_uniform(X, Y, Z),
                    mask=lambda X, Y, Z: acm.sphere_mask(X, Y, Z, (0.5, 0.5, 0.5), 0.2, delta))
@@ -115,10 +115,10 @@ def test_adaptive_run_stays_within_the_threshold_error_of_the_uniform_run():
     ic = lambda X, Y, Z: np.stack([np.sin(2 * math.pi * X) * np.cos(2 * math.pi * Y),
                                    0.5 * np.cos(2 * math.pi * X) * np.sin(2 * math.pi * Z),
                                    0.2 * np.sin(2 * math.pi * (Y + Z)), np.zeros_like(X)])
-    fa = Forest(nroot=(1, 1, 1), root_len=1.0, Bs=9, Jmin=1, Jmax=3, max_blocks=1 << 12)
+    fa = Forest(nroot=(1, 1, 1), root_len=1.0, Bs=9, Jmin=1, Jmax=3, max_blocks=1 << 10)
     A = Solver(fa, ph, eps=eps, dealias=False, ic=ic)
     A.initial_grid()
-    fu = Forest(nroot=(1, 1, 1), root_len=1.0, Bs=9, Jmin=3, Jmax=3, max_blocks=1 << 12)
+    fu = Forest(nroot=(1, 1, 1), root_len=1.0, Bs=9, Jmin=3, Jmax=3, max_blocks=1 << 10)
     fu.init_uniform(3)
     Uni = Solver(fu, ph, ic=ic)
     Uni.eval_ic()
