@@ -1056,9 +1056,10 @@ def main():
             "autotune": {"fine_wins_ctas_per_sm": tuned[0], "slab_ctas_per_sm": tuned[1],
                          "stage_kernel": {0: "pair (2 points/thread, packed f32x2)",
                                           1: "point (1 point/thread)",
-                                          2: "point, bulk-copy (TMA) staging of U/acc/chi"}[tuning["stage_variant"]],
+                                          2: "point, bulk-copy (TMA) staging of U/acc/chi",
+                                          3: "point, a block's rows over two CTAs"}[tuning["stage_variant"]],
                          "stage2_ms": {"pair": tuning["stage_ms"][0], "point": tuning["stage_ms"][1],
-                                       "point_tma": tuning["stage_ms"][2]}},
+                                       "point_tma": tuning["stage_ms"][2], "point_rows": tuning["stage_ms"][3]}},
             "clocks": clk,
         }
         print(json.dumps(line), flush=True)

@@ -246,9 +246,9 @@ acm_status acm_rk4_steps_batch(acm_forest* const* forests, int n, int nsteps, do
 /* Autotuner: on the current grid, time the two task-list kernels of the per-stage ghost
  * synchronisation -- fine wins and the coarse-face halo slabs -- for each number of CTAs per SM
  * walking the list (fine wins 2, 4, 8, 16; slabs 1, 2, 3) and keep the fastest of each for this
- * forest (either output may be NULL).  FP32 forests also time the two work layouts of the fused
- * stage kernel (ACM_STAGE_PAIR, ACM_STAGE_POINT below) on one RK stage of the live grid and keep
- * the faster.  Like every synchronisation it first lets finer leaves' values win on shared
+ * forest (either output may be NULL).  FP32 forests also time the forms of the fused stage
+ * kernel (ACM_STAGE_* below; blocks of 33^3 have one) on one RK stage of the live grid and keep
+ * the fastest.  Like every synchronisation it first lets finer leaves' values win on shared
  * boundary points of U; nothing else of the state changes (the stage timing writes only the
  * accumulator and a stage register, which every step rewrites before reading).  Synchronises
  * the stream.  No counterpart in the paper. */
@@ -259,12 +259,16 @@ acm_status acm_autotune(acm_forest* f, int* fw_ctas, int* slab_ctas);
  * FP32x2 arithmetic (FP32 forests only: fewer instructions, half the resident threads);
  * ACM_STAGE_POINT_TMA, one point per thread with the planes of U, the RK accumulator and the mask
  * brought into a shared-memory ring by mbarrier-tracked bulk copies one plane ahead (FP32 forests
- * only).  All compute every point by the same formula; ACM_STAGE_POINT and ACM_STAGE_POINT_TMA
- * give bitwise equal results, ACM_STAGE_PAIR differs in FP32 rounding order.  FP64 forests always
- * use ACM_STAGE_POINT. */
+ * only); ACM_STAGE_POINT_ROWS, one point per thread with a block's rows split over two CTAs of 9
+ * and 8 rows (FP32, Bs = 17: smaller CTAs, more of them per SM, each reading the other's rows
+ * next to its own like a halo).  All compute every point by the same formula; ACM_STAGE_POINT,
+ * ACM_STAGE_POINT_TMA and ACM_STAGE_POINT_ROWS give bitwise equal results, ACM_STAGE_PAIR
+ * differs in FP32 rounding order.  FP64 forests always use ACM_STAGE_POINT; forests of 33^3
+ * blocks always use their row-split form (three CTAs of 11 rows) whatever is set. */
 #define ACM_STAGE_PAIR 0
 #define ACM_STAGE_POINT 1
 #define ACM_STAGE_POINT_TMA 2
+#define ACM_STAGE_POINT_ROWS 3
 /* Force the stage kernel's form (until the next acm_autotune); drops a captured graph.
  * ACM_EINVAL for another value. */
 acm_status acm_set_stage_variant(acm_forest* f, int variant);
@@ -274,7 +278,7 @@ acm_status acm_set_stage_variant(acm_forest* f, int variant);
  * ACM_STAGE_*; 0 until it has timed them). */
 typedef struct {
   int fw_ctas_per_sm, slab_ctas_per_sm, stage_variant;
-  float stage_ms[3];
+  float stage_ms[4];
 } acm_tuning;
 acm_status acm_get_tuning(const acm_forest* f, acm_tuning* out);
 

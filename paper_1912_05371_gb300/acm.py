@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(HERE, "_lib", "libacm.so")
 
 ACM_IC_TAYLOR_GREEN, ACM_IC_UNIFORM, ACM_IC_PULSE, ACM_IC_PULSE_RING = 1, 2, 3, 4
 ACM_MASK_NONE, ACM_MASK_SPHERE, ACM_MASK_PLATE, ACM_MASK_FIELD = 0, 1, 2, 3
-ACM_STAGE_PAIR, ACM_STAGE_POINT, ACM_STAGE_POINT_TMA = 0, 1, 2
+ACM_STAGE_PAIR, ACM_STAGE_POINT, ACM_STAGE_POINT_TMA, ACM_STAGE_POINT_ROWS = 0, 1, 2, 3
 ACM_REG_U = 0
 
 
@@ -43,7 +43,7 @@ class Diag(C.Structure):
 
 class Tuning(C.Structure):
     _fields_ = [("fw_ctas_per_sm", C.c_int), ("slab_ctas_per_sm", C.c_int), ("stage_variant", C.c_int),
-                ("stage_ms", C.c_float * 3)]
+                ("stage_ms", C.c_float * 4)]
 
 
 class StepStats(C.Structure):
@@ -306,8 +306,9 @@ class Forest:
 
     def set_stage_variant(self, variant):
         """Force the stage kernel's form: ACM_STAGE_POINT (one point per thread), ACM_STAGE_PAIR
-        (two points per thread, FP32) or ACM_STAGE_POINT_TMA (one point per thread, bulk-copy
-        staging, FP32)."""
+        (two points per thread, FP32), ACM_STAGE_POINT_TMA (one point per thread, bulk-copy
+        staging, FP32) or ACM_STAGE_POINT_ROWS (one point per thread, a 17^3 block's rows over
+        two CTAs, FP32)."""
         self._check(self.L.acm_set_stage_variant(self.h, int(variant)))
 
     def tuning(self):

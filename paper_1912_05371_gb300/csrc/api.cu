@@ -88,7 +88,7 @@ struct acm_forest {
   int tune_fw_ctas = 8;            // fine-wins kernel: CTAs per SM walking the task list
   int tune_slab_ctas = 3;          // coarse-face slab kernel: CTAs per SM walking the task list
   int stage_variant = acm::kStagePoint;  // FP32 stage kernel: one point per thread, or two
-  float tune_stage_ms[3] = {0.f, 0.f, 0.f};   // the autotuner's times of the three (FP32)
+  float tune_stage_ms[4] = {0.f, 0.f, 0.f, 0.f};   // the autotuner's times of the forms (FP32)
 
   // host side of the current topology (the neighbourhood tables are built on the device from
   // the block list; the host leaf map is brought up to date only when a host query needs it)
@@ -1080,8 +1080,9 @@ acm_status autotune(acm_forest* f, int* fw_ctas, int* slab_ctas) {
     a.c_out = 0.0;
     best = 1e30f;
     int best_v = f->stage_variant;
-    for (int v : {acm::kStagePair, acm::kStagePoint, acm::kStagePointTMA}) {
+    for (int v : {acm::kStagePair, acm::kStagePoint, acm::kStagePointTMA, acm::kStagePointRows}) {
       if (f->gp.Bs == 33 && v != acm::kStagePoint) continue;   // the one form for 33^3 blocks
+      if (v == acm::kStagePointRows && f->gp.Bs != 17) continue;
       float ms = 0.f;
       acm_status s = time_launches(f, [&]() {
         acm::launch_stage<T>(2, f->gp.Bs, a, t, f->phk, f->d_err, f->st, v);
@@ -1931,10 +1932,12 @@ acm_status acm_autotune(acm_forest* f, int* fw_ctas, int* slab_ctas) {
 
 acm_status acm_set_stage_variant(acm_forest* f, int variant) {
   if (!f) return ACM_EINVAL;
-  if (variant != ACM_STAGE_PAIR && variant != ACM_STAGE_POINT && variant != ACM_STAGE_POINT_TMA)
+  if (variant != ACM_STAGE_PAIR && variant != ACM_STAGE_POINT && variant != ACM_STAGE_POINT_TMA &&
+      variant != ACM_STAGE_POINT_ROWS)
     return fail(f, ACM_EINVAL, "unknown stage kernel");
   f->stage_variant = variant == ACM_STAGE_PAIR ? acm::kStagePair
-                     : (variant == ACM_STAGE_POINT ? acm::kStagePoint : acm::kStagePointTMA);
+                     : (variant == ACM_STAGE_POINT ? acm::kStagePoint
+                        : (variant == ACM_STAGE_POINT_TMA ? acm::kStagePointTMA : acm::kStagePointRows));
   // a captured graph holds the old kernel
   if (f->gexec) { cudaGraphExecDestroy(f->gexec); f->gexec = nullptr; }
   if (f->graph) { cudaGraphDestroy(f->graph); f->graph = nullptr; }
@@ -1945,12 +1948,17 @@ acm_status acm_get_tuning(const acm_forest* f, acm_tuning* out) {
   if (!f || !out) return ACM_EINVAL;
   out->fw_ctas_per_sm = f->tune_fw_ctas;
   out->slab_ctas_per_sm = f->tune_slab_ctas;
-  out->stage_variant = f->gp.precision == 64 || f->gp.Bs == 33 ? ACM_STAGE_POINT
+  out->stage_variant = f->gp.precision == 64 || f->gp.Bs == 33 ||
+                               (f->stage_variant == acm::kStagePointRows && f->gp.Bs != 17)
+                           ? ACM_STAGE_POINT
                        : (f->stage_variant == acm::kStagePair ? ACM_STAGE_PAIR
-                          : (f->stage_variant == acm::kStagePoint ? ACM_STAGE_POINT : ACM_STAGE_POINT_TMA));
+                          : (f->stage_variant == acm::kStagePoint ? ACM_STAGE_POINT
+                             : (f->stage_variant == acm::kStagePointTMA ? ACM_STAGE_POINT_TMA
+                                                                         : ACM_STAGE_POINT_ROWS)));
   out->stage_ms[ACM_STAGE_PAIR] = f->tune_stage_ms[acm::kStagePair];
   out->stage_ms[ACM_STAGE_POINT] = f->tune_stage_ms[acm::kStagePoint];
   out->stage_ms[ACM_STAGE_POINT_TMA] = f->tune_stage_ms[acm::kStagePointTMA];
+  out->stage_ms[ACM_STAGE_POINT_ROWS] = f->tune_stage_ms[acm::kStagePointRows];
   return ACM_OK;
 }
 

@@ -28,11 +28,12 @@ namespace acm {
 
 namespace {
 
-template <typename T, int BS>
+template <typename T, int BS, int RYT = 0>
 struct Cfg {
   // rows (y) of the block one CTA updates: all of them up to Bs = 17; a CTA may have at most
-  // 1024 threads, so a Bs = 33 block goes to three CTAs of 11 rows
-  static constexpr int RY = BS <= 17 ? BS : 11;
+  // 1024 threads, so a Bs = 33 block goes to three CTAs of 11 rows; RYT != 0 chooses the rows
+  // per CTA (the autotuner's tile shape: a 17^3 block over two CTAs of 9 and 8 rows)
+  static constexpr int RY = RYT ? RYT : (BS <= 17 ? BS : 11);
   static constexpr int NS = (BS + RY - 1) / RY;    // CTAs per block
   static constexpr int NT = ((BS * RY + 31) / 32) * 32;
   static constexpr int H = RY + 6;       // plane rows: 3 halo rows each side
@@ -46,7 +47,7 @@ struct Cfg {
   static constexpr int NHC = 6 * (RY + BS);
   static constexpr int NH = 4 * NHC;
   static constexpr int HPT = (NH + NT - 1) / NT;   // halo values per thread
-  static constexpr int MINB = sizeof(T) == 4 ? (NT <= 352 ? 3 : 2) : 1;   // CTAs per SM
+  static constexpr int MINB = sizeof(T) == 4 ? (NT <= 160 ? 6 : (NT <= 352 ? 3 : 2)) : 1;   // CTAs per SM
   static_assert(4 * PW < 0x8000, "plane buffer offsets must fit 15 bits");
   static_assert(NS == 1 || sizeof(T) == 4, "row-split blocks are FP32 only");
 };
@@ -65,24 +66,24 @@ __host__ __device__ constexpr int staged_planes(bool mask) {
 // the point of use.
 // The update of one block (rank `rank` of the topology tp), rows part * RY .. of it; a: the
 // arrays, kc: the constants.
-template <typename T, int BS, int STAGE, bool TMA>
+template <typename T, int BS, int STAGE, bool TMA, int RYT = 0>
 __device__ __forceinline__ void stage_block(const StagePtrs<T>& a, const StageConst<T>& kc, const TopoK& tp,
                                             const PhysK& ph, int* err, const int rank, const int part) {
   using L = Lay<T, BS>;
   constexpr int M = L::M;
-  constexpr int NT = Cfg<T, BS>::NT;
-  constexpr int RY = Cfg<T, BS>::RY, NHC = Cfg<T, BS>::NHC;
-  static_assert(!TMA || Cfg<T, BS>::NS == 1, "the bulk-copy ring stages whole planes");
-  constexpr int W = Cfg<T, BS>::W;
-  constexpr int PW = Cfg<T, BS>::PW;
-  constexpr int HPT = Cfg<T, BS>::HPT;
+  constexpr int NT = Cfg<T, BS, RYT>::NT;
+  constexpr int RY = Cfg<T, BS, RYT>::RY, NHC = Cfg<T, BS, RYT>::NHC;
+  static_assert(!TMA || Cfg<T, BS, RYT>::NS == 1, "the bulk-copy ring stages whole planes");
+  constexpr int W = Cfg<T, BS, RYT>::W;
+  constexpr int PW = Cfg<T, BS, RYT>::PW;
+  constexpr int HPT = Cfg<T, BS, RYT>::HPT;
 
   __shared__ __align__(16) T buf[2][4][PW];
   __shared__ int ftype[6];
   __shared__ int fs[6][4];
   __shared__ T sp[3][BS];
   // x/y halo values of every plane as affine functions of z (see below)
-  constexpr int NH = Cfg<T, BS>::NH;
+  constexpr int NH = Cfg<T, BS, RYT>::NH;
   __shared__ unsigned hlo[NH], hhi[NH], hzd[NH];
 
   const int tid = threadIdx.x;
@@ -188,7 +189,7 @@ __device__ __forceinline__ void stage_block(const StagePtrs<T>& a, const StageCo
       const int i = tid + k * NT;
       if (i < NH) {
         const unsigned zd = hzd[i];
-        if (Cfg<T, BS>::NS > 1 && zd == 0) continue;
+        if (Cfg<T, BS, RYT>::NS > 1 && zd == 0) continue;
         const unsigned off = (zz > M / 2 ? hhi[i] : hlo[i]) + (unsigned)zz * (zd >> 16);
         cp_async_elem(B + (zd & 0x7fffu), ((zd & 0x8000u) ? a.slab : a.in) + (size_t)off);
       }
@@ -233,8 +234,8 @@ __device__ __forceinline__ void stage_block(const StagePtrs<T>& a, const StageCo
   // (stage input planes z + 4 + kPf, U, acc and chi planes z + kPf), one bulk request each
   // (this CTA's rows of the plane, widened to 16-byte boundaries inside the padded plane)
   constexpr int kPf = 2;
-  const int pf0 = Cfg<T, BS>::NS == 1 ? 0 : ((y0 * BS) & ~(L::VEC - 1));
-  const int pf1 = Cfg<T, BS>::NS == 1 ? L::PP : (((y0 + ny) * BS + L::VEC - 1) & ~(L::VEC - 1));
+  const int pf0 = Cfg<T, BS, RYT>::NS == 1 ? 0 : ((y0 * BS) & ~(L::VEC - 1));
+  const int pf1 = Cfg<T, BS, RYT>::NS == 1 ? L::PP : (((y0 + ny) * BS + L::VEC - 1) & ~(L::VEC - 1));
   const unsigned kPlaneBytes = (unsigned)((pf1 - pf0) * sizeof(T));
   auto prefetch_planes = [&](int zin, int zo) {
     const size_t pz = (size_t)zin * L::PP + pf0, po = (size_t)zo * L::PP + pf0;
@@ -399,19 +400,19 @@ __device__ __forceinline__ void stage_block(const StagePtrs<T>& a, const StageCo
   }
 }
 
-template <typename T, int BS, int STAGE, bool TMA = false>
-__global__ void __launch_bounds__(Cfg<T, BS>::NT, Cfg<T, BS>::MINB)
+template <typename T, int BS, int STAGE, bool TMA = false, int RYT = 0>
+__global__ void __launch_bounds__(Cfg<T, BS, RYT>::NT, Cfg<T, BS, RYT>::MINB)
 k_stage(const StageK<T> a, const TopoK tp, const PhysK ph, int* err) {
   const StagePtrs<T> p{a.in, a.U, a.acc, a.out, a.chi, a.slab, a.norms, a.coefp};
-  constexpr int NS = Cfg<T, BS>::NS;
-  stage_block<T, BS, STAGE, TMA>(p, a.kc, tp, ph, err, blockIdx.x / NS, blockIdx.x % NS);
+  constexpr int NS = Cfg<T, BS, RYT>::NS;
+  stage_block<T, BS, STAGE, TMA, RYT>(p, a.kc, tp, ph, err, blockIdx.x / NS, blockIdx.x % NS);
 }
 
 // Persistent form over several independent instances: the CTAs walk the work list of
 // (instance, rank) pairs, each instance with its own arrays and topology (desc) and the same
 // physics and constants; every block gets bitwise the update k_stage gives it.
-template <typename T, int BS, int STAGE>
-__global__ void __launch_bounds__(Cfg<T, BS>::NT, Cfg<T, BS>::MINB)
+template <typename T, int BS, int STAGE, int RYT = 0>
+__global__ void __launch_bounds__(Cfg<T, BS, RYT>::NT, Cfg<T, BS, RYT>::MINB)
 k_stage_multi(const StageConst<T> kc, const PhysK ph, const StageInst<T>* desc, const int2* work, int nwork,
               int* err) {
   for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
@@ -444,28 +445,28 @@ __global__ void k_rk_coefs(const unsigned long long* maxbits, RkK p, double* rk)
   rk[8] = dt / 3.0; rk[9] = dt / 6.0;
 }
 
-template <typename T, int BS, int STAGE, bool TMA>
+template <typename T, int BS, int STAGE, bool TMA, int RYT = 0>
 void launch_one(const StageK<T>& s, const TopoK& t, const PhysK& p, int* err, cudaStream_t st) {
-  const dim3 grid((unsigned)(t.n * Cfg<T, BS>::NS)), block(Cfg<T, BS>::NT);
+  const dim3 grid((unsigned)(t.n * Cfg<T, BS, RYT>::NS)), block(Cfg<T, BS, RYT>::NT);
   const size_t dyn = TMA ? (size_t)2 * staged_planes<STAGE>(p.mask != 0) * Lay<T, BS>::PP * sizeof(T) : 0;
   if (TMA) {
     // the ring comes on top of the kernel's static shared memory: opt in to its largest size
     static std::atomic<unsigned long long> opted{0};
-    smem_opt_in_stage(k_stage<T, BS, STAGE, TMA>, (size_t)2 * staged_planes<STAGE>(true) * Lay<T, BS>::PP * sizeof(T),
+    smem_opt_in_stage(k_stage<T, BS, STAGE, TMA, RYT>, (size_t)2 * staged_planes<STAGE>(true) * Lay<T, BS>::PP * sizeof(T),
                       opted);
   }
-  k_stage<T, BS, STAGE, TMA><<<grid, block, dyn, st>>>(s, t, p, err);
+  k_stage<T, BS, STAGE, TMA, RYT><<<grid, block, dyn, st>>>(s, t, p, err);
 }
 
-template <typename T, int BS, bool TMA>
+template <typename T, int BS, bool TMA, int RYT = 0>
 void launch_stage_bs(int stage, const StageK<T>& s, const TopoK& t, const PhysK& p, int* err, cudaStream_t st) {
   if (t.n <= 0) return;
   switch (stage) {
-    case 0: launch_one<T, BS, 0, TMA>(s, t, p, err, st); break;
-    case 1: launch_one<T, BS, 1, TMA>(s, t, p, err, st); break;
-    case 2: launch_one<T, BS, 2, TMA>(s, t, p, err, st); break;
-    case 3: launch_one<T, BS, 3, TMA>(s, t, p, err, st); break;
-    default: launch_one<T, BS, 4, TMA>(s, t, p, err, st); break;
+    case 0: launch_one<T, BS, 0, TMA, RYT>(s, t, p, err, st); break;
+    case 1: launch_one<T, BS, 1, TMA, RYT>(s, t, p, err, st); break;
+    case 2: launch_one<T, BS, 2, TMA, RYT>(s, t, p, err, st); break;
+    case 3: launch_one<T, BS, 3, TMA, RYT>(s, t, p, err, st); break;
+    default: launch_one<T, BS, 4, TMA, RYT>(s, t, p, err, st); break;
   }
 }
 
@@ -527,6 +528,10 @@ void launch_stage(int stage, int Bs, const StageK<T>& s, const TopoK& t, const P
   if constexpr (sizeof(T) == 4) {
     if (Bs == 33) {              // the point form, rows split over three CTAs
       launch_stage_bs<T, 33, false>(stage, a, t, p, err, st);
+      return;
+    }
+    if (variant == kStagePointRows && Bs == 17) {   // a block over two CTAs of 9 and 8 rows
+      launch_stage_bs<T, 17, false, 9>(stage, a, t, p, err, st);
       return;
     }
     if (variant == kStagePointTMA) {

@@ -97,15 +97,16 @@ def test_sync_ghosts_matches_oracle(A, prec, Bs, seed):
     assert max(err) < (1e-13 if prec == 64 else 1e-6), err
 
 
-# the stage kernel's forms (FP32: two points per thread; one; one with bulk-copy staging)
-PAIR, POINT, TMA = 0, 1, 2
+# the stage kernel's forms (FP32: two points per thread; one; one with bulk-copy staging; one
+# with a block's rows over two CTAs)
+PAIR, POINT, TMA, ROWS = 0, 1, 2, 3
 
 
 @pytest.mark.parametrize("prec,Bs,seed,masked,sponge,variant", [
     (64, 9, 7, True, True, POINT), (64, 17, 8, False, False, POINT), (32, 9, 9, True, True, PAIR),
     (32, 9, 9, True, True, POINT), (32, 17, 14, True, True, PAIR), (32, 17, 14, True, True, POINT),
     (32, 17, 14, True, True, TMA), (32, 9, 9, True, True, TMA), (32, 17, 16, False, False, TMA),
-    (64, 9, 10, False, True, POINT)])
+    (32, 17, 14, True, True, ROWS), (64, 9, 10, False, True, POINT)])
 def test_fused_rhs_matches_oracle(A, prec, Bs, seed, masked, sponge, variant):
     leaves = random_graded_leaves(seed, nroot=(2, 1, 1), J0=1, Jmax=3, n_target=70)
     grid = _grid(Bs=Bs, precision=prec)
@@ -135,7 +136,8 @@ def test_fused_rhs_matches_oracle(A, prec, Bs, seed, masked, sponge, variant):
 
 
 @pytest.mark.parametrize("prec,Bs,seed,variant", [(64, 9, 11, POINT), (64, 17, 12, POINT), (32, 17, 13, PAIR),
-                                                  (32, 17, 13, POINT), (32, 9, 15, PAIR), (32, 17, 13, TMA)])
+                                                  (32, 17, 13, POINT), (32, 9, 15, PAIR), (32, 17, 13, TMA),
+                                                  (32, 17, 13, ROWS)])
 def test_rk4_steps_match_oracle(A, prec, Bs, seed, variant):
     leaves = random_graded_leaves(seed, nroot=(2, 1, 1), J0=1, Jmax=3, n_target=70)
     grid = _grid(Bs=Bs, precision=prec)
@@ -151,15 +153,16 @@ def test_rk4_steps_match_oracle(A, prec, Bs, seed, variant):
     assert max(err) < TOL[prec], err
 
 
-@pytest.mark.parametrize("masked", [True, False])
-def test_bulk_copy_staging_is_bitwise_the_point_kernel(A, masked):
-    """The one-point stage kernel with U, the accumulator and chi staged by bulk copies computes
-    bitwise what the one with per-thread loads computes (FP32, graded layout, RK4 steps)."""
+@pytest.mark.parametrize("masked,other", [(True, TMA), (False, TMA), (True, ROWS), (False, ROWS)])
+def test_bulk_copy_staging_is_bitwise_the_point_kernel(A, masked, other):
+    """The one-point stage kernel with U, the accumulator and chi staged by bulk copies, and the
+    one with a block's rows over two CTAs, compute bitwise what the one-point kernel with
+    per-thread loads over whole blocks computes (FP32, graded layout, RK4 steps)."""
     leaves = random_graded_leaves(17, nroot=(2, 1, 1), J0=1, Jmax=3, n_target=70)
     grid = _grid(Bs=17, precision=32)
     mask = (1.2, 0.5, 0.5, 0.15, 0.05) if masked else None
     out = []
-    for variant in (POINT, TMA):
+    for variant in (POINT, other):
         f, S = _pair(A, grid, _phys(), leaves, fn_seed=17, mask=mask)
         f.set_stage_variant(variant)
         for _ in range(2):
