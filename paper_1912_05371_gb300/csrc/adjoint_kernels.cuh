@@ -442,9 +442,11 @@ k_adj_stage(const AdjStageK<T> a, const TopoK tp, const PhysK ph, const MaskK m)
 // point (the forward's decimation); fine wins' copies
 // between leaves are W's part (k_adj_fw_T).  Across a coarser face, q is held by a leaf if it lies
 // on one's lattice (its point gets the value), else it was predicted by the tensor DD-4 from the
-// even points of the 5 x (M/2 + 3)^2 coarse patch around the face: the transposed prediction is
-// summed per patch point in shared memory first, then each patch point goes to the leaf holding
-// it.  FP atomics: several blocks reach one point.  Runs after k_adj_stage.
+// even points of the 5 x (M/2 + 3)^2 coarse patch around the face: the predicted targets are kept
+// in shared memory and the transposed prediction is applied one axis at a time (along the face,
+// then across it) as gathers, each coarse point summing the fine points its prediction weights
+// reach; then each patch point goes to the leaf holding it.  FP atomics in global memory only:
+// several blocks reach one point.  Runs after k_adj_stage.
 //
 // E^T across same-level faces in gather form: block A adds to its own points the face-halo
 // targets of its same-level face neighbours that the forward read from A (the neighbour N's
@@ -532,6 +534,13 @@ struct HaloCfg {
   static constexpr int M = BS - 1;
   static constexpr int NTG = M / 2 + 3;               // even fine tangential coordinates -2 .. M + 2
   static constexpr int NPATCH = 5 * NTG * NTG;        // normal: 5 even fine coordinates beyond the face
+  // shared memory of a coarse face: the predicted halo targets h [f][l][t2][t1], then after the
+  // transposed prediction along t1, t2 and the normal a [f][l][t2][c1], b [f][l][c2][c1] (in h's
+  // place) and the patch [f][n][c2][c1] (in a's place)
+  static constexpr int NH3 = 3 * BS * BS, NA = 3 * BS * NTG, NB = 3 * NTG * NTG;
+  static constexpr int U0 = 4 * (NH3 > NB ? NH3 : NB);
+  static constexpr int U1 = 4 * (NA > NPATCH ? NA : NPATCH);
+  static constexpr size_t bytes = (size_t)(U0 + U1) * sizeof(T);
 };
 
 template <typename T, int BS>
@@ -540,18 +549,21 @@ __global__ void __launch_bounds__(kNA) k_adj_halo(const AdjStageK<T> a, const To
   using H = HaloCfg<T, BS>;
   constexpr int M = L::M, NTG = H::NTG, NP = H::NPATCH;
   __shared__ int nbh[kNbhStride];
-  __shared__ T acc[4 * NP];
+  extern __shared__ __align__(16) unsigned char hsm[];
+  T* hv = reinterpret_cast<T*>(hsm);                  // h, later b
+  T* acc = hv + H::U0;                                // a, later the patch
   const int rank = blockIdx.x / 6, F = blockIdx.x % 6;
-  for (int i = threadIdx.x; i < kNbhStride; i += kNA) nbh[i] = tp.nbh[(size_t)rank * kNbhStride + i];
-  __syncthreads();
   const int ax = F >> 1, side = F & 1;
   const int d = kFaceBox[F];
+  // a same-level neighbour gathers these targets itself (k_adj_samelevel): its CTA reads the
+  // face's type word only
+  if ((tp.nbh[(size_t)rank * kNbhStride + kNbhType + d] & 15) == kTypeLeaf) return;
+  for (int i = threadIdx.x; i < kNbhStride; i += kNA) nbh[i] = tp.nbh[(size_t)rank * kNbhStride + i];
+  __syncthreads();
   const int ty = nbh[kNbhType + d] & 15;
-  // a same-level neighbour gathers these targets itself (k_adj_samelevel)
-  if (ty == kTypeLeaf) return;
   const bool coarse = ty != kTypeLeaf && ty != kTypeRefined;
   if (coarse) {
-    for (int i = threadIdx.x; i < 4 * NP; i += kNA) acc[i] = T(0);
+    for (int i = threadIdx.x; i < 4 * H::NH3; i += kNA) hv[i] = T(0);
     __syncthreads();
   }
   const size_t bo = (size_t)tp.blist[rank] * L::BLK;
@@ -564,27 +576,20 @@ __global__ void __launch_bounds__(kNA) k_adj_halo(const AdjStageK<T> a, const To
   const T c_lam = T(a.c_lam), c_nu = T(a.c_nu);
   // threads run along the tangential axis with the smaller memory stride (x for y and z faces)
   const int o1 = ax == 0 ? 1 : 0, o2 = 3 - ax - o1;
-  const int dir = side ? 1 : -1;
   const T sg = side ? T(1) : T(-1);
   const T wd[4] = {T(-1) / T(16), T(9) / T(16), T(9) / T(16), T(-1) / T(16)};
   // E^T of one halo target q of component f with value de
   auto scatter = [&](const int (&q)[3], int f, int l, T de) {
     if (!coarse) {
-      int s, lc[3];
-      if (ty == kTypeLeaf) {
-        s = nbh[8 * d];
-        lc[ax] = side ? l : M - l;
-        lc[o1] = q[o1];
-        lc[o2] = q[o2];
-      } else {
-        int c = (side ? 0 : 1) << ax;
-        const int b1 = q[o1] > M / 2, b2 = q[o2] > M / 2;
-        c |= (b1 << o1) | (b2 << o2);
-        s = nbh[8 * d + c];
-        lc[ax] = side ? 2 * l : M - 2 * l;
-        lc[o1] = 2 * q[o1] - b1 * M;
-        lc[o2] = 2 * q[o2] - b2 * M;
-      }
+      // a finer face: the child's coinciding point (the forward's decimation)
+      int c = (side ? 0 : 1) << ax;
+      const int b1 = q[o1] > M / 2, b2 = q[o2] > M / 2;
+      c |= (b1 << o1) | (b2 << o2);
+      const int s = nbh[8 * d + c];
+      int lc[3];
+      lc[ax] = side ? 2 * l : M - 2 * l;
+      lc[o1] = 2 * q[o1] - b1 * M;
+      lc[o2] = 2 * q[o2] - b2 * M;
       if (s < 0) {
         atomicOr(err, 8);
         return;
@@ -617,25 +622,8 @@ __global__ void __launch_bounds__(kNA) k_adj_halo(const AdjStageK<T> a, const To
       atomicAdd(&a.nu[(size_t)s * L::BLK + (size_t)f * L::FS + L::idx(lc[0], lc[1], lc[2])], de);
       return;
     }
-    // predicted ghost: transposed tensor DD-4 (even points: weight 1, odd: -1, 9, 9, -1 over 16
-    // at -3, -1, 1, 3) onto the coarse patch (normal index from the face, tangential (c + 2) / 2)
-    const int nn = (q[ax] & 1) ? 4 : 1, n1 = (q[o1] & 1) ? 4 : 1, n2 = (q[o2] & 1) ? 4 : 1;
-    const int off[4] = {-3, -1, 1, 3};
-    const int nbase = side ? M - 2 : -6;
-    for (int kn = 0; kn < nn; ++kn) {
-      const int cn = nn == 4 ? q[ax] + off[kn] : q[ax];
-      const T wn = nn == 4 ? wd[kn] : T(1);
-      for (int k2 = 0; k2 < n2; ++k2) {
-        const int c2 = n2 == 4 ? q[o2] + off[k2] : q[o2];
-        const T w2 = n2 == 4 ? wd[k2] : T(1);
-        for (int k1 = 0; k1 < n1; ++k1) {
-          const int c1 = n1 == 4 ? q[o1] + off[k1] : q[o1];
-          const T w1 = n1 == 4 ? wd[k1] : T(1);
-          const int pi = (((cn - nbase) >> 1) * NTG + ((c2 + 2) >> 1)) * NTG + ((c1 + 2) >> 1);
-          atomicAdd(&acc[f * NP + pi], wn * w2 * w1 * de);
-        }
-      }
-    }
+    // a predicted ghost: kept for the transposed prediction below (each target has one thread)
+    hv[((f * 3 + l - 1) * BS + q[o2]) * BS + q[o1]] = de;
   };
   // a thread per (component, tangential point): the three halo layers from the three sources
   // next to the face, p_k at normal distance k = 0, 1, 2 inside it (q at layer l reads p_k with
@@ -680,6 +668,50 @@ __global__ void __launch_bounds__(kNA) k_adj_halo(const AdjStageK<T> a, const To
   }
   if (!coarse) return;
   __syncthreads();
+  // the transposed tensor DD-4 prediction, one axis at a time as gathers: a coarse point c (fine
+  // coordinate 2c - 2 along the face, nbase + 2n across it) takes the fine point it coincides
+  // with (weight 1) and the odd fine points at distance 1 and 3 (9/16, -1/16)
+  auto gather_line = [&](const T* src, int stride, int tc, int lo, int hi) -> T {
+    T v = T(0);
+    if (tc >= lo && tc <= hi) v += src[tc * stride];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int t = tc - (2 * k - 3);           // t + off_k = tc with off_k = -3, -1, 1, 3
+      if (t >= lo && t <= hi && (t & 1)) v += wd[k] * src[t * stride];
+    }
+    return v;
+  };
+  T* pa = acc;
+  for (int i = threadIdx.x; i < 4 * H::NA; i += kNA) {        // along t1: a[f][l][t2][c1]
+    const int c1 = i % NTG, r = i / NTG;                      // r = (f * 3 + l) * BS + t2
+    pa[i] = gather_line(hv + (size_t)r * BS, 1, 2 * c1 - 2, 0, M);
+  }
+  __syncthreads();
+  T* pb = hv;
+  for (int i = threadIdx.x; i < 4 * H::NB; i += kNA) {        // along t2: b[f][l][c2][c1]
+    const int c1 = i % NTG, c2 = (i / NTG) % NTG, fl = i / (NTG * NTG);
+    pb[i] = gather_line(pa + (size_t)fl * BS * NTG + c1, NTG, 2 * c2 - 2, 0, M);
+  }
+  __syncthreads();
+  const int nbase = side ? M - 2 : -6;
+  for (int i = threadIdx.x; i < 4 * NP; i += kNA) {           // across the face: patch[f][n][c2][c1]
+    const int c = i % (NTG * NTG), n = (i / (NTG * NTG)) % 5, f = i / NP;
+    // layer l sits at fine normal coordinate side ? M + l : -l, i.e. index l - 1 of b's rows at
+    // coordinate (side ? M + 1 : -1) + (side ? 1 : -1) (l - 1)
+    const int pn = nbase + 2 * n;
+    T v = T(0);
+#pragma unroll
+    for (int l = 1; l <= 3; ++l) {
+      const int qn = side ? M + l : -l;
+      const int off = pn - qn;
+      T w = T(0);
+      if (off == 0) w = T(1);
+      else if (qn & 1) w = off == -3 ? wd[0] : (off == -1 ? wd[1] : (off == 1 ? wd[2] : (off == 3 ? wd[3] : T(0))));
+      if (w != T(0)) v += w * pb[((size_t)(f * 3 + l - 1) * NTG * NTG) + c];
+    }
+    acc[i] = v;
+  }
+  __syncthreads();
   // each patch point to the leaf holding it (the prediction's sources are held directly)
   for (int i = threadIdx.x; i < 4 * NP; i += kNA) {
     const T v = acc[i];
@@ -687,7 +719,7 @@ __global__ void __launch_bounds__(kNA) k_adj_halo(const AdjStageK<T> a, const To
     const int f = i / NP, r = i % NP;
     const int kn = r / (NTG * NTG), k2 = (r / NTG) % NTG, k1 = r % NTG;
     int c[3];
-    c[ax] = (side ? M - 2 : -6) + 2 * kn;
+    c[ax] = nbase + 2 * kn;
     c[o2] = 2 * k2 - 2;
     c[o1] = 2 * k1 - 2;
     const long long o = direct_offset<T, BS>(nbh, c[0], c[1], c[2], f);
@@ -886,7 +918,9 @@ void stage(const AdjStageK<T>& a, const TopoK& t, const PhysK& ph, const MaskK& 
   smem_opt_in_stage(k_adj_stage<T, BS>, AdjCfg<T, BS>::bytes, opted);
   k_adj_stage<T, BS><<<g1(t.n * AdjCfg<T, BS>::NS), AdjCfg<T, BS>::NT, AdjCfg<T, BS>::bytes, st>>>(a, t, ph, m);
   k_adj_samelevel<T, BS><<<g1(t.n), kNA, 0, st>>>(a, t, ph, err);
-  k_adj_halo<T, BS><<<g1(6 * t.n), kNA, 0, st>>>(a, t, ph, err);
+  static std::atomic<unsigned long long> opted_h{0};
+  smem_opt_in_stage(k_adj_halo<T, BS>, HaloCfg<T, BS>::bytes, opted_h);
+  k_adj_halo<T, BS><<<g1(6 * t.n), kNA, HaloCfg<T, BS>::bytes, st>>>(a, t, ph, err);
   k_adj_fw_T<T, BS><<<fw_ctas(fw.max_tasks), kNA, 0, st>>>(a.nu, fw.tasks, fw.ntasks, t.nbh, t.blist);
 }
 
