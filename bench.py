@@ -819,6 +819,8 @@ def main():
                     help="host cores for the oracle's all-core figure (default: all, os.cpu_count())")
     ap.add_argument("--wavelet", type=int, default=40, choices=[40, 44],
                     help="wavelet of the main line: 40 = CDF 4/0 (default), 44 = CDF 4/4")
+    ap.add_argument("--adjoint-only", action="store_true",
+                    help="run only the adjoint workload (and its at-scale case) and print its JSON")
     ap.add_argument("--sweep", action="store_true",
                     help="run the random-grid performance study (Sec. 5.4) instead of the benchmark")
     ap.add_argument("--sweep-blocks", default="1000,2000,4000,8000,16000,24000")
@@ -831,6 +833,15 @@ def main():
         if not any(a.startswith("--steps") for a in sys.argv[1:]):
             args.steps = 15
         return random_grid_sweep(args)
+    if args.adjoint_only:
+        import torch
+        from paper_1912_05371_gb300 import acm as A
+        stream = torch.cuda.Stream()
+        with torch.cuda.stream(stream):
+            out = adjoint_measurement(A, stream)
+            out["at_scale"] = adjoint_at_scale(A, stream)
+        print(json.dumps({"adjoint": out}))
+        return 0
 
     import numpy as np
     import torch
