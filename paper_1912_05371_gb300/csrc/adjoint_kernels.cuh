@@ -155,7 +155,9 @@ struct AdjCfg {
   static_assert(NS == 1 || sizeof(T) == 4, "row-split blocks are FP32 only");
 };
 
-template <typename T, int BS>
+// MOVING: the moving box's parameter sensitivity (kind 2), compiled apart from the static masks'
+// form so that its FP64 pose arithmetic costs the static form no registers.
+template <typename T, int BS, bool MOVING>
 __global__ void __launch_bounds__(AdjCfg<T, BS>::NT, AdjCfg<T, BS>::MINB)
 k_adj_stage(const AdjStageK<T> a, const TopoK tp, const PhysK ph, const MaskK m) {
   using L = Lay<T, BS>;
@@ -312,7 +314,7 @@ k_adj_stage(const AdjStageK<T> a, const TopoK tp, const PhysK ph, const MaskK m)
   issue_halos(0, buf);
 
   const int ci = (y - y0 + 3) * W + x + 3;
-  const bool moving = m.kind == 2;
+  constexpr bool moving = MOVING;
   double dth = 0.0;
   const double hd = ph.h[bi.x];
   for (int z = 0; z <= M; ++z) {
@@ -402,7 +404,7 @@ k_adj_stage(const AdjStageK<T> a, const TopoK tp, const PhysK ph, const MaskK m)
         else if (a.sum_mode == 2) a.sum[o] += a.nup[o];
       }
       const T u = qy[0][3], v = qy[1][3], w = qy[2][3];
-      if (moving) {
+      if constexpr (MOVING) {
         const BoxPoint bp = box_point(m, lattice_coord(ph, bi, 0, x, M, hd) - m.p[9],
                                       lattice_coord(ph, bi, 1, y, M, hd) - m.p[10],
                                       lattice_coord(ph, bi, 2, z, M, hd) - m.p[11]);
@@ -914,9 +916,14 @@ inline unsigned fw_ctas(int64_t max_tasks) {
 template <typename T, int BS>
 void stage(const AdjStageK<T>& a, const TopoK& t, const PhysK& ph, const MaskK& m, const FwTasks& fw, int* err,
            cudaStream_t st) {
-  static std::atomic<unsigned long long> opted{0};
-  smem_opt_in_stage(k_adj_stage<T, BS>, AdjCfg<T, BS>::bytes, opted);
-  k_adj_stage<T, BS><<<g1(t.n * AdjCfg<T, BS>::NS), AdjCfg<T, BS>::NT, AdjCfg<T, BS>::bytes, st>>>(a, t, ph, m);
+  static std::atomic<unsigned long long> opted{0}, opted_m{0};
+  if (m.kind == 2) {
+    smem_opt_in_stage(k_adj_stage<T, BS, true>, AdjCfg<T, BS>::bytes, opted_m);
+    k_adj_stage<T, BS, true><<<g1(t.n * AdjCfg<T, BS>::NS), AdjCfg<T, BS>::NT, AdjCfg<T, BS>::bytes, st>>>(a, t, ph, m);
+  } else {
+    smem_opt_in_stage(k_adj_stage<T, BS, false>, AdjCfg<T, BS>::bytes, opted);
+    k_adj_stage<T, BS, false><<<g1(t.n * AdjCfg<T, BS>::NS), AdjCfg<T, BS>::NT, AdjCfg<T, BS>::bytes, st>>>(a, t, ph, m);
+  }
   k_adj_samelevel<T, BS><<<g1(t.n), kNA, 0, st>>>(a, t, ph, err);
   static std::atomic<unsigned long long> opted_h{0};
   smem_opt_in_stage(k_adj_halo<T, BS>, HaloCfg<T, BS>::bytes, opted_h);
