@@ -450,16 +450,71 @@ k_adj_stage(const AdjStageK<T> a, const TopoK tp, const PhysK ph, const MaskK m)
 // reach; then each patch point goes to the leaf holding it.  FP atomics in global memory only:
 // several blocks reach one point.  Runs after k_adj_stage.
 //
+// The face-halo targets of the four components at one tangential point: de[f][l - 1] for the
+// halo layers l = 1..3 beyond a face with normal axis ax (sg: +1 for the upper face, -1 for the
+// lower), from the three source points next to it (po[k]: element offset of the source at normal
+// distance k = 0, 1, 2 inside the face, component 0).  Each source value is read once for all
+// four components.
+template <typename T, int BS>
+__device__ __forceinline__ void face_targets(const AdjStageK<T>& a, const size_t (&po)[3], int ax, T sg, T ih,
+                                             T nu_ih2, T c0sq, const T (&am)[3], T c_lam, T c_nu, T (&de)[4][3]) {
+  using L = Lay<T, BS>;
+  const T d2[2] = {T(16), T(-1)};
+  T kap[4][3], uax[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    uax[k] = a.Y[po[k] + (size_t)ax * L::FS];
+#pragma unroll
+    for (int g = 0; g < 4; ++g) {
+      T kv = c_lam * a.lam[po[k] + (size_t)g * L::FS];
+      if (a.nup) kv += c_nu * a.nup[po[k] + (size_t)g * L::FS];
+      kap[g][k] = kv;
+    }
+  }
+#pragma unroll
+  for (int f = 0; f < 4; ++f) {
+    T Wk[3], Kk[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      if (f < 3) {
+        Kk[k] = kap[f][k];
+        Wk[k] = uax[k] * Kk[k];
+        if (f == ax) Wk[k] += c0sq * kap[3][k];
+      } else {
+        Kk[k] = T(0);
+        Wk[k] = kap[ax][k];
+      }
+    }
+#pragma unroll
+    for (int l = 1; l <= 3; ++l) {
+      T e = T(0), dd = T(0);
+#pragma unroll
+      for (int k = 0; k + l <= 3; ++k) {
+        e += sg * am[l + k - 1] * Wk[k];
+        if (l + k <= 2) dd += d2[l + k - 1] * Kk[k];
+      }
+      de[f][l - 1] = -ih * e + (f < 3 ? nu_ih2 * dd : T(0));
+    }
+  }
+}
+
 // E^T across same-level faces in gather form: block A adds to its own points the face-halo
 // targets of its same-level face neighbours that the forward read from A (the neighbour N's
 // halo point at distance l beyond the shared face is A's point at distance l inside it), each
 // computed from N's sources next to the face as k_adj_halo computes a halo target.  One CTA per
 // block walks its six faces in turn (a point near an edge takes one face's value at a time), so
-// the additions need no atomics; it runs after k_adj_stage and before k_adj_halo's atomics.
+// the additions need no atomics; a thread per tangential point of a face, all four components.
+// It runs after k_adj_stage and before k_adj_halo's atomics.
+template <int BS>
+struct SameCfg {
+  static constexpr int NT = BS * BS <= 1024 ? ((BS * BS + 31) / 32) * 32 : 384;
+};
+
 template <typename T, int BS>
-__global__ void __launch_bounds__(kNA) k_adj_samelevel(const AdjStageK<T> a, const TopoK tp, const PhysK ph, int* err) {
+__global__ void __launch_bounds__(SameCfg<BS>::NT)
+k_adj_samelevel(const AdjStageK<T> a, const TopoK tp, const PhysK ph, int* err) {
   using L = Lay<T, BS>;
-  constexpr int M = L::M;
+  constexpr int M = L::M, NT = SameCfg<BS>::NT;
   __shared__ int types[6], slots[6];
   const int rank = blockIdx.x;
   if (threadIdx.x < 6) {
@@ -475,7 +530,6 @@ __global__ void __launch_bounds__(kNA) k_adj_samelevel(const AdjStageK<T> a, con
   const T nu_ih2 = T(ph.nu / (12.0 * ph.h[bi.x] * ph.h[bi.x]));
   const T c0sq = T(ph.c0sq);
   const T am[3] = {T(ph.a1), T(ph.a2), T(ph.a3)};
-  const T d2[2] = {T(16), T(-1)};
   const T c_lam = T(a.c_lam), c_nu = T(a.c_nu);
   for (int F = 0; F < 6; ++F) {
     if (types[F] != kTypeLeaf) continue;                        // uniform over the CTA
@@ -490,41 +544,24 @@ __global__ void __launch_bounds__(kNA) k_adj_samelevel(const AdjStageK<T> a, con
     // at neighbour coordinate k (this block's upper face) or M - k (its lower face), and its
     // halo stencils take the sign of that face
     const T sg = side ? T(-1) : T(1);
-    for (int t = threadIdx.x; t < 4 * BS * BS; t += kNA) {
-      const int f = t / (BS * BS), uv = t % (BS * BS);
+    for (int uv = threadIdx.x; uv < BS * BS; uv += NT) {
       int p[3] = {0, 0, 0};
       p[o1] = uv % BS;
       p[o2] = uv / BS;
-      T Wk[3], Kk[3];
+      size_t po[3];
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
         p[ax] = side ? k : M - k;
-        const size_t po = nb + L::idx(p[0], p[1], p[2]);
-        auto kappa = [&](int g) -> T {
-          T kv = c_lam * a.lam[po + (size_t)g * L::FS];
-          if (a.nup) kv += c_nu * a.nup[po + (size_t)g * L::FS];
-          return kv;
-        };
-        if (f < 3) {
-          Kk[k] = kappa(f);
-          Wk[k] = a.Y[po + (size_t)ax * L::FS] * Kk[k];
-          if (f == ax) Wk[k] += c0sq * kappa(3);
-        } else {
-          Kk[k] = T(0);
-          Wk[k] = kappa(ax);
-        }
+        po[k] = nb + L::idx(p[0], p[1], p[2]);
       }
+      T de[4][3];
+      face_targets<T, BS>(a, po, ax, sg, ih, nu_ih2, c0sq, am, c_lam, c_nu, de);
 #pragma unroll
       for (int l = 1; l <= 3; ++l) {
-        T de = T(0), dd = T(0);
-#pragma unroll
-        for (int k = 0; k + l <= 3; ++k) {
-          de += sg * am[l + k - 1] * Wk[k];
-          if (l + k <= 2) dd += d2[l + k - 1] * Kk[k];
-        }
-        de = -ih * de + (f < 3 ? nu_ih2 * dd : T(0));
         p[ax] = side ? M - l : l;
-        a.nu[bo + (size_t)f * L::FS + L::idx(p[0], p[1], p[2])] += de;
+        const size_t o = bo + L::idx(p[0], p[1], p[2]);
+#pragma unroll
+        for (int f = 0; f < 4; ++f) a.nu[o + (size_t)f * L::FS] += de[f][l - 1];
       }
     }
     __syncthreads();
@@ -574,7 +611,6 @@ __global__ void __launch_bounds__(kNA) k_adj_halo(const AdjStageK<T> a, const To
   const T nu_ih2 = T(ph.nu / (12.0 * ph.h[bi.x] * ph.h[bi.x]));
   const T c0sq = T(ph.c0sq);
   const T am[3] = {T(ph.a1), T(ph.a2), T(ph.a3)};
-  const T d2[2] = {T(16), T(-1)};
   const T c_lam = T(a.c_lam), c_nu = T(a.c_nu);
   // threads run along the tangential axis with the smaller memory stride (x for y and z faces)
   const int o1 = ax == 0 ? 1 : 0, o2 = 3 - ax - o1;
@@ -627,45 +663,27 @@ __global__ void __launch_bounds__(kNA) k_adj_halo(const AdjStageK<T> a, const To
     // a predicted ghost: kept for the transposed prediction below (each target has one thread)
     hv[((f * 3 + l - 1) * BS + q[o2]) * BS + q[o1]] = de;
   };
-  // a thread per (component, tangential point): the three halo layers from the three sources
-  // next to the face, p_k at normal distance k = 0, 1, 2 inside it (q at layer l reads p_k with
-  // weight a_{l+k}, and its second difference d2_{l+k} for l + k <= 2)
-  for (int t = threadIdx.x; t < 4 * BS * BS; t += kNA) {
-    const int f = t / (BS * BS), uv = t % (BS * BS);
+  // a thread per tangential point, all four components: the three halo layers from the three
+  // sources next to the face, p_k at normal distance k = 0, 1, 2 inside it (q at layer l reads
+  // p_k with weight a_{l+k}, and its second difference d2_{l+k} for l + k <= 2)
+  for (int uv = threadIdx.x; uv < BS * BS; uv += kNA) {
     int q[3] = {0, 0, 0};
     q[o1] = uv % BS;
     q[o2] = uv / BS;
-    T Wk[3], Kk[3];
+    size_t po[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
       int p[3] = {q[0], q[1], q[2]};
       p[ax] = side ? M - k : k;
-      const size_t po = bo + L::idx(p[0], p[1], p[2]);
-      auto kappa = [&](int g) -> T {
-        T kv = c_lam * a.lam[po + (size_t)g * L::FS];
-        if (a.nup) kv += c_nu * a.nup[po + (size_t)g * L::FS];
-        return kv;
-      };
-      if (f < 3) {
-        Kk[k] = kappa(f);
-        Wk[k] = a.Y[po + (size_t)ax * L::FS] * Kk[k];
-        if (f == ax) Wk[k] += c0sq * kappa(3);
-      } else {
-        Kk[k] = T(0);
-        Wk[k] = kappa(ax);
-      }
+      po[k] = bo + L::idx(p[0], p[1], p[2]);
     }
+    T de[4][3];
+    face_targets<T, BS>(a, po, ax, sg, ih, nu_ih2, c0sq, am, c_lam, c_nu, de);
 #pragma unroll
     for (int l = 1; l <= 3; ++l) {
-      T de = T(0), dd = T(0);
-#pragma unroll
-      for (int k = 0; k + l <= 3; ++k) {
-        de += sg * am[l + k - 1] * Wk[k];
-        if (l + k <= 2) dd += d2[l + k - 1] * Kk[k];
-      }
-      de = -ih * de + (f < 3 ? nu_ih2 * dd : T(0));
       q[ax] = side ? M + l : -l;
-      scatter(q, f, l, de);
+#pragma unroll
+      for (int f = 0; f < 4; ++f) scatter(q, f, l, de[f][l - 1]);
     }
   }
   if (!coarse) return;
@@ -924,7 +942,7 @@ void stage(const AdjStageK<T>& a, const TopoK& t, const PhysK& ph, const MaskK& 
     smem_opt_in_stage(k_adj_stage<T, BS, false>, AdjCfg<T, BS>::bytes, opted);
     k_adj_stage<T, BS, false><<<g1(t.n * AdjCfg<T, BS>::NS), AdjCfg<T, BS>::NT, AdjCfg<T, BS>::bytes, st>>>(a, t, ph, m);
   }
-  k_adj_samelevel<T, BS><<<g1(t.n), kNA, 0, st>>>(a, t, ph, err);
+  k_adj_samelevel<T, BS><<<g1(t.n), SameCfg<BS>::NT, 0, st>>>(a, t, ph, err);
   static std::atomic<unsigned long long> opted_h{0};
   smem_opt_in_stage(k_adj_halo<T, BS>, HaloCfg<T, BS>::bytes, opted_h);
   k_adj_halo<T, BS><<<g1(6 * t.n), kNA, HaloCfg<T, BS>::bytes, st>>>(a, t, ph, err);
