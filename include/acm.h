@@ -394,6 +394,11 @@ acm_status acm_refine_all(acm_forest* f);
  * be NULL) receives the block count, *n_passes (may be NULL) the number of merging passes. */
 acm_status acm_coarsen(acm_forest* f, int64_t* n_blocks, int* n_passes);
 
+/* The grid adaptation after a time step (Sec. 3.5 step 3: details -> tags -> tree -> data
+ * moves): acm_coarsen, with the block count as an int (n_blocks may be NULL).  Errors as
+ * acm_coarsen. */
+acm_status acm_adapt(acm_forest* f, int* n_blocks);
+
 /* The paper's time step (Sec. 3.5): refine all, RK4 (dt as in acm_rk4_step), coarsen. */
 acm_status acm_step(acm_forest* f, double dt, double* dt_used, int64_t* n_blocks);
 

@@ -90,6 +90,7 @@ EXPORTS = {
     "acm_refine_all": (C.c_int, [C.c_void_p]),
     "acm_rhs": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int]),
     "acm_coarsen": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int)]),
+    "acm_adapt": (C.c_int, [C.c_void_p, C.POINTER(C.c_int)]),
     "acm_step": (C.c_int, [C.c_void_p, C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
     "acm_block_indicators": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64]),
     "acm_diagnostics": (C.c_int, [C.c_void_p, C.POINTER(Diag)]),
@@ -417,6 +418,12 @@ class Forest:
         n, p = C.c_int64(), C.c_int()
         self._check(self.L.acm_coarsen(self.h, C.byref(n), C.byref(p)))
         return n.value, p.value
+
+    def adapt(self):
+        """The grid adaptation after a step (acm_adapt: coarsening); returns the block count."""
+        n = C.c_int()
+        self._check(self.L.acm_adapt(self.h, C.byref(n)))
+        return n.value
 
     def step(self, dt=0.0):
         d, n = C.c_double(), C.c_int64()

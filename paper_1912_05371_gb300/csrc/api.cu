@@ -1974,6 +1974,13 @@ acm_status acm_coarsen(acm_forest* f, int64_t* n_blocks, int* n_passes) {
   return DISPATCH(f, coarsen, f, n_blocks, n_passes);
 }
 
+acm_status acm_adapt(acm_forest* f, int* n_blocks) {
+  int64_t n = 0;
+  const acm_status st = acm_coarsen(f, &n, nullptr);
+  if (st == ACM_OK && n_blocks) *n_blocks = (int)n;
+  return st;
+}
+
 acm_status acm_step(acm_forest* f, double dt, double* dt_used, int64_t* n_blocks) {
   if (!f) return ACM_EINVAL;
   acm_status s = acm_refine_all(f);

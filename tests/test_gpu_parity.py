@@ -274,6 +274,20 @@ def test_refine_and_coarsen_match_oracle(A, prec):
         assert max(err) < TOL[prec], err
 
 
+def test_adapt_is_the_coarsening(A):
+    """acm_adapt (the adaptation call after a step) leaves the grid and state acm_coarsen leaves."""
+    leaves = random_graded_leaves(15, nroot=(2, 1, 1), J0=1, Jmax=2, n_target=40)
+    grid = _grid(Bs=9, precision=64, Jmax=3)
+    out = []
+    for call in ("coarsen", "adapt"):
+        f, _ = _pair(A, grid, _phys(eps=3e-3), leaves, fn_seed=15)
+        f.refine_all()
+        n = f.coarsen()[0] if call == "coarsen" else f.adapt()
+        out.append((n, f.topology()["treecode"], f.read_fields()))
+    assert out[0][0] == out[1][0]
+    assert np.array_equal(out[0][1], out[1][1]) and np.array_equal(out[0][2], out[1][2])
+
+
 @pytest.mark.parametrize("prec,Bs", [(64, 9), (32, 9), (64, 17), (32, 17)])
 def test_cdf44_coarsen_to_jmin_matches_oracle(A, prec, Bs):
     """Every block tagged (huge threshold): the merges are decided by the grading alone, so the
