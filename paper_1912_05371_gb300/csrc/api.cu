@@ -917,6 +917,38 @@ acm_status coarsen(acm_forest* f, int64_t* n_blocks, int* n_passes) {
     if (s) return s;
     fresh = new_slot;
     ++passes;
+    // With CDF 4/0 the next pass can only merge a sister group whose members are all new parents
+    // or tagged already (the other blocks' indicators are unchanged): when there is none, that
+    // pass would merge nothing, and its indicator evaluation (a launch and a read-back) is skipped.
+    if (!c44) {
+      const double tc = now_ms();
+      std::vector<uint8_t> is_new(ind_slot.size(), 0);
+      for (int32_t sl : fresh) is_new[sl] = 1;
+      auto tagged = [&](size_t r) -> bool {
+        const BoxKey& b = f->order[r];
+        if (f->pp.coarsen_everywhere)
+          return b.J > 0 && f->last_refined.count(BoxKey{b.J - 1, b.x >> 1, b.y >> 1, b.z >> 1}) > 0;
+        if (b.J <= fo.Jmin) return false;
+        if (f->pp.dealias && b.J == fo.Jmax) return true;
+        const int32_t sl = f->blist[r];
+        return ind_slot[sl] < f->pp.eps && !(chr_slot[sl] > f->pp.mask_range_thr);
+      };
+      bool possible = false;
+      const size_t n2 = f->order.size();
+      for (size_t r = 0; r + 7 < n2 && !possible;) {
+        const BoxKey& b = f->order[r];
+        bool grp = b.J > 0 && (b.x & 1) == 0 && (b.y & 1) == 0 && (b.z & 1) == 0;
+        const BoxKey p{b.J - 1, b.x >> 1, b.y >> 1, b.z >> 1};
+        for (int c = 1; c < 8 && grp; ++c) grp = f->order[r + c] == acm::Forest::child(p, c);
+        if (!grp) { ++r; continue; }
+        bool ok = true;
+        for (int c = 0; c < 8 && ok; ++c) ok = is_new[f->blist[r + c]] || tagged(r + c);
+        possible = ok;
+        r += 8;
+      }
+      f->host_tree_ms += now_ms() - tc;
+      if (!possible) break;
+    }
   }
   if (n_blocks) *n_blocks = (int64_t)f->order.size();
   if (n_passes) *n_passes = passes;
