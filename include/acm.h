@@ -298,8 +298,10 @@ acm_status acm_get_tuning(const acm_forest* f, acm_tuning* out);
  * schedule takes the same steps in the same arithmetic, so the result does not depend on it
  * (up to the order of floating-point atomic sums).  ws: caller device buffer of at least
  * acm_adjoint_bytes(f, nsteps, ckpt) bytes (ACM_ENOMEM if smaller): nine registers and the
- * snapshots in the forest's precision, the mask's sensitivity and one FP64 array of
- * n_blocks x 4 x Bs^3 values (all sized for max_blocks).
+ * snapshots in the forest's precision, with ckpt > 0 also the four RK stage states of each of a
+ * segment's min(ckpt, nsteps) - 1 recomputed steps (a recomputed step keeps them for its
+ * adjoint, which then runs without repeating the step), the mask's sensitivity and one FP64
+ * array of n_blocks x 4 x Bs^3 values (all sized for max_blocks).
  * acm_adjoint_bytes returns 0 for an invalid ckpt (0), nsteps outside [1, 2^20] or a refused
  * binomial schedule (see acm_checkpoint_schedule).  The
  * forest's state and time are unchanged on return, also when the sweep stops on an error; the

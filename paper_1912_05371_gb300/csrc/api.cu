@@ -507,8 +507,10 @@ acm_status rk4(acm_forest* f, double dt, double* dt_used, T* const* save = nullp
   const acm::TopoK t = topo(f);
   const int64_t l0 = f->launches;
   for (int s = 1; s <= 4; ++s) {
-    T* in = s == 1 ? U : (s == 2 ? YA : (s == 3 ? YB : YA));
-    T* out = s == 1 ? YA : (s == 2 ? YB : (s == 3 ? YA : U));
+    // with `save` the stages write their outputs (the next stages' inputs) into save[1..3]
+    // themselves, so only U (the first stage's input) is copied
+    T* in = s == 1 ? U : (save ? save[s - 1] : (s == 2 ? YA : (s == 3 ? YB : YA)));
+    T* out = s == 4 ? U : (save ? save[s] : (s == 1 ? YA : (s == 2 ? YB : YA)));
     if (f->timing) CK(cudaEventRecord(f->ev[3 * (s - 1)], f->st));
     // stage 1 looks up the slabs' source points and caches them for stages 2-4 (same grid)
     acm_status st = sync_stage<T>(f, in, s > 1);
@@ -523,8 +525,8 @@ acm_status rk4(acm_forest* f, double dt, double* dt_used, T* const* save = nullp
       CKL();
       ++f->launches;
     }
-    if (save) {
-      acm::launch_copy_blocks<T>(f->gp.Bs, in, save[s - 1], f->d_blist, 1, (int64_t)f->order.size(), f->st);
+    if (save && s == 1) {
+      acm::launch_copy_blocks<T>(f->gp.Bs, in, save[0], f->d_blist, 1, (int64_t)f->order.size(), f->st);
       CKL();
       ++f->launches;
     }
@@ -1145,9 +1147,10 @@ acm_status autotune(acm_forest* f, int* fw_ctas, int* slab_ctas) {
 // FP64 array (n_blocks x 4 x Bs^3: the caller's dL/dU_N coming in, dJ/dU_0 going out) and the 4
 // parameter sums (FP64).
 struct AdjLayout {
-  size_t lam, nu[2], sum, y[4], tape, ck, gchi, dense, theta, total;
+  size_t lam, nu[2], sum, y[4], tape, ck, ys, gchi, dense, theta, total;
   size_t reg;    // bytes of a register in the forest's precision
   int64_t nslots;   // snapshots of the checkpoint schedule (ck: snapshot 0, 1, ...)
+  int64_t nys;      // steps whose four stage states can be kept between an advance and its turn
 };
 
 // policy > 0: equidistant checkpoints every policy steps; policy < 0: binomial checkpointing with
@@ -1166,6 +1169,11 @@ AdjLayout adj_layout(const acm_forest* f, int nsteps, int policy) {
   for (int s = 0; s < 4; ++s) L.y[s] = take(L.reg);
   L.tape = take(L.reg);
   L.ck = take(L.reg * (size_t)L.nslots);
+  // equidistant checkpoints every c steps: a segment's recomputed steps (at most c - 1) keep
+  // their stage states for their turns; binomial schedules never advance a step before its turn
+  const int64_t c = policy > 0 ? std::min<int64_t>(policy, nsteps) : 1;
+  L.nys = c - 1;
+  L.ys = take(L.reg * 4 * (size_t)L.nys);
   L.gchi = take((size_t)f->gp.max_blocks * (size_t)f->lay.FS * f->esz);
   L.dense = take((size_t)f->gp.max_blocks * 4 * (size_t)f->gp.Bs * f->gp.Bs * f->gp.Bs * 8);
   L.theta = take(64);
@@ -1329,9 +1337,29 @@ acm_status adjoint_sweep(acm_forest* f, int nsteps, double dt, int c, double wE,
     hi = k;
     return ACM_OK;
   };
+  // An advance of step k whose next appearance in the schedule is its turn keeps the step's
+  // stage states in a free slot of the stage-state tape (a segment's recomputation, equidistant
+  // checkpoints), and the turn then takes its adjoint without running the step again.
+  std::vector<uint8_t> keep_stages(sched.act.size(), 0);
+  {
+    std::vector<int8_t> next_op((size_t)nsteps, -1);
+    for (size_t i = sched.act.size(); i-- > 0;) {
+      const acm::ckpt::Action& a = sched.act[i];
+      if (a.op != acm::ckpt::ADVANCE && a.op != acm::ckpt::TURN) continue;
+      if (a.arg < 0 || a.arg >= nsteps) continue;
+      if (a.op == acm::ckpt::ADVANCE) keep_stages[i] = next_op[(size_t)a.arg] == acm::ckpt::TURN;
+      next_op[(size_t)a.arg] = a.op;
+    }
+  }
+  std::vector<int64_t> ys_free;
+  for (int64_t q = L.nys - 1; q >= 0; --q) ys_free.push_back(q);
+  std::vector<int64_t> ys_of((size_t)nsteps, -1);
+  auto ys_reg = [&](int64_t q, int st) { return S(L.ys + ((size_t)q * 4 + (size_t)st) * L.reg); };
   // the schedule's actions: snapshots are copies of U; a turn takes step k from U_k with its
-  // stage inputs kept and then the step's adjoint (lam' -> lam)
-  for (const acm::ckpt::Action& act : sched.act) {
+  // stage inputs kept (or finds them kept by the step's advance) and then the step's adjoint
+  // (lam' -> lam)
+  for (size_t ai = 0; ai < sched.act.size(); ++ai) {
+    const acm::ckpt::Action& act = sched.act[ai];
     const int k = act.arg;
     if (act.op == acm::ckpt::STORE || act.op == acm::ckpt::RESTORE) {
       if (k < 0 || k >= L.nslots) return fail(f, ACM_EINVAL, "snapshot index outside the workspace");
@@ -1344,26 +1372,45 @@ acm_status adjoint_sweep(acm_forest* f, int nsteps, double dt, int c, double wE,
     const double tk = t0 + k * dt;
     if (act.op == acm::ckpt::ADVANCE) {
       f->time = tk;                                // a moving mask follows the step's clock
-      if ((s = rk4<T>(f, dt, nullptr))) return s;
+      T* kept[4] = {nullptr, nullptr, nullptr, nullptr};
+      if (keep_stages[ai] && !ys_free.empty()) {
+        const int64_t q = ys_free.back();
+        ys_free.pop_back();
+        ys_of[(size_t)k] = q;
+        for (int st = 0; st < 4; ++st) kept[st] = ys_reg(q, st);
+      }
+      if ((s = rk4<T>(f, dt, nullptr, kept[0] ? kept : nullptr))) return s;
       if ((s = reached(k + 1))) return s;
       continue;
     }
-    CK(copy(U, TAPE));
-    f->time = tk;
-    if ((s = rk4<T>(f, dt, nullptr, Y))) return s;
-    if ((s = reached(k + 1))) return s;
-    if (k == nsteps - 1 && !vjp) objective(U, t0 + nsteps * dt);
+    const int64_t q = ys_of[(size_t)k];
+    T* Ys[4] = {Y[0], Y[1], Y[2], Y[3]};
+    const T* Uk = U;                               // U_k (restored) when the stages were kept
+    if (q >= 0) {
+      for (int st = 0; st < 4; ++st) Ys[st] = ys_reg(q, st);
+    } else {
+      CK(copy(U, TAPE));
+      Uk = TAPE;
+      f->time = tk;
+      if ((s = rk4<T>(f, dt, nullptr, Y))) return s;
+      if ((s = reached(k + 1))) return s;
+      if (k == nsteps - 1 && !vjp) objective(U, t0 + nsteps * dt);
+    }
     // the step's adjoint, RK stages 4, 3, 2, 1 (kappa_4 = dt/6 lam, kappa_3 = dt/3 lam + dt nu_4,
     // kappa_2 = dt/3 lam + dt/2 nu_3, kappa_1 = dt/6 lam + dt/2 nu_2), then
     // lam <- W^T (lam + nu_4 + nu_3 + nu_2 + nu_1)
-    if ((s = astage(Y[3], tk + dt, nullptr, dt / 6.0, 0.0, NUR[0], 0))) return s;
-    if ((s = astage(Y[2], tk + 0.5 * dt, NUR[0], dt / 3.0, dt, NUR[1], 1))) return s;
-    if ((s = astage(Y[1], tk + 0.5 * dt, NUR[1], dt / 3.0, dt / 2.0, NUR[0], 2))) return s;
-    if ((s = astage(Y[0], tk, NUR[0], dt / 6.0, dt / 2.0, NUR[1], 2))) return s;
+    if ((s = astage(Ys[3], tk + dt, nullptr, dt / 6.0, 0.0, NUR[0], 0))) return s;
+    if ((s = astage(Ys[2], tk + 0.5 * dt, NUR[0], dt / 3.0, dt, NUR[1], 1))) return s;
+    if ((s = astage(Ys[1], tk + 0.5 * dt, NUR[1], dt / 3.0, dt / 2.0, NUR[0], 2))) return s;
+    if ((s = astage(Ys[0], tk, NUR[0], dt / 6.0, dt / 2.0, NUR[1], 2))) return s;
     acm::launch_adj_sum3<T>(Bs, LAM, LAM, SUM, NUR[1], f->d_blist, nb, f->st);
     acm::launch_adj_fw_T<T>(Bs, LAM, fwt, f->d_blist, f->d_nbh, nb, f->st);
     f->launches += 2;
-    if (k >= 1 && !vjp) objective(TAPE, tk);
+    if (k >= 1 && !vjp) objective(Uk, tk);
+    if (q >= 0) {
+      ys_free.push_back(q);
+      ys_of[(size_t)k] = -1;
+    }
   }
   if (!plate && f->mask_on && f->mask.kind == 1) {
     acm::launch_adj_theta<T>(Bs, GCHI, f->d_blist, f->d_binfo, nb, f->phk, cur_mask(), TH, f->st);
