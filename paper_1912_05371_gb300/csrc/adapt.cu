@@ -1578,6 +1578,27 @@ __global__ void __launch_bounds__(kNT) k_diag(const T* reg, const T* chi, const 
   }
 }
 
+// Objective terms on the device: acc += wF C_eta^-1 sum_r h_r^3 part[4r] + wE sum_r h_r^3 part[4r+3] / 2
+// over the per-block sums of k_diag (or, with wE = 0, of k_solid_moment), one CTA, each thread's
+// blocks in a fixed order and a fixed reduction tree, so the sum is the same on every call.
+__global__ void __launch_bounds__(1024) k_diag_sum(const double* part, const int4* binfo, int64_t n, const PhysK ph,
+                                                   double wF, double wE, double* acc) {
+  __shared__ double red[1024];
+  double v = 0.0;
+  for (int64_t r = threadIdx.x; r < n; r += blockDim.x) {
+    const double h = ph.h[binfo[r].x];
+    const double h3 = h * h * h;
+    v += wF * part[4 * r] * h3 * ph.inv_ceta + wE * 0.5 * part[4 * r + 3] * h3;
+  }
+  red[threadIdx.x] = v;
+  __syncthreads();
+  for (int o = 512; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *acc += red[0];
+}
+
 // ---- (10) dense <-> pool ---------------------------------------------------------------------------
 template <typename T, int BS>
 __global__ void __launch_bounds__(kNT) k_gather(const T* reg, T* dense, const int32_t* blist, int ncomp, int comp_stride_blk) {
@@ -1786,6 +1807,10 @@ template <typename T>
 void launch_diag(int Bs, const T* reg, const T* chi, const int32_t* blist, int64_t n, double* out, cudaStream_t st) {
   if (n <= 0) return;
   ACM_BS_DISPATCH(Bs, k_diag, <<<grid1(n), kNT, 0, st>>>(reg, chi, blist, out));
+}
+void launch_diag_sum(const double* part, const int4* binfo, int64_t n, const PhysK& p, double wF, double wE,
+                     double* acc, cudaStream_t st) {
+  k_diag_sum<<<1, 1024, 0, st>>>(part, binfo, n, p, wF, wE, acc);
 }
 template <typename T>
 void launch_gather(int Bs, const T* reg, T* dense, const int32_t* blist, int64_t n, int ncomp, cudaStream_t st) {

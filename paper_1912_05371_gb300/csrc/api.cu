@@ -1181,42 +1181,6 @@ AdjLayout adj_layout(const acm_forest* f, int nsteps, int policy) {
   return L;
 }
 
-// F_x and E of the current state (Sec. 2.2), as acm_diagnostics sums them.
-template <typename T>
-acm_status force_energy(acm_forest* f, double* Fx, double* E) {
-  const size_t n = f->order.size();
-  acm::launch_diag<T>(f->gp.Bs, reinterpret_cast<const T*>(f->U),
-                      f->mask_on ? reinterpret_cast<const T*>(f->CHI) : nullptr, f->d_blist, (int64_t)n, f->d_diag,
-                      f->st);
-  CKL();
-  ++f->launches;
-  std::vector<double> part(n * 4);
-  CK(cudaMemcpyAsync(part.data(), f->d_diag, n * 4 * 8, cudaMemcpyDeviceToHost, f->st));
-  CK(cudaStreamSynchronize(f->st));
-  *Fx = 0.0;
-  *E = 0.0;
-  for (size_t r = 0; r < n; ++r) {
-    const double h = h_of(f, f->order[r].J);
-    const double h3 = h * h * h;
-    *Fx += part[4 * r] * h3 / f->pp.C_eta;
-    *E += 0.5 * part[4 * r + 3] * h3;
-  }
-  if (f->moving) {
-    // a moving body's force integrates chi (u - u_s) (pose and mask at the state's time)
-    acm::launch_solid_moment<T>(f->gp.Bs, reinterpret_cast<const T*>(f->CHI), f->d_blist, f->d_binfo, (int64_t)n,
-                                f->phk, f->mask, f->d_diag, f->st);
-    CKL();
-    ++f->launches;
-    CK(cudaMemcpyAsync(part.data(), f->d_diag, n * 4 * 8, cudaMemcpyDeviceToHost, f->st));
-    CK(cudaStreamSynchronize(f->st));
-    for (size_t r = 0; r < n; ++r) {
-      const double h = h_of(f, f->order[r].J);
-      *Fx -= part[4 * r] * h * h * h / f->pp.C_eta;
-    }
-  }
-  return ACM_OK;
-}
-
 template <typename T>
 acm_status adjoint_sweep(acm_forest* f, int nsteps, double dt, int c, double wE, void* ws, size_t ws_bytes,
                          double* J_out, double* dtheta, void* dU0, int64_t n_elems, int on_device, const void* lamN,
@@ -1325,17 +1289,24 @@ acm_status adjoint_sweep(acm_forest* f, int nsteps, double dt, int c, double wE,
     ++f->launches;
   }
   acm_status s;
-  // J's terms are summed when a state is first reached (U_1, ..., U_N in that order)
-  double J = 0.0;
+  // J's terms are summed on the device when a state is first reached (U_1, ..., U_N in that
+  // order), the force and energy as acm_diagnostics sums them (Sec. 2.2), into TH[7]; no host
+  // round trip per step
+  double* JDEV = TH + 7;
   int hi = 0;
   auto reached = [&](int k) -> acm_status {
     if (vjp || k <= hi) return ACM_OK;
-    double Fx, E;
-    const acm_status r = force_energy<T>(f, &Fx, &E);
-    if (r) return r;
-    J += (Fx + wE * E) / nsteps;
+    acm::launch_diag<T>(Bs, U, f->mask_on ? CHI : nullptr, f->d_blist, nb, f->d_diag, f->st);
+    acm::launch_diag_sum(f->d_diag, f->d_binfo, nb, f->phk, 1.0 / nsteps, wE / nsteps, JDEV, f->st);
+    f->launches += 2;
+    if (f->moving) {
+      // a moving body's force integrates chi (u - u_s) (pose and mask at the state's time)
+      acm::launch_solid_moment<T>(Bs, CHI, f->d_blist, f->d_binfo, nb, f->phk, f->mask, f->d_diag, f->st);
+      acm::launch_diag_sum(f->d_diag, f->d_binfo, nb, f->phk, -1.0 / nsteps, 0.0, JDEV, f->st);
+      f->launches += 2;
+    }
     hi = k;
-    return ACM_OK;
+    return cudaGetLastError() == cudaSuccess ? ACM_OK : fail(f, ACM_ECUDA, "objective kernel launch failed");
   };
   // An advance of step k whose next appearance in the schedule is its turn keeps the step's
   // stage states in a free slot of the stage-state tape (a segment's recomputation, equidistant
@@ -1418,6 +1389,8 @@ acm_status adjoint_sweep(acm_forest* f, int nsteps, double dt, int c, double wE,
   }
   CKL();
   CK(cudaMemcpyAsync(dtheta, TH, (plate ? 1 : 4) * sizeof(double), cudaMemcpyDeviceToHost, f->st));
+  double J = 0.0;
+  CK(cudaMemcpyAsync(&J, JDEV, sizeof(double), cudaMemcpyDeviceToHost, f->st));
   // the forest keeps its state, time and mask
   CK(copy(CKP(0), U));
   f->time = t0;

@@ -234,6 +234,10 @@ void launch_solid_moment(int Bs, const T* chi, const int32_t* blist, const int4*
 template <typename T>
 void launch_diag(int Bs, const T* reg, const T* chi, const int32_t* blist, int64_t n,
                  double* out, cudaStream_t st);
+// acc += wF C_eta^-1 sum_r h_r^3 part[4r] + wE sum_r h_r^3 part[4r+3] / 2 over n blocks (part: the
+// per-block sums of launch_diag or launch_solid_moment), on the device, in a fixed order.
+void launch_diag_sum(const double* part, const int4* binfo, int64_t n, const PhysK& p, double wF, double wE,
+                     double* acc, cudaStream_t st);
 
 // Block-order gather/scatter of interiors between the pool and a dense array.
 template <typename T>
