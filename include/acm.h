@@ -259,12 +259,13 @@ acm_status acm_autotune(acm_forest* f, int* fw_ctas, int* slab_ctas);
  * FP32x2 arithmetic (FP32 forests only: fewer instructions, half the resident threads);
  * ACM_STAGE_POINT_TMA, one point per thread with the planes of U, the RK accumulator and the mask
  * brought into a shared-memory ring by mbarrier-tracked bulk copies one plane ahead (FP32 forests
- * only); ACM_STAGE_POINT_ROWS, one point per thread with a block's rows split over two CTAs of 9
- * and 8 rows (FP32, Bs = 17: smaller CTAs, more of them per SM, each reading the other's rows
- * next to its own like a halo).  All compute every point by the same formula; ACM_STAGE_POINT,
- * ACM_STAGE_POINT_TMA and ACM_STAGE_POINT_ROWS give bitwise equal results, ACM_STAGE_PAIR
- * differs in FP32 rounding order.  FP64 forests always use ACM_STAGE_POINT; forests of 33^3
- * blocks always use their row-split form (three CTAs of 11 rows) whatever is set. */
+ * only); ACM_STAGE_POINT_ROWS, one point per thread with a block's rows split over CTAs of 9 rows (FP32,
+ * Bs = 17: two CTAs of 9 and 8 rows; Bs = 33: four of 9, 9, 9 and 6 rows; smaller CTAs, more of
+ * them per SM, each reading the rows next to its own like a halo).  All compute every point by
+ * the same formula; ACM_STAGE_POINT, ACM_STAGE_POINT_TMA and ACM_STAGE_POINT_ROWS give bitwise
+ * equal results, ACM_STAGE_PAIR differs in FP32 rounding order.  FP64 forests always use
+ * ACM_STAGE_POINT; forests of 33^3 blocks use ACM_STAGE_POINT_ROWS or else their three-CTA
+ * form (11 rows each) for ACM_STAGE_POINT, ACM_STAGE_PAIR and ACM_STAGE_POINT_TMA. */
 #define ACM_STAGE_PAIR 0
 #define ACM_STAGE_POINT 1
 #define ACM_STAGE_POINT_TMA 2

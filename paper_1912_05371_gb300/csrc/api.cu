@@ -1115,8 +1115,9 @@ acm_status autotune(acm_forest* f, int* fw_ctas, int* slab_ctas) {
     best = 1e30f;
     int best_v = f->stage_variant;
     for (int v : {acm::kStagePair, acm::kStagePoint, acm::kStagePointTMA, acm::kStagePointRows}) {
-      if (f->gp.Bs == 33 && v != acm::kStagePoint) continue;   // the one form for 33^3 blocks
-      if (v == acm::kStagePointRows && f->gp.Bs != 17) continue;
+      // 33^3 blocks: the row-split point form, three CTAs of 11 rows or four of 9
+      if (f->gp.Bs == 33 && v != acm::kStagePoint && v != acm::kStagePointRows) continue;
+      if (v == acm::kStagePointRows && f->gp.Bs == 9) continue;
       float ms = 0.f;
       acm_status s = time_launches(f, [&]() {
         acm::launch_stage<T>(2, f->gp.Bs, a, t, f->phk, f->d_err, f->st, v);
@@ -2000,8 +2001,9 @@ acm_status acm_get_tuning(const acm_forest* f, acm_tuning* out) {
   if (!f || !out) return ACM_EINVAL;
   out->fw_ctas_per_sm = f->tune_fw_ctas;
   out->slab_ctas_per_sm = f->tune_slab_ctas;
-  out->stage_variant = f->gp.precision == 64 || f->gp.Bs == 33 ||
-                               (f->stage_variant == acm::kStagePointRows && f->gp.Bs != 17)
+  out->stage_variant = f->gp.precision == 64 ||
+                               (f->gp.Bs == 33 && f->stage_variant != acm::kStagePointRows) ||
+                               (f->stage_variant == acm::kStagePointRows && f->gp.Bs == 9)
                            ? ACM_STAGE_POINT
                        : (f->stage_variant == acm::kStagePair ? ACM_STAGE_PAIR
                           : (f->stage_variant == acm::kStagePoint ? ACM_STAGE_POINT

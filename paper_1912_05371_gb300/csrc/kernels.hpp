@@ -120,8 +120,9 @@ void launch_rk_coefs(const unsigned long long* maxbits, const RkK& p, double* rk
 // err: device int set to 1 if a bounded wait inside the kernel expired (never cleared here).
 // variant kStagePair: FP32 fields take the two-points-per-thread kernel (stage_pair.cu);
 // kStagePointTMA: FP32 fields take the one-point kernel with U, the accumulator and chi staged
-// by bulk copies; kStagePointRows: FP32 blocks of 17^3 take the one-point kernel with a block's
-// rows over two CTAs; otherwise, and always for FP64 fields, the one-point kernel (stage.cu).
+// by bulk copies; kStagePointRows: FP32 blocks of 17^3 and 33^3 take the one-point kernel with a
+// block's rows over CTAs of 9 rows; otherwise, and always for FP64 fields, the one-point kernel
+// (stage.cu; 33^3 blocks over three CTAs of 11 rows).
 constexpr int kStagePair = 0, kStagePoint = 1, kStagePointTMA = 2, kStagePointRows = 3;
 template <typename T>
 void launch_stage(int stage, int Bs, const StageK<T>& s, const TopoK& t, const PhysK& p, int* err,

@@ -526,8 +526,9 @@ void launch_stage(int stage, int Bs, const StageK<T>& s, const TopoK& t, const P
   StageK<T> a = s;
   a.kc = stage_constants<T>(p, s.c_acc, s.c_out);
   if constexpr (sizeof(T) == 4) {
-    if (Bs == 33) {              // the point form, rows split over three CTAs
-      launch_stage_bs<T, 33, false>(stage, a, t, p, err, st);
+    if (Bs == 33) {              // the point form, rows split over three CTAs (or four of 9 rows)
+      if (variant == kStagePointRows) launch_stage_bs<T, 33, false, 9>(stage, a, t, p, err, st);
+      else launch_stage_bs<T, 33, false>(stage, a, t, p, err, st);
       return;
     }
     if (variant == kStagePointRows && Bs == 17) {   // a block over two CTAs of 9 and 8 rows

@@ -105,6 +105,22 @@ def test_bs33_rk4_steps_match_oracle(A):
     assert max(err) < 2e-5, err
 
 
+def test_bs33_row_tiles_are_bitwise_equal(A):
+    """The stage kernel's two tiles for 33^3 blocks (three CTAs of 11 rows, four of 9) compute
+    bitwise the same RK4 steps (mask and sponge on, FP32)."""
+    out = []
+    for variant in (A.ACM_STAGE_POINT, A.ACM_STAGE_POINT_ROWS):
+        f = A.Forest(_grid(), _phys())
+        f.set_leaves(LEAVES)
+        f.set_mask(A.ACM_MASK_SPHERE, MASK)
+        f.set_ic(A.ACM_IC_TAYLOR_GREEN, [2.0 * np.pi, 1.0])
+        f.set_stage_variant(variant)
+        for _ in range(2):
+            f.rk4_step(1e-3)
+        out.append(f.read_fields())
+    assert np.array_equal(out[0], out[1])
+
+
 def test_bs33_indicators_match_oracle(A):
     f, S = _pair(A, _grid(), _phys(sponge=0))
     ind, rng = f.block_indicators()
