@@ -75,6 +75,19 @@ def test_bs33_forest_is_fp32_and_cdf40_only(A):
     _same_topology(f, oracle_forest(_grid(), leaves=LEAVES, max_blocks=96))
 
 
+def test_bs33_sync_ghosts_matches_oracle(A):
+    """Every block's extended array (interior and 4 ghost layers, edges and corners included:
+    copies, decimations and DD-4 predictions) against the oracle's synchronisation."""
+    from oracle.sync import sync as osync
+    f, S = _pair(A, _grid(), _phys())
+    gpu = f.sync_ghosts()
+    ext = osync(S.fo, S.U, 4, "cube")
+    ref = np.stack([ext[S.fo.leaves[l]] for l in S.fo.sorted_leaves()])
+    assert not np.isnan(ref).any()
+    err = rel_linf(gpu.astype(np.float64), ref)
+    assert max(err) < 1e-6, err
+
+
 def test_bs33_mask_matches_oracle(A):
     f, S = _pair(A, _grid(), _phys())
     chi = f.read_mask().astype(np.float64)
