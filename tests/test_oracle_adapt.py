@@ -28,6 +28,29 @@ def _interior_field(S):
     return {leaf: S.U[s].copy() for leaf, s in S.fo.leaves.items()}
 
 
+def test_refine_predicts_cubics_exactly_with_33_cubed_blocks():
+    """Refinement of 33^3 blocks (the full-scale case's block size) is exact on cubics too: eight
+    roots, one of them refined once, all refined again."""
+    C = cubic_coefficients(12)
+    leaves = [(0, x, y, z) for z in range(2) for y in range(2) for x in range(2) if (x, y, z) != (1, 1, 1)]
+    leaves += [(1, 2 + (c & 1), 2 + ((c >> 1) & 1), 2 + ((c >> 2) & 1)) for c in range(8)]
+    fo = Forest(nroot=(2, 2, 2), root_len=1.0, Bs=33, Jmin=0, Jmax=2, max_blocks=160)
+    fo.set_leaves(leaves)
+    S = Solver(fo, acm.Physics(), ic=lambda X, Y, Z: _poly(C, X, Y, Z), eps=1e3, dealias=False)
+    S.eval_ic()
+    S.eval_mask()
+    S.refine_all()
+    assert len(fo.leaves) == 7 * 8 + 8 * 8 and fo.is_graded()
+    nchk = 0
+    for leaf, s in fo.leaves.items():
+        X, Y, Z = acm.block_coords(fo, leaf)
+        if min(X.min(), Y.min(), Z.min()) < 0.3 or max(X.max(), Y.max(), Z.max()) > 1.7:
+            continue                    # the parent's stencils would cross the periodic seam
+        assert np.abs(S.U[s] - _poly(C, X, Y, Z)).max() < 1e-11
+        nchk += 1
+    assert nchk > 10
+
+
 def test_refine_predicts_cubics_exactly_and_coarsen_restores():
     C = cubic_coefficients(11)
     leaves = random_graded_leaves(4, nroot=(2, 2, 2), J0=1, Jmax=2, n_target=80)

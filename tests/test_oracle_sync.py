@@ -76,6 +76,36 @@ def test_adaptive_ghosts_reproduce_cubics(seed):
     assert not np.isnan(ext[sorted(fo.leaves.values())]).any()
 
 
+def test_ghosts_reproduce_cubics_with_33_cubed_blocks():
+    """The same exactness for blocks of 33^3 (the full-scale case's block size): two roots, the
+    second refined once, so that a level-0 block meets level-1 blocks across the root faces."""
+    leaves = [(0, 0, 0, 0)] + [(1, 2 + (c & 1), (c >> 1) & 1, (c >> 2) & 1) for c in range(8)]
+    fo = Forest(nroot=(2, 1, 1), root_len=1.0, Bs=33, max_blocks=16)
+    fo.set_leaves(leaves)
+    C = cubic_coefficients(33)
+    F = _fill(fo, lambda X, Y, Z: _poly(C, X, Y, Z))
+    g = 4
+    ext = sync(fo, F, g)
+    M = fo.M
+    checked = 0
+    for leaf, s in fo.leaves.items():
+        J = leaf[0]
+        h = fo.h(J)
+        N = fo.npoints(J)
+        r = np.arange(-g, M + g + 1)
+        gi = [leaf[1 + a] * M + r for a in range(3)]
+        inside = [(v >= 10) & (v <= N[a] - 10) for a, v in enumerate(gi)]
+        mz, my, mx = np.meshgrid(inside[2], inside[1], inside[0], indexing="ij")
+        m = mz & my & mx
+        if not m.any():
+            continue
+        Z, Y, X = np.meshgrid(gi[2] * h, gi[1] * h, gi[0] * h, indexing="ij")
+        assert np.abs(ext[s] - _poly(C, X, Y, Z))[:, m].max() < 1e-12
+        checked += 1
+    assert checked == 9
+    assert not np.isnan(ext[sorted(fo.leaves.values())]).any()
+
+
 def test_fine_wins_and_redundancy():
     leaves = random_graded_leaves(7, nroot=(1, 1, 1), J0=1, Jmax=3, n_target=60)
     fo = Forest(nroot=(1, 1, 1), Bs=9, max_blocks=4096)
