@@ -841,6 +841,8 @@ def main():
                     help="wavelet of the main line: 40 = CDF 4/0 (default), 44 = CDF 4/4")
     ap.add_argument("--adjoint-only", action="store_true",
                     help="run only the adjoint workload (and its at-scale case) and print its JSON")
+    ap.add_argument("--fullscale-only", action="store_true",
+                    help="run only the full-scale plate case and print its JSON")
     ap.add_argument("--sweep", action="store_true",
                     help="run the random-grid performance study (Sec. 5.4) instead of the benchmark")
     ap.add_argument("--sweep-blocks", default="1000,2000,4000,8000,16000,24000")
@@ -853,6 +855,14 @@ def main():
         if not any(a.startswith("--steps") for a in sys.argv[1:]):
             args.steps = 15
         return random_grid_sweep(args)
+    if args.fullscale_only:
+        import torch
+        from paper_1912_05371_gb300 import acm as A
+        stream = torch.cuda.Stream()
+        with torch.cuda.stream(stream):
+            out = fullscale_plate(A, stream)
+        print(json.dumps({"fullscale": out}))
+        return 0
     if args.adjoint_only:
         import torch
         from paper_1912_05371_gb300 import acm as A
