@@ -87,6 +87,35 @@ __device__ __forceinline__ BoxPoint box_point(const MaskK& m, double rx, double 
   return o;
 }
 
+// A float estimate of the box's signed distance at offset r (the distance part of box_point, in
+// float): it decides which points are so far from the surface that tanh(d/delta) is +-1 in the
+// field precision (exactly in FP64 beyond 19.1 delta), where d chi/dtheta vanishes and chi is 0
+// (outside) or 1 (inside), and the FP64 distance and tanh need not be evaluated.
+__device__ __forceinline__ float box_distance_f(const MaskK& m, float rx, float ry, float rz) {
+  float n2 = 0.f, qmax = -1e30f;
+  for (int k = 0; k < 3; ++k) {
+    const float xb = (float)m.p[k] * rx + (float)m.p[3 + k] * ry + (float)m.p[6 + k] * rz;
+    const float q = fabsf(xb - (float)m.p[12 + k]) - (float)m.p[15 + k];
+    if (q > 0.f) n2 += q * q;
+    qmax = fmaxf(qmax, q);
+  }
+  return sqrtf(n2) + fminf(qmax, 0.f);
+}
+// d u_s/dtheta = (d omega/dtheta) x r, as box_point computes it.
+__device__ __forceinline__ void box_dus(const MaskK& m, double rx, double ry, double rz, double (&dus)[3]) {
+  const double* dw = m.p + 33;
+  dus[0] = dw[1] * rz - dw[2] * ry;
+  dus[1] = dw[2] * rx - dw[0] * rz;
+  dus[2] = dw[0] * ry - dw[1] * rx;
+}
+// Beyond this distance from the surface the box's chi is exactly 0 or 1 and its derivative 0
+// (FP64: tanh rounds to +-1 beyond 19.1 delta; FP32 fields: tanhf beyond 9.1 delta, the FP64
+// derivative left out there is below 1e-8 of its value at the surface).
+template <typename T>
+__device__ __forceinline__ double box_far(const MaskK& m) {
+  return (sizeof(T) == 8 ? 20.0 : 10.0) * m.p[18];
+}
+
 // Block reduction of one double per thread of an NT-thread CTA into *out (one atomic per CTA).
 template <int NT>
 __device__ __forceinline__ void block_add_n(double v, double* out) {
@@ -405,16 +434,28 @@ k_adj_stage(const AdjStageK<T> a, const TopoK tp, const PhysK ph, const MaskK m)
       }
       const T u = qy[0][3], v = qy[1][3], w = qy[2][3];
       if constexpr (MOVING) {
-        const BoxPoint bp = box_point(m, lattice_coord(ph, bi, 0, x, M, hd) - m.p[9],
-                                      lattice_coord(ph, bi, 1, y, M, hd) - m.p[10],
-                                      lattice_coord(ph, bi, 2, z, M, hd) - m.p[11]);
-        const double kk[3] = {(double)k0, (double)k1, (double)k2}, uu[3] = {(double)u, (double)v, (double)w};
-        double gc = 0.0, gu = 0.0;
-        for (int i = 0; i < 3; ++i) {
-          gc -= kk[i] * (uu[i] - bp.us[i]) * ph.inv_ceta;     // d/dchi of -chi (u - u_s) / C_eta
-          gu += (double)chiv * kk[i] * ph.inv_ceta * bp.dus[i]; // d/du_s, times d u_s / dtheta
-        }
-        dth += gc * bp.dchi + gu;
+        const double rx = lattice_coord(ph, bi, 0, x, M, hd) - m.p[9];
+        const double ry = lattice_coord(ph, bi, 1, y, M, hd) - m.p[10];
+        const double rz = lattice_coord(ph, bi, 2, z, M, hd) - m.p[11];
+        const double kk[3] = {(double)k0, (double)k1, (double)k2};
+        const float df = box_distance_f(m, (float)rx, (float)ry, (float)rz);
+        const double far = box_far<T>(m);
+        if (df < -far) {
+          // inside, away from the surface: chi = 1 and d chi = 0, only d u_s/dtheta acts
+          double dus[3], gu = 0.0;
+          box_dus(m, rx, ry, rz, dus);
+          for (int i = 0; i < 3; ++i) gu += (double)chiv * kk[i] * ph.inv_ceta * dus[i];
+          dth += gu;
+        } else if (!(df > far)) {
+          const BoxPoint bp = box_point(m, rx, ry, rz);
+          const double uu[3] = {(double)u, (double)v, (double)w};
+          double gc = 0.0, gu = 0.0;
+          for (int i = 0; i < 3; ++i) {
+            gc -= kk[i] * (uu[i] - bp.us[i]) * ph.inv_ceta;     // d/dchi of -chi (u - u_s) / C_eta
+            gu += (double)chiv * kk[i] * ph.inv_ceta * bp.dus[i]; // d/du_s, times d u_s / dtheta
+          }
+          dth += gc * bp.dchi + gu;
+        }                                                       // outside, far: no term
       } else if (ph.mask && a.gchi) {
         a.gchi[(size_t)slot * L::FS + pi] -= (k0 * u + k1 * v + k2 * w) * inv_ceta;
       }
@@ -841,10 +882,19 @@ __global__ void __launch_bounds__(kNA) k_adj_objective(const T* U, const T* chi,
     for (int f = 1; f < 3; ++f) lam[own + (size_t)f * L::FS + pi] += a_e * U[own + (size_t)f * L::FS + pi];
     if (moving) {
       const double u = (double)uT, c = (double)cT;
-      const BoxPoint bp = box_point(m, lattice_coord(ph, bi, 0, x, M, h) - m.p[9],
-                                    lattice_coord(ph, bi, 1, y, M, h) - m.p[10],
-                                    lattice_coord(ph, bi, 2, z, M, h) - m.p[11]);
-      dth += wN * h3 * ph.inv_ceta * ((u - bp.us[0]) * bp.dchi - c * bp.dus[0]);
+      const double rx = lattice_coord(ph, bi, 0, x, M, h) - m.p[9];
+      const double ry = lattice_coord(ph, bi, 1, y, M, h) - m.p[10];
+      const double rz = lattice_coord(ph, bi, 2, z, M, h) - m.p[11];
+      const float df = box_distance_f(m, (float)rx, (float)ry, (float)rz);
+      const double far = box_far<T>(m);
+      if (df < -far) {                          // chi = 1, d chi = 0: the u_s term only
+        double dus[3];
+        box_dus(m, rx, ry, rz, dus);
+        dth += wN * h3 * ph.inv_ceta * (0.0 - c * dus[0]);
+      } else if (!(df > far)) {
+        const BoxPoint bp = box_point(m, rx, ry, rz);
+        dth += wN * h3 * ph.inv_ceta * ((u - bp.us[0]) * bp.dchi - c * bp.dus[0]);
+      }
     } else if (ph.mask) {
       gchi[(size_t)slot * L::FS + pi] += a_chi * uT;
     }

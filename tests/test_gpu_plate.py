@@ -69,11 +69,13 @@ def test_moving_plate_steps_match_oracle(A, oracle_run, prec):
     assert abs(d["energy"] - E) <= ftol * E
 
 
-@pytest.mark.parametrize("ckpt", [dict(ckpt_every=1), dict(snapshots=1)])
-def test_moving_plate_adjoint_matches_oracle(A, ckpt):
-    """The gradient of the moving case with respect to the pitch amplitude (FP64, 8 blocks of 9^3,
-    2 steps) against the oracle's adjoint, which is pinned by central differences; equidistant
-    checkpoints, or binomial checkpointing with U_0 as the only snapshot."""
+@pytest.mark.parametrize("ckpt,prec", [(dict(ckpt_every=1), 64), (dict(snapshots=1), 64), (dict(ckpt_every=2), 32)])
+def test_moving_plate_adjoint_matches_oracle(A, ckpt, prec):
+    """The gradient of the moving case with respect to the pitch amplitude (8 blocks of 9^3, 2
+    steps) against the oracle's adjoint, which is pinned by central differences: FP64 with
+    equidistant checkpoints or binomial checkpointing with U_0 as the only snapshot, to rounding;
+    FP32 (states, adjoint variables and the box's per-point sensitivity in FP32, the sums onto the
+    parameter in FP64) within the FP32 rounding of the mask's signed distance."""
     from oracle.forest import Forest as OForest
     from oracle.plate import MovingPlateAdjoint
     from tests.test_gpu_adjoint import _per_point
@@ -88,7 +90,8 @@ def test_moving_plate_adjoint_matches_oracle(A, ckpt):
     S.eval_mask()
     dt, n = 2e-3, 2
     Jo, gUo, gao = MovingPlateAdjoint(S, dt, n, checkpoint_every=1).gradient(S.U.copy())
-    grid = dict(nroot=(1, 1, 1), root_len=1.0, Bs=9, g=4, Jmin=1, Jmax=1, precision=64, max_blocks=16, fd_scheme=1)
+    grid = dict(nroot=(1, 1, 1), root_len=1.0, Bs=9, g=4, Jmin=1, Jmax=1, precision=prec, max_blocks=16,
+                fd_scheme=1)
     f = A.Forest(grid, dict(nu=1e-2, c0=3.0, C_eta=1e-2, C_gamma=0.5, cfl=0.5))
     f.init_uniform(1)
     f.write_fields(block_order_fields(S))
@@ -99,9 +102,11 @@ def test_moving_plate_adjoint_matches_oracle(A, ckpt):
     assert np.array_equal(f.read_fields(), before) and f.diagnostics()["time"] == 0.0
     go = np.stack([gUo[fo.leaves[l]] for l in fo.sorted_leaves()])
     a, b = _per_point(fo, gU, 1), _per_point(fo, go, 1)
-    assert abs(J - Jo) <= 1e-12 * abs(Jo), (J, Jo)
-    assert abs(ga - gao) <= 1e-10 * abs(gao), (ga, gao)
-    assert np.abs(a - b).max() <= 1e-10 * np.abs(b).max()
+    tol_J, tol_g = (1e-12, 1e-10) if prec == 64 else (1e-5, 1e-4)
+    print(f"plate adjoint FP{prec}: J {J} vs {Jo}, dJ/dalpha_m {ga} vs {gao}")
+    assert abs(J - Jo) <= tol_J * abs(Jo), (J, Jo)
+    assert abs(ga - gao) <= tol_g * abs(gao), (ga, gao)
+    assert np.abs(a - b).max() <= tol_g * np.abs(b).max()
 
 
 def test_moving_plate_vjp_matches_oracle(A):
