@@ -674,9 +674,11 @@ struct RefSmem {
 };
 
 // Tensor DD-4 prediction at local point (gx, gy, gz) from the even lattice -4..M+4 in ev
-// (NEV points per axis): z outer, then y, then x.
+// (NEV points per axis; or a window of it starting at even index (bx, by, bz)): z outer, then
+// y, then x.
 template <typename T, int NEV>
-__device__ __forceinline__ T predict_from_even(const T* ev, int gx, int gy, int gz) {
+__device__ __forceinline__ T predict_from_even(const T* ev, int gx, int gy, int gz, int bx = 0, int by = 0,
+                                               int bz = 0) {
   const int p[3] = {gx, gy, gz};
   const T w[4] = {T(-1) / T(16), T(9) / T(16), T(9) / T(16), T(-1) / T(16)};
   const int o4[4] = {-3, -1, 1, 3};
@@ -684,13 +686,13 @@ __device__ __forceinline__ T predict_from_even(const T* ev, int gx, int gy, int 
   for (int a = 0; a < 3; ++a) cnt[a] = (p[a] & 1) ? 4 : 1;
   T accz = T(0);
   for (int kz = 0; kz < cnt[2]; ++kz) {
-    const int zz = ((cnt[2] == 4 ? gz + o4[kz] : gz) + 4) >> 1;
+    const int zz = (((cnt[2] == 4 ? gz + o4[kz] : gz) + 4) >> 1) - bz;
     T accy = T(0);
     for (int ky = 0; ky < cnt[1]; ++ky) {
-      const int yy = ((cnt[1] == 4 ? gy + o4[ky] : gy) + 4) >> 1;
+      const int yy = (((cnt[1] == 4 ? gy + o4[ky] : gy) + 4) >> 1) - by;
       T accx = T(0);
       for (int kx = 0; kx < cnt[0]; ++kx) {
-        const int xx = ((cnt[0] == 4 ? gx + o4[kx] : gx) + 4) >> 1;
+        const int xx = (((cnt[0] == 4 ? gx + o4[kx] : gx) + 4) >> 1) - bx;
         accx = accx + (cnt[0] == 4 ? w[kx] : T(1)) * ev[(zz * NEV + yy) * NEV + xx];
       }
       accy = accy + (cnt[1] == 4 ? w[ky] : T(1)) * accx;
@@ -852,6 +854,7 @@ struct RefBigSmem {
   static constexpr int M = BS - 1;
   static constexpr int NEV = M / 2 + 5;             // even lattice per axis: -4..M+4
   static constexpr int NP = M / 2 + 3;              // samples per axis one child uses
+  static constexpr int NW = M / 4 + 5;              // the even points one child's predictions read
   static constexpr int SUB = NP * NP * NP;
   static constexpr int EQ = (NEV * NEV * NEV > NP * NP * BS) ? NEV * NEV * NEV : NP * NP * BS;
   static constexpr int QY = NP * BS * BS;
@@ -863,10 +866,10 @@ __global__ void __launch_bounds__(RefBigSmem<T, BS>::NT, 1)
 k_refine_child(const T* src, T* dst, const int32_t* tasks, const int32_t* blist, const int32_t* nbh_all) {
   using L = Lay<T, BS>;
   using S = RefBigSmem<T, BS>;
-  constexpr int M = L::M, NEV = S::NEV, NP = S::NP, NT = S::NT;
+  constexpr int M = L::M, NW = S::NW, NP = S::NP, NT = S::NT;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sub = reinterpret_cast<T*>(smem_raw);
-  T* eq = sub + S::SUB;                         // even lattice ev, later the x-pass qx
+  T* eq = sub + S::SUB;                         // the child's window of the even lattice, later qx
   T* qy = eq + S::EQ;
   int* nbh = reinterpret_cast<int*>(qy + S::QY);
   const int tid = threadIdx.x;
@@ -880,9 +883,13 @@ k_refine_child(const T* src, T* dst, const int32_t* tasks, const int32_t* blist,
   for (int i = tid; i < kNbhStride; i += NT) nbh[i] = nbh_all[(size_t)prank * kNbhStride + i];
   __syncthreads();
   const int coarser = __syncthreads_or(tid < 27 && tid != 13 && (nbh[kNbhType + tid] & 15) == kTypeCoarser);
+  // the even points within 3 of the child's samples: local o - 3 .. o + NP + 2, even index
+  // b .. b + NW - 1 with b = (o - 3 + 4) / 2 (0 or M/4)
+  const int bw[3] = {(o[0] + 1) >> 1, (o[1] + 1) >> 1, (o[2] + 1) >> 1};
   if (coarser) {
-    for (int i = tid; i < NEV * NEV * NEV; i += NT) {
-      const int ex = 2 * (i % NEV) - 4, ey = 2 * ((i / NEV) % NEV) - 4, ez = 2 * (i / (NEV * NEV)) - 4;
+    for (int i = tid; i < NW * NW * NW; i += NT) {
+      const int ex = 2 * (bw[0] + i % NW) - 4, ey = 2 * (bw[1] + (i / NW) % NW) - 4,
+                ez = 2 * (bw[2] + i / (NW * NW)) - 4;
       long long off;
       if (ex >= 0 && ex <= M && ey >= 0 && ey <= M && ez >= 0 && ez <= M)
         off = (long long)pslot * L::BLK + (long long)f * L::FS + L::idx(ex, ey, ez);
@@ -899,7 +906,7 @@ k_refine_child(const T* src, T* dst, const int32_t* tasks, const int32_t* blist,
       v = pb[L::idx(gx, gy, gz)];
     } else {
       const long long off = direct_offset<T, BS>(nbh, gx, gy, gz, f);
-      v = off >= 0 ? src[off] : predict_from_even<T, NEV>(eq, gx, gy, gz);
+      v = off >= 0 ? src[off] : predict_from_even<T, NW>(eq, gx, gy, gz, bw[0], bw[1], bw[2]);
     }
     sub[i] = v;
   }
