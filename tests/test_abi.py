@@ -70,3 +70,36 @@ def test_host_only_argument_checks(libpath):
     assert L.acm_set_time(None, 0.0) == einval
     assert L.acm_write_mask(None, None, 0, 0) == einval
     assert L.acm_load_state(None, b"missing.acm") == einval and L.acm_save_state(None, b"x.acm") == einval
+
+
+def test_pool_limits_of_the_33_cubed_blocks(libpath):
+    """Blocks of 33^3 take FP32 fields and the CDF 4/0 merge only, and every block size keeps the
+    element offsets of a register and of the coarse-face slab buffer within 32 bits: the largest
+    accepted max_blocks holds fewer than 2^32 elements in one register of four components, and
+    not far fewer (the full-scale plate's 29,000 blocks of 33^3 fit)."""
+    from paper_1912_05371_gb300 import acm
+    L = acm.lib()
+    g = acm.GridParams()
+    g.nroot = (ctypes.c_int * 3)(1, 1, 1)
+    g.root_len, g.Bs, g.g, g.Jmin, g.Jmax, g.precision, g.max_blocks, g.fd_scheme = 8.0, 33, 4, 2, 7, 32, 29000, 1
+
+    def size(**kw):
+        for k, v in kw.items():
+            setattr(g, k, v)
+        return L.acm_pool_bytes(ctypes.byref(g))
+
+    assert size(precision=32, wavelet=40) > 29000 * 4 * 4 * 33 ** 3 * 4     # four RK registers
+    assert size(wavelet=0) == size(wavelet=40)
+    assert size(wavelet=44) == 0 and size(wavelet=40, precision=64) == 0
+    for Bs, prec in ((9, 32), (17, 32), (17, 64), (33, 32)):
+        lo, hi = 1, 1 << 30
+        g.precision, g.Bs, g.wavelet = prec, Bs, 40
+        assert size(max_blocks=lo) > 0
+        while hi - lo > 1:                  # the largest accepted max_blocks
+            mid = (lo + hi) // 2
+            if size(max_blocks=mid) > 0:
+                lo = mid
+            else:
+                hi = mid
+        assert lo * 4 * Bs ** 3 < 1 << 32, (Bs, prec, lo)
+        assert lo > 0.9 * (1 << 32) / (4 * (Bs + 2) ** 3), (Bs, prec, lo)  # not far below the cap
