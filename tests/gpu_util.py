@@ -91,3 +91,40 @@ def sponge_fn(phys):
 def sphere_fn(params):
     cx, cy, cz, R, delta = params
     return lambda X, Y, Z: oacm.sphere_mask(X, Y, Z, (cx, cy, cz), R, delta)
+
+
+def uniform_neighbourhood(get, nb, gx, gy, gz, M, r):
+    """The level-J lattice values around block (gx, gy, gz) of a uniform periodic grid of nb
+    blocks per axis, r <= M points beyond each face: (4, M + 1 + 2r, ...)^3, indexed (f, z, y,
+    x); get(gx, gy, gz) gives a block's (4, M + 1, M + 1, M + 1) values."""
+    big = np.empty((4,) + (3 * M + 1,) * 3)
+    for dz in (-1, 0, 1):
+        for dy in (-1, 0, 1):
+            for dx in (-1, 0, 1):
+                b = get((gx + dx) % nb[0], (gy + dy) % nb[1], (gz + dz) % nb[2])
+                z0, y0, x0 = (dz + 1) * M, (dy + 1) * M, (dx + 1) * M
+                big[:, z0:z0 + M + 1, y0:y0 + M + 1, x0:x0 + M + 1] = b
+    return big[:, M - r:2 * M + r + 1, M - r:2 * M + r + 1, M - r:2 * M + r + 1]
+
+
+def rk4_on_neighbourhood(E, M, h, ph, dt):
+    """One classical RK4 step (Sec. 2.3) of one block of a uniform periodic grid without mask or
+    sponge, from its state E widened by 12 points per side (four stages times the 3-point reach
+    of the stencils): the stages' right-hand sides are the oracle's block right-hand side over
+    the block widened by 9, 6, 3 and 0 points.  On such a grid every ghost value of the oracle
+    solver's step is a neighbour's value, so this is that step on the block."""
+    g = 3
+
+    def U(r):
+        o = 12 - r
+        n = M + 1 + 2 * r
+        return E[:, o:o + n, o:o + n, o:o + n]
+
+    def inner(K, r):
+        return K[:, r:K.shape[1] - r, r:K.shape[2] - r, r:K.shape[3] - r]
+
+    K1 = oacm.rhs_block(E, g, M + 18, h, ph)
+    K2 = oacm.rhs_block(U(9) + 0.5 * dt * K1, g, M + 12, h, ph)
+    K3 = oacm.rhs_block(U(6) + 0.5 * dt * K2, g, M + 6, h, ph)
+    K4 = oacm.rhs_block(U(3) + dt * K3, g, M, h, ph)
+    return U(0) + dt / 6.0 * (inner(K1, 9) + 2.0 * inner(K2, 6) + 2.0 * inner(K3, 3) + K4)

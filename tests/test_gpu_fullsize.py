@@ -137,3 +137,83 @@ def test_full_size_sphere_cdf44_parents_match_oracle(A):
     post_U = f.read_fields().astype(np.float64)
     assert len(post_leaves) < len(pre_leaves)
     assert check_cdf44_parents(grid, pre_leaves, pre_U, post_leaves, post_U) >= 1
+
+
+def test_full_size_33_cubed_offsets_past_2_31_rk4_step_matches_oracle(A):
+    """Blocks of 33^3 in slots whose element offsets pass 2^31, as in the full-scale plate case
+    (up to 29,000 blocks of 33^3, 4.2e9 elements per register): a uniform periodic grid of 16,384
+    blocks (box 4x1x1, level 4, 589 M points, a 56 GB pool) with a smooth state that differs
+    between the four roots, one RK4 step through the stage kernels; sampled blocks -- the two
+    highest slots, the slots around the first one whose block starts past 2^31 elements, and
+    the first slot, whose -x neighbour across the periodic seam is in the last root -- against
+    the oracle's step on their neighbourhood."""
+    import math
+
+    import torch
+
+    from tests.gpu_util import oracle_physics, rk4_on_neighbourhood, uniform_neighbourhood
+    Bs, J, nroot = 33, 4, (4, 1, 1)
+    M = Bs - 1
+    grid = dict(nroot=nroot, root_len=1.0, Bs=Bs, g=4, Jmin=J, Jmax=J, precision=32, max_blocks=16400,
+                fd_scheme=1)
+    phys = dict(nu=1e-2, c0=10.0, C_gamma=1.0, cfl=0.5)
+    f = A.Forest(grid, phys)
+    f.init_uniform(J)
+    t = f.topology()
+    n = len(t["slot"])
+    assert n == 16384
+    nb = tuple(r << J for r in nroot)
+    h = 1.0 / ((1 << J) * M)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    # a few Fourier modes of the box 4x1x1 (seeded), plus one of period 4 in x, at x = i h with i
+    # the wrapped global lattice index, built on the device
+    rng = np.random.default_rng(71)
+    modes = [[(rng.integers(-2, 3, 3), rng.uniform(0.2, 1.0), rng.uniform(0, 2 * math.pi)) for _ in range(3)]
+             for _ in range(4)]
+    Lb = [float(r) for r in nroot]
+    i = torch.arange(Bs, device=dev, dtype=torch.float64)
+    gxyz = [torch.as_tensor(t[k].astype(np.int64), device=dev) for k in ("gx", "gy", "gz")]
+    U0 = torch.empty((n, 4, Bs, Bs, Bs), dtype=torch.float32, device=dev)
+    for c0 in range(0, n, 1024):
+        sl = slice(c0, min(n, c0 + 1024))
+        X, Y, Z = (((g[sl, None] * M + i) % (nb[a] * M)) * h for a, g in enumerate(gxyz))
+        X, Y, Z = X[:, None, None, :], Y[:, None, :, None], Z[:, :, None, None]
+        for fc in range(4):
+            v = 0.3 * torch.sin(2 * math.pi * X / Lb[0])
+            for k, a, ph in modes[fc]:
+                v = v + a * torch.sin(2 * math.pi * (int(k[0]) * X / Lb[0] + int(k[1]) * Y / Lb[1]
+                                                     + int(k[2]) * Z / Lb[2]) + ph)
+            U0[sl, fc] = v.to(torch.float32)
+    f.write_fields(U0)
+    dt = 5e-5
+    f.rk4_step(dt)
+    U1 = torch.empty_like(U0)
+    f.read_fields(out=U1)
+    torch.cuda.synchronize()
+
+    slot = t["slot"].astype(np.int64)
+    past = -(-(1 << 31) // (4 * Bs ** 3))   # a register's block stride is at least 4 Bs^3 elements
+    assert slot.max() >= past + 1
+    by_slot = {int(s): b for b, s in enumerate(slot)}
+    by_xyz = {(int(t["gx"][b]), int(t["gy"][b]), int(t["gz"][b])): b for b in range(n)}
+    cache = {}
+
+    def get(x, y, z):
+        b = by_xyz[(x, y, z)]
+        if b not in cache:
+            cache[b] = U0[b].double().cpu().numpy()
+        return cache[b]
+
+    ph = oracle_physics(phys)
+    got, ref, moved = [], [], 0.0
+    for s in (n - 1, n - 2, past - 1, past, past + 1, 0):
+        b = by_slot[s]
+        xyz = (int(t["gx"][b]), int(t["gy"][b]), int(t["gz"][b]))
+        E = uniform_neighbourhood(get, nb, *xyz, M, 12)
+        ref.append(rk4_on_neighbourhood(E, M, h, ph, dt))
+        got.append(U1[b].double().cpu().numpy())
+        moved = max(moved, float(np.abs(ref[-1] - get(*xyz)).max()))
+    err = rel_linf(np.stack(got), np.stack(ref))
+    print("33^3 blocks past 2^31 elements: RK4 step rel. Linf per field", err, "largest change", moved)
+    assert max(err) < 2e-5, err
+    assert moved > 1e-3                     # the step changed the state well above the tolerance

@@ -289,3 +289,26 @@ def test_pulse_ring_combines_both_fields():
     F = acm.ic_pulse_ring(X, Y, Z, pulse, ring, L)
     assert np.array_equal(F[:3], acm.ic_vortex_ring(X, Y, Z, *ring, L)[:3])
     assert np.array_equal(F[3], acm.ic_pulse(X, Y, Z, *pulse, L)[3])
+
+
+def test_rk4_on_a_widened_block_is_the_solver_step():
+    """The sampled full-size parity check's reference: on a uniform periodic grid (no mask or
+    sponge) one RK4 step of a block computed from its neighbourhood, the stages' right-hand
+    sides over the block widened by 9, 6, 3 and 0 points, is bitwise the oracle solver's step
+    (whose ghosts are the neighbours' values)."""
+    from tests.gpu_util import (fill_from_function, oracle_forest, oracle_solver, rk4_on_neighbourhood,
+                                smooth_field, uniform_neighbourhood)
+    grid = dict(nroot=(2, 1, 1), root_len=1.0, Bs=17, Jmin=2, Jmax=2)
+    phys = dict(nu=1e-2, c0=10.0, C_gamma=1.0, cfl=0.5)
+    fo = oracle_forest(grid, J=2, max_blocks=128)
+    S = oracle_solver(fo, phys)
+    fill_from_function(S, lambda X, Y, Z: smooth_field(X, Y, Z, (2.0, 1.0, 1.0), 3))
+    U0 = S.U.copy()
+    dt = 2e-4
+    S.rk4(dt)
+    M, h = fo.M, fo.h(2)
+    for b in ((0, 0, 0), (7, 3, 3), (3, 1, 2)):
+        E = uniform_neighbourhood(lambda x, y, z: U0[fo.leaves[(2, x, y, z)]], (8, 4, 4), *b, M, 12)
+        r = rk4_on_neighbourhood(E, M, h, acm.Physics(nu=1e-2, c0=10.0, C_gamma=1.0), dt)
+        assert np.array_equal(r, S.U[fo.leaves[(2,) + b]])
+        assert np.abs(r - U0[fo.leaves[(2,) + b]]).max() > 0.1
