@@ -1140,11 +1140,12 @@ acm_status autotune(acm_forest* f, int* fw_ctas, int* slab_ctas) {
   return ACM_OK;
 }
 
-// ---- discrete adjoint of RK4 steps on the frozen grid (FP64 forests) ------------------------------
+// ---- discrete adjoint of RK4 steps on the frozen grid (FP32 and FP64 forests) --------------------
 // Workspace (caller-provided, 256-byte aligned regions), all adjoint registers in the forest's
 // precision and indexed like its registers: lam, the nu of two consecutive RK stages, the running
 // sum of the stage nus, the 4 stage states of the step being differentiated, the step's starting
-// state, the snapshots of the checkpoint schedule, the mask sensitivity (one component), a dense
+// state, the snapshots of the checkpoint schedule, the 4 stage states of each recomputed step of
+// an equidistant segment (kept for its turn), the mask sensitivity (one component), a dense
 // FP64 array (n_blocks x 4 x Bs^3: the caller's dL/dU_N coming in, dJ/dU_0 going out) and the 4
 // parameter sums (FP64).
 struct AdjLayout {
